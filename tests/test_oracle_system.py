@@ -1,0 +1,161 @@
+"""Pins of the oracle's whole discretisation (CPU only): sphere series,
+admittance sphere, interior monopole, reciprocity, Burton-Miller at an
+interior eigenfrequency, GMRES against a library solve."""
+import numpy as np
+import pytest
+
+import oracle
+from closed_forms import monopole, sphere_plane_wave
+from paper_2312_00005_gb300 import inputs
+
+C, RHO, A = 343.0, 1.21, 0.1
+PLANE_Z = [("plane", (0.0, 0.0, 1.0), 1.0)]
+
+
+@pytest.fixture(scope="module")
+def sphere1280():
+    return inputs.icosphere(3, A)
+
+
+def _relerr(a, b):
+    e = np.abs(a - b) / np.abs(b)
+    return e.max(), e.mean()
+
+
+def test_sound_hard_sphere_series(sphere1280):
+    """Sound-hard sphere, plane wave along +z, 1 kHz (ka = 1.83), N = 1280:
+    the surface pressure at the collocation points against the series
+    (evaluated at r = a at each centroid's polar angle), and the field on a
+    1 m sphere."""
+    nodes, tris = sphere1280
+    f = 1000.0
+    k = 2 * np.pi * f / C
+    p, q, info = oracle.solve(nodes, tris, f, sources=PLANE_Z)
+    assert info["converged"] and info["relres"] <= 1e-8
+    assert np.all(q == 0)
+    cen, nrm, area = oracle.geometry(nodes, tris)
+    mx, mean = _relerr(p, sphere_plane_wave(cen, k, A))
+    assert mx < 0.03 and mean < 0.008
+    pts = inputs.fibonacci_sphere(100, 1.0)
+    pf = oracle.field(nodes, tris, f, p, q, pts, sources=PLANE_Z)
+    mx, mean = _relerr(pf, sphere_plane_wave(pts, k, A))
+    assert mx < 1e-3
+
+
+def test_discretisation_error_falls_with_mesh_size():
+    """Error ~ 1/sqrt(N) (Sec. 5.1.2): 1280 -> 5120 roughly halves it."""
+    f = 1000.0
+    k = 2 * np.pi * f / C
+    means = []
+    for lev in (3, 4):
+        nodes, tris = inputs.icosphere(lev, A)
+        p, q, info = oracle.solve(nodes, tris, f, sources=PLANE_Z)
+        cen, _, _ = oracle.geometry(nodes, tris)
+        means.append(_relerr(p, sphere_plane_wave(cen, k, A))[1])
+    assert means[1] < means[0] / 1.5
+
+
+def test_admittance_sphere_series(sphere1280):
+    """Uniform admittance, beta = rho c Y = 0.3 + 0.2i: pins the sign reading
+    q = -i k beta p of the admittance condition."""
+    nodes, tris = sphere1280
+    n = tris.shape[0]
+    f = 1000.0
+    k = 2 * np.pi * f / C
+    beta = 0.3 + 0.2j
+    bct = np.full(n, oracle.ADMI, np.int32)
+    p, q, info = oracle.solve(nodes, tris, f, sources=PLANE_Z, bc_type=bct, beta=np.full(n, beta))
+    cen, _, _ = oracle.geometry(nodes, tris)
+    mx, mean = _relerr(p, sphere_plane_wave(cen, k, A, beta=beta))
+    assert mx < 0.03 and mean < 0.012
+    assert np.allclose(q, -1j * k * beta * p)
+    # the opposite sign convention is far off
+    wrong = sphere_plane_wave(cen, k, A, beta=-beta)
+    assert _relerr(p, wrong)[1] > 5 * mean
+    pts = inputs.fibonacci_sphere(50, 1.0)
+    pf = oracle.field(nodes, tris, f, p, q, pts, sources=PLANE_Z)
+    assert _relerr(pf, sphere_plane_wave(pts, k, A, beta=beta))[0] < 1e-3
+
+
+@pytest.mark.parametrize("kind", ["velo", "admi+velo", "pres"])
+def test_interior_monopole_reproduces_free_field(sphere1280, kind):
+    """A point source inside the closed surface, no incident field: the
+    exterior solution equals the free-field monopole (velocity, mixed
+    admittance + velocity, and pressure boundary data)."""
+    nodes, tris = sphere1280
+    n = tris.shape[0]
+    f = 1000.0
+    k, omega = 2 * np.pi * f / C, 2 * np.pi * f
+    x0 = np.array([0.02, -0.01, 0.03])
+    cen, nrm, _ = oracle.geometry(nodes, tris)
+    G, grad = monopole(cen, x0, k)
+    qn = np.einsum("ij,ij->i", grad, nrm)
+    beta = 0.25 - 0.1j
+    if kind == "velo":
+        p, q, info = oracle.solve(nodes, tris, f, bc_value=qn / (1j * omega * RHO))
+    elif kind == "admi+velo":
+        g = qn + 1j * k * beta * G
+        p, q, info = oracle.solve(nodes, tris, f, bc_type=np.full(n, oracle.ADMI),
+                                  beta=np.full(n, beta), bc_value=g / (1j * omega * RHO))
+    else:
+        p, q, info = oracle.solve(nodes, tris, f, bc_type=np.full(n, oracle.PRES), bc_value=G)
+    assert info["converged"]
+    if kind != "pres":
+        assert _relerr(p, G)[1] < 0.025
+    else:
+        assert np.mean(np.abs(q - qn)) / np.mean(np.abs(qn)) < 0.04
+    pts = inputs.fibonacci_sphere(40, 0.5)
+    pf = oracle.field(nodes, tris, f, p, q, pts)
+    Gf, _ = monopole(pts, x0, k)
+    assert _relerr(pf, Gf)[0] < 0.05
+
+
+def test_reciprocity(sphere1280):
+    """Sound-hard sphere, point sources at A and B outside: p_B(source at A)
+    equals p_A(source at B) within the discretisation error."""
+    nodes, tris = sphere1280
+    f = 1200.0
+    XA = np.array([0.3, 0.1, -0.2]); XB = np.array([-0.15, 0.25, 0.4])
+    pA, qA, _ = oracle.solve(nodes, tris, f, sources=[("point", XA, 1.0)])
+    pB, qB, _ = oracle.solve(nodes, tris, f, sources=[("point", XB, 1.0)])
+    vAB = oracle.field(nodes, tris, f, pA, qA, XB[None, :], sources=[("point", XA, 1.0)])[0]
+    vBA = oracle.field(nodes, tris, f, pB, qB, XA[None, :], sources=[("point", XB, 1.0)])[0]
+    scat = abs(vAB - oracle.incident(XB[None, :], None, 2 * np.pi * f / C, "point", XA)[0][0])
+    assert abs(vAB - vBA) < 0.02 * scat
+
+
+def test_burton_miller_at_interior_eigenfrequency(sphere1280):
+    """ka = pi is an interior Dirichlet eigenvalue of the sphere; the
+    Burton-Miller system stays uniquely solvable there (Sec. 2.5)."""
+    nodes, tris = sphere1280
+    f = C / (2 * A)                      # k a = pi
+    k = 2 * np.pi * f / C
+    p, q, info = oracle.solve(nodes, tris, f, sources=PLANE_Z)
+    assert info["converged"] and info["iterations"] < 80
+    cen, _, _ = oracle.geometry(nodes, tris)
+    assert _relerr(p, sphere_plane_wave(cen, k, A))[1] < 0.01
+
+
+def test_gmres_and_matvecs_against_library(sphere1280):
+    nodes, tris = sphere1280
+    n = tris.shape[0]
+    k = 2 * np.pi * 1500.0 / C
+    rng = np.random.default_rng(3)
+    bct = rng.integers(0, 3, n).astype(np.int32)
+    beta = rng.uniform(0, 0.5, n) * np.exp(1j * rng.uniform(-1.5, 1.5, n))
+    cp, cq, _, _ = oracle.column_coeffs(bct, k, C, RHO, beta)
+    A_ = oracle.assemble(nodes, tris, k, cp, cq)
+    x = inputs.random_complex(n, 11)
+    y = oracle.matvec_dense(A_, x)
+    assert np.allclose(y, A_ @ x, rtol=1e-12, atol=0)
+    rows = np.array([0, 17, 640, n - 1])
+    yr = oracle.matvec_rows(nodes, tris, k, cp, cq, x, rows)
+    assert np.allclose(yr, y[rows], rtol=1e-12, atol=1e-12 * np.abs(y).max())
+    b = inputs.random_complex(n, 12)
+    xs, info = oracle.gmres(A_, b, tol=1e-10)
+    ref = np.linalg.solve(A_, b)
+    assert info["converged"]
+    assert np.linalg.norm(xs - ref) < 1e-8 * np.linalg.norm(ref)
+    # GMRES reports non-convergence when capped (cf. the CGS warning, Sec. 3.2)
+    xs, info = oracle.gmres(A_, b, tol=1e-12, maxit=3)
+    assert not info["converged"] and info["iterations"] == 3
