@@ -1,0 +1,200 @@
+/*
+ * bemfmm.h -- C ABI of the GB300 (sm_103a) collocation BEM + fast multipole
+ * matrix-vector product for the 3D Helmholtz equation.
+ *
+ * Method: Kreuzer, Pollack, Brinkmann, Majdak, "NumCalc: An open-source BEM
+ * code for solving acoustic scattering problems", arXiv 2312.00005.
+ *   - constant elements on flat triangles, collocation at the element
+ *     midpoints (Sec. 2.2, 2.3);
+ *   - exterior problem (tau = 1) with Burton-Miller coupling gamma = i/k,
+ *     Eq. SystemI;
+ *   - near field by the quadrature of Sec. 3.1 (Duffy singular rule,
+ *     edge-integral hypersingular rule, subdivision while r~ < 1.3, regular
+ *     order from the a-priori estimates, m <= 6);
+ *   - far field by the plane-wave expansion of Eq. FMMBase with the
+ *     truncation of Eq. FMMTruncation and the admissibility of
+ *     Eq. Farfieldcond, per level (Sec. 3.3.4: operator
+ *     N + sum_l S(l) D(l) T(l)).
+ *
+ * Variables are pressures: p on the surface and q = dp/dn = i w rho v, with
+ * n the outward normal (pointing into the fluid, App. A) and time factor
+ * e^{-i w t}.  Complex numbers are interleaved (re, im): float2 ("cf32") on
+ * the device, double[2] on the host.
+ *
+ * Ownership: every entry point copies what it needs from host arrays before
+ * it returns.  Device buffers passed in belong to the caller and must hold the
+ * stated number of elements; the library never frees them.  Work is
+ * enqueued on the caller's CUDA stream (a cudaStream_t passed as void*;
+ * NULL = the legacy default stream) and is stream-ordered.  bem_solve,
+ * bem_matvec_host and bem_mesh_stats synchronise the stream before they
+ * return; bem_matvec and bem_evaluate do not.
+ *
+ * Errors: every function returns BEM_OK (0), a negative error code, or a
+ * positive warning code with all outputs written.  bem_last_error() gives a
+ * message for the calling thread's last non-zero status.  A mesh handle is
+ * not thread-safe: one thread at a time per mesh.
+ */
+#ifndef BEMFMM_H
+#define BEMFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define BEM_OK                 0
+#define BEM_E_ARG             -1  /* invalid argument */
+#define BEM_E_SUBDIV_LIMIT    -2  /* more than max_depth nested subdivisions (Sec. 4.1); the
+                                     message names the element */
+#define BEM_E_CUDA            -3  /* a CUDA call failed */
+#define BEM_E_OOM             -4  /* device allocation failed */
+#define BEM_E_TIMEOUT         -5  /* a device loop exhausted its iteration budget */
+#define BEM_E_INTERNAL        -6
+#define BEM_W_NOT_CONVERGED    1  /* GMRES stopped at max_iter above tol (cf. Sec. 3.2 warning) */
+#define BEM_W_UNDERRESOLVED    2  /* mean edge longer than a sixth of the wavelength (Sec. 2.2) */
+
+/* boundary condition per element (App. A, App. C.3); VELO with v = 0 is
+ * sound hard and is the default */
+#define BEM_VELO 0  /* normal particle velocity v given            */
+#define BEM_PRES 1  /* pressure p given                             */
+#define BEM_ADMI 2  /* admittance Y of the element's region (velocity into the wall = Y p),
+                       plus an optional extra normal velocity        */
+
+#define BEM_MODE_FMM    0  /* near field by quadrature + plane-wave FMM far field */
+#define BEM_MODE_DIRECT 1  /* every pair by quadrature (conventional BEM)          */
+
+#define BEM_SRC_PLANE 0    /* p = P0 e^{ik d.x}, d a unit direction (App. C.4)     */
+#define BEM_SRC_POINT 1    /* p = P0 e^{ikR}/(4 pi R), R = |x - x0| (Eq. PointSrc) */
+
+typedef struct bem_params {
+    int32_t mode;           /* BEM_MODE_FMM (default) or BEM_MODE_DIRECT                      */
+    double  quad_tol;       /* a-priori quadrature tolerance, 1e-3 (Sec. 3.1.4)                */
+    int32_t m_max;          /* cap on the regular order, 6 (Sec. 3.1.4), 1..6                  */
+    double  rt_subdiv;      /* subdivide while r~ < rt_subdiv, 1.3 (Sec. 3.1.3)                */
+    int32_t max_depth;      /* subdivision limit, 15 (Sec. 4.1)                                */
+    double  trunc_factor;   /* factor of Eq. FMMTruncation, 1.8                                */
+    int32_t L_min;          /* lower bound of the expansion length, 8 (Eq. FMMTruncation)      */
+    double  admissibility;  /* far if |z_i - z_j| > admissibility (r_i + r_j); 2/sqrt(3)        */
+    double  leaf_edge;      /* leaf box edge in metres; 0 = chosen from the mesh               */
+    double  stability_max;  /* far only if sum_n (2n+1)|h_n(kX)| / |h_0(kX)| <= this, 1e3     */
+    int32_t near_store;     /* 1: store near-field entries per frequency (default);
+                               0: recompute them inside every product                         */
+    int32_t restart;        /* GMRES restart length, 100                                       */
+} bem_params;
+
+typedef struct bem_medium {
+    double c;    /* speed of sound, m/s (343 if <= 0) */
+    double rho;  /* density, kg/m^3 (1.21 if <= 0)    */
+} bem_medium;
+
+typedef struct bem_source {
+    int32_t kind;    /* BEM_SRC_PLANE or BEM_SRC_POINT                    */
+    double  vec[3];  /* unit direction (plane) or position in m (point)   */
+    double  amp[2];  /* complex amplitude P0 in Pa (re, im)               */
+} bem_source;
+
+typedef struct bem_solve_info {
+    int32_t iterations;       /* matrix-vector products in GMRES              */
+    int32_t restarts;
+    double  relres;           /* final ||b - A u|| / ||b|| (GMRES estimate)    */
+    double  seconds;          /* wall time of the call                         */
+    int32_t levels;           /* FMM levels with interaction lists             */
+    int32_t L[16];            /* expansion length per used level, finest last  */
+    int64_t near_nnz;         /* stored near-field entries                     */
+    int32_t status;           /* same as the return value                      */
+} bem_solve_info;
+
+typedef struct bem_plan_stats {
+    int64_t n_elements;
+    int32_t leaf_level;         /* octree depth of the leaves                          */
+    int32_t levels;             /* levels with interaction lists                       */
+    int32_t level_depth[16];    /* octree depth of each used level, coarse to fine     */
+    int32_t L[16];              /* expansion length per used level                     */
+    int32_t n_clusters[16];     /* clusters per used level                             */
+    int64_t n_interactions[16]; /* interaction-list entries per used level             */
+    int32_t n_offsets[16];      /* distinct translation offsets per used level         */
+    int32_t n_leaves;
+    int64_t near_nnz;           /* near-field element pairs (with the diagonal)        */
+    int64_t near_quad_points;   /* quadrature points summed over the near pairs        */
+    double  leaf_edge;          /* metres                                              */
+    double  mean_edge;          /* mean element edge length, metres                    */
+    int64_t device_bytes;       /* device memory held by the mesh and this plan        */
+    int64_t far_pairs;          /* element pairs covered by the interaction lists;
+                                   near_nnz + far_pairs = n_elements^2                  */
+} bem_plan_stats;
+
+/* Paper defaults (Sec. 3.1, Eq. FMMTruncation, Eq. Farfieldcond). */
+void bem_params_default(bem_params *p);
+
+/* Create a mesh (App. A): nodes [n_nodes][3] in metres, tris [n_tris][3]
+ * 0-based node indices in counter-clockwise order seen from the fluid
+ * (outward normal; not checked, Sec. 2.1).  bc_type [n_tris] (NULL = all
+ * BEM_VELO), bc_value [n_tris][2] complex (NULL = 0): p for PRES, v for
+ * VELO, the extra velocity for ADMI.  region [n_tris] (NULL = 0) selects the
+ * admittance entry of ADMI elements.  params NULL = defaults.  Geometry,
+ * clustering and the frequency-independent plan are built here, and the
+ * mesh is copied to the current CUDA device.  *out receives the handle. */
+int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tris,
+                    const int32_t *bc_type, const double *bc_value, const int32_t *region,
+                    const bem_params *params, void **out);
+
+int bem_mesh_destroy(void *mesh);
+
+/* y = A x for n_rhs right-hand sides (Eq. SystemI, tau = 1), where A is the
+ * Burton-Miller matrix in the unknowns u (p on VELO / ADMI elements, q on
+ * PRES elements) with the boundary conditions folded in: column j enters as
+ * p_j = c^p_j u_j and q_j = c^q_j u_j with (c^p, c^q) = (1, 0) for VELO,
+ * (1, -ik rho c Y) for ADMI and (0, 1) for PRES.
+ * x_dev, y_dev: device cf32 [n_rhs][n_tris] in the caller's element order.
+ * admittance: host double [n_regions][2] (Y in m/(Pa s)); may be NULL when
+ * no element is ADMI.  Builds (or reuses) the plan for this frequency. */
+int bem_matvec(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
+               int32_t n_regions, const void *x_dev, void *y_dev, int32_t n_rhs, void *stream);
+
+/* As bem_matvec with host buffers x_host, y_host (cf32 [n_rhs][n_tris]):
+ * copies in, multiplies, copies out, synchronises. */
+int bem_matvec_host(void *mesh, double freq_hz, const bem_medium *medium,
+                    const double *admittance, int32_t n_regions, const void *x_host,
+                    void *y_host, int32_t n_rhs, void *stream);
+
+/* Solve Eq. SystemI at one frequency for the incident field of n_src
+ * sources and the mesh's boundary data, with restarted GMRES on the device
+ * (FP64 orthogonalisation and Givens rotations; FP32 products).  Writes the
+ * surface pressure p_dev and q_dev = dp/dn (device cf32 [n_tris] each, caller
+ * order; q_dev may be NULL).  tol: relative residual target (e.g. 1e-6).
+ * max_iter: cap on products.  info may be NULL.  Returns BEM_OK,
+ * BEM_W_NOT_CONVERGED (outputs hold the last iterate), or an error. */
+int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
+              int32_t n_regions, const bem_source *srcs, int32_t n_src, double tol,
+              int32_t max_iter, void *p_dev, void *q_dev, bem_solve_info *info, void *stream);
+
+/* Total pressure at M exterior points (Eq. BIE_I with lambda = 1):
+ * p(x) = p_inc(x) + sum_j [H(x)_j p_j - G(x)_j q_j], element integrals by
+ * the regular / quasi-singular rules measured from x.  p_dev, q_dev: device
+ * cf32 [n_tris] (caller order, as written by bem_solve).  pts: host double
+ * [M][3].  out_dev: device cf32 [M]. */
+int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem_source *srcs,
+                 int32_t n_src, const void *p_dev, const void *q_dev, const double *pts,
+                 int64_t M, void *out_dev, void *stream);
+
+/* Plan statistics for a frequency (builds the plan if needed). */
+int bem_mesh_stats(void *mesh, double freq_hz, const bem_medium *medium, bem_plan_stats *out);
+
+/* The same statistics computed on the host only (no CUDA call): geometry,
+ * clustering and the near / interaction lists of Sec. 3.3.4 for the given
+ * frequency and speed of sound.  device_bytes is 0. */
+int bem_plan_stats_host(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tris,
+                        const bem_params *params, double freq_hz, double c, bem_plan_stats *out);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t bem_launch_count(void);
+
+/* Message of the calling thread's last non-zero status ("" if none). */
+const char *bem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BEMFMM_H */

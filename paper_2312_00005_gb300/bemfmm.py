@@ -1,0 +1,300 @@
+"""Thin ctypes binding of the C ABI in ``include/bemfmm.h``.
+
+Argument marshalling only: every step of the BEM + FMM path runs in the CUDA
+library ``_bemfmm.so`` built from ``csrc/``.  PyTorch supplies device memory
+(complex64 CUDA tensors) and streams.  Importing this module loads the
+library and raises if it is missing; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "VELO", "PRES", "ADMI", "MODE_FMM", "MODE_DIRECT", "BemError", "Params", "Medium", "Source",
+    "SolveInfo", "PlanStats", "Mesh", "lib", "launch_count", "plane_wave", "point_source",
+]
+
+VELO, PRES, ADMI = 0, 1, 2
+MODE_FMM, MODE_DIRECT = 0, 1
+SRC_PLANE, SRC_POINT = 0, 1
+OK, W_NOT_CONVERGED, W_UNDERRESOLVED = 0, 1, 2
+E_SUBDIV_LIMIT = -2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_bemfmm.so")
+
+
+class BemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("bemfmm error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_int32), ("quad_tol", ctypes.c_double), ("m_max", ctypes.c_int32),
+        ("rt_subdiv", ctypes.c_double), ("max_depth", ctypes.c_int32), ("trunc_factor", ctypes.c_double),
+        ("L_min", ctypes.c_int32), ("admissibility", ctypes.c_double), ("leaf_edge", ctypes.c_double),
+        ("stability_max", ctypes.c_double), ("near_store", ctypes.c_int32), ("restart", ctypes.c_int32),
+    ]
+
+
+class Medium(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double), ("rho", ctypes.c_double)]
+
+
+class Source(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("vec", ctypes.c_double * 3), ("amp", ctypes.c_double * 2)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32), ("relres", ctypes.c_double),
+        ("seconds", ctypes.c_double), ("levels", ctypes.c_int32), ("L", ctypes.c_int32 * 16),
+        ("near_nnz", ctypes.c_int64), ("status", ctypes.c_int32),
+    ]
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [
+        ("n_elements", ctypes.c_int64), ("leaf_level", ctypes.c_int32), ("levels", ctypes.c_int32),
+        ("level_depth", ctypes.c_int32 * 16), ("L", ctypes.c_int32 * 16), ("n_clusters", ctypes.c_int32 * 16),
+        ("n_interactions", ctypes.c_int64 * 16), ("n_offsets", ctypes.c_int32 * 16), ("n_leaves", ctypes.c_int32),
+        ("near_nnz", ctypes.c_int64), ("near_quad_points", ctypes.c_int64), ("leaf_edge", ctypes.c_double),
+        ("mean_edge", ctypes.c_double), ("device_bytes", ctypes.c_int64), ("far_pairs", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        n = self.levels
+        return {
+            "n_elements": self.n_elements, "leaf_level": self.leaf_level, "levels": n,
+            "level_depth": list(self.level_depth[:n]), "L": list(self.L[:n]),
+            "n_clusters": list(self.n_clusters[:n]), "n_interactions": list(self.n_interactions[:n]),
+            "n_offsets": list(self.n_offsets[:n]), "n_leaves": self.n_leaves, "near_nnz": self.near_nnz,
+            "near_quad_points": self.near_quad_points, "leaf_edge": self.leaf_edge,
+            "mean_edge": self.mean_edge, "device_bytes": self.device_bytes, "far_pairs": self.far_pairs,
+        }
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_SO):
+            raise ImportError("bemfmm CUDA library not built (%s missing): run "
+                              "`python -m paper_2312_00005_gb300.build`" % _SO)
+        L = ctypes.CDLL(_SO)
+        P, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "bem_params_default": (None, [ctypes.POINTER(Params)]),
+            "bem_mesh_create": (ctypes.c_int, [P, i64, P, i64, P, P, P, ctypes.POINTER(Params), ctypes.POINTER(P)]),
+            "bem_mesh_destroy": (ctypes.c_int, [P]),
+            "bem_matvec": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), P, i32, P, P, i32, P]),
+            "bem_matvec_host": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), P, i32, P, P, i32, P]),
+            "bem_solve": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), P, i32, ctypes.POINTER(Source), i32, d, i32,
+                                         P, P, ctypes.POINTER(SolveInfo), P]),
+            "bem_evaluate": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), ctypes.POINTER(Source), i32, P, P, P,
+                                            i64, P, P]),
+            "bem_mesh_stats": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), ctypes.POINTER(PlanStats)]),
+            "bem_plan_stats_host": (ctypes.c_int, [P, i64, P, i64, ctypes.POINTER(Params), d, d,
+                                                   ctypes.POINTER(PlanStats)]),
+            "bem_launch_count": (ctypes.c_uint64, []),
+            "bem_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def launch_count() -> int:
+    return int(lib().bem_launch_count())
+
+
+def _check(code, allow_warn=True):
+    if code < 0 or (code > 0 and not allow_warn):
+        raise BemError(code, lib().bem_last_error().decode(errors="replace"))
+    return code
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().bem_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def plane_wave(direction=(0.0, 0.0, 1.0), amp=1.0 + 0.0j) -> Source:
+    s = Source()
+    s.kind = SRC_PLANE
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    s.vec[:] = list(d)
+    s.amp[:] = [complex(amp).real, complex(amp).imag]
+    return s
+
+
+def point_source(position, amp=1.0 + 0.0j) -> Source:
+    s = Source()
+    s.kind = SRC_POINT
+    s.vec[:] = [float(v) for v in position]
+    s.amp[:] = [complex(amp).real, complex(amp).imag]
+    return s
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, n=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous complex64 CUDA tensor")
+    if n is not None and t.numel() < n:
+        raise ValueError("tensor too small: %d < %d" % (t.numel(), n))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _admittance(adm):
+    if adm is None:
+        return None, 0
+    a = np.asarray(adm, dtype=np.complex128).reshape(-1)
+    buf = np.ascontiguousarray(np.stack([a.real, a.imag], axis=1))
+    return buf, a.shape[0]
+
+
+def plan_stats_host(nodes, tris, freq, c=343.0, params=None) -> dict:
+    """Clustering and near / interaction lists for a frequency, built on the
+    host only (no GPU needed)."""
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    p = params if params is not None else default_params()
+    st = PlanStats()
+    _check(lib().bem_plan_stats_host(nodes.ctypes.data_as(ctypes.c_void_p), nodes.shape[0],
+                                     tris.ctypes.data_as(ctypes.c_void_p), tris.shape[0], ctypes.byref(p),
+                                     float(freq), float(c), ctypes.byref(st)))
+    return st.as_dict()
+
+
+class Mesh:
+    """A surface mesh on the current CUDA device (App. A of the paper)."""
+
+    def __init__(self, nodes, tris, bc_type=None, bc_value=None, region=None, params=None, **kw):
+        L = lib()
+        self._nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+        self._tris = np.ascontiguousarray(tris, dtype=np.int32)
+        self.n = self._tris.shape[0]
+        bt = None if bc_type is None else np.ascontiguousarray(bc_type, dtype=np.int32)
+        bv = None
+        if bc_value is not None:
+            v = np.asarray(bc_value, dtype=np.complex128).reshape(-1)
+            bv = np.ascontiguousarray(np.stack([v.real, v.imag], axis=1))
+        rg = None if region is None else np.ascontiguousarray(region, dtype=np.int32)
+        p = params if params is not None else default_params(**kw)
+        self.params = p
+        h = ctypes.c_void_p()
+        ptr = (lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p))
+        _check(L.bem_mesh_create(ptr(self._nodes), self._nodes.shape[0], ptr(self._tris), self.n, ptr(bt), ptr(bv),
+                                 ptr(rg), ctypes.byref(p), ctypes.byref(h)), allow_warn=False)
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().bem_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _medium(c, rho):
+        return Medium(float(c), float(rho))
+
+    def matvec(self, freq, x, y=None, admittance=None, c=343.0, rho=1.21, stream=None):
+        """y = A x (Eq. SystemI in the unknowns u); x: complex64 CUDA tensor
+        [n] or [n_rhs, n] in the caller's element order."""
+        import torch
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        if y is None:
+            y = torch.empty_like(x)
+        adm, nreg = _admittance(admittance)
+        med = self._medium(c, rho)
+        code = lib().bem_matvec(self._h, float(freq), ctypes.byref(med),
+                                None if adm is None else adm.ctypes.data_as(ctypes.c_void_p), nreg,
+                                _dptr(x, nrhs * self.n), _dptr(y, nrhs * self.n), nrhs, _stream_ptr(stream))
+        _check(code)
+        return y
+
+    def matvec_host(self, freq, x, admittance=None, c=343.0, rho=1.21):
+        """As matvec with host arrays (copies inside the call)."""
+        xh = np.ascontiguousarray(np.asarray(x, dtype=np.complex64))
+        yh = np.empty_like(xh)
+        nrhs = 1 if xh.ndim == 1 else xh.shape[0]
+        adm, nreg = _admittance(admittance)
+        med = self._medium(c, rho)
+        _check(lib().bem_matvec_host(self._h, float(freq), ctypes.byref(med),
+                                     None if adm is None else adm.ctypes.data_as(ctypes.c_void_p), nreg,
+                                     xh.ctypes.data_as(ctypes.c_void_p), yh.ctypes.data_as(ctypes.c_void_p), nrhs,
+                                     None))
+        return yh
+
+    def solve(self, freq, sources=(), admittance=None, tol=1e-6, max_iter=1000, c=343.0, rho=1.21, p=None, q=None,
+              stream=None):
+        """Solve Eq. SystemI; returns (p, q, info) as complex64 CUDA tensors
+        in the caller's element order."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if p is None:
+            p = torch.empty(self.n, dtype=torch.complex64, device=dev)
+        if q is None:
+            q = torch.empty(self.n, dtype=torch.complex64, device=dev)
+        srcs = (Source * max(1, len(sources)))(*sources)
+        adm, nreg = _admittance(admittance)
+        med = self._medium(c, rho)
+        info = SolveInfo()
+        code = lib().bem_solve(self._h, float(freq), ctypes.byref(med),
+                               None if adm is None else adm.ctypes.data_as(ctypes.c_void_p), nreg, srcs,
+                               len(sources), float(tol), int(max_iter), _dptr(p, self.n), _dptr(q, self.n),
+                               ctypes.byref(info), _stream_ptr(stream))
+        _check(code)
+        d = {"iterations": info.iterations, "restarts": info.restarts, "relres": info.relres,
+             "seconds": info.seconds, "levels": info.levels, "L": list(info.L[:info.levels]),
+             "near_nnz": info.near_nnz, "status": code, "converged": code != W_NOT_CONVERGED}
+        return p, q, d
+
+    def evaluate(self, freq, p, q, points, sources=(), c=343.0, rho=1.21, out=None, stream=None):
+        """Total pressure at exterior points (Eq. BIE_I, lambda = 1)."""
+        import torch
+        pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 3))
+        m = pts.shape[0]
+        if out is None:
+            out = torch.empty(m, dtype=torch.complex64, device=p.device)
+        srcs = (Source * max(1, len(sources)))(*sources)
+        med = self._medium(c, rho)
+        _check(lib().bem_evaluate(self._h, float(freq), ctypes.byref(med), srcs, len(sources), _dptr(p, self.n),
+                                  _dptr(q, self.n), pts.ctypes.data_as(ctypes.c_void_p), m, _dptr(out, m),
+                                  _stream_ptr(stream)))
+        return out
+
+    def stats(self, freq, c=343.0, rho=1.21) -> dict:
+        st = PlanStats()
+        med = self._medium(c, rho)
+        _check(lib().bem_mesh_stats(self._h, float(freq), ctypes.byref(med), ctypes.byref(st)))
+        return st.as_dict()

@@ -1,0 +1,980 @@
+// bem_capi.cu -- implementation of the C ABI declared in include/bemfmm.h:
+// mesh set-up, per-frequency plans, the FMM matrix-vector product, the
+// device-resident GMRES driver and the field evaluation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/bemfmm.h"
+#include "bem_kernels.cuh"
+#include "bem_plan.hpp"
+
+using namespace bem;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+static std::atomic<uint64_t> g_launches{0};
+
+namespace {
+
+struct Fail {
+    int code;
+};
+
+int set_err(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+void ck(cudaError_t e, const char *what)
+{
+    if (e != cudaSuccess) {
+        g_err = std::string(what) + ": " + cudaGetErrorString(e);
+        throw Fail{e == cudaErrorMemoryAllocation ? BEM_E_OOM : BEM_E_CUDA};
+    }
+}
+
+void ck_launch(const char *what)
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    ck(cudaGetLastError(), what);
+}
+
+template <typename T>
+struct DevArr {
+    T *p = nullptr;
+    size_t n = 0;
+    DevArr() = default;
+    DevArr(const DevArr &) = delete;
+    DevArr &operator=(const DevArr &) = delete;
+    ~DevArr() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count)
+    {
+        if (count == n && p) return;
+        release();
+        if (count == 0) return;
+        ck(cudaMalloc((void **)&p, count * sizeof(T)), "cudaMalloc");
+        n = count;
+    }
+    void upload(const std::vector<T> &v, cudaStream_t s)
+    {
+        alloc(v.size());
+        if (!v.empty()) ck(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s), "H2D");
+    }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+inline unsigned nblocks(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+struct LevelDev {
+    int depth = 0, L = 0, nd = 0, nc = 0, noff = 0;
+    DevArr<float4> dirs;
+    DevArr<double> dirs_d;
+    DevArr<int> il_ptr, il_src, il_off, is_src, elem_cl;
+    DevArr<double> offs;
+    DevArr<float2> D, M, Lam;
+    DevArr<int64_t> cstart;
+    DevArr<float4> dz;
+    FarArgs args() const
+    {
+        FarArgs f;
+        f.nd = nd;
+        f.k = 0.f;
+        f.dirs = dirs.p;
+        f.il_ptr = il_ptr.p;
+        f.il_src = il_src.p;
+        f.il_off = il_off.p;
+        f.D = D.p;
+        f.M = M.p;
+        f.Lam = Lam.p;
+        f.cstart = cstart.p;
+        f.is_src = is_src.p;
+        f.dz = dz.p;
+        f.elem_cl = elem_cl.p;
+        return f;
+    }
+};
+
+struct Plan {
+    double freq = -1.0, c = -1.0, k = 0.0;
+    FreqPlan fp;
+    DevArr<int> leaf_of, col_ptr, cols;
+    DevArr<int64_t> row_ptr;
+    int64_t nnz = 0;
+    std::vector<std::unique_ptr<LevelDev>> lev;
+    DevArr<float2> val;
+    std::vector<float> val_key;   // host copy of the coefficients the stored values were made with
+    bool val_valid = false;
+};
+
+struct Coeffs {
+    std::vector<float2> cp, cq, cp0, cq0, z, aq;   // internal order
+    bool known_nonzero = false;
+};
+
+}  // namespace
+
+struct bem_mesh_impl {
+    int device = 0;
+    bem_params prm;
+    Geometry g;
+    Tree t;
+    int64_t n = 0;
+    std::vector<int32_t> bct, region, type_int;
+    std::vector<double> bcv;
+    DevArr<float4> chi, clo, nrm, va, e1, e2;
+    DevArr<double> cd, vad, e1d, e2d, ad;
+    DevArr<int64_t> perm;
+    DevArr<QuadTables> Q;
+    DevArr<int> type, err;
+    DevArr<float2> cp, cq, cp0, cq0, z, aq;
+    DevArr<float2> xint, ynear, alpha, beta, tmp, tmp2, bvec, uvec;
+    // GMRES workspace
+    DevArr<float2> V, w;
+    DevArr<double2> H, cs, sn, g_, hcol, part, yv;
+    DevArr<double> normpart;
+    DevArr<GmresState> st;
+    std::unique_ptr<Plan> plan;
+    cudaStream_t s = nullptr;
+    std::vector<float> coef_key;
+
+    ElemDev elem() const
+    {
+        ElemDev E;
+        E.n = n;
+        E.chi = chi.p; E.clo = clo.p; E.nrm = nrm.p; E.va = va.p; E.e1 = e1.p; E.e2 = e2.p;
+        E.cd = cd.p; E.vad = vad.p; E.e1d = e1d.p; E.e2d = e2d.p; E.ad = ad.p;
+        return E;
+    }
+    ~bem_mesh_impl()
+    {
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
+namespace {
+
+// ------------------------------------------------------------------ tables
+QuadTables make_tables(const bem_params &p)
+{
+    QuadTables Q;
+    memset(&Q, 0, sizeof Q);
+    for (int m = 1; m <= kMaxRule; ++m) {
+        std::vector<double> xi, eta, w;
+        conical_rule(m, xi, eta, w);
+        for (int q = 0; q < m * m; ++q) {
+            Q.tri_xi[m][q] = (float)xi[q];
+            Q.tri_eta[m][q] = (float)eta[q];
+            Q.tri_w[m][q] = (float)w[q];
+        }
+    }
+    std::vector<double> x, w;
+    gauss_legendre01(4, x, w);
+    for (int i = 0; i < 4; ++i) { Q.gl4_x[i] = (float)x[i]; Q.gl4_w[i] = (float)w[i]; }
+    gauss_legendre01(3, x, w);
+    for (int i = 0; i < 3; ++i) { Q.gl3_x[i] = (float)x[i]; Q.gl3_w[i] = (float)w[i]; }
+    double R[kMaxRule + 1] = {0};
+    order_thresholds(p.quad_tol, p.m_max, R);
+    for (int m = 1; m < p.m_max; ++m) { Q.R[m] = (float)R[m]; Q.Rd[m] = R[m]; }
+    Q.rt_sub = (float)p.rt_subdiv;
+    Q.rt_sub_d = p.rt_subdiv;
+    Q.m_max = p.m_max;
+    Q.max_depth = p.max_depth;
+    Q.edge_parts = 4;
+    return Q;
+}
+
+double wavenumber(double f, double c) { return 2.0 * M_PI * f / c; }
+
+void medium_of(const bem_medium *m, double &c, double &rho)
+{
+    c = (m && m->c > 0) ? m->c : 343.0;
+    rho = (m && m->rho > 0) ? m->rho : 1.21;
+}
+
+// ------------------------------------------------------------------ plan
+void build_plan_dev(bem_mesh_impl &M, double freq, double c)
+{
+    if (M.plan && M.plan->freq == freq && M.plan->c == c) return;
+    M.plan.reset();
+    auto P = std::make_unique<Plan>();
+    P->freq = freq;
+    P->c = c;
+    P->k = wavenumber(freq, c);
+    build_plan(M.g, M.t, M.prm, P->k, P->fp);
+    const FreqPlan &fp = P->fp;
+    const Level &Lf = M.t.lv[M.t.leaf_depth];
+    const int nl = (int)Lf.start.size();
+    cudaStream_t s = M.s;
+    // near field: per-leaf column lists and per-row offsets
+    std::vector<int> col_ptr(nl + 1, 0), cols;
+    for (int t = 0; t < nl; ++t) {
+        for (int q = fp.near_ptr[t]; q < fp.near_ptr[t + 1]; ++q) {
+            int sl = fp.near_src[q];
+            for (int64_t e = Lf.start[sl]; e < Lf.start[sl] + Lf.count[sl]; ++e) cols.push_back((int)e);
+        }
+        col_ptr[t + 1] = (int)cols.size();
+    }
+    std::vector<int> leaf_of(M.n);
+    std::vector<int64_t> row_ptr(M.n + 1, 0);
+    for (int64_t i = 0; i < M.n; ++i) {
+        leaf_of[i] = Lf.elem_cluster[i];
+        row_ptr[i + 1] = row_ptr[i] + (col_ptr[leaf_of[i] + 1] - col_ptr[leaf_of[i]]);
+    }
+    P->nnz = row_ptr[M.n];
+    P->leaf_of.upload(leaf_of, s);
+    P->col_ptr.upload(col_ptr, s);
+    P->cols.upload(cols, s);
+    P->row_ptr.upload(row_ptr, s);
+    // far levels
+    for (const FarLevel &F : fp.far) {
+        auto D = std::make_unique<LevelDev>();
+        const Level &L = M.t.lv[F.depth];
+        D->depth = F.depth;
+        D->L = F.L;
+        D->nd = 2 * F.L * F.L;
+        D->nc = F.nc;
+        D->noff = (int)(F.offsets.size() / 3);
+        std::vector<double> sd, sw;
+        sphere_grid(F.L, sd, sw);
+        std::vector<float4> dirs(D->nd);
+        for (int q = 0; q < D->nd; ++q)
+            dirs[q] = make_float4((float)sd[3 * q], (float)sd[3 * q + 1], (float)sd[3 * q + 2], (float)sw[q]);
+        D->dirs.upload(dirs, s);
+        D->dirs_d.upload(sd, s);
+        D->il_ptr.upload(F.il_ptr, s);
+        D->il_src.upload(F.il_src, s);
+        D->il_off.upload(F.il_off, s);
+        D->offs.upload(F.offsets, s);
+        std::vector<int> is_src(F.nc, 0);
+        for (int v : F.il_src) is_src[v] = 1;
+        D->is_src.upload(is_src, s);
+        std::vector<int64_t> cst(F.nc + 1);
+        for (int cc = 0; cc < F.nc; ++cc) cst[cc] = L.start[cc];
+        cst[F.nc] = M.n;
+        D->cstart.upload(cst, s);
+        std::vector<float4> dz(M.n);
+        std::vector<int> ecl(M.n);
+        for (int64_t i = 0; i < M.n; ++i) {
+            const int cc = L.elem_cluster[i];
+            ecl[i] = cc;
+            const int64_t e = M.t.perm[i];
+            dz[i] = make_float4((float)(L.z[3 * cc] - M.g.cen[3 * e]), (float)(L.z[3 * cc + 1] - M.g.cen[3 * e + 1]),
+                                (float)(L.z[3 * cc + 2] - M.g.cen[3 * e + 2]), 0.f);
+        }
+        D->dz.upload(dz, s);
+        D->elem_cl.upload(ecl, s);
+        D->D.alloc((size_t)D->noff * D->nd);
+        D->M.alloc((size_t)D->nc * D->nd);
+        D->Lam.alloc((size_t)D->nc * D->nd);
+        const int64_t tot = (int64_t)D->noff * D->nd;
+        if (tot > 0) {
+            k_dtable<<<nblocks(tot, 128), 128, 0, s>>>(D->offs.p, D->noff, D->dirs_d.p, D->nd, D->L, P->k, D->D.p);
+            ck_launch("k_dtable");
+        }
+        P->lev.push_back(std::move(D));
+    }
+    M.plan = std::move(P);
+}
+
+NearArgs near_args(const bem_mesh_impl &M, const Plan &P, const float2 *cp, const float2 *cq)
+{
+    NearArgs a;
+    a.E = M.elem();
+    a.N.leaf_of = P.leaf_of.p;
+    a.N.col_ptr = P.col_ptr.p;
+    a.N.cols = P.cols.p;
+    a.N.row_ptr = P.row_ptr.p;
+    a.Q = M.Q.p;
+    a.k = (float)P.k;
+    a.ik_inv = (float)(1.0 / P.k);
+    a.cp = cp;
+    a.cq = cq;
+    return a;
+}
+
+// coefficient sets (Eq. SystemI with the boundary conditions folded in)
+void make_coeffs(bem_mesh_impl &M, double k, double omega, double c, double rho, const double *adm, int nreg, Coeffs &C)
+{
+    const int64_t n = M.n;
+    C.cp.assign(n, make_float2(0.f, 0.f));
+    C.cq = C.cp0 = C.cq0 = C.z = C.aq = C.cp;
+    C.known_nonzero = false;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t e = M.t.perm[i];
+        const int ty = M.bct[e];
+        const double vr = M.bcv[2 * e], vi = M.bcv[2 * e + 1];
+        if (ty == BEM_PRES) {
+            C.cq[i] = make_float2(1.f, 0.f);
+            C.cp0[i] = make_float2(1.f, 0.f);
+            C.z[i] = make_float2((float)vr, (float)vi);
+        } else {
+            C.cp[i] = make_float2(1.f, 0.f);
+            C.cq0[i] = make_float2(1.f, 0.f);
+            // g = i w rho v
+            C.z[i] = make_float2((float)(-omega * rho * vi), (float)(omega * rho * vr));
+            if (ty == BEM_ADMI) {
+                const int r = M.region[e];
+                const double yr = adm[2 * r], yi = adm[2 * r + 1];
+                // a = -i k beta, beta = rho c Y
+                const double br = rho * c * yr, bi = rho * c * yi;
+                C.cq[i] = make_float2((float)(k * bi), (float)(-k * br));
+                C.aq[i] = C.cq[i];
+            }
+        }
+        if (C.z[i].x != 0.f || C.z[i].y != 0.f) C.known_nonzero = true;
+    }
+}
+
+void upload_coeffs(bem_mesh_impl &M, const Coeffs &C)
+{
+    M.cp.upload(C.cp, M.s);
+    M.cq.upload(C.cq, M.s);
+    M.cp0.upload(C.cp0, M.s);
+    M.cq0.upload(C.cq0, M.s);
+    M.z.upload(C.z, M.s);
+    M.aq.upload(C.aq, M.s);
+}
+
+void check_err(bem_mesh_impl &M)
+{
+    int e = INT_MAX;
+    ck(cudaMemcpyAsync(&e, M.err.p, sizeof(int), cudaMemcpyDeviceToHost, M.s), "D2H err");
+    ck(cudaStreamSynchronize(M.s), "sync");
+    if (e != INT_MAX) {
+        char buf[160];
+        snprintf(buf, sizeof buf,
+                 "number of subelements which are subdivided in a loop exceeds %d at element %lld",
+                 M.prm.max_depth, (long long)M.t.perm[e]);
+        g_err = buf;
+        throw Fail{BEM_E_SUBDIV_LIMIT};
+    }
+}
+
+void reset_err(bem_mesh_impl &M)
+{
+    const int v = INT_MAX;
+    ck(cudaMemcpyAsync(M.err.p, &v, sizeof(int), cudaMemcpyHostToDevice, M.s), "H2D err");
+}
+
+// Make sure the stored near-field values match the current unknowns' coefficients.
+void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
+{
+    Plan &P = *M.plan;
+    std::vector<float> key;
+    key.reserve(4 * M.n);
+    for (int64_t i = 0; i < M.n; ++i) {
+        key.push_back(C.cp[i].x); key.push_back(C.cp[i].y);
+        key.push_back(C.cq[i].x); key.push_back(C.cq[i].y);
+    }
+    if (!M.prm.near_store || P.fp.direct) {
+        if (!P.val_valid) {
+            // one fused pass validates the subdivision limit for this plan
+            reset_err(M);
+            M.tmp.alloc(M.n);
+            ck(cudaMemsetAsync(M.tmp.p, 0, M.n * sizeof(float2), M.s), "memset");
+            NearArgs a = near_args(M, P, M.cp.p, M.cq.p);
+            k_near_fused<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, M.tmp.p, M.ynear.p, M.err.p, nullptr);
+            ck_launch("k_near_fused");
+            check_err(M);
+            P.val_valid = true;
+        }
+        return;
+    }
+    if (P.val_valid && key == P.val_key) return;
+    P.val.alloc((size_t)P.nnz);
+    reset_err(M);
+    NearArgs a = near_args(M, P, M.cp.p, M.cq.p);
+    k_near_store<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, P.val.p, M.err.p);
+    ck_launch("k_near_store");
+    check_err(M);
+    P.val_key.swap(key);
+    P.val_valid = true;
+}
+
+// y = A x with the given column coefficients.  x: caller order when
+// perm_in, else internal (optionally x + (*jidx) n).  y: caller order when
+// perm_out.  use_store: use the stored near-field values.
+void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool use_store, const float2 *x,
+                     const int *jidx, bool perm_in, float2 *y, bool perm_out, const int *skip, cudaStream_t s)
+{
+    Plan &P = *M.plan;
+    const int64_t n = M.n;
+    PrepArgs pa;
+    pa.n = n;
+    pa.x = x;
+    pa.jidx = jidx;
+    pa.perm = perm_in ? M.perm.p : nullptr;
+    pa.xint = M.xint.p;
+    const bool far = !P.lev.empty();
+    pa.alpha = far ? M.alpha.p : nullptr;
+    pa.beta = far ? M.beta.p : nullptr;
+    pa.chi = M.chi.p;
+    pa.nrm = M.nrm.p;
+    pa.cp = cp;
+    pa.cq = cq;
+    pa.k = (float)P.k;
+    k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, skip);
+    ck_launch("k_prep");
+    NearArgs na = near_args(M, P, cp, cq);
+    if (use_store && M.prm.near_store && !P.fp.direct) {
+        k_near_spmv<<<nblocks(n, 8), 256, 0, s>>>(na, P.val.p, M.xint.p, M.ynear.p, skip);
+        ck_launch("k_near_spmv");
+    } else {
+        k_near_fused<<<nblocks(n, 8), 256, 0, s>>>(na, M.xint.p, M.ynear.p, M.err.p, skip);
+        ck_launch("k_near_fused");
+    }
+    DisaggArgs da;
+    da.n = n;
+    da.nrm = M.nrm.p;
+    da.perm = perm_out ? M.perm.p : nullptr;
+    da.k = (float)P.k;
+    da.nlev = (int)P.lev.size();
+    for (size_t l = 0; l < P.lev.size(); ++l) {
+        LevelDev &D = *P.lev[l];
+        FarArgs f = D.args();
+        f.k = (float)P.k;
+        const int tpb = 256;
+        const size_t smem = tpb * (sizeof(float4) + 4 * sizeof(float2));
+        k_aggregate<<<D.nc, tpb, smem, s>>>(f, M.alpha.p, M.beta.p, skip);
+        ck_launch("k_aggregate");
+        k_transfer<<<D.nc, 128, 0, s>>>(f, skip);
+        ck_launch("k_transfer");
+        da.lev[l] = f;
+    }
+    k_disaggregate<<<nblocks(n, 8), 256, 0, s>>>(da, M.ynear.p, y, skip);
+    ck_launch("k_disaggregate");
+}
+
+void ensure_work(bem_mesh_impl &M)
+{
+    M.xint.alloc(M.n);
+    M.ynear.alloc(M.n);
+    M.alpha.alloc(M.n);
+    M.beta.alloc(3 * M.n);
+    M.tmp.alloc(M.n);
+    M.tmp2.alloc(M.n);
+}
+
+void prepare(bem_mesh_impl &M, double freq, const bem_medium *med, const double *adm, int nreg, Coeffs &C)
+{
+    double c, rho;
+    medium_of(med, c, rho);
+    if (!(freq > 0) || !std::isfinite(freq)) { g_err = "frequency must be positive"; throw Fail{BEM_E_ARG}; }
+    for (int64_t e = 0; e < M.n; ++e)
+        if (M.bct[e] == BEM_ADMI) {
+            if (!adm || M.region[e] >= nreg) {
+                g_err = "admittance missing for an ADMI element's region";
+                throw Fail{BEM_E_ARG};
+            }
+        }
+    ck(cudaSetDevice(M.device), "cudaSetDevice");
+    ensure_work(M);
+    build_plan_dev(M, freq, c);
+    make_coeffs(M, M.plan->k, 2.0 * M_PI * freq, c, rho, adm, nreg, C);
+    upload_coeffs(M, C);
+    ensure_near_values(M, C);
+}
+
+int resolution_warning(const bem_mesh_impl &M, double freq, const bem_medium *med)
+{
+    double c, rho;
+    medium_of(med, c, rho);
+    const double lambda = c / freq;
+    if (M.g.mean_edge > lambda / 6.0) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "mean element edge %.4g m exceeds a sixth of the wavelength (%.4g m)",
+                 M.g.mean_edge, lambda / 6.0);
+        g_err = buf;
+        return BEM_W_UNDERRESOLVED;
+    }
+    return BEM_OK;
+}
+
+std::vector<SourceDev> sources_of(const bem_source *srcs, int n)
+{
+    std::vector<SourceDev> v(n);
+    for (int i = 0; i < n; ++i) {
+        if (srcs[i].kind != BEM_SRC_PLANE && srcs[i].kind != BEM_SRC_POINT) {
+            g_err = "unknown source kind";
+            throw Fail{BEM_E_ARG};
+        }
+        v[i].kind = srcs[i].kind;
+        for (int q = 0; q < 3; ++q) v[i].v[q] = srcs[i].vec[q];
+        v[i].amp[0] = srcs[i].amp[0];
+        v[i].amp[1] = srcs[i].amp[1];
+    }
+    return v;
+}
+
+void join_streams(cudaStream_t from, cudaStream_t to)
+{
+    cudaEvent_t ev;
+    ck(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    ck(cudaEventRecord(ev, from), "record");
+    ck(cudaStreamWaitEvent(to, ev, 0), "wait");
+    cudaEventDestroy(ev);
+}
+
+
+void fill_stats(const Geometry &g, const Tree &t, const FreqPlan &fp, bem_plan_stats *out)
+{
+    memset(out, 0, sizeof *out);
+    out->n_elements = g.n;
+    out->leaf_level = t.leaf_depth;
+    out->levels = (int)fp.far.size();
+    int64_t far_pairs = 0;
+    for (size_t l = 0; l < fp.far.size() && l < 16; ++l) {
+        const FarLevel &F = fp.far[l];
+        const Level &L = t.lv[F.depth];
+        out->level_depth[l] = F.depth;
+        out->L[l] = F.L;
+        out->n_clusters[l] = F.nc;
+        out->n_interactions[l] = F.n_inter;
+        out->n_offsets[l] = (int)(F.offsets.size() / 3);
+        for (int c = 0; c < F.nc; ++c)
+            for (int q = F.il_ptr[c]; q < F.il_ptr[c + 1]; ++q) far_pairs += L.count[c] * L.count[F.il_src[q]];
+    }
+    out->far_pairs = far_pairs;
+    out->n_leaves = (int)t.lv[t.leaf_depth].start.size();
+    out->near_nnz = fp.nnz;
+    out->near_quad_points = -1;
+    out->leaf_edge = t.lv[t.leaf_depth].box;
+    out->mean_edge = g.mean_edge;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+void bem_params_default(bem_params *p)
+{
+    if (!p) return;
+    p->mode = BEM_MODE_FMM;
+    p->quad_tol = 1e-3;
+    p->m_max = 6;
+    p->rt_subdiv = 1.3;
+    p->max_depth = 15;
+    p->trunc_factor = 1.8;
+    p->L_min = 8;
+    p->admissibility = 2.0 / std::sqrt(3.0);
+    p->leaf_edge = 0.0;
+    p->stability_max = 1e3;
+    p->near_store = 1;
+    p->restart = 100;
+}
+
+const char *bem_last_error(void) { return g_err.c_str(); }
+
+uint64_t bem_launch_count(void) { return g_launches.load(); }
+
+int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tris,
+                    const int32_t *bc_type, const double *bc_value, const int32_t *region,
+                    const bem_params *params, void **out)
+{
+    if (!out) return set_err(BEM_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!nodes || !tris || n_nodes < 3 || n_tris < 1) return set_err(BEM_E_ARG, "empty mesh");
+    if (n_tris > INT_MAX / 2) return set_err(BEM_E_ARG, "too many elements");
+    bem_params p;
+    bem_params_default(&p);
+    if (params) p = *params;
+    if (p.m_max < 1 || p.m_max > kMaxRule) return set_err(BEM_E_ARG, "m_max must be in 1..6");
+    if (p.max_depth < 0 || p.max_depth > 15) return set_err(BEM_E_ARG, "max_depth must be in 0..15");
+    if (p.restart < 2 || p.restart > kMaxRestart) return set_err(BEM_E_ARG, "restart must be in 2..256");
+    if (!(p.quad_tol > 0) || !(p.rt_subdiv > 0) || !(p.admissibility > 0) || p.L_min < 1 || p.L_min > 200)
+        return set_err(BEM_E_ARG, "invalid parameter");
+    try {
+        auto M = std::make_unique<bem_mesh_impl>();
+        M->prm = p;
+        M->n = n_tris;
+        std::string e = compute_geometry(nodes, n_nodes, tris, n_tris, M->g);
+        if (!e.empty()) return set_err(BEM_E_ARG, e);
+        M->bct.assign(n_tris, BEM_VELO);
+        M->bcv.assign(2 * n_tris, 0.0);
+        M->region.assign(n_tris, 0);
+        for (int64_t j = 0; j < n_tris; ++j) {
+            if (bc_type) {
+                if (bc_type[j] < 0 || bc_type[j] > 2) return set_err(BEM_E_ARG, "bad boundary type");
+                M->bct[j] = bc_type[j];
+            }
+            if (bc_value) { M->bcv[2 * j] = bc_value[2 * j]; M->bcv[2 * j + 1] = bc_value[2 * j + 1]; }
+            if (region) {
+                if (region[j] < 0) return set_err(BEM_E_ARG, "negative region");
+                M->region[j] = region[j];
+            }
+        }
+        const double leaf = p.mode == BEM_MODE_DIRECT ? 0.0
+                            : (p.leaf_edge > 0 ? p.leaf_edge : auto_leaf_edge(M->g, p));
+        build_tree(M->g, leaf, M->t);
+        ck(cudaGetDevice(&M->device), "cudaGetDevice");
+        ck(cudaStreamCreateWithFlags(&M->s, cudaStreamNonBlocking), "stream");
+        const int64_t n = n_tris;
+        std::vector<float4> chi(n), clo(n), nr(n), va(n), e1(n), e2(n);
+        std::vector<double> cd(3 * n), vad(3 * n), e1d(3 * n), e2d(3 * n), ad(n);
+        std::vector<int> ty(n);
+        M->type_int.resize(n);
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t j = M->t.perm[i];
+            const double *c = &M->g.cen[3 * j];
+            const float h0 = (float)c[0], h1 = (float)c[1], h2 = (float)c[2];
+            chi[i] = make_float4(h0, h1, h2, (float)M->g.area[j]);
+            clo[i] = make_float4((float)(c[0] - h0), (float)(c[1] - h1), (float)(c[2] - h2), 0.f);
+            nr[i] = make_float4((float)M->g.nrm[3 * j], (float)M->g.nrm[3 * j + 1], (float)M->g.nrm[3 * j + 2], 0.f);
+            va[i] = make_float4((float)M->g.va[3 * j], (float)M->g.va[3 * j + 1], (float)M->g.va[3 * j + 2], 0.f);
+            e1[i] = make_float4((float)M->g.e1[3 * j], (float)M->g.e1[3 * j + 1], (float)M->g.e1[3 * j + 2], 0.f);
+            e2[i] = make_float4((float)M->g.e2[3 * j], (float)M->g.e2[3 * j + 1], (float)M->g.e2[3 * j + 2], 0.f);
+            for (int q = 0; q < 3; ++q) {
+                cd[3 * i + q] = c[q];
+                vad[3 * i + q] = M->g.va[3 * j + q];
+                e1d[3 * i + q] = M->g.e1[3 * j + q];
+                e2d[3 * i + q] = M->g.e2[3 * j + q];
+            }
+            ad[i] = M->g.area[j];
+            ty[i] = M->bct[j];
+        }
+        cudaStream_t s = M->s;
+        M->chi.upload(chi, s); M->clo.upload(clo, s); M->nrm.upload(nr, s);
+        M->va.upload(va, s); M->e1.upload(e1, s); M->e2.upload(e2, s);
+        M->cd.upload(cd, s); M->vad.upload(vad, s); M->e1d.upload(e1d, s); M->e2d.upload(e2d, s);
+        M->ad.upload(ad, s);
+        M->perm.upload(M->t.perm, s);
+        M->type.upload(ty, s);
+        std::vector<QuadTables> qt(1, make_tables(p));
+        M->Q.upload(qt, s);
+        M->err.alloc(1);
+        ck(cudaStreamSynchronize(s), "sync");
+        *out = M.release();
+        return BEM_OK;
+    } catch (Fail &f) {
+        return f.code;
+    } catch (std::bad_alloc &) {
+        return set_err(BEM_E_OOM, "host allocation failed");
+    }
+}
+
+int bem_mesh_destroy(void *mesh)
+{
+    if (!mesh) return set_err(BEM_E_ARG, "mesh is NULL");
+    auto *M = (bem_mesh_impl *)mesh;
+    cudaSetDevice(M->device);
+    if (M->s) cudaStreamSynchronize(M->s);
+    delete M;
+    return BEM_OK;
+}
+
+int bem_matvec(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
+               int32_t n_regions, const void *x_dev, void *y_dev, int32_t n_rhs, void *stream)
+{
+    if (!mesh || !x_dev || !y_dev || n_rhs < 1) return set_err(BEM_E_ARG, "bad argument");
+    auto &M = *(bem_mesh_impl *)mesh;
+    try {
+        cudaStream_t us = (cudaStream_t)stream;
+        Coeffs C;
+        join_streams(us, M.s);
+        prepare(M, freq_hz, medium, admittance, n_regions, C);
+        for (int r = 0; r < n_rhs; ++r) {
+            const float2 *x = (const float2 *)x_dev + (int64_t)r * M.n;
+            float2 *y = (float2 *)y_dev + (int64_t)r * M.n;
+            matvec_internal(M, M.cp.p, M.cq.p, true, x, nullptr, true, y, true, nullptr, M.s);
+        }
+        join_streams(M.s, us);
+        return resolution_warning(M, freq_hz, medium);
+    } catch (Fail &f) {
+        return f.code;
+    }
+}
+
+int bem_matvec_host(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
+                    int32_t n_regions, const void *x_host, void *y_host, int32_t n_rhs, void *stream)
+{
+    if (!mesh || !x_host || !y_host || n_rhs < 1) return set_err(BEM_E_ARG, "bad argument");
+    auto &M = *(bem_mesh_impl *)mesh;
+    try {
+        ck(cudaSetDevice(M.device), "cudaSetDevice");
+        M.bvec.alloc((size_t)M.n * n_rhs);
+        M.uvec.alloc((size_t)M.n * n_rhs);
+        cudaStream_t us = (cudaStream_t)stream;
+        const size_t bytes = (size_t)M.n * n_rhs * sizeof(float2);
+        ck(cudaMemcpyAsync(M.bvec.p, x_host, bytes, cudaMemcpyHostToDevice, us), "H2D x");
+        int st = bem_matvec(mesh, freq_hz, medium, admittance, n_regions, M.bvec.p, M.uvec.p, n_rhs, stream);
+        if (st < 0) return st;
+        ck(cudaMemcpyAsync(y_host, M.uvec.p, bytes, cudaMemcpyDeviceToHost, us), "D2H y");
+        ck(cudaStreamSynchronize(us), "sync");
+        return st;
+    } catch (Fail &f) {
+        return f.code;
+    }
+}
+
+int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
+              int32_t n_regions, const bem_source *srcs, int32_t n_src, double tol, int32_t max_iter,
+              void *p_dev, void *q_dev, bem_solve_info *info, void *stream)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (!mesh || !p_dev || n_src < 0 || (n_src > 0 && !srcs) || !(tol > 0) || max_iter < 1)
+        return set_err(BEM_E_ARG, "bad argument");
+    auto &M = *(bem_mesh_impl *)mesh;
+    try {
+        cudaStream_t us = (cudaStream_t)stream;
+        Coeffs C;
+        join_streams(us, M.s);
+        prepare(M, freq_hz, medium, admittance, n_regions, C);
+        Plan &P = *M.plan;
+        cudaStream_t s = M.s;
+        const int64_t n = M.n;
+        const int m = M.prm.restart;
+        // right-hand side: incident field minus the known boundary data
+        std::vector<SourceDev> sv = sources_of(srcs, n_src);
+        DevArr<SourceDev> sdev;
+        sdev.upload(sv, s);
+        M.bvec.alloc(n);
+        M.uvec.alloc(n);
+        if (n_src > 0) {
+            k_rhs<<<nblocks(n, 256), 256, 0, s>>>(M.cd.p, M.nrm.p, n, P.k, sdev.p, n_src, M.bvec.p);
+            ck_launch("k_rhs");
+        } else {
+            ck(cudaMemsetAsync(M.bvec.p, 0, n * sizeof(float2), s), "memset");
+        }
+        if (C.known_nonzero) {
+            reset_err(M);
+            matvec_internal(M, M.cp0.p, M.cq0.p, false, M.z.p, nullptr, false, M.tmp2.p, false, nullptr, s);
+            check_err(M);
+            k_sub<<<nblocks(n, 256), 256, 0, s>>>(M.bvec.p, M.tmp2.p, n);
+            ck_launch("k_sub");
+        }
+        // GMRES workspace
+        M.V.alloc((size_t)(m + 1) * n);
+        M.w.alloc(n);
+        M.H.alloc((size_t)(m + 1) * m);
+        M.cs.alloc(m);
+        M.sn.alloc(m);
+        M.g_.alloc(m + 1);
+        M.hcol.alloc(m + 1);
+        M.yv.alloc(m + 1);
+        const int nblk = (int)std::min<int64_t>(148, std::max<int64_t>(1, n / 2048));
+        M.part.alloc((size_t)(m + 1) * nblk);
+        const int nnorm = (int)nblocks(n, 256);
+        M.normpart.alloc(std::max(nnorm, nblk));
+        M.st.alloc(1);
+        GmresState hs;
+        memset(&hs, 0, sizeof hs);
+        hs.tol = tol;
+        hs.maxit = max_iter;
+        ck(cudaMemcpyAsync(M.st.p, &hs, sizeof hs, cudaMemcpyHostToDevice, s), "H2D st");
+        ck(cudaMemsetAsync(M.uvec.p, 0, n * sizeof(float2), s), "memset x");
+        ck(cudaMemsetAsync(M.H.p, 0, M.H.bytes(), s), "memset H");
+        // start: r0 = b
+        k_norm_part<<<nnorm, 256, 0, s>>>(M.bvec.p, n, M.normpart.p);
+        ck_launch("k_norm_part");
+        k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.bvec.p, n, M.normpart.p, nnorm, M.g_.p, m, 1);
+        ck_launch("k_gm_start");
+        // one Arnoldi step, captured once as a graph and replayed
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t gexec = nullptr;
+        int* jptr = &M.st.p->j;
+        const int *done = &M.st.p->done;
+        uint64_t before = g_launches.load();
+        ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
+        matvec_internal(M, M.cp.p, M.cq.p, true, M.V.p, jptr, false, M.w.p, false, done, s);
+        for (int pass = 0; pass < 2; ++pass) {
+            k_gm_dots<<<dim3(nblk, m + 1), 256, 0, s>>>(M.V.p, M.w.p, n, M.st.p, M.part.p, nblk);
+            ck_launch("k_gm_dots");
+            k_gm_reduce<<<1, 256, 0, s>>>(M.st.p, M.part.p, nblk, M.H.p, M.hcol.p, m, pass);
+            ck_launch("k_gm_reduce");
+            k_gm_update<<<nnorm, 256, 0, s>>>(M.V.p, M.w.p, n, M.st.p, M.hcol.p, pass == 1 ? M.normpart.p : nullptr);
+            ck_launch("k_gm_update");
+        }
+        k_gm_givens<<<1, 32, 0, s>>>(M.st.p, M.H.p, M.cs.p, M.sn.p, M.g_.p, M.normpart.p, nnorm, m);
+        ck_launch("k_gm_givens");
+        k_gm_scale<<<nblocks(n, 256), 256, 0, s>>>(M.V.p, M.w.p, n, M.st.p);
+        ck_launch("k_gm_scale");
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        ck(ce, "end capture");
+        const uint64_t per_step = g_launches.load() - before;
+        g_launches.fetch_sub(per_step);   // captured, not launched
+        ck(cudaGraphInstantiate(&gexec, graph, 0), "instantiate");
+        int restarts = 0, total_iters = 0;
+        bool converged = false;
+        GmresState h;
+        const int batch = 4;
+        for (;;) {
+            // Arnoldi cycle
+            for (int guard = 0; guard < m + batch; guard += batch) {
+                for (int b = 0; b < batch; ++b) {
+                    ck(cudaGraphLaunch(gexec, s), "graph launch");
+                    g_launches.fetch_add(per_step);
+                }
+                ck(cudaMemcpyAsync(&h, M.st.p, sizeof h, cudaMemcpyDeviceToHost, s), "D2H st");
+                ck(cudaStreamSynchronize(s), "sync");
+                if (h.done) break;
+            }
+            k_gm_backsolve<<<1, 32, 0, s>>>(M.st.p, M.H.p, M.g_.p, M.yv.p, m);
+            ck_launch("k_gm_backsolve");
+            k_gm_xupdate<<<nblocks(n, 256), 256, 0, s>>>(M.uvec.p, M.V.p, n, M.st.p, M.yv.p);
+            ck_launch("k_gm_xupdate");
+            total_iters = h.iters;
+            if (h.converged || h.iters >= max_iter) { converged = h.converged; break; }
+            // restart: r = b - A x
+            ++restarts;
+            matvec_internal(M, M.cp.p, M.cq.p, true, M.uvec.p, nullptr, false, M.w.p, false, nullptr, s);
+            k_rsub<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.bvec.p, n);   // w = b - A x
+            ck_launch("k_rsub");
+            k_norm_part<<<nnorm, 256, 0, s>>>(M.w.p, n, M.normpart.p);
+            ck_launch("k_norm_part");
+            k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.w.p, n, M.normpart.p, nnorm, M.g_.p, m, 0);
+            ck_launch("k_gm_start");
+            ck(cudaMemsetAsync(M.H.p, 0, M.H.bytes(), s), "memset H");
+            ck(cudaMemcpyAsync(&h, M.st.p, sizeof h, cudaMemcpyDeviceToHost, s), "D2H st");
+            ck(cudaStreamSynchronize(s), "sync");
+            if (h.done) { converged = true; total_iters = h.iters; break; }
+        }
+        cudaGraphExecDestroy(gexec);
+        cudaGraphDestroy(graph);
+        // p and q in the caller's order
+        k_pq<<<nblocks(n, 256), 256, 0, s>>>(M.uvec.p, M.z.p, M.aq.p, M.type.p, M.perm.p, n, (float2 *)p_dev,
+                                             (float2 *)q_dev);
+        ck_launch("k_pq");
+        check_err(M);
+        join_streams(s, us);
+        ck(cudaStreamSynchronize(us), "sync");
+        int status = converged ? BEM_OK : BEM_W_NOT_CONVERGED;
+        if (!converged) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "GMRES: relative residual %.3g after %d products (tol %.3g)", h.resid,
+                     total_iters, tol);
+            g_err = buf;
+        } else if (resolution_warning(M, freq_hz, medium) != BEM_OK) {
+            status = BEM_W_UNDERRESOLVED;
+        }
+        if (info) {
+            memset(info, 0, sizeof *info);
+            info->iterations = total_iters;
+            info->restarts = restarts;
+            info->relres = h.resid;
+            info->levels = (int)P.lev.size();
+            for (size_t l = 0; l < P.lev.size() && l < 16; ++l) info->L[l] = P.lev[l]->L;
+            info->near_nnz = P.nnz;
+            info->status = status;
+            info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        }
+        return status;
+    } catch (Fail &f) {
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(M.s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t g;
+            cudaStreamEndCapture(M.s, &g);
+            if (g) cudaGraphDestroy(g);
+        }
+        return f.code;
+    }
+}
+
+int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem_source *srcs, int32_t n_src,
+                 const void *p_dev, const void *q_dev, const double *pts, int64_t M_pts, void *out_dev,
+                 void *stream)
+{
+    if (!mesh || !p_dev || !q_dev || !pts || M_pts < 0 || !out_dev || n_src < 0 || (n_src > 0 && !srcs))
+        return set_err(BEM_E_ARG, "bad argument");
+    if (M_pts == 0) return BEM_OK;
+    auto &M = *(bem_mesh_impl *)mesh;
+    try {
+        double c, rho;
+        medium_of(medium, c, rho);
+        if (!(freq_hz > 0)) return set_err(BEM_E_ARG, "frequency must be positive");
+        ck(cudaSetDevice(M.device), "cudaSetDevice");
+        ensure_work(M);
+        cudaStream_t us = (cudaStream_t)stream;
+        join_streams(us, M.s);
+        cudaStream_t s = M.s;
+        const int64_t n = M.n;
+        k_gather<<<nblocks(n, 256), 256, 0, s>>>((const float2 *)p_dev, M.perm.p, n, M.tmp.p);
+        ck_launch("k_gather");
+        k_gather<<<nblocks(n, 256), 256, 0, s>>>((const float2 *)q_dev, M.perm.p, n, M.tmp2.p);
+        ck_launch("k_gather");
+        std::vector<double> hp(pts, pts + 3 * M_pts);
+        DevArr<double> dp;
+        dp.upload(hp, s);
+        std::vector<SourceDev> sv = sources_of(srcs, n_src);
+        DevArr<SourceDev> sdev;
+        sdev.upload(sv, s);
+        reset_err(M);
+        const double k = wavenumber(freq_hz, c);
+        k_field<<<(unsigned)M_pts, 256, 0, s>>>(M.elem(), M.Q.p, dp.p, M_pts, (float)k, M.tmp.p, M.tmp2.p, sdev.p,
+                                              n_src, (float2 *)out_dev, M.err.p);
+        ck_launch("k_field");
+        check_err(M);
+        join_streams(s, us);
+        return BEM_OK;
+    } catch (Fail &f) {
+        return f.code;
+    }
+}
+
+int bem_plan_stats_host(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tris,
+                        const bem_params *params, double freq_hz, double c, bem_plan_stats *out)
+{
+    if (!nodes || !tris || !out || n_nodes < 3 || n_tris < 1 || !(freq_hz > 0)) return set_err(BEM_E_ARG, "bad argument");
+    bem_params p;
+    bem_params_default(&p);
+    if (params) p = *params;
+    if (p.m_max < 1 || p.m_max > kMaxRule) return set_err(BEM_E_ARG, "m_max must be in 1..6");
+    try {
+        Geometry g;
+        std::string e = compute_geometry(nodes, n_nodes, tris, n_tris, g);
+        if (!e.empty()) return set_err(BEM_E_ARG, e);
+        Tree t;
+        const double leaf = p.mode == BEM_MODE_DIRECT ? 0.0 : (p.leaf_edge > 0 ? p.leaf_edge : auto_leaf_edge(g, p));
+        build_tree(g, leaf, t);
+        FreqPlan fp;
+        build_plan(g, t, p, wavenumber(freq_hz, c > 0 ? c : 343.0), fp);
+        fill_stats(g, t, fp, out);
+        return BEM_OK;
+    } catch (std::bad_alloc &) {
+        return set_err(BEM_E_OOM, "host allocation failed");
+    }
+}
+
+int bem_mesh_stats(void *mesh, double freq_hz, const bem_medium *medium, bem_plan_stats *out)
+{
+    if (!mesh || !out) return set_err(BEM_E_ARG, "bad argument");
+    auto &M = *(bem_mesh_impl *)mesh;
+    try {
+        double c, rho;
+        medium_of(medium, c, rho);
+        if (!(freq_hz > 0)) return set_err(BEM_E_ARG, "frequency must be positive");
+        ck(cudaSetDevice(M.device), "cudaSetDevice");
+        ensure_work(M);
+        build_plan_dev(M, freq_hz, c);
+        ck(cudaStreamSynchronize(M.s), "sync");
+        Plan &P = *M.plan;
+        fill_stats(M.g, M.t, P.fp, out);
+        int64_t bytes = 0;
+        bytes += M.chi.bytes() * 6 + M.cd.bytes() * 4 + M.ad.bytes() + M.perm.bytes();
+        bytes += P.cols.bytes() + P.row_ptr.bytes() + P.val.bytes();
+        for (auto &L : P.lev) bytes += L->D.bytes() + L->M.bytes() + L->Lam.bytes() + L->dz.bytes();
+        out->device_bytes = bytes;
+        return BEM_OK;
+    } catch (Fail &f) {
+        return f.code;
+    }
+}
+
+}  // extern "C"

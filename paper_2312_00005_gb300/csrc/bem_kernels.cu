@@ -1,0 +1,652 @@
+// bem_kernels.cu -- CUDA kernels (sm_103a) of the BEM + FMM matrix-vector
+// product, the incident field, the field evaluation and the device-resident
+// GMRES primitives.  Method: arXiv 2312.00005 (NumCalc); each kernel names
+// the section or equation it computes.
+#include "bem_kernels.cuh"
+
+namespace bem {
+
+// ------------------------------------------------------------------ warp helpers
+__device__ __forceinline__ float2 warp_sum(float2 v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+__device__ __forceinline__ double2 warp_sum_d(double2 v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+__device__ __forceinline__ bool skip_now(const int *skip) { return skip != nullptr && *(volatile const int *)skip != 0; }
+
+// ------------------------------------------------------------------ near field
+// Stored near field (Sec. 3.3.3, matrix N): one warp per collocation row i,
+// lanes over the row's near columns (the elements of the near leaves of i's
+// leaf, concatenated); writes A_ij for the unknowns' column coefficients.
+__global__ void k_near_store(NearArgs a, float2 *__restrict__ val, int *__restrict__ err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= a.E.n) return;
+    const QuadTables &Q = *a.Q;
+    const float4 ch = a.E.chi[i], cl = a.E.clo[i];
+    const float3 xhi = f3(ch), xlo = f3(cl), nx = f3(a.E.nrm[i]);
+    const double xd[3] = {a.E.cd[3 * i], a.E.cd[3 * i + 1], a.E.cd[3 * i + 2]};
+    const int t = a.N.leaf_of[i];
+    const int p0 = a.N.col_ptr[t], nc = a.N.col_ptr[t + 1] - p0;
+    const int64_t base = a.N.row_ptr[i];
+    for (int p = lane; p < nc; p += 32) {
+        const int j = a.N.cols[p0 + p];
+        float2 v;
+        if (!bm_entry(a.E, i, j, xhi, xlo, xd, nx, a.k, a.ik_inv, Q, a.cp[j], a.cq[j], v)) {
+            atomicMin(err, j);
+            v = make_float2(0.f, 0.f);
+        }
+        val[base + p] = v;
+    }
+}
+
+// Near-field product with stored entries: y_i = sum_p val[row_i + p] x[col_p].
+__global__ void k_near_spmv(NearArgs a, const float2 *__restrict__ val, const float2 *__restrict__ x,
+                            float2 *__restrict__ y, const int *skip)
+{
+    if (skip_now(skip)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= a.E.n) return;
+    const int t = a.N.leaf_of[i];
+    const int p0 = a.N.col_ptr[t], nc = a.N.col_ptr[t + 1] - p0;
+    const float2 *__restrict__ v = val + a.N.row_ptr[i];
+    const int *__restrict__ cols = a.N.cols + p0;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int p = lane; p < nc; p += 32) acc = cfma(__ldcs(v + p), x[cols[p]], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) y[i] = acc;
+}
+
+// Near-field product with the entries recomputed on the fly (no storage);
+// also the conventional dense BEM product when the near list is everything.
+__global__ void k_near_fused(NearArgs a, const float2 *__restrict__ x, float2 *__restrict__ y,
+                             int *__restrict__ err, const int *skip)
+{
+    if (skip_now(skip)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= a.E.n) return;
+    const QuadTables &Q = *a.Q;
+    const float4 ch = a.E.chi[i], cl = a.E.clo[i];
+    const float3 xhi = f3(ch), xlo = f3(cl), nx = f3(a.E.nrm[i]);
+    const double xd[3] = {a.E.cd[3 * i], a.E.cd[3 * i + 1], a.E.cd[3 * i + 2]};
+    const int t = a.N.leaf_of[i];
+    const int p0 = a.N.col_ptr[t], nc = a.N.col_ptr[t + 1] - p0;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int p = lane; p < nc; p += 32) {
+        const int j = a.N.cols[p0 + p];
+        const float2 cp = a.cp[j], cq = a.cq[j];
+        if (cp.x == 0.f && cp.y == 0.f && cq.x == 0.f && cq.y == 0.f) continue;
+        float2 v;
+        if (!bm_entry(a.E, i, j, xhi, xlo, xd, nx, a.k, a.ik_inv, Q, cp, cq, v)) {
+            atomicMin(err, j);
+            continue;
+        }
+        acc = cfma(v, x[j], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) y[i] = acc;
+}
+
+// ------------------------------------------------------------------ far field
+// Per product: gather x into the internal order (x_int[i] = x[perm[i]] or
+// x = xbase + jidx * n) and form the aggregation weights of the centroid
+// rule, alpha_i = A_i cq_i x_i and beta_i = ik A_i cp_i x_i n_i, so that the
+// column factor of Sec. 3.3.1 is alpha_i + beta_i . s.
+__global__ void k_prep(PrepArgs a, const int *skip)
+{
+    if (skip_now(skip)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const float2 *xb = a.x;
+    if (a.jidx) xb += (int64_t)(*a.jidx) * a.n;
+    const float2 xv = a.perm ? xb[a.perm[i]] : xb[i];
+    a.xint[i] = xv;
+    if (a.alpha) {
+        const float A = a.chi[i].w;
+        const float3 nn = f3(a.nrm[i]);
+        const float2 cq = a.cq[i], cp = a.cp[i];
+        a.alpha[i] = cscale(cmul(cq, xv), A);
+        // ik A cp x
+        const float2 t = cscale(cmul(cp, xv), A);
+        const float2 b = make_float2(-a.k * t.y, a.k * t.x);
+        a.beta[3 * i] = cscale(b, nn.x);
+        a.beta[3 * i + 1] = cscale(b, nn.y);
+        a.beta[3 * i + 2] = cscale(b, nn.z);
+    }
+}
+
+// Aggregation (Sec. 3.3.3, matrix T(l) with the centroid rule): for every
+// source cluster c and direction s_nu,
+//   M_c(nu) = sum_{j in c} e^{ik (z_c - x_j).s_nu} (alpha_j + beta_j . s_nu).
+__global__ void k_aggregate(FarArgs f, const float2 *__restrict__ alpha, const float2 *__restrict__ beta,
+                            const int *skip)
+{
+    if (skip_now(skip)) return;
+    const int c = blockIdx.x;
+    if (!f.is_src[c]) return;
+    extern __shared__ float4 sm[];
+    float4 *sd = sm;                              // z_c - x_j
+    float2 *sa = (float2 *)(sm + blockDim.x);     // alpha_j
+    float2 *sb = sa + blockDim.x;                 // beta_j (x, y, z)
+    const int64_t e0 = f.cstart[c], ne = f.cstart[c + 1] - e0;
+    for (int nu0 = 0; nu0 < f.nd; nu0 += blockDim.x) {
+        const int nu = nu0 + threadIdx.x;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (nu < f.nd) s = f.dirs[nu];
+        const float3 sv = f3(s);
+        float2 acc = make_float2(0.f, 0.f);
+        for (int64_t c0 = 0; c0 < ne; c0 += blockDim.x) {
+            const int cnt = (int)min((int64_t)blockDim.x, ne - c0);
+            __syncthreads();
+            if (threadIdx.x < cnt) {
+                const int64_t j = e0 + c0 + threadIdx.x;
+                sd[threadIdx.x] = f.dz[j];
+                sa[threadIdx.x] = alpha[j];
+                sb[3 * threadIdx.x] = beta[3 * j];
+                sb[3 * threadIdx.x + 1] = beta[3 * j + 1];
+                sb[3 * threadIdx.x + 2] = beta[3 * j + 2];
+            }
+            __syncthreads();
+            if (nu < f.nd) {
+                for (int q = 0; q < cnt; ++q) {
+                    const float ph = f.k * dot3f(f3(sd[q]), sv);
+                    float sn, cs;
+                    sincosf(ph, &sn, &cs);
+                    float2 w = sa[q];
+                    w = cfma(sb[3 * q], make_float2(sv.x, 0.f), w);
+                    w = cfma(sb[3 * q + 1], make_float2(sv.y, 0.f), w);
+                    w = cfma(sb[3 * q + 2], make_float2(sv.z, 0.f), w);
+                    acc = cfma(make_float2(cs, sn), w, acc);
+                }
+            }
+        }
+        if (nu < f.nd) f.M[(int64_t)c * f.nd + nu] = acc;
+    }
+}
+
+// Diagonal transfer (Sec. 3.3.3, matrix D(l)): for every target cluster t
+// with an interaction list (Sec. 3.3.4),
+//   Lambda_t(nu) = sum_{s in I(t)} D_L(z_t - z_s, s_nu) M_s(nu).
+__global__ void k_transfer(FarArgs f, const int *skip)
+{
+    if (skip_now(skip)) return;
+    const int t = blockIdx.x;
+    const int b = f.il_ptr[t], e = f.il_ptr[t + 1];
+    if (b == e) return;
+    for (int nu = threadIdx.x; nu < f.nd; nu += blockDim.x) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int q = b; q < e; ++q) {
+            const float2 D = f.D[(int64_t)f.il_off[q] * f.nd + nu];
+            const float2 M = f.M[(int64_t)f.il_src[q] * f.nd + nu];
+            acc = cfma(D, M, acc);
+        }
+        f.Lam[(int64_t)t * f.nd + nu] = acc;
+    }
+}
+
+// Disaggregation over all levels (Sec. 3.3.3, matrix S(l), with the
+// Burton-Miller row operator 1 + s.n_i) and the final sum with the near field:
+//   y_i = near_i + (ik/16 pi^2) sum_l sum_nu w_nu (1 + s_nu.n_i)
+//                   e^{ik (x_i - z_t).s_nu} Lambda_t(nu).
+// One warp per element; writes y[perm[i]] (caller order) or y[i].
+__global__ void k_disaggregate(DisaggArgs a, const float2 *__restrict__ ynear, float2 *__restrict__ y,
+                               const int *skip)
+{
+    if (skip_now(skip)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= a.n) return;
+    const float3 ni = f3(a.nrm[i]);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int l = 0; l < a.nlev; ++l) {
+        const FarArgs &f = a.lev[l];
+        const int c = f.elem_cl[i];
+        if (f.il_ptr[c] == f.il_ptr[c + 1]) continue;
+        const float3 dz = f3(f.dz[i]);                 // z_c - x_i
+        const float2 *__restrict__ lam = f.Lam + (int64_t)c * f.nd;
+        for (int nu = lane; nu < f.nd; nu += 32) {
+            const float4 s = f.dirs[nu];
+            const float ph = -f.k * dot3f(dz, f3(s));
+            float sn, cs;
+            sincosf(ph, &sn, &cs);
+            const float wf = s.w * (1.0f + dot3f(f3(s), ni));
+            acc = cfma(make_float2(cs * wf, sn * wf), lam[nu], acc);
+        }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        // (ik / 16 pi^2) acc
+        const float s = a.k * 0.00633257397764611f;   // k / (16 pi^2)
+        float2 far = make_float2(-s * acc.y, s * acc.x);
+        float2 out = cadd(ynear[i], far);
+        if (a.perm) y[a.perm[i]] = out;
+        else y[i] = out;
+    }
+}
+
+// Translation table per distinct offset X (Eq. FMMBase):
+//   D_L(X, s_nu) = sum_{n=0}^{L} i^n (2n+1) h_n(k|X|) P_n(X.s_nu / |X|),
+// FP64, spherical Hankel functions by upward recursion (Sec. 4.2).
+__global__ void k_dtable(const double *__restrict__ offs, int noff, const double *__restrict__ dirs, int nd,
+                         int L, double k, float2 *__restrict__ D)
+{
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)noff * nd) return;
+    const int o = (int)(id / nd), nu = (int)(id % nd);
+    const double X0 = offs[3 * o], X1 = offs[3 * o + 1], X2 = offs[3 * o + 2];
+    const double R = sqrt(X0 * X0 + X1 * X1 + X2 * X2);
+    const double x = k * R;
+    const double t = (X0 * dirs[3 * nu] + X1 * dirs[3 * nu + 1] + X2 * dirs[3 * nu + 2]) / R;
+    double sx, cx;
+    sincos(x, &sx, &cx);
+    // h_0 = -i e^{ix}/x, h_1 = -e^{ix}(x + i)/x^2
+    double h0r = sx / x, h0i = -cx / x;
+    double h1r = -(cx * x - sx) / (x * x), h1i = -(sx * x + cx) / (x * x);
+    double p0 = 1.0, p1 = t;
+    double sr = h0r, si = h0i;                      // n = 0 term: i^0 * 1 * h0 * 1
+    if (L >= 1) {                                   // n = 1: i * 3 * h1 * t
+        sr += -3.0 * h1i * t;
+        si += 3.0 * h1r * t;
+    }
+    for (int n = 1; n < L; ++n) {
+        const double f = (2.0 * n + 1.0) / x;
+        const double h2r = f * h1r - h0r, h2i = f * h1i - h0i;
+        const double p2 = ((2.0 * n + 1.0) * t * p1 - n * p0) / (n + 1.0);
+        const int m = n + 1;
+        const double c = (2.0 * m + 1.0) * p2;
+        // i^m (h2r + i h2i) c
+        double ar = h2r * c, ai = h2i * c;
+        switch (m & 3) {
+            case 0: sr += ar; si += ai; break;
+            case 1: sr -= ai; si += ar; break;
+            case 2: sr -= ar; si -= ai; break;
+            default: sr += ai; si -= ar; break;
+        }
+        h0r = h1r; h0i = h1i; h1r = h2r; h1i = h2i;
+        p0 = p1; p1 = p2;
+    }
+    D[id] = make_float2((float)sr, (float)si);
+}
+
+// ------------------------------------------------------------------ incident field
+// b_i = sum_src [p_inc(x_i) - gamma dp_inc/dn(x_i)] (right-hand side of
+// Eq. SystemI), gamma = i/k; FP64 phases.  Output in the internal order.
+__global__ void k_rhs(const double *__restrict__ cd, const float4 *__restrict__ nrm, int64_t n, double k,
+                      const SourceDev *__restrict__ src, int nsrc, float2 *__restrict__ b)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x0 = cd[3 * i], x1 = cd[3 * i + 1], x2 = cd[3 * i + 2];
+    const double n0 = nrm[i].x, n1 = nrm[i].y, n2 = nrm[i].z;
+    double br = 0.0, bi = 0.0;
+    for (int q = 0; q < nsrc; ++q) {
+        const SourceDev s = src[q];
+        double pr, pi, dr, di;
+        if (s.kind == 0) {
+            const double ph = k * (s.v[0] * x0 + s.v[1] * x1 + s.v[2] * x2);
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            pr = s.amp[0] * cs - s.amp[1] * sn;
+            pi = s.amp[0] * sn + s.amp[1] * cs;
+            const double kd = k * (s.v[0] * n0 + s.v[1] * n1 + s.v[2] * n2);
+            dr = -kd * pi;              // ik (d.n) p
+            di = kd * pr;
+        } else {
+            const double d0 = x0 - s.v[0], d1 = x1 - s.v[1], d2 = x2 - s.v[2];
+            const double R = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+            double sn, cs;
+            sincos(k * R, &sn, &cs);
+            const double g = 1.0 / (4.0 * 3.14159265358979323846 * R);
+            const double gr = g * cs, gi = g * sn;
+            pr = s.amp[0] * gr - s.amp[1] * gi;
+            pi = s.amp[0] * gi + s.amp[1] * gr;
+            const double dn = (d0 * n0 + d1 * n1 + d2 * n2) / R;
+            // p (ik - 1/R) dn
+            const double fr = -dn / R, fi = k * dn;
+            dr = pr * fr - pi * fi;
+            di = pr * fi + pi * fr;
+        }
+        // p - (i/k) dp
+        br += pr + di / k;
+        bi += pi - dr / k;
+    }
+    b[i] = make_float2((float)br, (float)bi);
+}
+
+// ------------------------------------------------------------------ field evaluation
+// p(x) = p_inc(x) + sum_j [H(x)_j p_j - G(x)_j q_j] (Eq. BIE_I, lambda = 1);
+// one block per field point, threads over elements.
+__global__ void k_field(ElemDev E, const QuadTables *__restrict__ Qp, const double *__restrict__ pts, int64_t M,
+                        float k, const float2 *__restrict__ p, const float2 *__restrict__ q,
+                        const SourceDev *__restrict__ src, int nsrc, float2 *__restrict__ out, int *err)
+{
+    const int64_t m = blockIdx.x;
+    if (m >= M) return;
+    const QuadTables &Q = *Qp;
+    const double xd[3] = {pts[3 * m], pts[3 * m + 1], pts[3 * m + 2]};
+    const float3 xhi = make_float3((float)xd[0], (float)xd[1], (float)xd[2]);
+    const float3 xlo = make_float3((float)(xd[0] - (double)xhi.x), (float)(xd[1] - (double)xhi.y),
+                                   (float)(xd[2] - (double)xhi.z));
+    float2 acc = make_float2(0.f, 0.f);
+    for (int64_t j = threadIdx.x; j < E.n; j += blockDim.x) {
+        float2 G = make_float2(0.f, 0.f), H = make_float2(0.f, 0.f);
+        if (!integrate_regular<true>(E, j, xhi, xlo, xd, make_float3(0.f, 0.f, 1.f), k, 1.0f / k, Q, G, H)) {
+            atomicMin(err, (int)j);
+            continue;
+        }
+        acc = cadd(acc, csub(cmul(H, p[j]), cmul(G, q[j])));
+    }
+    __shared__ float2 red[32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float2 v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : make_float2(0.f, 0.f);
+        v = warp_sum(v);
+        if (threadIdx.x == 0) {
+            double br = v.x, bi = v.y;
+            for (int s = 0; s < nsrc; ++s) {
+                const SourceDev S = src[s];
+                double sn, cs, gr, gi;
+                if (S.kind == 0) {
+                    sincos((double)k * (S.v[0] * xd[0] + S.v[1] * xd[1] + S.v[2] * xd[2]), &sn, &cs);
+                    gr = cs; gi = sn;
+                } else {
+                    const double d0 = xd[0] - S.v[0], d1 = xd[1] - S.v[1], d2 = xd[2] - S.v[2];
+                    const double R = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                    sincos((double)k * R, &sn, &cs);
+                    gr = cs / (4.0 * 3.14159265358979323846 * R);
+                    gi = sn / (4.0 * 3.14159265358979323846 * R);
+                }
+                br += S.amp[0] * gr - S.amp[1] * gi;
+                bi += S.amp[0] * gi + S.amp[1] * gr;
+            }
+            out[m] = make_float2((float)br, (float)bi);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ vector helpers
+__global__ void k_gather(const float2 *__restrict__ x, const int64_t *__restrict__ perm, int64_t n,
+                         float2 *__restrict__ y)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = x[perm[i]];
+}
+__global__ void k_scatter(const float2 *__restrict__ x, const int64_t *__restrict__ perm, int64_t n,
+                          float2 *__restrict__ y)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[perm[i]] = x[i];
+}
+// b <- b - y
+__global__ void k_sub(float2 *__restrict__ b, const float2 *__restrict__ y, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = csub(b[i], y[i]);
+}
+// w <- b - w
+__global__ void k_rsub(float2 *__restrict__ w, const float2 *__restrict__ b, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w[i] = csub(b[i], w[i]);
+}
+// p, q from the unknowns u and the known data z (internal order), written in
+// the caller order: VELO/ADMI: p = u, q = a u + z; PRES: p = z, q = u.
+__global__ void k_pq(const float2 *__restrict__ u, const float2 *__restrict__ z, const float2 *__restrict__ aq,
+                     const int *__restrict__ type, const int64_t *__restrict__ perm, int64_t n,
+                     float2 *__restrict__ p, float2 *__restrict__ q)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float2 pv, qv;
+    if (type[i] == 1) { pv = z[i]; qv = u[i]; }
+    else { pv = u[i]; qv = cfma(aq[i], u[i], z[i]); }
+    p[perm[i]] = pv;
+    if (q) q[perm[i]] = qv;
+}
+
+// ------------------------------------------------------------------ GMRES
+// Partial dot products h_l = sum_i conj(V_l[i]) w[i] for l <= j: FP32
+// products summed per thread, FP64 across threads and blocks.
+__global__ void k_gm_dots(const float2 *__restrict__ V, const float2 *__restrict__ w, int64_t n,
+                          const GmresState *st, double2 *__restrict__ part, int nblk)
+{
+    if (st->done) return;
+    const int l = blockIdx.y;
+    if (l > st->j) return;
+    const float2 *vl = V + (int64_t)l * n;
+    double2 acc = make_double2(0.0, 0.0);
+    const int64_t chunk = (n + nblk - 1) / nblk;
+    const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+    for (int64_t i0 = b0 + threadIdx.x; i0 < b1; i0 += 8 * (int64_t)blockDim.x) {
+        float2 s = make_float2(0.f, 0.f);
+        for (int u = 0; u < 8; ++u) {
+            const int64_t i = i0 + (int64_t)u * blockDim.x;
+            if (i < b1) {
+                const float2 a = vl[i], b = w[i];
+                s.x = fmaf(a.x, b.x, fmaf(a.y, b.y, s.x));
+                s.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, s.y));
+            }
+        }
+        acc.x += s.x;
+        acc.y += s.y;
+    }
+    acc = warp_sum_d(acc);
+    __shared__ double2 red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double2 v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : make_double2(0.0, 0.0);
+        v = warp_sum_d(v);
+        if (threadIdx.x == 0) part[(int64_t)l * nblk + blockIdx.x] = v;
+    }
+}
+
+// Reduce the partial sums; pass 0 sets H[:, j], pass 1 adds (CGS2).
+__global__ void k_gm_reduce(GmresState *st, const double2 *__restrict__ part, int nblk, double2 *__restrict__ H,
+                            double2 *__restrict__ hcol, int m, int pass)
+{
+    if (st->done) return;
+    const int j = st->j;
+    for (int l = threadIdx.x; l <= j; l += blockDim.x) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int b = 0; b < nblk; ++b) {
+            s.x += part[(int64_t)l * nblk + b].x;
+            s.y += part[(int64_t)l * nblk + b].y;
+        }
+        hcol[l] = s;
+        double2 &h = H[(int64_t)l * m + j];
+        if (pass == 0) h = s;
+        else { h.x += s.x; h.y += s.y; }
+    }
+}
+
+// w <- w - sum_{l<=j} hcol_l V_l; with norm != null also partial ||w||^2.
+__global__ void k_gm_update(const float2 *__restrict__ V, float2 *__restrict__ w, int64_t n, const GmresState *st,
+                            const double2 *__restrict__ hcol, double *__restrict__ normpart)
+{
+    if (st->done) return;
+    const int j = st->j;
+    __shared__ float2 hs[kMaxRestart + 1];
+    for (int l = threadIdx.x; l <= j; l += blockDim.x) hs[l] = make_float2((float)hcol[l].x, (float)hcol[l].y);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double nrm = 0.0;
+    if (i < n) {
+        float2 acc = w[i];
+        for (int l = 0; l <= j; ++l) {
+            const float2 v = V[(int64_t)l * n + i];
+            const float2 h = hs[l];
+            acc.x -= h.x * v.x - h.y * v.y;
+            acc.y -= h.x * v.y + h.y * v.x;
+        }
+        w[i] = acc;
+        nrm = (double)acc.x * acc.x + (double)acc.y * acc.y;
+    }
+    if (normpart) {
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        __shared__ double red[32];
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (threadIdx.x == 0) normpart[blockIdx.x] = v;
+        }
+    }
+}
+
+// Givens step (single thread, FP64): h_{j+1,j} = ||w||, apply the previous
+// rotations to column j, form the new rotation, update g and the residual
+// estimate; decide whether the cycle ends.
+__global__ void k_gm_givens(GmresState *st, double2 *__restrict__ H, double2 *__restrict__ cs,
+                            double2 *__restrict__ sn, double2 *__restrict__ g, const double *__restrict__ normpart,
+                            int nblk, int m)
+{
+    if (threadIdx.x != 0 || st->done) return;
+    const int j = st->j;
+    double nn = 0.0;
+    for (int b = 0; b < nblk; ++b) nn += normpart[b];
+    const double hn = sqrt(nn);
+    H[(int64_t)(j + 1) * m + j] = make_double2(hn, 0.0);
+    for (int l = 0; l < j; ++l) {
+        const double2 h0 = H[(int64_t)l * m + j], h1 = H[(int64_t)(l + 1) * m + j];
+        const double2 c = cs[l], s = sn[l];
+        // [conj(c) conj(s); -s c] [h0; h1]
+        H[(int64_t)l * m + j] = make_double2(c.x * h0.x + c.y * h0.y + s.x * h1.x + s.y * h1.y,
+                                             c.x * h0.y - c.y * h0.x + s.x * h1.y - s.y * h1.x);
+        H[(int64_t)(l + 1) * m + j] = make_double2(-(s.x * h0.x - s.y * h0.y) + c.x * h1.x - c.y * h1.y,
+                                                   -(s.x * h0.y + s.y * h0.x) + c.x * h1.y + c.y * h1.x);
+    }
+    const double2 h0 = H[(int64_t)j * m + j];
+    const double den = sqrt(h0.x * h0.x + h0.y * h0.y + hn * hn);
+    double2 c, s;
+    if (den == 0.0) { c = make_double2(1.0, 0.0); s = make_double2(0.0, 0.0); }
+    else { c = make_double2(h0.x / den, h0.y / den); s = make_double2(hn / den, 0.0); }
+    cs[j] = c;
+    sn[j] = s;
+    H[(int64_t)j * m + j] = make_double2(den, 0.0);
+    H[(int64_t)(j + 1) * m + j] = make_double2(0.0, 0.0);
+    const double2 g0 = g[j];
+    g[j] = make_double2(c.x * g0.x + c.y * g0.y, c.x * g0.y - c.y * g0.x);
+    g[j + 1] = make_double2(-(s.x * g0.x - s.y * g0.y), -(s.x * g0.y + s.y * g0.x));
+    const double res = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y) / st->bnorm;
+    st->resid = res;
+    st->iters += 1;
+    st->hn = hn;
+    st->ncols = j + 1;
+    if (res <= st->tol || hn <= 1e-300 * st->bnorm || j + 1 >= m || st->iters >= st->maxit) {
+        st->done = 1;
+        st->converged = res <= st->tol;
+    } else {
+        st->j = j + 1;
+    }
+}
+
+// V_{j} <- w / h_{j,j-1} for the new column index j (after the Givens step).
+__global__ void k_gm_scale(float2 *__restrict__ V, const float2 *__restrict__ w, int64_t n, const GmresState *st)
+{
+    if (st->done) return;
+    const int j = st->j;
+    const float inv = (float)(1.0 / st->hn);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) V[(int64_t)j * n + i] = cscale(w[i], inv);
+}
+
+// Back substitution (single thread, FP64): y = R^{-1} g over ncols columns.
+__global__ void k_gm_backsolve(const GmresState *st, const double2 *__restrict__ H, const double2 *__restrict__ g,
+                               double2 *__restrict__ y, int m)
+{
+    if (threadIdx.x != 0) return;
+    const int nc = st->ncols;
+    for (int l = nc - 1; l >= 0; --l) {
+        double2 s = g[l];
+        for (int c = l + 1; c < nc; ++c) {
+            const double2 h = H[(int64_t)l * m + c], yc = y[c];
+            s.x -= h.x * yc.x - h.y * yc.y;
+            s.y -= h.x * yc.y + h.y * yc.x;
+        }
+        const double2 d = H[(int64_t)l * m + l];
+        const double dd = d.x * d.x + d.y * d.y;
+        y[l] = make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd);
+    }
+}
+
+// x <- x + sum_l y_l V_l
+__global__ void k_gm_xupdate(float2 *__restrict__ x, const float2 *__restrict__ V, int64_t n,
+                             const GmresState *st, const double2 *__restrict__ y)
+{
+    __shared__ float2 ys[kMaxRestart + 1];
+    const int nc = st->ncols;
+    for (int l = threadIdx.x; l < nc; l += blockDim.x) ys[l] = make_float2((float)y[l].x, (float)y[l].y);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float2 acc = x[i];
+    for (int l = 0; l < nc; ++l) acc = cfma(ys[l], V[(int64_t)l * n + i], acc);
+    x[i] = acc;
+}
+
+// r = b - A x is formed by the caller; here: V_0 = r / ||r|| with ||r|| from
+// normpart, and the cycle state is reset.
+__global__ void k_gm_start(GmresState *st, float2 *__restrict__ V, const float2 *__restrict__ r, int64_t n,
+                           const double *__restrict__ normpart, int nblk, double2 *__restrict__ g, int m, int first)
+{
+    __shared__ double beta_s;
+    if (threadIdx.x == 0) {
+        double nn = 0.0;
+        for (int b = 0; b < nblk; ++b) nn += normpart[b];
+        beta_s = sqrt(nn);
+    }
+    __syncthreads();
+    const double beta = beta_s;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) V[i] = beta > 0.0 ? cscale(r[i], (float)(1.0 / beta)) : make_float2(0.f, 0.f);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (first) st->bnorm = beta;
+        st->beta = beta;
+        st->j = 0;
+        st->ncols = 0;
+        st->done = 0;
+        st->converged = 0;
+        st->resid = st->bnorm > 0.0 ? beta / st->bnorm : 0.0;
+        for (int l = 0; l <= m; ++l) g[l] = make_double2(0.0, 0.0);
+        g[0] = make_double2(beta, 0.0);
+        if (st->resid <= st->tol) { st->done = 1; st->converged = 1; }
+    }
+}
+
+// partial ||r||^2 per block
+__global__ void k_norm_part(const float2 *__restrict__ r, int64_t n, double *__restrict__ part)
+{
+    double v = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v += (double)r[i].x * r[i].x + (double)r[i].y * r[i].y;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = s;
+    }
+}
+
+}  // namespace bem

@@ -1,0 +1,104 @@
+// bem_kernels.cuh -- kernel argument blocks and kernel declarations.
+#pragma once
+
+#include "bem_device.cuh"
+
+namespace bem {
+
+constexpr int kMaxRestart = 256;
+constexpr int kMaxFarLevels = 16;
+
+struct NearDev {
+    const int *leaf_of;      // per element: leaf cluster
+    const int *col_ptr;      // per leaf (+1): offsets into cols
+    const int *cols;         // concatenated near columns of each leaf
+    const int64_t *row_ptr;  // per element (+1): offsets into the stored values
+};
+
+struct NearArgs {
+    ElemDev E;
+    NearDev N;
+    const QuadTables *Q;
+    float k, ik_inv;
+    const float2 *cp, *cq;   // column coefficients (internal order)
+};
+
+struct PrepArgs {
+    int64_t n;
+    const float2 *x;         // input vector (caller order if perm, else internal)
+    const int *jidx;         // optional: x += (*jidx) * n
+    const int64_t *perm;     // optional: internal -> caller
+    float2 *xint;
+    float2 *alpha, *beta;    // far-field weights (alpha n, beta 3n); may be null
+    const float4 *chi, *nrm;
+    const float2 *cp, *cq;
+    float k;
+};
+
+struct FarArgs {
+    int nd;                  // 2 L^2 directions
+    float k;
+    const float4 *dirs;      // (s, w)
+    const int *il_ptr, *il_src, *il_off;
+    const float2 *D;         // [noff][nd]
+    float2 *M, *Lam;         // [nc][nd]
+    const int64_t *cstart;   // [nc + 1] element ranges
+    const int *is_src;       // [nc]
+    const float4 *dz;        // per element: z_c - x_j
+    const int *elem_cl;      // per element: cluster at this level
+};
+
+struct DisaggArgs {
+    int64_t n;
+    const float4 *nrm;
+    const int64_t *perm;     // optional
+    float k;
+    int nlev;
+    FarArgs lev[kMaxFarLevels];
+};
+
+struct SourceDev {
+    int kind;
+    double v[3];
+    double amp[2];
+};
+
+struct GmresState {
+    int j, done, converged, iters, ncols, maxit;
+    double bnorm, beta, resid, tol, hn;
+};
+
+__global__ void k_near_store(NearArgs a, float2 *val, int *err);
+__global__ void k_near_spmv(NearArgs a, const float2 *val, const float2 *x, float2 *y, const int *skip);
+__global__ void k_near_fused(NearArgs a, const float2 *x, float2 *y, int *err, const int *skip);
+__global__ void k_prep(PrepArgs a, const int *skip);
+__global__ void k_aggregate(FarArgs f, const float2 *alpha, const float2 *beta, const int *skip);
+__global__ void k_transfer(FarArgs f, const int *skip);
+__global__ void k_disaggregate(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
+__global__ void k_dtable(const double *offs, int noff, const double *dirs, int nd, int L, double k, float2 *D);
+__global__ void k_rhs(const double *cd, const float4 *nrm, int64_t n, double k, const SourceDev *src, int nsrc,
+                      float2 *b);
+__global__ void k_field(ElemDev E, const QuadTables *Q, const double *pts, int64_t M, float k, const float2 *p,
+                        const float2 *q, const SourceDev *src, int nsrc, float2 *out, int *err);
+__global__ void k_gather(const float2 *x, const int64_t *perm, int64_t n, float2 *y);
+__global__ void k_scatter(const float2 *x, const int64_t *perm, int64_t n, float2 *y);
+__global__ void k_sub(float2 *b, const float2 *y, int64_t n);
+__global__ void k_rsub(float2 *w, const float2 *b, int64_t n);
+__global__ void k_pq(const float2 *u, const float2 *z, const float2 *aq, const int *type, const int64_t *perm,
+                     int64_t n, float2 *p, float2 *q);
+__global__ void k_gm_dots(const float2 *V, const float2 *w, int64_t n, const GmresState *st, double2 *part,
+                          int nblk);
+__global__ void k_gm_reduce(GmresState *st, const double2 *part, int nblk, double2 *H, double2 *hcol, int m,
+                            int pass);
+__global__ void k_gm_update(const float2 *V, float2 *w, int64_t n, const GmresState *st, const double2 *hcol,
+                            double *normpart);
+__global__ void k_gm_givens(GmresState *st, double2 *H, double2 *cs, double2 *sn, double2 *g,
+                            const double *normpart, int nblk, int m);
+__global__ void k_gm_scale(float2 *V, const float2 *w, int64_t n, const GmresState *st);
+__global__ void k_gm_backsolve(const GmresState *st, const double2 *H, const double2 *g, double2 *y, int m);
+__global__ void k_gm_xupdate(float2 *x, const float2 *V, int64_t n, const GmresState *st, const double2 *y);
+__global__ void k_gm_start(GmresState *st, float2 *V, const float2 *r, int64_t n, const double *normpart, int nblk,
+                           double2 *g, int m, int first);
+__global__ void k_norm_part(const float2 *r, int64_t n, double *part);
+
+}  // namespace bem

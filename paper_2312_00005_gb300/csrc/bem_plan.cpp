@@ -1,0 +1,477 @@
+// bem_plan.cpp -- host-side geometry, quadrature tables and cluster plan.
+// See bem_plan.hpp for the paper sections each part follows.
+#include "bem_plan.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <map>
+#include <numeric>
+#include <tuple>
+
+namespace bem {
+
+namespace {
+inline void sub3(const double *a, const double *b, double *o) { o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }
+inline double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+inline void cross3(const double *a, const double *b, double *o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+inline double norm3(const double *a) { return std::sqrt(dot3(a, a)); }
+}  // namespace
+
+// ------------------------------------------------------------------ geometry
+std::string compute_geometry(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n,
+                             Geometry &g)
+{
+    g.n = n;
+    g.cen.assign(3 * n, 0.0);
+    g.nrm.assign(3 * n, 0.0);
+    g.area.assign(n, 0.0);
+    g.va.assign(3 * n, 0.0);
+    g.e1.assign(3 * n, 0.0);
+    g.e2.assign(3 * n, 0.0);
+    g.vrad.assign(n, 0.0);
+    g.vmin.assign(3, 1e300);
+    g.vmax.assign(3, -1e300);
+    double edge_sum = 0.0;
+    g.max_area = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        int32_t ia = tris[3 * j], ib = tris[3 * j + 1], ic = tris[3 * j + 2];
+        if (ia < 0 || ib < 0 || ic < 0 || ia >= n_nodes || ib >= n_nodes || ic >= n_nodes) {
+            char buf[128];
+            snprintf(buf, sizeof buf, "element %lld has a node index out of range", (long long)j);
+            return buf;
+        }
+        const double *a = nodes + 3 * ia, *b = nodes + 3 * ib, *c = nodes + 3 * ic;
+        double ab[3], ac[3], bc[3], cr[3];
+        sub3(b, a, ab);
+        sub3(c, a, ac);
+        sub3(c, b, bc);
+        cross3(ab, ac, cr);
+        double l = norm3(cr);
+        if (!(l > 0.0) || !std::isfinite(l)) {
+            char buf[128];
+            snprintf(buf, sizeof buf, "element %lld is degenerate (zero area)", (long long)j);
+            return buf;
+        }
+        g.area[j] = 0.5 * l;
+        g.max_area = std::max(g.max_area, g.area[j]);
+        for (int i = 0; i < 3; ++i) {
+            g.nrm[3 * j + i] = cr[i] / l;
+            g.cen[3 * j + i] = (a[i] + b[i] + c[i]) / 3.0;
+            g.e1[3 * j + i] = ab[i];
+            g.e2[3 * j + i] = ac[i];
+        }
+        for (int i = 0; i < 3; ++i) g.va[3 * j + i] = a[i] - g.cen[3 * j + i];
+        const double *vs[3] = {a, b, c};
+        double vr = 0.0;
+        for (int v = 0; v < 3; ++v) {
+            double d[3];
+            sub3(vs[v], &g.cen[3 * j], d);
+            vr = std::max(vr, norm3(d));
+            for (int i = 0; i < 3; ++i) {
+                g.vmin[i] = std::min(g.vmin[i], vs[v][i]);
+                g.vmax[i] = std::max(g.vmax[i], vs[v][i]);
+            }
+        }
+        g.vrad[j] = vr;
+        edge_sum += norm3(ab) + norm3(ac) + norm3(bc);
+    }
+    g.mean_edge = n ? edge_sum / (3.0 * n) : 0.0;
+    return "";
+}
+
+// ------------------------------------------------------------------ Golub-Welsch
+// Eigen-decomposition of a small symmetric matrix by cyclic Jacobi rotations.
+static void sym_eig(int n, std::vector<double> &A, std::vector<double> &V)
+{
+    V.assign(n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A[p * n + q] * A[p * n + q];
+        if (off < 1e-34) break;
+        for (int p = 0; p < n; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[p * n + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                double app = A[p * n + p], aqq = A[q * n + q];
+                double theta = 0.5 * (aqq - app) / apq;
+                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - s * vkq;
+                    V[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+        }
+    }
+}
+
+// Nodes/weights on [-1,1] from recurrence coefficients (diag a_k, offdiag b_k)
+// and the moment mu0 of the weight.
+static void golub_welsch(int n, const std::vector<double> &a, const std::vector<double> &b, double mu0,
+                         std::vector<double> &x, std::vector<double> &w)
+{
+    std::vector<double> J(n * n, 0.0), V;
+    for (int i = 0; i < n; ++i) J[i * n + i] = a[i];
+    for (int i = 0; i + 1 < n; ++i) J[i * n + i + 1] = J[(i + 1) * n + i] = b[i];
+    sym_eig(n, J, V);
+    std::vector<int> idx(n);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::sort(idx.begin(), idx.end(), [&](int p, int q) { return J[p * n + p] < J[q * n + q]; });
+    x.resize(n);
+    w.resize(n);
+    for (int r = 0; r < n; ++r) {
+        int c = idx[r];
+        x[r] = J[c * n + c];
+        w[r] = mu0 * V[0 * n + c] * V[0 * n + c];
+    }
+}
+
+void gauss_legendre01(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    std::vector<double> a(n, 0.0), b(n > 1 ? n - 1 : 0);
+    for (int k = 1; k < n; ++k) b[k - 1] = k / std::sqrt(4.0 * k * k - 1.0);
+    golub_welsch(n, a, b, 2.0, x, w);
+    for (int i = 0; i < n; ++i) { x[i] = 0.5 * (x[i] + 1.0); w[i] *= 0.5; }
+}
+
+void gauss_jacobi10_01(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    // Jacobi alpha = 1, beta = 0 on [-1,1] (weight 1 - t):
+    //   a_k = (beta^2 - alpha^2) / ((2k+s)(2k+s+2)), s = alpha + beta
+    //   b_k = sqrt(4k(k+alpha)(k+beta)(k+s) / ((2k+s)^2 (2k+s+1)(2k+s-1)))
+    const double al = 1.0, be = 0.0, s = al + be;
+    std::vector<double> a(n), b(n > 1 ? n - 1 : 0);
+    for (int k = 0; k < n; ++k) a[k] = (be * be - al * al) / ((2.0 * k + s) * (2.0 * k + s + 2.0));
+    for (int k = 1; k < n; ++k) {
+        double t = 2.0 * k + s;
+        b[k - 1] = std::sqrt(4.0 * k * (k + al) * (k + be) * (k + s) / (t * t * (t + 1.0) * (t - 1.0)));
+    }
+    golub_welsch(n, a, b, 2.0, x, w);
+    // u = (t + 1)/2, (1 - u) = (1 - t)/2, du = dt/2  =>  w_u = w_t / 4
+    for (int i = 0; i < n; ++i) { x[i] = 0.5 * (x[i] + 1.0); w[i] *= 0.25; }
+}
+
+void conical_rule(int m, std::vector<double> &xi, std::vector<double> &eta, std::vector<double> &w)
+{
+    std::vector<double> uj, wj, vl, wl;
+    gauss_jacobi10_01(m, uj, wj);
+    gauss_legendre01(m, vl, wl);
+    xi.clear(); eta.clear(); w.clear();
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) {
+            xi.push_back(uj[a]);
+            eta.push_back((1.0 - uj[a]) * vl[b]);
+            w.push_back(wj[a] * wl[b]);
+        }
+}
+
+void order_thresholds(double tol, int m_max, double *R)
+{
+    // eps_G = 32 q^(2m+1), eps_H = 64 (2m+1) q^(2m+2),
+    // eps_E = 128 (m+1)(2m+1) q^(2m+3), q = 1 / (2 r~): each is below tol
+    // exactly when r~ exceeds 1 / (2 q*), q* the root of eps = tol.
+    for (int m = 1; m < m_max; ++m) {
+        double qG = std::pow(tol / 32.0, 1.0 / (2.0 * m + 1.0));
+        double qH = std::pow(tol / (64.0 * (2.0 * m + 1.0)), 1.0 / (2.0 * m + 2.0));
+        double qE = std::pow(tol / (128.0 * (m + 1.0) * (2.0 * m + 1.0)), 1.0 / (2.0 * m + 3.0));
+        double q = std::min(qG, std::min(qH, qE));
+        R[m] = 0.5 / q;
+    }
+}
+
+void sphere_grid(int L, std::vector<double> &s, std::vector<double> &w)
+{
+    std::vector<double> t, wt;
+    gauss_legendre01(L, t, wt);      // on [0,1]: cos(theta) = 2t - 1, weight 2 wt
+    s.resize(3 * 2 * L * L);
+    w.resize(2 * L * L);
+    int q = 0;
+    for (int a = 0; a < L; ++a) {
+        double ct = 2.0 * t[a] - 1.0, st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+        for (int b = 0; b < 2 * L; ++b) {
+            double ph = M_PI * b / L;
+            s[3 * q] = st * std::cos(ph);
+            s[3 * q + 1] = st * std::sin(ph);
+            s[3 * q + 2] = ct;
+            w[q] = 2.0 * wt[a] * M_PI / L;
+            ++q;
+        }
+    }
+}
+
+double hankel_growth(double x, int L)
+{
+    std::complex<double> I(0.0, 1.0), e = std::exp(I * x);
+    std::complex<double> h0 = -I * e / x, h1 = -e * (x + I) / (x * x);
+    double a0 = std::abs(h0), sum = a0;
+    if (L >= 1) sum += 3.0 * std::abs(h1);
+    for (int n = 1; n < L; ++n) {
+        std::complex<double> h2 = (2.0 * n + 1.0) / x * h1 - h0;
+        sum += (2.0 * n + 3.0) * std::abs(h2);
+        h0 = h1;
+        h1 = h2;
+        if (!std::isfinite(sum)) return 1e300;
+    }
+    return sum / a0;
+}
+
+// ------------------------------------------------------------------ tree
+static inline uint64_t spread3(uint64_t v)
+{
+    v &= 0x1fffff;
+    v = (v | v << 32) & 0x1f00000000ffffULL;
+    v = (v | v << 16) & 0x1f0000ff0000ffULL;
+    v = (v | v << 8) & 0x100f00f00f00f00fULL;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+    v = (v | v << 2) & 0x1249249249249249ULL;
+    return v;
+}
+
+double auto_leaf_edge(const Geometry &g, const bem_params &p)
+{
+    // Far pairs must keep every element pair at the regular order m = 1
+    // (the centroid rule of the far field), i.e. midpoint distances above
+    // R_1 sqrt(A_max).  Leaves a fifth of that radius keep the near field
+    // close to its minimum without crowding the interaction lists.
+    double R[kMaxRule + 1] = {0};
+    order_thresholds(p.quad_tol, std::max(2, p.m_max), R);
+    double r1 = R[1] * std::sqrt(g.max_area);
+    return std::max(r1 / 5.0, 2.0 * g.mean_edge);
+}
+
+void build_tree(const Geometry &g, double leaf_edge, Tree &t)
+{
+    const int64_t n = g.n;
+    double ext = 0.0;
+    for (int i = 0; i < 3; ++i) ext = std::max(ext, g.vmax[i] - g.vmin[i]);
+    ext *= 1.0 + 1e-9;
+    if (ext <= 0) ext = 1.0;
+    for (int i = 0; i < 3; ++i) t.origin[i] = 0.5 * (g.vmin[i] + g.vmax[i]) - 0.5 * ext;
+    t.edge = ext;
+    int depth = 0;
+    if (leaf_edge > 0) depth = (int)std::lround(std::log2(ext / leaf_edge));
+    depth = std::max(0, std::min(depth, 20));
+    t.leaf_depth = depth;
+    const int64_t side = (int64_t)1 << depth;
+    const double box = ext / side;
+    std::vector<uint64_t> code(n);
+    std::vector<int32_t> bx(3 * n);
+    for (int64_t j = 0; j < n; ++j) {
+        for (int i = 0; i < 3; ++i) {
+            int64_t b = (int64_t)std::floor((g.cen[3 * j + i] - t.origin[i]) / box);
+            b = std::max<int64_t>(0, std::min<int64_t>(side - 1, b));
+            bx[3 * j + i] = (int32_t)b;
+        }
+        code[j] = spread3(bx[3 * j]) | (spread3(bx[3 * j + 1]) << 1) | (spread3(bx[3 * j + 2]) << 2);
+    }
+    t.perm.resize(n);
+    std::iota(t.perm.begin(), t.perm.end(), 0);
+    std::stable_sort(t.perm.begin(), t.perm.end(), [&](int64_t a, int64_t b) { return code[a] < code[b]; });
+    t.lv.assign(depth + 1, Level());
+    for (int d = 0; d <= depth; ++d) {
+        Level &L = t.lv[d];
+        L.depth = d;
+        L.box = ext / (double)((int64_t)1 << d);
+        L.elem_cluster.assign(n, -1);
+        int shift = 3 * (depth - d);
+        int64_t i = 0;
+        while (i < n) {
+            uint64_t key = code[t.perm[i]] >> shift;
+            int64_t j = i;
+            while (j < n && (code[t.perm[j]] >> shift) == key) ++j;
+            int32_t c = (int32_t)L.start.size();
+            L.start.push_back(i);
+            L.count.push_back(j - i);
+            int64_t e0 = t.perm[i];
+            int sh = depth - d;
+            L.ix.push_back(bx[3 * e0] >> sh);
+            L.iy.push_back(bx[3 * e0 + 1] >> sh);
+            L.iz.push_back(bx[3 * e0 + 2] >> sh);
+            double z[3] = {t.origin[0] + (L.ix.back() + 0.5) * L.box, t.origin[1] + (L.iy.back() + 0.5) * L.box,
+                           t.origin[2] + (L.iz.back() + 0.5) * L.box};
+            double rad = 0.0, crad = 0.0, amax = 0.0;
+            for (int64_t q = i; q < j; ++q) {
+                int64_t e = t.perm[q];
+                L.elem_cluster[q] = c;
+                double d3[3];
+                sub3(&g.cen[3 * e], z, d3);
+                double dc = norm3(d3);
+                crad = std::max(crad, dc);
+                rad = std::max(rad, dc + g.vrad[e]);
+                amax = std::max(amax, g.area[e]);
+            }
+            // vertex radius: exact maximum over the three vertices
+            rad = 0.0;
+            for (int64_t q = i; q < j; ++q) {
+                int64_t e = t.perm[q];
+                for (int v = 0; v < 3; ++v) {
+                    double vx[3];
+                    for (int k = 0; k < 3; ++k) {
+                        double base = g.cen[3 * e + k] + g.va[3 * e + k];
+                        if (v == 1) base += g.e1[3 * e + k];
+                        if (v == 2) base += g.e2[3 * e + k];
+                        vx[k] = base - z[k];
+                    }
+                    rad = std::max(rad, norm3(vx));
+                }
+            }
+            for (int k = 0; k < 3; ++k) L.z.push_back(z[k]);
+            L.rad.push_back(rad);
+            L.crad.push_back(crad);
+            L.amax.push_back(amax);
+            L.rmax = std::max(L.rmax, rad);
+            i = j;
+        }
+    }
+    // parent / children links (clusters are nested runs of the Morton order)
+    for (int d = 0; d <= depth; ++d) {
+        Level &L = t.lv[d];
+        int nc = (int)L.start.size();
+        L.parent.assign(nc, -1);
+        L.child0.assign(nc, 0);
+        L.nchild.assign(nc, 0);
+        if (d > 0) {
+            const Level &P = t.lv[d - 1];
+            for (int c = 0; c < nc; ++c) L.parent[c] = P.elem_cluster[L.start[c]];
+        }
+    }
+    for (int d = 0; d < depth; ++d) {
+        Level &L = t.lv[d];
+        const Level &C = t.lv[d + 1];
+        int nc = (int)L.start.size();
+        for (int c = 0; c < nc; ++c) { L.child0[c] = -1; L.nchild[c] = 0; }
+        for (int c = 0; c < (int)C.start.size(); ++c) {
+            int p = C.parent[c];
+            if (L.child0[p] < 0) L.child0[p] = c;
+            L.nchild[p]++;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ plan
+void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k, FreqPlan &fp)
+{
+    fp = FreqPlan();
+    fp.k = k;
+    fp.direct = (p.mode == BEM_MODE_DIRECT);
+    const int D = t.leaf_depth;
+    double R[kMaxRule + 1] = {0};
+    order_thresholds(p.quad_tol, std::max(2, p.m_max), R);
+    const double r1 = R[1] * (1.0 + 1e-9);
+    // expansion length per depth (Eq. FMMTruncation with the level's largest radius)
+    std::vector<int> Ld(D + 1, 0);
+    for (int d = 0; d <= D; ++d) {
+        double x = 2.0 * t.lv[d].rmax * k;
+        double L = x + p.trunc_factor * std::log10(x + M_PI);
+        Ld[d] = std::max(p.L_min, (int)std::ceil(L - 1e-12));
+    }
+    // near lists per depth, interaction lists per depth
+    std::vector<std::vector<int32_t>> near_prev(1, std::vector<int32_t>(1, 0));
+    std::vector<FarLevel> far_all(D + 1);
+    std::map<std::tuple<int, int, int>, double> growth_cache;
+    for (int d = 1; d <= D; ++d) {
+        const Level &L = t.lv[d];
+        const Level &P = t.lv[d - 1];
+        int nc = (int)L.start.size();
+        std::vector<std::vector<int32_t>> near_cur(nc);
+        FarLevel &F = far_all[d];
+        F.depth = d;
+        F.L = Ld[d];
+        F.nc = nc;
+        F.il_ptr.assign(nc + 1, 0);
+        std::map<std::tuple<int, int, int>, int> off_index;
+        growth_cache.clear();
+        std::vector<std::vector<std::pair<int32_t, int32_t>>> il(nc);
+        for (int c = 0; c < nc; ++c) {
+            int par = L.parent[c];
+            for (int32_t sp : near_prev[par]) {
+                for (int s = P.child0[sp]; s < P.child0[sp] + P.nchild[sp]; ++s) {
+                    bool far = !fp.direct;
+                    if (far) {
+                        double X[3] = {L.z[3 * c] - L.z[3 * s], L.z[3 * c + 1] - L.z[3 * s + 1],
+                                       L.z[3 * c + 2] - L.z[3 * s + 2]};
+                        double dist = norm3(X);
+                        if (!(dist > p.admissibility * (L.rad[c] + L.rad[s]))) far = false;
+                        if (far && !(dist - L.crad[c] - L.crad[s] > r1 * std::sqrt(L.amax[s]))) far = false;
+                        if (far) {
+                            auto key = std::make_tuple(L.ix[c] - L.ix[s], L.iy[c] - L.iy[s], L.iz[c] - L.iz[s]);
+                            auto it = growth_cache.find(key);
+                            double gr;
+                            if (it == growth_cache.end()) {
+                                gr = hankel_growth(k * dist, F.L);
+                                growth_cache[key] = gr;
+                            } else {
+                                gr = it->second;
+                            }
+                            if (!(gr <= p.stability_max)) far = false;
+                        }
+                    }
+                    if (far) {
+                        auto key = std::make_tuple(L.ix[c] - L.ix[s], L.iy[c] - L.iy[s], L.iz[c] - L.iz[s]);
+                        auto it = off_index.find(key);
+                        int oi;
+                        if (it == off_index.end()) {
+                            oi = (int)off_index.size();
+                            off_index[key] = oi;
+                            F.offsets.push_back(std::get<0>(key) * L.box);
+                            F.offsets.push_back(std::get<1>(key) * L.box);
+                            F.offsets.push_back(std::get<2>(key) * L.box);
+                        } else {
+                            oi = it->second;
+                        }
+                        il[c].push_back({s, oi});
+                    } else {
+                        near_cur[c].push_back(s);
+                    }
+                }
+            }
+        }
+        for (int c = 0; c < nc; ++c) {
+            F.il_ptr[c + 1] = F.il_ptr[c] + (int32_t)il[c].size();
+            for (auto &e : il[c]) { F.il_src.push_back(e.first); F.il_off.push_back(e.second); }
+        }
+        F.n_inter = (int64_t)F.il_src.size();
+        near_prev.swap(near_cur);
+    }
+    if (D == 0) near_prev.assign(1, std::vector<int32_t>(1, 0));
+    // leaf near lists
+    const Level &Lf = t.lv[D];
+    int nl = (int)Lf.start.size();
+    fp.near_ptr.assign(nl + 1, 0);
+    fp.nnz = 0;
+    for (int c = 0; c < nl; ++c) {
+        std::vector<int32_t> v = near_prev[c];
+        std::sort(v.begin(), v.end());
+        int64_t cols = 0;
+        for (int32_t s : v) { fp.near_src.push_back(s); cols += Lf.count[s]; }
+        fp.near_ptr[c + 1] = (int32_t)fp.near_src.size();
+        fp.nnz += cols * Lf.count[c];
+    }
+    for (int d = 1; d <= D; ++d)
+        if (far_all[d].n_inter > 0) {
+            fp.far.push_back(std::move(far_all[d]));
+            fp.max_L = std::max(fp.max_L, fp.far.back().L);
+        }
+}
+
+}  // namespace bem

@@ -1,0 +1,107 @@
+// bem_plan.hpp -- host-side (C++, FP64) geometry, quadrature tables and the
+// cluster tree / per-frequency plan of the BEM + FMM operator.
+//
+// Method: arXiv 2312.00005 (NumCalc).  Geometry Sec. 2.3 / App. A;
+// quadrature Sec. 3.1; clustering and lists Sec. 3.3.2-3.3.4; truncation
+// Eq. FMMTruncation; admissibility Eq. Farfieldcond.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/bemfmm.h"
+
+namespace bem {
+
+constexpr int kMaxRule = 6;          // regular order cap supported on the device
+constexpr int kMaxLevels = 16;
+
+// ---------------------------------------------------------------- geometry
+struct Geometry {
+    int64_t n = 0;
+    std::vector<double> cen;   // 3n midpoints (mean of the vertices)
+    std::vector<double> nrm;   // 3n unit normals, (b - a) x (c - a) / |.|
+    std::vector<double> area;  // n
+    std::vector<double> va;    // 3n vertex a relative to the midpoint
+    std::vector<double> e1;    // 3n b - a
+    std::vector<double> e2;    // 3n c - a
+    std::vector<double> vmin, vmax;  // bounding box of all vertices
+    std::vector<double> vrad;  // per element: max distance of its vertices to its midpoint
+    double mean_edge = 0.0;
+    double max_area = 0.0;
+};
+
+// Returns an empty string or an error message (degenerate triangle, bad index).
+std::string compute_geometry(const double *nodes, int64_t n_nodes, const int32_t *tris,
+                             int64_t n, Geometry &g);
+
+// ---------------------------------------------------------------- quadrature tables
+// Gauss rules by the Golub-Welsch eigenvalue method (Jacobi rotations on the
+// symmetric tridiagonal Jacobi matrix of the three-term recurrence).
+void gauss_legendre01(int n, std::vector<double> &x, std::vector<double> &w);  // on [0,1]
+void gauss_jacobi10_01(int n, std::vector<double> &x, std::vector<double> &w); // weight (1-u) on [0,1]
+// m x m conical-product triangle rule on {xi, eta >= 0, xi + eta <= 1}:
+// xi = u (Gauss-Jacobi(1,0)), eta = (1 - u) v (Gauss-Legendre); weights sum 1/2.
+void conical_rule(int m, std::vector<double> &xi, std::vector<double> &eta, std::vector<double> &w);
+// R[m] for m = 1..m_max-1: the regular order is the smallest m with r~ > R[m]
+// (all three a-priori estimates of Sec. 3.1.4 below tol), else m_max.
+void order_thresholds(double tol, int m_max, double *R);
+// unit-sphere grid: L Gauss-Legendre nodes in cos(theta) x 2L azimuths
+// phi = pi b / L; weights w_GL * pi / L (sum 4 pi).  s: 3 * 2L^2.
+void sphere_grid(int L, std::vector<double> &s, std::vector<double> &w);
+// sum_{n<=L} (2n+1) |h_n(x)| / |h_0(x)| (h_n by upward recursion)
+double hankel_growth(double x, int L);
+
+// ---------------------------------------------------------------- tree
+struct Level {
+    int depth = 0;
+    double box = 0.0;                 // box edge at this depth
+    std::vector<int64_t> start, count;  // element ranges (internal order)
+    std::vector<int32_t> ix, iy, iz;  // integer box coordinates
+    std::vector<double> z;            // 3 * nc box centres
+    std::vector<double> rad;          // max |vertex - z| (admissibility radius, Sec. 3.3.1)
+    std::vector<double> crad;         // max |midpoint - z|
+    std::vector<double> amax;         // max element area
+    std::vector<int32_t> parent;      // cluster index at depth - 1
+    std::vector<int32_t> child0, nchild;  // children range at depth + 1
+    std::vector<int32_t> elem_cluster;    // per element (internal order)
+    double rmax = 0.0;
+};
+
+struct Tree {
+    double origin[3] = {0, 0, 0};
+    double edge = 0.0;
+    int leaf_depth = 0;
+    std::vector<int64_t> perm;        // internal -> caller index
+    std::vector<Level> lv;            // depth 0 .. leaf_depth
+};
+
+void build_tree(const Geometry &g, double leaf_edge, Tree &t);
+double auto_leaf_edge(const Geometry &g, const bem_params &p);
+
+// ---------------------------------------------------------------- per-frequency plan
+struct FarLevel {
+    int depth = 0;
+    int L = 0;
+    int nc = 0;                          // clusters at this depth
+    std::vector<int32_t> il_ptr;         // nc + 1
+    std::vector<int32_t> il_src, il_off; // interaction list entries
+    std::vector<double> offsets;         // 3 * noff translation vectors z_t - z_s
+    int64_t n_inter = 0;
+};
+
+struct FreqPlan {
+    double k = 0.0;
+    bool direct = false;
+    std::vector<FarLevel> far;           // used levels, coarse to fine
+    // near field at the leaf depth: per leaf a list of source leaves
+    std::vector<int32_t> near_ptr, near_src;
+    int64_t nnz = 0;
+    int max_L = 0;
+};
+
+// Builds near and interaction lists (Sec. 3.3.4) for wavenumber k.
+void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k, FreqPlan &fp);
+
+}  // namespace bem

@@ -1,0 +1,140 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.  Tolerances:
+  * direct product (every pair by quadrature, FP32):   ||y - y_o|| / ||y_o|| <= 2e-5
+  * FMM product: FP32 part 2e-5 plus the FMM truncation bound stated per case
+  * surface pressure of a solve (FP32 products, GMRES tol 1e-7): <= 1e-4
+  * field at exterior points: <= 1e-4
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_00005_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+C, RHO = 343.0, 1.21
+
+
+@pytest.fixture(scope="module")
+def bem():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_00005_gb300 import bemfmm
+    bemfmm.lib()
+    return bemfmm
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _mixed_bc(n, seed):
+    rng = np.random.default_rng(seed)
+    bct = rng.integers(0, 3, n).astype(np.int32)
+    region = rng.integers(0, 4, n).astype(np.int32)
+    adm = (rng.uniform(0, 0.5, 4) * np.exp(1j * rng.uniform(-1.5, 1.5, 4))) / (RHO * C)
+    return bct, region, adm
+
+
+def _oracle_coeffs(bct, region, adm, k):
+    beta = RHO * C * adm[region]
+    cp, cq, _, _ = oracle.column_coeffs(bct, k, C, RHO, beta)
+    return cp, cq
+
+
+@pytest.mark.parametrize("lev,freq", [(2, 800.0), (3, 1500.0)])
+def test_direct_matvec_matches_oracle(bem, lev, freq):
+    nodes, tris = inputs.icosphere(lev, 0.1)
+    n = tris.shape[0]
+    k = 2 * np.pi * freq / C
+    bct, region, adm = _mixed_bc(n, 5)
+    mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region, mode=bem.MODE_DIRECT)
+    x = inputs.random_complex(n, 21)
+    y = mesh.matvec(freq, torch.tensor(x, dtype=torch.complex64, device="cuda"), admittance=adm, c=C, rho=RHO)
+    cp, cq = _oracle_coeffs(bct, region, adm, k)
+    A = oracle.assemble(nodes, tris, k, cp, cq)
+    yo = A @ x
+    err = _rel(y.cpu().numpy(), yo)
+    assert err < 2e-5, err
+
+
+def test_fmm_matvec_matches_oracle(bem):
+    """N = 5120 at 2 kHz: three FMM levels.  The FMM far field reproduces the
+    paper's dense operator up to the plane-wave truncation (Eq. FMMTruncation);
+    a larger truncation factor shrinks the difference."""
+    nodes, tris = inputs.icosphere(4, 0.1)
+    n = tris.shape[0]
+    freq = 2000.0
+    k = 2 * np.pi * freq / C
+    bct, region, adm = _mixed_bc(n, 7)
+    x = inputs.random_complex(n, 22)
+    cp, cq = _oracle_coeffs(bct, region, adm, k)
+    A = oracle.assemble(nodes, tris, k, cp, cq)
+    yo = A @ x
+    errs = {}
+    for tf in (1.8, 6.0):
+        mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region, trunc_factor=tf)
+        st = mesh.stats(freq, c=C)
+        assert st["levels"] >= 2
+        y = mesh.matvec(freq, torch.tensor(x, dtype=torch.complex64, device="cuda"), admittance=adm, c=C, rho=RHO)
+        errs[tf] = _rel(y.cpu().numpy(), yo)
+        mesh.close()
+    print("fmm matvec rel err", errs)
+    assert errs[1.8] < 2e-3, errs
+    assert errs[6.0] < 1e-4, errs
+
+
+def test_solve_and_field_match_oracle(bem):
+    nodes, tris = inputs.icosphere(3, 0.1)
+    freq = 1000.0
+    pts = inputs.fibonacci_sphere(100, 1.0)
+    mesh = bem.Mesh(nodes, tris)
+    src = [bem.plane_wave((0, 0, 1))]
+    p, q, info = mesh.solve(freq, src, tol=1e-7, c=C, rho=RHO)
+    assert info["converged"], info
+    fld = mesh.evaluate(freq, p, q, pts, src, c=C, rho=RHO)
+    po, qo, _ = oracle.solve(nodes, tris, freq, c=C, rho=RHO, sources=[("plane", (0, 0, 1.0), 1.0)])
+    fo = oracle.field(nodes, tris, freq, po, qo, pts, c=C, sources=[("plane", (0, 0, 1.0), 1.0)])
+    ep = _rel(p.cpu().numpy(), po)
+    ef = _rel(fld.cpu().numpy(), fo)
+    assert ep < 1e-4, ep
+    assert ef < 1e-4, ef
+    assert np.allclose(q.cpu().numpy(), 0)
+
+
+def test_mixed_boundary_solve_matches_oracle(bem):
+    nodes, tris = inputs.icosphere(3, 0.1)
+    n = tris.shape[0]
+    freq = 1200.0
+    k, omega = 2 * np.pi * freq / C, 2 * np.pi * freq
+    bct, region, adm = _mixed_bc(n, 9)
+    rng = np.random.default_rng(4)
+    bcv = (rng.normal(size=n) + 1j * rng.normal(size=n)) * 1e-3
+    bcv[bct == 1] *= 1e3       # pressures of order 1 Pa
+    mesh = bem.Mesh(nodes, tris, bc_type=bct, bc_value=bcv, region=region)
+    src = [bem.point_source((0.3, 0.1, -0.2), 2.0 + 1.0j)]
+    p, q, info = mesh.solve(freq, src, admittance=adm, tol=1e-7, c=C, rho=RHO)
+    po, qo, _ = oracle.solve(nodes, tris, freq, c=C, rho=RHO, sources=[("point", (0.3, 0.1, -0.2), 2.0 + 1.0j)],
+                             bc_type=bct, bc_value=bcv, beta=RHO * C * adm[region])
+    assert _rel(p.cpu().numpy(), po) < 1e-4
+    assert _rel(q.cpu().numpy(), qo) < 2e-4
+
+
+def test_subdivision_limit_is_reported(bem):
+    nodes, tris = inputs.icosphere(1, 0.1)
+    tris = np.vstack([tris, tris[5:6]])
+    mesh = bem.Mesh(nodes, tris)
+    with pytest.raises(bem.BemError) as e:
+        mesh.solve(1000.0, [bem.plane_wave()])
+    assert e.value.code == bem.E_SUBDIV_LIMIT
+    assert "element 5" in str(e.value) or "element 80" in str(e.value)
+
+
+def test_not_converged_warning(bem):
+    nodes, tris = inputs.icosphere(2, 0.1)
+    mesh = bem.Mesh(nodes, tris)
+    p, q, info = mesh.solve(1000.0, [bem.plane_wave()], tol=1e-12, max_iter=2)
+    assert info["status"] == bem.W_NOT_CONVERGED and not info["converged"]
+    assert info["iterations"] == 2

@@ -1,0 +1,90 @@
+"""CPU checks of the CUDA library: it builds for sm_103a, loads, exports
+every entry point declared in include/*.h, and its host-side plan (Sec. 3.3.4
+near / interaction lists) covers every element pair exactly once."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2312_00005_gb300 import bemfmm, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"\b(bem_[a-z_0-9]+)\s*\(", txt):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2312_00005_gb300 import build
+    build.build()
+    return bemfmm.lib()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert {"bem_mesh_create", "bem_matvec", "bem_solve", "bem_evaluate", "bem_last_error"} <= names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_params_default_are_the_papers(lib):
+    p = bemfmm.default_params()
+    assert p.quad_tol == 1e-3 and p.m_max == 6 and p.rt_subdiv == 1.3 and p.max_depth == 15
+    assert p.trunc_factor == 1.8 and p.L_min == 8
+    assert abs(p.admissibility - 2 / np.sqrt(3)) < 1e-15
+
+
+@pytest.mark.parametrize("lev,freq", [(3, 1000.0), (4, 2000.0), (5, 4000.0)])
+def test_plan_partitions_all_pairs(lib, lev, freq):
+    nodes, tris = inputs.icosphere(lev, 0.1)
+    n = tris.shape[0]
+    st = bemfmm.plan_stats_host(nodes, tris, freq)
+    assert st["near_nnz"] + st["far_pairs"] == n * n
+    assert st["near_nnz"] >= n                  # the diagonal is near
+    for L in st["L"]:
+        assert L >= 8
+
+
+def test_plan_on_ragged_head_like_surface(lib):
+    nodes, tris = inputs.bumpy_ellipsoid(13)      # 3380 triangles, uneven sizes
+    n = tris.shape[0]
+    st = bemfmm.plan_stats_host(nodes, tris, 3000.0)
+    assert st["near_nnz"] + st["far_pairs"] == n * n
+
+
+def test_direct_mode_plan_is_dense(lib):
+    nodes, tris = inputs.icosphere(2, 0.1)
+    p = bemfmm.default_params(mode=bemfmm.MODE_DIRECT)
+    st = bemfmm.plan_stats_host(nodes, tris, 1000.0, params=p)
+    assert st["near_nnz"] == tris.shape[0] ** 2 and st["far_pairs"] == 0 and st["levels"] == 0
+
+
+def test_low_frequency_falls_back_to_near_field(lib):
+    """At low k the Hankel growth bound (FP32 stability) rejects far pairs."""
+    nodes, tris = inputs.icosphere(4, 0.1)
+    hi = bemfmm.plan_stats_host(nodes, tris, 4000.0)
+    lo = bemfmm.plan_stats_host(nodes, tris, 50.0)
+    assert lo["far_pairs"] < hi["far_pairs"]
+
+
+def test_bad_arguments_are_rejected(lib):
+    nodes, tris = inputs.icosphere(1, 0.1)
+    bad = tris.copy()
+    bad[0, 0] = 10 ** 6
+    with pytest.raises(bemfmm.BemError):
+        bemfmm.plan_stats_host(nodes, bad, 1000.0)
+    deg = tris.copy()
+    deg[0, 1] = deg[0, 0]
+    with pytest.raises(bemfmm.BemError):
+        bemfmm.plan_stats_host(nodes, deg, 1000.0)
