@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Benchmark of the FMM-BEM matrix-vector product inside the iterative solve.
+
+Workload (default): sound-hard sphere r = 0.1 m as an icosphere of 20480
+triangles, plane wave along +z at 4 kHz, c = 343 m/s, rho = 1.21 kg/m^3,
+100 field points on a 1 m sphere (synthetic mesh standing in for the
+paper's sphere benchmark meshes).
+
+One step = one whole pass of the hot path at one frequency: per-frequency
+plan and translation tables, near-field quadrature, device GMRES to a
+relative residual of 1e-6 with FMM products, and the field at the 100
+points.  The mesh (geometry, clustering) is created once, outside the timed
+region.  value = FMM matrix-vector products per second of timed solve time;
+ms_per_step = seconds per frequency.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FMM-BEM matvecs/s and solve s/frequency at stated rel. error vs FP64; % roofline"
+UNIT = "matvecs/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _workload(name):
+    from paper_2312_00005_gb300 import inputs
+    return inputs.workload(name)
+
+
+# ---------------------------------------------------------------------- oracle CPU legs
+def oracle_sample(W, seconds=15.0, gmres_iters=40):
+    """Time the FP64 oracle on a bounded sample of the same workload and scale
+    it to matvecs/s of a full dense solve: assembly of all N rows (rows are
+    computed on the fly, sample timed) + gmres_iters dense products (a dense
+    row block, sample timed).  Returns (matvecs/s, description, threads)."""
+    import oracle
+    nodes, tris, f, c, rho = W["nodes"], W["tris"], W["freq"], W["c"], W["rho"]
+    n = tris.shape[0]
+    k = 2 * math.pi * f / c
+    cp = np.ones(n, np.complex128)
+    cq = np.zeros(n, np.complex128)
+    x = np.ones(n, np.complex128)
+    rng = np.random.default_rng(0)
+    oracle.lib()
+    threads = oracle.num_threads()
+    # calibrate
+    rows = rng.choice(n, size=min(n, 2 * threads), replace=False)
+    t0 = time.perf_counter()
+    oracle.matvec_rows(nodes, tris, k, cp, cq, x, rows)
+    dt = time.perf_counter() - t0
+    per_row = dt / len(rows)
+    nrows = int(max(len(rows), min(n, 0.7 * seconds / max(per_row, 1e-9))))
+    rows = rng.choice(n, size=nrows, replace=False)
+    t0 = time.perf_counter()
+    oracle.matvec_rows(nodes, tris, k, cp, cq, x, rows)
+    t_rows = time.perf_counter() - t0
+    t_assemble = t_rows / nrows * n
+    # dense product on a row block of a stored matrix
+    blk = int(min(n, max(256, (64 << 20) // (16 * n))))
+    A = (rng.normal(size=(blk, n)) + 1j * rng.normal(size=(blk, n))).astype(np.complex128)
+    xv = np.ascontiguousarray(x)
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.matvec_dense_block(A, xv)
+    t_mv = (time.perf_counter() - t0) / reps * (n / blk)
+    total = t_assemble + gmres_iters * t_mv
+    desc = ("oracle (FP64 C, OpenMP) on %d sampled rows of the %d x %d operator with the paper's quadrature "
+            "(%.2f s) -> assembly %.1f s; dense product on a %d-row block -> %.3f s per product; "
+            "solve = assembly + %d products" % (nrows, n, n, t_rows, t_assemble, blk, t_mv, gmres_iters))
+    return gmres_iters / total, desc, threads, total
+
+
+# ---------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    from paper_2312_00005_gb300 import bemfmm, build as bld
+    from paper_2312_00005_gb300 import inputs
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    bld.build()
+    bemfmm.lib()
+    W = _workload(args.workload)
+    nodes, tris, f, c, rho = W["nodes"], W["tris"], W["freq"], W["c"], W["rho"]
+    n = tris.shape[0]
+    pts = W["field_points"]
+    src = [bemfmm.plane_wave(W["plane_dir"], W["amp"])]
+    mesh = bemfmm.Mesh(nodes, tris)
+    dev = torch.device("cuda", local)
+    p = torch.empty(n, dtype=torch.complex64, device=dev)
+    q = torch.empty(n, dtype=torch.complex64, device=dev)
+    fld = torch.empty(pts.shape[0], dtype=torch.complex64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def one_step():
+        _, _, info = mesh.solve(f, src, tol=args.tol, max_iter=args.max_iter, c=c, rho=rho, p=p, q=q)
+        mesh.evaluate(f, p, q, pts, src, c=c, rho=rho, out=fld)
+        return info
+
+    def timed(k_steps, host_io=False):
+        tot_ms, mv, last = 0.0, 0, None
+        hp = torch.empty(n, dtype=torch.complex64, pin_memory=True)
+        hq = torch.empty(n, dtype=torch.complex64, pin_memory=True)
+        hf = torch.empty(pts.shape[0], dtype=torch.complex64, pin_memory=True)
+        for s in range(k_steps):
+            mesh.release_plan()
+            flush.fill_(float(s))
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = one_step()
+            if host_io:
+                hp.copy_(p, non_blocking=True)
+                hq.copy_(q, non_blocking=True)
+                hf.copy_(fld, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot_ms += e0.elapsed_time(e1)
+            mv += info["iterations"] + info["restarts"]
+            last = info
+        return tot_ms, mv, last
+
+    # warm-up
+    for _ in range(args.warmup):
+        mesh.release_plan()
+        one_step()
+    torch.cuda.synchronize()
+    # headline timed region (device-resident inputs)
+    clk = Clocks(local)
+    clk.start()
+    l0 = bemfmm.launch_count()
+    t_ms, mvs, info = timed(args.steps)
+    launches = bemfmm.launch_count() - l0
+    clocks = clk.stop()
+    # end-to-end through the public API with host buffers (field points from
+    # the host, results copied back to pinned host memory inside the region)
+    e_ms, e_mvs, _ = timed(args.steps, host_io=True)
+    # per-kernel CUDA-event timing on the library's stream (second pass)
+    bemfmm.timing_enable(True)
+    k_ms, k_mvs, _ = timed(args.steps)
+    kernels = {}
+    for name in ["k_near_spmv", "k_near_store", "k_aggregate", "k_transfer", "k_disaggregate", "k_prep",
+                 "k_gm_dots", "k_gm_update", "k_gm_reduce", "k_gm_givens", "k_gm_scale", "k_dtable", "k_rhs",
+                 "k_field", "k_gm_xupdate", "k_gm_backsolve", "k_pq", "k_gm_start", "k_norm_part", "k_gather"]:
+        ms, cnt = bemfmm.timing_get(name)
+        if cnt:
+            kernels[name] = {"total_ms": ms, "launches": cnt, "avg_us": 1e3 * ms / cnt}
+    bemfmm.timing_enable(False)
+    stats = mesh.stats(f, c=c)
+
+    # max over ranks
+    t_max = t_ms
+    total_mv = mvs
+    e_max, e_tot = e_ms, e_mvs
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms, e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max, e_max = float(tt[0]), float(tt[1])
+        mm = torch.tensor([mvs, e_mvs], dtype=torch.float64, device=dev)
+        dist.all_reduce(mm, op=dist.ReduceOp.SUM)
+        total_mv, e_tot = float(mm[0]), float(mm[1])
+    value = total_mv / (t_max / 1e3)
+    e2e = e_tot / (e_max / 1e3)
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # accuracy of the measured result
+    acc = series_errors(W, p.cpu().numpy(), fld.cpu().numpy())
+    acc.update(residual_vs_fp64(W, p.cpu().numpy(), args))
+
+    peaks, peak_src = _peaks()
+    roof = roofline(kernels, stats, n, peaks, peak_src)
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "cf32", "data": "synthetic",
+        "config": {"workload": W["name"], "n_elements": n, "freq_hz": f, "mesh": "icosphere r=0.1 m",
+                   "source": "plane wave +z", "field_points": int(pts.shape[0]), "gmres_tol": args.tol,
+                   "l2_flush": "256 MB write between steps", "parallelism": "replicas" if ws > 1 else "single"},
+        "solve_s_per_frequency": round(t_max / args.steps / 1e3, 6),
+        "matvecs_per_solve": round(mvs / args.steps, 2),
+        "gmres_iterations": info["iterations"], "relres": info["relres"],
+        "rel_error": acc,
+        "plan": {k: stats[k] for k in ("levels", "L", "n_clusters", "n_interactions", "near_nnz", "far_pairs",
+                                       "leaf_edge")},
+        "kernels": kernels,
+        "roofline": roof,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "e2e": {"value": round(e2e, 2), "unit": UNIT,
+                "h2d_bytes_per_step": int(pts.size * 8 + 64),
+                "d2h_bytes_per_step": int((2 * n + pts.shape[0]) * 8)},
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        v, desc, thr, tot = oracle_sample(W, seconds=args.cpu_seconds, gmres_iters=max(1, int(round(mvs / args.steps))))
+        out["cpu_baseline"] = {"value": round(v, 4), "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc,
+                               "solve_s_per_frequency_est": round(tot, 2)}
+    print(json.dumps(out))
+    sys.stdout.flush()
+    mesh.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def series_errors(W, p, fld):
+    """Relative errors of the measured surface pressure (at the collocation
+    points) and field against the sound-hard sphere series solution."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from closed_forms import sphere_plane_wave
+    import oracle
+    k = 2 * math.pi * W["freq"] / W["c"]
+    cen, _, _ = oracle.geometry(W["nodes"], W["tris"])
+    ps = sphere_plane_wave(cen, k, 0.1)
+    pf = sphere_plane_wave(W["field_points"], k, 0.1)
+    es = np.abs(p - ps) / np.abs(ps)
+    ef = np.abs(fld - pf) / np.abs(pf)
+    return {"surface_vs_series_mean": float(es.mean()), "surface_vs_series_max": float(es.max()),
+            "field_vs_series_max": float(ef.max())}
+
+
+def residual_vs_fp64(W, p, args, nrows=48):
+    """FP64 residual of the measured surface pressure on sampled rows of the
+    paper's dense operator (oracle, rows computed one by one)."""
+    import oracle
+    nodes, tris, f, c = W["nodes"], W["tris"], W["freq"], W["c"]
+    n = tris.shape[0]
+    k = 2 * math.pi * f / c
+    rows = np.random.default_rng(1).choice(n, size=nrows, replace=False)
+    cp = np.ones(n, np.complex128)
+    cq = np.zeros(n, np.complex128)
+    Ap = oracle.matvec_rows(nodes, tris, k, cp, cq, p.astype(np.complex128), rows)
+    cen, nrm, _ = oracle.geometry(nodes, tris)
+    b = oracle.rhs(cen[rows], nrm[rows], k, [("plane", W["plane_dir"], W["amp"])])
+    return {"fp64_residual_sampled_rows": float(np.linalg.norm(Ap - b) / np.linalg.norm(b)), "rows": nrows}
+
+
+def roofline(kernels, stats, n, peaks, peak_src):
+    """Roofline of the kernel with the largest total time in the timed steps."""
+    if not kernels:
+        return None
+    name = max(kernels, key=lambda k: kernels[k]["total_ms"])
+    avg_s = kernels[name]["avg_us"] * 1e-6
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    nnz = stats["near_nnz"]
+    if name == "k_near_spmv":
+        # values (8 B per near pair) + column list (4 B per leaf column) + x, y
+        byts = 8 * nnz + 16 * n
+        ach = byts / avg_s / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "traffic": None, "algorithmic_bytes": byts,
+                "peak_source": peak_src}
+    return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None, "avg_us": kernels[name]["avg_us"], "peak_source": peak_src}
+
+
+# ---------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    W = _workload(args.workload)
+    n = W["tris"].shape[0]
+    per = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(W, seconds=per)
+    vals, descs, tots = [], [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, d, thr, tot = oracle_sample(W, seconds=per)
+        vals.append(v)
+        descs.append(d)
+        tots.append(tot)
+    wall = time.perf_counter() - t0
+    v = float(np.mean(vals))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * float(np.mean(tots)), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": W["name"], "n_elements": n, "freq_hz": W["freq"]},
+        "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": thr, "kind": "oracle", "sample": descs[-1]},
+        "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "sample_wall_s": round(wall, 2),
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sphere20480_4k")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--max-iter", type=int, default=1000)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -188,6 +188,19 @@ int bem_mesh_stats(void *mesh, double freq_hz, const bem_medium *medium, bem_pla
 int bem_plan_stats_host(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tris,
                         const bem_params *params, double freq_hz, double c, bem_plan_stats *out);
 
+/* Free the per-frequency plan of a mesh (lists, translation tables, stored
+ * near-field entries); the next call at any frequency rebuilds it. */
+int bem_mesh_release_plan(void *mesh);
+
+/* Kernel timing with CUDA events recorded on the library's own stream around
+ * every kernel it launches (the GMRES step is then launched kernel by kernel
+ * instead of as a CUDA graph).  enable = 1 starts (and clears) the record,
+ * 0 stops it.  bem_timing_get returns, for the kernel named `name` (e.g.
+ * "k_near_spmv"), the summed milliseconds and the number of launches
+ * resolved so far; it returns BEM_E_ARG for a name never timed. */
+int bem_timing_enable(int enable);
+int bem_timing_get(const char *name, double *total_ms, int64_t *launches);
+
 /* Number of kernels this library has launched in this process. */
 uint64_t bem_launch_count(void);
 

@@ -78,6 +78,7 @@ def lib():
                 "orc_assemble": (i, [P, P, l, d, P, P, P, P, P]),
                 "orc_matvec_rows": (i, [P, P, l, d, P, P, P, P, P, l, P, P]),
                 "orc_matvec_dense": (None, [P, l, P, P]),
+                "orc_matvec_block": (None, [P, l, l, P, P]),
                 "orc_gmres": (i, [P, l, P, P, d, i, i, P, P]),
                 "orc_incident": (None, [P, P, l, d, i, P, P, P, P]),
                 "orc_field": (i, [P, P, l, d, P, P, P, P, l, P, P]),
@@ -266,6 +267,14 @@ def matvec_dense(A, x):
     A, x = _c128(A), _c128(x)
     y = np.zeros(A.shape[0], np.complex128)
     lib().orc_matvec_dense(_p(A), A.shape[0], _p(x), _p(y))
+    return y
+
+
+def matvec_dense_block(A, x):
+    """y = A x for a dense (rows x n) block."""
+    A, x = _c128(A), _c128(x)
+    y = np.zeros(A.shape[0], np.complex128)
+    lib().orc_matvec_block(_p(A), A.shape[0], A.shape[1], _p(x), _p(y))
     return y
 
 

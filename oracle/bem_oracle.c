@@ -667,6 +667,19 @@ void orc_matvec_dense(const double *A, long n, const double *x, double *y)
     }
 }
 
+/* y = A x for a dense row-major complex block A of `rows` x n */
+void orc_matvec_block(const double *A, long rows, long n, const double *x, double *y)
+{
+    const cplx *Av = (const cplx *)A, *xv = (const cplx *)x;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < rows; ++i) {
+        cplx s = 0.0;
+        for (long j = 0; j < n; ++j) s += Av[i * n + j] * xv[j];
+        y[2 * i] = creal(s);
+        y[2 * i + 1] = cimag(s);
+    }
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

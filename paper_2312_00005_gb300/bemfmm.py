@@ -14,7 +14,8 @@ import numpy as np
 
 __all__ = [
     "VELO", "PRES", "ADMI", "MODE_FMM", "MODE_DIRECT", "BemError", "Params", "Medium", "Source",
-    "SolveInfo", "PlanStats", "Mesh", "lib", "launch_count", "plane_wave", "point_source",
+    "SolveInfo", "PlanStats", "Mesh", "lib", "launch_count", "plane_wave", "point_source", "timing_enable",
+    "timing_get", "plan_stats_host", "default_params",
 ]
 
 VELO, PRES, ADMI = 0, 1, 2
@@ -104,6 +105,10 @@ def lib():
             "bem_mesh_stats": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), ctypes.POINTER(PlanStats)]),
             "bem_plan_stats_host": (ctypes.c_int, [P, i64, P, i64, ctypes.POINTER(Params), d, d,
                                                    ctypes.POINTER(PlanStats)]),
+            "bem_mesh_release_plan": (ctypes.c_int, [P]),
+            "bem_timing_enable": (ctypes.c_int, [ctypes.c_int]),
+            "bem_timing_get": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_int64)]),
             "bem_launch_count": (ctypes.c_uint64, []),
             "bem_last_error": (ctypes.c_char_p, []),
         }
@@ -117,6 +122,20 @@ def lib():
 
 def launch_count() -> int:
     return int(lib().bem_launch_count())
+
+
+def timing_enable(flag: bool) -> None:
+    """Per-kernel CUDA-event timing on the library's stream (see the header)."""
+    lib().bem_timing_enable(1 if flag else 0)
+
+
+def timing_get(name: str):
+    """(total milliseconds, launches) recorded for kernel `name`."""
+    ms, n = ctypes.c_double(0.0), ctypes.c_int64(0)
+    code = lib().bem_timing_get(name.encode(), ctypes.byref(ms), ctypes.byref(n))
+    if code != 0:
+        return 0.0, 0
+    return ms.value, n.value
 
 
 def _check(code, allow_warn=True):
@@ -292,6 +311,10 @@ class Mesh:
                                   _dptr(q, self.n), pts.ctypes.data_as(ctypes.c_void_p), m, _dptr(out, m),
                                   _stream_ptr(stream)))
         return out
+
+    def release_plan(self):
+        """Free the per-frequency plan; the next call rebuilds it."""
+        _check(lib().bem_mesh_release_plan(self._h))
 
     def stats(self, freq, c=343.0, rho=1.21) -> dict:
         st = PlanStats()

@@ -24,6 +24,19 @@ using namespace bem;
 static thread_local std::string g_err;
 static std::atomic<uint64_t> g_launches{0};
 
+// optional per-kernel event timing (see bem_timing_enable)
+#include <map>
+#include <mutex>
+static bool g_timing = false;
+static std::mutex g_tmu;
+struct TimingRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+static std::vector<TimingRec> g_pending;
+static std::vector<cudaEvent_t> g_pool;
+static std::map<std::string, std::pair<double, int64_t>> g_tacc;
+
 namespace {
 
 struct Fail {
@@ -48,6 +61,62 @@ void ck_launch(const char *what)
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     ck(cudaGetLastError(), what);
+}
+
+cudaEvent_t pool_event()
+{
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    ck(cudaEventCreate(&e), "cudaEventCreate");
+    return e;
+}
+
+// Records an event pair around the kernel launched in its scope when timing
+// is on and the stream is not being captured.
+struct KTimer {
+    const char *name;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    KTimer(const char *n, cudaStream_t st) : name(n), s(st)
+    {
+        if (!g_timing) return;
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+        std::lock_guard<std::mutex> lk(g_tmu);
+        a = pool_event();
+        cudaEventRecord(a, s);
+    }
+    ~KTimer()
+    {
+        if (!a) return;
+        std::lock_guard<std::mutex> lk(g_tmu);
+        cudaEvent_t b = pool_event();
+        cudaEventRecord(b, s);
+        g_pending.push_back({name, a, b});
+    }
+};
+
+// Accumulates the elapsed times of completed event pairs.
+void resolve_timing()
+{
+    std::lock_guard<std::mutex> lk(g_tmu);
+    std::vector<TimingRec> keep;
+    for (auto &r : g_pending) {
+        if (cudaEventQuery(r.b) != cudaSuccess) { keep.push_back(r); continue; }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            auto &acc = g_tacc[r.name];
+            acc.first += ms;
+            acc.second += 1;
+        }
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_pending.swap(keep);
 }
 
 template <typename T>
@@ -285,7 +354,10 @@ void build_plan_dev(bem_mesh_impl &M, double freq, double c)
         D->Lam.alloc((size_t)D->nc * D->nd);
         const int64_t tot = (int64_t)D->noff * D->nd;
         if (tot > 0) {
-            k_dtable<<<nblocks(tot, 128), 128, 0, s>>>(D->offs.p, D->noff, D->dirs_d.p, D->nd, D->L, P->k, D->D.p);
+            {
+                KTimer kt_("k_dtable", s);
+                k_dtable<<<nblocks(tot, 128), 128, 0, s>>>(D->offs.p, D->noff, D->dirs_d.p, D->nd, D->L, P->k, D->D.p);
+            }
             ck_launch("k_dtable");
         }
         P->lev.push_back(std::move(D));
@@ -390,7 +462,10 @@ void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
             M.tmp.alloc(M.n);
             ck(cudaMemsetAsync(M.tmp.p, 0, M.n * sizeof(float2), M.s), "memset");
             NearArgs a = near_args(M, P, M.cp.p, M.cq.p);
-            k_near_fused<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, M.tmp.p, M.ynear.p, M.err.p, nullptr);
+            {
+                KTimer kt_("k_near_fused", M.s);
+                k_near_fused<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, M.tmp.p, M.ynear.p, M.err.p, nullptr);
+            }
             ck_launch("k_near_fused");
             check_err(M);
             P.val_valid = true;
@@ -401,7 +476,10 @@ void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
     P.val.alloc((size_t)P.nnz);
     reset_err(M);
     NearArgs a = near_args(M, P, M.cp.p, M.cq.p);
-    k_near_store<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, P.val.p, M.err.p);
+    {
+        KTimer kt_("k_near_store", M.s);
+        k_near_store<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, P.val.p, M.err.p);
+    }
     ck_launch("k_near_store");
     check_err(M);
     P.val_key.swap(key);
@@ -430,14 +508,23 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     pa.cp = cp;
     pa.cq = cq;
     pa.k = (float)P.k;
-    k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, skip);
+    {
+        KTimer kt_("k_prep", s);
+        k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, skip);
+    }
     ck_launch("k_prep");
     NearArgs na = near_args(M, P, cp, cq);
     if (use_store && M.prm.near_store && !P.fp.direct) {
-        k_near_spmv<<<nblocks(n, 8), 256, 0, s>>>(na, P.val.p, M.xint.p, M.ynear.p, skip);
+        {
+            KTimer kt_("k_near_spmv", s);
+            k_near_spmv<<<nblocks(n, 8), 256, 0, s>>>(na, P.val.p, M.xint.p, M.ynear.p, skip);
+        }
         ck_launch("k_near_spmv");
     } else {
-        k_near_fused<<<nblocks(n, 8), 256, 0, s>>>(na, M.xint.p, M.ynear.p, M.err.p, skip);
+        {
+            KTimer kt_("k_near_fused", s);
+            k_near_fused<<<nblocks(n, 8), 256, 0, s>>>(na, M.xint.p, M.ynear.p, M.err.p, skip);
+        }
         ck_launch("k_near_fused");
     }
     DisaggArgs da;
@@ -452,13 +539,22 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
         f.k = (float)P.k;
         const int tpb = 256;
         const size_t smem = tpb * (sizeof(float4) + 4 * sizeof(float2));
-        k_aggregate<<<D.nc, tpb, smem, s>>>(f, M.alpha.p, M.beta.p, skip);
+        {
+            KTimer kt_("k_aggregate", s);
+            k_aggregate<<<D.nc, tpb, smem, s>>>(f, M.alpha.p, M.beta.p, skip);
+        }
         ck_launch("k_aggregate");
-        k_transfer<<<D.nc, 128, 0, s>>>(f, skip);
+        {
+            KTimer kt_("k_transfer", s);
+            k_transfer<<<D.nc, 128, 0, s>>>(f, skip);
+        }
         ck_launch("k_transfer");
         da.lev[l] = f;
     }
-    k_disaggregate<<<nblocks(n, 8), 256, 0, s>>>(da, M.ynear.p, y, skip);
+    {
+        KTimer kt_("k_disaggregate", s);
+        k_disaggregate<<<nblocks(n, 8), 256, 0, s>>>(da, M.ynear.p, y, skip);
+    }
     ck_launch("k_disaggregate");
 }
 
@@ -718,6 +814,7 @@ int bem_matvec_host(void *mesh, double freq_hz, const bem_medium *medium, const 
         if (st < 0) return st;
         ck(cudaMemcpyAsync(y_host, M.uvec.p, bytes, cudaMemcpyDeviceToHost, us), "D2H y");
         ck(cudaStreamSynchronize(us), "sync");
+        resolve_timing();
         return st;
     } catch (Fail &f) {
         return f.code;
@@ -748,7 +845,10 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         M.bvec.alloc(n);
         M.uvec.alloc(n);
         if (n_src > 0) {
-            k_rhs<<<nblocks(n, 256), 256, 0, s>>>(M.cd.p, M.nrm.p, n, P.k, sdev.p, n_src, M.bvec.p);
+            {
+                KTimer kt_("k_rhs", s);
+                k_rhs<<<nblocks(n, 256), 256, 0, s>>>(M.cd.p, M.nrm.p, n, P.k, sdev.p, n_src, M.bvec.p);
+            }
             ck_launch("k_rhs");
         } else {
             ck(cudaMemsetAsync(M.bvec.p, 0, n * sizeof(float2), s), "memset");
@@ -757,7 +857,10 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
             reset_err(M);
             matvec_internal(M, M.cp0.p, M.cq0.p, false, M.z.p, nullptr, false, M.tmp2.p, false, nullptr, s);
             check_err(M);
-            k_sub<<<nblocks(n, 256), 256, 0, s>>>(M.bvec.p, M.tmp2.p, n);
+            {
+                KTimer kt_("k_sub", s);
+                k_sub<<<nblocks(n, 256), 256, 0, s>>>(M.bvec.p, M.tmp2.p, n);
+            }
             ck_launch("k_sub");
         }
         // GMRES workspace
@@ -782,53 +885,92 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         ck(cudaMemsetAsync(M.uvec.p, 0, n * sizeof(float2), s), "memset x");
         ck(cudaMemsetAsync(M.H.p, 0, M.H.bytes(), s), "memset H");
         // start: r0 = b
-        k_norm_part<<<nnorm, 256, 0, s>>>(M.bvec.p, n, M.normpart.p);
+        {
+            KTimer kt_("k_norm_part", s);
+            k_norm_part<<<nnorm, 256, 0, s>>>(M.bvec.p, n, M.normpart.p);
+        }
         ck_launch("k_norm_part");
-        k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.bvec.p, n, M.normpart.p, nnorm, M.g_.p, m, 1);
+        {
+            KTimer kt_("k_gm_start", s);
+            k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.bvec.p, n, M.normpart.p, nnorm, M.g_.p, m, 1);
+        }
         ck_launch("k_gm_start");
         // one Arnoldi step, captured once as a graph and replayed
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t gexec = nullptr;
         int* jptr = &M.st.p->j;
         const int *done = &M.st.p->done;
-        uint64_t before = g_launches.load();
-        ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
-        matvec_internal(M, M.cp.p, M.cq.p, true, M.V.p, jptr, false, M.w.p, false, done, s);
-        for (int pass = 0; pass < 2; ++pass) {
-            k_gm_dots<<<dim3(nblk, m + 1), 256, 0, s>>>(M.V.p, M.w.p, n, M.st.p, M.part.p, nblk);
-            ck_launch("k_gm_dots");
-            k_gm_reduce<<<1, 256, 0, s>>>(M.st.p, M.part.p, nblk, M.H.p, M.hcol.p, m, pass);
-            ck_launch("k_gm_reduce");
-            k_gm_update<<<nnorm, 256, 0, s>>>(M.V.p, M.w.p, n, M.st.p, M.hcol.p, pass == 1 ? M.normpart.p : nullptr);
-            ck_launch("k_gm_update");
+        auto arnoldi_step = [&]() {
+            matvec_internal(M, M.cp.p, M.cq.p, true, M.V.p, jptr, false, M.w.p, false, done, s);
+            for (int pass = 0; pass < 2; ++pass) {
+                {
+                    KTimer kt_("k_gm_dots", s);
+                    k_gm_dots<<<dim3(nblk, m + 1), 256, 0, s>>>(M.V.p, M.w.p, n, M.st.p, M.part.p, nblk);
+                }
+                ck_launch("k_gm_dots");
+                {
+                    KTimer kt_("k_gm_reduce", s);
+                    k_gm_reduce<<<1, 256, 0, s>>>(M.st.p, M.part.p, nblk, M.H.p, M.hcol.p, m, pass);
+                }
+                ck_launch("k_gm_reduce");
+                {
+                    KTimer kt_("k_gm_update", s);
+                    k_gm_update<<<nnorm, 256, 0, s>>>(M.V.p, M.w.p, n, M.st.p, M.hcol.p, pass == 1 ? M.normpart.p : nullptr);
+                }
+                ck_launch("k_gm_update");
+            }
+            {
+                KTimer kt_("k_gm_givens", s);
+                k_gm_givens<<<1, 32, 0, s>>>(M.st.p, M.H.p, M.cs.p, M.sn.p, M.g_.p, M.normpart.p, nnorm, m);
+            }
+            ck_launch("k_gm_givens");
+            {
+                KTimer kt_("k_gm_scale", s);
+                k_gm_scale<<<nblocks(n, 256), 256, 0, s>>>(M.V.p, M.w.p, n, M.st.p);
+            }
+            ck_launch("k_gm_scale");
+        };
+        const bool use_graph = !g_timing;
+        uint64_t per_step = 0;
+        if (use_graph) {
+            const uint64_t before = g_launches.load();
+            ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
+            arnoldi_step();
+            ck(cudaStreamEndCapture(s, &graph), "end capture");
+            per_step = g_launches.load() - before;
+            g_launches.fetch_sub(per_step);   // captured, not launched
+            ck(cudaGraphInstantiate(&gexec, graph, 0), "instantiate");
         }
-        k_gm_givens<<<1, 32, 0, s>>>(M.st.p, M.H.p, M.cs.p, M.sn.p, M.g_.p, M.normpart.p, nnorm, m);
-        ck_launch("k_gm_givens");
-        k_gm_scale<<<nblocks(n, 256), 256, 0, s>>>(M.V.p, M.w.p, n, M.st.p);
-        ck_launch("k_gm_scale");
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        ck(ce, "end capture");
-        const uint64_t per_step = g_launches.load() - before;
-        g_launches.fetch_sub(per_step);   // captured, not launched
-        ck(cudaGraphInstantiate(&gexec, graph, 0), "instantiate");
         int restarts = 0, total_iters = 0;
         bool converged = false;
         GmresState h;
-        const int batch = 4;
+        // with event timing on, one step per status read so that no timed
+        // launch is a skipped one
+        const int batch = use_graph ? 4 : 1;
         for (;;) {
             // Arnoldi cycle
             for (int guard = 0; guard < m + batch; guard += batch) {
                 for (int b = 0; b < batch; ++b) {
-                    ck(cudaGraphLaunch(gexec, s), "graph launch");
-                    g_launches.fetch_add(per_step);
+                    if (use_graph) {
+                        ck(cudaGraphLaunch(gexec, s), "graph launch");
+                        g_launches.fetch_add(per_step);
+                    } else {
+                        arnoldi_step();
+                    }
                 }
                 ck(cudaMemcpyAsync(&h, M.st.p, sizeof h, cudaMemcpyDeviceToHost, s), "D2H st");
                 ck(cudaStreamSynchronize(s), "sync");
                 if (h.done) break;
             }
-            k_gm_backsolve<<<1, 32, 0, s>>>(M.st.p, M.H.p, M.g_.p, M.yv.p, m);
+            {
+                KTimer kt_("k_gm_backsolve", s);
+                k_gm_backsolve<<<1, 32, 0, s>>>(M.st.p, M.H.p, M.g_.p, M.yv.p, m);
+            }
             ck_launch("k_gm_backsolve");
-            k_gm_xupdate<<<nblocks(n, 256), 256, 0, s>>>(M.uvec.p, M.V.p, n, M.st.p, M.yv.p);
+            {
+                KTimer kt_("k_gm_xupdate", s);
+                k_gm_xupdate<<<nblocks(n, 256), 256, 0, s>>>(M.uvec.p, M.V.p, n, M.st.p, M.yv.p);
+            }
             ck_launch("k_gm_xupdate");
             total_iters = h.iters;
             if (h.converged || h.iters >= max_iter) { converged = h.converged; break; }
@@ -837,24 +979,34 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
             matvec_internal(M, M.cp.p, M.cq.p, true, M.uvec.p, nullptr, false, M.w.p, false, nullptr, s);
             k_rsub<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.bvec.p, n);   // w = b - A x
             ck_launch("k_rsub");
-            k_norm_part<<<nnorm, 256, 0, s>>>(M.w.p, n, M.normpart.p);
+            {
+                KTimer kt_("k_norm_part", s);
+                k_norm_part<<<nnorm, 256, 0, s>>>(M.w.p, n, M.normpart.p);
+            }
             ck_launch("k_norm_part");
-            k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.w.p, n, M.normpart.p, nnorm, M.g_.p, m, 0);
+            {
+                KTimer kt_("k_gm_start", s);
+                k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.w.p, n, M.normpart.p, nnorm, M.g_.p, m, 0);
+            }
             ck_launch("k_gm_start");
             ck(cudaMemsetAsync(M.H.p, 0, M.H.bytes(), s), "memset H");
             ck(cudaMemcpyAsync(&h, M.st.p, sizeof h, cudaMemcpyDeviceToHost, s), "D2H st");
             ck(cudaStreamSynchronize(s), "sync");
             if (h.done) { converged = true; total_iters = h.iters; break; }
         }
-        cudaGraphExecDestroy(gexec);
-        cudaGraphDestroy(graph);
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
         // p and q in the caller's order
-        k_pq<<<nblocks(n, 256), 256, 0, s>>>(M.uvec.p, M.z.p, M.aq.p, M.type.p, M.perm.p, n, (float2 *)p_dev,
+        {
+            KTimer kt_("k_pq", s);
+            k_pq<<<nblocks(n, 256), 256, 0, s>>>(M.uvec.p, M.z.p, M.aq.p, M.type.p, M.perm.p, n, (float2 *)p_dev,
                                              (float2 *)q_dev);
+        }
         ck_launch("k_pq");
         check_err(M);
         join_streams(s, us);
         ck(cudaStreamSynchronize(us), "sync");
+        resolve_timing();
         int status = converged ? BEM_OK : BEM_W_NOT_CONVERGED;
         if (!converged) {
             char buf[160];
@@ -905,9 +1057,15 @@ int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem
         join_streams(us, M.s);
         cudaStream_t s = M.s;
         const int64_t n = M.n;
-        k_gather<<<nblocks(n, 256), 256, 0, s>>>((const float2 *)p_dev, M.perm.p, n, M.tmp.p);
+        {
+            KTimer kt_("k_gather", s);
+            k_gather<<<nblocks(n, 256), 256, 0, s>>>((const float2 *)p_dev, M.perm.p, n, M.tmp.p);
+        }
         ck_launch("k_gather");
-        k_gather<<<nblocks(n, 256), 256, 0, s>>>((const float2 *)q_dev, M.perm.p, n, M.tmp2.p);
+        {
+            KTimer kt_("k_gather", s);
+            k_gather<<<nblocks(n, 256), 256, 0, s>>>((const float2 *)q_dev, M.perm.p, n, M.tmp2.p);
+        }
         ck_launch("k_gather");
         std::vector<double> hp(pts, pts + 3 * M_pts);
         DevArr<double> dp;
@@ -917,15 +1075,53 @@ int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem
         sdev.upload(sv, s);
         reset_err(M);
         const double k = wavenumber(freq_hz, c);
-        k_field<<<(unsigned)M_pts, 256, 0, s>>>(M.elem(), M.Q.p, dp.p, M_pts, (float)k, M.tmp.p, M.tmp2.p, sdev.p,
+        {
+            KTimer kt_("k_field", s);
+            k_field<<<(unsigned)M_pts, 256, 0, s>>>(M.elem(), M.Q.p, dp.p, M_pts, (float)k, M.tmp.p, M.tmp2.p, sdev.p,
                                               n_src, (float2 *)out_dev, M.err.p);
+        }
         ck_launch("k_field");
         check_err(M);
         join_streams(s, us);
+        resolve_timing();
         return BEM_OK;
     } catch (Fail &f) {
         return f.code;
     }
+}
+
+int bem_mesh_release_plan(void *mesh)
+{
+    if (!mesh) return set_err(BEM_E_ARG, "mesh is NULL");
+    auto &M = *(bem_mesh_impl *)mesh;
+    cudaSetDevice(M.device);
+    if (M.s) cudaStreamSynchronize(M.s);
+    M.plan.reset();
+    return BEM_OK;
+}
+
+int bem_timing_enable(int enable)
+{
+    if (enable) {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        g_tacc.clear();
+    } else {
+        resolve_timing();
+    }
+    g_timing = enable != 0;
+    return BEM_OK;
+}
+
+int bem_timing_get(const char *name, double *total_ms, int64_t *launches)
+{
+    if (!name || !total_ms || !launches) return set_err(BEM_E_ARG, "bad argument");
+    resolve_timing();
+    std::lock_guard<std::mutex> lk(g_tmu);
+    auto it = g_tacc.find(name);
+    if (it == g_tacc.end()) { *total_ms = 0.0; *launches = 0; return set_err(BEM_E_ARG, "kernel never timed"); }
+    *total_ms = it->second.first;
+    *launches = it->second.second;
+    return BEM_OK;
 }
 
 int bem_plan_stats_host(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tris,

@@ -138,3 +138,96 @@ def test_not_converged_warning(bem):
     p, q, info = mesh.solve(1000.0, [bem.plane_wave()], tol=1e-12, max_iter=2)
     assert info["status"] == bem.W_NOT_CONVERGED and not info["converged"]
     assert info["iterations"] == 2
+
+
+def test_fmm_truncation_error_is_measurable(bem):
+    """A deliberately short expansion (L = 3) makes the plane-wave truncation
+    error visible, which shows the far field carries the far pairs; the
+    paper's truncation (factor 1.8, L >= 8) removes it."""
+    nodes, tris = inputs.icosphere(4, 0.1)
+    n = tris.shape[0]
+    freq = 2000.0
+    k = 2 * np.pi * freq / C
+    x = inputs.random_complex(n, 23)
+    A = oracle.assemble(nodes, tris, k, np.ones(n, complex), np.zeros(n, complex))
+    yo = A @ x
+    errs = {}
+    for L_min, tf in ((3, 0.0), (8, 1.8)):
+        mesh = bem.Mesh(nodes, tris, L_min=L_min, trunc_factor=tf)
+        st = mesh.stats(freq, c=C)
+        assert st["far_pairs"] > 0.5 * n * n
+        y = mesh.matvec(freq, torch.tensor(x, dtype=torch.complex64, device="cuda"), c=C, rho=RHO)
+        errs[L_min] = _rel(y.cpu().numpy(), yo)
+        mesh.close()
+    print("truncation", errs)
+    assert errs[3] > 1e-5 and errs[3] > 10 * errs[8], errs
+    assert errs[8] < 2e-5, errs
+
+
+def test_head_like_surface_fmm_matvec(bem):
+    """Ragged, uneven head-like surface (N = 3380, bumps, varying element
+    sizes) with mixed boundary conditions, FMM against the dense oracle."""
+    nodes, tris = inputs.bumpy_ellipsoid(13)
+    n = tris.shape[0]
+    freq = 3000.0
+    k = 2 * np.pi * freq / C
+    bct, region, adm = _mixed_bc(n, 11)
+    cp, cq = _oracle_coeffs(bct, region, adm, k)
+    A = oracle.assemble(nodes, tris, k, cp, cq)
+    x = inputs.random_complex(n, 24)
+    mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region)
+    y = mesh.matvec(freq, torch.tensor(x, dtype=torch.complex64, device="cuda"), admittance=adm, c=C, rho=RHO)
+    assert _rel(y.cpu().numpy(), A @ x) < 2e-5
+
+
+@pytest.fixture(scope="module")
+def big_sphere():
+    W = inputs.workload("sphere20480_4k")
+    return W
+
+
+def test_full_size_matvec_sampled_rows(bem, big_sphere):
+    """Bench workload (N = 20480, 4 kHz) in the bench's configuration:
+    sampled rows of the FMM product against the oracle's rows, each summed
+    exactly over all N columns in FP64."""
+    W = big_sphere
+    nodes, tris, f = W["nodes"], W["tris"], W["freq"]
+    n = tris.shape[0]
+    k = 2 * np.pi * f / C
+    x = inputs.random_complex(n, 25)
+    mesh = bem.Mesh(nodes, tris)
+    st = mesh.stats(f, c=C)
+    assert st["levels"] >= 3 and st["near_nnz"] + st["far_pairs"] == n * n
+    y = mesh.matvec(f, torch.tensor(x, dtype=torch.complex64, device="cuda"), c=C, rho=RHO).cpu().numpy()
+    rows = np.random.default_rng(2).choice(n, size=96, replace=False)
+    rows = np.concatenate([rows, [0, n - 1]])
+    yo = oracle.matvec_rows(nodes, tris, k, np.ones(n, complex), np.zeros(n, complex), x, rows)
+    err = _rel(y[rows], yo)
+    assert err < 2e-5, err
+
+
+def test_full_size_solve_residual_and_series(bem, big_sphere):
+    """Bench workload solve: FP64 residual of the GPU solution on sampled
+    rows of the paper's operator, and the sphere series."""
+    from closed_forms import sphere_plane_wave
+    W = big_sphere
+    nodes, tris, f = W["nodes"], W["tris"], W["freq"]
+    n = tris.shape[0]
+    k = 2 * np.pi * f / C
+    mesh = bem.Mesh(nodes, tris)
+    src = [bem.plane_wave((0, 0, 1))]
+    p, q, info = mesh.solve(f, src, tol=1e-6, c=C, rho=RHO)
+    assert info["converged"], info
+    pv = p.cpu().numpy().astype(np.complex128)
+    rows = np.random.default_rng(3).choice(n, size=64, replace=False)
+    Ap = oracle.matvec_rows(nodes, tris, k, np.ones(n, complex), np.zeros(n, complex), pv, rows)
+    cen, nrm, _ = oracle.geometry(nodes, tris)
+    b = oracle.rhs(cen[rows], nrm[rows], k, [("plane", (0, 0, 1.0), 1.0)])
+    res = float(np.linalg.norm(Ap - b) / np.linalg.norm(b))
+    assert res < 2e-5, res
+    ps = sphere_plane_wave(cen, k, 0.1)
+    e = np.abs(pv - ps) / np.abs(ps)
+    assert e.mean() < 0.01 and e.max() < 0.05
+    fld = mesh.evaluate(f, p, q, W["field_points"], src, c=C, rho=RHO).cpu().numpy()
+    fs = sphere_plane_wave(W["field_points"], k, 0.1)
+    assert np.max(np.abs(fld - fs) / np.abs(fs)) < 0.01
