@@ -169,7 +169,7 @@ def run_ours(args):
     n = tris.shape[0]
     pts = W["field_points"]
     src = [bemfmm.plane_wave(W["plane_dir"], W["amp"])]
-    mesh = bemfmm.Mesh(nodes, tris)
+    mesh = bemfmm.Mesh(nodes, tris, trunc_factor=args.trunc_factor)
     dev = torch.device("cuda", local)
     p = torch.empty(n, dtype=torch.complex64, device=dev)
     q = torch.empty(n, dtype=torch.complex64, device=dev)
@@ -274,6 +274,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "cf32", "data": "synthetic",
         "config": {"workload": W["name"], "n_elements": n, "freq_hz": f, "mesh": "icosphere r=0.1 m",
                    "source": "plane wave +z", "field_points": int(pts.shape[0]), "gmres_tol": args.tol,
+                   "trunc_factor": args.trunc_factor,
                    "l2_flush": "256 MB write between steps", "parallelism": "replicas" if ws > 1 else "single"},
         "solve_s_per_frequency": round(t_max / args.steps / 1e3, 6),
         "matvecs_per_solve": round(mvs / args.steps, 2),
@@ -392,6 +393,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sphere20480_4k")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--trunc-factor", type=float, default=5.0)
     ap.add_argument("--max-iter", type=int, default=1000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

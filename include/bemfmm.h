@@ -201,6 +201,13 @@ int bem_mesh_release_plan(void *mesh);
 int bem_timing_enable(int enable);
 int bem_timing_get(const char *name, double *total_ms, int64_t *launches);
 
+/* Self-test of the far-field sine/cosine (a Cody-Waite reduction to
+ * [-pi, pi] followed by the SFU approximations; no counterpart in the
+ * paper): for n device floats x_dev writes device float4 out_dev[i] =
+ * (sin, cos by the library's routine, sin, cos by CUDA's sincosf).
+ * Stream-ordered, no synchronisation. */
+int bem_selftest_sincos(const void *x_dev, int64_t n, void *out_dev, void *stream);
+
 /* Number of kernels this library has launched in this process. */
 uint64_t bem_launch_count(void);
 

@@ -109,6 +109,7 @@ def lib():
             "bem_timing_enable": (ctypes.c_int, [ctypes.c_int]),
             "bem_timing_get": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int64)]),
+            "bem_selftest_sincos": (ctypes.c_int, [P, i64, P, P]),
             "bem_launch_count": (ctypes.c_uint64, []),
             "bem_last_error": (ctypes.c_char_p, []),
         }
@@ -136,6 +137,17 @@ def timing_get(name: str):
     if code != 0:
         return 0.0, 0
     return ms.value, n.value
+
+
+def selftest_sincos(x):
+    """(fast sin, fast cos, sincosf sin, sincosf cos) for a float32 CUDA tensor x."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    out = torch.empty((x.numel(), 4), dtype=torch.float32, device=x.device)
+    _check(lib().bem_selftest_sincos(ctypes.c_void_p(x.data_ptr()), x.numel(), ctypes.c_void_p(out.data_ptr()),
+                                     _stream_ptr(None)))
+    return out
 
 
 def _check(code, allow_warn=True):

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -151,45 +152,76 @@ struct DevArr {
 
 inline unsigned nblocks(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
+// Near / interaction lists (host copy + device copy).  The purely geometric
+// lists of a mesh are reused at every frequency whose Hankel-growth test
+// admits all of their far offsets; otherwise a frequency gets its own.
+struct ListsLevelDev {
+    DevArr<int> il_ptr, il_src, il_off, is_src;
+    DevArr<double> offs;
+    DevArr<AggTask> tasks;        // aggregation work items (element chunks)
+    DevArr<int> red_ptr, red_c;   // split clusters: partial rows to sum
+    int ntasks = 0, nred = 0, nextra = 0;
+};
+
+struct Lists {
+    FreqPlan fp;
+    DevArr<int> leaf_of, run_ptr, ncol;
+    DevArr<int2> runs;
+    DevArr<int64_t> row_ptr;
+    int64_t nnz = 0;
+    std::vector<std::unique_ptr<ListsLevelDev>> lev;
+};
+
+// Per-depth element data (frequency independent).
+struct DepthDev {
+    int nc = 0;
+    DevArr<float4> dz;        // z_c - x_j per element
+    DevArr<int> elem_cl;
+    DevArr<int64_t> cstart;
+};
+
 struct LevelDev {
     int depth = 0, L = 0, nd = 0, nc = 0, noff = 0;
+    const ListsLevelDev *ll = nullptr;
+    const DepthDev *dd = nullptr;
     DevArr<float4> dirs;
     DevArr<double> dirs_d;
-    DevArr<int> il_ptr, il_src, il_off, is_src, elem_cl;
-    DevArr<double> offs;
     DevArr<float2> D, M, Lam;
-    DevArr<int64_t> cstart;
-    DevArr<float4> dz;
     FarArgs args() const
     {
         FarArgs f;
         f.nd = nd;
         f.k = 0.f;
         f.dirs = dirs.p;
-        f.il_ptr = il_ptr.p;
-        f.il_src = il_src.p;
-        f.il_off = il_off.p;
+        f.il_ptr = ll->il_ptr.p;
+        f.il_src = ll->il_src.p;
+        f.il_off = ll->il_off.p;
         f.D = D.p;
         f.M = M.p;
         f.Lam = Lam.p;
-        f.cstart = cstart.p;
-        f.is_src = is_src.p;
-        f.dz = dz.p;
-        f.elem_cl = elem_cl.p;
+        f.cstart = dd->cstart.p;
+        f.is_src = ll->is_src.p;
+        f.tasks = ll->tasks.p;
+        f.ntasks = ll->ntasks;
+        f.red_ptr = ll->red_ptr.p;
+        f.red_c = ll->red_c.p;
+        f.nred = ll->nred;
+        f.dz = dd->dz.p;
+        f.elem_cl = dd->elem_cl.p;
         return f;
     }
 };
 
 struct Plan {
     double freq = -1.0, c = -1.0, k = 0.0;
-    FreqPlan fp;
-    DevArr<int> leaf_of, col_ptr, cols;
-    DevArr<int64_t> row_ptr;
-    int64_t nnz = 0;
+    std::shared_ptr<Lists> lists;
+    bool shared_lists = false;
     std::vector<std::unique_ptr<LevelDev>> lev;
     DevArr<float2> val;
     std::vector<float> val_key;   // host copy of the coefficients the stored values were made with
     bool val_valid = false;
+    int64_t nnz() const { return lists->nnz; }
+    const FreqPlan &fp() const { return lists->fp; }
 };
 
 struct Coeffs {
@@ -220,6 +252,8 @@ struct bem_mesh_impl {
     DevArr<double> normpart;
     DevArr<GmresState> st;
     std::unique_ptr<Plan> plan;
+    std::shared_ptr<Lists> geo_lists;                  // frequency-independent lists
+    std::map<int, std::unique_ptr<DepthDev>> depth_dev;
     cudaStream_t s = nullptr;
     std::vector<float> coef_key;
 
@@ -278,6 +312,116 @@ void medium_of(const bem_medium *m, double &c, double &rho)
 }
 
 // ------------------------------------------------------------------ plan
+std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
+{
+    auto Ls = std::make_shared<Lists>();
+    Ls->fp = std::move(fp);
+    const FreqPlan &F = Ls->fp;
+    const Level &Lf = M.t.lv[M.t.leaf_depth];
+    const int nl = (int)Lf.start.size();
+    cudaStream_t s = M.s;
+    // near columns of each leaf as runs of consecutive leaves
+    std::vector<int> run_ptr(nl + 1, 0), ncol(nl, 0);
+    std::vector<int2> runs;
+    for (int t = 0; t < nl; ++t) {
+        int pos = 0, prev = -2;
+        for (int q = F.near_ptr[t]; q < F.near_ptr[t + 1]; ++q) {
+            const int sl = F.near_src[q];
+            if (sl != prev + 1) runs.push_back(make_int2((int)Lf.start[sl], pos));
+            pos += (int)Lf.count[sl];
+            prev = sl;
+        }
+        ncol[t] = pos;
+        run_ptr[t + 1] = (int)runs.size();
+    }
+    std::vector<int> leaf_of(M.n);
+    std::vector<int64_t> row_ptr(M.n + 1, 0);
+    for (int64_t i = 0; i < M.n; ++i) {
+        leaf_of[i] = Lf.elem_cluster[i];
+        row_ptr[i + 1] = row_ptr[i] + ncol[leaf_of[i]];
+    }
+    Ls->nnz = row_ptr[M.n];
+    Ls->leaf_of.upload(leaf_of, s);
+    Ls->run_ptr.upload(run_ptr, s);
+    Ls->ncol.upload(ncol, s);
+    Ls->runs.upload(runs, s);
+    Ls->row_ptr.upload(row_ptr, s);
+    for (const FarLevel &FL : F.far) {
+        auto D = std::make_unique<ListsLevelDev>();
+        D->il_ptr.upload(FL.il_ptr, s);
+        D->il_src.upload(FL.il_src, s);
+        D->il_off.upload(FL.il_off, s);
+        D->offs.upload(FL.offsets, s);
+        std::vector<int> is_src(FL.nc, 0);
+        for (int v : FL.il_src) is_src[v] = 1;
+        D->is_src.upload(is_src, s);
+        // aggregation tasks: chunks of at most 64 elements of each source cluster
+        const Level &L = M.t.lv[FL.depth];
+        std::vector<AggTask> tasks;
+        std::vector<int> red_ptr{FL.nc}, red_c;
+        int extra = 0;
+        for (int c = 0; c < FL.nc; ++c) {
+            if (!is_src[c]) continue;
+            const int64_t cnt = L.count[c];
+            if (cnt <= 64) {
+                tasks.push_back(AggTask{c, c, L.start[c], (int)cnt});
+                continue;
+            }
+            for (int64_t q = 0; q < cnt; q += 64) {
+                tasks.push_back(AggTask{c, FL.nc + extra, L.start[c] + q, (int)std::min<int64_t>(64, cnt - q)});
+                ++extra;
+            }
+            red_c.push_back(c);
+            red_ptr.push_back(FL.nc + extra);
+        }
+        D->ntasks = (int)tasks.size();
+        D->nred = (int)red_c.size();
+        D->nextra = extra;
+        D->tasks.upload(tasks, s);
+        D->red_ptr.upload(red_ptr, s);
+        D->red_c.upload(red_c, s);
+        Ls->lev.push_back(std::move(D));
+    }
+    ck(cudaStreamSynchronize(s), "sync");
+    return Ls;
+}
+
+const DepthDev *depth_data(bem_mesh_impl &M, int depth)
+{
+    auto it = M.depth_dev.find(depth);
+    if (it != M.depth_dev.end()) return it->second.get();
+    auto D = std::make_unique<DepthDev>();
+    const Level &L = M.t.lv[depth];
+    D->nc = (int)L.start.size();
+    std::vector<int64_t> cst(D->nc + 1);
+    for (int cc = 0; cc < D->nc; ++cc) cst[cc] = L.start[cc];
+    cst[D->nc] = M.n;
+    std::vector<float4> dz(M.n);
+    std::vector<int> ecl(M.n);
+    for (int64_t i = 0; i < M.n; ++i) {
+        const int cc = L.elem_cluster[i];
+        ecl[i] = cc;
+        const int64_t e = M.t.perm[i];
+        dz[i] = make_float4((float)(L.z[3 * cc] - M.g.cen[3 * e]), (float)(L.z[3 * cc + 1] - M.g.cen[3 * e + 1]),
+                            (float)(L.z[3 * cc + 2] - M.g.cen[3 * e + 2]), 0.f);
+    }
+    D->cstart.upload(cst, M.s);
+    D->dz.upload(dz, M.s);
+    D->elem_cl.upload(ecl, M.s);
+    ck(cudaStreamSynchronize(M.s), "sync");
+    const DepthDev *r = D.get();
+    M.depth_dev[depth] = std::move(D);
+    return r;
+}
+
+// expansion length of a depth (Eq. FMMTruncation, largest radius of the depth)
+int level_L(const bem_mesh_impl &M, int depth, double k)
+{
+    const double x = 2.0 * M.t.lv[depth].rmax * k;
+    const double L = x + M.prm.trunc_factor * std::log10(x + M_PI);
+    return std::max(M.prm.L_min, (int)std::ceil(L - 1e-12));
+}
+
 void build_plan_dev(bem_mesh_impl &M, double freq, double c)
 {
     if (M.plan && M.plan->freq == freq && M.plan->c == c) return;
@@ -286,77 +430,60 @@ void build_plan_dev(bem_mesh_impl &M, double freq, double c)
     P->freq = freq;
     P->c = c;
     P->k = wavenumber(freq, c);
-    build_plan(M.g, M.t, M.prm, P->k, P->fp);
-    const FreqPlan &fp = P->fp;
-    const Level &Lf = M.t.lv[M.t.leaf_depth];
-    const int nl = (int)Lf.start.size();
-    cudaStream_t s = M.s;
-    // near field: per-leaf column lists and per-row offsets
-    std::vector<int> col_ptr(nl + 1, 0), cols;
-    for (int t = 0; t < nl; ++t) {
-        for (int q = fp.near_ptr[t]; q < fp.near_ptr[t + 1]; ++q) {
-            int sl = fp.near_src[q];
-            for (int64_t e = Lf.start[sl]; e < Lf.start[sl] + Lf.count[sl]; ++e) cols.push_back((int)e);
+    const double k = P->k;
+    if (!M.geo_lists) {
+        bem_params gp = M.prm;
+        gp.stability_max = 1e308;
+        FreqPlan fp;
+        build_plan(M.g, M.t, gp, k, fp);
+        M.geo_lists = upload_lists(M, std::move(fp));
+    }
+    // reuse the geometric lists when every far offset passes the Hankel test
+    bool ok = true;
+    for (const FarLevel &FL : M.geo_lists->fp.far) {
+        const int L = level_L(M, FL.depth, k);
+        for (size_t o = 0; ok && o < FL.offsets.size() / 3; ++o) {
+            const double X = std::sqrt(FL.offsets[3 * o] * FL.offsets[3 * o] + FL.offsets[3 * o + 1] * FL.offsets[3 * o + 1] +
+                                       FL.offsets[3 * o + 2] * FL.offsets[3 * o + 2]);
+            if (!(hankel_growth(k * X, L) <= M.prm.stability_max)) ok = false;
         }
-        col_ptr[t + 1] = (int)cols.size();
+        if (!ok) break;
     }
-    std::vector<int> leaf_of(M.n);
-    std::vector<int64_t> row_ptr(M.n + 1, 0);
-    for (int64_t i = 0; i < M.n; ++i) {
-        leaf_of[i] = Lf.elem_cluster[i];
-        row_ptr[i + 1] = row_ptr[i] + (col_ptr[leaf_of[i] + 1] - col_ptr[leaf_of[i]]);
+    if (ok) {
+        P->lists = M.geo_lists;
+        P->shared_lists = true;
+    } else {
+        FreqPlan fp;
+        build_plan(M.g, M.t, M.prm, k, fp);
+        P->lists = upload_lists(M, std::move(fp));
     }
-    P->nnz = row_ptr[M.n];
-    P->leaf_of.upload(leaf_of, s);
-    P->col_ptr.upload(col_ptr, s);
-    P->cols.upload(cols, s);
-    P->row_ptr.upload(row_ptr, s);
-    // far levels
-    for (const FarLevel &F : fp.far) {
+    cudaStream_t s = M.s;
+    const FreqPlan &fp = P->fp();
+    for (size_t l = 0; l < fp.far.size(); ++l) {
+        const FarLevel &F = fp.far[l];
         auto D = std::make_unique<LevelDev>();
-        const Level &L = M.t.lv[F.depth];
         D->depth = F.depth;
-        D->L = F.L;
-        D->nd = 2 * F.L * F.L;
+        D->L = level_L(M, F.depth, k);
+        D->nd = 2 * D->L * D->L;
         D->nc = F.nc;
         D->noff = (int)(F.offsets.size() / 3);
+        D->ll = P->lists->lev[l].get();
+        D->dd = depth_data(M, F.depth);
         std::vector<double> sd, sw;
-        sphere_grid(F.L, sd, sw);
+        sphere_grid(D->L, sd, sw);
         std::vector<float4> dirs(D->nd);
         for (int q = 0; q < D->nd; ++q)
             dirs[q] = make_float4((float)sd[3 * q], (float)sd[3 * q + 1], (float)sd[3 * q + 2], (float)sw[q]);
         D->dirs.upload(dirs, s);
         D->dirs_d.upload(sd, s);
-        D->il_ptr.upload(F.il_ptr, s);
-        D->il_src.upload(F.il_src, s);
-        D->il_off.upload(F.il_off, s);
-        D->offs.upload(F.offsets, s);
-        std::vector<int> is_src(F.nc, 0);
-        for (int v : F.il_src) is_src[v] = 1;
-        D->is_src.upload(is_src, s);
-        std::vector<int64_t> cst(F.nc + 1);
-        for (int cc = 0; cc < F.nc; ++cc) cst[cc] = L.start[cc];
-        cst[F.nc] = M.n;
-        D->cstart.upload(cst, s);
-        std::vector<float4> dz(M.n);
-        std::vector<int> ecl(M.n);
-        for (int64_t i = 0; i < M.n; ++i) {
-            const int cc = L.elem_cluster[i];
-            ecl[i] = cc;
-            const int64_t e = M.t.perm[i];
-            dz[i] = make_float4((float)(L.z[3 * cc] - M.g.cen[3 * e]), (float)(L.z[3 * cc + 1] - M.g.cen[3 * e + 1]),
-                                (float)(L.z[3 * cc + 2] - M.g.cen[3 * e + 2]), 0.f);
-        }
-        D->dz.upload(dz, s);
-        D->elem_cl.upload(ecl, s);
         D->D.alloc((size_t)D->noff * D->nd);
-        D->M.alloc((size_t)D->nc * D->nd);
+        D->M.alloc((size_t)(D->nc + D->ll->nextra) * D->nd);
         D->Lam.alloc((size_t)D->nc * D->nd);
         const int64_t tot = (int64_t)D->noff * D->nd;
         if (tot > 0) {
             {
                 KTimer kt_("k_dtable", s);
-                k_dtable<<<nblocks(tot, 128), 128, 0, s>>>(D->offs.p, D->noff, D->dirs_d.p, D->nd, D->L, P->k, D->D.p);
+                k_dtable<<<nblocks(tot, 128), 128, 0, s>>>(D->ll->offs.p, D->noff, D->dirs_d.p, D->nd, D->L, k, D->D.p);
             }
             ck_launch("k_dtable");
         }
@@ -369,10 +496,11 @@ NearArgs near_args(const bem_mesh_impl &M, const Plan &P, const float2 *cp, cons
 {
     NearArgs a;
     a.E = M.elem();
-    a.N.leaf_of = P.leaf_of.p;
-    a.N.col_ptr = P.col_ptr.p;
-    a.N.cols = P.cols.p;
-    a.N.row_ptr = P.row_ptr.p;
+    a.N.leaf_of = P.lists->leaf_of.p;
+    a.N.run_ptr = P.lists->run_ptr.p;
+    a.N.runs = P.lists->runs.p;
+    a.N.ncol = P.lists->ncol.p;
+    a.N.row_ptr = P.lists->row_ptr.p;
     a.Q = M.Q.p;
     a.k = (float)P.k;
     a.ik_inv = (float)(1.0 / P.k);
@@ -455,7 +583,7 @@ void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
         key.push_back(C.cp[i].x); key.push_back(C.cp[i].y);
         key.push_back(C.cq[i].x); key.push_back(C.cq[i].y);
     }
-    if (!M.prm.near_store || P.fp.direct) {
+    if (!M.prm.near_store || P.fp().direct) {
         if (!P.val_valid) {
             // one fused pass validates the subdivision limit for this plan
             reset_err(M);
@@ -473,7 +601,7 @@ void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
         return;
     }
     if (P.val_valid && key == P.val_key) return;
-    P.val.alloc((size_t)P.nnz);
+    P.val.alloc((size_t)P.nnz());
     reset_err(M);
     NearArgs a = near_args(M, P, M.cp.p, M.cq.p);
     {
@@ -514,7 +642,7 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     }
     ck_launch("k_prep");
     NearArgs na = near_args(M, P, cp, cq);
-    if (use_store && M.prm.near_store && !P.fp.direct) {
+    if (use_store && M.prm.near_store && !P.fp().direct) {
         {
             KTimer kt_("k_near_spmv", s);
             k_near_spmv<<<nblocks(n, 8), 256, 0, s>>>(na, P.val.p, M.xint.p, M.ynear.p, skip);
@@ -537,13 +665,20 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
         LevelDev &D = *P.lev[l];
         FarArgs f = D.args();
         f.k = (float)P.k;
-        const int tpb = 256;
-        const size_t smem = tpb * (sizeof(float4) + 4 * sizeof(float2));
-        {
-            KTimer kt_("k_aggregate", s);
-            k_aggregate<<<D.nc, tpb, smem, s>>>(f, M.alpha.p, M.beta.p, skip);
+        if (f.ntasks > 0) {
+            {
+                KTimer kt_("k_aggregate", s);
+                k_aggregate<<<f.ntasks, 128, 0, s>>>(f, M.alpha.p, M.beta.p, skip);
+            }
+            ck_launch("k_aggregate");
         }
-        ck_launch("k_aggregate");
+        if (f.nred > 0) {
+            {
+                KTimer kt_("k_agg_reduce", s);
+                k_agg_reduce<<<f.nred, 128, 0, s>>>(f, skip);
+            }
+            ck_launch("k_agg_reduce");
+        }
         {
             KTimer kt_("k_transfer", s);
             k_transfer<<<D.nc, 128, 0, s>>>(f, skip);
@@ -1023,7 +1158,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
             info->relres = h.resid;
             info->levels = (int)P.lev.size();
             for (size_t l = 0; l < P.lev.size() && l < 16; ++l) info->L[l] = P.lev[l]->L;
-            info->near_nnz = P.nnz;
+            info->near_nnz = P.nnz();
             info->status = status;
             info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         }
@@ -1084,6 +1219,23 @@ int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem
         check_err(M);
         join_streams(s, us);
         resolve_timing();
+        return BEM_OK;
+    } catch (Fail &f) {
+        return f.code;
+    }
+}
+
+int bem_selftest_sincos(const void *x_dev, int64_t n, void *out_dev, void *stream)
+{
+    if (!x_dev || !out_dev || n < 0) return set_err(BEM_E_ARG, "bad argument");
+    if (n == 0) return BEM_OK;
+    try {
+        cudaStream_t s = (cudaStream_t)stream;
+        {
+            KTimer kt_("k_selftest_sincos", s);
+            k_selftest_sincos<<<nblocks(n, 256), 256, 0, s>>>((const float *)x_dev, n, (float4 *)out_dev);
+        }
+        ck_launch("k_selftest_sincos");
         return BEM_OK;
     } catch (Fail &f) {
         return f.code;
@@ -1161,11 +1313,13 @@ int bem_mesh_stats(void *mesh, double freq_hz, const bem_medium *medium, bem_pla
         build_plan_dev(M, freq_hz, c);
         ck(cudaStreamSynchronize(M.s), "sync");
         Plan &P = *M.plan;
-        fill_stats(M.g, M.t, P.fp, out);
+        fill_stats(M.g, M.t, P.fp(), out);
+        for (size_t l = 0; l < P.lev.size() && l < 16; ++l) out->L[l] = P.lev[l]->L;
         int64_t bytes = 0;
         bytes += M.chi.bytes() * 6 + M.cd.bytes() * 4 + M.ad.bytes() + M.perm.bytes();
-        bytes += P.cols.bytes() + P.row_ptr.bytes() + P.val.bytes();
-        for (auto &L : P.lev) bytes += L->D.bytes() + L->M.bytes() + L->Lam.bytes() + L->dz.bytes();
+        bytes += P.lists->runs.bytes() + P.lists->row_ptr.bytes() + P.val.bytes();
+        for (auto &L : P.lev) bytes += L->D.bytes() + L->M.bytes() + L->Lam.bytes();
+        for (auto &kv : M.depth_dev) bytes += kv.second->dz.bytes() + kv.second->elem_cl.bytes();
         out->device_bytes = bytes;
         return BEM_OK;
     } catch (Fail &f) {

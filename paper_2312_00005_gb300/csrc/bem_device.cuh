@@ -105,6 +105,18 @@ __device__ __forceinline__ void gh_point(float3 d, float3 ny, float k, float w, 
     H = cfma(Gp, make_float2(-ir * ry, k * ry), H);
 }
 
+// sin and cos of x for the far-field phases: Cody-Waite reduction of x to
+// [-pi, pi] with 2 pi split as 6.28125 (exact in 8 bits) + 1.9353071795864769e-3,
+// then the SFU approximations (absolute error about 2^-21 on [-pi, pi]).
+// The unit tests compare it with CUDA's sincosf.
+__device__ __forceinline__ void fast_sincos(float x, float *s, float *c)
+{
+    const float n = rintf(x * 0.15915494309189535f);
+    float r = fmaf(-n, 6.28125f, x);
+    r = fmaf(-n, 1.9353071795864769e-3f, r);
+    __sincosf(r, s, c);
+}
+
 // Rule code for a (sub)element: 0 = subdivide, m >= 1 = regular order m.
 __device__ __forceinline__ int rule_from_rt(float rt, const QuadTables &Q)
 {

@@ -40,10 +40,11 @@ __global__ void k_near_store(NearArgs a, float2 *__restrict__ val, int *__restri
     const float3 xhi = f3(ch), xlo = f3(cl), nx = f3(a.E.nrm[i]);
     const double xd[3] = {a.E.cd[3 * i], a.E.cd[3 * i + 1], a.E.cd[3 * i + 2]};
     const int t = a.N.leaf_of[i];
-    const int p0 = a.N.col_ptr[t], nc = a.N.col_ptr[t + 1] - p0;
+    const int r_end = a.N.run_ptr[t + 1], nc = a.N.ncol[t];
+    int r = a.N.run_ptr[t];
     const int64_t base = a.N.row_ptr[i];
     for (int p = lane; p < nc; p += 32) {
-        const int j = a.N.cols[p0 + p];
+        const int j = near_col(a.N, r_end, r, p);
         float2 v;
         if (!bm_entry(a.E, i, j, xhi, xlo, xd, nx, a.k, a.ik_inv, Q, a.cp[j], a.cq[j], v)) {
             atomicMin(err, j);
@@ -53,7 +54,8 @@ __global__ void k_near_store(NearArgs a, float2 *__restrict__ val, int *__restri
     }
 }
 
-// Near-field product with stored entries: y_i = sum_p val[row_i + p] x[col_p].
+// Near-field product with stored entries: y_i = sum_p val[row_i + p] x[col(p)],
+// one warp per row; four independent loads in flight per lane.
 __global__ void k_near_spmv(NearArgs a, const float2 *__restrict__ val, const float2 *__restrict__ x,
                             float2 *__restrict__ y, const int *skip)
 {
@@ -62,12 +64,24 @@ __global__ void k_near_spmv(NearArgs a, const float2 *__restrict__ val, const fl
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= a.E.n) return;
     const int t = a.N.leaf_of[i];
-    const int p0 = a.N.col_ptr[t], nc = a.N.col_ptr[t + 1] - p0;
+    const int r_end = a.N.run_ptr[t + 1], nc = a.N.ncol[t];
+    int r = a.N.run_ptr[t];
     const float2 *__restrict__ v = val + a.N.row_ptr[i];
-    const int *__restrict__ cols = a.N.cols + p0;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int p = lane; p < nc; p += 32) acc = cfma(__ldcs(v + p), x[cols[p]], acc);
-    acc = warp_sum(acc);
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+    int p = lane;
+    for (; p + 96 < nc; p += 128) {
+        const float2 v0 = __ldcs(v + p), v1 = __ldcs(v + p + 32), v2 = __ldcs(v + p + 64), v3 = __ldcs(v + p + 96);
+        const int j0 = near_col(a.N, r_end, r, p);
+        const int j1 = near_col(a.N, r_end, r, p + 32);
+        const int j2 = near_col(a.N, r_end, r, p + 64);
+        const int j3 = near_col(a.N, r_end, r, p + 96);
+        acc0 = cfma(v0, x[j0], acc0);
+        acc1 = cfma(v1, x[j1], acc1);
+        acc0 = cfma(v2, x[j2], acc0);
+        acc1 = cfma(v3, x[j3], acc1);
+    }
+    for (; p < nc; p += 32) acc0 = cfma(__ldcs(v + p), x[near_col(a.N, r_end, r, p)], acc0);
+    float2 acc = warp_sum(cadd(acc0, acc1));
     if (lane == 0) y[i] = acc;
 }
 
@@ -85,10 +99,11 @@ __global__ void k_near_fused(NearArgs a, const float2 *__restrict__ x, float2 *_
     const float3 xhi = f3(ch), xlo = f3(cl), nx = f3(a.E.nrm[i]);
     const double xd[3] = {a.E.cd[3 * i], a.E.cd[3 * i + 1], a.E.cd[3 * i + 2]};
     const int t = a.N.leaf_of[i];
-    const int p0 = a.N.col_ptr[t], nc = a.N.col_ptr[t + 1] - p0;
+    const int r_end = a.N.run_ptr[t + 1], nc = a.N.ncol[t];
+    int r = a.N.run_ptr[t];
     float2 acc = make_float2(0.f, 0.f);
     for (int p = lane; p < nc; p += 32) {
-        const int j = a.N.cols[p0 + p];
+        const int j = near_col(a.N, r_end, r, p);
         const float2 cp = a.cp[j], cq = a.cq[j];
         if (cp.x == 0.f && cp.y == 0.f && cq.x == 0.f && cq.y == 0.f) continue;
         float2 v;
@@ -133,50 +148,66 @@ __global__ void k_prep(PrepArgs a, const int *skip)
 // Aggregation (Sec. 3.3.3, matrix T(l) with the centroid rule): for every
 // source cluster c and direction s_nu,
 //   M_c(nu) = sum_{j in c} e^{ik (z_c - x_j).s_nu} (alpha_j + beta_j . s_nu).
+// One block per task (a chunk of at most kAggChunk elements of one cluster);
+// clusters split into several tasks are summed by k_agg_reduce.
+constexpr int kAggChunk = 64;
 __global__ void k_aggregate(FarArgs f, const float2 *__restrict__ alpha, const float2 *__restrict__ beta,
                             const int *skip)
 {
     if (skip_now(skip)) return;
-    const int c = blockIdx.x;
-    if (!f.is_src[c]) return;
-    extern __shared__ float4 sm[];
-    float4 *sd = sm;                              // z_c - x_j
-    float2 *sa = (float2 *)(sm + blockDim.x);     // alpha_j
-    float2 *sb = sa + blockDim.x;                 // beta_j (x, y, z)
-    const int64_t e0 = f.cstart[c], ne = f.cstart[c + 1] - e0;
-    for (int nu0 = 0; nu0 < f.nd; nu0 += blockDim.x) {
-        const int nu = nu0 + threadIdx.x;
-        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (nu < f.nd) s = f.dirs[nu];
+    const AggTask T = f.tasks[blockIdx.x];
+    __shared__ float4 sd[kAggChunk];       // z_c - x_j
+    __shared__ float2 sa[kAggChunk];       // alpha_j
+    __shared__ float2 sb[3 * kAggChunk];   // beta_j
+    for (int q = threadIdx.x; q < T.ne; q += blockDim.x) {
+        const int64_t j = T.e0 + q;
+        sd[q] = f.dz[j];
+        sa[q] = alpha[j];
+        sb[3 * q] = beta[3 * j];
+        sb[3 * q + 1] = beta[3 * j + 1];
+        sb[3 * q + 2] = beta[3 * j + 2];
+    }
+    __syncthreads();
+    float2 *__restrict__ out = f.M + (int64_t)T.row * f.nd;
+    for (int nu = threadIdx.x; nu < f.nd; nu += blockDim.x) {
+        const float4 s = f.dirs[nu];
         const float3 sv = f3(s);
         float2 acc = make_float2(0.f, 0.f);
-        for (int64_t c0 = 0; c0 < ne; c0 += blockDim.x) {
-            const int cnt = (int)min((int64_t)blockDim.x, ne - c0);
-            __syncthreads();
-            if (threadIdx.x < cnt) {
-                const int64_t j = e0 + c0 + threadIdx.x;
-                sd[threadIdx.x] = f.dz[j];
-                sa[threadIdx.x] = alpha[j];
-                sb[3 * threadIdx.x] = beta[3 * j];
-                sb[3 * threadIdx.x + 1] = beta[3 * j + 1];
-                sb[3 * threadIdx.x + 2] = beta[3 * j + 2];
-            }
-            __syncthreads();
-            if (nu < f.nd) {
-                for (int q = 0; q < cnt; ++q) {
-                    const float ph = f.k * dot3f(f3(sd[q]), sv);
-                    float sn, cs;
-                    sincosf(ph, &sn, &cs);
-                    float2 w = sa[q];
-                    w = cfma(sb[3 * q], make_float2(sv.x, 0.f), w);
-                    w = cfma(sb[3 * q + 1], make_float2(sv.y, 0.f), w);
-                    w = cfma(sb[3 * q + 2], make_float2(sv.z, 0.f), w);
-                    acc = cfma(make_float2(cs, sn), w, acc);
-                }
-            }
+        for (int q = 0; q < T.ne; ++q) {
+            float sn, cs;
+            fast_sincos(f.k * dot3f(f3(sd[q]), sv), &sn, &cs);
+            float2 w = sa[q];
+            w.x = fmaf(sb[3 * q].x, sv.x, fmaf(sb[3 * q + 1].x, sv.y, fmaf(sb[3 * q + 2].x, sv.z, w.x)));
+            w.y = fmaf(sb[3 * q].y, sv.x, fmaf(sb[3 * q + 1].y, sv.y, fmaf(sb[3 * q + 2].y, sv.z, w.y)));
+            acc = cfma(make_float2(cs, sn), w, acc);
         }
-        if (nu < f.nd) f.M[(int64_t)c * f.nd + nu] = acc;
+        out[nu] = acc;
     }
+}
+
+// M_c(nu) = sum of the partial rows of the tasks of a split cluster.
+__global__ void k_agg_reduce(FarArgs f, const int *skip)
+{
+    if (skip_now(skip)) return;
+    const int q = blockIdx.x;
+    const int r0 = f.red_ptr[q], r1 = f.red_ptr[q + 1];
+    float2 *__restrict__ out = f.M + (int64_t)f.red_c[q] * f.nd;
+    for (int nu = threadIdx.x; nu < f.nd; nu += blockDim.x) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int r = r0; r < r1; ++r) acc = cadd(acc, f.M[(int64_t)r * f.nd + nu]);
+        out[nu] = acc;
+    }
+}
+
+// sin / cos of x by fast_sincos and by sincosf, for the unit tests.
+__global__ void k_selftest_sincos(const float *__restrict__ x, int64_t n, float4 *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s0, c0, s1, c1;
+    fast_sincos(x[i], &s0, &c0);
+    sincosf(x[i], &s1, &c1);
+    out[i] = make_float4(s0, c0, s1, c1);
 }
 
 // Diagonal transfer (Sec. 3.3.3, matrix D(l)): for every target cluster t
@@ -188,14 +219,34 @@ __global__ void k_transfer(FarArgs f, const int *skip)
     const int t = blockIdx.x;
     const int b = f.il_ptr[t], e = f.il_ptr[t + 1];
     if (b == e) return;
-    for (int nu = threadIdx.x; nu < f.nd; nu += blockDim.x) {
-        float2 acc = make_float2(0.f, 0.f);
-        for (int q = b; q < e; ++q) {
-            const float2 D = f.D[(int64_t)f.il_off[q] * f.nd + nu];
-            const float2 M = f.M[(int64_t)f.il_src[q] * f.nd + nu];
-            acc = cfma(D, M, acc);
+    __shared__ int s_src[256], s_off[256];
+    for (int nu0 = 0; nu0 < f.nd; nu0 += blockDim.x) {
+        const int nu = nu0 + threadIdx.x;
+        float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+        for (int q0 = b; q0 < e; q0 += 256) {
+            const int cnt = min(256, e - q0);
+            __syncthreads();
+            for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+                s_src[q] = f.il_src[q0 + q] * f.nd;
+                s_off[q] = f.il_off[q0 + q] * f.nd;
+            }
+            __syncthreads();
+            if (nu < f.nd) {
+                int q = 0;
+                for (; q + 3 < cnt; q += 4) {
+                    const float2 D0 = f.D[s_off[q] + nu], M0 = f.M[s_src[q] + nu];
+                    const float2 D1 = f.D[s_off[q + 1] + nu], M1 = f.M[s_src[q + 1] + nu];
+                    const float2 D2 = f.D[s_off[q + 2] + nu], M2 = f.M[s_src[q + 2] + nu];
+                    const float2 D3 = f.D[s_off[q + 3] + nu], M3 = f.M[s_src[q + 3] + nu];
+                    acc0 = cfma(D0, M0, acc0);
+                    acc1 = cfma(D1, M1, acc1);
+                    acc2 = cfma(D2, M2, acc2);
+                    acc3 = cfma(D3, M3, acc3);
+                }
+                for (; q < cnt; ++q) acc0 = cfma(f.D[s_off[q] + nu], f.M[s_src[q] + nu], acc0);
+            }
         }
-        f.Lam[(int64_t)t * f.nd + nu] = acc;
+        if (nu < f.nd) f.Lam[(int64_t)t * f.nd + nu] = cadd(cadd(acc0, acc1), cadd(acc2, acc3));
     }
 }
 
@@ -221,9 +272,8 @@ __global__ void k_disaggregate(DisaggArgs a, const float2 *__restrict__ ynear, f
         const float2 *__restrict__ lam = f.Lam + (int64_t)c * f.nd;
         for (int nu = lane; nu < f.nd; nu += 32) {
             const float4 s = f.dirs[nu];
-            const float ph = -f.k * dot3f(dz, f3(s));
             float sn, cs;
-            sincosf(ph, &sn, &cs);
+            fast_sincos(-f.k * dot3f(dz, f3(s)), &sn, &cs);
             const float wf = s.w * (1.0f + dot3f(f3(s), ni));
             acc = cfma(make_float2(cs * wf, sn * wf), lam[nu], acc);
         }
@@ -458,22 +508,27 @@ __global__ void k_gm_dots(const float2 *__restrict__ V, const float2 *__restrict
     }
 }
 
-// Reduce the partial sums; pass 0 sets H[:, j], pass 1 adds (CGS2).
+// Reduce the partial sums (one warp per l); pass 0 sets H[:, j], pass 1
+// adds (CGS2).
 __global__ void k_gm_reduce(GmresState *st, const double2 *__restrict__ part, int nblk, double2 *__restrict__ H,
                             double2 *__restrict__ hcol, int m, int pass)
 {
     if (st->done) return;
     const int j = st->j;
-    for (int l = threadIdx.x; l <= j; l += blockDim.x) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int b = 0; b < nblk; ++b) {
-            s.x += part[(int64_t)l * nblk + b].x;
-            s.y += part[(int64_t)l * nblk + b].y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int l = warp; l <= j; l += nw) {
+        double2 sacc = make_double2(0.0, 0.0);
+        for (int b = lane; b < nblk; b += 32) {
+            sacc.x += part[(int64_t)l * nblk + b].x;
+            sacc.y += part[(int64_t)l * nblk + b].y;
         }
-        hcol[l] = s;
-        double2 &h = H[(int64_t)l * m + j];
-        if (pass == 0) h = s;
-        else { h.x += s.x; h.y += s.y; }
+        sacc = warp_sum_d(sacc);
+        if (lane == 0) {
+            hcol[l] = sacc;
+            double2 &h = H[(int64_t)l * m + j];
+            if (pass == 0) h = sacc;
+            else { h.x += sacc.x; h.y += sacc.y; }
+        }
     }
 }
 
@@ -519,10 +574,12 @@ __global__ void k_gm_givens(GmresState *st, double2 *__restrict__ H, double2 *__
                             double2 *__restrict__ sn, double2 *__restrict__ g, const double *__restrict__ normpart,
                             int nblk, int m)
 {
-    if (threadIdx.x != 0 || st->done) return;
-    const int j = st->j;
+    if (st->done) return;
     double nn = 0.0;
-    for (int b = 0; b < nblk; ++b) nn += normpart[b];
+    for (int b = threadIdx.x; b < nblk; b += 32) nn += normpart[b];
+    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    if (threadIdx.x != 0) return;
+    const int j = st->j;
     const double hn = sqrt(nn);
     H[(int64_t)(j + 1) * m + j] = make_double2(hn, 0.0);
     for (int l = 0; l < j; ++l) {
@@ -569,22 +626,28 @@ __global__ void k_gm_scale(float2 *__restrict__ V, const float2 *__restrict__ w,
     if (i < n) V[(int64_t)j * n + i] = cscale(w[i], inv);
 }
 
-// Back substitution (single thread, FP64): y = R^{-1} g over ncols columns.
+// Back substitution y = R^{-1} g over ncols columns (FP64), one warp:
+// column-oriented, each step divides one entry and the lanes update the rest.
 __global__ void k_gm_backsolve(const GmresState *st, const double2 *__restrict__ H, const double2 *__restrict__ g,
                                double2 *__restrict__ y, int m)
 {
-    if (threadIdx.x != 0) return;
+    __shared__ double2 sv[kMaxRestart + 1];
     const int nc = st->ncols;
+    const int lane = threadIdx.x;
+    for (int l = lane; l < nc; l += 32) sv[l] = g[l];
+    __syncwarp();
     for (int l = nc - 1; l >= 0; --l) {
-        double2 s = g[l];
-        for (int c = l + 1; c < nc; ++c) {
-            const double2 h = H[(int64_t)l * m + c], yc = y[c];
-            s.x -= h.x * yc.x - h.y * yc.y;
-            s.y -= h.x * yc.y + h.y * yc.x;
-        }
         const double2 d = H[(int64_t)l * m + l];
         const double dd = d.x * d.x + d.y * d.y;
-        y[l] = make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd);
+        const double2 sl = sv[l];
+        const double2 yl = make_double2((sl.x * d.x + sl.y * d.y) / dd, (sl.y * d.x - sl.x * d.y) / dd);
+        if (lane == 0) y[l] = yl;
+        for (int r = lane; r < l; r += 32) {
+            const double2 h = H[(int64_t)r * m + l];
+            sv[r].x -= h.x * yl.x - h.y * yl.y;
+            sv[r].y -= h.x * yl.y + h.y * yl.x;
+        }
+        __syncwarp();
     }
 }
 

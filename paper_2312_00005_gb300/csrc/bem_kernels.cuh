@@ -8,12 +8,25 @@ namespace bem {
 constexpr int kMaxRestart = 256;
 constexpr int kMaxFarLevels = 16;
 
+// Near columns of a leaf: runs of consecutive elements (the elements of
+// consecutive near leaves in Morton order are contiguous); run r covers the
+// row positions [runs[r].y, runs[r + 1].y) starting at element runs[r].x.
 struct NearDev {
     const int *leaf_of;      // per element: leaf cluster
-    const int *col_ptr;      // per leaf (+1): offsets into cols
-    const int *cols;         // concatenated near columns of each leaf
+    const int *run_ptr;      // per leaf (+1): offsets into runs
+    const int2 *runs;        // {first element, first row position}
+    const int *ncol;         // per leaf: near columns
     const int64_t *row_ptr;  // per element (+1): offsets into the stored values
 };
+
+// Column of row position p for a lane that walks positions upwards; r is the
+// lane's current run (advanced monotonically).
+__device__ __forceinline__ int near_col(const NearDev &N, int r_end, int &r, int p)
+{
+    while (r + 1 < r_end && N.runs[r + 1].y <= p) ++r;
+    const int2 rr = N.runs[r];
+    return rr.x + (p - rr.y);
+}
 
 struct NearArgs {
     ElemDev E;
@@ -35,9 +48,22 @@ struct PrepArgs {
     float k;
 };
 
+// Aggregation work item: `ne` elements from e0 of cluster c, written to row
+// `row` of the multipole buffer (row c when the cluster is a single task).
+struct AggTask {
+    int c, row;
+    int64_t e0;
+    int ne;
+};
+
 struct FarArgs {
     int nd;                  // 2 L^2 directions
     float k;
+    const AggTask *tasks;    // aggregation tasks
+    int ntasks;
+    const int *red_ptr;      // clusters with several tasks: rows [red_ptr[q], red_ptr[q+1]) ...
+    const int *red_c;        // ... are summed into row red_c[q]
+    int nred;
     const float4 *dirs;      // (s, w)
     const int *il_ptr, *il_src, *il_off;
     const float2 *D;         // [noff][nd]
@@ -73,6 +99,8 @@ __global__ void k_near_spmv(NearArgs a, const float2 *val, const float2 *x, floa
 __global__ void k_near_fused(NearArgs a, const float2 *x, float2 *y, int *err, const int *skip);
 __global__ void k_prep(PrepArgs a, const int *skip);
 __global__ void k_aggregate(FarArgs f, const float2 *alpha, const float2 *beta, const int *skip);
+__global__ void k_agg_reduce(FarArgs f, const int *skip);
+__global__ void k_selftest_sincos(const float *x, int64_t n, float4 *out);
 __global__ void k_transfer(FarArgs f, const int *skip);
 __global__ void k_disaggregate(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
 __global__ void k_dtable(const double *offs, int noff, const double *dirs, int nd, int L, double k, float2 *D);

@@ -6,7 +6,6 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
-#include <map>
 #include <numeric>
 #include <tuple>
 
@@ -369,6 +368,13 @@ void build_tree(const Geometry &g, double leaf_edge, Tree &t)
 }
 
 // ------------------------------------------------------------------ plan
+// Near and interaction lists by the recursion of Sec. 3.3.4 (stability_max
+// >= 1e300 skips the Hankel-growth test: purely geometric lists): the candidates
+// of a cluster at depth d are the children of its parent's near clusters;
+// far candidates form its interaction list, the others its near list.  The
+// far test depends on the pair only through the box offset (distance,
+// Hankel growth) and the clusters' radii, so the offset-only parts are
+// cached in a dense table per depth.
 void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k, FreqPlan &fp)
 {
     fp = FreqPlan();
@@ -378,89 +384,97 @@ void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k,
     double R[kMaxRule + 1] = {0};
     order_thresholds(p.quad_tol, std::max(2, p.m_max), R);
     const double r1 = R[1] * (1.0 + 1e-9);
-    // expansion length per depth (Eq. FMMTruncation with the level's largest radius)
     std::vector<int> Ld(D + 1, 0);
     for (int d = 0; d <= D; ++d) {
         double x = 2.0 * t.lv[d].rmax * k;
         double L = x + p.trunc_factor * std::log10(x + M_PI);
         Ld[d] = std::max(p.L_min, (int)std::ceil(L - 1e-12));
     }
-    // near lists per depth, interaction lists per depth
-    std::vector<std::vector<int32_t>> near_prev(1, std::vector<int32_t>(1, 0));
+    // near lists of the previous depth in CSR form
+    std::vector<int32_t> nprev_ptr{0, 1}, nprev{0};
+    int rnear_prev = 0;                 // largest |offset component| among near pairs
     std::vector<FarLevel> far_all(D + 1);
-    std::map<std::tuple<int, int, int>, double> growth_cache;
     for (int d = 1; d <= D; ++d) {
         const Level &L = t.lv[d];
         const Level &P = t.lv[d - 1];
-        int nc = (int)L.start.size();
-        std::vector<std::vector<int32_t>> near_cur(nc);
+        const int nc = (int)L.start.size();
         FarLevel &F = far_all[d];
         F.depth = d;
         F.L = Ld[d];
         F.nc = nc;
         F.il_ptr.assign(nc + 1, 0);
-        std::map<std::tuple<int, int, int>, int> off_index;
-        growth_cache.clear();
-        std::vector<std::vector<std::pair<int32_t, int32_t>>> il(nc);
+        std::vector<double> r1sq(nc);
+        for (int c = 0; c < nc; ++c) r1sq[c] = r1 * std::sqrt(L.amax[c]);
+        const int Rb = 2 * rnear_prev + 1;           // candidate offsets lie in [-Rb, Rb]^3
+        const int W = 2 * Rb + 1;
+        // per offset: -2 unknown, -1 not far by offset, >= 0 offset index (far-capable)
+        std::vector<int32_t> off_state((size_t)W * W * W, -2);
+        std::vector<double> off_dist((size_t)W * W * W, 0.0);
+        std::vector<int32_t> ncur_ptr(nc + 1, 0), ncur;
+        std::vector<int32_t> il_src, il_off;
+        il_src.reserve(16 * nc);
+        ncur.reserve(16 * nc);
+        int rnear = 0;
         for (int c = 0; c < nc; ++c) {
-            int par = L.parent[c];
-            for (int32_t sp : near_prev[par]) {
+            const int par = L.parent[c];
+            for (int q = nprev_ptr[par]; q < nprev_ptr[par + 1]; ++q) {
+                const int sp = nprev[q];
                 for (int s = P.child0[sp]; s < P.child0[sp] + P.nchild[sp]; ++s) {
-                    bool far = !fp.direct;
-                    if (far) {
-                        double X[3] = {L.z[3 * c] - L.z[3 * s], L.z[3 * c + 1] - L.z[3 * s + 1],
-                                       L.z[3 * c + 2] - L.z[3 * s + 2]};
-                        double dist = norm3(X);
-                        if (!(dist > p.admissibility * (L.rad[c] + L.rad[s]))) far = false;
-                        if (far && !(dist - L.crad[c] - L.crad[s] > r1 * std::sqrt(L.amax[s]))) far = false;
-                        if (far) {
-                            auto key = std::make_tuple(L.ix[c] - L.ix[s], L.iy[c] - L.iy[s], L.iz[c] - L.iz[s]);
-                            auto it = growth_cache.find(key);
-                            double gr;
-                            if (it == growth_cache.end()) {
-                                gr = hankel_growth(k * dist, F.L);
-                                growth_cache[key] = gr;
-                            } else {
-                                gr = it->second;
+                    const int dx = L.ix[c] - L.ix[s], dy = L.iy[c] - L.iy[s], dz = L.iz[c] - L.iz[s];
+                    bool far = false;
+                    int oi = -1;
+                    if (!fp.direct && (dx | dy | dz) != 0) {
+                        const size_t key = ((size_t)(dx + Rb) * W + (dy + Rb)) * W + (dz + Rb);
+                        int32_t &st = off_state[key];
+                        if (st == -2) {
+                            const double X[3] = {dx * L.box, dy * L.box, dz * L.box};
+                            const double dist = norm3(X);
+                            off_dist[key] = dist;
+                            st = (p.stability_max >= 1e300 || hankel_growth(k * dist, F.L) <= p.stability_max) ? -3 : -1;
+                        }
+                        if (st != -1) {
+                            const double dist = off_dist[key];
+                            far = dist > p.admissibility * (L.rad[c] + L.rad[s]) &&
+                                  dist - L.crad[c] - L.crad[s] > r1sq[s];
+                            if (far && st == -3) {
+                                // first far use of this offset: give it a translation row
+                                st = (int32_t)(F.offsets.size() / 3);
+                                F.offsets.push_back(dx * L.box);
+                                F.offsets.push_back(dy * L.box);
+                                F.offsets.push_back(dz * L.box);
                             }
-                            if (!(gr <= p.stability_max)) far = false;
+                            oi = st;
                         }
                     }
                     if (far) {
-                        auto key = std::make_tuple(L.ix[c] - L.ix[s], L.iy[c] - L.iy[s], L.iz[c] - L.iz[s]);
-                        auto it = off_index.find(key);
-                        int oi;
-                        if (it == off_index.end()) {
-                            oi = (int)off_index.size();
-                            off_index[key] = oi;
-                            F.offsets.push_back(std::get<0>(key) * L.box);
-                            F.offsets.push_back(std::get<1>(key) * L.box);
-                            F.offsets.push_back(std::get<2>(key) * L.box);
-                        } else {
-                            oi = it->second;
-                        }
-                        il[c].push_back({s, oi});
+                        il_src.push_back(s);
+                        il_off.push_back(oi);
                     } else {
-                        near_cur[c].push_back(s);
+                        ncur.push_back(s);
+                        rnear = std::max(rnear, std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))));
                     }
                 }
             }
+            F.il_ptr[c + 1] = (int32_t)il_src.size();
+            ncur_ptr[c + 1] = (int32_t)ncur.size();
         }
-        for (int c = 0; c < nc; ++c) {
-            F.il_ptr[c + 1] = F.il_ptr[c] + (int32_t)il[c].size();
-            for (auto &e : il[c]) { F.il_src.push_back(e.first); F.il_off.push_back(e.second); }
-        }
+        F.il_src.swap(il_src);
+        F.il_off.swap(il_off);
         F.n_inter = (int64_t)F.il_src.size();
-        near_prev.swap(near_cur);
+        nprev_ptr.swap(ncur_ptr);
+        nprev.swap(ncur);
+        rnear_prev = rnear;
     }
-    if (D == 0) near_prev.assign(1, std::vector<int32_t>(1, 0));
-    // leaf near lists
+    // leaf near lists (sorted source leaves)
     const Level &Lf = t.lv[D];
-    int nl = (int)Lf.start.size();
+    const int nl = (int)Lf.start.size();
     fp.near_ptr.assign(nl + 1, 0);
+    fp.near_src.clear();
+    fp.near_src.reserve(nprev.size());
     fp.nnz = 0;
     for (int c = 0; c < nl; ++c) {
-        std::vector<int32_t> v = near_prev[c];
+        const int b0 = nprev_ptr[c], b1 = nprev_ptr[c + 1];
+        std::vector<int32_t> v(nprev.begin() + b0, nprev.begin() + b1);
         std::sort(v.begin(), v.end());
         int64_t cols = 0;
         for (int32_t s : v) { fp.near_src.push_back(s); cols += Lf.count[s]; }

@@ -1,9 +1,12 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
-the same seeded inputs.  Tolerances:
-  * direct product (every pair by quadrature, FP32):   ||y - y_o|| / ||y_o|| <= 2e-5
-  * FMM product: FP32 part 2e-5 plus the FMM truncation bound stated per case
-  * surface pressure of a solve (FP32 products, GMRES tol 1e-7): <= 1e-4
-  * field at exterior points: <= 1e-4
+the same seeded inputs.  Tolerances (relative l2):
+  * direct product (every pair by quadrature, FP32):        2e-5
+  * FMM product, random vectors:                             2e-5
+  * FMM product, smooth vectors (far sums add coherently): the plane-wave
+    truncation error of Eq. FMMTruncation dominates: <= 1e-3 at the paper's
+    factor 1.8 (its FMM-vs-direct level, Sec. 5.1.3), <= 1e-4 at factor 5
+  * surface pressure of a solve (FP32 products, GMRES tol 1e-7): 1e-4
+  * field at exterior points: 1e-4
 """
 import numpy as np
 import pytest
@@ -206,15 +209,38 @@ def test_full_size_matvec_sampled_rows(bem, big_sphere):
     assert err < 2e-5, err
 
 
-def test_full_size_solve_residual_and_series(bem, big_sphere):
+def test_full_size_smooth_vector_truncation(bem, big_sphere):
+    """Smooth vector (the incident plane wave at the midpoints) at full size:
+    the FMM truncation error is stated per factor (paper's 1.8, and 5)."""
+    W = big_sphere
+    nodes, tris, f = W["nodes"], W["tris"], W["freq"]
+    n = tris.shape[0]
+    k = 2 * np.pi * f / C
+    cen, _, _ = oracle.geometry(nodes, tris)
+    x = np.exp(1j * k * cen[:, 2])
+    rows = np.random.default_rng(5).choice(n, size=96, replace=False)
+    yo = oracle.matvec_rows(nodes, tris, k, np.ones(n, complex), np.zeros(n, complex), x, rows)
+    errs = {}
+    for tf in (1.8, 5.0):
+        mesh = bem.Mesh(nodes, tris, trunc_factor=tf)
+        y = mesh.matvec(f, torch.tensor(x, dtype=torch.complex64, device="cuda"), c=C, rho=RHO).cpu().numpy()
+        errs[tf] = _rel(y[rows], yo)
+        mesh.close()
+    print("smooth-vector FMM error by truncation factor", errs)
+    assert errs[1.8] < 1e-3 and errs[5.0] < 1e-4, errs
+
+
+@pytest.mark.parametrize("tf,tol", [(1.8, 1e-3), (5.0, 1e-4)])
+def test_full_size_solve_residual_and_series(bem, big_sphere, tf, tol):
     """Bench workload solve: FP64 residual of the GPU solution on sampled
-    rows of the paper's operator, and the sphere series."""
+    rows of the paper's dense operator (FMM truncation + FP32), and the
+    sphere series (discretisation error)."""
     from closed_forms import sphere_plane_wave
     W = big_sphere
     nodes, tris, f = W["nodes"], W["tris"], W["freq"]
     n = tris.shape[0]
     k = 2 * np.pi * f / C
-    mesh = bem.Mesh(nodes, tris)
+    mesh = bem.Mesh(nodes, tris, trunc_factor=tf)
     src = [bem.plane_wave((0, 0, 1))]
     p, q, info = mesh.solve(f, src, tol=1e-6, c=C, rho=RHO)
     assert info["converged"], info
@@ -224,10 +250,20 @@ def test_full_size_solve_residual_and_series(bem, big_sphere):
     cen, nrm, _ = oracle.geometry(nodes, tris)
     b = oracle.rhs(cen[rows], nrm[rows], k, [("plane", (0, 0, 1.0), 1.0)])
     res = float(np.linalg.norm(Ap - b) / np.linalg.norm(b))
-    assert res < 2e-5, res
+    print("fp64 residual of the GPU solution, factor", tf, res)
+    assert res < tol, res
     ps = sphere_plane_wave(cen, k, 0.1)
     e = np.abs(pv - ps) / np.abs(ps)
     assert e.mean() < 0.01 and e.max() < 0.05
     fld = mesh.evaluate(f, p, q, W["field_points"], src, c=C, rho=RHO).cpu().numpy()
     fs = sphere_plane_wave(W["field_points"], k, 0.1)
     assert np.max(np.abs(fld - fs) / np.abs(fs)) < 0.01
+
+
+def test_fast_sincos_against_cuda(bem):
+    """The far field's Cody-Waite + SFU sine/cosine against CUDA's sincosf on
+    the phase range of the far field (|x| <= 200 rad)."""
+    x = torch.linspace(-200.0, 200.0, 400001, dtype=torch.float32, device="cuda")
+    out = bem.selftest_sincos(x).cpu().numpy().astype(np.float64)
+    err = np.max(np.abs(out[:, 0:2] - out[:, 2:4]))
+    assert err < 2e-6, err
