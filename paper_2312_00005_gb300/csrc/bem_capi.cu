@@ -120,10 +120,13 @@ void resolve_timing()
     g_pending.swap(keep);
 }
 
+// Device array with grow-only capacity: alloc() reuses the allocation when
+// it is large enough, so buffers handed from one plan to the next are not
+// reallocated.
 template <typename T>
 struct DevArr {
     T *p = nullptr;
-    size_t n = 0;
+    size_t n = 0, cap = 0;
     DevArr() = default;
     DevArr(const DevArr &) = delete;
     DevArr &operator=(const DevArr &) = delete;
@@ -132,15 +135,21 @@ struct DevArr {
     {
         if (p) cudaFree(p);
         p = nullptr;
-        n = 0;
+        n = cap = 0;
     }
     void alloc(size_t count)
     {
-        if (count == n && p) return;
+        if (count <= cap && p) { n = count; return; }
         release();
         if (count == 0) return;
         ck(cudaMalloc((void **)&p, count * sizeof(T)), "cudaMalloc");
-        n = count;
+        n = cap = count;
+    }
+    void swap(DevArr &o)
+    {
+        std::swap(p, o.p);
+        std::swap(n, o.n);
+        std::swap(cap, o.cap);
     }
     void upload(const std::vector<T> &v, cudaStream_t s)
     {
@@ -170,6 +179,10 @@ struct Lists {
     DevArr<int64_t> row_ptr;
     int64_t nnz = 0;
     std::vector<std::unique_ptr<ListsLevelDev>> lev;
+    // all levels together, for the one-launch far-field kernels
+    DevArr<AggTask> all_tasks;
+    DevArr<int2> all_reds, all_targets;
+    int n_tasks = 0, n_reds = 0, n_targets = 0;
 };
 
 // Per-depth element data (frequency independent).
@@ -217,6 +230,8 @@ struct Plan {
     std::shared_ptr<Lists> lists;
     bool shared_lists = false;
     std::vector<std::unique_ptr<LevelDev>> lev;
+    DevArr<LevelsArgs> largs;     // device copy of the per-level arguments
+    LevelsArgs hargs;
     DevArr<float2> val;
     std::vector<float> val_key;   // host copy of the coefficients the stored values were made with
     bool val_valid = false;
@@ -253,6 +268,11 @@ struct bem_mesh_impl {
     DevArr<GmresState> st;
     std::unique_ptr<Plan> plan;
     std::shared_ptr<Lists> geo_lists;                  // frequency-independent lists
+    // buffers kept from the previous plan (reused by the next frequency's plan)
+    DevArr<float2> spare_val;
+    std::vector<std::unique_ptr<DevArr<float2>>> spare_bufs;
+    DevArr<SourceDev> srcbuf;
+    DevArr<double> ptsbuf;
     std::map<int, std::unique_ptr<DepthDev>> depth_dev;
     cudaStream_t s = nullptr;
     std::vector<float> coef_key;
@@ -346,7 +366,10 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
     Ls->ncol.upload(ncol, s);
     Ls->runs.upload(runs, s);
     Ls->row_ptr.upload(row_ptr, s);
+    std::vector<AggTask> all_tasks;
+    std::vector<int2> all_reds, all_targets;
     for (const FarLevel &FL : F.far) {
+        const int lev_index = (int)Ls->lev.size();
         auto D = std::make_unique<ListsLevelDev>();
         D->il_ptr.upload(FL.il_ptr, s);
         D->il_src.upload(FL.il_src, s);
@@ -364,11 +387,12 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
             if (!is_src[c]) continue;
             const int64_t cnt = L.count[c];
             if (cnt <= 64) {
-                tasks.push_back(AggTask{c, c, L.start[c], (int)cnt});
+                tasks.push_back(AggTask{c, c, L.start[c], (int)cnt, lev_index});
                 continue;
             }
             for (int64_t q = 0; q < cnt; q += 64) {
-                tasks.push_back(AggTask{c, FL.nc + extra, L.start[c] + q, (int)std::min<int64_t>(64, cnt - q)});
+                tasks.push_back(AggTask{c, FL.nc + extra, L.start[c] + q, (int)std::min<int64_t>(64, cnt - q),
+                                        lev_index});
                 ++extra;
             }
             red_c.push_back(c);
@@ -380,8 +404,18 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
         D->tasks.upload(tasks, s);
         D->red_ptr.upload(red_ptr, s);
         D->red_c.upload(red_c, s);
+        all_tasks.insert(all_tasks.end(), tasks.begin(), tasks.end());
+        for (int q = 0; q < D->nred; ++q) all_reds.push_back(make_int2(lev_index, q));
+        for (int c = 0; c < FL.nc; ++c)
+            if (FL.il_ptr[c + 1] > FL.il_ptr[c]) all_targets.push_back(make_int2(lev_index, c));
         Ls->lev.push_back(std::move(D));
     }
+    Ls->n_tasks = (int)all_tasks.size();
+    Ls->n_reds = (int)all_reds.size();
+    Ls->n_targets = (int)all_targets.size();
+    Ls->all_tasks.upload(all_tasks, s);
+    Ls->all_reds.upload(all_reds, s);
+    Ls->all_targets.upload(all_targets, s);
     ck(cudaStreamSynchronize(s), "sync");
     return Ls;
 }
@@ -422,10 +456,41 @@ int level_L(const bem_mesh_impl &M, int depth, double k)
     return std::max(M.prm.L_min, (int)std::ceil(L - 1e-12));
 }
 
+// Moves the large buffers of the current plan into the mesh's spares.
+void recycle_plan(bem_mesh_impl &M)
+{
+    if (!M.plan) return;
+    ck(cudaStreamSynchronize(M.s), "sync");
+    M.spare_val.swap(M.plan->val);
+    for (auto &L : M.plan->lev) {
+        for (DevArr<float2> *b : {&L->D, &L->M, &L->Lam}) {
+            auto d = std::make_unique<DevArr<float2>>();
+            d->swap(*b);
+            M.spare_bufs.push_back(std::move(d));
+        }
+    }
+    M.plan.reset();
+}
+
+// Takes the spare buffer with the smallest sufficient capacity (or any).
+void take_spare(bem_mesh_impl &M, DevArr<float2> &dst, size_t count)
+{
+    int best = -1;
+    for (int i = 0; i < (int)M.spare_bufs.size(); ++i) {
+        const size_t c = M.spare_bufs[i]->cap;
+        if (c >= count && (best < 0 || c < M.spare_bufs[best]->cap)) best = i;
+    }
+    if (best >= 0) {
+        dst.swap(*M.spare_bufs[best]);
+        M.spare_bufs.erase(M.spare_bufs.begin() + best);
+    }
+    dst.alloc(count);
+}
+
 void build_plan_dev(bem_mesh_impl &M, double freq, double c)
 {
     if (M.plan && M.plan->freq == freq && M.plan->c == c) return;
-    M.plan.reset();
+    recycle_plan(M);
     auto P = std::make_unique<Plan>();
     P->freq = freq;
     P->c = c;
@@ -476,9 +541,9 @@ void build_plan_dev(bem_mesh_impl &M, double freq, double c)
             dirs[q] = make_float4((float)sd[3 * q], (float)sd[3 * q + 1], (float)sd[3 * q + 2], (float)sw[q]);
         D->dirs.upload(dirs, s);
         D->dirs_d.upload(sd, s);
-        D->D.alloc((size_t)D->noff * D->nd);
-        D->M.alloc((size_t)(D->nc + D->ll->nextra) * D->nd);
-        D->Lam.alloc((size_t)D->nc * D->nd);
+        take_spare(M, D->D, (size_t)D->noff * D->nd);
+        take_spare(M, D->M, (size_t)(D->nc + D->ll->nextra) * D->nd);
+        take_spare(M, D->Lam, (size_t)D->nc * D->nd);
         const int64_t tot = (int64_t)D->noff * D->nd;
         if (tot > 0) {
             {
@@ -489,6 +554,22 @@ void build_plan_dev(bem_mesh_impl &M, double freq, double c)
         }
         P->lev.push_back(std::move(D));
     }
+    LevelsArgs &A = P->hargs;
+    memset(&A, 0, sizeof A);
+    A.nlev = (int)P->lev.size();
+    A.tasks = P->lists->all_tasks.p;
+    A.ntasks = P->lists->n_tasks;
+    A.reds = P->lists->all_reds.p;
+    A.nreds = P->lists->n_reds;
+    A.targets = P->lists->all_targets.p;
+    A.ntargets = P->lists->n_targets;
+    for (size_t l = 0; l < P->lev.size(); ++l) {
+        A.lev[l] = P->lev[l]->args();
+        A.lev[l].k = (float)k;
+    }
+    std::vector<LevelsArgs> hv(1, A);
+    P->largs.upload(hv, s);
+    ck(cudaStreamSynchronize(s), "sync");
     M.plan = std::move(P);
 }
 
@@ -601,6 +682,7 @@ void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
         return;
     }
     if (P.val_valid && key == P.val_key) return;
+    if (!P.val.p) P.val.swap(M.spare_val);
     P.val.alloc((size_t)P.nnz());
     reset_err(M);
     NearArgs a = near_args(M, P, M.cp.p, M.cq.p);
@@ -661,31 +743,29 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     da.perm = perm_out ? M.perm.p : nullptr;
     da.k = (float)P.k;
     da.nlev = (int)P.lev.size();
-    for (size_t l = 0; l < P.lev.size(); ++l) {
-        LevelDev &D = *P.lev[l];
-        FarArgs f = D.args();
-        f.k = (float)P.k;
-        if (f.ntasks > 0) {
-            {
-                KTimer kt_("k_aggregate", s);
-                k_aggregate<<<f.ntasks, 128, 0, s>>>(f, M.alpha.p, M.beta.p, skip);
-            }
-            ck_launch("k_aggregate");
+    const LevelsArgs &A = P.hargs;
+    if (A.ntasks > 0) {
+        {
+            KTimer kt_("k_aggregate", s);
+            k_aggregate<<<A.ntasks, 128, 0, s>>>(P.largs.p, M.alpha.p, M.beta.p, skip);
         }
-        if (f.nred > 0) {
-            {
-                KTimer kt_("k_agg_reduce", s);
-                k_agg_reduce<<<f.nred, 128, 0, s>>>(f, skip);
-            }
-            ck_launch("k_agg_reduce");
+        ck_launch("k_aggregate");
+    }
+    if (A.nreds > 0) {
+        {
+            KTimer kt_("k_agg_reduce", s);
+            k_agg_reduce<<<A.nreds, 128, 0, s>>>(P.largs.p, skip);
         }
+        ck_launch("k_agg_reduce");
+    }
+    if (A.ntargets > 0) {
         {
             KTimer kt_("k_transfer", s);
-            k_transfer<<<D.nc, 128, 0, s>>>(f, skip);
+            k_transfer<<<A.ntargets, 128, 0, s>>>(P.largs.p, skip);
         }
         ck_launch("k_transfer");
-        da.lev[l] = f;
     }
+    for (int l = 0; l < A.nlev; ++l) da.lev[l] = A.lev[l];
     {
         KTimer kt_("k_disaggregate", s);
         k_disaggregate<<<nblocks(n, 8), 256, 0, s>>>(da, M.ynear.p, y, skip);
@@ -975,7 +1055,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         const int m = M.prm.restart;
         // right-hand side: incident field minus the known boundary data
         std::vector<SourceDev> sv = sources_of(srcs, n_src);
-        DevArr<SourceDev> sdev;
+        DevArr<SourceDev> &sdev = M.srcbuf;
         sdev.upload(sv, s);
         M.bvec.alloc(n);
         M.uvec.alloc(n);
@@ -1203,10 +1283,10 @@ int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem
         }
         ck_launch("k_gather");
         std::vector<double> hp(pts, pts + 3 * M_pts);
-        DevArr<double> dp;
+        DevArr<double> &dp = M.ptsbuf;
         dp.upload(hp, s);
         std::vector<SourceDev> sv = sources_of(srcs, n_src);
-        DevArr<SourceDev> sdev;
+        DevArr<SourceDev> &sdev = M.srcbuf;
         sdev.upload(sv, s);
         reset_err(M);
         const double k = wavenumber(freq_hz, c);
@@ -1249,6 +1329,8 @@ int bem_mesh_release_plan(void *mesh)
     cudaSetDevice(M.device);
     if (M.s) cudaStreamSynchronize(M.s);
     M.plan.reset();
+    M.spare_val.release();
+    M.spare_bufs.clear();
     return BEM_OK;
 }
 

@@ -151,11 +151,12 @@ __global__ void k_prep(PrepArgs a, const int *skip)
 // One block per task (a chunk of at most kAggChunk elements of one cluster);
 // clusters split into several tasks are summed by k_agg_reduce.
 constexpr int kAggChunk = 64;
-__global__ void k_aggregate(FarArgs f, const float2 *__restrict__ alpha, const float2 *__restrict__ beta,
-                            const int *skip)
+__global__ void k_aggregate(const LevelsArgs *__restrict__ A, const float2 *__restrict__ alpha,
+                            const float2 *__restrict__ beta, const int *skip)
 {
     if (skip_now(skip)) return;
-    const AggTask T = f.tasks[blockIdx.x];
+    const AggTask T = A->tasks[blockIdx.x];
+    const FarArgs &f = A->lev[T.lev];
     __shared__ float4 sd[kAggChunk];       // z_c - x_j
     __shared__ float2 sa[kAggChunk];       // alpha_j
     __shared__ float2 sb[3 * kAggChunk];   // beta_j
@@ -186,10 +187,12 @@ __global__ void k_aggregate(FarArgs f, const float2 *__restrict__ alpha, const f
 }
 
 // M_c(nu) = sum of the partial rows of the tasks of a split cluster.
-__global__ void k_agg_reduce(FarArgs f, const int *skip)
+__global__ void k_agg_reduce(const LevelsArgs *__restrict__ A, const int *skip)
 {
     if (skip_now(skip)) return;
-    const int q = blockIdx.x;
+    const int2 lq = A->reds[blockIdx.x];
+    const FarArgs &f = A->lev[lq.x];
+    const int q = lq.y;
     const int r0 = f.red_ptr[q], r1 = f.red_ptr[q + 1];
     float2 *__restrict__ out = f.M + (int64_t)f.red_c[q] * f.nd;
     for (int nu = threadIdx.x; nu < f.nd; nu += blockDim.x) {
@@ -213,10 +216,12 @@ __global__ void k_selftest_sincos(const float *__restrict__ x, int64_t n, float4
 // Diagonal transfer (Sec. 3.3.3, matrix D(l)): for every target cluster t
 // with an interaction list (Sec. 3.3.4),
 //   Lambda_t(nu) = sum_{s in I(t)} D_L(z_t - z_s, s_nu) M_s(nu).
-__global__ void k_transfer(FarArgs f, const int *skip)
+__global__ void k_transfer(const LevelsArgs *__restrict__ A, const int *skip)
 {
     if (skip_now(skip)) return;
-    const int t = blockIdx.x;
+    const int2 lt = A->targets[blockIdx.x];
+    const FarArgs &f = A->lev[lt.x];
+    const int t = lt.y;
     const int b = f.il_ptr[t], e = f.il_ptr[t + 1];
     if (b == e) return;
     __shared__ int s_src[256], s_off[256];
@@ -575,45 +580,55 @@ __global__ void k_gm_givens(GmresState *st, double2 *__restrict__ H, double2 *__
                             int nblk, int m)
 {
     if (st->done) return;
+    __shared__ double2 sh[kMaxRestart + 1], scs[kMaxRestart], ssn[kMaxRestart];
+    const int j = st->j;
     double nn = 0.0;
     for (int b = threadIdx.x; b < nblk; b += 32) nn += normpart[b];
     for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-    if (threadIdx.x != 0) return;
-    const int j = st->j;
-    const double hn = sqrt(nn);
-    H[(int64_t)(j + 1) * m + j] = make_double2(hn, 0.0);
-    for (int l = 0; l < j; ++l) {
-        const double2 h0 = H[(int64_t)l * m + j], h1 = H[(int64_t)(l + 1) * m + j];
-        const double2 c = cs[l], s = sn[l];
-        // [conj(c) conj(s); -s c] [h0; h1]
-        H[(int64_t)l * m + j] = make_double2(c.x * h0.x + c.y * h0.y + s.x * h1.x + s.y * h1.y,
-                                             c.x * h0.y - c.y * h0.x + s.x * h1.y - s.y * h1.x);
-        H[(int64_t)(l + 1) * m + j] = make_double2(-(s.x * h0.x - s.y * h0.y) + c.x * h1.x - c.y * h1.y,
-                                                   -(s.x * h0.y + s.y * h0.x) + c.x * h1.y + c.y * h1.x);
+    // stage column j of H and the previous rotations (the serial loop below
+    // then runs on shared memory instead of dependent global loads)
+    for (int l = threadIdx.x; l <= j; l += 32) sh[l] = H[(int64_t)l * m + j];
+    for (int l = threadIdx.x; l < j; l += 32) { scs[l] = cs[l]; ssn[l] = sn[l]; }
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        const double hn = sqrt(nn);
+        sh[j + 1] = make_double2(hn, 0.0);
+        for (int l = 0; l < j; ++l) {
+            const double2 h0 = sh[l], h1 = sh[l + 1];
+            const double2 c = scs[l], s = ssn[l];
+            // [conj(c) conj(s); -s c] [h0; h1]
+            sh[l] = make_double2(c.x * h0.x + c.y * h0.y + s.x * h1.x + s.y * h1.y,
+                                 c.x * h0.y - c.y * h0.x + s.x * h1.y - s.y * h1.x);
+            sh[l + 1] = make_double2(-(s.x * h0.x - s.y * h0.y) + c.x * h1.x - c.y * h1.y,
+                                     -(s.x * h0.y + s.y * h0.x) + c.x * h1.y + c.y * h1.x);
+        }
+        const double2 h0 = sh[j];
+        const double den = sqrt(h0.x * h0.x + h0.y * h0.y + hn * hn);
+        double2 c, s;
+        if (den == 0.0) { c = make_double2(1.0, 0.0); s = make_double2(0.0, 0.0); }
+        else { c = make_double2(h0.x / den, h0.y / den); s = make_double2(hn / den, 0.0); }
+        cs[j] = c;
+        sn[j] = s;
+        sh[j] = make_double2(den, 0.0);
+        sh[j + 1] = make_double2(0.0, 0.0);
+        const double2 g0 = g[j];
+        g[j] = make_double2(c.x * g0.x + c.y * g0.y, c.x * g0.y - c.y * g0.x);
+        const double2 g1 = make_double2(-(s.x * g0.x - s.y * g0.y), -(s.x * g0.y + s.y * g0.x));
+        g[j + 1] = g1;
+        const double res = sqrt(g1.x * g1.x + g1.y * g1.y) / st->bnorm;
+        st->resid = res;
+        st->iters += 1;
+        st->hn = hn;
+        st->ncols = j + 1;
+        if (res <= st->tol || hn <= 1e-300 * st->bnorm || j + 1 >= m || st->iters >= st->maxit) {
+            st->done = 1;
+            st->converged = res <= st->tol;
+        } else {
+            st->j = j + 1;
+        }
     }
-    const double2 h0 = H[(int64_t)j * m + j];
-    const double den = sqrt(h0.x * h0.x + h0.y * h0.y + hn * hn);
-    double2 c, s;
-    if (den == 0.0) { c = make_double2(1.0, 0.0); s = make_double2(0.0, 0.0); }
-    else { c = make_double2(h0.x / den, h0.y / den); s = make_double2(hn / den, 0.0); }
-    cs[j] = c;
-    sn[j] = s;
-    H[(int64_t)j * m + j] = make_double2(den, 0.0);
-    H[(int64_t)(j + 1) * m + j] = make_double2(0.0, 0.0);
-    const double2 g0 = g[j];
-    g[j] = make_double2(c.x * g0.x + c.y * g0.y, c.x * g0.y - c.y * g0.x);
-    g[j + 1] = make_double2(-(s.x * g0.x - s.y * g0.y), -(s.x * g0.y + s.y * g0.x));
-    const double res = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y) / st->bnorm;
-    st->resid = res;
-    st->iters += 1;
-    st->hn = hn;
-    st->ncols = j + 1;
-    if (res <= st->tol || hn <= 1e-300 * st->bnorm || j + 1 >= m || st->iters >= st->maxit) {
-        st->done = 1;
-        st->converged = res <= st->tol;
-    } else {
-        st->j = j + 1;
-    }
+    __syncwarp();
+    for (int l = threadIdx.x; l <= j + 1; l += 32) H[(int64_t)l * m + j] = sh[l];
 }
 
 // V_{j} <- w / h_{j,j-1} for the new column index j (after the Givens step).

@@ -54,6 +54,7 @@ struct AggTask {
     int c, row;
     int64_t e0;
     int ne;
+    int lev;                 // index of the level (in LevelsArgs) the task belongs to
 };
 
 struct FarArgs {
@@ -72,6 +73,18 @@ struct FarArgs {
     const int *is_src;       // [nc]
     const float4 *dz;        // per element: z_c - x_j
     const int *elem_cl;      // per element: cluster at this level
+};
+
+// All far levels of a plan, for the kernels that run every level in one launch.
+struct LevelsArgs {
+    int nlev;
+    const AggTask *tasks;    // aggregation tasks of every level
+    int ntasks;
+    const int2 *reds;        // (level, split-cluster index) pairs to sum
+    int nreds;
+    const int2 *targets;     // (level, target cluster) pairs with interaction lists
+    int ntargets;
+    FarArgs lev[kMaxFarLevels];
 };
 
 struct DisaggArgs {
@@ -98,10 +111,10 @@ __global__ void k_near_store(NearArgs a, float2 *val, int *err);
 __global__ void k_near_spmv(NearArgs a, const float2 *val, const float2 *x, float2 *y, const int *skip);
 __global__ void k_near_fused(NearArgs a, const float2 *x, float2 *y, int *err, const int *skip);
 __global__ void k_prep(PrepArgs a, const int *skip);
-__global__ void k_aggregate(FarArgs f, const float2 *alpha, const float2 *beta, const int *skip);
-__global__ void k_agg_reduce(FarArgs f, const int *skip);
+__global__ void k_aggregate(const LevelsArgs *A, const float2 *alpha, const float2 *beta, const int *skip);
+__global__ void k_agg_reduce(const LevelsArgs *A, const int *skip);
 __global__ void k_selftest_sincos(const float *x, int64_t n, float4 *out);
-__global__ void k_transfer(FarArgs f, const int *skip);
+__global__ void k_transfer(const LevelsArgs *A, const int *skip);
 __global__ void k_disaggregate(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
 __global__ void k_dtable(const double *offs, int noff, const double *dirs, int nd, int L, double k, float2 *D);
 __global__ void k_rhs(const double *cd, const float4 *nrm, int64_t n, double k, const SourceDev *src, int nsrc,
