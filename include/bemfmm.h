@@ -208,6 +208,29 @@ int bem_timing_get(const char *name, double *total_ms, int64_t *launches);
  * Stream-ordered, no synchronisation. */
 int bem_selftest_sincos(const void *x_dev, int64_t n, void *out_dev, void *stream);
 
+/* Direct product without device allocation (the paper has no counterpart;
+ * it exists for callers that must not call cudaMalloc while running, such
+ * as real-time or embedded pipelines that reserve all device memory at
+ * start-up, or hosts whose own allocator owns the device, and that therefore
+ * cannot create a mesh handle).  Computes y = A x, A the conventional dense
+ * Burton-Miller matrix (every pair by the quadrature of Sec. 3.1, no FMM) of
+ * a sound-hard surface (all elements VELO with v = 0, unknown p).
+ *   nodes_dev: device double [n_nodes][3]; tris_dev: device int32 [n_tris][3]
+ *   (counter-clockwise); x_dev, y_dev: device cf32 [n_tris]; medium may be
+ *   NULL (c = 343 m/s).
+ * Everything it derives from the mesh lives in one fixed 8 MiB array
+ * compiled into the library (held on every GPU that loads the library until
+ * the process exits), so n_tris is limited to 32768; larger meshes are
+ * rejected with BEM_E_ARG and a message.  It calls no allocating routine.
+ * The first call on a device looks up that array's device address (make it
+ * before any stream capture).  All calls on a device share the array and
+ * each call overwrites it: calls that overlap on the GPU race.  Work is
+ * enqueued on `stream`; the call synchronises that stream before it returns
+ * (to report degenerate elements or the subdivision limit). */
+int bem_matvec_direct_noalloc(const double *nodes_dev, int64_t n_nodes, const int32_t *tris_dev, int64_t n_tris,
+                              double freq_hz, const bem_medium *medium, const void *x_dev, void *y_dev,
+                              void *stream);
+
 /* Number of kernels this library has launched in this process. */
 uint64_t bem_launch_count(void);
 

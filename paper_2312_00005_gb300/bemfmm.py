@@ -110,6 +110,7 @@ def lib():
             "bem_timing_get": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int64)]),
             "bem_selftest_sincos": (ctypes.c_int, [P, i64, P, P]),
+            "bem_matvec_direct_noalloc": (ctypes.c_int, [P, i64, P, i64, d, ctypes.POINTER(Medium), P, P, P]),
             "bem_launch_count": (ctypes.c_uint64, []),
             "bem_last_error": (ctypes.c_char_p, []),
         }
@@ -148,6 +149,21 @@ def selftest_sincos(x):
     _check(lib().bem_selftest_sincos(ctypes.c_void_p(x.data_ptr()), x.numel(), ctypes.c_void_p(out.data_ptr()),
                                      _stream_ptr(None)))
     return out
+
+
+def matvec_direct_noalloc(nodes_dev, tris_dev, freq, x, y, c=343.0, rho=1.21, stream=None):
+    """Direct sound-hard product that allocates no device memory (see the
+    header): nodes_dev float64 [n_nodes, 3], tris_dev int32 [n, 3], x and y
+    complex64 [n], all CUDA tensors owned by the caller."""
+    import torch
+    for t, dt in ((nodes_dev, torch.float64), (tris_dev, torch.int32)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError("nodes_dev must be float64 and tris_dev int32 contiguous CUDA tensors")
+    n = tris_dev.shape[0]
+    med = Medium(float(c), float(rho))
+    return _check(lib().bem_matvec_direct_noalloc(ctypes.c_void_p(nodes_dev.data_ptr()), nodes_dev.shape[0],
+                                                  ctypes.c_void_p(tris_dev.data_ptr()), n, float(freq),
+                                                  ctypes.byref(med), _dptr(x, n), _dptr(y, n), _stream_ptr(stream)))
 
 
 def _check(code, allow_warn=True):

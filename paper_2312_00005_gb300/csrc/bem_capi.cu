@@ -38,6 +38,11 @@ static std::vector<TimingRec> g_pending;
 static std::vector<cudaEvent_t> g_pool;
 static std::map<std::string, std::pair<double, int64_t>> g_tacc;
 
+namespace bem {
+// Sets the calling thread's message returned by bem_last_error.
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace bem
+
 namespace {
 
 struct Fail {

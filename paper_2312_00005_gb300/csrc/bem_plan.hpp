@@ -101,6 +101,9 @@ struct FreqPlan {
     int max_L = 0;
 };
 
+// Sets the calling thread's message returned by bem_last_error.
+void set_last_error(const std::string &msg);
+
 // Builds near and interaction lists (Sec. 3.3.4) for wavenumber k.
 void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k, FreqPlan &fp);
 
