@@ -194,7 +194,9 @@ def run_ours(args):
         info["freq"] = fs
         return info
 
-    def timed(k_steps, host_io=False):
+    phases = {"setup_s": 0.0, "rhs_s": 0.0, "gmres_s": 0.0, "solve_call_s": 0.0, "evaluate_call_s": 0.0}
+
+    def timed(k_steps, host_io=False, record=False):
         tot_ms, mv, last = 0.0, 0, None
         hp = torch.empty(n, dtype=torch.complex64, pin_memory=True)
         hq = torch.empty(n, dtype=torch.complex64, pin_memory=True)
@@ -206,7 +208,14 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
+            th = time.perf_counter()
             info = one_step()
+            if record:
+                phases["setup_s"] += info["setup_seconds"]
+                phases["rhs_s"] += info["rhs_seconds"]
+                phases["gmres_s"] += info["gmres_seconds"]
+                phases["solve_call_s"] += info["seconds"]
+                phases["evaluate_call_s"] += time.perf_counter() - th - info["seconds"]
             if host_io:
                 hp.copy_(p, non_blocking=True)
                 hq.copy_(q, non_blocking=True)
@@ -226,7 +235,7 @@ def run_ours(args):
     clk = Clocks(local)
     clk.start()
     l0 = bemfmm.launch_count()
-    t_ms, mvs, info = timed(args.steps)
+    t_ms, mvs, info = timed(args.steps, record=True)
     launches = bemfmm.launch_count() - l0
     clocks = clk.stop()
     # end-to-end through the public API with host buffers (field points from
@@ -236,8 +245,8 @@ def run_ours(args):
     bemfmm.timing_enable(True)
     k_ms, k_mvs, _ = timed(args.steps)
     kernels = {}
-    for name in ["k_near_spmv", "k_near_store", "k_aggregate", "k_transfer", "k_disaggregate", "k_prep",
-                 "k_gm_dots", "k_gm_update", "k_gm_reduce", "k_gm_givens", "k_gm_scale", "k_dtable", "k_rhs",
+    for name in ["k_near_spmv", "k_near_store", "k_near_store_heavy", "k_near_classify", "k_aggregate", "k_transfer", "k_disaggregate", "k_prep",
+                 "k_gm_dots", "k_gm_update", "k_agg_reduce", "k_dtable", "k_rhs",
                  "k_field", "k_gm_xupdate", "k_gm_backsolve", "k_pq", "k_gm_start", "k_norm_part", "k_gather"]:
         ms, cnt = bemfmm.timing_get(name)
         if cnt:
@@ -288,6 +297,7 @@ def run_ours(args):
         "solve_s_per_frequency": round(t_max / args.steps / 1e3, 6),
         "matvecs_per_solve": round(mvs / args.steps, 2),
         "gmres_iterations": info["iterations"], "relres": info["relres"],
+        "host_phases_ms_per_step": {k: round(1e3 * v / args.steps, 3) for k, v in phases.items()},
         "rel_error": acc,
         "plan": {k: stats[k] for k in ("levels", "L", "n_clusters", "n_interactions", "near_nnz", "far_pairs",
                                        "leaf_edge")},

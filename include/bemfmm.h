@@ -104,6 +104,9 @@ typedef struct bem_solve_info {
     int32_t L[16];            /* expansion length per used level, finest last  */
     int64_t near_nnz;         /* stored near-field entries                     */
     int32_t status;           /* same as the return value                      */
+    double  setup_seconds;    /* plan, coefficients and near-field entries     */
+    double  rhs_seconds;      /* incident field and known boundary data        */
+    double  gmres_seconds;    /* GMRES iterations (graph build included)       */
 } bem_solve_info;
 
 typedef struct bem_plan_stats {

@@ -55,7 +55,8 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [
         ("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32), ("relres", ctypes.c_double),
         ("seconds", ctypes.c_double), ("levels", ctypes.c_int32), ("L", ctypes.c_int32 * 16),
-        ("near_nnz", ctypes.c_int64), ("status", ctypes.c_int32),
+        ("near_nnz", ctypes.c_int64), ("status", ctypes.c_int32), ("setup_seconds", ctypes.c_double),
+        ("rhs_seconds", ctypes.c_double), ("gmres_seconds", ctypes.c_double),
     ]
 
 
@@ -323,7 +324,9 @@ class Mesh:
         _check(code)
         d = {"iterations": info.iterations, "restarts": info.restarts, "relres": info.relres,
              "seconds": info.seconds, "levels": info.levels, "L": list(info.L[:info.levels]),
-             "near_nnz": info.near_nnz, "status": code, "converged": code != W_NOT_CONVERGED}
+             "near_nnz": info.near_nnz, "status": code, "converged": code != W_NOT_CONVERGED,
+             "setup_seconds": info.setup_seconds, "rhs_seconds": info.rhs_seconds,
+             "gmres_seconds": info.gmres_seconds}
         return p, q, d
 
     def evaluate(self, freq, p, q, points, sources=(), c=343.0, rho=1.21, out=None, stream=None):

@@ -179,6 +179,8 @@ struct ListsLevelDev {
 
 struct Lists {
     FreqPlan fp;
+    int max_ncol = 0;
+    DevArr<int64_t> leaf_start;
     DevArr<int> leaf_of, run_ptr, ncol;
     DevArr<int2> runs;
     DevArr<int64_t> row_ptr;
@@ -187,7 +189,11 @@ struct Lists {
     // all levels together, for the one-launch far-field kernels
     DevArr<AggTask> all_tasks;
     DevArr<int2> all_reds, all_targets;
+    DevArr<unsigned int> red_cnt;
     int n_tasks = 0, n_reds = 0, n_targets = 0;
+    // expensive near pairs (row, position), listed on first use
+    DevArr<int2> heavy;
+    int64_t n_heavy = -1;
 };
 
 // Per-depth element data (frequency independent).
@@ -270,9 +276,11 @@ struct bem_mesh_impl {
     DevArr<float2> V, w;
     DevArr<double2> H, cs, sn, g_, hcol, part, yv;
     DevArr<double> normpart;
+    DevArr<unsigned int> cnt;
     DevArr<GmresState> st;
     std::unique_ptr<Plan> plan;
     std::shared_ptr<Lists> geo_lists;                  // frequency-independent lists
+    std::shared_ptr<Lists> last_lists;                 // lists of the last frequency-specific build
     // buffers kept from the previous plan (reused by the next frequency's plan)
     DevArr<float2> spare_val;
     std::vector<std::unique_ptr<DevArr<float2>>> spare_bufs;
@@ -360,11 +368,16 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
         run_ptr[t + 1] = (int)runs.size();
     }
     std::vector<int> leaf_of(M.n);
-    std::vector<int64_t> row_ptr(M.n + 1, 0);
+    std::vector<int64_t> row_ptr(M.n + 1, 0), leaf_start(nl + 1, M.n);
     for (int64_t i = 0; i < M.n; ++i) {
         leaf_of[i] = Lf.elem_cluster[i];
         row_ptr[i + 1] = row_ptr[i] + ncol[leaf_of[i]];
     }
+    for (int t = 0; t < nl; ++t) {
+        leaf_start[t] = Lf.start[t];
+        Ls->max_ncol = std::max(Ls->max_ncol, ncol[t]);
+    }
+    Ls->leaf_start.upload(leaf_start, s);
     Ls->nnz = row_ptr[M.n];
     Ls->leaf_of.upload(leaf_of, s);
     Ls->run_ptr.upload(run_ptr, s);
@@ -392,12 +405,14 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
             if (!is_src[c]) continue;
             const int64_t cnt = L.count[c];
             if (cnt <= 64) {
-                tasks.push_back(AggTask{c, c, L.start[c], (int)cnt, lev_index});
+                tasks.push_back(AggTask{c, c, L.start[c], (int)cnt, lev_index, -1, -1});
                 continue;
             }
+            const int red = (int)red_c.size();
+            const int gred = (int)all_reds.size() + red;
             for (int64_t q = 0; q < cnt; q += 64) {
                 tasks.push_back(AggTask{c, FL.nc + extra, L.start[c] + q, (int)std::min<int64_t>(64, cnt - q),
-                                        lev_index});
+                                        lev_index, red, gred});
                 ++extra;
             }
             red_c.push_back(c);
@@ -421,6 +436,8 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
     Ls->all_tasks.upload(all_tasks, s);
     Ls->all_reds.upload(all_reds, s);
     Ls->all_targets.upload(all_targets, s);
+    Ls->red_cnt.alloc(std::max(1, Ls->n_reds));
+    ck(cudaMemsetAsync(Ls->red_cnt.p, 0, std::max(1, Ls->n_reds) * sizeof(unsigned int), s), "memset");
     ck(cudaStreamSynchronize(s), "sync");
     return Ls;
 }
@@ -519,13 +536,33 @@ void build_plan_dev(bem_mesh_impl &M, double freq, double c)
         }
         if (!ok) break;
     }
+    // else reuse the last frequency's lists when every stability verdict its
+    // build evaluated (and the expansion length per depth) is unchanged: the
+    // recursion then makes the same decisions
+    bool reuse_last = false;
+    if (!ok && M.last_lists) {
+        const FreqPlan &lf = M.last_lists->fp;
+        reuse_last = true;
+        for (size_t d = 0; reuse_last && d < lf.Ld.size(); ++d)
+            if (level_L(M, (int)d, k) != lf.Ld[d]) reuse_last = false;
+        for (size_t q = 0; reuse_last && q < lf.verdicts.size(); ++q) {
+            const Verdict &v = lf.verdicts[q];
+            const double b = M.t.lv[v.depth].box;
+            const double X = b * std::sqrt((double)v.dx * v.dx + (double)v.dy * v.dy + (double)v.dz * v.dz);
+            if ((hankel_growth(k * X, v.L) <= M.prm.stability_max) != v.stable) reuse_last = false;
+        }
+    }
     if (ok) {
         P->lists = M.geo_lists;
+        P->shared_lists = true;
+    } else if (reuse_last) {
+        P->lists = M.last_lists;
         P->shared_lists = true;
     } else {
         FreqPlan fp;
         build_plan(M.g, M.t, M.prm, k, fp);
         P->lists = upload_lists(M, std::move(fp));
+        M.last_lists = P->lists;
     }
     cudaStream_t s = M.s;
     const FreqPlan &fp = P->fp();
@@ -568,6 +605,7 @@ void build_plan_dev(bem_mesh_impl &M, double freq, double c)
     A.nreds = P->lists->n_reds;
     A.targets = P->lists->all_targets.p;
     A.ntargets = P->lists->n_targets;
+    A.red_cnt = P->lists->red_cnt.p;
     for (size_t l = 0; l < P->lev.size(); ++l) {
         A.lev[l] = P->lev[l]->args();
         A.lev[l].k = (float)k;
@@ -587,6 +625,7 @@ NearArgs near_args(const bem_mesh_impl &M, const Plan &P, const float2 *cp, cons
     a.N.runs = P.lists->runs.p;
     a.N.ncol = P.lists->ncol.p;
     a.N.row_ptr = P.lists->row_ptr.p;
+    a.N.leaf_start = P.lists->leaf_start.p;
     a.Q = M.Q.p;
     a.k = (float)P.k;
     a.ik_inv = (float)(1.0 / P.k);
@@ -691,11 +730,43 @@ void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
     P.val.alloc((size_t)P.nnz());
     reset_err(M);
     NearArgs a = near_args(M, P, M.cp.p, M.cq.p);
+    Lists &Ls = *P.lists;
+    if (Ls.n_heavy < 0) {
+        // count, then list, the expensive pairs of these lists (geometry only)
+        DevArr<unsigned long long> cnt;
+        cnt.alloc(1);
+        ck(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), M.s), "memset");
+        {
+            KTimer kt_("k_near_classify", M.s);
+            k_near_classify<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, nullptr, cnt.p, 0ull);
+        }
+        ck_launch("k_near_classify");
+        unsigned long long h = 0;
+        ck(cudaMemcpyAsync(&h, cnt.p, sizeof h, cudaMemcpyDeviceToHost, M.s), "D2H");
+        ck(cudaStreamSynchronize(M.s), "sync");
+        Ls.heavy.alloc(std::max<unsigned long long>(h, 1));
+        ck(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), M.s), "memset");
+        {
+            KTimer kt_("k_near_classify", M.s);
+            k_near_classify<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, Ls.heavy.p, cnt.p, h);
+        }
+        ck_launch("k_near_classify");
+        ck(cudaStreamSynchronize(M.s), "sync");
+        Ls.n_heavy = (int64_t)h;
+    }
     {
         KTimer kt_("k_near_store", M.s);
-        k_near_store<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, P.val.p, M.err.p);
+        k_near_store_light<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, P.val.p, M.err.p);
     }
     ck_launch("k_near_store");
+    if (Ls.n_heavy > 0) {
+        {
+            KTimer kt_("k_near_store_heavy", M.s);
+            k_near_store_heavy<<<nblocks(Ls.n_heavy, 128), 128, 0, M.s>>>(a, Ls.heavy.p, Ls.n_heavy, P.val.p,
+                                                                          M.err.p);
+        }
+        ck_launch("k_near_store_heavy");
+    }
     check_err(M);
     P.val_key.swap(key);
     P.val_valid = true;
@@ -705,7 +776,8 @@ void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
 // perm_in, else internal (optionally x + (*jidx) n).  y: caller order when
 // perm_out.  use_store: use the stored near-field values.
 void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool use_store, const float2 *x,
-                     const int *jidx, bool perm_in, float2 *y, bool perm_out, const int *skip, cudaStream_t s)
+                     const int *jidx, bool perm_in, float2 *y, bool perm_out, const int *skip, cudaStream_t s,
+                     const float2 *gm_w = nullptr, float2 *gm_v = nullptr, const GmresState *gm_st = nullptr)
 {
     Plan &P = *M.plan;
     const int64_t n = M.n;
@@ -723,6 +795,9 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     pa.cp = cp;
     pa.cq = cq;
     pa.k = (float)P.k;
+    pa.wsrc = gm_w;
+    pa.vdst = gm_v;
+    pa.st = gm_st;
     {
         KTimer kt_("k_prep", s);
         k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, skip);
@@ -730,11 +805,21 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     ck_launch("k_prep");
     NearArgs na = near_args(M, P, cp, cq);
     if (use_store && M.prm.near_store && !P.fp().direct) {
-        {
-            KTimer kt_("k_near_spmv", s);
-            k_near_spmv<<<nblocks(n, 8), 256, 0, s>>>(na, P.val.p, M.xint.p, M.ynear.p, skip);
+        const size_t xs_bytes = (size_t)P.lists->max_ncol * sizeof(float2);
+        const int nleaf = (int)(P.lists->leaf_start.n - 1);
+        if (xs_bytes <= 160 * 1024) {
+            {
+                KTimer kt_("k_near_spmv", s);
+                k_near_spmv_leaf<<<nleaf, 128, xs_bytes, s>>>(na, P.val.p, M.xint.p, M.ynear.p, skip);
+            }
+            ck_launch("k_near_spmv");
+        } else {
+            {
+                KTimer kt_("k_near_spmv", s);
+                k_near_spmv<<<nblocks(n, 8), 256, 0, s>>>(na, P.val.p, M.xint.p, M.ynear.p, skip);
+            }
+            ck_launch("k_near_spmv");
         }
-        ck_launch("k_near_spmv");
     } else {
         {
             KTimer kt_("k_near_fused", s);
@@ -755,13 +840,6 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
             k_aggregate<<<A.ntasks, 128, 0, s>>>(P.largs.p, M.alpha.p, M.beta.p, skip);
         }
         ck_launch("k_aggregate");
-    }
-    if (A.nreds > 0) {
-        {
-            KTimer kt_("k_agg_reduce", s);
-            k_agg_reduce<<<A.nreds, 128, 0, s>>>(P.largs.p, skip);
-        }
-        ck_launch("k_agg_reduce");
     }
     if (A.ntargets > 0) {
         {
@@ -973,6 +1051,8 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         M->ad.upload(ad, s);
         M->perm.upload(M->t.perm, s);
         M->type.upload(ty, s);
+        ck(cudaFuncSetAttribute(k_near_spmv_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024),
+           "cudaFuncSetAttribute");
         std::vector<QuadTables> qt(1, make_tables(p));
         M->Q.upload(qt, s);
         M->err.alloc(1);
@@ -1054,6 +1134,8 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         Coeffs C;
         join_streams(us, M.s);
         prepare(M, freq_hz, medium, admittance, n_regions, C);
+        ck(cudaStreamSynchronize(M.s), "sync");
+        auto t_setup = std::chrono::steady_clock::now();
         Plan &P = *M.plan;
         cudaStream_t s = M.s;
         const int64_t n = M.n;
@@ -1083,6 +1165,8 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
             }
             ck_launch("k_sub");
         }
+        ck(cudaStreamSynchronize(s), "sync");
+        auto t_rhs = std::chrono::steady_clock::now();
         // GMRES workspace
         M.V.alloc((size_t)(m + 1) * n);
         M.w.alloc(n);
@@ -1120,35 +1204,41 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         cudaGraphExec_t gexec = nullptr;
         int* jptr = &M.st.p->j;
         const int *done = &M.st.p->done;
+        M.cnt.alloc(m + 2);
+        ck(cudaMemsetAsync(M.cnt.p, 0, (m + 2) * sizeof(unsigned int), s), "memset cnt");
+        GmresArgs ga;
+        ga.V = M.V.p;
+        ga.w = M.w.p;
+        ga.n = n;
+        ga.st = M.st.p;
+        ga.part = M.part.p;
+        ga.nblk = nblk;
+        ga.H = M.H.p;
+        ga.hcol = M.hcol.p;
+        ga.cs = M.cs.p;
+        ga.sn = M.sn.p;
+        ga.g = M.g_.p;
+        ga.normpart = M.normpart.p;
+        ga.nnorm = nnorm;
+        ga.cnt = M.cnt.p;
+        ga.m = m;
+        // one Arnoldi step: product (the gather forms V_j = w / h_{j,j-1}),
+        // two classical Gram-Schmidt passes, Givens step
         auto arnoldi_step = [&]() {
-            matvec_internal(M, M.cp.p, M.cq.p, true, M.V.p, jptr, false, M.w.p, false, done, s);
+            matvec_internal(M, M.cp.p, M.cq.p, true, M.V.p, jptr, false, M.w.p, false, done, s, M.w.p, M.V.p,
+                            M.st.p);
             for (int pass = 0; pass < 2; ++pass) {
                 {
                     KTimer kt_("k_gm_dots", s);
-                    k_gm_dots<<<dim3(nblk, m + 1), 256, 0, s>>>(M.V.p, M.w.p, n, M.st.p, M.part.p, nblk);
+                    k_gm_dots<<<dim3(nblk, m + 1), 256, 0, s>>>(ga, pass);
                 }
                 ck_launch("k_gm_dots");
                 {
-                    KTimer kt_("k_gm_reduce", s);
-                    k_gm_reduce<<<1, 256, 0, s>>>(M.st.p, M.part.p, nblk, M.H.p, M.hcol.p, m, pass);
-                }
-                ck_launch("k_gm_reduce");
-                {
                     KTimer kt_("k_gm_update", s);
-                    k_gm_update<<<nnorm, 256, 0, s>>>(M.V.p, M.w.p, n, M.st.p, M.hcol.p, pass == 1 ? M.normpart.p : nullptr);
+                    k_gm_update<<<nnorm, 256, 0, s>>>(ga, pass);
                 }
                 ck_launch("k_gm_update");
             }
-            {
-                KTimer kt_("k_gm_givens", s);
-                k_gm_givens<<<1, 32, 0, s>>>(M.st.p, M.H.p, M.cs.p, M.sn.p, M.g_.p, M.normpart.p, nnorm, m);
-            }
-            ck_launch("k_gm_givens");
-            {
-                KTimer kt_("k_gm_scale", s);
-                k_gm_scale<<<nblocks(n, 256), 256, 0, s>>>(M.V.p, M.w.p, n, M.st.p);
-            }
-            ck_launch("k_gm_scale");
         };
         const bool use_graph = !g_timing;
         uint64_t per_step = 0;
@@ -1216,6 +1306,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         }
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
+        auto t_gmres = std::chrono::steady_clock::now();
         // p and q in the caller's order
         {
             KTimer kt_("k_pq", s);
@@ -1246,6 +1337,9 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
             info->near_nnz = P.nnz();
             info->status = status;
             info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            info->setup_seconds = std::chrono::duration<double>(t_setup - t0).count();
+            info->rhs_seconds = std::chrono::duration<double>(t_rhs - t_setup).count();
+            info->gmres_seconds = std::chrono::duration<double>(t_gmres - t_rhs).count();
         }
         return status;
     } catch (Fail &f) {
@@ -1334,6 +1428,7 @@ int bem_mesh_release_plan(void *mesh)
     cudaSetDevice(M.device);
     if (M.s) cudaStreamSynchronize(M.s);
     M.plan.reset();
+    M.last_lists.reset();
     M.spare_val.release();
     M.spare_bufs.clear();
     return BEM_OK;

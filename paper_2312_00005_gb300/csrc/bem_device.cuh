@@ -141,6 +141,20 @@ __device__ __forceinline__ bool rt_ambiguous(float rt, const QuadTables &Q)
     return false;
 }
 
+// Expensive pair: the self term, or an element whose r~ (whole element) is
+// below R_3, i.e. that needs subdivision or a rule of order >= 4.  The cheap
+// pairs take 1 to 9 quadrature points.
+__device__ __forceinline__ bool heavy_pair(const ElemDev &E, int64_t i, int64_t j, float3 xhi, float3 xlo,
+                                           const QuadTables &Q)
+{
+    if (i == j) return true;
+    if (Q.m_max <= 3) return false;
+    const float4 ch = E.chi[j], cl = E.clo[j];
+    const float3 D0 = add3(sub3f(f3(ch), xhi), sub3f(f3(cl), xlo));
+    const float rt0 = sqrtf(dot3f(D0, D0) / ch.w);
+    return !(rt0 > Q.R[3] * (1.0f + 1e-5f));
+}
+
 // Sub-triangle in the reference coordinates (xi, eta) of its element.
 struct SubTri {
     float x0, y0, x1, y1, x2, y2;
@@ -162,6 +176,17 @@ __device__ bool integrate_regular(const ElemDev &E, int64_t j, float3 xhi, float
     const float3 va = f3(E.va[j]), e1 = f3(E.e1[j]), e2 = f3(E.e2[j]), ny = f3(E.nrm[j]);
     const float3 base = add3(D0, va);                                   // a - x
     const float area = ch.w;
+    // Fast path: r~ of the whole element clearly above R_1 (order m = 1, no
+    // subdivision).  The 1 x 1 conical rule is the centroid rule (node
+    // (1/3, 1/3), weight 1/2), so the integral is A_j K(x, x_j).
+    if (Q.m_max > 1) {
+        const float rt0 = sqrtf(dot3f(D0, D0) / area);
+        if (rt0 > Q.R[1] * (1.0f + 1e-5f)) {
+            if (kField) gh_point(D0, ny, k, area, A0, A1);
+            else bm_point(D0, nx, ny, k, ik_inv, area, A0, A1);
+            return true;
+        }
+    }
     SubTri stack[3 * 15 + 4];
     int top = 0;
     stack[top++] = SubTri{0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0};

@@ -54,6 +54,77 @@ __global__ void k_near_store(NearArgs a, float2 *__restrict__ val, int *__restri
     }
 }
 
+// Lists the expensive near pairs (row, position) once per set of lists;
+// with heavy == nullptr only counts them.
+__global__ void k_near_classify(NearArgs a, int2 *__restrict__ heavy, unsigned long long *count,
+                                unsigned long long cap)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= a.E.n) return;
+    const QuadTables &Q = *a.Q;
+    const float3 xhi = f3(a.E.chi[i]), xlo = f3(a.E.clo[i]);
+    const int t = a.N.leaf_of[i];
+    const int r_end = a.N.run_ptr[t + 1], nc = a.N.ncol[t];
+    int r = a.N.run_ptr[t];
+    for (int p = lane; p < nc; p += 32) {
+        const int j = near_col(a.N, r_end, r, p);
+        if (!heavy_pair(a.E, i, j, xhi, xlo, Q)) continue;
+        const unsigned long long q = atomicAdd(count, 1ull);
+        if (heavy && q < cap) heavy[q] = make_int2((int)i, p);
+    }
+}
+
+// Stored near field, cheap pairs: as k_near_store but leaving the expensive
+// pairs to k_near_store_heavy (so no warp waits on a lane with 100+ points).
+__global__ void k_near_store_light(NearArgs a, float2 *__restrict__ val, int *__restrict__ err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= a.E.n) return;
+    const QuadTables &Q = *a.Q;
+    const float4 ch = a.E.chi[i], cl = a.E.clo[i];
+    const float3 xhi = f3(ch), xlo = f3(cl), nx = f3(a.E.nrm[i]);
+    const double xd[3] = {a.E.cd[3 * i], a.E.cd[3 * i + 1], a.E.cd[3 * i + 2]};
+    const int t = a.N.leaf_of[i];
+    const int r_end = a.N.run_ptr[t + 1], nc = a.N.ncol[t];
+    int r = a.N.run_ptr[t];
+    const int64_t base = a.N.row_ptr[i];
+    for (int p = lane; p < nc; p += 32) {
+        const int j = near_col(a.N, r_end, r, p);
+        if (heavy_pair(a.E, i, j, xhi, xlo, Q)) continue;
+        float2 v;
+        if (!bm_entry(a.E, i, j, xhi, xlo, xd, nx, a.k, a.ik_inv, Q, a.cp[j], a.cq[j], v)) {
+            atomicMin(err, j);
+            v = make_float2(0.f, 0.f);
+        }
+        val[base + p] = v;
+    }
+}
+
+// Stored near field, expensive pairs: one thread per listed pair.
+__global__ void k_near_store_heavy(NearArgs a, const int2 *__restrict__ heavy, int64_t nheavy,
+                                   float2 *__restrict__ val, int *__restrict__ err)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nheavy) return;
+    const int2 ip = heavy[q];
+    const int64_t i = ip.x;
+    const QuadTables &Q = *a.Q;
+    const float4 ch = a.E.chi[i], cl = a.E.clo[i];
+    const float3 xhi = f3(ch), xlo = f3(cl), nx = f3(a.E.nrm[i]);
+    const double xd[3] = {a.E.cd[3 * i], a.E.cd[3 * i + 1], a.E.cd[3 * i + 2]};
+    const int t = a.N.leaf_of[i];
+    int r = a.N.run_ptr[t];
+    const int j = near_col(a.N, a.N.run_ptr[t + 1], r, ip.y);
+    float2 v;
+    if (!bm_entry(a.E, i, j, xhi, xlo, xd, nx, a.k, a.ik_inv, Q, a.cp[j], a.cq[j], v)) {
+        atomicMin(err, j);
+        v = make_float2(0.f, 0.f);
+    }
+    val[a.N.row_ptr[i] + ip.y] = v;
+}
+
 // Near-field product with stored entries: y_i = sum_p val[row_i + p] x[col(p)],
 // one warp per row; four independent loads in flight per lane.
 __global__ void k_near_spmv(NearArgs a, const float2 *__restrict__ val, const float2 *__restrict__ x,
@@ -83,6 +154,41 @@ __global__ void k_near_spmv(NearArgs a, const float2 *__restrict__ val, const fl
     for (; p < nc; p += 32) acc0 = cfma(__ldcs(v + p), x[near_col(a.N, r_end, r, p)], acc0);
     float2 acc = warp_sum(cadd(acc0, acc1));
     if (lane == 0) y[i] = acc;
+}
+
+// Near-field product, one block per leaf: the rows of a leaf share its column
+// list, so x at those columns is staged once in shared memory; each warp then
+// streams one row's entries (coalesced, four loads in flight per lane).
+__global__ void k_near_spmv_leaf(NearArgs a, const float2 *__restrict__ val, const float2 *__restrict__ x,
+                                 float2 *__restrict__ y, const int *skip)
+{
+    if (skip_now(skip)) return;
+    extern __shared__ float2 xs[];
+    const int t = blockIdx.x;
+    const int r0 = a.N.run_ptr[t], r1 = a.N.run_ptr[t + 1], nc = a.N.ncol[t];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = r0 + warp; r < r1; r += nw) {
+        const int2 rr = a.N.runs[r];
+        const int end = (r + 1 < r1) ? a.N.runs[r + 1].y : nc;
+        for (int p = rr.y + lane; p < end; p += 32) xs[p] = x[rr.x + (p - rr.y)];
+    }
+    __syncthreads();
+    const int64_t e0 = a.N.leaf_start[t], e1 = a.N.leaf_start[t + 1];
+    for (int64_t i = e0 + warp; i < e1; i += nw) {
+        const float2 *__restrict__ v = val + a.N.row_ptr[i];
+        float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+        int p = lane;
+        for (; p + 96 < nc; p += 128) {
+            const float2 v0 = __ldcs(v + p), v1 = __ldcs(v + p + 32), v2 = __ldcs(v + p + 64), v3 = __ldcs(v + p + 96);
+            acc0 = cfma(v0, xs[p], acc0);
+            acc1 = cfma(v1, xs[p + 32], acc1);
+            acc2 = cfma(v2, xs[p + 64], acc2);
+            acc3 = cfma(v3, xs[p + 96], acc3);
+        }
+        for (; p < nc; p += 32) acc0 = cfma(__ldcs(v + p), xs[p], acc0);
+        const float2 acc = warp_sum(cadd(cadd(acc0, acc1), cadd(acc2, acc3)));
+        if (lane == 0) y[i] = acc;
+    }
 }
 
 // Near-field product with the entries recomputed on the fly (no storage);
@@ -128,8 +234,19 @@ __global__ void k_prep(PrepArgs a, const int *skip)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const float2 *xb = a.x;
-    if (a.jidx) xb += (int64_t)(*a.jidx) * a.n;
-    const float2 xv = a.perm ? xb[a.perm[i]] : xb[i];
+    float2 xv;
+    if (a.wsrc) {
+        const int j = *a.jidx;
+        if (j > 0) {
+            xv = cscale(a.wsrc[i], (float)(1.0 / a.st->hn));
+            a.vdst[(int64_t)j * a.n + i] = xv;
+        } else {
+            xv = a.x[i];
+        }
+    } else {
+        if (a.jidx) xb += (int64_t)(*a.jidx) * a.n;
+        xv = a.perm ? xb[a.perm[i]] : xb[i];
+    }
     a.xint[i] = xv;
     if (a.alpha) {
         const float A = a.chi[i].w;
@@ -149,7 +266,7 @@ __global__ void k_prep(PrepArgs a, const int *skip)
 // source cluster c and direction s_nu,
 //   M_c(nu) = sum_{j in c} e^{ik (z_c - x_j).s_nu} (alpha_j + beta_j . s_nu).
 // One block per task (a chunk of at most kAggChunk elements of one cluster);
-// clusters split into several tasks are summed by k_agg_reduce.
+// the last task of a cluster split into several tasks sums their partial rows.
 constexpr int kAggChunk = 64;
 __global__ void k_aggregate(const LevelsArgs *__restrict__ A, const float2 *__restrict__ alpha,
                             const float2 *__restrict__ beta, const int *skip)
@@ -184,22 +301,31 @@ __global__ void k_aggregate(const LevelsArgs *__restrict__ A, const float2 *__re
         }
         out[nu] = acc;
     }
-}
-
-// M_c(nu) = sum of the partial rows of the tasks of a split cluster.
-__global__ void k_agg_reduce(const LevelsArgs *__restrict__ A, const int *skip)
-{
-    if (skip_now(skip)) return;
-    const int2 lq = A->reds[blockIdx.x];
-    const FarArgs &f = A->lev[lq.x];
-    const int q = lq.y;
-    const int r0 = f.red_ptr[q], r1 = f.red_ptr[q + 1];
-    float2 *__restrict__ out = f.M + (int64_t)f.red_c[q] * f.nd;
+    if (T.red < 0) return;
+    // split cluster: the last of its tasks to finish sums the partial rows
+    // in row order into M_c
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int ntask = f.red_ptr[T.red + 1] - f.red_ptr[T.red];
+        last = atomicAdd(&A->red_cnt[T.gred], 1u) == (unsigned)(ntask - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int r0 = f.red_ptr[T.red], r1 = f.red_ptr[T.red + 1];
+    float2 *__restrict__ dst = f.M + (int64_t)T.c * f.nd;
     for (int nu = threadIdx.x; nu < f.nd; nu += blockDim.x) {
         float2 acc = make_float2(0.f, 0.f);
-        for (int r = r0; r < r1; ++r) acc = cadd(acc, f.M[(int64_t)r * f.nd + nu]);
-        out[nu] = acc;
+        for (int rr = r0; rr < r1; ++rr) {
+            const volatile float2 *src = f.M + (int64_t)rr * f.nd + nu;
+            acc.x += src->x;
+            acc.y += src->y;
+        }
+        dst[nu] = acc;
     }
+    if (threadIdx.x == 0) A->red_cnt[T.gred] = 0;
 }
 
 // sin / cos of x by fast_sincos and by sincosf, for the unit tests.
@@ -477,120 +603,121 @@ __global__ void k_pq(const float2 *__restrict__ u, const float2 *__restrict__ z,
 }
 
 // ------------------------------------------------------------------ GMRES
-// Partial dot products h_l = sum_i conj(V_l[i]) w[i] for l <= j: FP32
-// products summed per thread, FP64 across threads and blocks.
-__global__ void k_gm_dots(const float2 *__restrict__ V, const float2 *__restrict__ w, int64_t n,
-                          const GmresState *st, double2 *__restrict__ part, int nblk)
+// Dot products h_l = sum_i conj(V_l[i]) w[i], l <= j, for one CGS pass:
+// FP32 products summed per thread, FP64 across threads and blocks.  The last
+// block of row l to finish sums the row's partials in block order (so the
+// result does not depend on scheduling) and sets (pass 0) or adds to
+// (pass 1) H[l][j].
+__global__ void k_gm_dots(GmresArgs a, int pass)
 {
+    const GmresState *st = a.st;
     if (st->done) return;
     const int l = blockIdx.y;
-    if (l > st->j) return;
-    const float2 *vl = V + (int64_t)l * n;
+    const int j = st->j;
+    if (l > j) return;
+    const float2 *vl = a.V + (int64_t)l * a.n;
+    const float2 *w = a.w;
     double2 acc = make_double2(0.0, 0.0);
-    const int64_t chunk = (n + nblk - 1) / nblk;
-    const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+    const int64_t chunk = (a.n + a.nblk - 1) / a.nblk;
+    const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(a.n, b0 + chunk);
     for (int64_t i0 = b0 + threadIdx.x; i0 < b1; i0 += 8 * (int64_t)blockDim.x) {
-        float2 s = make_float2(0.f, 0.f);
+        float2 sacc = make_float2(0.f, 0.f);
         for (int u = 0; u < 8; ++u) {
             const int64_t i = i0 + (int64_t)u * blockDim.x;
             if (i < b1) {
-                const float2 a = vl[i], b = w[i];
-                s.x = fmaf(a.x, b.x, fmaf(a.y, b.y, s.x));
-                s.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, s.y));
+                const float2 x = vl[i], y = w[i];
+                sacc.x = fmaf(x.x, y.x, fmaf(x.y, y.y, sacc.x));
+                sacc.y = fmaf(x.x, y.y, fmaf(-x.y, y.x, sacc.y));
             }
         }
-        acc.x += s.x;
-        acc.y += s.y;
+        acc.x += sacc.x;
+        acc.y += sacc.y;
     }
     acc = warp_sum_d(acc);
     __shared__ double2 red[32];
+    __shared__ bool last;
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x < 32) {
         double2 v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : make_double2(0.0, 0.0);
         v = warp_sum_d(v);
-        if (threadIdx.x == 0) part[(int64_t)l * nblk + blockIdx.x] = v;
+        if (threadIdx.x == 0) {
+            a.part[(int64_t)l * a.nblk + blockIdx.x] = v;
+            __threadfence();
+            last = atomicAdd(&a.cnt[l], 1u) == (unsigned)(a.nblk - 1);
+        }
+    }
+    __syncthreads();
+    if (!last) return;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const volatile double2 *pp = a.part + (int64_t)l * a.nblk;
+        double sx = 0.0, sy = 0.0;
+        for (int b = 0; b < a.nblk; ++b) { sx += pp[b].x; sy += pp[b].y; }
+        a.hcol[l] = make_double2(sx, sy);
+        double2 &h = a.H[(int64_t)l * a.m + j];
+        if (pass == 0) h = make_double2(sx, sy);
+        else { h.x += sx; h.y += sy; }
+        a.cnt[l] = 0;
     }
 }
 
-// Reduce the partial sums (one warp per l); pass 0 sets H[:, j], pass 1
-// adds (CGS2).
-__global__ void k_gm_reduce(GmresState *st, const double2 *__restrict__ part, int nblk, double2 *__restrict__ H,
-                            double2 *__restrict__ hcol, int m, int pass)
+// w <- w - sum_{l<=j} hcol_l V_l.  In the last pass the blocks also leave
+// partial ||w||^2; the last block to finish then does the Givens step (FP64):
+// h_{j+1,j} = ||w||, apply the previous rotations to column j, form the new
+// rotation, update g and the residual estimate, and decide whether the cycle
+// ends.  The division of w by h_{j+1,j} happens in the next product's gather.
+__global__ void k_gm_update(GmresArgs a, int last_pass)
 {
-    if (st->done) return;
-    const int j = st->j;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int l = warp; l <= j; l += nw) {
-        double2 sacc = make_double2(0.0, 0.0);
-        for (int b = lane; b < nblk; b += 32) {
-            sacc.x += part[(int64_t)l * nblk + b].x;
-            sacc.y += part[(int64_t)l * nblk + b].y;
-        }
-        sacc = warp_sum_d(sacc);
-        if (lane == 0) {
-            hcol[l] = sacc;
-            double2 &h = H[(int64_t)l * m + j];
-            if (pass == 0) h = sacc;
-            else { h.x += sacc.x; h.y += sacc.y; }
-        }
-    }
-}
-
-// w <- w - sum_{l<=j} hcol_l V_l; with norm != null also partial ||w||^2.
-__global__ void k_gm_update(const float2 *__restrict__ V, float2 *__restrict__ w, int64_t n, const GmresState *st,
-                            const double2 *__restrict__ hcol, double *__restrict__ normpart)
-{
+    GmresState *st = a.st;
     if (st->done) return;
     const int j = st->j;
     __shared__ float2 hs[kMaxRestart + 1];
-    for (int l = threadIdx.x; l <= j; l += blockDim.x) hs[l] = make_float2((float)hcol[l].x, (float)hcol[l].y);
+    for (int l = threadIdx.x; l <= j; l += blockDim.x) hs[l] = make_float2((float)a.hcol[l].x, (float)a.hcol[l].y);
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double nrm = 0.0;
-    if (i < n) {
-        float2 acc = w[i];
+    if (i < a.n) {
+        float2 acc = a.w[i];
         for (int l = 0; l <= j; ++l) {
-            const float2 v = V[(int64_t)l * n + i];
+            const float2 v = a.V[(int64_t)l * a.n + i];
             const float2 h = hs[l];
             acc.x -= h.x * v.x - h.y * v.y;
             acc.y -= h.x * v.y + h.y * v.x;
         }
-        w[i] = acc;
+        a.w[i] = acc;
         nrm = (double)acc.x * acc.x + (double)acc.y * acc.y;
     }
-    if (normpart) {
-        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-        __shared__ double red[32];
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (threadIdx.x == 0) normpart[blockIdx.x] = v;
+    if (!last_pass) return;
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    __shared__ double red[32];
+    __shared__ bool last;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) {
+            a.normpart[blockIdx.x] = v;
+            __threadfence();
+            last = atomicAdd(&a.cnt[a.m + 1], 1u) == (unsigned)(gridDim.x - 1);
         }
     }
-}
-
-// Givens step (single thread, FP64): h_{j+1,j} = ||w||, apply the previous
-// rotations to column j, form the new rotation, update g and the residual
-// estimate; decide whether the cycle ends.
-__global__ void k_gm_givens(GmresState *st, double2 *__restrict__ H, double2 *__restrict__ cs,
-                            double2 *__restrict__ sn, double2 *__restrict__ g, const double *__restrict__ normpart,
-                            int nblk, int m)
-{
-    if (st->done) return;
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    // ---- Givens step, one warp of the last block
     __shared__ double2 sh[kMaxRestart + 1], scs[kMaxRestart], ssn[kMaxRestart];
-    const int j = st->j;
+    __threadfence();
     double nn = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += 32) nn += normpart[b];
-    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-    // stage column j of H and the previous rotations (the serial loop below
-    // then runs on shared memory instead of dependent global loads)
-    for (int l = threadIdx.x; l <= j; l += 32) sh[l] = H[(int64_t)l * m + j];
-    for (int l = threadIdx.x; l < j; l += 32) { scs[l] = cs[l]; ssn[l] = sn[l]; }
+    const volatile double *np = a.normpart;
+    if (threadIdx.x == 0)
+        for (int b = 0; b < (int)gridDim.x; ++b) nn += np[b];     // block order: deterministic
+    const int m = a.m;
+    for (int l = threadIdx.x; l <= j; l += 32) sh[l] = a.H[(int64_t)l * m + j];
+    for (int l = threadIdx.x; l < j; l += 32) { scs[l] = a.cs[l]; ssn[l] = a.sn[l]; }
     __syncwarp();
     if (threadIdx.x == 0) {
+        a.cnt[m + 1] = 0;
         const double hn = sqrt(nn);
         sh[j + 1] = make_double2(hn, 0.0);
         for (int l = 0; l < j; ++l) {
@@ -607,14 +734,14 @@ __global__ void k_gm_givens(GmresState *st, double2 *__restrict__ H, double2 *__
         double2 c, s;
         if (den == 0.0) { c = make_double2(1.0, 0.0); s = make_double2(0.0, 0.0); }
         else { c = make_double2(h0.x / den, h0.y / den); s = make_double2(hn / den, 0.0); }
-        cs[j] = c;
-        sn[j] = s;
+        a.cs[j] = c;
+        a.sn[j] = s;
         sh[j] = make_double2(den, 0.0);
         sh[j + 1] = make_double2(0.0, 0.0);
-        const double2 g0 = g[j];
-        g[j] = make_double2(c.x * g0.x + c.y * g0.y, c.x * g0.y - c.y * g0.x);
+        const double2 g0 = a.g[j];
+        a.g[j] = make_double2(c.x * g0.x + c.y * g0.y, c.x * g0.y - c.y * g0.x);
         const double2 g1 = make_double2(-(s.x * g0.x - s.y * g0.y), -(s.x * g0.y + s.y * g0.x));
-        g[j + 1] = g1;
+        a.g[j + 1] = g1;
         const double res = sqrt(g1.x * g1.x + g1.y * g1.y) / st->bnorm;
         st->resid = res;
         st->iters += 1;
@@ -628,17 +755,7 @@ __global__ void k_gm_givens(GmresState *st, double2 *__restrict__ H, double2 *__
         }
     }
     __syncwarp();
-    for (int l = threadIdx.x; l <= j + 1; l += 32) H[(int64_t)l * m + j] = sh[l];
-}
-
-// V_{j} <- w / h_{j,j-1} for the new column index j (after the Givens step).
-__global__ void k_gm_scale(float2 *__restrict__ V, const float2 *__restrict__ w, int64_t n, const GmresState *st)
-{
-    if (st->done) return;
-    const int j = st->j;
-    const float inv = (float)(1.0 / st->hn);
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) V[(int64_t)j * n + i] = cscale(w[i], inv);
+    for (int l = threadIdx.x; l <= j + 1; l += 32) a.H[(int64_t)l * m + j] = sh[l];
 }
 
 // Back substitution y = R^{-1} g over ncols columns (FP64), one warp:

@@ -17,6 +17,7 @@ struct NearDev {
     const int2 *runs;        // {first element, first row position}
     const int *ncol;         // per leaf: near columns
     const int64_t *row_ptr;  // per element (+1): offsets into the stored values
+    const int64_t *leaf_start;  // per leaf (+1): first element (rows of a leaf are contiguous)
 };
 
 // Column of row position p for a lane that walks positions upwards; r is the
@@ -36,6 +37,11 @@ struct NearArgs {
     const float2 *cp, *cq;   // column coefficients (internal order)
 };
 
+struct GmresState {
+    int j, done, converged, iters, ncols, maxit;
+    double bnorm, beta, resid, tol, hn;
+};
+
 struct PrepArgs {
     int64_t n;
     const float2 *x;         // input vector (caller order if perm, else internal)
@@ -46,6 +52,11 @@ struct PrepArgs {
     const float4 *chi, *nrm;
     const float2 *cp, *cq;
     float k;
+    // GMRES mode (x = V, jidx set): for j > 0 the new basis vector is
+    // w / h_{j,j-1} (st->hn); it is formed here and stored to V_j.
+    const float2 *wsrc;
+    float2 *vdst;
+    const GmresState *st;
 };
 
 // Aggregation work item: `ne` elements from e0 of cluster c, written to row
@@ -55,6 +66,8 @@ struct AggTask {
     int64_t e0;
     int ne;
     int lev;                 // index of the level (in LevelsArgs) the task belongs to
+    int red;                 // split cluster: index of its partial-row range (in FarArgs), else -1
+    int gred;                // split cluster: index of its arrival counter, else -1
 };
 
 struct FarArgs {
@@ -84,6 +97,7 @@ struct LevelsArgs {
     int nreds;
     const int2 *targets;     // (level, target cluster) pairs with interaction lists
     int ntargets;
+    unsigned int *red_cnt;   // arrival counters of the split clusters (zero between uses)
     FarArgs lev[kMaxFarLevels];
 };
 
@@ -102,17 +116,15 @@ struct SourceDev {
     double amp[2];
 };
 
-struct GmresState {
-    int j, done, converged, iters, ncols, maxit;
-    double bnorm, beta, resid, tol, hn;
-};
-
 __global__ void k_near_store(NearArgs a, float2 *val, int *err);
+__global__ void k_near_classify(NearArgs a, int2 *heavy, unsigned long long *count, unsigned long long cap);
+__global__ void k_near_store_light(NearArgs a, float2 *val, int *err);
+__global__ void k_near_store_heavy(NearArgs a, const int2 *heavy, int64_t nheavy, float2 *val, int *err);
 __global__ void k_near_spmv(NearArgs a, const float2 *val, const float2 *x, float2 *y, const int *skip);
+__global__ void k_near_spmv_leaf(NearArgs a, const float2 *val, const float2 *x, float2 *y, const int *skip);
 __global__ void k_near_fused(NearArgs a, const float2 *x, float2 *y, int *err, const int *skip);
 __global__ void k_prep(PrepArgs a, const int *skip);
 __global__ void k_aggregate(const LevelsArgs *A, const float2 *alpha, const float2 *beta, const int *skip);
-__global__ void k_agg_reduce(const LevelsArgs *A, const int *skip);
 __global__ void k_selftest_sincos(const float *x, int64_t n, float4 *out);
 __global__ void k_transfer(const LevelsArgs *A, const int *skip);
 __global__ void k_disaggregate(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
@@ -127,15 +139,21 @@ __global__ void k_sub(float2 *b, const float2 *y, int64_t n);
 __global__ void k_rsub(float2 *w, const float2 *b, int64_t n);
 __global__ void k_pq(const float2 *u, const float2 *z, const float2 *aq, const int *type, const int64_t *perm,
                      int64_t n, float2 *p, float2 *q);
-__global__ void k_gm_dots(const float2 *V, const float2 *w, int64_t n, const GmresState *st, double2 *part,
-                          int nblk);
-__global__ void k_gm_reduce(GmresState *st, const double2 *part, int nblk, double2 *H, double2 *hcol, int m,
-                            int pass);
-__global__ void k_gm_update(const float2 *V, float2 *w, int64_t n, const GmresState *st, const double2 *hcol,
-                            double *normpart);
-__global__ void k_gm_givens(GmresState *st, double2 *H, double2 *cs, double2 *sn, double2 *g,
-                            const double *normpart, int nblk, int m);
-__global__ void k_gm_scale(float2 *V, const float2 *w, int64_t n, const GmresState *st);
+struct GmresArgs {
+    float2 *V, *w;
+    int64_t n;
+    GmresState *st;
+    double2 *part;           // [m + 1][nblk] dot partials
+    int nblk;
+    double2 *H, *hcol, *cs, *sn, *g;
+    double *normpart;        // [nnorm] norm partials
+    int nnorm;
+    unsigned int *cnt;       // [m + 2] arrival counters (zero between uses)
+    int m;
+};
+
+__global__ void k_gm_dots(GmresArgs a, int pass);
+__global__ void k_gm_update(GmresArgs a, int last_pass);
 __global__ void k_gm_backsolve(const GmresState *st, const double2 *H, const double2 *g, double2 *y, int m);
 __global__ void k_gm_xupdate(float2 *x, const float2 *V, int64_t n, const GmresState *st, const double2 *y);
 __global__ void k_gm_start(GmresState *st, float2 *V, const float2 *r, int64_t n, const double *normpart, int nblk,

@@ -390,6 +390,7 @@ void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k,
         double L = x + p.trunc_factor * std::log10(x + M_PI);
         Ld[d] = std::max(p.L_min, (int)std::ceil(L - 1e-12));
     }
+    fp.Ld = Ld;
     // near lists of the previous depth in CSR form
     std::vector<int32_t> nprev_ptr{0, 1}, nprev{0};
     int rnear_prev = 0;                 // largest |offset component| among near pairs
@@ -430,7 +431,13 @@ void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k,
                             const double X[3] = {dx * L.box, dy * L.box, dz * L.box};
                             const double dist = norm3(X);
                             off_dist[key] = dist;
-                            st = (p.stability_max >= 1e300 || hankel_growth(k * dist, F.L) <= p.stability_max) ? -3 : -1;
+                            if (p.stability_max >= 1e300) {
+                                st = -3;
+                            } else {
+                                const bool ok = hankel_growth(k * dist, F.L) <= p.stability_max;
+                                st = ok ? -3 : -1;
+                                fp.verdicts.push_back(Verdict{d, dx, dy, dz, F.L, ok});
+                            }
                         }
                         if (st != -1) {
                             const double dist = off_dist[key];

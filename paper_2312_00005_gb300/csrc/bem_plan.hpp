@@ -91,9 +91,18 @@ struct FarLevel {
     int64_t n_inter = 0;
 };
 
+// A Hankel-growth verdict the list builder evaluated: depth, box offset,
+// expansion length, and whether the offset passed.
+struct Verdict {
+    int depth, dx, dy, dz, L;
+    bool stable;
+};
+
 struct FreqPlan {
     double k = 0.0;
     bool direct = false;
+    std::vector<Verdict> verdicts;       // every stability test the build evaluated
+    std::vector<int> Ld;                 // expansion length per depth used by the build
     std::vector<FarLevel> far;           // used levels, coarse to fine
     // near field at the leaf depth: per leaf a list of source leaves
     std::vector<int32_t> near_ptr, near_src;
