@@ -300,7 +300,7 @@ def run_ours(args):
         "host_phases_ms_per_step": {k: round(1e3 * v / args.steps, 3) for k, v in phases.items()},
         "rel_error": acc,
         "plan": {k: stats[k] for k in ("levels", "L", "n_clusters", "n_interactions", "near_nnz", "far_pairs",
-                                       "leaf_edge")},
+                                       "leaf_edge", "leaf_level", "autotune")},
         "kernels": kernels,
         "roofline": roof,
         "clocks": clocks,

@@ -82,6 +82,8 @@ typedef struct bem_params {
     int32_t near_store;     /* 1: store near-field entries per frequency (default);
                                0: recompute them inside every product                         */
     int32_t restart;        /* GMRES restart length, 100                                       */
+    int32_t autotune;       /* 1: choose the leaf size by timing candidates on the GPU at the
+                               mesh's first plan (when leaf_edge is 0; default); 0: off       */
 } bem_params;
 
 typedef struct bem_medium {
@@ -126,6 +128,9 @@ typedef struct bem_plan_stats {
     int64_t device_bytes;       /* device memory held by the mesh and this plan        */
     int64_t far_pairs;          /* element pairs covered by the interaction lists;
                                    near_nnz + far_pairs = n_elements^2                  */
+    int32_t n_tuned;            /* leaf depths the autotuner timed (0: not run)        */
+    int32_t tuned_depth[4];     /* ... their octree depths                             */
+    double  tuned_seconds[4];   /* ... estimated seconds per solve (entries + 40 products) */
 } bem_plan_stats;
 
 /* Paper defaults (Sec. 3.1, Eq. FMMTruncation, Eq. Farfieldcond). */

@@ -40,6 +40,7 @@ class Params(ctypes.Structure):
         ("rt_subdiv", ctypes.c_double), ("max_depth", ctypes.c_int32), ("trunc_factor", ctypes.c_double),
         ("L_min", ctypes.c_int32), ("admissibility", ctypes.c_double), ("leaf_edge", ctypes.c_double),
         ("stability_max", ctypes.c_double), ("near_store", ctypes.c_int32), ("restart", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
     ]
 
 
@@ -67,6 +68,7 @@ class PlanStats(ctypes.Structure):
         ("n_interactions", ctypes.c_int64 * 16), ("n_offsets", ctypes.c_int32 * 16), ("n_leaves", ctypes.c_int32),
         ("near_nnz", ctypes.c_int64), ("near_quad_points", ctypes.c_int64), ("leaf_edge", ctypes.c_double),
         ("mean_edge", ctypes.c_double), ("device_bytes", ctypes.c_int64), ("far_pairs", ctypes.c_int64),
+        ("n_tuned", ctypes.c_int32), ("tuned_depth", ctypes.c_int32 * 4), ("tuned_seconds", ctypes.c_double * 4),
     ]
 
     def as_dict(self):
@@ -78,6 +80,7 @@ class PlanStats(ctypes.Structure):
             "n_offsets": list(self.n_offsets[:n]), "n_leaves": self.n_leaves, "near_nnz": self.near_nnz,
             "near_quad_points": self.near_quad_points, "leaf_edge": self.leaf_edge,
             "mean_edge": self.mean_edge, "device_bytes": self.device_bytes, "far_pairs": self.far_pairs,
+            "autotune": [(self.tuned_depth[q], self.tuned_seconds[q]) for q in range(self.n_tuned)],
         }
 
 

@@ -270,6 +270,7 @@ struct bem_mesh_impl {
     DevArr<int64_t> perm;
     DevArr<QuadTables> Q;
     DevArr<int> type, err;
+    DevArr<int> tma_err;          // set by a kernel whose bulk copy did not complete in time
     DevArr<float2> cp, cq, cp0, cq0, z, aq;
     DevArr<float2> xint, ynear, alpha, beta, tmp, tmp2, bvec, uvec;
     // GMRES workspace
@@ -280,7 +281,10 @@ struct bem_mesh_impl {
     DevArr<GmresState> st;
     std::unique_ptr<Plan> plan;
     std::shared_ptr<Lists> geo_lists;                  // frequency-independent lists
-    std::shared_ptr<Lists> last_lists;                 // lists of the last frequency-specific build
+    std::vector<std::shared_ptr<Lists>> freq_lists;    // recent frequency-specific builds (newest last)
+    int leaf_depth = 0;                                // leaf depth of the lists (autotuned)
+    bool tuned = false;
+    std::vector<std::pair<int, double>> tune_log;      // (leaf depth, estimated seconds per solve)
     // buffers kept from the previous plan (reused by the next frequency's plan)
     DevArr<float2> spare_val;
     std::vector<std::unique_ptr<DevArr<float2>>> spare_bufs;
@@ -350,7 +354,7 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
     auto Ls = std::make_shared<Lists>();
     Ls->fp = std::move(fp);
     const FreqPlan &F = Ls->fp;
-    const Level &Lf = M.t.lv[M.t.leaf_depth];
+    const Level &Lf = M.t.lv[F.leaf_depth];
     const int nl = (int)Lf.start.size();
     cudaStream_t s = M.s;
     // near columns of each leaf as runs of consecutive leaves
@@ -369,9 +373,11 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
     }
     std::vector<int> leaf_of(M.n);
     std::vector<int64_t> row_ptr(M.n + 1, 0), leaf_start(nl + 1, M.n);
+    // rows padded to an even length: every row (and every leaf's block of
+    // rows) starts on a 16-byte boundary for the TMA product
     for (int64_t i = 0; i < M.n; ++i) {
         leaf_of[i] = Lf.elem_cluster[i];
-        row_ptr[i + 1] = row_ptr[i] + ncol[leaf_of[i]];
+        row_ptr[i + 1] = row_ptr[i] + ((ncol[leaf_of[i]] + 1) & ~1);
     }
     for (int t = 0; t < nl; ++t) {
         leaf_start[t] = Lf.start[t];
@@ -509,61 +515,12 @@ void take_spare(bem_mesh_impl &M, DevArr<float2> &dst, size_t count)
     dst.alloc(count);
 }
 
-void build_plan_dev(bem_mesh_impl &M, double freq, double c)
+// Per-frequency part of a plan on given lists: expansion lengths, sphere
+// grids, translation tables (GPU), buffers and the kernel argument block.
+void finish_plan(bem_mesh_impl &M, Plan &Pl)
 {
-    if (M.plan && M.plan->freq == freq && M.plan->c == c) return;
-    recycle_plan(M);
-    auto P = std::make_unique<Plan>();
-    P->freq = freq;
-    P->c = c;
-    P->k = wavenumber(freq, c);
+    Plan *P = &Pl;
     const double k = P->k;
-    if (!M.geo_lists) {
-        bem_params gp = M.prm;
-        gp.stability_max = 1e308;
-        FreqPlan fp;
-        build_plan(M.g, M.t, gp, k, fp);
-        M.geo_lists = upload_lists(M, std::move(fp));
-    }
-    // reuse the geometric lists when every far offset passes the Hankel test
-    bool ok = true;
-    for (const FarLevel &FL : M.geo_lists->fp.far) {
-        const int L = level_L(M, FL.depth, k);
-        for (size_t o = 0; ok && o < FL.offsets.size() / 3; ++o) {
-            const double X = std::sqrt(FL.offsets[3 * o] * FL.offsets[3 * o] + FL.offsets[3 * o + 1] * FL.offsets[3 * o + 1] +
-                                       FL.offsets[3 * o + 2] * FL.offsets[3 * o + 2]);
-            if (!(hankel_growth(k * X, L) <= M.prm.stability_max)) ok = false;
-        }
-        if (!ok) break;
-    }
-    // else reuse the last frequency's lists when every stability verdict its
-    // build evaluated (and the expansion length per depth) is unchanged: the
-    // recursion then makes the same decisions
-    bool reuse_last = false;
-    if (!ok && M.last_lists) {
-        const FreqPlan &lf = M.last_lists->fp;
-        reuse_last = true;
-        for (size_t d = 0; reuse_last && d < lf.Ld.size(); ++d)
-            if (level_L(M, (int)d, k) != lf.Ld[d]) reuse_last = false;
-        for (size_t q = 0; reuse_last && q < lf.verdicts.size(); ++q) {
-            const Verdict &v = lf.verdicts[q];
-            const double b = M.t.lv[v.depth].box;
-            const double X = b * std::sqrt((double)v.dx * v.dx + (double)v.dy * v.dy + (double)v.dz * v.dz);
-            if ((hankel_growth(k * X, v.L) <= M.prm.stability_max) != v.stable) reuse_last = false;
-        }
-    }
-    if (ok) {
-        P->lists = M.geo_lists;
-        P->shared_lists = true;
-    } else if (reuse_last) {
-        P->lists = M.last_lists;
-        P->shared_lists = true;
-    } else {
-        FreqPlan fp;
-        build_plan(M.g, M.t, M.prm, k, fp);
-        P->lists = upload_lists(M, std::move(fp));
-        M.last_lists = P->lists;
-    }
     cudaStream_t s = M.s;
     const FreqPlan &fp = P->fp();
     for (size_t l = 0; l < fp.far.size(); ++l) {
@@ -613,6 +570,73 @@ void build_plan_dev(bem_mesh_impl &M, double freq, double c)
     std::vector<LevelsArgs> hv(1, A);
     P->largs.upload(hv, s);
     ck(cudaStreamSynchronize(s), "sync");
+}
+
+void autotune_leaf_depth(bem_mesh_impl &M, double k);
+
+void build_plan_dev(bem_mesh_impl &M, double freq, double c)
+{
+    if (M.plan && M.plan->freq == freq && M.plan->c == c) return;
+    recycle_plan(M);
+    auto P = std::make_unique<Plan>();
+    P->freq = freq;
+    P->c = c;
+    P->k = wavenumber(freq, c);
+    const double k = P->k;
+    if (!M.geo_lists) {
+        if (!M.tuned) autotune_leaf_depth(M, k);
+        if (!M.geo_lists) {
+            bem_params gp = M.prm;
+            gp.stability_max = 1e308;
+            FreqPlan fp;
+            build_plan(M.g, M.t, gp, k, fp, M.leaf_depth);
+            M.geo_lists = upload_lists(M, std::move(fp));
+        }
+    }
+    // reuse the geometric lists when every far offset passes the Hankel test
+    bool ok = true;
+    for (const FarLevel &FL : M.geo_lists->fp.far) {
+        const int L = level_L(M, FL.depth, k);
+        for (size_t o = 0; ok && o < FL.offsets.size() / 3; ++o) {
+            const double X = std::sqrt(FL.offsets[3 * o] * FL.offsets[3 * o] + FL.offsets[3 * o + 1] * FL.offsets[3 * o + 1] +
+                                       FL.offsets[3 * o + 2] * FL.offsets[3 * o + 2]);
+            if (!(hankel_growth(k * X, L) <= M.prm.stability_max)) ok = false;
+        }
+        if (!ok) break;
+    }
+    // else reuse a recent frequency-specific build when every stability
+    // verdict it evaluated (and the expansion length per depth) is unchanged:
+    // the recursion then makes the same decisions
+    std::shared_ptr<Lists> reuse;
+    if (!ok) {
+        for (auto it = M.freq_lists.rbegin(); it != M.freq_lists.rend() && !reuse; ++it) {
+            const FreqPlan &lf = (*it)->fp;
+            bool same = true;
+            for (size_t d = 0; same && d < lf.Ld.size(); ++d)
+                if (level_L(M, (int)d, k) != lf.Ld[d]) same = false;
+            for (size_t q = 0; same && q < lf.verdicts.size(); ++q) {
+                const Verdict &v = lf.verdicts[q];
+                const double b = M.t.lv[v.depth].box;
+                const double X = b * std::sqrt((double)v.dx * v.dx + (double)v.dy * v.dy + (double)v.dz * v.dz);
+                if ((hankel_growth(k * X, v.L) <= M.prm.stability_max) != v.stable) same = false;
+            }
+            if (same) reuse = *it;
+        }
+    }
+    if (ok) {
+        P->lists = M.geo_lists;
+        P->shared_lists = true;
+    } else if (reuse) {
+        P->lists = reuse;
+        P->shared_lists = true;
+    } else {
+        FreqPlan fp;
+        build_plan(M.g, M.t, M.prm, k, fp, M.leaf_depth);
+        P->lists = upload_lists(M, std::move(fp));
+        M.freq_lists.push_back(P->lists);
+        if (M.freq_lists.size() > 4) M.freq_lists.erase(M.freq_lists.begin());
+    }
+    finish_plan(M, *P);
     M.plan = std::move(P);
 }
 
@@ -679,9 +703,15 @@ void upload_coeffs(bem_mesh_impl &M, const Coeffs &C)
 
 void check_err(bem_mesh_impl &M)
 {
-    int e = INT_MAX;
+    int e = INT_MAX, te = 0;
     ck(cudaMemcpyAsync(&e, M.err.p, sizeof(int), cudaMemcpyDeviceToHost, M.s), "D2H err");
+    ck(cudaMemcpyAsync(&te, M.tma_err.p, sizeof(int), cudaMemcpyDeviceToHost, M.s), "D2H err");
     ck(cudaStreamSynchronize(M.s), "sync");
+    if (te != 0) {
+        ck(cudaMemsetAsync(M.tma_err.p, 0, sizeof(int), M.s), "memset");
+        g_err = "a bulk copy of near-field entries did not complete within its wait limit";
+        throw Fail{BEM_E_TIMEOUT};
+    }
     if (e != INT_MAX) {
         char buf[160];
         snprintf(buf, sizeof buf,
@@ -698,38 +728,15 @@ void reset_err(bem_mesh_impl &M)
     ck(cudaMemcpyAsync(M.err.p, &v, sizeof(int), cudaMemcpyHostToDevice, M.s), "H2D err");
 }
 
-// Make sure the stored near-field values match the current unknowns' coefficients.
-void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
+// Stored near-field entries of plan P for the column coefficients (cp, cq):
+// the expensive pairs are listed once per set of lists, then computed by
+// their own kernel.
+void store_near(bem_mesh_impl &M, Plan &P, const float2 *cp, const float2 *cq)
 {
-    Plan &P = *M.plan;
-    std::vector<float> key;
-    key.reserve(4 * M.n);
-    for (int64_t i = 0; i < M.n; ++i) {
-        key.push_back(C.cp[i].x); key.push_back(C.cp[i].y);
-        key.push_back(C.cq[i].x); key.push_back(C.cq[i].y);
-    }
-    if (!M.prm.near_store || P.fp().direct) {
-        if (!P.val_valid) {
-            // one fused pass validates the subdivision limit for this plan
-            reset_err(M);
-            M.tmp.alloc(M.n);
-            ck(cudaMemsetAsync(M.tmp.p, 0, M.n * sizeof(float2), M.s), "memset");
-            NearArgs a = near_args(M, P, M.cp.p, M.cq.p);
-            {
-                KTimer kt_("k_near_fused", M.s);
-                k_near_fused<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, M.tmp.p, M.ynear.p, M.err.p, nullptr);
-            }
-            ck_launch("k_near_fused");
-            check_err(M);
-            P.val_valid = true;
-        }
-        return;
-    }
-    if (P.val_valid && key == P.val_key) return;
     if (!P.val.p) P.val.swap(M.spare_val);
     P.val.alloc((size_t)P.nnz());
     reset_err(M);
-    NearArgs a = near_args(M, P, M.cp.p, M.cq.p);
+    NearArgs a = near_args(M, P, cp, cq);
     Lists &Ls = *P.lists;
     if (Ls.n_heavy < 0) {
         // count, then list, the expensive pairs of these lists (geometry only)
@@ -768,6 +775,37 @@ void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
         ck_launch("k_near_store_heavy");
     }
     check_err(M);
+}
+
+// Make sure the stored near-field values match the current unknowns' coefficients.
+void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
+{
+    Plan &P = *M.plan;
+    std::vector<float> key;
+    key.reserve(4 * M.n);
+    for (int64_t i = 0; i < M.n; ++i) {
+        key.push_back(C.cp[i].x); key.push_back(C.cp[i].y);
+        key.push_back(C.cq[i].x); key.push_back(C.cq[i].y);
+    }
+    if (!M.prm.near_store || P.fp().direct) {
+        if (!P.val_valid) {
+            // one fused pass validates the subdivision limit for this plan
+            reset_err(M);
+            M.tmp.alloc(M.n);
+            ck(cudaMemsetAsync(M.tmp.p, 0, M.n * sizeof(float2), M.s), "memset");
+            NearArgs a = near_args(M, P, M.cp.p, M.cq.p);
+            {
+                KTimer kt_("k_near_fused", M.s);
+                k_near_fused<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, M.tmp.p, M.ynear.p, M.err.p, nullptr);
+            }
+            ck_launch("k_near_fused");
+            check_err(M);
+            P.val_valid = true;
+        }
+        return;
+    }
+    if (P.val_valid && key == P.val_key) return;
+    store_near(M, P, M.cp.p, M.cq.p);
     P.val_key.swap(key);
     P.val_valid = true;
 }
@@ -810,7 +848,7 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
         if (xs_bytes <= 160 * 1024) {
             {
                 KTimer kt_("k_near_spmv", s);
-                k_near_spmv_leaf<<<nleaf, 128, xs_bytes, s>>>(na, P.val.p, M.xint.p, M.ynear.p, skip);
+                k_near_spmv_leaf<<<nleaf, 256, xs_bytes, s>>>(na, P.val.p, M.xint.p, M.ynear.p, skip);
             }
             ck_launch("k_near_spmv");
         } else {
@@ -849,11 +887,85 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
         ck_launch("k_transfer");
     }
     for (int l = 0; l < A.nlev; ++l) da.lev[l] = A.lev[l];
+    da.leaf_start = P.lists->leaf_start.p;
+    da.sum_nd = 0;
+    for (int l = 0; l < A.nlev; ++l) da.sum_nd += A.lev[l].nd;
     {
         KTimer kt_("k_disaggregate", s);
-        k_disaggregate<<<nblocks(n, 8), 256, 0, s>>>(da, M.ynear.p, y, skip);
+        const int nleaf = (int)(P.lists->leaf_start.n - 1);
+        k_disaggregate<<<nleaf, 128, (size_t)std::max(1, da.sum_nd) * sizeof(float2), s>>>(da, M.ynear.p, y, skip);
     }
     ck_launch("k_disaggregate");
+}
+
+// Leaf-size autotuner: builds the geometric lists for the automatic leaf
+// depth and its neighbours, times the near-field entries and a few FMA
+// products of each on this GPU, and keeps the depth with the smallest
+// estimated solve time (entries + 40 products).  Runs once per mesh.
+void autotune_leaf_depth(bem_mesh_impl &M, double k)
+{
+    M.tuned = true;
+    if (!M.prm.autotune || M.prm.mode == BEM_MODE_DIRECT || M.prm.leaf_edge > 0 || M.n < 4096) return;
+    const int64_t n = M.n;
+    DevArr<float2> tcp, tcq, tx, ty;
+    std::vector<float2> h1(n, make_float2(1.f, 0.f)), h0(n, make_float2(0.f, 0.f)), hx(n);
+    for (int64_t i = 0; i < n; ++i) hx[i] = make_float2(std::cos(0.37 * i), std::sin(0.11 * i));
+    tcp.upload(h1, M.s);
+    tcq.upload(h0, M.s);
+    tx.upload(hx, M.s);
+    ty.alloc(n);
+    cudaEvent_t e0, e1, e2;
+    ck(cudaEventCreate(&e0), "event");
+    ck(cudaEventCreate(&e1), "event");
+    ck(cudaEventCreate(&e2), "event");
+    std::shared_ptr<Lists> best;
+    int best_d = M.leaf_depth;
+    double best_cost = 1e300;
+    for (int d = M.leaf_depth - 1; d <= M.leaf_depth + 1; ++d) {
+        if (d < 1 || d > M.t.leaf_depth) continue;
+        bem_params gp = M.prm;
+        gp.stability_max = 1e308;
+        FreqPlan fp;
+        build_plan(M.g, M.t, gp, k, fp, d);
+        if (fp.far.empty() && d != M.leaf_depth) continue;
+        auto lists = upload_lists(M, std::move(fp));
+        auto P = std::make_unique<Plan>();
+        P->k = k;
+        P->lists = lists;
+        finish_plan(M, *P);
+        std::unique_ptr<Plan> keep;
+        keep.swap(M.plan);
+        M.plan = std::move(P);
+        M.plan->val.alloc((size_t)M.plan->nnz());
+        ck(cudaEventRecord(e0, M.s), "record");
+        store_near(M, *M.plan, tcp.p, tcq.p);
+        ck(cudaEventRecord(e1, M.s), "record");
+        ck(cudaEventSynchronize(e1), "sync");
+        float ms_store = 0.f, ms_mv = 0.f;
+        ck(cudaEventElapsedTime(&ms_store, e0, e1), "elapsed");
+        matvec_internal(M, tcp.p, tcq.p, true, tx.p, nullptr, false, ty.p, false, nullptr, M.s);   // warm-up
+        ck(cudaEventRecord(e1, M.s), "record");
+        for (int r = 0; r < 3; ++r) matvec_internal(M, tcp.p, tcq.p, true, tx.p, nullptr, false, ty.p, false, nullptr, M.s);
+        ck(cudaEventRecord(e2, M.s), "record");
+        ck(cudaEventSynchronize(e2), "sync");
+        ck(cudaEventElapsedTime(&ms_mv, e1, e2), "elapsed");
+        const double cost = 1e-3 * (ms_store + 40.0 * ms_mv / 3.0);
+        M.tune_log.push_back({d, cost});
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = lists;
+            best_d = d;
+        }
+        M.plan.reset();
+        M.plan.swap(keep);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    if (best) {
+        M.leaf_depth = best_d;
+        M.geo_lists = best;
+    }
 }
 
 void ensure_work(bem_mesh_impl &M)
@@ -931,7 +1043,7 @@ void fill_stats(const Geometry &g, const Tree &t, const FreqPlan &fp, bem_plan_s
 {
     memset(out, 0, sizeof *out);
     out->n_elements = g.n;
-    out->leaf_level = t.leaf_depth;
+    out->leaf_level = fp.leaf_depth;
     out->levels = (int)fp.far.size();
     int64_t far_pairs = 0;
     for (size_t l = 0; l < fp.far.size() && l < 16; ++l) {
@@ -946,10 +1058,10 @@ void fill_stats(const Geometry &g, const Tree &t, const FreqPlan &fp, bem_plan_s
             for (int q = F.il_ptr[c]; q < F.il_ptr[c + 1]; ++q) far_pairs += L.count[c] * L.count[F.il_src[q]];
     }
     out->far_pairs = far_pairs;
-    out->n_leaves = (int)t.lv[t.leaf_depth].start.size();
+    out->n_leaves = (int)t.lv[fp.leaf_depth].start.size();
     out->near_nnz = fp.nnz;
     out->near_quad_points = -1;
-    out->leaf_edge = t.lv[t.leaf_depth].box;
+    out->leaf_edge = t.lv[fp.leaf_depth].box;
     out->mean_edge = g.mean_edge;
 }
 
@@ -973,6 +1085,7 @@ void bem_params_default(bem_params *p)
     p->stability_max = 1e3;
     p->near_store = 1;
     p->restart = 100;
+    p->autotune = 1;
 }
 
 const char *bem_last_error(void) { return g_err.c_str(); }
@@ -1017,7 +1130,12 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         }
         const double leaf = p.mode == BEM_MODE_DIRECT ? 0.0
                             : (p.leaf_edge > 0 ? p.leaf_edge : auto_leaf_edge(M->g, p));
-        build_tree(M->g, leaf, M->t);
+        const bool tune = p.autotune && p.mode != BEM_MODE_DIRECT && !(p.leaf_edge > 0) && n_tris >= 4096;
+        // one level deeper than the automatic leaves so the tuner can try a
+        // finer leaf size; the lists use M->leaf_depth
+        build_tree(M->g, tune ? 0.5 * leaf : leaf, M->t);
+        M->leaf_depth = tune ? std::max(0, M->t.leaf_depth - 1) : M->t.leaf_depth;
+        M->tuned = !tune;
         ck(cudaGetDevice(&M->device), "cudaGetDevice");
         ck(cudaStreamCreateWithFlags(&M->s, cudaStreamNonBlocking), "stream");
         const int64_t n = n_tris;
@@ -1053,9 +1171,16 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         M->type.upload(ty, s);
         ck(cudaFuncSetAttribute(k_near_spmv_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024),
            "cudaFuncSetAttribute");
+        ck(cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 100 * 16),
+           "cudaFuncSetAttribute");
+        ck(cudaFuncSetAttribute(k_disaggregate, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024),
+           "cudaFuncSetAttribute");
+
         std::vector<QuadTables> qt(1, make_tables(p));
         M->Q.upload(qt, s);
         M->err.alloc(1);
+        M->tma_err.alloc(1);
+        ck(cudaMemsetAsync(M->tma_err.p, 0, sizeof(int), s), "memset");
         ck(cudaStreamSynchronize(s), "sync");
         *out = M.release();
         return BEM_OK;
@@ -1176,9 +1301,9 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         M.g_.alloc(m + 1);
         M.hcol.alloc(m + 1);
         M.yv.alloc(m + 1);
-        const int nblk = (int)std::min<int64_t>(148, std::max<int64_t>(1, n / 2048));
+        const int nblk = (int)std::min<int64_t>(256, std::max<int64_t>(1, n / 1024));
         M.part.alloc((size_t)(m + 1) * nblk);
-        const int nnorm = (int)nblocks(n, 256);
+        const int nnorm = (int)nblocks(n, 128);
         M.normpart.alloc(std::max(nnorm, nblk));
         M.st.alloc(1);
         GmresState hs;
@@ -1230,12 +1355,12 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
             for (int pass = 0; pass < 2; ++pass) {
                 {
                     KTimer kt_("k_gm_dots", s);
-                    k_gm_dots<<<dim3(nblk, m + 1), 256, 0, s>>>(ga, pass);
+                    k_gm_dots<<<dim3(nblk, m + 1), 128, 0, s>>>(ga, pass);
                 }
                 ck_launch("k_gm_dots");
                 {
                     KTimer kt_("k_gm_update", s);
-                    k_gm_update<<<nnorm, 256, 0, s>>>(ga, pass);
+                    k_gm_update<<<nnorm, 128, 0, s>>>(ga, pass);
                 }
                 ck_launch("k_gm_update");
             }
@@ -1274,7 +1399,9 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
             }
             {
                 KTimer kt_("k_gm_backsolve", s);
-                k_gm_backsolve<<<1, 32, 0, s>>>(M.st.p, M.H.p, M.g_.p, M.yv.p, m);
+                const int tri_cols = std::min(m, 100);
+                k_gm_backsolve<<<1, 32, (size_t)tri_cols * tri_cols * sizeof(double2), s>>>(M.st.p, M.H.p, M.g_.p,
+                                                                                           M.yv.p, m, tri_cols);
             }
             ck_launch("k_gm_backsolve");
             {
@@ -1428,7 +1555,7 @@ int bem_mesh_release_plan(void *mesh)
     cudaSetDevice(M.device);
     if (M.s) cudaStreamSynchronize(M.s);
     M.plan.reset();
-    M.last_lists.reset();
+    M.freq_lists.clear();
     M.spare_val.release();
     M.spare_bufs.clear();
     return BEM_OK;
@@ -1497,6 +1624,11 @@ int bem_mesh_stats(void *mesh, double freq_hz, const bem_medium *medium, bem_pla
         Plan &P = *M.plan;
         fill_stats(M.g, M.t, P.fp(), out);
         for (size_t l = 0; l < P.lev.size() && l < 16; ++l) out->L[l] = P.lev[l]->L;
+        out->n_tuned = (int)std::min<size_t>(4, M.tune_log.size());
+        for (int q = 0; q < out->n_tuned; ++q) {
+            out->tuned_depth[q] = M.tune_log[q].first;
+            out->tuned_seconds[q] = M.tune_log[q].second;
+        }
         int64_t bytes = 0;
         bytes += M.chi.bytes() * 6 + M.cd.bytes() * 4 + M.ad.bytes() + M.perm.bytes();
         bytes += P.lists->runs.bytes() + P.lists->row_ptr.bytes() + P.val.bytes();

@@ -24,6 +24,27 @@ __device__ __forceinline__ double2 warp_sum_d(double2 v)
     return v;
 }
 
+// Sum of p[0..n) by one warp in a fixed order (lane l adds p[l], p[l+32],
+// ..., then a fixed shuffle tree): deterministic, and the loads are issued in
+// parallel instead of as a dependent chain.
+__device__ __forceinline__ double warp_sum_array(const volatile double *p, int n)
+{
+    double v = 0.0;
+    for (int b = threadIdx.x & 31; b < n; b += 32) v += p[b];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double2 warp_sum_array2(const volatile double2 *p, int n)
+{
+    double2 v = make_double2(0.0, 0.0);
+    for (int b = threadIdx.x & 31; b < n; b += 32) { v.x += p[b].x; v.y += p[b].y; }
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
 __device__ __forceinline__ bool skip_now(const int *skip) { return skip != nullptr && *(volatile const int *)skip != 0; }
 
 // ------------------------------------------------------------------ near field
@@ -170,7 +191,15 @@ __global__ void k_near_spmv_leaf(NearArgs a, const float2 *__restrict__ val, con
     for (int r = r0 + warp; r < r1; r += nw) {
         const int2 rr = a.N.runs[r];
         const int end = (r + 1 < r1) ? a.N.runs[r + 1].y : nc;
-        for (int p = rr.y + lane; p < end; p += 32) xs[p] = x[rr.x + (p - rr.y)];
+        int p = rr.y + lane;
+        for (; p + 224 < end; p += 256) {
+            float2 t8[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t8[u] = x[rr.x + (p + 32 * u - rr.y)];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) xs[p + 32 * u] = t8[u];
+        }
+        for (; p < end; p += 32) xs[p] = x[rr.x + (p - rr.y)];
     }
     __syncthreads();
     const int64_t e0 = a.N.leaf_start[t], e1 = a.N.leaf_start[t + 1];
@@ -178,6 +207,18 @@ __global__ void k_near_spmv_leaf(NearArgs a, const float2 *__restrict__ val, con
         const float2 *__restrict__ v = val + a.N.row_ptr[i];
         float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
         int p = lane;
+        for (; p + 480 < nc; p += 512) {
+            float2 vv[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) vv[u] = __ldcs(v + p + 32 * u);
+#pragma unroll
+            for (int u = 0; u < 16; u += 4) {
+                acc0 = cfma(vv[u], xs[p + 32 * u], acc0);
+                acc1 = cfma(vv[u + 1], xs[p + 32 * (u + 1)], acc1);
+                acc2 = cfma(vv[u + 2], xs[p + 32 * (u + 2)], acc2);
+                acc3 = cfma(vv[u + 3], xs[p + 32 * (u + 3)], acc3);
+            }
+        }
         for (; p + 96 < nc; p += 128) {
             const float2 v0 = __ldcs(v + p), v1 = __ldcs(v + p + 32), v2 = __ldcs(v + p + 64), v3 = __ldcs(v + p + 96);
             acc0 = cfma(v0, xs[p], acc0);
@@ -364,15 +405,21 @@ __global__ void k_transfer(const LevelsArgs *__restrict__ A, const int *skip)
             __syncthreads();
             if (nu < f.nd) {
                 int q = 0;
-                for (; q + 3 < cnt; q += 4) {
-                    const float2 D0 = f.D[s_off[q] + nu], M0 = f.M[s_src[q] + nu];
-                    const float2 D1 = f.D[s_off[q + 1] + nu], M1 = f.M[s_src[q + 1] + nu];
-                    const float2 D2 = f.D[s_off[q + 2] + nu], M2 = f.M[s_src[q + 2] + nu];
-                    const float2 D3 = f.D[s_off[q + 3] + nu], M3 = f.M[s_src[q + 3] + nu];
-                    acc0 = cfma(D0, M0, acc0);
-                    acc1 = cfma(D1, M1, acc1);
-                    acc2 = cfma(D2, M2, acc2);
-                    acc3 = cfma(D3, M3, acc3);
+                for (; q + 7 < cnt; q += 8) {
+                    float2 Dv[8], Mv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        Dv[u] = f.D[s_off[q + u] + nu];
+                        Mv[u] = f.M[s_src[q + u] + nu];
+                    }
+                    acc0 = cfma(Dv[0], Mv[0], acc0);
+                    acc1 = cfma(Dv[1], Mv[1], acc1);
+                    acc2 = cfma(Dv[2], Mv[2], acc2);
+                    acc3 = cfma(Dv[3], Mv[3], acc3);
+                    acc0 = cfma(Dv[4], Mv[4], acc0);
+                    acc1 = cfma(Dv[5], Mv[5], acc1);
+                    acc2 = cfma(Dv[6], Mv[6], acc2);
+                    acc3 = cfma(Dv[7], Mv[7], acc3);
                 }
                 for (; q < cnt; ++q) acc0 = cfma(f.D[s_off[q] + nu], f.M[s_src[q] + nu], acc0);
             }
@@ -385,38 +432,64 @@ __global__ void k_transfer(const LevelsArgs *__restrict__ A, const int *skip)
 // Burton-Miller row operator 1 + s.n_i) and the final sum with the near field:
 //   y_i = near_i + (ik/16 pi^2) sum_l sum_nu w_nu (1 + s_nu.n_i)
 //                   e^{ik (x_i - z_t).s_nu} Lambda_t(nu).
-// One warp per element; writes y[perm[i]] (caller order) or y[i].
+// One block per leaf: the elements of a leaf share their cluster at every
+// level, so the Lambda rows of the leaf's ancestors are staged in shared
+// memory once; each warp then takes one element at a time (lanes over nu) and
+// writes y[perm[i]] (caller order) or y[i].
 __global__ void k_disaggregate(DisaggArgs a, const float2 *__restrict__ ynear, float2 *__restrict__ y,
                                const int *skip)
 {
     if (skip_now(skip)) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= a.n) return;
-    const float3 ni = f3(a.nrm[i]);
-    float2 acc = make_float2(0.f, 0.f);
-    for (int l = 0; l < a.nlev; ++l) {
-        const FarArgs &f = a.lev[l];
-        const int c = f.elem_cl[i];
-        if (f.il_ptr[c] == f.il_ptr[c + 1]) continue;
-        const float3 dz = f3(f.dz[i]);                 // z_c - x_i
-        const float2 *__restrict__ lam = f.Lam + (int64_t)c * f.nd;
-        for (int nu = lane; nu < f.nd; nu += 32) {
-            const float4 s = f.dirs[nu];
-            float sn, cs;
-            fast_sincos(-f.k * dot3f(dz, f3(s)), &sn, &cs);
-            const float wf = s.w * (1.0f + dot3f(f3(s), ni));
-            acc = cfma(make_float2(cs * wf, sn * wf), lam[nu], acc);
+    extern __shared__ float2 lam_s[];           // sum_nd entries
+    __shared__ int s_off[kMaxFarLevels + 1], s_has[kMaxFarLevels];
+    const int t = blockIdx.x;
+    const int64_t e0 = a.leaf_start[t], e1 = a.leaf_start[t + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) {
+        int off = 0;
+        for (int l = 0; l < a.nlev; ++l) {
+            const FarArgs &f = a.lev[l];
+            const int c = f.elem_cl[e0];
+            s_has[l] = f.il_ptr[c] != f.il_ptr[c + 1];
+            s_off[l] = off;
+            off += f.nd;
         }
+        s_off[a.nlev] = off;
     }
-    acc = warp_sum(acc);
-    if (lane == 0) {
-        // (ik / 16 pi^2) acc
-        const float s = a.k * 0.00633257397764611f;   // k / (16 pi^2)
-        float2 far = make_float2(-s * acc.y, s * acc.x);
-        float2 out = cadd(ynear[i], far);
-        if (a.perm) y[a.perm[i]] = out;
-        else y[i] = out;
+    __syncthreads();
+    for (int l = 0; l < a.nlev; ++l) {
+        if (!s_has[l]) continue;
+        const FarArgs &f = a.lev[l];
+        const float2 *__restrict__ src = f.Lam + (int64_t)f.elem_cl[e0] * f.nd;
+        for (int nu = threadIdx.x; nu < f.nd; nu += blockDim.x) lam_s[s_off[l] + nu] = src[nu];
+    }
+    __syncthreads();
+    for (int64_t i = e0 + warp; i < e1; i += nw) {
+        const float3 ni = f3(a.nrm[i]);
+        float2 acc = make_float2(0.f, 0.f);
+        for (int l = 0; l < a.nlev; ++l) {
+            if (!s_has[l]) continue;
+            const FarArgs &f = a.lev[l];
+            const float3 dz = f3(f.dz[i]);             // z_c - x_i
+            const float2 *lam = lam_s + s_off[l];
+            const float kk = -f.k;
+            for (int nu = lane; nu < f.nd; nu += 32) {
+                const float4 s = f.dirs[nu];
+                float sn, cs;
+                fast_sincos(kk * dot3f(dz, f3(s)), &sn, &cs);
+                const float wf = s.w * (1.0f + dot3f(f3(s), ni));
+                acc = cfma(make_float2(cs * wf, sn * wf), lam[nu], acc);
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            // (ik / 16 pi^2) acc
+            const float sc = a.k * 0.00633257397764611f;   // k / (16 pi^2)
+            const float2 far = make_float2(-sc * acc.y, sc * acc.x);
+            const float2 out = cadd(ynear[i], far);
+            if (a.perm) y[a.perm[i]] = out;
+            else y[i] = out;
+        }
     }
 }
 
@@ -612,6 +685,7 @@ __global__ void k_gm_dots(GmresArgs a, int pass)
 {
     const GmresState *st = a.st;
     if (st->done) return;
+    if (pass == 1 && !st->reorth) return;
     const int l = blockIdx.y;
     const int j = st->j;
     if (l > j) return;
@@ -648,76 +722,31 @@ __global__ void k_gm_dots(GmresArgs a, int pass)
         }
     }
     __syncthreads();
-    if (!last) return;
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    const double2 sum = warp_sum_array2(a.part + (int64_t)l * a.nblk, a.nblk);
     if (threadIdx.x == 0) {
-        __threadfence();
-        const volatile double2 *pp = a.part + (int64_t)l * a.nblk;
-        double sx = 0.0, sy = 0.0;
-        for (int b = 0; b < a.nblk; ++b) { sx += pp[b].x; sy += pp[b].y; }
-        a.hcol[l] = make_double2(sx, sy);
+        a.hcol[l] = sum;
         double2 &h = a.H[(int64_t)l * a.m + j];
-        if (pass == 0) h = make_double2(sx, sy);
-        else { h.x += sx; h.y += sy; }
+        if (pass == 0) h = sum;
+        else { h.x += sum.x; h.y += sum.y; }
         a.cnt[l] = 0;
     }
 }
 
-// w <- w - sum_{l<=j} hcol_l V_l.  In the last pass the blocks also leave
-// partial ||w||^2; the last block to finish then does the Givens step (FP64):
-// h_{j+1,j} = ||w||, apply the previous rotations to column j, form the new
-// rotation, update g and the residual estimate, and decide whether the cycle
-// ends.  The division of w by h_{j+1,j} happens in the next product's gather.
-__global__ void k_gm_update(GmresArgs a, int last_pass)
+// Givens step (FP64), run by one warp: h_{j+1,j} = ||w|| (nn = ||w||^2),
+// apply the previous rotations to column j, form the new rotation, update g
+// and the residual estimate, and decide whether the cycle ends.  The
+// division of w by h_{j+1,j} happens in the next product's gather.
+__device__ void gm_givens_warp(const GmresArgs &a, double nn, int j)
 {
-    GmresState *st = a.st;
-    if (st->done) return;
-    const int j = st->j;
-    __shared__ float2 hs[kMaxRestart + 1];
-    for (int l = threadIdx.x; l <= j; l += blockDim.x) hs[l] = make_float2((float)a.hcol[l].x, (float)a.hcol[l].y);
-    __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double nrm = 0.0;
-    if (i < a.n) {
-        float2 acc = a.w[i];
-        for (int l = 0; l <= j; ++l) {
-            const float2 v = a.V[(int64_t)l * a.n + i];
-            const float2 h = hs[l];
-            acc.x -= h.x * v.x - h.y * v.y;
-            acc.y -= h.x * v.y + h.y * v.x;
-        }
-        a.w[i] = acc;
-        nrm = (double)acc.x * acc.x + (double)acc.y * acc.y;
-    }
-    if (!last_pass) return;
-    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-    __shared__ double red[32];
-    __shared__ bool last;
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (threadIdx.x == 0) {
-            a.normpart[blockIdx.x] = v;
-            __threadfence();
-            last = atomicAdd(&a.cnt[a.m + 1], 1u) == (unsigned)(gridDim.x - 1);
-        }
-    }
-    __syncthreads();
-    if (!last || threadIdx.x >= 32) return;
-    // ---- Givens step, one warp of the last block
     __shared__ double2 sh[kMaxRestart + 1], scs[kMaxRestart], ssn[kMaxRestart];
-    __threadfence();
-    double nn = 0.0;
-    const volatile double *np = a.normpart;
-    if (threadIdx.x == 0)
-        for (int b = 0; b < (int)gridDim.x; ++b) nn += np[b];     // block order: deterministic
+    GmresState *st = a.st;
     const int m = a.m;
     for (int l = threadIdx.x; l <= j; l += 32) sh[l] = a.H[(int64_t)l * m + j];
     for (int l = threadIdx.x; l < j; l += 32) { scs[l] = a.cs[l]; ssn[l] = a.sn[l]; }
     __syncwarp();
     if (threadIdx.x == 0) {
-        a.cnt[m + 1] = 0;
         const double hn = sqrt(nn);
         sh[j + 1] = make_double2(hn, 0.0);
         for (int l = 0; l < j; ++l) {
@@ -758,24 +787,105 @@ __global__ void k_gm_update(GmresArgs a, int last_pass)
     for (int l = threadIdx.x; l <= j + 1; l += 32) a.H[(int64_t)l * m + j] = sh[l];
 }
 
+// w <- w - sum_{l<=j} hcol_l V_l for one Gram-Schmidt pass; the blocks leave
+// partial ||w||^2 and the last block to finish sums them in block order.
+// After pass 0 it decides whether a second pass is needed (the norm fell
+// below a tenth of its value before the pass: Daniel-Gragg-Kaufman-Stewart
+// reorthogonalisation test with eta = 0.1); if not, or after pass 1, it runs
+// the Givens step.  Pass 1 kernels return at once when no second pass is due.
+__global__ void k_gm_update(GmresArgs a, int pass)
+{
+    GmresState *st = a.st;
+    if (st->done) return;
+    if (pass == 1 && !st->reorth) return;
+    const int j = st->j;
+    __shared__ float2 hs[kMaxRestart + 1];
+    for (int l = threadIdx.x; l <= j; l += blockDim.x) hs[l] = make_float2((float)a.hcol[l].x, (float)a.hcol[l].y);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double nrm = 0.0;
+    if (i < a.n) {
+        float2 acc = a.w[i];
+        for (int l = 0; l <= j; ++l) {
+            const float2 v = a.V[(int64_t)l * a.n + i];
+            const float2 h = hs[l];
+            acc.x -= h.x * v.x - h.y * v.y;
+            acc.y -= h.x * v.y + h.y * v.x;
+        }
+        a.w[i] = acc;
+        nrm = (double)acc.x * acc.x + (double)acc.y * acc.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    __shared__ double red[32];
+    __shared__ bool last;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) {
+            a.normpart[blockIdx.x] = v;
+            __threadfence();
+            last = atomicAdd(&a.cnt[a.m + 1], 1u) == (unsigned)(gridDim.x - 1);
+        }
+    }
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    __shared__ double s_nn;
+    __shared__ int s_go;
+    const double nn_w = warp_sum_array(a.normpart, (int)gridDim.x);     // fixed order: deterministic
+    double hh_w = 0.0;
+    if (pass == 0) {
+        for (int l = threadIdx.x; l <= j; l += 32) hh_w += a.hcol[l].x * a.hcol[l].x + a.hcol[l].y * a.hcol[l].y;
+        for (int o = 16; o > 0; o >>= 1) hh_w += __shfl_xor_sync(0xffffffffu, hh_w, o);
+    }
+    if (threadIdx.x == 0) {
+        a.cnt[a.m + 1] = 0;
+        const double nn = nn_w;
+        s_nn = nn;
+        int go = 1;
+        if (pass == 0) {
+            const double hh = hh_w;
+            // ||w_after|| < eta ||w_before||, eta = 0.1, with
+            // ||w_before||^2 = ||w_after||^2 + sum |h_l|^2
+            const int need = nn * (1.0 - 0.01) < 0.01 * hh;
+            st->reorth = need;
+            st->n_reorth += need;
+            go = !need;
+        }
+        s_go = go;
+    }
+    __syncwarp();
+    if (s_go) gm_givens_warp(a, s_nn, j);
+}
+
 // Back substitution y = R^{-1} g over ncols columns (FP64), one warp:
 // column-oriented, each step divides one entry and the lanes update the rest.
+// The triangle is staged in shared memory when it fits (smem_cols columns).
 __global__ void k_gm_backsolve(const GmresState *st, const double2 *__restrict__ H, const double2 *__restrict__ g,
-                               double2 *__restrict__ y, int m)
+                               double2 *__restrict__ y, int m, int smem_cols)
 {
+    extern __shared__ double2 tri[];       // [nc][nc] when nc <= smem_cols
     __shared__ double2 sv[kMaxRestart + 1];
     const int nc = st->ncols;
     const int lane = threadIdx.x;
+    const bool in_smem = nc <= smem_cols;
     for (int l = lane; l < nc; l += 32) sv[l] = g[l];
+    if (in_smem)
+        for (int q = lane; q < nc * nc; q += 32) {
+            const int r = q / nc, c = q % nc;
+            tri[q] = H[(int64_t)r * m + c];
+        }
     __syncwarp();
     for (int l = nc - 1; l >= 0; --l) {
-        const double2 d = H[(int64_t)l * m + l];
+        const double2 d = in_smem ? tri[l * nc + l] : H[(int64_t)l * m + l];
         const double dd = d.x * d.x + d.y * d.y;
         const double2 sl = sv[l];
         const double2 yl = make_double2((sl.x * d.x + sl.y * d.y) / dd, (sl.y * d.x - sl.x * d.y) / dd);
         if (lane == 0) y[l] = yl;
         for (int r = lane; r < l; r += 32) {
-            const double2 h = H[(int64_t)r * m + l];
+            const double2 h = in_smem ? tri[r * nc + l] : H[(int64_t)r * m + l];
             sv[r].x -= h.x * yl.x - h.y * yl.y;
             sv[r].y -= h.x * yl.y + h.y * yl.x;
         }

@@ -40,6 +40,8 @@ struct NearArgs {
 struct GmresState {
     int j, done, converged, iters, ncols, maxit;
     double bnorm, beta, resid, tol, hn;
+    int reorth;              // second Gram-Schmidt pass needed for the current column
+    int n_reorth;            // columns that needed it
 };
 
 struct PrepArgs {
@@ -107,6 +109,8 @@ struct DisaggArgs {
     const int64_t *perm;     // optional
     float k;
     int nlev;
+    const int64_t *leaf_start;  // leaves (+1): element ranges
+    int sum_nd;              // sum of nd over the levels (shared-memory rows)
     FarArgs lev[kMaxFarLevels];
 };
 
@@ -154,7 +158,8 @@ struct GmresArgs {
 
 __global__ void k_gm_dots(GmresArgs a, int pass);
 __global__ void k_gm_update(GmresArgs a, int last_pass);
-__global__ void k_gm_backsolve(const GmresState *st, const double2 *H, const double2 *g, double2 *y, int m);
+__global__ void k_gm_backsolve(const GmresState *st, const double2 *H, const double2 *g, double2 *y, int m,
+                               int smem_cols);
 __global__ void k_gm_xupdate(float2 *x, const float2 *V, int64_t n, const GmresState *st, const double2 *y);
 __global__ void k_gm_start(GmresState *st, float2 *V, const float2 *r, int64_t n, const double *normpart, int nblk,
                            double2 *g, int m, int first);

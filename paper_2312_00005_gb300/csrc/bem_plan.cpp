@@ -375,12 +375,13 @@ void build_tree(const Geometry &g, double leaf_edge, Tree &t)
 // far test depends on the pair only through the box offset (distance,
 // Hankel growth) and the clusters' radii, so the offset-only parts are
 // cached in a dense table per depth.
-void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k, FreqPlan &fp)
+void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k, FreqPlan &fp, int leaf_depth)
 {
     fp = FreqPlan();
     fp.k = k;
     fp.direct = (p.mode == BEM_MODE_DIRECT);
-    const int D = t.leaf_depth;
+    const int D = (leaf_depth < 0 || leaf_depth > t.leaf_depth) ? t.leaf_depth : leaf_depth;
+    fp.leaf_depth = D;
     double R[kMaxRule + 1] = {0};
     order_thresholds(p.quad_tol, std::max(2, p.m_max), R);
     const double r1 = R[1] * (1.0 + 1e-9);

@@ -101,6 +101,7 @@ struct Verdict {
 struct FreqPlan {
     double k = 0.0;
     bool direct = false;
+    int leaf_depth = 0;                  // depth of the leaves these lists end at
     std::vector<Verdict> verdicts;       // every stability test the build evaluated
     std::vector<int> Ld;                 // expansion length per depth used by the build
     std::vector<FarLevel> far;           // used levels, coarse to fine
@@ -114,6 +115,9 @@ struct FreqPlan {
 void set_last_error(const std::string &msg);
 
 // Builds near and interaction lists (Sec. 3.3.4) for wavenumber k.
-void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k, FreqPlan &fp);
+// leaf_depth < 0: the tree's own leaf depth; otherwise any depth 0..leaf_depth
+// (clusters at every depth are runs of the same element order).
+void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k, FreqPlan &fp,
+                int leaf_depth = -1);
 
 }  // namespace bem
