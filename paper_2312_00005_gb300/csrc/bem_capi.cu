@@ -13,6 +13,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/bemfmm.h"
@@ -292,6 +293,10 @@ struct bem_mesh_impl {
     DevArr<double> ptsbuf;
     std::map<int, std::unique_ptr<DepthDev>> depth_dev;
     cudaStream_t s = nullptr;
+    // side stream for the far-field upward pass, which runs beside the
+    // near-field product (fork after k_prep, join before k_disaggregate)
+    cudaStream_t s_far = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<float> coef_key;
 
     ElemDev elem() const
@@ -304,6 +309,9 @@ struct bem_mesh_impl {
     }
     ~bem_mesh_impl()
     {
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (s_far) cudaStreamDestroy(s_far);
         if (s) cudaStreamDestroy(s);
     }
 };
@@ -841,6 +849,31 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
         k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, skip);
     }
     ck_launch("k_prep");
+    // The far-field upward pass (aggregation, transfer) depends only on
+    // k_prep and runs on the high-priority side stream beside the near-field
+    // product; k_disaggregate joins both.  With kernel timing on, everything
+    // stays on one stream so each kernel is timed alone.
+    const LevelsArgs &A = P.hargs;
+    const bool fork = !g_timing && (A.ntasks > 0 || A.ntargets > 0);
+    cudaStream_t sf = fork ? M.s_far : s;
+    if (fork) {
+        ck(cudaEventRecord(M.ev_fork, s), "record fork");
+        ck(cudaStreamWaitEvent(sf, M.ev_fork, 0), "wait fork");
+    }
+    if (A.ntasks > 0) {
+        {
+            KTimer kt_("k_aggregate", sf);
+            k_aggregate<<<A.ntasks, 128, 0, sf>>>(P.largs.p, M.alpha.p, M.beta.p, skip);
+        }
+        ck_launch("k_aggregate");
+    }
+    if (A.ntargets > 0) {
+        {
+            KTimer kt_("k_transfer", sf);
+            k_transfer<<<A.ntargets, 128, 0, sf>>>(P.largs.p, skip);
+        }
+        ck_launch("k_transfer");
+    }
     NearArgs na = near_args(M, P, cp, cq);
     if (use_store && M.prm.near_store && !P.fp().direct) {
         const size_t xs_bytes = (size_t)P.lists->max_ncol * sizeof(float2);
@@ -871,20 +904,9 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     da.perm = perm_out ? M.perm.p : nullptr;
     da.k = (float)P.k;
     da.nlev = (int)P.lev.size();
-    const LevelsArgs &A = P.hargs;
-    if (A.ntasks > 0) {
-        {
-            KTimer kt_("k_aggregate", s);
-            k_aggregate<<<A.ntasks, 128, 0, s>>>(P.largs.p, M.alpha.p, M.beta.p, skip);
-        }
-        ck_launch("k_aggregate");
-    }
-    if (A.ntargets > 0) {
-        {
-            KTimer kt_("k_transfer", s);
-            k_transfer<<<A.ntargets, 128, 0, s>>>(P.largs.p, skip);
-        }
-        ck_launch("k_transfer");
+    if (fork) {
+        ck(cudaEventRecord(M.ev_join, sf), "record join");
+        ck(cudaStreamWaitEvent(s, M.ev_join, 0), "wait join");
     }
     for (int l = 0; l < A.nlev; ++l) da.lev[l] = A.lev[l];
     da.leaf_start = P.lists->leaf_start.p;
@@ -918,9 +940,7 @@ void autotune_leaf_depth(bem_mesh_impl &M, double k)
     ck(cudaEventCreate(&e0), "event");
     ck(cudaEventCreate(&e1), "event");
     ck(cudaEventCreate(&e2), "event");
-    std::shared_ptr<Lists> best;
-    int best_d = M.leaf_depth;
-    double best_cost = 1e300;
+    std::vector<std::tuple<int, double, std::shared_ptr<Lists>>> cand;
     for (int d = M.leaf_depth - 1; d <= M.leaf_depth + 1; ++d) {
         if (d < 1 || d > M.t.leaf_depth) continue;
         bem_params gp = M.prm;
@@ -951,17 +971,30 @@ void autotune_leaf_depth(bem_mesh_impl &M, double k)
         ck(cudaEventElapsedTime(&ms_mv, e1, e2), "elapsed");
         const double cost = 1e-3 * (ms_store + 40.0 * ms_mv / 3.0);
         M.tune_log.push_back({d, cost});
-        if (cost < best_cost) {
-            best_cost = cost;
-            best = lists;
-            best_d = d;
-        }
+        cand.emplace_back(d, cost, lists);
         M.plan.reset();
         M.plan.swap(keep);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
+    // Another depth replaces the automatic one only when it is at least 5%
+    // faster, so that near ties do not flip between runs.
+    std::shared_ptr<Lists> best;
+    int best_d = M.leaf_depth;
+    double best_cost = 1e300, auto_cost = 1e300;
+    for (auto &c : cand)
+        if (std::get<0>(c) == M.leaf_depth) {
+            auto_cost = std::get<1>(c);
+            best = std::get<2>(c);
+            best_cost = 0.95 * auto_cost;
+        }
+    for (auto &c : cand)
+        if (std::get<0>(c) != M.leaf_depth && std::get<1>(c) < best_cost) {
+            best_cost = std::get<1>(c);
+            best_d = std::get<0>(c);
+            best = std::get<2>(c);
+        }
     if (best) {
         M.leaf_depth = best_d;
         M.geo_lists = best;
@@ -1138,6 +1171,13 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         M->tuned = !tune;
         ck(cudaGetDevice(&M->device), "cudaGetDevice");
         ck(cudaStreamCreateWithFlags(&M->s, cudaStreamNonBlocking), "stream");
+        {
+            int lo = 0, hi = 0;
+            ck(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
+            ck(cudaStreamCreateWithPriority(&M->s_far, cudaStreamNonBlocking, hi), "stream");
+            ck(cudaEventCreateWithFlags(&M->ev_fork, cudaEventDisableTiming), "event");
+            ck(cudaEventCreateWithFlags(&M->ev_join, cudaEventDisableTiming), "event");
+        }
         const int64_t n = n_tris;
         std::vector<float4> chi(n), clo(n), nr(n), va(n), e1(n), e2(n);
         std::vector<double> cd(3 * n), vad(3 * n), e1d(3 * n), e2d(3 * n), ad(n);
