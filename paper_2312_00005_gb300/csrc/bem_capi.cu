@@ -22,6 +22,9 @@
 
 using namespace bem;
 
+// Arnoldi steps captured in one CUDA graph (one status read per graph)
+constexpr int kStepsPerGraph = 4;
+
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_err;
 static std::atomic<uint64_t> g_launches{0};
@@ -278,7 +281,7 @@ struct bem_mesh_impl {
     DevArr<float2> V, w;
     DevArr<double2> H, cs, sn, g_, hcol, part, yv;
     DevArr<double> normpart;
-    DevArr<unsigned int> cnt;
+    DevArr<unsigned int> gbar;   // grid barrier of the fused Gram-Schmidt step
     DevArr<GmresState> st;
     std::unique_ptr<Plan> plan;
     std::shared_ptr<Lists> geo_lists;                  // frequency-independent lists
@@ -297,6 +300,9 @@ struct bem_mesh_impl {
     // near-field product (fork after k_prep, join before k_disaggregate)
     cudaStream_t s_far = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // side stream and events of the GMRES Givens steps inside one graph
+    cudaStream_t s_giv = nullptr;
+    cudaEvent_t ev_orth[kStepsPerGraph] = {}, ev_giv[kStepsPerGraph] = {};
     std::vector<float> coef_key;
 
     ElemDev elem() const
@@ -309,6 +315,11 @@ struct bem_mesh_impl {
     }
     ~bem_mesh_impl()
     {
+        for (int t = 0; t < kStepsPerGraph; ++t) {
+            if (ev_orth[t]) cudaEventDestroy(ev_orth[t]);
+            if (ev_giv[t]) cudaEventDestroy(ev_giv[t]);
+        }
+        if (s_giv) cudaStreamDestroy(s_giv);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
         if (s_far) cudaStreamDestroy(s_far);
@@ -821,34 +832,45 @@ void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
 // y = A x with the given column coefficients.  x: caller order when
 // perm_in, else internal (optionally x + (*jidx) n).  y: caller order when
 // perm_out.  use_store: use the stored near-field values.
-void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool use_store, const float2 *x,
-                     const int *jidx, bool perm_in, float2 *y, bool perm_out, const int *skip, cudaStream_t s,
-                     const float2 *gm_w = nullptr, float2 *gm_v = nullptr, const GmresState *gm_st = nullptr)
+PrepArgs prep_args(bem_mesh_impl &M, const float2 *cp, const float2 *cq, const float2 *x)
 {
-    Plan &P = *M.plan;
-    const int64_t n = M.n;
+    const bool far = !M.plan->lev.empty();
     PrepArgs pa;
-    pa.n = n;
+    pa.n = M.n;
     pa.x = x;
-    pa.jidx = jidx;
-    pa.perm = perm_in ? M.perm.p : nullptr;
+    pa.jidx = nullptr;
+    pa.perm = nullptr;
     pa.xint = M.xint.p;
-    const bool far = !P.lev.empty();
     pa.alpha = far ? M.alpha.p : nullptr;
     pa.beta = far ? M.beta.p : nullptr;
     pa.chi = M.chi.p;
     pa.nrm = M.nrm.p;
     pa.cp = cp;
     pa.cq = cq;
-    pa.k = (float)P.k;
-    pa.wsrc = gm_w;
-    pa.vdst = gm_v;
-    pa.st = gm_st;
-    {
-        KTimer kt_("k_prep", s);
-        k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, skip);
+    pa.k = (float)M.plan->k;
+    return pa;
+}
+
+// y = A x with the given column coefficients.  x: caller order when
+// perm_in, else internal (optionally x + (*jidx) n).  y: caller order when
+// perm_out.  use_store: use the stored near-field values.  prepared: the
+// product inputs (x_int, alpha, beta) are already formed and x is unused.
+void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool use_store, const float2 *x,
+                     const int *jidx, bool perm_in, float2 *y, bool perm_out, const int *skip, cudaStream_t s,
+                     bool prepared = false)
+{
+    Plan &P = *M.plan;
+    const int64_t n = M.n;
+    if (!prepared) {
+        PrepArgs pa = prep_args(M, cp, cq, x);
+        pa.jidx = jidx;
+        pa.perm = perm_in ? M.perm.p : nullptr;
+        {
+            KTimer kt_("k_prep", s);
+            k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, skip);
+        }
+        ck_launch("k_prep");
     }
-    ck_launch("k_prep");
     // The far-field upward pass (aggregation, transfer) depends only on
     // k_prep and runs on the high-priority side stream beside the near-field
     // product; k_disaggregate joins both.  With kernel timing on, everything
@@ -964,11 +986,18 @@ void autotune_leaf_depth(bem_mesh_impl &M, double k)
         float ms_store = 0.f, ms_mv = 0.f;
         ck(cudaEventElapsedTime(&ms_store, e0, e1), "elapsed");
         matvec_internal(M, tcp.p, tcq.p, true, tx.p, nullptr, false, ty.p, false, nullptr, M.s);   // warm-up
-        ck(cudaEventRecord(e1, M.s), "record");
-        for (int r = 0; r < 3; ++r) matvec_internal(M, tcp.p, tcq.p, true, tx.p, nullptr, false, ty.p, false, nullptr, M.s);
-        ck(cudaEventRecord(e2, M.s), "record");
-        ck(cudaEventSynchronize(e2), "sync");
-        ck(cudaEventElapsedTime(&ms_mv, e1, e2), "elapsed");
+        // the fastest of three rounds of three products
+        ms_mv = 1e30f;
+        for (int round = 0; round < 3; ++round) {
+            float ms = 0.f;
+            ck(cudaEventRecord(e1, M.s), "record");
+            for (int r = 0; r < 3; ++r)
+                matvec_internal(M, tcp.p, tcq.p, true, tx.p, nullptr, false, ty.p, false, nullptr, M.s);
+            ck(cudaEventRecord(e2, M.s), "record");
+            ck(cudaEventSynchronize(e2), "sync");
+            ck(cudaEventElapsedTime(&ms, e1, e2), "elapsed");
+            ms_mv = std::min(ms_mv, ms);
+        }
         const double cost = 1e-3 * (ms_store + 40.0 * ms_mv / 3.0);
         M.tune_log.push_back({d, cost});
         cand.emplace_back(d, cost, lists);
@@ -978,7 +1007,7 @@ void autotune_leaf_depth(bem_mesh_impl &M, double k)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
-    // Another depth replaces the automatic one only when it is at least 5%
+    // Another depth replaces the automatic one only when it is at least 3%
     // faster, so that near ties do not flip between runs.
     std::shared_ptr<Lists> best;
     int best_d = M.leaf_depth;
@@ -987,7 +1016,7 @@ void autotune_leaf_depth(bem_mesh_impl &M, double k)
         if (std::get<0>(c) == M.leaf_depth) {
             auto_cost = std::get<1>(c);
             best = std::get<2>(c);
-            best_cost = 0.95 * auto_cost;
+            best_cost = 0.97 * auto_cost;
         }
     for (auto &c : cand)
         if (std::get<0>(c) != M.leaf_depth && std::get<1>(c) < best_cost) {
@@ -1177,6 +1206,11 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
             ck(cudaStreamCreateWithPriority(&M->s_far, cudaStreamNonBlocking, hi), "stream");
             ck(cudaEventCreateWithFlags(&M->ev_fork, cudaEventDisableTiming), "event");
             ck(cudaEventCreateWithFlags(&M->ev_join, cudaEventDisableTiming), "event");
+            ck(cudaStreamCreateWithFlags(&M->s_giv, cudaStreamNonBlocking), "stream");
+            for (int t = 0; t < kStepsPerGraph; ++t) {
+                ck(cudaEventCreateWithFlags(&M->ev_orth[t], cudaEventDisableTiming), "event");
+                ck(cudaEventCreateWithFlags(&M->ev_giv[t], cudaEventDisableTiming), "event");
+            }
         }
         const int64_t n = n_tris;
         std::vector<float4> chi(n), clo(n), nr(n), va(n), e1(n), e2(n);
@@ -1341,11 +1375,28 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         M.g_.alloc(m + 1);
         M.hcol.alloc(m + 1);
         M.yv.alloc(m + 1);
-        const int nblk = (int)std::min<int64_t>(256, std::max<int64_t>(1, n / 1024));
+        // the fused Gram-Schmidt step: one cooperative launch, block b owns
+        // rows [b R, b R + R) with R <= kOrthoMaxRows; all blocks co-resident
+        int nblk = 0;
+        {
+            int per_sm = 0, nsm = 0;
+            ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gm_ortho, kOrthoThreads, 0), "occupancy");
+            ck(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, M.device), "attribute");
+            const int64_t cap = (int64_t)per_sm * nsm;
+            const int64_t want = std::max<int64_t>(1, (n + 63) / 64);
+            nblk = (int)std::min(cap, want);
+            if ((n + nblk - 1) / nblk > kOrthoMaxRows)
+                throw Fail{set_err(BEM_E_ARG, "GMRES: " + std::to_string(n) + " unknowns exceed the fused "
+                                                  "Gram-Schmidt step's limit of " +
+                                                  std::to_string(cap * kOrthoMaxRows))};
+        }
+        const int orows = (int)((n + nblk - 1) / nblk);
         M.part.alloc((size_t)(m + 1) * nblk);
-        const int nnorm = (int)nblocks(n, 128);
+        const int nnorm = (int)nblocks(n, 256);
         M.normpart.alloc(std::max(nnorm, nblk));
         M.st.alloc(1);
+        M.gbar.alloc(2);
+        ck(cudaMemsetAsync(M.gbar.p, 0, 2 * sizeof(unsigned int), s), "memset barrier");
         GmresState hs;
         memset(&hs, 0, sizeof hs);
         hs.tol = tol;
@@ -1353,6 +1404,16 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         ck(cudaMemcpyAsync(M.st.p, &hs, sizeof hs, cudaMemcpyHostToDevice, s), "H2D st");
         ck(cudaMemsetAsync(M.uvec.p, 0, n * sizeof(float2), s), "memset x");
         ck(cudaMemsetAsync(M.H.p, 0, M.H.bytes(), s), "memset H");
+        // the product inputs of v_0 (later basis vectors get theirs from
+        // k_gm_ortho)
+        auto prep_v0 = [&]() {
+            PrepArgs pa = prep_args(M, M.cp.p, M.cq.p, M.V.p);
+            {
+                KTimer kt_("k_prep", s);
+                k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, nullptr);
+            }
+            ck_launch("k_prep");
+        };
         // start: r0 = b
         {
             KTimer kt_("k_norm_part", s);
@@ -1364,14 +1425,13 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
             k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.bvec.p, n, M.normpart.p, nnorm, M.g_.p, m, 1);
         }
         ck_launch("k_gm_start");
+        prep_v0();
         // one Arnoldi step, captured once as a graph and replayed
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t gexec = nullptr;
-        int* jptr = &M.st.p->j;
         const int *done = &M.st.p->done;
-        M.cnt.alloc(m + 2);
-        ck(cudaMemsetAsync(M.cnt.p, 0, (m + 2) * sizeof(unsigned int), s), "memset cnt");
-        GmresArgs ga;
+        OrthoArgs oa;
+        GmresArgs &ga = oa.g;
         ga.V = M.V.p;
         ga.w = M.w.p;
         ga.n = n;
@@ -1384,57 +1444,92 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         ga.sn = M.sn.p;
         ga.g = M.g_.p;
         ga.normpart = M.normpart.p;
-        ga.nnorm = nnorm;
-        ga.cnt = M.cnt.p;
         ga.m = m;
-        // one Arnoldi step: product (the gather forms V_j = w / h_{j,j-1}),
-        // two classical Gram-Schmidt passes, Givens step
-        auto arnoldi_step = [&]() {
-            matvec_internal(M, M.cp.p, M.cq.p, true, M.V.p, jptr, false, M.w.p, false, done, s, M.w.p, M.V.p,
-                            M.st.p);
-            for (int pass = 0; pass < 2; ++pass) {
-                {
-                    KTimer kt_("k_gm_dots", s);
-                    k_gm_dots<<<dim3(nblk, m + 1), 128, 0, s>>>(ga, pass);
-                }
-                ck_launch("k_gm_dots");
-                {
-                    KTimer kt_("k_gm_update", s);
-                    k_gm_update<<<nnorm, 128, 0, s>>>(ga, pass);
-                }
-                ck_launch("k_gm_update");
-            }
-        };
+        oa.next = prep_args(M, M.cp.p, M.cq.p, nullptr);
+        oa.bar = M.gbar.p;
+        oa.err = &M.st.p->fault;
+        oa.rows = orows;
+        // one Arnoldi step: product of v_j (inputs already formed), then the
+        // fused Gram-Schmidt / Givens step, which also forms v_{j+1}
         const bool use_graph = !g_timing;
-        uint64_t per_step = 0;
+        // Arnoldi steps per graph (and per status read).  With event timing
+        // on, one step per read and every kernel on one stream, so that each
+        // kernel is timed alone and no timed launch is a skipped one.
+        const int batch = use_graph ? kStepsPerGraph : 1;
+        auto ortho = [&]() {
+            KTimer kt_("k_gm_ortho", s);
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(nblk);
+            cfg.blockDim = dim3(kOrthoThreads);
+            cfg.dynamicSmemBytes = 0;
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            ck(cudaLaunchKernelEx(&cfg, k_gm_ortho, oa), "k_gm_ortho");
+            g_launches.fetch_add(1);
+        };
+        auto givens = [&](cudaStream_t gs) {
+            {
+                KTimer kt_("k_gm_givens", gs);
+                k_gm_givens<<<1, 32, 0, gs>>>(ga);
+            }
+            ck_launch("k_gm_givens");
+        };
+        // nsteps Arnoldi steps: product of v_j (inputs already formed), the
+        // fused Gram-Schmidt step (which also forms v_{j+1}'s inputs), then
+        // the Givens step.  In the graph the Givens step of step t runs on a
+        // side stream beside the product of step t + 1, which does not need
+        // it; step t + 1's Gram-Schmidt waits for it.
+        auto arnoldi_steps = [&](int nsteps) {
+            const bool side = use_graph;
+            for (int t = 0; t < nsteps; ++t) {
+                matvec_internal(M, M.cp.p, M.cq.p, true, nullptr, nullptr, false, M.w.p, false, done, s, true);
+                if (side && t > 0) ck(cudaStreamWaitEvent(s, M.ev_giv[t - 1], 0), "wait givens");
+                ortho();
+                if (side) {
+                    ck(cudaEventRecord(M.ev_orth[t], s), "record ortho");
+                    ck(cudaStreamWaitEvent(M.s_giv, M.ev_orth[t], 0), "wait ortho");
+                    givens(M.s_giv);
+                    ck(cudaEventRecord(M.ev_giv[t], M.s_giv), "record givens");
+                } else {
+                    givens(s);
+                }
+            }
+            if (side) ck(cudaStreamWaitEvent(s, M.ev_giv[nsteps - 1], 0), "join givens");
+        };
+        uint64_t per_graph = 0;
         if (use_graph) {
             const uint64_t before = g_launches.load();
             ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
-            arnoldi_step();
+            arnoldi_steps(batch);
             ck(cudaStreamEndCapture(s, &graph), "end capture");
-            per_step = g_launches.load() - before;
-            g_launches.fetch_sub(per_step);   // captured, not launched
+            per_graph = g_launches.load() - before;
+            g_launches.fetch_sub(per_graph);   // captured, not launched
             ck(cudaGraphInstantiate(&gexec, graph, 0), "instantiate");
         }
         int restarts = 0, total_iters = 0;
         bool converged = false;
         GmresState h;
-        // with event timing on, one step per status read so that no timed
-        // launch is a skipped one
-        const int batch = use_graph ? 4 : 1;
         for (;;) {
             // Arnoldi cycle
             for (int guard = 0; guard < m + batch; guard += batch) {
-                for (int b = 0; b < batch; ++b) {
-                    if (use_graph) {
-                        ck(cudaGraphLaunch(gexec, s), "graph launch");
-                        g_launches.fetch_add(per_step);
-                    } else {
-                        arnoldi_step();
-                    }
+                if (use_graph) {
+                    ck(cudaGraphLaunch(gexec, s), "graph launch");
+                    g_launches.fetch_add(per_graph);
+                } else {
+                    arnoldi_steps(1);
                 }
                 ck(cudaMemcpyAsync(&h, M.st.p, sizeof h, cudaMemcpyDeviceToHost, s), "D2H st");
                 ck(cudaStreamSynchronize(s), "sync");
+                if (h.fault) {
+                    if (gexec) cudaGraphExecDestroy(gexec);
+                    if (graph) cudaGraphDestroy(graph);
+                    throw Fail{set_err(BEM_E_TIMEOUT, "GMRES: a grid barrier wait of the fused Gram-Schmidt "
+                                                      "step gave up")};
+                }
                 if (h.done) break;
             }
             {
@@ -1466,6 +1561,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
                 k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.w.p, n, M.normpart.p, nnorm, M.g_.p, m, 0);
             }
             ck_launch("k_gm_start");
+            prep_v0();
             ck(cudaMemsetAsync(M.H.p, 0, M.H.bytes(), s), "memset H");
             ck(cudaMemcpyAsync(&h, M.st.p, sizeof h, cudaMemcpyDeviceToHost, s), "D2H st");
             ck(cudaStreamSynchronize(s), "sync");

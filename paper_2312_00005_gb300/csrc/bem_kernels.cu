@@ -269,25 +269,8 @@ __global__ void k_near_fused(NearArgs a, const float2 *__restrict__ x, float2 *_
 // x = xbase + jidx * n) and form the aggregation weights of the centroid
 // rule, alpha_i = A_i cq_i x_i and beta_i = ik A_i cp_i x_i n_i, so that the
 // column factor of Sec. 3.3.1 is alpha_i + beta_i . s.
-__global__ void k_prep(PrepArgs a, const int *skip)
+__device__ __forceinline__ void prep_store(const PrepArgs &a, int64_t i, float2 xv)
 {
-    if (skip_now(skip)) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const float2 *xb = a.x;
-    float2 xv;
-    if (a.wsrc) {
-        const int j = *a.jidx;
-        if (j > 0) {
-            xv = cscale(a.wsrc[i], (float)(1.0 / a.st->hn));
-            a.vdst[(int64_t)j * a.n + i] = xv;
-        } else {
-            xv = a.x[i];
-        }
-    } else {
-        if (a.jidx) xb += (int64_t)(*a.jidx) * a.n;
-        xv = a.perm ? xb[a.perm[i]] : xb[i];
-    }
     a.xint[i] = xv;
     if (a.alpha) {
         const float A = a.chi[i].w;
@@ -301,6 +284,15 @@ __global__ void k_prep(PrepArgs a, const int *skip)
         a.beta[3 * i + 1] = cscale(b, nn.y);
         a.beta[3 * i + 2] = cscale(b, nn.z);
     }
+}
+__global__ void k_prep(PrepArgs a, const int *skip)
+{
+    if (skip_now(skip)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const float2 *xb = a.x;
+    if (a.jidx) xb += (int64_t)(*a.jidx) * a.n;
+    prep_store(a, i, a.perm ? xb[a.perm[i]] : xb[i]);
 }
 
 // Aggregation (Sec. 3.3.3, matrix T(l) with the centroid rule): for every
@@ -675,101 +667,77 @@ __global__ void k_pq(const float2 *__restrict__ u, const float2 *__restrict__ z,
     if (q) q[perm[i]] = qv;
 }
 
-// ------------------------------------------------------------------ GMRES
-// Dot products h_l = sum_i conj(V_l[i]) w[i], l <= j, for one CGS pass:
-// FP32 products summed per thread, FP64 across threads and blocks.  The last
-// block of row l to finish sums the row's partials in block order (so the
-// result does not depend on scheduling) and sets (pass 0) or adds to
-// (pass 1) H[l][j].
-__global__ void k_gm_dots(GmresArgs a, int pass)
-{
-    const GmresState *st = a.st;
-    if (st->done) return;
-    if (pass == 1 && !st->reorth) return;
-    const int l = blockIdx.y;
-    const int j = st->j;
-    if (l > j) return;
-    const float2 *vl = a.V + (int64_t)l * a.n;
-    const float2 *w = a.w;
-    double2 acc = make_double2(0.0, 0.0);
-    const int64_t chunk = (a.n + a.nblk - 1) / a.nblk;
-    const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(a.n, b0 + chunk);
-    for (int64_t i0 = b0 + threadIdx.x; i0 < b1; i0 += 8 * (int64_t)blockDim.x) {
-        float2 sacc = make_float2(0.f, 0.f);
-        for (int u = 0; u < 8; ++u) {
-            const int64_t i = i0 + (int64_t)u * blockDim.x;
-            if (i < b1) {
-                const float2 x = vl[i], y = w[i];
-                sacc.x = fmaf(x.x, y.x, fmaf(x.y, y.y, sacc.x));
-                sacc.y = fmaf(x.x, y.y, fmaf(-x.y, y.x, sacc.y));
-            }
-        }
-        acc.x += sacc.x;
-        acc.y += sacc.y;
-    }
-    acc = warp_sum_d(acc);
-    __shared__ double2 red[32];
-    __shared__ bool last;
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double2 v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : make_double2(0.0, 0.0);
-        v = warp_sum_d(v);
-        if (threadIdx.x == 0) {
-            a.part[(int64_t)l * a.nblk + blockIdx.x] = v;
-            __threadfence();
-            last = atomicAdd(&a.cnt[l], 1u) == (unsigned)(a.nblk - 1);
-        }
-    }
-    __syncthreads();
-    if (!last || threadIdx.x >= 32) return;
-    __threadfence();
-    const double2 sum = warp_sum_array2(a.part + (int64_t)l * a.nblk, a.nblk);
-    if (threadIdx.x == 0) {
-        a.hcol[l] = sum;
-        double2 &h = a.H[(int64_t)l * a.m + j];
-        if (pass == 0) h = sum;
-        else { h.x += sum.x; h.y += sum.y; }
-        a.cnt[l] = 0;
-    }
-}
 
+// ------------------------------------------------------------------ GMRES
 // Givens step (FP64), run by one warp: h_{j+1,j} = ||w|| (nn = ||w||^2),
 // apply the previous rotations to column j, form the new rotation, update g
-// and the residual estimate, and decide whether the cycle ends.  The
-// division of w by h_{j+1,j} happens in the next product's gather.
+// and the residual estimate, and decide whether the cycle ends.
+//
+// Rotation l maps (t_l, h_{l+1}) to (conj(c_l) t_l + s_l h_{l+1},
+// -s_l t_l + c_l h_{l+1}) with s_l real, so the running entry obeys the affine
+// recurrence t_{l+1} = a_l t_l + b_l, a_l = -s_l, b_l = c_l h_{l+1}.  The warp
+// composes these maps with a prefix scan (|a_l| <= 1: no growth) instead of
+// applying j rotations one after another in one thread: FP64 issue is scarce
+// on this part, and the serial chain costs j times its latency.
 __device__ void gm_givens_warp(const GmresArgs &a, double nn, int j)
 {
-    __shared__ double2 sh[kMaxRestart + 1], scs[kMaxRestart], ssn[kMaxRestart];
+    __shared__ double2 sh[kMaxRestart + 1], shr[kMaxRestart + 1];
+    __shared__ double2 s_tj;
     GmresState *st = a.st;
     const int m = a.m;
-    for (int l = threadIdx.x; l <= j; l += 32) sh[l] = a.H[(int64_t)l * m + j];
-    for (int l = threadIdx.x; l < j; l += 32) { scs[l] = a.cs[l]; ssn[l] = a.sn[l]; }
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    for (int l = lane; l <= j; l += 32) sh[l] = __ldcg(a.H + (int64_t)l * m + j);
     __syncwarp();
-    if (threadIdx.x == 0) {
-        const double hn = sqrt(nn);
-        sh[j + 1] = make_double2(hn, 0.0);
-        for (int l = 0; l < j; ++l) {
-            const double2 h0 = sh[l], h1 = sh[l + 1];
-            const double2 c = scs[l], s = ssn[l];
-            // [conj(c) conj(s); -s c] [h0; h1]
-            sh[l] = make_double2(c.x * h0.x + c.y * h0.y + s.x * h1.x + s.y * h1.y,
-                                 c.x * h0.y - c.y * h0.x + s.x * h1.y - s.y * h1.x);
-            sh[l + 1] = make_double2(-(s.x * h0.x - s.y * h0.y) + c.x * h1.x - c.y * h1.y,
-                                     -(s.x * h0.y + s.y * h0.x) + c.x * h1.y + c.y * h1.x);
+    const int K = (j + 31) / 32;                 // rotations per lane
+    const int l0 = min(j, lane * K), l1 = min(j, l0 + K);
+    double A = 1.0;
+    double2 B = make_double2(0.0, 0.0);
+    for (int l = l0; l < l1; ++l) {
+        const double2 c = __ldcg(a.cs + l);
+        const double sl = __ldcg(&a.sn[l].x);
+        const double2 h1 = sh[l + 1];
+        const double bx = c.x * h1.x - c.y * h1.y, by = c.x * h1.y + c.y * h1.x;
+        A = -sl * A;
+        B = make_double2(fma(-sl, B.x, bx), fma(-sl, B.y, by));
+    }
+    // inclusive scan: mine o (lane - o)'s
+    for (int o = 1; o < 32; o <<= 1) {
+        const double Ap = __shfl_up_sync(full, A, o);
+        const double Bx = __shfl_up_sync(full, B.x, o), By = __shfl_up_sync(full, B.y, o);
+        if (lane >= o) {
+            B = make_double2(fma(A, Bx, B.x), fma(A, By, B.y));
+            A *= Ap;
         }
-        const double2 h0 = sh[j];
-        const double den = sqrt(h0.x * h0.x + h0.y * h0.y + hn * hn);
-        double2 c, s;
-        if (den == 0.0) { c = make_double2(1.0, 0.0); s = make_double2(0.0, 0.0); }
-        else { c = make_double2(h0.x / den, h0.y / den); s = make_double2(hn / den, 0.0); }
+    }
+    double Ae = __shfl_up_sync(full, A, 1);
+    double Bex = __shfl_up_sync(full, B.x, 1), Bey = __shfl_up_sync(full, B.y, 1);
+    if (lane == 0) { Ae = 1.0; Bex = 0.0; Bey = 0.0; }
+    const double2 h0 = sh[0];
+    double2 t = make_double2(fma(Ae, h0.x, Bex), fma(Ae, h0.y, Bey));
+    for (int l = l0; l < l1; ++l) {
+        const double2 c = __ldcg(a.cs + l);
+        const double sl = __ldcg(&a.sn[l].x);
+        const double2 h1 = sh[l + 1];
+        shr[l] = make_double2(c.x * t.x + c.y * t.y + sl * h1.x, c.x * t.y - c.y * t.x + sl * h1.y);
+        t = make_double2(-sl * t.x + c.x * h1.x - c.y * h1.y, -sl * t.y + c.x * h1.y + c.y * h1.x);
+    }
+    if ((j == 0 && lane == 0) || (l0 < l1 && l1 == j)) s_tj = t;
+    __syncwarp();
+    if (lane == 0) {
+        const double hn = sqrt(nn);
+        const double2 hj = s_tj;
+        const double den = sqrt(hj.x * hj.x + hj.y * hj.y + hn * hn);
+        double2 c, sv;
+        if (den == 0.0) { c = make_double2(1.0, 0.0); sv = make_double2(0.0, 0.0); }
+        else { c = make_double2(hj.x / den, hj.y / den); sv = make_double2(hn / den, 0.0); }
         a.cs[j] = c;
-        a.sn[j] = s;
-        sh[j] = make_double2(den, 0.0);
-        sh[j + 1] = make_double2(0.0, 0.0);
+        a.sn[j] = sv;
+        shr[j] = make_double2(den, 0.0);
+        shr[j + 1] = make_double2(0.0, 0.0);
         const double2 g0 = a.g[j];
         a.g[j] = make_double2(c.x * g0.x + c.y * g0.y, c.x * g0.y - c.y * g0.x);
-        const double2 g1 = make_double2(-(s.x * g0.x - s.y * g0.y), -(s.x * g0.y + s.y * g0.x));
+        const double2 g1 = make_double2(-(sv.x * g0.x - sv.y * g0.y), -(sv.x * g0.y + sv.y * g0.x));
         a.g[j + 1] = g1;
         const double res = sqrt(g1.x * g1.x + g1.y * g1.y) / st->bnorm;
         st->resid = res;
@@ -784,80 +752,250 @@ __device__ void gm_givens_warp(const GmresArgs &a, double nn, int j)
         }
     }
     __syncwarp();
-    for (int l = threadIdx.x; l <= j + 1; l += 32) a.H[(int64_t)l * m + j] = sh[l];
+    for (int l = lane; l <= j + 1; l += 32) a.H[(int64_t)l * m + j] = shr[l];
 }
 
-// w <- w - sum_{l<=j} hcol_l V_l for one Gram-Schmidt pass; the blocks leave
-// partial ||w||^2 and the last block to finish sums them in block order.
-// After pass 0 it decides whether a second pass is needed (the norm fell
-// below a tenth of its value before the pass: Daniel-Gragg-Kaufman-Stewart
-// reorthogonalisation test with eta = 0.1); if not, or after pass 1, it runs
-// the Givens step.  Pass 1 kernels return at once when no second pass is due.
-__global__ void k_gm_update(GmresArgs a, int pass)
+// Grid barrier of a cooperative launch.  Thread 0 of each block arrives on
+// bar[0]; the last arrival resets it and advances the generation bar[1].
+// A wait gives up after kSpinLimit polls and sets *err, so a lost block can
+// never hang the GPU (the host reports the error).
+constexpr unsigned int kSpinLimit = 1u << 23;
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
 {
-    GmresState *st = a.st;
-    if (st->done) return;
-    if (pass == 1 && !st->reorth) return;
-    const int j = st->j;
-    __shared__ float2 hs[kMaxRestart + 1];
-    for (int l = threadIdx.x; l <= j; l += blockDim.x) hs[l] = make_float2((float)a.hcol[l].x, (float)a.hcol[l].y);
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void grid_barrier(unsigned int *bar, int *err)
+{
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double nrm = 0.0;
-    if (i < a.n) {
-        float2 acc = a.w[i];
-        for (int l = 0; l <= j; ++l) {
-            const float2 v = a.V[(int64_t)l * a.n + i];
-            const float2 h = hs[l];
-            acc.x -= h.x * v.x - h.y * v.y;
-            acc.y -= h.x * v.y + h.y * v.x;
-        }
-        a.w[i] = acc;
-        nrm = (double)acc.x * acc.x + (double)acc.y * acc.y;
-    }
-    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-    __shared__ double red[32];
-    __shared__ bool last;
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (threadIdx.x == 0) {
-            a.normpart[blockIdx.x] = v;
-            __threadfence();
-            last = atomicAdd(&a.cnt[a.m + 1], 1u) == (unsigned)(gridDim.x - 1);
-        }
-    }
-    __syncthreads();
-    if (!last || threadIdx.x >= 32) return;
-    __threadfence();
-    __shared__ double s_nn;
-    __shared__ int s_go;
-    const double nn_w = warp_sum_array(a.normpart, (int)gridDim.x);     // fixed order: deterministic
-    double hh_w = 0.0;
-    if (pass == 0) {
-        for (int l = threadIdx.x; l <= j; l += 32) hh_w += a.hcol[l].x * a.hcol[l].x + a.hcol[l].y * a.hcol[l].y;
-        for (int o = 16; o > 0; o >>= 1) hh_w += __shfl_xor_sync(0xffffffffu, hh_w, o);
-    }
     if (threadIdx.x == 0) {
-        a.cnt[a.m + 1] = 0;
-        const double nn = nn_w;
-        s_nn = nn;
-        int go = 1;
-        if (pass == 0) {
-            const double hh = hh_w;
-            // ||w_after|| < eta ||w_before||, eta = 0.1, with
-            // ||w_before||^2 = ||w_after||^2 + sum |h_l|^2
-            const int need = nn * (1.0 - 0.01) < 0.01 * hh;
+        const unsigned int g0 = ld_acquire_gpu(bar + 1);
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            // polls are plain acquire loads (served by L2 without
+            // serialising behind the arrivals, unlike atomics)
+            unsigned int it = 0;
+            while (ld_acquire_gpu(bar + 1) == g0) {
+                if (++it > kSpinLimit || *(volatile int *)err) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(20);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Compensated FP32 ("float-float") sums: s + e holds the running sum to
+// about 2^-44 relative.  The reductions below are issued by every block in
+// a fixed order, so all blocks derive identical values without FP64, whose
+// issue rate and latency on this part would dominate the step.
+struct FF {
+    float2 hi, lo;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void ff_add1(float &hi, float &lo, float xh, float xl)
+{
+    float s, e;
+    two_sum(hi, xh, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, xl));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+__device__ __forceinline__ void ff_add(FF &a, const FF &b)
+{
+    ff_add1(a.hi.x, a.lo.x, b.hi.x, b.lo.x);
+    ff_add1(a.hi.y, a.lo.y, b.hi.y, b.lo.y);
+}
+// sum of p[0..n) (float2) by one warp: lane order, then a fixed xor tree
+__device__ __forceinline__ FF warp_sum_ff(const volatile float2 *p, int n)
+{
+    FF v = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    for (int q = threadIdx.x & 31; q < n; q += 32) {
+        const FF x = {make_float2(p[q].x, p[q].y), make_float2(0.f, 0.f)};
+        ff_add(v, x);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        FF x;
+        x.hi.x = __shfl_xor_sync(0xffffffffu, v.hi.x, o);
+        x.hi.y = __shfl_xor_sync(0xffffffffu, v.hi.y, o);
+        x.lo.x = __shfl_xor_sync(0xffffffffu, v.lo.x, o);
+        x.lo.y = __shfl_xor_sync(0xffffffffu, v.lo.y, o);
+        // both partners add in the same operand order: identical results
+        if ((threadIdx.x & o) == 0) ff_add(v, x);
+        else { ff_add(x, v); v = x; }
+    }
+    return v;
+}
+
+// Classical Gram-Schmidt with selective reorthogonalisation (second pass
+// when ||w_after|| < 0.1 ||w_before||), then the next basis vector
+// v_{j+1} = w / ||w|| with its product inputs; the Givens step follows in
+// k_gm_givens.  Block b owns rows [b R, b R + R) of every vector: FP32
+// within a block, compensated FP32 across blocks, every reduction in a
+// fixed order, so all blocks derive identical values.
+__global__ void __launch_bounds__(kOrthoThreads) k_gm_ortho(OrthoArgs a)
+{
+    const GmresArgs &g = a.g;
+    GmresState *st = g.st;
+    if (*(volatile int *)&st->done || *(volatile int *)a.err) return;
+    const int j = *(volatile int *)&st->j;
+    const int G = gridDim.x, b = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = kOrthoThreads / 32;
+    constexpr int kRowsPerPass = 128, kCg = kOrthoThreads / kRowsPerPass;
+    const int64_t r0 = (int64_t)b * a.rows;
+    const int64_t rem = g.n - r0;
+    const int R = rem <= 0 ? 0 : (int)(rem < a.rows ? rem : (int64_t)a.rows);
+    float2 *part = (float2 *)g.part;              // [m + 1][G]
+    float2 *npart = (float2 *)g.normpart;         // [G] (x: ||w||^2 partial)
+    __shared__ float2 ws[kOrthoMaxRows];
+    __shared__ float2 hs[kMaxRestart + 1];
+    __shared__ float2 cpart[kOrthoThreads];
+    __shared__ float red[kOrthoThreads / 32];
+    __shared__ float s_hh;
+    __shared__ double s_nn;
+    for (int i = threadIdx.x; i < R; i += kOrthoThreads) ws[i] = g.w[r0 + i];
+    __syncthreads();
+    double nn = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        // dots: warp handles columns l0 .. l0 + 7, lanes stride the rows
+        for (int l0 = warp * 8; l0 <= j; l0 += nwarp * 8) {
+            float2 acc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.f, 0.f);
+            for (int i = lane; i < R; i += 32) {
+                const float2 y = ws[i];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (l0 + u <= j) {
+                        const float2 x = __ldcg(g.V + (int64_t)(l0 + u) * g.n + r0 + i);
+                        acc[u].x = fmaf(x.x, y.x, fmaf(x.y, y.y, acc[u].x));
+                        acc[u].y = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc[u].y));
+                    }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float2 d = warp_sum(acc[u]);
+                if (lane == 0 && l0 + u <= j) part[(int64_t)(l0 + u) * G + b] = d;
+            }
+        }
+        grid_barrier(a.bar, a.err);
+        // block b reduces columns b, b + G, ... (<= j)
+        if (warp == 0)
+            for (int l = b; l <= j; l += G) {
+                const FF sum = warp_sum_ff(part + (int64_t)l * G, G);
+                if (lane == 0) {
+                    const double2 h = make_double2((double)sum.hi.x + (double)sum.lo.x,
+                                                   (double)sum.hi.y + (double)sum.lo.y);
+                    g.hcol[l] = h;
+                    double2 *hp = g.H + (int64_t)l * g.m + j;
+                    if (pass == 0) *hp = h;
+                    else { const double2 h0 = __ldcg(hp); *hp = make_double2(h0.x + h.x, h0.y + h.y); }
+                }
+            }
+        grid_barrier(a.bar, a.err);
+        for (int l = threadIdx.x; l <= j; l += kOrthoThreads) {
+            const double2 h = __ldcg(g.hcol + l);
+            hs[l] = make_float2((float)h.x, (float)h.y);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            float hh = 0.f;
+            for (int l = lane; l <= j; l += 32) hh = fmaf(hs[l].x, hs[l].x, fmaf(hs[l].y, hs[l].y, hh));
+            for (int o = 16; o > 0; o >>= 1) hh += __shfl_xor_sync(0xffffffffu, hh, o);
+            if (lane == 0) s_hh = hh;
+        }
+        // update: w_i -= sum_l h_l v_l[i]; kCg column groups per row
+        float nrm = 0.f;
+        {
+            const int cg = threadIdx.x / kRowsPerPass, rr = threadIdx.x % kRowsPerPass;
+            for (int i0 = 0; i0 < R; i0 += kRowsPerPass) {
+                const int i = i0 + rr;
+                float2 acc = make_float2(0.f, 0.f);
+                if (i < R) {
+                    const float2 *vp = g.V + r0 + i;
+#pragma unroll 8
+                    for (int l = cg; l <= j; l += kCg) {
+                        const float2 v = __ldcg(vp + (int64_t)l * g.n);
+                        const float2 h = hs[l];
+                        acc.x = fmaf(h.x, v.x, fmaf(-h.y, v.y, acc.x));
+                        acc.y = fmaf(h.x, v.y, fmaf(h.y, v.x, acc.y));
+                    }
+                }
+                cpart[threadIdx.x] = acc;
+                __syncthreads();
+                if (cg == 0 && i < R) {
+                    float2 c = cpart[rr];
+#pragma unroll
+                    for (int q = 1; q < kCg; ++q) {
+                        c.x += cpart[rr + q * kRowsPerPass].x;
+                        c.y += cpart[rr + q * kRowsPerPass].y;
+                    }
+                    float2 wv = ws[i];
+                    wv.x -= c.x;
+                    wv.y -= c.y;
+                    ws[i] = wv;
+                    g.w[r0 + i] = wv;
+                    nrm = fmaf(wv.x, wv.x, fmaf(wv.y, wv.y, nrm));
+                }
+                __syncthreads();
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        if (lane == 0) red[warp] = nrm;
+        __syncthreads();
+        if (warp == 0) {
+            float v = lane < nwarp ? red[lane] : 0.f;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) npart[b] = make_float2(v, 0.f);
+        }
+        grid_barrier(a.bar, a.err);
+        if (warp == 0) {
+            const FF v = warp_sum_ff(npart, G);
+            if (lane == 0) s_nn = (double)v.hi.x + (double)v.lo.x;
+        }
+        __syncthreads();
+        nn = s_nn;
+        if (pass == 1) break;
+        // ||w_before||^2 = ||w_after||^2 + sum |h_l|^2; second pass when
+        // ||w_after|| < 0.1 ||w_before||
+        const bool need = (float)nn * 0.99f < 0.01f * s_hh;
+        if (b == 0 && threadIdx.x == 0) {
             st->reorth = need;
             st->n_reorth += need;
-            go = !need;
         }
-        s_go = go;
+        if (!need) break;
     }
-    __syncwarp();
-    if (s_go) gm_givens_warp(a, s_nn, j);
+    if (b == 0 && threadIdx.x == 0) st->nn = nn;
+    // next basis vector and the product inputs (unused when the cycle ends)
+    const float nf = (float)nn;
+    const float sc = nf > 0.f ? 1.f / sqrtf(nf) : 0.f;
+    float2 *vn = g.V + (int64_t)(j + 1) * g.n;
+    for (int i = threadIdx.x; i < R; i += kOrthoThreads) {
+        const float2 xv = cscale(ws[i], sc);
+        vn[r0 + i] = xv;
+        prep_store(a.next, r0 + i, xv);
+    }
+}
+
+// Givens step of the column k_gm_ortho just formed (one warp).
+__global__ void k_gm_givens(GmresArgs a)
+{
+    GmresState *st = a.st;
+    if (*(volatile int *)&st->done || st->fault) return;
+    gm_givens_warp(a, st->nn, st->j);
 }
 
 // Back substitution y = R^{-1} g over ncols columns (FP64), one warp:

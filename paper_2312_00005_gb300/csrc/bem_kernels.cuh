@@ -42,6 +42,8 @@ struct GmresState {
     double bnorm, beta, resid, tol, hn;
     int reorth;              // second Gram-Schmidt pass needed for the current column
     int n_reorth;            // columns that needed it
+    int fault;               // a grid barrier wait gave up (never reset by a restart)
+    double nn;               // ||w||^2 after orthogonalisation (k_gm_ortho -> k_gm_givens)
 };
 
 struct PrepArgs {
@@ -54,11 +56,6 @@ struct PrepArgs {
     const float4 *chi, *nrm;
     const float2 *cp, *cq;
     float k;
-    // GMRES mode (x = V, jidx set): for j > 0 the new basis vector is
-    // w / h_{j,j-1} (st->hn); it is formed here and stored to V_j.
-    const float2 *wsrc;
-    float2 *vdst;
-    const GmresState *st;
 };
 
 // Aggregation work item: `ne` elements from e0 of cluster c, written to row
@@ -150,14 +147,26 @@ struct GmresArgs {
     double2 *part;           // [m + 1][nblk] dot partials
     int nblk;
     double2 *H, *hcol, *cs, *sn, *g;
-    double *normpart;        // [nnorm] norm partials
-    int nnorm;
-    unsigned int *cnt;       // [m + 2] arrival counters (zero between uses)
+    double *normpart;        // [nblk] norm partials
     int m;
 };
 
-__global__ void k_gm_dots(GmresArgs a, int pass);
-__global__ void k_gm_update(GmresArgs a, int last_pass);
+// One Gram-Schmidt step of the Arnoldi process in a single cooperative
+// launch (all blocks co-resident): dots, update, norm and the next
+// product's inputs, separated by grid barriers whose waits give up after a
+// bounded number of polls (err = 1).  k_gm_givens then takes the Givens
+// step.  Partials are stored as float2 inside the part / normpart buffers.
+struct OrthoArgs {
+    GmresArgs g;             // g.nblk = gridDim.x; g.part [m + 1][nblk], g.normpart [nblk]
+    PrepArgs next;           // inputs of the next product, formed from V_{j+1}
+    unsigned int *bar;       // [2] grid barrier: arrivals, generation (zero at the first launch)
+    int *err;                // &st->fault
+    int rows;                // rows of the basis per block
+};
+constexpr int kOrthoThreads = 256;
+constexpr int kOrthoMaxRows = 1024;    // rows per block staged in shared memory
+__global__ void k_gm_ortho(OrthoArgs a);
+__global__ void k_gm_givens(GmresArgs a);
 __global__ void k_gm_backsolve(const GmresState *st, const double2 *H, const double2 *g, double2 *y, int m,
                                int smem_cols);
 __global__ void k_gm_xupdate(float2 *x, const float2 *V, int64_t n, const GmresState *st, const double2 *y);
