@@ -171,7 +171,13 @@ def run_ours(args):
     n = tris.shape[0]
     pts = W["field_points"]
     src = [bemfmm.plane_wave(W["plane_dir"], W["amp"])]
-    mesh = bemfmm.Mesh(nodes, tris, trunc_factor=args.trunc_factor)
+    mkw = {"trunc_factor": args.trunc_factor}
+    if args.leaf_edge > 0:
+        # a fixed leaf size (no autotuning): profiling runs pin the tree the
+        # timed run chose, since kernels slowed down by a profiler would
+        # steer the tuner elsewhere
+        mkw.update(leaf_edge=args.leaf_edge, autotune=0)
+    mesh = bemfmm.Mesh(nodes, tris, **mkw)
     dev = torch.device("cuda", local)
     p = torch.empty(n, dtype=torch.complex64, device=dev)
     q = torch.empty(n, dtype=torch.complex64, device=dev)
@@ -416,6 +422,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=1000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--leaf-edge", type=float, default=0.0,
+                    help="fixed leaf box edge in m (default: automatic, autotuned)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -209,11 +209,11 @@ int bem_mesh_release_plan(void *mesh);
 int bem_timing_enable(int enable);
 int bem_timing_get(const char *name, double *total_ms, int64_t *launches);
 
-/* Self-test of the far-field sine/cosine (a Cody-Waite reduction to
- * [-pi, pi] followed by the SFU approximations; no counterpart in the
- * paper): for n device floats x_dev writes device float4 out_dev[i] =
- * (sin, cos by the library's routine, sin, cos by CUDA's sincosf).
- * Stream-ordered, no synchronisation. */
+/* Self-test of the far-field sine/cosine of 2 pi t, t in turns (an exact
+ * reduction to [-1/2, 1/2] turn followed by the SFU approximations; no
+ * counterpart in the paper): for n device floats x_dev (= t) writes device
+ * float4 out_dev[i] = (sin, cos by the library's routine, sin, cos by CUDA's
+ * sincospif(2 t)).  Stream-ordered, no synchronisation. */
 int bem_selftest_sincos(const void *x_dev, int64_t n, void *out_dev, void *stream);
 
 /* Direct product without device allocation (the paper has no counterpart;

@@ -145,7 +145,8 @@ def timing_get(name: str):
 
 
 def selftest_sincos(x):
-    """(fast sin, fast cos, sincosf sin, sincosf cos) for a float32 CUDA tensor x."""
+    """(fast sin, fast cos, sincospif sin, sincospif cos) of 2 pi x for a float32
+    CUDA tensor x of phases in turns."""
     import torch
     if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
         raise TypeError("expected a contiguous float32 CUDA tensor")

@@ -24,6 +24,9 @@ using namespace bem;
 
 // Arnoldi steps captured in one CUDA graph (one status read per graph)
 constexpr int kStepsPerGraph = 4;
+// dynamic shared memory of k_disaggregate: first-half directions and
+// weighted Lambda rows of every level (16 bytes per direction)
+constexpr size_t kDisaggSmem = 200 * 1024;
 
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_err;
@@ -276,7 +279,8 @@ struct bem_mesh_impl {
     DevArr<int> type, err;
     DevArr<int> tma_err;          // set by a kernel whose bulk copy did not complete in time
     DevArr<float2> cp, cq, cp0, cq0, z, aq;
-    DevArr<float2> xint, ynear, alpha, beta, tmp, tmp2, bvec, uvec;
+    DevArr<float2> xint, ynear, tmp, tmp2, bvec, uvec;
+    DevArr<float4> wts;          // far-field weights (alpha, c) per element
     // GMRES workspace
     DevArr<float2> V, w;
     DevArr<double2> H, cs, sn, g_, hcol, part, yv;
@@ -841,8 +845,7 @@ PrepArgs prep_args(bem_mesh_impl &M, const float2 *cp, const float2 *cq, const f
     pa.jidx = nullptr;
     pa.perm = nullptr;
     pa.xint = M.xint.p;
-    pa.alpha = far ? M.alpha.p : nullptr;
-    pa.beta = far ? M.beta.p : nullptr;
+    pa.wts = far ? M.wts.p : nullptr;
     pa.chi = M.chi.p;
     pa.nrm = M.nrm.p;
     pa.cp = cp;
@@ -854,7 +857,8 @@ PrepArgs prep_args(bem_mesh_impl &M, const float2 *cp, const float2 *cq, const f
 // y = A x with the given column coefficients.  x: caller order when
 // perm_in, else internal (optionally x + (*jidx) n).  y: caller order when
 // perm_out.  use_store: use the stored near-field values.  prepared: the
-// product inputs (x_int, alpha, beta) are already formed and x is unused.
+// product inputs (x_int and the far-field weights) are already formed and x
+// is unused.
 void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool use_store, const float2 *x,
                      const int *jidx, bool perm_in, float2 *y, bool perm_out, const int *skip, cudaStream_t s,
                      bool prepared = false)
@@ -885,7 +889,7 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     if (A.ntasks > 0) {
         {
             KTimer kt_("k_aggregate", sf);
-            k_aggregate<<<A.ntasks, 128, 0, sf>>>(P.largs.p, M.alpha.p, M.beta.p, skip);
+            k_aggregate<<<A.ntasks, 128, 0, sf>>>(P.largs.p, M.wts.p, M.nrm.p, skip);
         }
         ck_launch("k_aggregate");
     }
@@ -937,7 +941,12 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     {
         KTimer kt_("k_disaggregate", s);
         const int nleaf = (int)(P.lists->leaf_start.n - 1);
-        k_disaggregate<<<nleaf, 128, (size_t)std::max(1, da.sum_nd) * sizeof(float2), s>>>(da, M.ynear.p, y, skip);
+        const size_t smem = (size_t)std::max(2, da.sum_nd) / 2 * sizeof(float4) + (size_t)da.sum_nd * sizeof(float2);
+        if (smem > kDisaggSmem)
+            throw Fail{set_err(BEM_E_ARG, "far field: " + std::to_string(da.sum_nd) +
+                                              " directions over all levels exceed the disaggregation kernel's "
+                                              "shared-memory staging")};
+        k_disaggregate<<<nleaf, 128, smem, s>>>(da, M.ynear.p, y, skip);
     }
     ck_launch("k_disaggregate");
 }
@@ -1034,8 +1043,7 @@ void ensure_work(bem_mesh_impl &M)
 {
     M.xint.alloc(M.n);
     M.ynear.alloc(M.n);
-    M.alpha.alloc(M.n);
-    M.beta.alloc(3 * M.n);
+    M.wts.alloc(M.n);
     M.tmp.alloc(M.n);
     M.tmp2.alloc(M.n);
 }
@@ -1247,7 +1255,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
            "cudaFuncSetAttribute");
         ck(cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 100 * 16),
            "cudaFuncSetAttribute");
-        ck(cudaFuncSetAttribute(k_disaggregate, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024),
+        ck(cudaFuncSetAttribute(k_disaggregate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDisaggSmem),
            "cudaFuncSetAttribute");
 
         std::vector<QuadTables> qt(1, make_tables(p));
@@ -1382,7 +1390,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
             int per_sm = 0, nsm = 0;
             ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gm_ortho, kOrthoThreads, 0), "occupancy");
             ck(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, M.device), "attribute");
-            const int64_t cap = (int64_t)per_sm * nsm;
+            const int64_t cap = std::min<int64_t>((int64_t)per_sm * nsm, kOrthoMaxBlocks);
             const int64_t want = std::max<int64_t>(1, (n + 63) / 64);
             nblk = (int)std::min(cap, want);
             if ((n + nblk - 1) / nblk > kOrthoMaxRows)

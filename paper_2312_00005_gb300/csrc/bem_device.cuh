@@ -105,16 +105,16 @@ __device__ __forceinline__ void gh_point(float3 d, float3 ny, float k, float w, 
     H = cfma(Gp, make_float2(-ir * ry, k * ry), H);
 }
 
-// sin and cos of x for the far-field phases: Cody-Waite reduction of x to
-// [-pi, pi] with 2 pi split as 6.28125 (exact in 8 bits) + 1.9353071795864769e-3,
-// then the SFU approximations (absolute error about 2^-21 on [-pi, pi]).
-// The unit tests compare it with CUDA's sincosf.
-__device__ __forceinline__ void fast_sincos(float x, float *s, float *c)
+// sin and cos of 2 pi t for the far-field phases, t in turns: t - round(t)
+// is exact, so the reduction adds no error; then the SFU approximations on
+// [-pi, pi] (absolute error about 2^-21).  The unit tests compare it with
+// CUDA's sincospif.
+__device__ __forceinline__ void sincos_turns(float t, float *s, float *c)
 {
-    const float n = rintf(x * 0.15915494309189535f);
-    float r = fmaf(-n, 6.28125f, x);
-    r = fmaf(-n, 1.9353071795864769e-3f, r);
-    __sincosf(r, s, c);
+    // round to the nearest integer by adding and removing 1.5 2^23 (exact
+    // for |t| < 2^22; the far-field phases stay far below)
+    const float r = t - __fsub_rn(__fadd_rn(t, 12582912.f), 12582912.f);
+    __sincosf(r * 6.28318548f, s, c);
 }
 
 // Rule code for a (sub)element: 0 = subdivide, m >= 1 = regular order m.

@@ -24,27 +24,6 @@ __device__ __forceinline__ double2 warp_sum_d(double2 v)
     return v;
 }
 
-// Sum of p[0..n) by one warp in a fixed order (lane l adds p[l], p[l+32],
-// ..., then a fixed shuffle tree): deterministic, and the loads are issued in
-// parallel instead of as a dependent chain.
-__device__ __forceinline__ double warp_sum_array(const volatile double *p, int n)
-{
-    double v = 0.0;
-    for (int b = threadIdx.x & 31; b < n; b += 32) v += p[b];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ double2 warp_sum_array2(const volatile double2 *p, int n)
-{
-    double2 v = make_double2(0.0, 0.0);
-    for (int b = threadIdx.x & 31; b < n; b += 32) { v.x += p[b].x; v.y += p[b].y; }
-    for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-    }
-    return v;
-}
-
 __device__ __forceinline__ bool skip_now(const int *skip) { return skip != nullptr && *(volatile const int *)skip != 0; }
 
 // ------------------------------------------------------------------ near field
@@ -267,22 +246,17 @@ __global__ void k_near_fused(NearArgs a, const float2 *__restrict__ x, float2 *_
 // ------------------------------------------------------------------ far field
 // Per product: gather x into the internal order (x_int[i] = x[perm[i]] or
 // x = xbase + jidx * n) and form the aggregation weights of the centroid
-// rule, alpha_i = A_i cq_i x_i and beta_i = ik A_i cp_i x_i n_i, so that the
-// column factor of Sec. 3.3.1 is alpha_i + beta_i . s.
+// rule, alpha_i = A_i cq_i x_i and c_i = ik A_i cp_i x_i, so that the column
+// factor of Sec. 3.3.1 is alpha_i + c_i (n_i . s).
 __device__ __forceinline__ void prep_store(const PrepArgs &a, int64_t i, float2 xv)
 {
     a.xint[i] = xv;
-    if (a.alpha) {
+    if (a.wts) {
         const float A = a.chi[i].w;
-        const float3 nn = f3(a.nrm[i]);
-        const float2 cq = a.cq[i], cp = a.cp[i];
-        a.alpha[i] = cscale(cmul(cq, xv), A);
-        // ik A cp x
-        const float2 t = cscale(cmul(cp, xv), A);
-        const float2 b = make_float2(-a.k * t.y, a.k * t.x);
-        a.beta[3 * i] = cscale(b, nn.x);
-        a.beta[3 * i + 1] = cscale(b, nn.y);
-        a.beta[3 * i + 2] = cscale(b, nn.z);
+        const float2 al = cscale(cmul(a.cq[i], xv), A);
+        const float2 t = cscale(cmul(a.cp[i], xv), A);
+        // (alpha, c) = (A cq x, ik A cp x)
+        a.wts[i] = make_float4(al.x, al.y, -a.k * t.y, a.k * t.x);
     }
 }
 __global__ void k_prep(PrepArgs a, const int *skip)
@@ -297,42 +271,51 @@ __global__ void k_prep(PrepArgs a, const int *skip)
 
 // Aggregation (Sec. 3.3.3, matrix T(l) with the centroid rule): for every
 // source cluster c and direction s_nu,
-//   M_c(nu) = sum_{j in c} e^{ik (z_c - x_j).s_nu} (alpha_j + beta_j . s_nu).
-// One block per task (a chunk of at most kAggChunk elements of one cluster);
-// the last task of a cluster split into several tasks sums their partial rows.
+//   M_c(nu) = sum_{j in c} e^{ik (z_c - x_j).s_nu} (alpha_j + c_j (n_j . s_nu)).
+// One block per task (a chunk of at most kAggChunk elements of one cluster),
+// one antipodal pair of directions per thread; phases in turns.  The last
+// task of a cluster split into several tasks sums their partial rows.
 constexpr int kAggChunk = 64;
-__global__ void k_aggregate(const LevelsArgs *__restrict__ A, const float2 *__restrict__ alpha,
-                            const float2 *__restrict__ beta, const int *skip)
+__global__ void k_aggregate(const LevelsArgs *__restrict__ A, const float4 *__restrict__ wts,
+                            const float4 *__restrict__ nrm, const int *skip)
 {
     if (skip_now(skip)) return;
     const AggTask T = A->tasks[blockIdx.x];
     const FarArgs &f = A->lev[T.lev];
-    __shared__ float4 sd[kAggChunk];       // z_c - x_j
-    __shared__ float2 sa[kAggChunk];       // alpha_j
-    __shared__ float2 sb[3 * kAggChunk];   // beta_j
+    __shared__ float4 sd[kAggChunk];       // (z_c - x_j) k / (2 pi)
+    __shared__ float4 sw[kAggChunk];       // (alpha_j, c_j)
+    __shared__ float4 sn[kAggChunk];       // n_j
+    const float kt = f.k * 0.15915494309189535f;
     for (int q = threadIdx.x; q < T.ne; q += blockDim.x) {
         const int64_t j = T.e0 + q;
-        sd[q] = f.dz[j];
-        sa[q] = alpha[j];
-        sb[3 * q] = beta[3 * j];
-        sb[3 * q + 1] = beta[3 * j + 1];
-        sb[3 * q + 2] = beta[3 * j + 2];
+        const float4 d = f.dz[j];
+        sd[q] = make_float4(kt * d.x, kt * d.y, kt * d.z, 0.f);
+        sw[q] = wts[j];
+        sn[q] = nrm[j];
     }
     __syncthreads();
+    // directions in antipodal halves: s_{p + h} = -s_p, so one phase serves
+    // both, e^{ik d.(-s)} = conj(e^{ik d.s}), and n.(-s) = -(n.s)
     float2 *__restrict__ out = f.M + (int64_t)T.row * f.nd;
-    for (int nu = threadIdx.x; nu < f.nd; nu += blockDim.x) {
-        const float4 s = f.dirs[nu];
-        const float3 sv = f3(s);
-        float2 acc = make_float2(0.f, 0.f);
+    const int h = f.nd / 2;
+    for (int p = threadIdx.x; p < h; p += blockDim.x) {
+        const float4 sv = f.dirs[p];
+        float2 accp = make_float2(0.f, 0.f), accm = accp;
         for (int q = 0; q < T.ne; ++q) {
-            float sn, cs;
-            fast_sincos(f.k * dot3f(f3(sd[q]), sv), &sn, &cs);
-            float2 w = sa[q];
-            w.x = fmaf(sb[3 * q].x, sv.x, fmaf(sb[3 * q + 1].x, sv.y, fmaf(sb[3 * q + 2].x, sv.z, w.x)));
-            w.y = fmaf(sb[3 * q].y, sv.x, fmaf(sb[3 * q + 1].y, sv.y, fmaf(sb[3 * q + 2].y, sv.z, w.y)));
-            acc = cfma(make_float2(cs, sn), w, acc);
+            const float4 d = sd[q], w = sw[q], n = sn[q];
+            float sn0, cs0;
+            sincos_turns(fmaf(d.x, sv.x, fmaf(d.y, sv.y, d.z * sv.z)), &sn0, &cs0);
+            const float t = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
+            const float ctx = w.z * t, cty = w.w * t;
+            const float2 wp = make_float2(w.x + ctx, w.y + cty), wm = make_float2(w.x - ctx, w.y - cty);
+            // (cs + i sn) wp and (cs - i sn) wm
+            accp.x = fmaf(cs0, wp.x, fmaf(-sn0, wp.y, accp.x));
+            accp.y = fmaf(cs0, wp.y, fmaf(sn0, wp.x, accp.y));
+            accm.x = fmaf(cs0, wm.x, fmaf(sn0, wm.y, accm.x));
+            accm.y = fmaf(cs0, wm.y, fmaf(-sn0, wm.x, accm.y));
         }
-        out[nu] = acc;
+        out[p] = accp;
+        out[p + h] = accm;
     }
     if (T.red < 0) return;
     // split cluster: the last of its tasks to finish sums the partial rows
@@ -361,14 +344,14 @@ __global__ void k_aggregate(const LevelsArgs *__restrict__ A, const float2 *__re
     if (threadIdx.x == 0) A->red_cnt[T.gred] = 0;
 }
 
-// sin / cos of x by fast_sincos and by sincosf, for the unit tests.
+// sin / cos of 2 pi x by sincos_turns and by sincospif, for the unit tests.
 __global__ void k_selftest_sincos(const float *__restrict__ x, int64_t n, float4 *__restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float s0, c0, s1, c1;
-    fast_sincos(x[i], &s0, &c0);
-    sincosf(x[i], &s1, &c1);
+    sincos_turns(x[i], &s0, &c0);
+    sincospif(2.f * x[i], &s1, &c1);
     out[i] = make_float4(s0, c0, s1, c1);
 }
 
@@ -425,63 +408,110 @@ __global__ void k_transfer(const LevelsArgs *__restrict__ A, const int *skip)
 //   y_i = near_i + (ik/16 pi^2) sum_l sum_nu w_nu (1 + s_nu.n_i)
 //                   e^{ik (x_i - z_t).s_nu} Lambda_t(nu).
 // One block per leaf: the elements of a leaf share their cluster at every
-// level, so the Lambda rows of the leaf's ancestors are staged in shared
-// memory once; each warp then takes one element at a time (lanes over nu) and
-// writes y[perm[i]] (caller order) or y[i].
-__global__ void k_disaggregate(DisaggArgs a, const float2 *__restrict__ ynear, float2 *__restrict__ y,
+// level, so the weighted Lambda rows of the leaf's ancestors and the
+// directions are staged in shared memory once.  Threads take antipodal
+// direction pairs (s_p, -s_p) of all levels (one phase and its conjugate),
+// each for a chunk of kDisChunk elements held in registers; the block then
+// sums each element's partials in a fixed order and writes y[perm[i]]
+// (caller order) or y[i].
+constexpr int kDisChunk = 8;
+__global__ void __launch_bounds__(128, 8) k_disaggregate(DisaggArgs a, const float2 *__restrict__ ynear, float2 *__restrict__ y,
                                const int *skip)
 {
     if (skip_now(skip)) return;
-    extern __shared__ float2 lam_s[];           // sum_nd entries
-    __shared__ int s_off[kMaxFarLevels + 1], s_has[kMaxFarLevels];
+    extern __shared__ float4 dsm[];   // [sum_nd / 2] first-half directions, then [sum_nd] w Lambda (float2)
+    float4 *dir_s = dsm;
+    float2 *lam_s = (float2 *)(dsm + a.sum_nd / 2);
+    __shared__ int s_lev[kMaxFarLevels], s_poff[kMaxFarLevels + 1], s_loff[kMaxFarLevels], s_h[kMaxFarLevels];
+    __shared__ int s_nact;
+    __shared__ float4 dzs[kDisChunk][kMaxFarLevels];   // -k/(2 pi) (z_c - x_i) per active level
+    __shared__ float4 ns[kDisChunk];
+    __shared__ float2 red[32][kDisChunk];
     const int t = blockIdx.x;
     const int64_t e0 = a.leaf_start[t], e1 = a.leaf_start[t + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) {
-        int off = 0;
+        // active levels (the leaf's cluster has an interaction list there)
+        int na = 0, poff = 0, loff = 0;
         for (int l = 0; l < a.nlev; ++l) {
             const FarArgs &f = a.lev[l];
             const int c = f.elem_cl[e0];
-            s_has[l] = f.il_ptr[c] != f.il_ptr[c + 1];
-            s_off[l] = off;
-            off += f.nd;
+            if (f.il_ptr[c] == f.il_ptr[c + 1]) continue;
+            s_lev[na] = l;
+            s_poff[na] = poff;
+            s_loff[na] = loff;
+            s_h[na] = f.nd / 2;
+            poff += f.nd / 2;
+            loff += f.nd;
+            ++na;
         }
-        s_off[a.nlev] = off;
+        s_poff[na] = poff;
+        s_nact = na;
     }
     __syncthreads();
-    for (int l = 0; l < a.nlev; ++l) {
-        if (!s_has[l]) continue;
-        const FarArgs &f = a.lev[l];
+    const int na = s_nact, HP = s_poff[na];
+    for (int u = 0; u < na; ++u) {
+        const FarArgs &f = a.lev[s_lev[u]];
         const float2 *__restrict__ src = f.Lam + (int64_t)f.elem_cl[e0] * f.nd;
-        for (int nu = threadIdx.x; nu < f.nd; nu += blockDim.x) lam_s[s_off[l] + nu] = src[nu];
+        for (int nu = threadIdx.x; nu < f.nd; nu += blockDim.x) {
+            const float4 d = f.dirs[nu];
+            if (nu < f.nd / 2) dir_s[s_poff[u] + nu] = make_float4(d.x, d.y, d.z, __int_as_float(u));
+            lam_s[s_loff[u] + nu] = cscale(src[nu], d.w);
+        }
     }
-    __syncthreads();
-    for (int64_t i = e0 + warp; i < e1; i += nw) {
-        const float3 ni = f3(a.nrm[i]);
-        float2 acc = make_float2(0.f, 0.f);
-        for (int l = 0; l < a.nlev; ++l) {
-            if (!s_has[l]) continue;
-            const FarArgs &f = a.lev[l];
-            const float3 dz = f3(f.dz[i]);             // z_c - x_i
-            const float2 *lam = lam_s + s_off[l];
-            const float kk = -f.k;
-            for (int nu = lane; nu < f.nd; nu += 32) {
-                const float4 s = f.dirs[nu];
-                float sn, cs;
-                fast_sincos(kk * dot3f(dz, f3(s)), &sn, &cs);
-                const float wf = s.w * (1.0f + dot3f(f3(s), ni));
-                acc = cfma(make_float2(cs * wf, sn * wf), lam[nu], acc);
+    for (int64_t c0 = e0; c0 < e1; c0 += kDisChunk) {
+        const int cnt = (int)min((int64_t)kDisChunk, e1 - c0);
+        for (int v = threadIdx.x; v < cnt * na; v += blockDim.x) {
+            const int q = v / na, u = v % na;
+            const FarArgs &f = a.lev[s_lev[u]];
+            const float kt = -f.k * 0.15915494309189535f;
+            const float4 dz = f.dz[c0 + q];              // z_c - x_i
+            dzs[q][u] = make_float4(kt * dz.x, kt * dz.y, kt * dz.z, 0.f);
+        }
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) ns[q] = a.nrm[c0 + q];
+        __syncthreads();
+        float2 acc[kDisChunk];
+#pragma unroll
+        for (int q = 0; q < kDisChunk; ++q) acc[q] = make_float2(0.f, 0.f);
+        for (int pf = threadIdx.x; pf < HP; pf += blockDim.x) {
+            const float4 sv = dir_s[pf];
+            const int u = __float_as_int(sv.w);
+            const int base = s_loff[u] + (pf - s_poff[u]);
+            const float2 lp = lam_s[base], lm = lam_s[base + s_h[u]];
+#pragma unroll
+            for (int q = 0; q < kDisChunk; ++q) {
+                if (q < cnt) {
+                    const float4 d = dzs[q][u], n = ns[q];
+                    float sn0, cs0;
+                    sincos_turns(fmaf(d.x, sv.x, fmaf(d.y, sv.y, d.z * sv.z)), &sn0, &cs0);
+                    const float tn = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
+                    const float2 gp = cscale(lp, 1.f + tn), gm = cscale(lm, 1.f - tn);
+                    // (cs + i sn) gp + (cs - i sn) gm
+                    const float2 sp = make_float2(gp.x + gm.x, gp.y + gm.y);
+                    const float2 dm = make_float2(gp.x - gm.x, gp.y - gm.y);
+                    acc[q].x = fmaf(cs0, sp.x, fmaf(-sn0, dm.y, acc[q].x));
+                    acc[q].y = fmaf(cs0, sp.y, fmaf(sn0, dm.x, acc[q].y));
+                }
             }
         }
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            // (ik / 16 pi^2) acc
+#pragma unroll
+        for (int q = 0; q < kDisChunk; ++q) {
+            const float2 v = warp_sum(acc[q]);
+            if (lane == 0) red[warp][q] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            const int q = threadIdx.x;
+            float2 v = red[0][q];
+            for (int w = 1; w < nw; ++w) v = cadd(v, red[w][q]);
+            const int64_t i = c0 + q;
+            // (ik / 16 pi^2) v
             const float sc = a.k * 0.00633257397764611f;   // k / (16 pi^2)
-            const float2 far = make_float2(-sc * acc.y, sc * acc.x);
-            const float2 out = cadd(ynear[i], far);
+            const float2 out = cadd(ynear[i], make_float2(-sc * v.y, sc * v.x));
             if (a.perm) y[a.perm[i]] = out;
             else y[i] = out;
         }
+        __syncthreads();
     }
 }
 
@@ -819,13 +849,24 @@ __device__ __forceinline__ void ff_add(FF &a, const FF &b)
     ff_add1(a.hi.x, a.lo.x, b.hi.x, b.lo.x);
     ff_add1(a.hi.y, a.lo.y, b.hi.y, b.lo.y);
 }
-// sum of p[0..n) (float2) by one warp: lane order, then a fixed xor tree
-__device__ __forceinline__ FF warp_sum_ff(const volatile float2 *p, int n)
+// sum of p[0..n), n <= 32 kFFLoads (float2, written by other blocks before
+// a grid barrier: read through L2) by one warp: lane order, then a fixed
+// xor tree.  All loads are issued before the first add.
+constexpr int kFFLoads = 16;
+__device__ __forceinline__ FF warp_sum_ff(const float2 *p, int n)
 {
     FF v = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    for (int q = threadIdx.x & 31; q < n; q += 32) {
-        const FF x = {make_float2(p[q].x, p[q].y), make_float2(0.f, 0.f)};
-        ff_add(v, x);
+    const int lane = threadIdx.x & 31;
+    float2 x[kFFLoads];
+#pragma unroll
+    for (int u = 0; u < kFFLoads; ++u) {
+        const int q = lane + 32 * u;
+        x[u] = q < n ? __ldcg(p + q) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kFFLoads; ++u) {
+        const FF t = {x[u], make_float2(0.f, 0.f)};
+        ff_add(v, t);
     }
     for (int o = 16; o > 0; o >>= 1) {
         FF x;
@@ -875,6 +916,7 @@ __global__ void __launch_bounds__(kOrthoThreads) k_gm_ortho(OrthoArgs a)
             float2 acc[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.f, 0.f);
+#pragma unroll 4
             for (int i = lane; i < R; i += 32) {
                 const float2 y = ws[i];
 #pragma unroll

@@ -52,7 +52,7 @@ struct PrepArgs {
     const int *jidx;         // optional: x += (*jidx) * n
     const int64_t *perm;     // optional: internal -> caller
     float2 *xint;
-    float2 *alpha, *beta;    // far-field weights (alpha n, beta 3n); may be null
+    float4 *wts;             // far-field weights (alpha, c) per element; may be null
     const float4 *chi, *nrm;
     const float2 *cp, *cq;
     float k;
@@ -125,7 +125,7 @@ __global__ void k_near_spmv(NearArgs a, const float2 *val, const float2 *x, floa
 __global__ void k_near_spmv_leaf(NearArgs a, const float2 *val, const float2 *x, float2 *y, const int *skip);
 __global__ void k_near_fused(NearArgs a, const float2 *x, float2 *y, int *err, const int *skip);
 __global__ void k_prep(PrepArgs a, const int *skip);
-__global__ void k_aggregate(const LevelsArgs *A, const float2 *alpha, const float2 *beta, const int *skip);
+__global__ void k_aggregate(const LevelsArgs *A, const float4 *wts, const float4 *nrm, const int *skip);
 __global__ void k_selftest_sincos(const float *x, int64_t n, float4 *out);
 __global__ void k_transfer(const LevelsArgs *A, const int *skip);
 __global__ void k_disaggregate(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
@@ -164,6 +164,7 @@ struct OrthoArgs {
     int rows;                // rows of the basis per block
 };
 constexpr int kOrthoThreads = 256;
+constexpr int kOrthoMaxBlocks = 512;   // partials per reduction: 32 lanes x 16 loads
 constexpr int kOrthoMaxRows = 1024;    // rows per block staged in shared memory
 __global__ void k_gm_ortho(OrthoArgs a);
 __global__ void k_gm_givens(GmresArgs a);

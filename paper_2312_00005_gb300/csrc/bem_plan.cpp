@@ -202,20 +202,40 @@ void sphere_grid(int L, std::vector<double> &s, std::vector<double> &w)
 {
     std::vector<double> t, wt;
     gauss_legendre01(L, t, wt);      // on [0,1]: cos(theta) = 2t - 1, weight 2 wt
-    s.resize(3 * 2 * L * L);
-    w.resize(2 * L * L);
-    int q = 0;
+    // cos(theta) nodes and weights made exactly symmetric about 0
+    std::vector<double> ct(L), wc(L);
     for (int a = 0; a < L; ++a) {
-        double ct = 2.0 * t[a] - 1.0, st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
-        for (int b = 0; b < 2 * L; ++b) {
-            double ph = M_PI * b / L;
-            s[3 * q] = st * std::cos(ph);
-            s[3 * q + 1] = st * std::sin(ph);
-            s[3 * q + 2] = ct;
-            w[q] = 2.0 * wt[a] * M_PI / L;
-            ++q;
-        }
+        ct[a] = 2.0 * t[a] - 1.0;
+        wc[a] = 2.0 * wt[a];
     }
+    for (int a = 0; a < L / 2; ++a) {
+        const int b = L - 1 - a;
+        const double m = 0.5 * (ct[b] - ct[a]), v = 0.5 * (wc[a] + wc[b]);
+        ct[a] = -m;
+        ct[b] = m;
+        wc[a] = wc[b] = v;
+    }
+    if (L % 2) ct[L / 2] = 0.0;
+    const int half = L * L;
+    s.resize(3 * 2 * half);
+    w.resize(2 * half);
+    int q = 0;
+    auto put = [&](int a, int b) {
+        const double st = std::sqrt(std::max(0.0, 1.0 - ct[a] * ct[a]));
+        const double ph = M_PI * b / L;
+        s[3 * q] = st * std::cos(ph);
+        s[3 * q + 1] = st * std::sin(ph);
+        s[3 * q + 2] = ct[a];
+        w[q] = wc[a] * M_PI / L;
+        // the antipode -s_q (theta -> pi - theta, phi -> phi + pi)
+        for (int c = 0; c < 3; ++c) s[3 * (q + half) + c] = -s[3 * q + c];
+        w[q + half] = w[q];
+        ++q;
+    };
+    for (int a = 0; a < L / 2; ++a)
+        for (int b = 0; b < 2 * L; ++b) put(a, b);
+    if (L % 2)
+        for (int b = 0; b < L; ++b) put(L / 2, b);
 }
 
 double hankel_growth(double x, int L)

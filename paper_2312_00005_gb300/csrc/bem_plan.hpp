@@ -48,7 +48,9 @@ void conical_rule(int m, std::vector<double> &xi, std::vector<double> &eta, std:
 // (all three a-priori estimates of Sec. 3.1.4 below tol), else m_max.
 void order_thresholds(double tol, int m_max, double *R);
 // unit-sphere grid: L Gauss-Legendre nodes in cos(theta) x 2L azimuths
-// phi = pi b / L; weights w_GL * pi / L (sum 4 pi).  s: 3 * 2L^2.
+// phi = pi b / L; weights w_GL * pi / L (sum 4 pi).  s: 3 * 2L^2, ordered in
+// antipodal halves: for q < L^2, s_{q + L^2} = -s_q exactly (same weight),
+// so a phase e^{ik d.s} serves both (the second is the conjugate).
 void sphere_grid(int L, std::vector<double> &s, std::vector<double> &w);
 // sum_{n<=L} (2n+1) |h_n(x)| / |h_0(x)| (h_n by upward recursion)
 double hankel_growth(double x, int L);

@@ -261,9 +261,10 @@ def test_full_size_solve_residual_and_series(bem, big_sphere, tf, tol):
 
 
 def test_fast_sincos_against_cuda(bem):
-    """The far field's Cody-Waite + SFU sine/cosine against CUDA's sincosf on
-    the phase range of the far field (|x| <= 200 rad)."""
-    x = torch.linspace(-200.0, 200.0, 400001, dtype=torch.float32, device="cuda")
+    """The far field's sine/cosine of 2 pi t (t in turns: exact reduction,
+    then the SFU) against CUDA's sincospif on the phase range of the far
+    field (|t| <= 32 turns, about 200 rad)."""
+    x = torch.linspace(-32.0, 32.0, 400001, dtype=torch.float32, device="cuda")
     out = bem.selftest_sincos(x).cpu().numpy().astype(np.float64)
     err = np.max(np.abs(out[:, 0:2] - out[:, 2:4]))
     assert err < 2e-6, err
