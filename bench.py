@@ -360,6 +360,34 @@ def residual_vs_fp64(W, p, args, nrows=48):
     return {"fp64_residual_sampled_rows": float(np.linalg.norm(Ap - b) / np.linalg.norm(b)), "rows": nrows}
 
 
+# DRAM traffic of one k_near_spmv_items launch (dram__bytes_read.sum +
+# dram__bytes_write.sum) from an ncu capture of this workload with the tree
+# the timed run chooses; valid only while the kernel's source and launch and
+# the plan (near_nnz) are the ones captured.  The capture command and its
+# figures are in profiles/k_near_spmv_items_sphere20480_4k.md.
+SPMV_TRAFFIC = {"source_sha256": None, "near_nnz": None, "bytes": None}
+
+
+def _spmv_source_hash():
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_2312_00005_gb300", "csrc", "bem_kernels.cu")).read()
+    capi = open(os.path.join(ROOT, "paper_2312_00005_gb300", "csrc", "bem_capi.cu")).read()
+    i0 = src.index("__device__ __forceinline__ float2 spmv_segment(")
+    i1 = src.index("\n}\n", src.index("k_near_spmv_items(NearArgs a"))
+    launch = [ln.strip() for ln in capi.splitlines() if "k_near_spmv_items<<<" in ln or "kSpmvItemEntries =" in ln]
+    return hashlib.sha256((src[i0:i1] + "\n".join(launch)).encode()).hexdigest()
+
+
+def spmv_traffic(nnz):
+    t = SPMV_TRAFFIC
+    if t["bytes"] is None or t["near_nnz"] != nnz:
+        return None
+    try:
+        return t["bytes"] if _spmv_source_hash() == t["source_sha256"] else None
+    except (OSError, ValueError):
+        return None
+
+
 def roofline(kernels, stats, n, peaks, peak_src):
     """Roofline of the kernel with the largest total time in the timed steps."""
     if not kernels:
@@ -373,7 +401,7 @@ def roofline(kernels, stats, n, peaks, peak_src):
         byts = 8 * nnz + 16 * n
         ach = byts / avg_s / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(ach / hbm, 4), "traffic": None, "algorithmic_bytes": byts,
+                "frac": round(ach / hbm, 4), "traffic": spmv_traffic(nnz), "algorithmic_bytes": byts,
                 "peak_source": peak_src}
     return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
             "traffic": None, "avg_us": kernels[name]["avg_us"], "peak_source": peak_src}

@@ -24,6 +24,8 @@ using namespace bem;
 
 // Arnoldi steps captured in one CUDA graph (one status read per graph)
 constexpr int kStepsPerGraph = 4;
+// values per work item of the stored near-field product
+constexpr int64_t kSpmvItemEntries = 65536;
 // dynamic shared memory of k_disaggregate: first-half directions and
 // weighted Lambda rows of every level (16 bytes per direction)
 constexpr size_t kDisaggSmem = 200 * 1024;
@@ -191,6 +193,8 @@ struct Lists {
     DevArr<int> leaf_of, run_ptr, ncol;
     DevArr<int2> runs;
     DevArr<int64_t> row_ptr;
+    DevArr<int4> spmv_items;      // (leaf, first row, end row) work items of the product
+    int n_spmv_items = 0;
     int64_t nnz = 0;
     std::vector<std::unique_ptr<ListsLevelDev>> lev;
     // all levels together, for the one-launch far-field kernels
@@ -277,7 +281,6 @@ struct bem_mesh_impl {
     DevArr<int64_t> perm;
     DevArr<QuadTables> Q;
     DevArr<int> type, err;
-    DevArr<int> tma_err;          // set by a kernel whose bulk copy did not complete in time
     DevArr<float2> cp, cq, cp0, cq0, z, aq;
     DevArr<float2> xint, ynear, tmp, tmp2, bvec, uvec;
     DevArr<float4> wts;          // far-field weights (alpha, c) per element
@@ -413,6 +416,22 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
     Ls->ncol.upload(ncol, s);
     Ls->runs.upload(runs, s);
     Ls->row_ptr.upload(row_ptr, s);
+    {
+        // about kSpmvItemEntries values per item (at most kSpmvMaxItemRows
+        // rows), a leaf's rows split evenly
+        std::vector<int4> items;
+        for (int t = 0; t < nl; ++t) {
+            const int rows = (int)Lf.count[t];
+            if (rows == 0) continue;
+            const int rpi = (int)std::max<int64_t>(1, std::min<int64_t>(kSpmvMaxItemRows,
+                                                                        kSpmvItemEntries / std::max(1, ncol[t])));
+            const int nit = (rows + rpi - 1) / rpi;
+            for (int q = 0; q < nit; ++q)
+                items.push_back(make_int4(t, (int)((int64_t)rows * q / nit), (int)((int64_t)rows * (q + 1) / nit), 0));
+        }
+        Ls->n_spmv_items = (int)items.size();
+        Ls->spmv_items.upload(items, s);
+    }
     std::vector<AggTask> all_tasks;
     std::vector<int2> all_reds, all_targets;
     for (const FarLevel &FL : F.far) {
@@ -726,15 +745,9 @@ void upload_coeffs(bem_mesh_impl &M, const Coeffs &C)
 
 void check_err(bem_mesh_impl &M)
 {
-    int e = INT_MAX, te = 0;
+    int e = INT_MAX;
     ck(cudaMemcpyAsync(&e, M.err.p, sizeof(int), cudaMemcpyDeviceToHost, M.s), "D2H err");
-    ck(cudaMemcpyAsync(&te, M.tma_err.p, sizeof(int), cudaMemcpyDeviceToHost, M.s), "D2H err");
     ck(cudaStreamSynchronize(M.s), "sync");
-    if (te != 0) {
-        ck(cudaMemsetAsync(M.tma_err.p, 0, sizeof(int), M.s), "memset");
-        g_err = "a bulk copy of near-field entries did not complete within its wait limit";
-        throw Fail{BEM_E_TIMEOUT};
-    }
     if (e != INT_MAX) {
         char buf[160];
         snprintf(buf, sizeof buf,
@@ -903,11 +916,11 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     NearArgs na = near_args(M, P, cp, cq);
     if (use_store && M.prm.near_store && !P.fp().direct) {
         const size_t xs_bytes = (size_t)P.lists->max_ncol * sizeof(float2);
-        const int nleaf = (int)(P.lists->leaf_start.n - 1);
         if (xs_bytes <= 160 * 1024) {
-            {
+            if (P.lists->n_spmv_items > 0) {
                 KTimer kt_("k_near_spmv", s);
-                k_near_spmv_leaf<<<nleaf, 256, xs_bytes, s>>>(na, P.val.p, M.xint.p, M.ynear.p, skip);
+                k_near_spmv_items<<<P.lists->n_spmv_items, kSpmvThreads, xs_bytes, s>>>(
+                    na, P.lists->spmv_items.p, P.val.p, M.xint.p, M.ynear.p, skip);
             }
             ck_launch("k_near_spmv");
         } else {
@@ -1251,7 +1264,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         M->ad.upload(ad, s);
         M->perm.upload(M->t.perm, s);
         M->type.upload(ty, s);
-        ck(cudaFuncSetAttribute(k_near_spmv_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024),
+        ck(cudaFuncSetAttribute(k_near_spmv_items, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024),
            "cudaFuncSetAttribute");
         ck(cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 100 * 16),
            "cudaFuncSetAttribute");
@@ -1261,8 +1274,6 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         std::vector<QuadTables> qt(1, make_tables(p));
         M->Q.upload(qt, s);
         M->err.alloc(1);
-        M->tma_err.alloc(1);
-        ck(cudaMemsetAsync(M->tma_err.p, 0, sizeof(int), s), "memset");
         ck(cudaStreamSynchronize(s), "sync");
         *out = M.release();
         return BEM_OK;
@@ -1437,7 +1448,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         // one Arnoldi step, captured once as a graph and replayed
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t gexec = nullptr;
-        const int *done = &M.st.p->done;
+        const int *done = &M.st.p->skip_prod;   // uniform within every product launch
         OrthoArgs oa;
         GmresArgs &ga = oa.g;
         ga.V = M.V.p;

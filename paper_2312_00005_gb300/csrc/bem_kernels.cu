@@ -156,58 +156,116 @@ __global__ void k_near_spmv(NearArgs a, const float2 *__restrict__ val, const fl
     if (lane == 0) y[i] = acc;
 }
 
-// Near-field product, one block per leaf: the rows of a leaf share its column
-// list, so x at those columns is staged once in shared memory; each warp then
-// streams one row's entries (coalesced, four loads in flight per lane).
-__global__ void k_near_spmv_leaf(NearArgs a, const float2 *__restrict__ val, const float2 *__restrict__ x,
-                                 float2 *__restrict__ y, const int *skip)
+// Stored near field (Sec. 3.3.3, matrix N) over work items: an item is a
+// range of rows of one leaf; the leaf's near columns x are staged in shared
+// memory (kept while consecutive items share the leaf) and the item's values
+// (rows x ncol, contiguous) are split evenly among the warps, which stream
+// them from HBM (evict-first, 16 loads per lane in flight).  Each warp
+// leaves a partial per row it touched; the block sums them in warp order.
+// One block per item: items are small, so the block scheduler balances the
+// work across SMs (and shares them with the far-field kernels running
+// beside) whatever the leaf sizes.
+__device__ __forceinline__ float2 spmv_segment(const float2 *__restrict__ v, const float2 *__restrict__ xs, int c0,
+                                               int c1, int lane)
+{
+    // sum_{c0 <= c < c1} v[c] xs[c] with c0 even: column pairs per 16-byte
+    // load (v and xs 16-byte aligned), the odd last column alone
+    const float4 *__restrict__ v4 = reinterpret_cast<const float4 *>(v);
+    const float4 *__restrict__ x4 = reinterpret_cast<const float4 *>(xs);
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+    int q = (c0 >> 1) + lane;
+    const int qe = c1 >> 1;
+    for (; q + 480 < qe; q += 512) {
+        float4 vv[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) vv[u] = __ldcs(v4 + q + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 16; u += 2) {
+            const float4 xa = x4[q + 32 * u], xb = x4[q + 32 * (u + 1)];
+            acc0 = cfma(make_float2(vv[u].x, vv[u].y), make_float2(xa.x, xa.y), acc0);
+            acc1 = cfma(make_float2(vv[u].z, vv[u].w), make_float2(xa.z, xa.w), acc1);
+            acc2 = cfma(make_float2(vv[u + 1].x, vv[u + 1].y), make_float2(xb.x, xb.y), acc2);
+            acc3 = cfma(make_float2(vv[u + 1].z, vv[u + 1].w), make_float2(xb.z, xb.w), acc3);
+        }
+    }
+    for (; q + 96 < qe; q += 128) {
+        float4 vv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) vv[u] = __ldcs(v4 + q + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; u += 2) {
+            const float4 xa = x4[q + 32 * u], xb = x4[q + 32 * (u + 1)];
+            acc0 = cfma(make_float2(vv[u].x, vv[u].y), make_float2(xa.x, xa.y), acc0);
+            acc1 = cfma(make_float2(vv[u].z, vv[u].w), make_float2(xa.z, xa.w), acc1);
+            acc2 = cfma(make_float2(vv[u + 1].x, vv[u + 1].y), make_float2(xb.x, xb.y), acc2);
+            acc3 = cfma(make_float2(vv[u + 1].z, vv[u + 1].w), make_float2(xb.z, xb.w), acc3);
+        }
+    }
+    for (; q < qe; q += 32) {
+        const float4 vv = __ldcs(v4 + q), xa = x4[q];
+        acc0 = cfma(make_float2(vv.x, vv.y), make_float2(xa.x, xa.y), acc0);
+        acc1 = cfma(make_float2(vv.z, vv.w), make_float2(xa.z, xa.w), acc1);
+    }
+    if ((c1 & 1) && lane == 0) acc2 = cfma(v[c1 - 1], xs[c1 - 1], acc2);
+    return warp_sum(cadd(cadd(acc0, acc1), cadd(acc2, acc3)));
+}
+
+__global__ void __launch_bounds__(kSpmvThreads) k_near_spmv_items(NearArgs a, const int4 *__restrict__ items,
+                                                                  const float2 *__restrict__ val,
+                                                                  const float2 *__restrict__ x,
+                                                                  float2 *__restrict__ y, const int *skip)
 {
     if (skip_now(skip)) return;
     extern __shared__ float2 xs[];
-    const int t = blockIdx.x;
-    const int r0 = a.N.run_ptr[t], r1 = a.N.run_ptr[t + 1], nc = a.N.ncol[t];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int r = r0 + warp; r < r1; r += nw) {
-        const int2 rr = a.N.runs[r];
-        const int end = (r + 1 < r1) ? a.N.runs[r + 1].y : nc;
-        int p = rr.y + lane;
-        for (; p + 224 < end; p += 256) {
-            float2 t8[8];
+    constexpr int kW = kSpmvThreads / 32;
+    static_assert(kSpmvMaxItemRows * kW == kSpmvThreads, "one partial slot per thread");
+    __shared__ float2 part[kSpmvMaxItemRows][kW];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int4 W = items[blockIdx.x];
+    const int t = W.x;
+    const int nc = a.N.ncol[t];
+    {
+        const int r0 = a.N.run_ptr[t], r1 = a.N.run_ptr[t + 1];
+        for (int r = r0 + warp; r < r1; r += kW) {
+            const int2 rr = a.N.runs[r];
+            const int end = (r + 1 < r1) ? a.N.runs[r + 1].y : nc;
+            int p = rr.y + lane;
+            for (; p + 224 < end; p += 256) {
+                float2 t8[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) t8[u] = x[rr.x + (p + 32 * u - rr.y)];
+                for (int u = 0; u < 8; ++u) t8[u] = x[rr.x + (p + 32 * u - rr.y)];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) xs[p + 32 * u] = t8[u];
+                for (int u = 0; u < 8; ++u) xs[p + 32 * u] = t8[u];
+            }
+            for (; p < end; p += 32) xs[p] = x[rr.x + (p - rr.y)];
         }
-        for (; p < end; p += 32) xs[p] = x[rr.x + (p - rr.y)];
+    }
+    part[threadIdx.x / kW][threadIdx.x % kW] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int64_t i0 = a.N.leaf_start[t] + W.y;
+    const int nrow = min(W.z - W.y, kSpmvMaxItemRows);   // the host never makes larger items
+    // the item's rows (stride ncp, padded to even) split at even positions
+    const int ncp = (nc + 1) & ~1;
+    const int64_t total = (int64_t)nrow * ncp;
+    int64_t qa = (total * warp / kW) & ~(int64_t)1;
+    const int64_t qb = warp == kW - 1 ? total : (total * (warp + 1) / kW) & ~(int64_t)1;
+    while (qa < qb) {
+        const int r = (int)(qa / ncp);
+        const int c0 = (int)(qa - (int64_t)r * ncp);
+        const int c1 = (int)min((int64_t)ncp, (int64_t)c0 + (qb - qa));
+        const int c1r = min(c1, nc);
+        if (c0 < c1r) {
+            const float2 acc = spmv_segment(val + a.N.row_ptr[i0 + r], xs, c0, c1r, lane);
+            if (lane == 0) part[r][warp] = acc;
+        }
+        qa += c1 - c0;
     }
     __syncthreads();
-    const int64_t e0 = a.N.leaf_start[t], e1 = a.N.leaf_start[t + 1];
-    for (int64_t i = e0 + warp; i < e1; i += nw) {
-        const float2 *__restrict__ v = val + a.N.row_ptr[i];
-        float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
-        int p = lane;
-        for (; p + 480 < nc; p += 512) {
-            float2 vv[16];
+    if (threadIdx.x < nrow) {
+        float2 sum = part[threadIdx.x][0];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) vv[u] = __ldcs(v + p + 32 * u);
-#pragma unroll
-            for (int u = 0; u < 16; u += 4) {
-                acc0 = cfma(vv[u], xs[p + 32 * u], acc0);
-                acc1 = cfma(vv[u + 1], xs[p + 32 * (u + 1)], acc1);
-                acc2 = cfma(vv[u + 2], xs[p + 32 * (u + 2)], acc2);
-                acc3 = cfma(vv[u + 3], xs[p + 32 * (u + 3)], acc3);
-            }
-        }
-        for (; p + 96 < nc; p += 128) {
-            const float2 v0 = __ldcs(v + p), v1 = __ldcs(v + p + 32), v2 = __ldcs(v + p + 64), v3 = __ldcs(v + p + 96);
-            acc0 = cfma(v0, xs[p], acc0);
-            acc1 = cfma(v1, xs[p + 32], acc1);
-            acc2 = cfma(v2, xs[p + 64], acc2);
-            acc3 = cfma(v3, xs[p + 96], acc3);
-        }
-        for (; p < nc; p += 32) acc0 = cfma(__ldcs(v + p), xs[p], acc0);
-        const float2 acc = warp_sum(cadd(cadd(acc0, acc1), cadd(acc2, acc3)));
-        if (lane == 0) y[i] = acc;
+        for (int w = 1; w < kW; ++w) sum = cadd(sum, part[threadIdx.x][w]);
+        y[i0 + threadIdx.x] = sum;
     }
 }
 
@@ -891,7 +949,9 @@ __global__ void __launch_bounds__(kOrthoThreads) k_gm_ortho(OrthoArgs a)
 {
     const GmresArgs &g = a.g;
     GmresState *st = g.st;
-    if (*(volatile int *)&st->done || *(volatile int *)a.err) return;
+    const int done = *(volatile int *)&st->done;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->skip_prod = done;
+    if (done || *(volatile int *)a.err) return;
     const int j = *(volatile int *)&st->j;
     const int G = gridDim.x, b = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = kOrthoThreads / 32;
@@ -1109,6 +1169,7 @@ __global__ void k_gm_start(GmresState *st, float2 *__restrict__ V, const float2 
         st->j = 0;
         st->ncols = 0;
         st->done = 0;
+        st->skip_prod = 0;
         st->converged = 0;
         st->resid = st->bnorm > 0.0 ? beta / st->bnorm : 0.0;
         for (int l = 0; l <= m; ++l) g[l] = make_double2(0.0, 0.0);

@@ -44,6 +44,11 @@ struct GmresState {
     int n_reorth;            // columns that needed it
     int fault;               // a grid barrier wait gave up (never reset by a restart)
     double nn;               // ||w||^2 after orthogonalisation (k_gm_ortho -> k_gm_givens)
+    // Skip flag of the product kernels: a copy of done taken by k_gm_ortho
+    // (in stream order before the next product).  done itself is set by
+    // k_gm_givens on a side stream while that product runs, so reading it
+    // there could differ between the threads of one block.
+    int skip_prod;
 };
 
 struct PrepArgs {
@@ -122,7 +127,12 @@ __global__ void k_near_classify(NearArgs a, int2 *heavy, unsigned long long *cou
 __global__ void k_near_store_light(NearArgs a, float2 *val, int *err);
 __global__ void k_near_store_heavy(NearArgs a, const int2 *heavy, int64_t nheavy, float2 *val, int *err);
 __global__ void k_near_spmv(NearArgs a, const float2 *val, const float2 *x, float2 *y, const int *skip);
-__global__ void k_near_spmv_leaf(NearArgs a, const float2 *val, const float2 *x, float2 *y, const int *skip);
+// Stored near-field product over work items (leaf, first row, end row),
+// one block per item.
+constexpr int kSpmvThreads = 128;
+constexpr int kSpmvMaxItemRows = 32;
+__global__ void k_near_spmv_items(NearArgs a, const int4 *items, const float2 *val, const float2 *x, float2 *y,
+                                  const int *skip);
 __global__ void k_near_fused(NearArgs a, const float2 *x, float2 *y, int *err, const int *skip);
 __global__ void k_prep(PrepArgs a, const int *skip);
 __global__ void k_aggregate(const LevelsArgs *A, const float4 *wts, const float4 *nrm, const int *skip);
