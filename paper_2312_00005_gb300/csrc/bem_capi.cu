@@ -589,7 +589,11 @@ void finish_plan(bem_mesh_impl &M, Plan &Pl)
         if (tot > 0) {
             {
                 KTimer kt_("k_dtable", s);
-                k_dtable<<<nblocks(tot, 128), 128, 0, s>>>(D->ll->offs.p, D->noff, D->dirs_d.p, D->nd, D->L, k, D->D.p);
+                if (D->L > kMaxTableL)
+                    throw Fail{set_err(BEM_E_ARG, "far field: expansion length " + std::to_string(D->L) +
+                                                      " exceeds the translation-table limit " +
+                                                      std::to_string(kMaxTableL))};
+                k_dtable<<<D->noff, 128, 0, s>>>(D->ll->offs.p, D->noff, D->dirs_d.p, D->nd, D->L, k, D->D.p);
             }
             ck_launch("k_dtable");
         }
@@ -871,10 +875,13 @@ PrepArgs prep_args(bem_mesh_impl &M, const float2 *cp, const float2 *cq, const f
 // perm_in, else internal (optionally x + (*jidx) n).  y: caller order when
 // perm_out.  use_store: use the stored near-field values.  prepared: the
 // product inputs (x_int and the far-field weights) are already formed and x
-// is unused.
+// is unused.  far_only: y receives the far-field part alone and the
+// near-field part stays in M.ynear (the caller adds them); the whole far
+// chain (aggregation, transfer, disaggregation) then runs on the side
+// stream beside the near-field product.
 void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool use_store, const float2 *x,
                      const int *jidx, bool perm_in, float2 *y, bool perm_out, const int *skip, cudaStream_t s,
-                     bool prepared = false)
+                     bool prepared = false, bool far_only = false)
 {
     Plan &P = *M.plan;
     const int64_t n = M.n;
@@ -943,25 +950,30 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     da.perm = perm_out ? M.perm.p : nullptr;
     da.k = (float)P.k;
     da.nlev = (int)P.lev.size();
-    if (fork) {
+    if (fork && !far_only) {
         ck(cudaEventRecord(M.ev_join, sf), "record join");
         ck(cudaStreamWaitEvent(s, M.ev_join, 0), "wait join");
     }
+    cudaStream_t sd = far_only ? sf : s;
     for (int l = 0; l < A.nlev; ++l) da.lev[l] = A.lev[l];
     da.leaf_start = P.lists->leaf_start.p;
     da.sum_nd = 0;
     for (int l = 0; l < A.nlev; ++l) da.sum_nd += A.lev[l].nd;
     {
-        KTimer kt_("k_disaggregate", s);
+        KTimer kt_("k_disaggregate", sd);
         const int nleaf = (int)(P.lists->leaf_start.n - 1);
         const size_t smem = (size_t)std::max(2, da.sum_nd) / 2 * sizeof(float4) + (size_t)da.sum_nd * sizeof(float2);
         if (smem > kDisaggSmem)
             throw Fail{set_err(BEM_E_ARG, "far field: " + std::to_string(da.sum_nd) +
                                               " directions over all levels exceed the disaggregation kernel's "
                                               "shared-memory staging")};
-        k_disaggregate<<<nleaf, 128, smem, s>>>(da, M.ynear.p, y, skip);
+        k_disaggregate<<<nleaf, 128, smem, sd>>>(da, far_only ? nullptr : M.ynear.p, y, skip);
     }
     ck_launch("k_disaggregate");
+    if (fork && far_only) {
+        ck(cudaEventRecord(M.ev_join, sf), "record join");
+        ck(cudaStreamWaitEvent(s, M.ev_join, 0), "wait join");
+    }
 }
 
 // Leaf-size autotuner: builds the geometric lists for the automatic leaf
@@ -1465,6 +1477,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         ga.normpart = M.normpart.p;
         ga.m = m;
         oa.next = prep_args(M, M.cp.p, M.cq.p, nullptr);
+        oa.wnear = M.ynear.p;
         oa.bar = M.gbar.p;
         oa.err = &M.st.p->fault;
         oa.rows = orows;
@@ -1505,7 +1518,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         auto arnoldi_steps = [&](int nsteps) {
             const bool side = use_graph;
             for (int t = 0; t < nsteps; ++t) {
-                matvec_internal(M, M.cp.p, M.cq.p, true, nullptr, nullptr, false, M.w.p, false, done, s, true);
+                matvec_internal(M, M.cp.p, M.cq.p, true, nullptr, nullptr, false, M.w.p, false, done, s, true, true);
                 if (side && t > 0) ck(cudaStreamWaitEvent(s, M.ev_giv[t - 1], 0), "wait givens");
                 ortho();
                 if (side) {

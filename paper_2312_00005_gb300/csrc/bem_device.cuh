@@ -60,6 +60,19 @@ __device__ __forceinline__ float3 mad3(float s, float3 a, float3 b)
     return make_float3(fmaf(s, a.x, b.x), fmaf(s, a.y, b.y), fmaf(s, a.z, b.z));
 }
 
+// sin and cos of 2 pi t, t in turns: t - round(t) is exact, so the
+// reduction adds no error; then the SFU approximations on [-pi, pi]
+// (absolute error about 2^-21).  Used for the phases e^{ikr} of the regular
+// quadrature points and of the far field.  The unit tests compare it with
+// CUDA's sincospif.
+__device__ __forceinline__ void sincos_turns(float t, float *s, float *c)
+{
+    // round to the nearest integer by adding and removing 1.5 2^23 (exact
+    // for |t| < 2^22; the phases stay far below)
+    const float r = t - __fsub_rn(__fadd_rn(t, 12582912.f), 12582912.f);
+    __sincosf(r * 6.28318548f, s, c);
+}
+
 // ------------------------------------------------------------------ kernels
 // Burton-Miller column kernels at one quadrature point (Eq. SystemI, tau = 1,
 // gamma = i/k), with d = y - x, weight w:
@@ -77,7 +90,7 @@ __device__ __forceinline__ void bm_point(float3 d, float3 nx, float3 ny, float k
     float ir = rsqrtf(r2);
     float r = r2 * ir;
     float s, c;
-    sincosf(k * r, &s, &c);
+    sincos_turns(k * r * 0.15915494309189535f, &s, &c);
     float g = w * ir * kInv4Pi;
     float2 G = make_float2(c * g, s * g);
     float rx = dot3f(d, nx) * ir, ry = dot3f(d, ny) * ir, nn = dot3f(nx, ny);
@@ -96,7 +109,7 @@ __device__ __forceinline__ void gh_point(float3 d, float3 ny, float k, float w, 
     float ir = rsqrtf(r2);
     float r = r2 * ir;
     float s, c;
-    sincosf(k * r, &s, &c);
+    sincos_turns(k * r * 0.15915494309189535f, &s, &c);
     float g = w * ir * kInv4Pi;
     float2 Gp = make_float2(c * g, s * g);
     float ry = dot3f(d, ny) * ir;
@@ -105,17 +118,6 @@ __device__ __forceinline__ void gh_point(float3 d, float3 ny, float k, float w, 
     H = cfma(Gp, make_float2(-ir * ry, k * ry), H);
 }
 
-// sin and cos of 2 pi t for the far-field phases, t in turns: t - round(t)
-// is exact, so the reduction adds no error; then the SFU approximations on
-// [-pi, pi] (absolute error about 2^-21).  The unit tests compare it with
-// CUDA's sincospif.
-__device__ __forceinline__ void sincos_turns(float t, float *s, float *c)
-{
-    // round to the nearest integer by adding and removing 1.5 2^23 (exact
-    // for |t| < 2^22; the far-field phases stay far below)
-    const float r = t - __fsub_rn(__fadd_rn(t, 12582912.f), 12582912.f);
-    __sincosf(r * 6.28318548f, s, c);
-}
 
 // Rule code for a (sub)element: 0 = subdivide, m >= 1 = regular order m.
 __device__ __forceinline__ int rule_from_rt(float rt, const QuadTables &Q)
@@ -184,6 +186,32 @@ __device__ bool integrate_regular(const ElemDev &E, int64_t j, float3 xhi, float
         if (rt0 > Q.R[1] * (1.0f + 1e-5f)) {
             if (kField) gh_point(D0, ny, k, area, A0, A1);
             else bm_point(D0, nx, ny, k, ik_inv, area, A0, A1);
+            return true;
+        }
+    }
+    // Whole element under one regular rule (no subdivision): the common
+    // case, handled without the subdivision stack.  Same decision as the
+    // first step of the loop below (the unit triangle's centroid is x_j).
+    {
+        const float rt = sqrtf(dot3f(D0, D0) / area);
+        int code;
+        if (!rt_ambiguous(rt, Q)) {
+            code = rule_from_rt(rt, Q);
+        } else {
+            double d[3];
+            for (int q = 0; q < 3; ++q)
+                d[q] = (xd[q] - E.cd[3 * j + q]) -
+                       (E.vad[3 * j + q] + (1.0 / 3.0) * E.e1d[3 * j + q] + (1.0 / 3.0) * E.e2d[3 * j + q]);
+            code = rule_from_rt_d(sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) / sqrt(E.ad[j]), Q);
+        }
+        if (code > 0) {
+            const int nq = code * code;
+            for (int q = 0; q < nq; ++q) {
+                const float3 d = mad3(Q.tri_eta[code][q], e2, mad3(Q.tri_xi[code][q], e1, base));
+                const float w = 2.0f * area * Q.tri_w[code][q];
+                if (kField) gh_point(d, ny, k, w, A0, A1);
+                else bm_point(d, nx, ny, k, ik_inv, w, A0, A1);
+            }
             return true;
         }
     }

@@ -462,7 +462,8 @@ __global__ void k_transfer(const LevelsArgs *__restrict__ A, const int *skip)
 }
 
 // Disaggregation over all levels (Sec. 3.3.3, matrix S(l), with the
-// Burton-Miller row operator 1 + s.n_i) and the final sum with the near field:
+// Burton-Miller row operator 1 + s.n_i) and the sum with the near field
+// (when ynear is given; else y receives the far part alone):
 //   y_i = near_i + (ik/16 pi^2) sum_l sum_nu w_nu (1 + s_nu.n_i)
 //                   e^{ik (x_i - z_t).s_nu} Lambda_t(nu).
 // One block per leaf: the elements of a leaf share their cluster at every
@@ -565,7 +566,8 @@ __global__ void __launch_bounds__(128, 8) k_disaggregate(DisaggArgs a, const flo
             const int64_t i = c0 + q;
             // (ik / 16 pi^2) v
             const float sc = a.k * 0.00633257397764611f;   // k / (16 pi^2)
-            const float2 out = cadd(ynear[i], make_float2(-sc * v.y, sc * v.x));
+            const float2 far = make_float2(-sc * v.y, sc * v.x);
+            const float2 out = ynear ? cadd(ynear[i], far) : far;
             if (a.perm) y[a.perm[i]] = out;
             else y[i] = out;
         }
@@ -579,42 +581,70 @@ __global__ void __launch_bounds__(128, 8) k_disaggregate(DisaggArgs a, const flo
 __global__ void k_dtable(const double *__restrict__ offs, int noff, const double *__restrict__ dirs, int nd,
                          int L, double k, float2 *__restrict__ D)
 {
-    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= (int64_t)noff * nd) return;
-    const int o = (int)(id / nd), nu = (int)(id % nd);
+    // one block per offset X: the coefficients c_n = (2n+1) i^n h_n(k|X|)
+    // depend on X only and are formed once (thread 0, upward recursion);
+    // threads then take antipodal direction pairs (s, -s): with
+    // P_n(-t) = (-1)^n P_n(t), the even and odd partial sums give both
+    // D(X, s) = E + O and D(X, -s) = E - O.
+    __shared__ double2 cn[kMaxTableL + 1];
+    __shared__ double inv[kMaxTableL + 1];
+    const int o = blockIdx.x;
     const double X0 = offs[3 * o], X1 = offs[3 * o + 1], X2 = offs[3 * o + 2];
     const double R = sqrt(X0 * X0 + X1 * X1 + X2 * X2);
-    const double x = k * R;
-    const double t = (X0 * dirs[3 * nu] + X1 * dirs[3 * nu + 1] + X2 * dirs[3 * nu + 2]) / R;
-    double sx, cx;
-    sincos(x, &sx, &cx);
-    // h_0 = -i e^{ix}/x, h_1 = -e^{ix}(x + i)/x^2
-    double h0r = sx / x, h0i = -cx / x;
-    double h1r = -(cx * x - sx) / (x * x), h1i = -(sx * x + cx) / (x * x);
-    double p0 = 1.0, p1 = t;
-    double sr = h0r, si = h0i;                      // n = 0 term: i^0 * 1 * h0 * 1
-    if (L >= 1) {                                   // n = 1: i * 3 * h1 * t
-        sr += -3.0 * h1i * t;
-        si += 3.0 * h1r * t;
-    }
-    for (int n = 1; n < L; ++n) {
-        const double f = (2.0 * n + 1.0) / x;
-        const double h2r = f * h1r - h0r, h2i = f * h1i - h0i;
-        const double p2 = ((2.0 * n + 1.0) * t * p1 - n * p0) / (n + 1.0);
-        const int m = n + 1;
-        const double c = (2.0 * m + 1.0) * p2;
-        // i^m (h2r + i h2i) c
-        double ar = h2r * c, ai = h2i * c;
-        switch (m & 3) {
-            case 0: sr += ar; si += ai; break;
-            case 1: sr -= ai; si += ar; break;
-            case 2: sr -= ar; si -= ai; break;
-            default: sr += ai; si -= ar; break;
+    if (threadIdx.x == 0) {
+        const double x = k * R;
+        double sx, cx;
+        sincos(x, &sx, &cx);
+        // h_0 = -i e^{ix}/x, h_1 = -e^{ix}(x + i)/x^2
+        double h0r = sx / x, h0i = -cx / x;
+        double h1r = -(cx * x - sx) / (x * x), h1i = -(sx * x + cx) / (x * x);
+        const double ix = 1.0 / x;
+        for (int n = 0; n <= L; ++n) {
+            double hr, hi;
+            if (n == 0) { hr = h0r; hi = h0i; }
+            else if (n == 1) { hr = h1r; hi = h1i; }
+            else {
+                const double f = (2.0 * n - 1.0) * ix;
+                hr = f * h1r - h0r;
+                hi = f * h1i - h0i;
+                h0r = h1r; h0i = h1i; h1r = hr; h1i = hi;
+            }
+            // (2n+1) i^n h_n
+            const double c = 2.0 * n + 1.0;
+            double ar = c * hr, ai = c * hi;
+            switch (n & 3) {
+                case 0: cn[n] = make_double2(ar, ai); break;
+                case 1: cn[n] = make_double2(-ai, ar); break;
+                case 2: cn[n] = make_double2(-ar, -ai); break;
+                default: cn[n] = make_double2(ai, -ar); break;
+            }
+            inv[n] = 1.0 / (n + 1.0);
         }
-        h0r = h1r; h0i = h1i; h1r = h2r; h1i = h2i;
-        p0 = p1; p1 = p2;
     }
-    D[id] = make_float2((float)sr, (float)si);
+    __syncthreads();
+    const double iR = 1.0 / R;
+    const int h = nd / 2;
+    float2 *__restrict__ Drow = D + (int64_t)o * nd;
+    for (int p = threadIdx.x; p < h; p += blockDim.x) {
+        const double t = (X0 * dirs[3 * p] + X1 * dirs[3 * p + 1] + X2 * dirs[3 * p + 2]) * iR;
+        double p0 = 1.0, p1 = t;
+        double er = cn[0].x, ei = cn[0].y, odr = 0.0, odi = 0.0;
+        if (L >= 1) {
+            odr = cn[1].x * t;
+            odi = cn[1].y * t;
+        }
+        for (int n = 1; n < L; ++n) {
+            // P_{n+1} = ((2n+1) t P_n - n P_{n-1}) / (n+1)
+            const double p2 = ((2.0 * n + 1.0) * t * p1 - n * p0) * inv[n];
+            const double2 c = cn[n + 1];
+            if (n & 1) { er = fma(c.x, p2, er); ei = fma(c.y, p2, ei); }
+            else { odr = fma(c.x, p2, odr); odi = fma(c.y, p2, odi); }
+            p0 = p1;
+            p1 = p2;
+        }
+        Drow[p] = make_float2((float)(er + odr), (float)(ei + odi));
+        Drow[p + h] = make_float2((float)(er - odr), (float)(ei - odi));
+    }
 }
 
 // ------------------------------------------------------------------ incident field
@@ -967,7 +997,8 @@ __global__ void __launch_bounds__(kOrthoThreads) k_gm_ortho(OrthoArgs a)
     __shared__ float red[kOrthoThreads / 32];
     __shared__ float s_hh;
     __shared__ double s_nn;
-    for (int i = threadIdx.x; i < R; i += kOrthoThreads) ws[i] = g.w[r0 + i];
+    // w = A v_j: far part (g.w) + near part
+    for (int i = threadIdx.x; i < R; i += kOrthoThreads) ws[i] = cadd(g.w[r0 + i], a.wnear[r0 + i]);
     __syncthreads();
     double nn = 0.0;
     for (int pass = 0; pass < 2; ++pass) {

@@ -139,6 +139,8 @@ __global__ void k_aggregate(const LevelsArgs *A, const float4 *wts, const float4
 __global__ void k_selftest_sincos(const float *x, int64_t n, float4 *out);
 __global__ void k_transfer(const LevelsArgs *A, const int *skip);
 __global__ void k_disaggregate(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
+// largest expansion length of the translation tables (shared-memory rows)
+constexpr int kMaxTableL = 255;
 __global__ void k_dtable(const double *offs, int noff, const double *dirs, int nd, int L, double k, float2 *D);
 __global__ void k_rhs(const double *cd, const float4 *nrm, int64_t n, double k, const SourceDev *src, int nsrc,
                       float2 *b);
@@ -169,6 +171,7 @@ struct GmresArgs {
 struct OrthoArgs {
     GmresArgs g;             // g.nblk = gridDim.x; g.part [m + 1][nblk], g.normpart [nblk]
     PrepArgs next;           // inputs of the next product, formed from V_{j+1}
+    const float2 *wnear;     // near-field part of the product (g.w holds the far part)
     unsigned int *bar;       // [2] grid barrier: arrivals, generation (zero at the first launch)
     int *err;                // &st->fault
     int rows;                // rows of the basis per block
