@@ -200,6 +200,7 @@ struct Lists {
     // all levels together, for the one-launch far-field kernels
     DevArr<AggTask> all_tasks;
     DevArr<int2> all_reds, all_targets;
+    std::vector<int2> h_targets;   // host copy of all_targets
     DevArr<unsigned int> red_cnt;
     int n_tasks = 0, n_reds = 0, n_targets = 0;
     // expensive near pairs (row, position), listed on first use
@@ -248,6 +249,7 @@ struct LevelDev {
 };
 
 struct Plan {
+    DevArr<int4> tgroups;         // transfer blocks (level, target, first direction)
     double freq = -1.0, c = -1.0, k = 0.0;
     std::shared_ptr<Lists> lists;
     bool shared_lists = false;
@@ -484,6 +486,7 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
     Ls->all_tasks.upload(all_tasks, s);
     Ls->all_reds.upload(all_reds, s);
     Ls->all_targets.upload(all_targets, s);
+    Ls->h_targets = all_targets;
     Ls->red_cnt.alloc(std::max(1, Ls->n_reds));
     ck(cudaMemsetAsync(Ls->red_cnt.p, 0, std::max(1, Ls->n_reds) * sizeof(unsigned int), s), "memset");
     ck(cudaStreamSynchronize(s), "sync");
@@ -608,6 +611,16 @@ void finish_plan(bem_mesh_impl &M, Plan &Pl)
     A.nreds = P->lists->n_reds;
     A.targets = P->lists->all_targets.p;
     A.ntargets = P->lists->n_targets;
+    {
+        // transfer blocks for this plan's expansion lengths: (level, target,
+        // first direction)
+        std::vector<int4> tg;
+        for (const int2 &lt : P->lists->h_targets)
+            for (int nu0 = 0; nu0 < P->lev[lt.x]->nd; nu0 += kTransferDirs) tg.push_back(make_int4(lt.x, lt.y, nu0, 0));
+        P->tgroups.upload(tg, s);
+        A.tgroups = P->tgroups.p;
+        A.ntgroups = (int)tg.size();
+    }
     A.red_cnt = P->lists->red_cnt.p;
     for (size_t l = 0; l < P->lev.size(); ++l) {
         A.lev[l] = P->lev[l]->args();
@@ -914,9 +927,9 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
         ck_launch("k_aggregate");
     }
     if (A.ntargets > 0) {
-        {
+        if (A.ntgroups > 0) {
             KTimer kt_("k_transfer", sf);
-            k_transfer<<<A.ntargets, 128, 0, sf>>>(P.largs.p, skip);
+            k_transfer_split<<<A.ntgroups, 256, 0, sf>>>(P.largs.p, skip);
         }
         ck_launch("k_transfer");
     }
@@ -1278,6 +1291,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         M->type.upload(ty, s);
         ck(cudaFuncSetAttribute(k_near_spmv_items, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024),
            "cudaFuncSetAttribute");
+
         ck(cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 100 * 16),
            "cudaFuncSetAttribute");
         ck(cudaFuncSetAttribute(k_disaggregate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDisaggSmem),

@@ -416,48 +416,49 @@ __global__ void k_selftest_sincos(const float *__restrict__ x, int64_t n, float4
 // Diagonal transfer (Sec. 3.3.3, matrix D(l)): for every target cluster t
 // with an interaction list (Sec. 3.3.4),
 //   Lambda_t(nu) = sum_{s in I(t)} D_L(z_t - z_s, s_nu) M_s(nu).
-__global__ void k_transfer(const LevelsArgs *__restrict__ A, const int *skip)
+// Each target's interaction list is split among the warps of a block: a
+// block takes one target and kTransferDirs
+// directions (lanes), its 8 warps take every 8th entry, and the partial sums
+// are added in warp order.  Short dependent load chains per warp and many
+// blocks keep enough D and M loads in flight to cover the L2 latency.
+__global__ void __launch_bounds__(256) k_transfer_split(const LevelsArgs *__restrict__ A, const int *skip)
 {
     if (skip_now(skip)) return;
-    const int2 lt = A->targets[blockIdx.x];
-    const FarArgs &f = A->lev[lt.x];
-    const int t = lt.y;
+    __shared__ float2 part[8][kTransferDirs];
+    const int4 T = A->tgroups[blockIdx.x];
+    const FarArgs &f = A->lev[T.x];
+    const int t = T.y, nu0 = T.z, nd = f.nd;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nu = nu0 + lane;
+    const bool live = nu < nd;
     const int b = f.il_ptr[t], e = f.il_ptr[t + 1];
-    if (b == e) return;
-    __shared__ int s_src[256], s_off[256];
-    for (int nu0 = 0; nu0 < f.nd; nu0 += blockDim.x) {
-        const int nu = nu0 + threadIdx.x;
-        float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
-        for (int q0 = b; q0 < e; q0 += 256) {
-            const int cnt = min(256, e - q0);
-            __syncthreads();
-            for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-                s_src[q] = f.il_src[q0 + q] * f.nd;
-                s_off[q] = f.il_off[q0 + q] * f.nd;
-            }
-            __syncthreads();
-            if (nu < f.nd) {
-                int q = 0;
-                for (; q + 7 < cnt; q += 8) {
-                    float2 Dv[8], Mv[8];
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+    if (live) {
+        int q = b + warp;
+        for (; q + 24 < e; q += 32) {
+            float2 dv[4], mv[4];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        Dv[u] = f.D[s_off[q + u] + nu];
-                        Mv[u] = f.M[s_src[q + u] + nu];
-                    }
-                    acc0 = cfma(Dv[0], Mv[0], acc0);
-                    acc1 = cfma(Dv[1], Mv[1], acc1);
-                    acc2 = cfma(Dv[2], Mv[2], acc2);
-                    acc3 = cfma(Dv[3], Mv[3], acc3);
-                    acc0 = cfma(Dv[4], Mv[4], acc0);
-                    acc1 = cfma(Dv[5], Mv[5], acc1);
-                    acc2 = cfma(Dv[6], Mv[6], acc2);
-                    acc3 = cfma(Dv[7], Mv[7], acc3);
-                }
-                for (; q < cnt; ++q) acc0 = cfma(f.D[s_off[q] + nu], f.M[s_src[q] + nu], acc0);
+            for (int u = 0; u < 4; ++u) {
+                const int qq = q + 8 * u;
+                dv[u] = __ldg(f.D + (int64_t)__ldg(f.il_off + qq) * nd + nu);
+                mv[u] = f.M[(int64_t)__ldg(f.il_src + qq) * nd + nu];
             }
+            acc0 = cfma(dv[0], mv[0], acc0);
+            acc1 = cfma(dv[1], mv[1], acc1);
+            acc0 = cfma(dv[2], mv[2], acc0);
+            acc1 = cfma(dv[3], mv[3], acc1);
         }
-        if (nu < f.nd) f.Lam[(int64_t)t * f.nd + nu] = cadd(cadd(acc0, acc1), cadd(acc2, acc3));
+        for (; q < e; q += 8)
+            acc0 = cfma(__ldg(f.D + (int64_t)__ldg(f.il_off + q) * nd + nu),
+                        f.M[(int64_t)__ldg(f.il_src + q) * nd + nu], acc0);
+    }
+    part[warp][lane] = cadd(acc0, acc1);
+    __syncthreads();
+    if (warp == 0 && live) {
+        float2 sum = part[0][lane];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) sum = cadd(sum, part[w][lane]);
+        f.Lam[(int64_t)t * nd + nu] = sum;
     }
 }
 

@@ -101,6 +101,8 @@ struct LevelsArgs {
     int nreds;
     const int2 *targets;     // (level, target cluster) pairs with interaction lists
     int ntargets;
+    const int4 *tgroups;     // transfer blocks: (level, target cluster, first direction, 0)
+    int ntgroups;
     unsigned int *red_cnt;   // arrival counters of the split clusters (zero between uses)
     FarArgs lev[kMaxFarLevels];
 };
@@ -137,7 +139,10 @@ __global__ void k_near_fused(NearArgs a, const float2 *x, float2 *y, int *err, c
 __global__ void k_prep(PrepArgs a, const int *skip);
 __global__ void k_aggregate(const LevelsArgs *A, const float4 *wts, const float4 *nrm, const int *skip);
 __global__ void k_selftest_sincos(const float *x, int64_t n, float4 *out);
-__global__ void k_transfer(const LevelsArgs *A, const int *skip);
+// Transfer with the interaction list of one target split among 8 warps:
+// one block per (target, kTransferDirs directions).
+constexpr int kTransferDirs = 32;
+__global__ void k_transfer_split(const LevelsArgs *A, const int *skip);
 __global__ void k_disaggregate(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
 // largest expansion length of the translation tables (shared-memory rows)
 constexpr int kMaxTableL = 255;
