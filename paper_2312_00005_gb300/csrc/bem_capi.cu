@@ -359,7 +359,12 @@ QuadTables make_tables(const bem_params &p)
     for (int i = 0; i < 3; ++i) { Q.gl3_x[i] = (float)x[i]; Q.gl3_w[i] = (float)w[i]; }
     double R[kMaxRule + 1] = {0};
     order_thresholds(p.quad_tol, p.m_max, R);
-    for (int m = 1; m < p.m_max; ++m) { Q.R[m] = (float)R[m]; Q.Rd[m] = R[m]; }
+    for (int m = 1; m < p.m_max; ++m) {
+        Q.R[m] = (float)R[m];
+        Q.Rd[m] = R[m];
+        Q.R2[m] = (float)(R[m] * R[m]);
+    }
+    Q.heavy_rt2 = p.m_max > 3 ? (float)((R[3] * (1.0 + 1e-5)) * (R[3] * (1.0 + 1e-5))) : 0.f;
     Q.rt_sub = (float)p.rt_subdiv;
     Q.rt_sub_d = p.rt_subdiv;
     Q.m_max = p.m_max;
@@ -816,7 +821,9 @@ void store_near(bem_mesh_impl &M, Plan &P, const float2 *cp, const float2 *cq)
     }
     {
         KTimer kt_("k_near_store", M.s);
-        k_near_store_light<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, P.val.p, M.err.p);
+        const int nleaf = (int)(P.lists->leaf_start.n - 1);
+        const dim3 grid(nleaf, nblocks(std::max(1, P.lists->max_ncol), 256));
+        k_near_store_light<<<grid, 256, 0, M.s>>>(a, P.val.p, M.err.p);
     }
     ck_launch("k_near_store");
     if (Ls.n_heavy > 0) {

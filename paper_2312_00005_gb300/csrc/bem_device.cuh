@@ -18,6 +18,10 @@ struct QuadTables {
     double Rd[kRules];
     float rt_sub;
     double rt_sub_d;
+    // squared thresholds of the light / heavy split: a pair is light when
+    // r~^2 > heavy_rt2 = (R_3 (1 + 1e-5))^2; R2[m] = R_m^2
+    float R2[kRules];
+    float heavy_rt2;
     int m_max;
     int max_depth;
     int edge_parts;
@@ -143,18 +147,25 @@ __device__ __forceinline__ bool rt_ambiguous(float rt, const QuadTables &Q)
     return false;
 }
 
+// r~^2 of the whole element j seen from x (x_j - x from high / low parts,
+// 1/area_j given), with every rounding spelled out so that the classifier
+// and the light-entry kernel derive the same bits.
+__device__ __forceinline__ float pair_rt2(float3 xj_hi, float3 xj_lo, float3 xi_hi, float3 xi_lo, float inv_area,
+                                          float3 &D0)
+{
+    D0 = make_float3(__fadd_rn(__fsub_rn(xj_hi.x, xi_hi.x), __fsub_rn(xj_lo.x, xi_lo.x)),
+                     __fadd_rn(__fsub_rn(xj_hi.y, xi_hi.y), __fsub_rn(xj_lo.y, xi_lo.y)),
+                     __fadd_rn(__fsub_rn(xj_hi.z, xi_hi.z), __fsub_rn(xj_lo.z, xi_lo.z)));
+    return __fmul_rn(__fmaf_rn(D0.x, D0.x, __fmaf_rn(D0.y, D0.y, __fmul_rn(D0.z, D0.z))), inv_area);
+}
 // Expensive pair: the self term, or an element whose r~ (whole element) is
-// below R_3, i.e. that needs subdivision or a rule of order >= 4.  The cheap
-// pairs take 1 to 9 quadrature points.
-__device__ __forceinline__ bool heavy_pair(const ElemDev &E, int64_t i, int64_t j, float3 xhi, float3 xlo,
-                                           const QuadTables &Q)
+// not clearly above R_3, i.e. that may need subdivision or a rule of order
+// >= 4.  The cheap pairs take 1 to 9 quadrature points.
+__device__ __forceinline__ bool heavy_rt2(int64_t i, int64_t j, float rt2, const QuadTables &Q)
 {
     if (i == j) return true;
     if (Q.m_max <= 3) return false;
-    const float4 ch = E.chi[j], cl = E.clo[j];
-    const float3 D0 = add3(sub3f(f3(ch), xhi), sub3f(f3(cl), xlo));
-    const float rt0 = sqrtf(dot3f(D0, D0) / ch.w);
-    return !(rt0 > Q.R[3] * (1.0f + 1e-5f));
+    return !(rt2 > Q.heavy_rt2);
 }
 
 // Sub-triangle in the reference coordinates (xi, eta) of its element.

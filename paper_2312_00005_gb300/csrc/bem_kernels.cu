@@ -69,36 +69,170 @@ __global__ void k_near_classify(NearArgs a, int2 *__restrict__ heavy, unsigned l
     int r = a.N.run_ptr[t];
     for (int p = lane; p < nc; p += 32) {
         const int j = near_col(a.N, r_end, r, p);
-        if (!heavy_pair(a.E, i, j, xhi, xlo, Q)) continue;
+        const float4 cj = a.E.chi[j];
+        float3 D0;
+        const float rt2 = pair_rt2(f3(cj), f3(a.E.clo[j]), xhi, xlo, __frcp_rn(cj.w), D0);
+        if (!heavy_rt2(i, j, rt2, Q)) continue;
         const unsigned long long q = atomicAdd(count, 1ull);
         if (heavy && q < cap) heavy[q] = make_int2((int)i, p);
     }
 }
 
-// Stored near field, cheap pairs: as k_near_store but leaving the expensive
-// pairs to k_near_store_heavy (so no warp waits on a lane with 100+ points).
-__global__ void k_near_store_light(NearArgs a, float2 *__restrict__ val, int *__restrict__ err)
+// Near-field entries except the expensive pairs (self, order >= 4 or
+// subdivided: k_near_store_heavy).  One block per (leaf, 256 columns): a
+// thread holds its column's element data in registers and walks the leaf's
+// rows, whose data sit in shared memory (broadcast reads); the 32 columns of
+// a warp then write 32 consecutive values of one row.  r~ is compared in
+// squared form (FP64 when within 2e-5 of a threshold).
+constexpr int kLightRows = 64;
+// the general rule out of line, so that the common path keeps few registers
+__device__ __noinline__ bool general_entry(const ElemDev &E, int64_t i, int64_t j, float3 xhi, float3 xlo,
+                                           const double *xd, float3 nx, float k, float ik_inv, const QuadTables &Q,
+                                           float2 cpj, float2 cqj, float2 *out)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= a.E.n) return;
+    return bm_entry(E, i, j, xhi, xlo, xd, nx, k, ik_inv, Q, cpj, cqj, *out);
+}
+// Entry A_ij of order 2 or 3 over the whole element j (no subdivision).
+__device__ __forceinline__ float2 order23_entry(const ElemDev &E, int j, float3 D0, float3 nx, float k, float ik_inv,
+                                                const QuadTables &Q, int code, float2 cpj, float2 cqj)
+{
+    const float4 cj = E.chi[j];
+    const float3 ny = f3(E.nrm[j]), e1 = f3(E.e1[j]), e2 = f3(E.e2[j]);
+    const float3 base = add3(D0, f3(E.va[j]));          // a - x
+    float2 Kp = make_float2(0.f, 0.f), Kq = Kp;
+    const int nq = code * code;
+    for (int u = 0; u < nq; ++u) {
+        const float3 d = mad3(Q.tri_eta[code][u], e2, mad3(Q.tri_xi[code][u], e1, base));
+        bm_point(d, nx, ny, k, ik_inv, 2.0f * cj.w * Q.tri_w[code][u], Kp, Kq);
+    }
+    return cadd(cmul(cpj, Kp), cmul(cqj, Kq));
+}
+
+__global__ void __launch_bounds__(256) k_near_store_light(NearArgs a, float2 *__restrict__ val,
+                                                          int *__restrict__ err)
+{
+    __shared__ float4 s_hi[kLightRows], s_lo[kLightRows], s_n[kLightRows];
+    __shared__ double s_xd[kLightRows][3];
+    __shared__ int64_t s_rp[kLightRows];
+    // per warp: queued order-2 / order-3 entries (row slot, column position, column)
+    __shared__ int3 s_q[8][2][64];
+    const int t = blockIdx.x;
+    const int nc = a.N.ncol[t];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = blockIdx.y * blockDim.x + threadIdx.x;
+    if ((int)(blockIdx.y * blockDim.x) >= nc) return;
     const QuadTables &Q = *a.Q;
-    const float4 ch = a.E.chi[i], cl = a.E.clo[i];
-    const float3 xhi = f3(ch), xlo = f3(cl), nx = f3(a.E.nrm[i]);
-    const double xd[3] = {a.E.cd[3 * i], a.E.cd[3 * i + 1], a.E.cd[3 * i + 2]};
-    const int t = a.N.leaf_of[i];
-    const int r_end = a.N.run_ptr[t + 1], nc = a.N.ncol[t];
-    int r = a.N.run_ptr[t];
-    const int64_t base = a.N.row_ptr[i];
-    for (int p = lane; p < nc; p += 32) {
-        const int j = near_col(a.N, r_end, r, p);
-        if (heavy_pair(a.E, i, j, xhi, xlo, Q)) continue;
-        float2 v;
-        if (!bm_entry(a.E, i, j, xhi, xlo, xd, nx, a.k, a.ik_inv, Q, a.cp[j], a.cq[j], v)) {
-            atomicMin(err, j);
-            v = make_float2(0.f, 0.f);
+    const int64_t e0 = a.N.leaf_start[t], e1 = a.N.leaf_start[t + 1];
+    const bool live = p < nc;
+    const unsigned lt = (1u << lane) - 1u;
+    // this thread's column: binary search of the leaf's runs
+    int j = 0;
+    float4 cj = make_float4(0.f, 0.f, 0.f, 1.f), lj = cj, nj = cj;
+    float2 cpj = make_float2(0.f, 0.f), cqj = cpj;
+    if (live) {
+        int lo = a.N.run_ptr[t], hi = a.N.run_ptr[t + 1] - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.N.runs[mid].y <= p) lo = mid;
+            else hi = mid - 1;
         }
-        val[base + p] = v;
+        const int2 rr = a.N.runs[lo];
+        j = rr.x + (p - rr.y);
+        cj = a.E.chi[j];
+        lj = a.E.clo[j];
+        nj = a.E.nrm[j];
+        cpj = a.cp[j];
+        cqj = a.cq[j];
+    }
+    const float inv_area = __frcp_rn(cj.w);
+    int nq2 = 0, nq3 = 0;      // warp-uniform queue lengths
+    // computes 32 queued entries of order c (one per lane; fewer on a flush)
+    auto run_queue = [&](int c, int cnt) {
+        if (lane < cnt) {
+            const int3 e = s_q[warp][c - 2][lane];
+            const float4 cjq = a.E.chi[e.z];
+            float3 D0;
+            pair_rt2(f3(cjq), f3(a.E.clo[e.z]), f3(s_hi[e.x]), f3(s_lo[e.x]), __frcp_rn(cjq.w), D0);
+            val[s_rp[e.x] + e.y] = order23_entry(a.E, e.z, D0, f3(s_n[e.x]), a.k, a.ik_inv, Q, c, a.cp[e.z], a.cq[e.z]);
+        }
+        __syncwarp();
+        // keep the entries beyond the first 32
+        const int rest = cnt > 32 ? cnt - 32 : 0;
+        int3 keep = make_int3(0, 0, 0);
+        if (lane < rest) keep = s_q[warp][c - 2][32 + lane];
+        __syncwarp();
+        if (lane < rest) s_q[warp][c - 2][lane] = keep;
+        __syncwarp();
+        return rest;
+    };
+    for (int64_t b0 = e0; b0 < e1; b0 += kLightRows) {
+        const int nr = (int)min((int64_t)kLightRows, e1 - b0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+            s_hi[q] = a.E.chi[b0 + q];
+            s_lo[q] = a.E.clo[b0 + q];
+            s_n[q] = a.E.nrm[b0 + q];
+            s_xd[q][0] = a.E.cd[3 * (b0 + q)];
+            s_xd[q][1] = a.E.cd[3 * (b0 + q) + 1];
+            s_xd[q][2] = a.E.cd[3 * (b0 + q) + 2];
+            s_rp[q] = a.N.row_ptr[b0 + q];
+        }
+        __syncthreads();
+        for (int q = 0; q < nr; ++q) {
+            const int64_t i = b0 + q;
+            int code = -1;
+            float3 D0 = make_float3(0.f, 0.f, 0.f);
+            if (live) {
+                const float3 xhi = f3(s_hi[q]), xlo = f3(s_lo[q]);
+                const float rt2 = pair_rt2(f3(cj), f3(lj), xhi, xlo, inv_area, D0);
+                if (!heavy_rt2(i, j, rt2, Q)) {
+                    if (Q.m_max > 3) {
+                        const float g = 2e-5f;
+                        if (fabsf(rt2 - Q.R2[1]) <= g * Q.R2[1] || fabsf(rt2 - Q.R2[2]) <= g * Q.R2[2]) {
+                            double d[3];
+                            for (int c = 0; c < 3; ++c)
+                                d[c] = (s_xd[q][c] - a.E.cd[3 * j + c]) -
+                                       (a.E.vad[3 * j + c] + (1.0 / 3.0) * a.E.e1d[3 * j + c] +
+                                        (1.0 / 3.0) * a.E.e2d[3 * j + c]);
+                            code = rule_from_rt_d(sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) / sqrt(a.E.ad[j]), Q);
+                        } else {
+                            code = rt2 > Q.R2[1] ? 1 : (rt2 > Q.R2[2] ? 2 : 3);
+                        }
+                    } else {
+                        code = 0;
+                    }
+                }
+            }
+            if (code == 1) {
+                // the 1 x 1 conical rule is the centroid rule
+                float2 Kp = make_float2(0.f, 0.f), Kq = Kp;
+                bm_point(D0, f3(s_n[q]), f3(nj), a.k, a.ik_inv, cj.w, Kp, Kq);
+                val[s_rp[q] + p] = cadd(cmul(cpj, Kp), cmul(cqj, Kq));
+            } else if (code == 0) {
+                // subdivision or a high order (only when the heavy split is
+                // off, m_max <= 3): the general rule
+                const double xd[3] = {s_xd[q][0], s_xd[q][1], s_xd[q][2]};
+                float2 v;
+                if (!general_entry(a.E, i, j, f3(s_hi[q]), f3(s_lo[q]), xd, f3(s_n[q]), a.k, a.ik_inv, Q, cpj,
+                                   cqj, &v)) {
+                    atomicMin(err, j);
+                    v = make_float2(0.f, 0.f);
+                }
+                val[s_rp[q] + p] = v;
+            }
+            // queue orders 2 and 3 for batches of one order
+            const unsigned m2 = __ballot_sync(0xffffffffu, code == 2), m3 = __ballot_sync(0xffffffffu, code == 3);
+            if (code == 2) s_q[warp][0][nq2 + __popc(m2 & lt)] = make_int3(q, p, j);
+            if (code == 3) s_q[warp][1][nq3 + __popc(m3 & lt)] = make_int3(q, p, j);
+            nq2 += __popc(m2);
+            nq3 += __popc(m3);
+            __syncwarp();
+            if (nq2 >= 32) nq2 = run_queue(2, nq2);
+            if (nq3 >= 32) nq3 = run_queue(3, nq3);
+        }
+        // the rows' data are replaced next: flush
+        while (nq2 > 0) nq2 = run_queue(2, nq2);
+        while (nq3 > 0) nq3 = run_queue(3, nq3);
     }
 }
 
