@@ -797,23 +797,31 @@ void store_near(bem_mesh_impl &M, Plan &P, const float2 *cp, const float2 *cq)
     NearArgs a = near_args(M, P, cp, cq);
     Lists &Ls = *P.lists;
     if (Ls.n_heavy < 0) {
-        // count, then list, the expensive pairs of these lists (geometry only)
-        DevArr<unsigned long long> cnt;
-        cnt.alloc(1);
-        ck(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), M.s), "memset");
+        // count, then list, the expensive pairs of these lists (geometry
+        // only), grouped by kind
+        DevArr<unsigned long long> cnt, off;
+        cnt.alloc(kHeavyKinds);
+        off.alloc(kHeavyKinds);
+        ck(cudaMemsetAsync(cnt.p, 0, kHeavyKinds * sizeof(unsigned long long), M.s), "memset");
         {
             KTimer kt_("k_near_classify", M.s);
-            k_near_classify<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, nullptr, cnt.p, 0ull);
+            k_near_classify<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, nullptr, cnt.p, nullptr);
         }
         ck_launch("k_near_classify");
-        unsigned long long h = 0;
-        ck(cudaMemcpyAsync(&h, cnt.p, sizeof h, cudaMemcpyDeviceToHost, M.s), "D2H");
+        unsigned long long hk[kHeavyKinds], ho[kHeavyKinds];
+        ck(cudaMemcpyAsync(hk, cnt.p, sizeof hk, cudaMemcpyDeviceToHost, M.s), "D2H");
         ck(cudaStreamSynchronize(M.s), "sync");
+        unsigned long long h = 0;
+        for (int q = 0; q < kHeavyKinds; ++q) {
+            ho[q] = h;
+            h += hk[q];
+        }
         Ls.heavy.alloc(std::max<unsigned long long>(h, 1));
-        ck(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), M.s), "memset");
+        ck(cudaMemcpyAsync(off.p, ho, sizeof ho, cudaMemcpyHostToDevice, M.s), "H2D");
+        ck(cudaMemsetAsync(cnt.p, 0, kHeavyKinds * sizeof(unsigned long long), M.s), "memset");
         {
             KTimer kt_("k_near_classify", M.s);
-            k_near_classify<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, Ls.heavy.p, cnt.p, h);
+            k_near_classify<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, Ls.heavy.p, cnt.p, off.p);
         }
         ck_launch("k_near_classify");
         ck(cudaStreamSynchronize(M.s), "sync");

@@ -54,10 +54,13 @@ __global__ void k_near_store(NearArgs a, float2 *__restrict__ val, int *__restri
     }
 }
 
-// Lists the expensive near pairs (row, position) once per set of lists;
-// with heavy == nullptr only counts them.
+// Expensive pairs (heavy_rt2) of the stored near field, listed by kind so
+// that the warps of k_near_store_heavy take pairs of one kind: 0 = self term,
+// 1 = subdivided element, 1 + m = regular order m >= 4 (a sorting hint from
+// FP32 r~; the heavy kernel decides the rules itself).  Pass 1 (heavy null)
+// counts per kind; pass 2 writes each pair at off[kind] + its rank.
 __global__ void k_near_classify(NearArgs a, int2 *__restrict__ heavy, unsigned long long *count,
-                                unsigned long long cap)
+                                const unsigned long long *off)
 {
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -73,8 +76,18 @@ __global__ void k_near_classify(NearArgs a, int2 *__restrict__ heavy, unsigned l
         float3 D0;
         const float rt2 = pair_rt2(f3(cj), f3(a.E.clo[j]), xhi, xlo, __frcp_rn(cj.w), D0);
         if (!heavy_rt2(i, j, rt2, Q)) continue;
-        const unsigned long long q = atomicAdd(count, 1ull);
-        if (heavy && q < cap) heavy[q] = make_int2((int)i, p);
+        int kind;
+        if (i == j) {
+            kind = 0;
+        } else if (rt2 < Q.rt_sub * Q.rt_sub) {
+            kind = 1;
+        } else {
+            int m = 1;
+            while (m < Q.m_max && !(rt2 > Q.R2[m])) ++m;
+            kind = 1 + m;
+        }
+        const unsigned long long q = atomicAdd(count + kind, 1ull);
+        if (heavy) heavy[off[kind] + q] = make_int2((int)i, p);
     }
 }
 

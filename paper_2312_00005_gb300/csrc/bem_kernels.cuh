@@ -125,7 +125,8 @@ struct SourceDev {
 };
 
 __global__ void k_near_store(NearArgs a, float2 *val, int *err);
-__global__ void k_near_classify(NearArgs a, int2 *heavy, unsigned long long *count, unsigned long long cap);
+constexpr int kHeavyKinds = 8;          // self, subdivided, orders 2 .. 6 (see k_near_classify)
+__global__ void k_near_classify(NearArgs a, int2 *heavy, unsigned long long *count, const unsigned long long *off);
 __global__ void k_near_store_light(NearArgs a, float2 *val, int *err);
 __global__ void k_near_store_heavy(NearArgs a, const int2 *heavy, int64_t nheavy, float2 *val, int *err);
 __global__ void k_near_spmv(NearArgs a, const float2 *val, const float2 *x, float2 *y, const int *skip);
