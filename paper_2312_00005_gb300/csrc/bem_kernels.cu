@@ -626,10 +626,10 @@ __global__ void __launch_bounds__(128, 8) k_disaggregate(DisaggArgs a, const flo
                                const int *skip)
 {
     if (skip_now(skip)) return;
-    extern __shared__ float4 dsm[];   // [sum_nd / 2] first-half directions, then [sum_nd] w Lambda (float2)
+    extern __shared__ float4 dsm[];   // [sum_nd / 2] first-half directions, then [sum_nd / 2] (A, B) pairs
     float4 *dir_s = dsm;
-    float2 *lam_s = (float2 *)(dsm + a.sum_nd / 2);
-    __shared__ int s_lev[kMaxFarLevels], s_poff[kMaxFarLevels + 1], s_loff[kMaxFarLevels], s_h[kMaxFarLevels];
+    float4 *ab_s = dsm + a.sum_nd / 2;
+    __shared__ int s_lev[kMaxFarLevels], s_poff[kMaxFarLevels + 1];
     __shared__ int s_nact;
     __shared__ float4 dzs[kDisChunk][kMaxFarLevels];   // -k/(2 pi) (z_c - x_i) per active level
     __shared__ float4 ns[kDisChunk];
@@ -639,17 +639,14 @@ __global__ void __launch_bounds__(128, 8) k_disaggregate(DisaggArgs a, const flo
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) {
         // active levels (the leaf's cluster has an interaction list there)
-        int na = 0, poff = 0, loff = 0;
+        int na = 0, poff = 0;
         for (int l = 0; l < a.nlev; ++l) {
             const FarArgs &f = a.lev[l];
             const int c = f.elem_cl[e0];
             if (f.il_ptr[c] == f.il_ptr[c + 1]) continue;
             s_lev[na] = l;
             s_poff[na] = poff;
-            s_loff[na] = loff;
-            s_h[na] = f.nd / 2;
             poff += f.nd / 2;
-            loff += f.nd;
             ++na;
         }
         s_poff[na] = poff;
@@ -657,13 +654,19 @@ __global__ void __launch_bounds__(128, 8) k_disaggregate(DisaggArgs a, const flo
     }
     __syncthreads();
     const int na = s_nact, HP = s_poff[na];
+    // per antipodal pair p of each active level: the direction s_p and, with
+    // the weighted rows lp = w Lambda(s_p), lm = w Lambda(-s_p), A = lp + lm
+    // and B = lp - lm, so that (1 + t) lp + (1 - t) lm = A + t B and
+    // (1 + t) lp - (1 - t) lm = B + t A
     for (int u = 0; u < na; ++u) {
         const FarArgs &f = a.lev[s_lev[u]];
         const float2 *__restrict__ src = f.Lam + (int64_t)f.elem_cl[e0] * f.nd;
-        for (int nu = threadIdx.x; nu < f.nd; nu += blockDim.x) {
-            const float4 d = f.dirs[nu];
-            if (nu < f.nd / 2) dir_s[s_poff[u] + nu] = make_float4(d.x, d.y, d.z, __int_as_float(u));
-            lam_s[s_loff[u] + nu] = cscale(src[nu], d.w);
+        const int h = f.nd / 2;
+        for (int q = threadIdx.x; q < h; q += blockDim.x) {
+            const float4 d = f.dirs[q];
+            const float2 lp = cscale(src[q], d.w), lm = cscale(src[q + h], d.w);
+            dir_s[s_poff[u] + q] = make_float4(d.x, d.y, d.z, __int_as_float(u));
+            ab_s[s_poff[u] + q] = make_float4(lp.x + lm.x, lp.y + lm.y, lp.x - lm.x, lp.y - lm.y);
         }
     }
     for (int64_t c0 = e0; c0 < e1; c0 += kDisChunk) {
@@ -683,8 +686,7 @@ __global__ void __launch_bounds__(128, 8) k_disaggregate(DisaggArgs a, const flo
         for (int pf = threadIdx.x; pf < HP; pf += blockDim.x) {
             const float4 sv = dir_s[pf];
             const int u = __float_as_int(sv.w);
-            const int base = s_loff[u] + (pf - s_poff[u]);
-            const float2 lp = lam_s[base], lm = lam_s[base + s_h[u]];
+            const float4 ab = ab_s[pf];
 #pragma unroll
             for (int q = 0; q < kDisChunk; ++q) {
                 if (q < cnt) {
@@ -692,12 +694,11 @@ __global__ void __launch_bounds__(128, 8) k_disaggregate(DisaggArgs a, const flo
                     float sn0, cs0;
                     sincos_turns(fmaf(d.x, sv.x, fmaf(d.y, sv.y, d.z * sv.z)), &sn0, &cs0);
                     const float tn = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
-                    const float2 gp = cscale(lp, 1.f + tn), gm = cscale(lm, 1.f - tn);
-                    // (cs + i sn) gp + (cs - i sn) gm
-                    const float2 sp = make_float2(gp.x + gm.x, gp.y + gm.y);
-                    const float2 dm = make_float2(gp.x - gm.x, gp.y - gm.y);
-                    acc[q].x = fmaf(cs0, sp.x, fmaf(-sn0, dm.y, acc[q].x));
-                    acc[q].y = fmaf(cs0, sp.y, fmaf(sn0, dm.x, acc[q].y));
+                    // (cs + i sn)(1 + t) lp + (cs - i sn)(1 - t) lm = cs sp + i sn dm
+                    const float spx = fmaf(tn, ab.z, ab.x), spy = fmaf(tn, ab.w, ab.y);
+                    const float dmx = fmaf(tn, ab.x, ab.z), dmy = fmaf(tn, ab.y, ab.w);
+                    acc[q].x = fmaf(cs0, spx, fmaf(-sn0, dmy, acc[q].x));
+                    acc[q].y = fmaf(cs0, spy, fmaf(sn0, dmx, acc[q].y));
                 }
             }
         }
