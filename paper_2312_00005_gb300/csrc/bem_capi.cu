@@ -304,6 +304,7 @@ struct bem_mesh_impl {
     DevArr<SourceDev> srcbuf;
     DevArr<double> ptsbuf;
     std::map<int, std::unique_ptr<DepthDev>> depth_dev;
+    std::map<int, double> growth_root;                 // x*(L) of the Hankel stability test
     cudaStream_t s = nullptr;
     // side stream for the far-field upward pass, which runs beside the
     // near-field product (fork after k_prep, join before k_disaggregate)
@@ -657,16 +658,33 @@ void build_plan_dev(bem_mesh_impl &M, double freq, double c)
             M.geo_lists = upload_lists(M, std::move(fp));
         }
     }
+    // The Hankel growth sum_{n<=L}(2n+1)|h_n(x)|/|h_0(x)| decreases with x,
+    // so "stable" is x >= x*(L), the root of growth = stability_max, found
+    // once per L by bisection; the per-frequency reuse tests below then need
+    // no Hankel evaluations.
+    auto stable_from = [&](int L) {
+        auto it = M.growth_root.find(L);
+        if (it != M.growth_root.end()) return it->second;
+        double lo = 1e-9, hi = 1.0;
+        while (!(hankel_growth(hi, L) <= M.prm.stability_max)) hi *= 2.0;
+        for (int it2 = 0; it2 < 200 && hi - lo > 1e-13 * hi; ++it2) {
+            const double mid = 0.5 * (lo + hi);
+            if (hankel_growth(mid, L) <= M.prm.stability_max) hi = mid;
+            else lo = mid;
+        }
+        M.growth_root[L] = hi;
+        return hi;
+    };
     // reuse the geometric lists when every far offset passes the Hankel test
+    // (the shortest offset of each level decides)
     bool ok = true;
     for (const FarLevel &FL : M.geo_lists->fp.far) {
-        const int L = level_L(M, FL.depth, k);
-        for (size_t o = 0; ok && o < FL.offsets.size() / 3; ++o) {
-            const double X = std::sqrt(FL.offsets[3 * o] * FL.offsets[3 * o] + FL.offsets[3 * o + 1] * FL.offsets[3 * o + 1] +
-                                       FL.offsets[3 * o + 2] * FL.offsets[3 * o + 2]);
-            if (!(hankel_growth(k * X, L) <= M.prm.stability_max)) ok = false;
-        }
-        if (!ok) break;
+        double xmin = 1e300;
+        for (size_t o = 0; o < FL.offsets.size() / 3; ++o)
+            xmin = std::min(xmin, FL.offsets[3 * o] * FL.offsets[3 * o] + FL.offsets[3 * o + 1] * FL.offsets[3 * o + 1] +
+                                      FL.offsets[3 * o + 2] * FL.offsets[3 * o + 2]);
+        if (FL.offsets.empty()) continue;
+        if (!(k * std::sqrt(xmin) >= stable_from(level_L(M, FL.depth, k)))) { ok = false; break; }
     }
     // else reuse a recent frequency-specific build when every stability
     // verdict it evaluated (and the expansion length per depth) is unchanged:
@@ -682,7 +700,7 @@ void build_plan_dev(bem_mesh_impl &M, double freq, double c)
                 const Verdict &v = lf.verdicts[q];
                 const double b = M.t.lv[v.depth].box;
                 const double X = b * std::sqrt((double)v.dx * v.dx + (double)v.dy * v.dy + (double)v.dz * v.dz);
-                if ((hankel_growth(k * X, v.L) <= M.prm.stability_max) != v.stable) same = false;
+                if ((k * X >= stable_from(v.L)) != v.stable) same = false;
             }
             if (same) reuse = *it;
         }
