@@ -572,6 +572,7 @@ __global__ void __launch_bounds__(256) k_transfer_split(const LevelsArgs *__rest
 {
     if (skip_now(skip)) return;
     __shared__ float2 part[8][kTransferDirs];
+    __shared__ int2 s_ent[kTransferEntries];      // (source cluster, offset) of the list entries
     const int4 T = A->tgroups[blockIdx.x];
     const FarArgs &f = A->lev[T.x];
     const int t = T.y, nu0 = T.z, nd = f.nd;
@@ -580,24 +581,31 @@ __global__ void __launch_bounds__(256) k_transfer_split(const LevelsArgs *__rest
     const bool live = nu < nd;
     const int b = f.il_ptr[t], e = f.il_ptr[t + 1];
     float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
-    if (live) {
-        int q = b + warp;
-        for (; q + 24 < e; q += 32) {
+    for (int c0 = b; c0 < e; c0 += kTransferEntries) {
+        const int cnt = min(kTransferEntries, e - c0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x)
+            s_ent[q] = make_int2(f.il_src[c0 + q], f.il_off[c0 + q]);
+        __syncthreads();
+        if (!live) continue;
+        int q = warp;
+        for (; q + 24 < cnt; q += 32) {
             float2 dv[4], mv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int qq = q + 8 * u;
-                dv[u] = __ldg(f.D + (int64_t)__ldg(f.il_off + qq) * nd + nu);
-                mv[u] = f.M[(int64_t)__ldg(f.il_src + qq) * nd + nu];
+                const int2 en = s_ent[q + 8 * u];
+                dv[u] = __ldg(f.D + (int64_t)en.y * nd + nu);
+                mv[u] = f.M[(int64_t)en.x * nd + nu];
             }
             acc0 = cfma(dv[0], mv[0], acc0);
             acc1 = cfma(dv[1], mv[1], acc1);
             acc0 = cfma(dv[2], mv[2], acc0);
             acc1 = cfma(dv[3], mv[3], acc1);
         }
-        for (; q < e; q += 8)
-            acc0 = cfma(__ldg(f.D + (int64_t)__ldg(f.il_off + q) * nd + nu),
-                        f.M[(int64_t)__ldg(f.il_src + q) * nd + nu], acc0);
+        for (; q < cnt; q += 8) {
+            const int2 en = s_ent[q];
+            acc0 = cfma(__ldg(f.D + (int64_t)en.y * nd + nu), f.M[(int64_t)en.x * nd + nu], acc0);
+        }
     }
     part[warp][lane] = cadd(acc0, acc1);
     __syncthreads();

@@ -143,6 +143,7 @@ __global__ void k_selftest_sincos(const float *x, int64_t n, float4 *out);
 // Transfer with the interaction list of one target split among 8 warps:
 // one block per (target, kTransferDirs directions).
 constexpr int kTransferDirs = 32;
+constexpr int kTransferEntries = 512;     // interaction-list entries staged per pass
 __global__ void k_transfer_split(const LevelsArgs *A, const int *skip);
 __global__ void k_disaggregate(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
 // largest expansion length of the translation tables (shared-memory rows)
