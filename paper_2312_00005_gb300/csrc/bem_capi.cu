@@ -270,6 +270,16 @@ struct Coeffs {
 
 }  // namespace
 
+// The state of one frequency: plan, column coefficients, error flag.
+struct Frame {
+    std::unique_ptr<Plan> plan;
+    DevArr<float2> cp, cq, cp0, cq0, z, aq;    // column coefficients, known data (internal order)
+    DevArr<int> err;                           // first element whose subdivision failed
+    DevArr<float2> vtmp, vout;                 // scratch of the fused validation pass
+    cudaStream_t s = nullptr;                  // stream of this frame's setup work
+    bool known_nonzero = false;
+};
+
 struct bem_mesh_impl {
     int device = 0;
     bem_params prm;
@@ -282,8 +292,7 @@ struct bem_mesh_impl {
     DevArr<double> cd, vad, e1d, e2d, ad;
     DevArr<int64_t> perm;
     DevArr<QuadTables> Q;
-    DevArr<int> type, err;
-    DevArr<float2> cp, cq, cp0, cq0, z, aq;
+    DevArr<int> type;
     DevArr<float2> xint, ynear, tmp, tmp2, bvec, uvec;
     DevArr<float4> wts;          // far-field weights (alpha, c) per element
     // GMRES workspace
@@ -292,7 +301,11 @@ struct bem_mesh_impl {
     DevArr<double> normpart;
     DevArr<unsigned int> gbar;   // grid barrier of the fused Gram-Schmidt step
     DevArr<GmresState> st;
-    std::unique_ptr<Plan> plan;
+    // frequency state: cur serves the products and the solve; next is filled
+    // by the setup thread of a frequency sweep for the following frequency
+    // (its work on s_setup) while cur's GMRES runs
+    Frame cur, next;
+    cudaStream_t s_setup = nullptr;
     std::shared_ptr<Lists> geo_lists;                  // frequency-independent lists
     std::vector<std::shared_ptr<Lists>> freq_lists;    // recent frequency-specific builds (newest last)
     int leaf_depth = 0;                                // leaf depth of the lists (autotuned)
@@ -330,12 +343,18 @@ struct bem_mesh_impl {
             if (ev_giv[t]) cudaEventDestroy(ev_giv[t]);
         }
         if (s_giv) cudaStreamDestroy(s_giv);
+        if (s_setup) cudaStreamDestroy(s_setup);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
         if (s_far) cudaStreamDestroy(s_far);
         if (s) cudaStreamDestroy(s);
     }
 };
+
+// The frame the calling thread works on: a sweep's setup thread points this
+// at the mesh's next frame; every other caller uses cur.
+static thread_local Frame *t_frame = nullptr;
+static inline Frame &fr(bem_mesh_impl &M) { return t_frame ? *t_frame : M.cur; }
 
 namespace {
 
@@ -390,7 +409,7 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
     const FreqPlan &F = Ls->fp;
     const Level &Lf = M.t.lv[F.leaf_depth];
     const int nl = (int)Lf.start.size();
-    cudaStream_t s = M.s;
+    cudaStream_t s = fr(M).s;
     // near columns of each leaf as runs of consecutive leaves
     std::vector<int> run_ptr(nl + 1, 0), ncol(nl, 0);
     std::vector<int2> runs;
@@ -518,10 +537,10 @@ const DepthDev *depth_data(bem_mesh_impl &M, int depth)
         dz[i] = make_float4((float)(L.z[3 * cc] - M.g.cen[3 * e]), (float)(L.z[3 * cc + 1] - M.g.cen[3 * e + 1]),
                             (float)(L.z[3 * cc + 2] - M.g.cen[3 * e + 2]), 0.f);
     }
-    D->cstart.upload(cst, M.s);
-    D->dz.upload(dz, M.s);
-    D->elem_cl.upload(ecl, M.s);
-    ck(cudaStreamSynchronize(M.s), "sync");
+    D->cstart.upload(cst, fr(M).s);
+    D->dz.upload(dz, fr(M).s);
+    D->elem_cl.upload(ecl, fr(M).s);
+    ck(cudaStreamSynchronize(fr(M).s), "sync");
     const DepthDev *r = D.get();
     M.depth_dev[depth] = std::move(D);
     return r;
@@ -538,17 +557,17 @@ int level_L(const bem_mesh_impl &M, int depth, double k)
 // Moves the large buffers of the current plan into the mesh's spares.
 void recycle_plan(bem_mesh_impl &M)
 {
-    if (!M.plan) return;
-    ck(cudaStreamSynchronize(M.s), "sync");
-    M.spare_val.swap(M.plan->val);
-    for (auto &L : M.plan->lev) {
+    if (!fr(M).plan) return;
+    ck(cudaStreamSynchronize(fr(M).s), "sync");
+    M.spare_val.swap(fr(M).plan->val);
+    for (auto &L : fr(M).plan->lev) {
         for (DevArr<float2> *b : {&L->D, &L->M, &L->Lam}) {
             auto d = std::make_unique<DevArr<float2>>();
             d->swap(*b);
             M.spare_bufs.push_back(std::move(d));
         }
     }
-    M.plan.reset();
+    fr(M).plan.reset();
 }
 
 // Takes the spare buffer with the smallest sufficient capacity (or any).
@@ -572,7 +591,7 @@ void finish_plan(bem_mesh_impl &M, Plan &Pl)
 {
     Plan *P = &Pl;
     const double k = P->k;
-    cudaStream_t s = M.s;
+    cudaStream_t s = fr(M).s;
     const FreqPlan &fp = P->fp();
     for (size_t l = 0; l < fp.far.size(); ++l) {
         const FarLevel &F = fp.far[l];
@@ -641,7 +660,7 @@ void autotune_leaf_depth(bem_mesh_impl &M, double k);
 
 void build_plan_dev(bem_mesh_impl &M, double freq, double c)
 {
-    if (M.plan && M.plan->freq == freq && M.plan->c == c) return;
+    if (fr(M).plan && fr(M).plan->freq == freq && fr(M).plan->c == c) return;
     recycle_plan(M);
     auto P = std::make_unique<Plan>();
     P->freq = freq;
@@ -719,7 +738,7 @@ void build_plan_dev(bem_mesh_impl &M, double freq, double c)
         if (M.freq_lists.size() > 4) M.freq_lists.erase(M.freq_lists.begin());
     }
     finish_plan(M, *P);
-    M.plan = std::move(P);
+    fr(M).plan = std::move(P);
 }
 
 NearArgs near_args(const bem_mesh_impl &M, const Plan &P, const float2 *cp, const float2 *cq)
@@ -775,19 +794,19 @@ void make_coeffs(bem_mesh_impl &M, double k, double omega, double c, double rho,
 
 void upload_coeffs(bem_mesh_impl &M, const Coeffs &C)
 {
-    M.cp.upload(C.cp, M.s);
-    M.cq.upload(C.cq, M.s);
-    M.cp0.upload(C.cp0, M.s);
-    M.cq0.upload(C.cq0, M.s);
-    M.z.upload(C.z, M.s);
-    M.aq.upload(C.aq, M.s);
+    fr(M).cp.upload(C.cp, fr(M).s);
+    fr(M).cq.upload(C.cq, fr(M).s);
+    fr(M).cp0.upload(C.cp0, fr(M).s);
+    fr(M).cq0.upload(C.cq0, fr(M).s);
+    fr(M).z.upload(C.z, fr(M).s);
+    fr(M).aq.upload(C.aq, fr(M).s);
 }
 
 void check_err(bem_mesh_impl &M)
 {
     int e = INT_MAX;
-    ck(cudaMemcpyAsync(&e, M.err.p, sizeof(int), cudaMemcpyDeviceToHost, M.s), "D2H err");
-    ck(cudaStreamSynchronize(M.s), "sync");
+    ck(cudaMemcpyAsync(&e, fr(M).err.p, sizeof(int), cudaMemcpyDeviceToHost, fr(M).s), "D2H err");
+    ck(cudaStreamSynchronize(fr(M).s), "sync");
     if (e != INT_MAX) {
         char buf[160];
         snprintf(buf, sizeof buf,
@@ -801,7 +820,7 @@ void check_err(bem_mesh_impl &M)
 void reset_err(bem_mesh_impl &M)
 {
     const int v = INT_MAX;
-    ck(cudaMemcpyAsync(M.err.p, &v, sizeof(int), cudaMemcpyHostToDevice, M.s), "H2D err");
+    ck(cudaMemcpyAsync(fr(M).err.p, &v, sizeof(int), cudaMemcpyHostToDevice, fr(M).s), "H2D err");
 }
 
 // Stored near-field entries of plan P for the column coefficients (cp, cq):
@@ -820,43 +839,43 @@ void store_near(bem_mesh_impl &M, Plan &P, const float2 *cp, const float2 *cq)
         DevArr<unsigned long long> cnt, off;
         cnt.alloc(kHeavyKinds);
         off.alloc(kHeavyKinds);
-        ck(cudaMemsetAsync(cnt.p, 0, kHeavyKinds * sizeof(unsigned long long), M.s), "memset");
+        ck(cudaMemsetAsync(cnt.p, 0, kHeavyKinds * sizeof(unsigned long long), fr(M).s), "memset");
         {
-            KTimer kt_("k_near_classify", M.s);
-            k_near_classify<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, nullptr, cnt.p, nullptr);
+            KTimer kt_("k_near_classify", fr(M).s);
+            k_near_classify<<<nblocks(M.n, 8), 256, 0, fr(M).s>>>(a, nullptr, cnt.p, nullptr);
         }
         ck_launch("k_near_classify");
         unsigned long long hk[kHeavyKinds], ho[kHeavyKinds];
-        ck(cudaMemcpyAsync(hk, cnt.p, sizeof hk, cudaMemcpyDeviceToHost, M.s), "D2H");
-        ck(cudaStreamSynchronize(M.s), "sync");
+        ck(cudaMemcpyAsync(hk, cnt.p, sizeof hk, cudaMemcpyDeviceToHost, fr(M).s), "D2H");
+        ck(cudaStreamSynchronize(fr(M).s), "sync");
         unsigned long long h = 0;
         for (int q = 0; q < kHeavyKinds; ++q) {
             ho[q] = h;
             h += hk[q];
         }
         Ls.heavy.alloc(std::max<unsigned long long>(h, 1));
-        ck(cudaMemcpyAsync(off.p, ho, sizeof ho, cudaMemcpyHostToDevice, M.s), "H2D");
-        ck(cudaMemsetAsync(cnt.p, 0, kHeavyKinds * sizeof(unsigned long long), M.s), "memset");
+        ck(cudaMemcpyAsync(off.p, ho, sizeof ho, cudaMemcpyHostToDevice, fr(M).s), "H2D");
+        ck(cudaMemsetAsync(cnt.p, 0, kHeavyKinds * sizeof(unsigned long long), fr(M).s), "memset");
         {
-            KTimer kt_("k_near_classify", M.s);
-            k_near_classify<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, Ls.heavy.p, cnt.p, off.p);
+            KTimer kt_("k_near_classify", fr(M).s);
+            k_near_classify<<<nblocks(M.n, 8), 256, 0, fr(M).s>>>(a, Ls.heavy.p, cnt.p, off.p);
         }
         ck_launch("k_near_classify");
-        ck(cudaStreamSynchronize(M.s), "sync");
+        ck(cudaStreamSynchronize(fr(M).s), "sync");
         Ls.n_heavy = (int64_t)h;
     }
     {
-        KTimer kt_("k_near_store", M.s);
+        KTimer kt_("k_near_store", fr(M).s);
         const int nleaf = (int)(P.lists->leaf_start.n - 1);
         const dim3 grid(nleaf, nblocks(std::max(1, P.lists->max_ncol), 256));
-        k_near_store_light<<<grid, 256, 0, M.s>>>(a, P.val.p, M.err.p);
+        k_near_store_light<<<grid, 256, 0, fr(M).s>>>(a, P.val.p, fr(M).err.p);
     }
     ck_launch("k_near_store");
     if (Ls.n_heavy > 0) {
         {
-            KTimer kt_("k_near_store_heavy", M.s);
-            k_near_store_heavy<<<nblocks(Ls.n_heavy, 128), 128, 0, M.s>>>(a, Ls.heavy.p, Ls.n_heavy, P.val.p,
-                                                                          M.err.p);
+            KTimer kt_("k_near_store_heavy", fr(M).s);
+            k_near_store_heavy<<<nblocks(Ls.n_heavy, 128), 128, 0, fr(M).s>>>(a, Ls.heavy.p, Ls.n_heavy, P.val.p,
+                                                                          fr(M).err.p);
         }
         ck_launch("k_near_store_heavy");
     }
@@ -866,7 +885,7 @@ void store_near(bem_mesh_impl &M, Plan &P, const float2 *cp, const float2 *cq)
 // Make sure the stored near-field values match the current unknowns' coefficients.
 void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
 {
-    Plan &P = *M.plan;
+    Plan &P = *fr(M).plan;
     std::vector<float> key;
     key.reserve(4 * M.n);
     for (int64_t i = 0; i < M.n; ++i) {
@@ -877,12 +896,14 @@ void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
         if (!P.val_valid) {
             // one fused pass validates the subdivision limit for this plan
             reset_err(M);
-            M.tmp.alloc(M.n);
-            ck(cudaMemsetAsync(M.tmp.p, 0, M.n * sizeof(float2), M.s), "memset");
-            NearArgs a = near_args(M, P, M.cp.p, M.cq.p);
+            Frame &F = fr(M);
+            F.vtmp.alloc(M.n);
+            F.vout.alloc(M.n);
+            ck(cudaMemsetAsync(F.vtmp.p, 0, M.n * sizeof(float2), F.s), "memset");
+            NearArgs a = near_args(M, P, F.cp.p, F.cq.p);
             {
-                KTimer kt_("k_near_fused", M.s);
-                k_near_fused<<<nblocks(M.n, 8), 256, 0, M.s>>>(a, M.tmp.p, M.ynear.p, M.err.p, nullptr);
+                KTimer kt_("k_near_fused", F.s);
+                k_near_fused<<<nblocks(M.n, 8), 256, 0, F.s>>>(a, F.vtmp.p, F.vout.p, F.err.p, nullptr);
             }
             ck_launch("k_near_fused");
             check_err(M);
@@ -891,7 +912,7 @@ void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
         return;
     }
     if (P.val_valid && key == P.val_key) return;
-    store_near(M, P, M.cp.p, M.cq.p);
+    store_near(M, P, fr(M).cp.p, fr(M).cq.p);
     P.val_key.swap(key);
     P.val_valid = true;
 }
@@ -901,7 +922,7 @@ void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
 // perm_out.  use_store: use the stored near-field values.
 PrepArgs prep_args(bem_mesh_impl &M, const float2 *cp, const float2 *cq, const float2 *x)
 {
-    const bool far = !M.plan->lev.empty();
+    const bool far = !fr(M).plan->lev.empty();
     PrepArgs pa;
     pa.n = M.n;
     pa.x = x;
@@ -913,7 +934,7 @@ PrepArgs prep_args(bem_mesh_impl &M, const float2 *cp, const float2 *cq, const f
     pa.nrm = M.nrm.p;
     pa.cp = cp;
     pa.cq = cq;
-    pa.k = (float)M.plan->k;
+    pa.k = (float)fr(M).plan->k;
     return pa;
 }
 
@@ -929,7 +950,7 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
                      const int *jidx, bool perm_in, float2 *y, bool perm_out, const int *skip, cudaStream_t s,
                      bool prepared = false, bool far_only = false)
 {
-    Plan &P = *M.plan;
+    Plan &P = *fr(M).plan;
     const int64_t n = M.n;
     if (!prepared) {
         PrepArgs pa = prep_args(M, cp, cq, x);
@@ -986,7 +1007,7 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     } else {
         {
             KTimer kt_("k_near_fused", s);
-            k_near_fused<<<nblocks(n, 8), 256, 0, s>>>(na, M.xint.p, M.ynear.p, M.err.p, skip);
+            k_near_fused<<<nblocks(n, 8), 256, 0, s>>>(na, M.xint.p, M.ynear.p, fr(M).err.p, skip);
         }
         ck_launch("k_near_fused");
     }
@@ -1056,11 +1077,11 @@ void autotune_leaf_depth(bem_mesh_impl &M, double k)
         P->lists = lists;
         finish_plan(M, *P);
         std::unique_ptr<Plan> keep;
-        keep.swap(M.plan);
-        M.plan = std::move(P);
-        M.plan->val.alloc((size_t)M.plan->nnz());
+        keep.swap(fr(M).plan);
+        fr(M).plan = std::move(P);
+        fr(M).plan->val.alloc((size_t)fr(M).plan->nnz());
         ck(cudaEventRecord(e0, M.s), "record");
-        store_near(M, *M.plan, tcp.p, tcq.p);
+        store_near(M, *fr(M).plan, tcp.p, tcq.p);
         ck(cudaEventRecord(e1, M.s), "record");
         ck(cudaEventSynchronize(e1), "sync");
         float ms_store = 0.f, ms_mv = 0.f;
@@ -1081,8 +1102,8 @@ void autotune_leaf_depth(bem_mesh_impl &M, double k)
         const double cost = 1e-3 * (ms_store + 40.0 * ms_mv / 3.0);
         M.tune_log.push_back({d, cost});
         cand.emplace_back(d, cost, lists);
-        M.plan.reset();
-        M.plan.swap(keep);
+        fr(M).plan.reset();
+        fr(M).plan.swap(keep);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1134,7 +1155,7 @@ void prepare(bem_mesh_impl &M, double freq, const bem_medium *med, const double 
     ck(cudaSetDevice(M.device), "cudaSetDevice");
     ensure_work(M);
     build_plan_dev(M, freq, c);
-    make_coeffs(M, M.plan->k, 2.0 * M_PI * freq, c, rho, adm, nreg, C);
+    make_coeffs(M, fr(M).plan->k, 2.0 * M_PI * freq, c, rho, adm, nreg, C);
     upload_coeffs(M, C);
     ensure_near_values(M, C);
 }
@@ -1279,6 +1300,9 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         M->tuned = !tune;
         ck(cudaGetDevice(&M->device), "cudaGetDevice");
         ck(cudaStreamCreateWithFlags(&M->s, cudaStreamNonBlocking), "stream");
+        ck(cudaStreamCreateWithFlags(&M->s_setup, cudaStreamNonBlocking), "stream");
+        M->cur.s = M->s;
+        M->next.s = M->s_setup;
         {
             int lo = 0, hi = 0;
             ck(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
@@ -1332,7 +1356,13 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
 
         std::vector<QuadTables> qt(1, make_tables(p));
         M->Q.upload(qt, s);
-        M->err.alloc(1);
+        {
+            const int none = INT_MAX;
+            for (Frame *F : {&M->cur, &M->next}) {
+                F->err.alloc(1);
+                ck(cudaMemcpyAsync(F->err.p, &none, sizeof none, cudaMemcpyHostToDevice, s), "H2D err");
+            }
+        }
         ck(cudaStreamSynchronize(s), "sync");
         *out = M.release();
         return BEM_OK;
@@ -1366,7 +1396,7 @@ int bem_matvec(void *mesh, double freq_hz, const bem_medium *medium, const doubl
         for (int r = 0; r < n_rhs; ++r) {
             const float2 *x = (const float2 *)x_dev + (int64_t)r * M.n;
             float2 *y = (float2 *)y_dev + (int64_t)r * M.n;
-            matvec_internal(M, M.cp.p, M.cq.p, true, x, nullptr, true, y, true, nullptr, M.s);
+            matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, x, nullptr, true, y, true, nullptr, M.s);
         }
         join_streams(M.s, us);
         return resolution_warning(M, freq_hz, medium);
@@ -1413,7 +1443,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         prepare(M, freq_hz, medium, admittance, n_regions, C);
         ck(cudaStreamSynchronize(M.s), "sync");
         auto t_setup = std::chrono::steady_clock::now();
-        Plan &P = *M.plan;
+        Plan &P = *fr(M).plan;
         cudaStream_t s = M.s;
         const int64_t n = M.n;
         const int m = M.prm.restart;
@@ -1434,7 +1464,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         }
         if (C.known_nonzero) {
             reset_err(M);
-            matvec_internal(M, M.cp0.p, M.cq0.p, false, M.z.p, nullptr, false, M.tmp2.p, false, nullptr, s);
+            matvec_internal(M, fr(M).cp0.p, fr(M).cq0.p, false, fr(M).z.p, nullptr, false, M.tmp2.p, false, nullptr, s);
             check_err(M);
             {
                 KTimer kt_("k_sub", s);
@@ -1485,7 +1515,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         // the product inputs of v_0 (later basis vectors get theirs from
         // k_gm_ortho)
         auto prep_v0 = [&]() {
-            PrepArgs pa = prep_args(M, M.cp.p, M.cq.p, M.V.p);
+            PrepArgs pa = prep_args(M, fr(M).cp.p, fr(M).cq.p, M.V.p);
             {
                 KTimer kt_("k_prep", s);
                 k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, nullptr);
@@ -1523,7 +1553,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         ga.g = M.g_.p;
         ga.normpart = M.normpart.p;
         ga.m = m;
-        oa.next = prep_args(M, M.cp.p, M.cq.p, nullptr);
+        oa.next = prep_args(M, fr(M).cp.p, fr(M).cq.p, nullptr);
         oa.wnear = M.ynear.p;
         oa.bar = M.gbar.p;
         oa.err = &M.st.p->fault;
@@ -1565,7 +1595,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         auto arnoldi_steps = [&](int nsteps) {
             const bool side = use_graph;
             for (int t = 0; t < nsteps; ++t) {
-                matvec_internal(M, M.cp.p, M.cq.p, true, nullptr, nullptr, false, M.w.p, false, done, s, true, true);
+                matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, nullptr, nullptr, false, M.w.p, false, done, s, true, true);
                 if (side && t > 0) ck(cudaStreamWaitEvent(s, M.ev_giv[t - 1], 0), "wait givens");
                 ortho();
                 if (side) {
@@ -1627,7 +1657,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
             if (h.converged || h.iters >= max_iter) { converged = h.converged; break; }
             // restart: r = b - A x
             ++restarts;
-            matvec_internal(M, M.cp.p, M.cq.p, true, M.uvec.p, nullptr, false, M.w.p, false, nullptr, s);
+            matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, M.uvec.p, nullptr, false, M.w.p, false, nullptr, s);
             k_rsub<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.bvec.p, n);   // w = b - A x
             ck_launch("k_rsub");
             {
@@ -1652,7 +1682,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         // p and q in the caller's order
         {
             KTimer kt_("k_pq", s);
-            k_pq<<<nblocks(n, 256), 256, 0, s>>>(M.uvec.p, M.z.p, M.aq.p, M.type.p, M.perm.p, n, (float2 *)p_dev,
+            k_pq<<<nblocks(n, 256), 256, 0, s>>>(M.uvec.p, fr(M).z.p, fr(M).aq.p, M.type.p, M.perm.p, n, (float2 *)p_dev,
                                              (float2 *)q_dev);
         }
         ck_launch("k_pq");
@@ -1734,7 +1764,7 @@ int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem
         {
             KTimer kt_("k_field", s);
             k_field<<<(unsigned)M_pts, 256, 0, s>>>(M.elem(), M.Q.p, dp.p, M_pts, (float)k, M.tmp.p, M.tmp2.p, sdev.p,
-                                              n_src, (float2 *)out_dev, M.err.p);
+                                              n_src, (float2 *)out_dev, fr(M).err.p);
         }
         ck_launch("k_field");
         check_err(M);
@@ -1769,7 +1799,7 @@ int bem_mesh_release_plan(void *mesh)
     auto &M = *(bem_mesh_impl *)mesh;
     cudaSetDevice(M.device);
     if (M.s) cudaStreamSynchronize(M.s);
-    M.plan.reset();
+    fr(M).plan.reset();
     M.freq_lists.clear();
     M.spare_val.release();
     M.spare_bufs.clear();
@@ -1836,7 +1866,7 @@ int bem_mesh_stats(void *mesh, double freq_hz, const bem_medium *medium, bem_pla
         ensure_work(M);
         build_plan_dev(M, freq_hz, c);
         ck(cudaStreamSynchronize(M.s), "sync");
-        Plan &P = *M.plan;
+        Plan &P = *fr(M).plan;
         fill_stats(M.g, M.t, P.fp(), out);
         for (size_t l = 0; l < P.lev.size() && l < 16; ++l) out->L[l] = P.lev[l]->L;
         out->n_tuned = (int)std::min<size_t>(4, M.tune_log.size());
