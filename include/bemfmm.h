@@ -178,6 +178,28 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
               int32_t n_regions, const bem_source *srcs, int32_t n_src, double tol,
               int32_t max_iter, void *p_dev, void *q_dev, bem_solve_info *info, void *stream);
 
+/* Frequency sweep (the paper solves the frequencies of a sweep
+ * independently and splits sweeps into frequency ranges, appendix
+ * "Command-line parameters", subsection Parallelization; the overlap below
+ * is this library's own): solves Eq. SystemI at n_freq frequencies freqs_hz
+ * (host) in order, as n_freq calls of bem_solve would, with the same
+ * arguments per frequency and the same results.  While the GMRES of
+ * frequency i runs, a host thread prepares frequency i + 1 (its plan,
+ * translation tables and near-field entries) on a second stream and set of
+ * buffers, so that work overlaps the solve.
+ *   p_dev, q_dev: device cf32 [n_freq][n_tris] (q_dev may be NULL when
+ *   n_pts = 0); pts: host double [n_pts][3] field points (may be NULL with
+ *   n_pts = 0); field_dev: device cf32 [n_freq][n_pts], the exterior field
+ *   (Eq. BIE_I with lambda = 1) at each frequency; infos: host [n_freq] or
+ *   NULL.
+ * Returns on the first error (the outputs of earlier frequencies are
+ * written); otherwise BEM_OK or the first warning met (its message in
+ * bem_last_error).  The caller's stream is joined and synchronised. */
+int bem_solve_sweep(void *mesh, const double *freqs_hz, int32_t n_freq, const bem_medium *medium,
+                    const double *admittance, int32_t n_regions, const bem_source *srcs, int32_t n_src,
+                    double tol, int32_t max_iter, void *p_dev, void *q_dev, const double *pts,
+                    int64_t n_pts, void *field_dev, bem_solve_info *infos, void *stream);
+
 /* Total pressure at M exterior points (Eq. BIE_I with lambda = 1):
  * p(x) = p_inc(x) + sum_j [H(x)_j p_j - G(x)_j q_j], element integrals by
  * the regular / quasi-singular rules measured from x.  p_dev, q_dev: device

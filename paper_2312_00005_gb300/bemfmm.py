@@ -106,6 +106,8 @@ def lib():
                                          P, P, ctypes.POINTER(SolveInfo), P]),
             "bem_evaluate": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), ctypes.POINTER(Source), i32, P, P, P,
                                             i64, P, P]),
+            "bem_solve_sweep": (ctypes.c_int, [P, P, i32, ctypes.POINTER(Medium), P, i32, ctypes.POINTER(Source), i32,
+                                               d, i32, P, P, P, i64, P, ctypes.POINTER(SolveInfo), P]),
             "bem_mesh_stats": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), ctypes.POINTER(PlanStats)]),
             "bem_plan_stats_host": (ctypes.c_int, [P, i64, P, i64, ctypes.POINTER(Params), d, d,
                                                    ctypes.POINTER(PlanStats)]),
@@ -332,6 +334,49 @@ class Mesh:
              "setup_seconds": info.setup_seconds, "rhs_seconds": info.rhs_seconds,
              "gmres_seconds": info.gmres_seconds}
         return p, q, d
+
+    def solve_sweep(self, freqs, sources=(), admittance=None, tol=1e-6, max_iter=1000, c=343.0, rho=1.21,
+                    points=None, p=None, q=None, field=None, stream=None):
+        """Solve Eq. SystemI at each frequency of freqs (the next frequency's
+        plan and near-field entries are prepared while the current one is
+        solved); returns (p, q, field, infos): complex64 CUDA tensors
+        [n_freq, n_tris] (field [n_freq, n_points], or None without points)
+        and one info dict per frequency."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        fr = np.ascontiguousarray(np.asarray(freqs, dtype=np.float64).reshape(-1))
+        nf = fr.shape[0]
+        if p is None:
+            p = torch.empty((nf, self.n), dtype=torch.complex64, device=dev)
+        if q is None:
+            q = torch.empty((nf, self.n), dtype=torch.complex64, device=dev)
+        npts = 0
+        pts = None
+        if points is not None:
+            pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 3))
+            npts = pts.shape[0]
+            if field is None:
+                field = torch.empty((nf, npts), dtype=torch.complex64, device=dev)
+        srcs = (Source * max(1, len(sources)))(*sources)
+        adm, nreg = _admittance(admittance)
+        med = self._medium(c, rho)
+        infos = (SolveInfo * nf)()
+        code = lib().bem_solve_sweep(self._h, fr.ctypes.data_as(ctypes.c_void_p), nf, ctypes.byref(med),
+                                     None if adm is None else adm.ctypes.data_as(ctypes.c_void_p), nreg, srcs,
+                                     len(sources), float(tol), int(max_iter), _dptr(p, nf * self.n),
+                                     _dptr(q, nf * self.n),
+                                     None if pts is None else pts.ctypes.data_as(ctypes.c_void_p), npts,
+                                     None if field is None else _dptr(field, nf * npts), infos,
+                                     _stream_ptr(stream))
+        _check(code)
+        out = []
+        for info in infos:
+            out.append({"iterations": info.iterations, "restarts": info.restarts, "relres": info.relres,
+                        "seconds": info.seconds, "levels": info.levels, "L": list(info.L[:info.levels]),
+                        "near_nnz": info.near_nnz, "status": info.status,
+                        "converged": info.status != W_NOT_CONVERGED, "setup_seconds": info.setup_seconds,
+                        "rhs_seconds": info.rhs_seconds, "gmres_seconds": info.gmres_seconds})
+        return p, q, (field if npts else None), out
 
     def evaluate(self, freq, p, q, points, sources=(), c=343.0, rho=1.21, out=None, stream=None):
         """Total pressure at exterior points (Eq. BIE_I, lambda = 1)."""

@@ -13,6 +13,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -800,6 +801,7 @@ void upload_coeffs(bem_mesh_impl &M, const Coeffs &C)
     fr(M).cq0.upload(C.cq0, fr(M).s);
     fr(M).z.upload(C.z, fr(M).s);
     fr(M).aq.upload(C.aq, fr(M).s);
+    fr(M).known_nonzero = C.known_nonzero;
 }
 
 void check_err(bem_mesh_impl &M)
@@ -1428,21 +1430,15 @@ int bem_matvec_host(void *mesh, double freq_hz, const bem_medium *medium, const 
     }
 }
 
-int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
-              int32_t n_regions, const bem_source *srcs, int32_t n_src, double tol, int32_t max_iter,
-              void *p_dev, void *q_dev, bem_solve_info *info, void *stream)
+namespace {
+
+// Solve with the current frame's plan (prepared for freq_hz): right-hand
+// side, GMRES, p and q in the caller's order.  Throws Fail.
+int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, const bem_source *srcs, int32_t n_src,
+                double tol, int32_t max_iter, void *p_dev, void *q_dev, bem_solve_info *info, cudaStream_t us,
+                std::chrono::steady_clock::time_point t0, std::chrono::steady_clock::time_point t_setup)
 {
-    auto t0 = std::chrono::steady_clock::now();
-    if (!mesh || !p_dev || n_src < 0 || (n_src > 0 && !srcs) || !(tol > 0) || max_iter < 1)
-        return set_err(BEM_E_ARG, "bad argument");
-    auto &M = *(bem_mesh_impl *)mesh;
-    try {
-        cudaStream_t us = (cudaStream_t)stream;
-        Coeffs C;
-        join_streams(us, M.s);
-        prepare(M, freq_hz, medium, admittance, n_regions, C);
-        ck(cudaStreamSynchronize(M.s), "sync");
-        auto t_setup = std::chrono::steady_clock::now();
+    {
         Plan &P = *fr(M).plan;
         cudaStream_t s = M.s;
         const int64_t n = M.n;
@@ -1462,7 +1458,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         } else {
             ck(cudaMemsetAsync(M.bvec.p, 0, n * sizeof(float2), s), "memset");
         }
-        if (C.known_nonzero) {
+        if (fr(M).known_nonzero) {
             reset_err(M);
             matvec_internal(M, fr(M).cp0.p, fr(M).cq0.p, false, fr(M).z.p, nullptr, false, M.tmp2.p, false, nullptr, s);
             check_err(M);
@@ -1714,13 +1710,149 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
             info->gmres_seconds = std::chrono::duration<double>(t_gmres - t_rhs).count();
         }
         return status;
+    }
+}
+
+// Ends a stream capture that a failure left open.
+void abandon_capture(bem_mesh_impl &M)
+{
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(M.s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        cudaGraph_t g;
+        cudaStreamEndCapture(M.s, &g);
+        if (g) cudaGraphDestroy(g);
+    }
+}
+
+// Exchanges the frequency state of two frames (not their streams).
+void swap_frames(Frame &a, Frame &b)
+{
+    std::swap(a.plan, b.plan);
+    a.cp.swap(b.cp);
+    a.cq.swap(b.cq);
+    a.cp0.swap(b.cp0);
+    a.cq0.swap(b.cq0);
+    a.z.swap(b.z);
+    a.aq.swap(b.aq);
+    a.err.swap(b.err);
+    a.vtmp.swap(b.vtmp);
+    a.vout.swap(b.vout);
+    std::swap(a.known_nonzero, b.known_nonzero);
+}
+
+}  // namespace
+
+int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
+              int32_t n_regions, const bem_source *srcs, int32_t n_src, double tol, int32_t max_iter,
+              void *p_dev, void *q_dev, bem_solve_info *info, void *stream)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (!mesh || !p_dev || n_src < 0 || (n_src > 0 && !srcs) || !(tol > 0) || max_iter < 1)
+        return set_err(BEM_E_ARG, "bad argument");
+    auto &M = *(bem_mesh_impl *)mesh;
+    try {
+        cudaStream_t us = (cudaStream_t)stream;
+        Coeffs C;
+        join_streams(us, M.s);
+        prepare(M, freq_hz, medium, admittance, n_regions, C);
+        ck(cudaStreamSynchronize(M.s), "sync");
+        return solve_frame(M, freq_hz, medium, srcs, n_src, tol, max_iter, p_dev, q_dev, info, us, t0,
+                           std::chrono::steady_clock::now());
     } catch (Fail &f) {
-        cudaStreamCaptureStatus cs;
-        if (cudaStreamIsCapturing(M.s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
-            cudaGraph_t g;
-            cudaStreamEndCapture(M.s, &g);
-            if (g) cudaGraphDestroy(g);
+        abandon_capture(M);
+        return f.code;
+    }
+}
+
+int bem_solve_sweep(void *mesh, const double *freqs_hz, int32_t n_freq, const bem_medium *medium,
+                    const double *admittance, int32_t n_regions, const bem_source *srcs, int32_t n_src, double tol,
+                    int32_t max_iter, void *p_dev, void *q_dev, const double *pts, int64_t n_pts, void *field_dev,
+                    bem_solve_info *infos, void *stream)
+{
+    if (!mesh || !freqs_hz || n_freq < 1 || !p_dev || n_src < 0 || (n_src > 0 && !srcs) || !(tol > 0) ||
+        max_iter < 1 || n_pts < 0 || (n_pts > 0 && (!pts || !field_dev || !q_dev)))
+        return set_err(BEM_E_ARG, "bad argument");
+    for (int32_t i = 0; i < n_freq; ++i)
+        if (!(freqs_hz[i] > 0) || !std::isfinite(freqs_hz[i])) return set_err(BEM_E_ARG, "frequency must be positive");
+    auto &M = *(bem_mesh_impl *)mesh;
+    const int64_t n = M.n;
+    int worst = BEM_OK;
+    std::string worst_msg;
+    try {
+        cudaStream_t us = (cudaStream_t)stream;
+        join_streams(us, M.s);
+        auto t0 = std::chrono::steady_clock::now();
+        {
+            Coeffs C;
+            prepare(M, freqs_hz[0], medium, admittance, n_regions, C);
+            ck(cudaStreamSynchronize(M.s), "sync");
         }
+        for (int32_t i = 0; i < n_freq; ++i) {
+            auto t_setup = std::chrono::steady_clock::now();
+            // the next frequency's plan and near-field entries, on the setup
+            // thread and stream, while this frequency's GMRES runs
+            std::thread ahead;
+            int next_code = BEM_OK;
+            std::string next_msg;
+            if (i + 1 < n_freq) {
+                const double fn = freqs_hz[i + 1];
+                ahead = std::thread([&M, &next_code, &next_msg, fn, medium, admittance, n_regions]() {
+                    t_frame = &M.next;
+                    try {
+                        ck(cudaSetDevice(M.device), "cudaSetDevice");
+                        Coeffs Cn;
+                        prepare(M, fn, medium, admittance, n_regions, Cn);
+                        ck(cudaStreamSynchronize(M.s_setup), "sync");
+                    } catch (Fail &f) {
+                        next_code = f.code;
+                        next_msg = g_err;
+                    } catch (std::exception &e) {
+                        next_code = BEM_E_INTERNAL;
+                        next_msg = e.what();
+                    }
+                    t_frame = nullptr;
+                });
+            }
+            int st = BEM_OK;
+            try {
+                bem_solve_info *info = infos ? infos + i : nullptr;
+                float2 *p = (float2 *)p_dev + (int64_t)i * n;
+                float2 *q = q_dev ? (float2 *)q_dev + (int64_t)i * n : nullptr;
+                st = solve_frame(M, freqs_hz[i], medium, srcs, n_src, tol, max_iter, p, q, info, us, t0, t_setup);
+                if (n_pts > 0) {
+                    const int se = bem_evaluate(mesh, freqs_hz[i], medium, srcs, n_src, p, q, pts, n_pts,
+                                                (float2 *)field_dev + (int64_t)i * n_pts, stream);
+                    if (se < 0) throw Fail{se};
+                }
+                ck(cudaStreamSynchronize(us), "sync");
+            } catch (Fail &f) {
+                abandon_capture(M);
+                const std::string msg = g_err;
+                if (ahead.joinable()) ahead.join();
+                g_err = msg;
+                return f.code;
+            }
+            if (st > 0 && worst == BEM_OK) {
+                worst = st;
+                worst_msg = g_err;
+            }
+            t0 = std::chrono::steady_clock::now();
+            if (ahead.joinable()) {
+                ahead.join();
+                if (next_code != BEM_OK) {
+                    g_err = next_msg;
+                    return next_code;
+                }
+                swap_frames(M.cur, M.next);
+                t_frame = &M.next;      // the finished frequency's buffers become spares
+                recycle_plan(M);
+                t_frame = nullptr;
+            }
+        }
+        if (worst != BEM_OK) g_err = worst_msg;
+        return worst;
+    } catch (Fail &f) {
+        abandon_capture(M);
         return f.code;
     }
 }

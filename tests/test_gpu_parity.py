@@ -268,3 +268,36 @@ def test_fast_sincos_against_cuda(bem):
     out = bem.selftest_sincos(x).cpu().numpy().astype(np.float64)
     err = np.max(np.abs(out[:, 0:2] - out[:, 2:4]))
     assert err < 2e-6, err
+
+
+def test_sweep_matches_single_solves(bem):
+    """bem_solve_sweep (the next frequency prepared on a second stream and
+    host thread while the current one is solved) gives the results of one
+    bem_solve per frequency: FMM plans, admittance regions with known data,
+    field points, and a frequency jump that needs new lists."""
+    nodes, tris = inputs.icosphere(4, 0.1)
+    n = tris.shape[0]
+    # admittance everywhere (two regions, upper and lower half) plus a
+    # seeded extra velocity: frequency-dependent column coefficients and
+    # known data in every frame
+    cen = nodes[tris].mean(axis=1)
+    bc = np.full(n, bem.ADMI, np.int32)
+    region = (cen[:, 2] > 0).astype(np.int32)
+    adm = np.array([0.2 * (1 - 0.3j), 0.4 * (1 + 0.2j)]) / (RHO * C)
+    rng = np.random.default_rng(11)
+    bcv = (rng.normal(size=n) + 1j * rng.normal(size=n)) * 1e-4
+    freqs = [2000.0, 2000.5, 3100.0]
+    pts = inputs.fibonacci_sphere(20, 1.0)
+    src = [bem.plane_wave((0.3, 0.0, 0.95))]
+    mesh = bem.Mesh(nodes, tris, bc_type=bc, bc_value=bcv, region=region, trunc_factor=5.0)
+    ps, qs, fl, infos = mesh.solve_sweep(freqs, src, admittance=adm, tol=1e-6, c=C, rho=RHO, points=pts)
+    assert all(i["converged"] for i in infos), [(i["iterations"], i["relres"]) for i in infos]
+    ref = bem.Mesh(nodes, tris, bc_type=bc, bc_value=bcv, region=region, trunc_factor=5.0)
+    for k, f in enumerate(freqs):
+        p1, q1, info = ref.solve(f, src, admittance=adm, tol=1e-6, c=C, rho=RHO)
+        f1 = ref.evaluate(f, p1, q1, pts, src, c=C, rho=RHO)
+        for a, b in ((ps[k], p1), (qs[k], q1), (fl[k], f1)):
+            a = a.cpu().numpy().astype(np.complex128)
+            b = b.cpu().numpy().astype(np.complex128)
+            assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b), (f, np.linalg.norm(a - b) / np.linalg.norm(b))
+        assert infos[k]["iterations"] == info["iterations"]
