@@ -191,6 +191,8 @@ struct Lists {
     FreqPlan fp;
     int max_ncol = 0;
     DevArr<int64_t> leaf_start;
+    DevArr<int2> dis_tasks;       // disaggregation work items (element ranges)
+    int n_dis_tasks = 0;
     DevArr<int> leaf_of, run_ptr, ncol;
     DevArr<int2> runs;
     DevArr<int64_t> row_ptr;
@@ -199,7 +201,7 @@ struct Lists {
     int64_t nnz = 0;
     std::vector<std::unique_ptr<ListsLevelDev>> lev;
     // all levels together, for the one-launch far-field kernels
-    DevArr<AggTask> all_tasks;
+    std::vector<AggTask> h_tasks;    // aggregation element chunks of every level (host)
     DevArr<int2> all_reds, all_targets;
     std::vector<int2> h_targets;   // host copy of all_targets
     DevArr<unsigned int> red_cnt;
@@ -251,6 +253,7 @@ struct LevelDev {
 
 struct Plan {
     DevArr<int4> tgroups;         // transfer blocks (level, target, first direction)
+    DevArr<AggTask> agg_tasks;    // aggregation blocks (element chunk, first direction pair)
     double freq = -1.0, c = -1.0, k = 0.0;
     std::shared_ptr<Lists> lists;
     bool shared_lists = false;
@@ -438,6 +441,20 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
         Ls->max_ncol = std::max(Ls->max_ncol, ncol[t]);
     }
     Ls->leaf_start.upload(leaf_start, s);
+    {
+        // disaggregation tasks: each leaf split into ranges of at most
+        // kDisTask elements of nearly equal size, largest first
+        std::vector<int2> dt;
+        for (int t = 0; t < nl; ++t) {
+            const int64_t a = leaf_start[t], cnt = leaf_start[t + 1] - a;
+            const int64_t nch = (cnt + kDisTask - 1) / kDisTask;
+            for (int64_t q = 0; q < nch; ++q)
+                dt.push_back(make_int2((int)(a + cnt * q / nch), (int)(a + cnt * (q + 1) / nch)));
+        }
+        std::stable_sort(dt.begin(), dt.end(), [](int2 u, int2 v) { return u.y - u.x > v.y - v.x; });
+        Ls->n_dis_tasks = (int)dt.size();
+        Ls->dis_tasks.upload(dt, s);
+    }
     Ls->nnz = row_ptr[M.n];
     Ls->leaf_of.upload(leaf_of, s);
     Ls->run_ptr.upload(run_ptr, s);
@@ -472,7 +489,9 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
         std::vector<int> is_src(FL.nc, 0);
         for (int v : FL.il_src) is_src[v] = 1;
         D->is_src.upload(is_src, s);
-        // aggregation tasks: chunks of at most 64 elements of each source cluster
+        // aggregation tasks: chunks of at most kAggChunk elements of each
+        // source cluster, of nearly equal size (each plan expands them into
+        // ranges of direction pairs for its expansion lengths)
         const Level &L = M.t.lv[FL.depth];
         std::vector<AggTask> tasks;
         std::vector<int> red_ptr{FL.nc}, red_c;
@@ -480,15 +499,16 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
         for (int c = 0; c < FL.nc; ++c) {
             if (!is_src[c]) continue;
             const int64_t cnt = L.count[c];
-            if (cnt <= 64) {
-                tasks.push_back(AggTask{c, c, L.start[c], (int)cnt, lev_index, -1, -1});
+            const int64_t nch = std::max<int64_t>(1, (cnt + kAggChunk - 1) / kAggChunk);
+            if (nch == 1) {
+                tasks.push_back(AggTask{c, c, L.start[c], (int)cnt, lev_index, -1, -1, 0});
                 continue;
             }
             const int red = (int)red_c.size();
             const int gred = (int)all_reds.size() + red;
-            for (int64_t q = 0; q < cnt; q += 64) {
-                tasks.push_back(AggTask{c, FL.nc + extra, L.start[c] + q, (int)std::min<int64_t>(64, cnt - q),
-                                        lev_index, red, gred});
+            for (int64_t q = 0; q < nch; ++q) {
+                const int64_t a = cnt * q / nch, b = cnt * (q + 1) / nch;
+                tasks.push_back(AggTask{c, FL.nc + extra, L.start[c] + a, (int)(b - a), lev_index, red, gred, 0});
                 ++extra;
             }
             red_c.push_back(c);
@@ -509,7 +529,7 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
     Ls->n_tasks = (int)all_tasks.size();
     Ls->n_reds = (int)all_reds.size();
     Ls->n_targets = (int)all_targets.size();
-    Ls->all_tasks.upload(all_tasks, s);
+    Ls->h_tasks = all_tasks;
     Ls->all_reds.upload(all_reds, s);
     Ls->all_targets.upload(all_targets, s);
     Ls->h_targets = all_targets;
@@ -631,8 +651,20 @@ void finish_plan(bem_mesh_impl &M, Plan &Pl)
     LevelsArgs &A = P->hargs;
     memset(&A, 0, sizeof A);
     A.nlev = (int)P->lev.size();
-    A.tasks = P->lists->all_tasks.p;
-    A.ntasks = P->lists->n_tasks;
+    {
+        // aggregation blocks for this plan's expansion lengths: every
+        // element chunk times the ranges of kAggThreads direction pairs
+        std::vector<AggTask> at;
+        for (const AggTask &t : P->lists->h_tasks)
+            for (int p0 = 0; p0 < P->lev[t.lev]->nd / 2; p0 += kAggThreads) {
+                AggTask u = t;
+                u.p0 = p0;
+                at.push_back(u);
+            }
+        P->agg_tasks.upload(at, s);
+        A.tasks = P->agg_tasks.p;
+        A.ntasks = (int)at.size();
+    }
     A.reds = P->lists->all_reds.p;
     A.nreds = P->lists->n_reds;
     A.targets = P->lists->all_targets.p;
@@ -978,7 +1010,7 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     if (A.ntasks > 0) {
         {
             KTimer kt_("k_aggregate", sf);
-            k_aggregate<<<A.ntasks, 128, 0, sf>>>(P.largs.p, M.wts.p, M.nrm.p, skip);
+            k_aggregate<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, M.nrm.p, skip);
         }
         ck_launch("k_aggregate");
     }
@@ -1025,18 +1057,18 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     }
     cudaStream_t sd = far_only ? sf : s;
     for (int l = 0; l < A.nlev; ++l) da.lev[l] = A.lev[l];
-    da.leaf_start = P.lists->leaf_start.p;
+    da.tasks = P.lists->dis_tasks.p;
     da.sum_nd = 0;
     for (int l = 0; l < A.nlev; ++l) da.sum_nd += A.lev[l].nd;
     {
         KTimer kt_("k_disaggregate", sd);
-        const int nleaf = (int)(P.lists->leaf_start.n - 1);
         const size_t smem = (size_t)std::max(2, da.sum_nd) / 2 * sizeof(float4) + (size_t)da.sum_nd * sizeof(float2);
         if (smem > kDisaggSmem)
             throw Fail{set_err(BEM_E_ARG, "far field: " + std::to_string(da.sum_nd) +
                                               " directions over all levels exceed the disaggregation kernel's "
                                               "shared-memory staging")};
-        k_disaggregate<<<nleaf, 128, smem, sd>>>(da, far_only ? nullptr : M.ynear.p, y, skip);
+        if (P.lists->n_dis_tasks > 0)
+            k_disaggregate<<<P.lists->n_dis_tasks, 128, smem, sd>>>(da, far_only ? nullptr : M.ynear.p, y, skip);
     }
     ck_launch("k_disaggregate");
     if (fork && far_only) {

@@ -477,12 +477,15 @@ __global__ void k_prep(PrepArgs a, const int *skip)
 // Aggregation (Sec. 3.3.3, matrix T(l) with the centroid rule): for every
 // source cluster c and direction s_nu,
 //   M_c(nu) = sum_{j in c} e^{ik (z_c - x_j).s_nu} (alpha_j + c_j (n_j . s_nu)).
-// One block per task (a chunk of at most kAggChunk elements of one cluster),
-// one antipodal pair of directions per thread; phases in turns.  The last
-// task of a cluster split into several tasks sums their partial rows.
-constexpr int kAggChunk = 64;
-__global__ void k_aggregate(const LevelsArgs *__restrict__ A, const float4 *__restrict__ wts,
-                            const float4 *__restrict__ nrm, const int *skip)
+// One block per task: a chunk of at most kAggChunk elements of one cluster
+// and kAggThreads antipodal direction pairs, one pair per thread; phases in
+// turns.  Tasks of equal size keep every block short, so no large cluster
+// sets the kernel's length.  For a cluster split into several element
+// chunks, the last of its blocks to finish sums the chunks' partial rows in
+// row order.
+__global__ void __launch_bounds__(kAggThreads) k_aggregate(const LevelsArgs *__restrict__ A,
+                                                           const float4 *__restrict__ wts,
+                                                           const float4 *__restrict__ nrm, const int *skip)
 {
     if (skip_now(skip)) return;
     const AggTask T = A->tasks[blockIdx.x];
@@ -503,7 +506,8 @@ __global__ void k_aggregate(const LevelsArgs *__restrict__ A, const float4 *__re
     // both, e^{ik d.(-s)} = conj(e^{ik d.s}), and n.(-s) = -(n.s)
     float2 *__restrict__ out = f.M + (int64_t)T.row * f.nd;
     const int h = f.nd / 2;
-    for (int p = threadIdx.x; p < h; p += blockDim.x) {
+    const int p = T.p0 + threadIdx.x;
+    if (p < h) {
         const float4 sv = f.dirs[p];
         float2 accp = make_float2(0.f, 0.f), accm = accp;
         for (int q = 0; q < T.ne; ++q) {
@@ -511,8 +515,8 @@ __global__ void k_aggregate(const LevelsArgs *__restrict__ A, const float4 *__re
             float sn0, cs0;
             sincos_turns(fmaf(d.x, sv.x, fmaf(d.y, sv.y, d.z * sv.z)), &sn0, &cs0);
             const float t = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
-            const float ctx = w.z * t, cty = w.w * t;
-            const float2 wp = make_float2(w.x + ctx, w.y + cty), wm = make_float2(w.x - ctx, w.y - cty);
+            const float2 wp = make_float2(fmaf(w.z, t, w.x), fmaf(w.w, t, w.y));
+            const float2 wm = make_float2(fmaf(-w.z, t, w.x), fmaf(-w.w, t, w.y));
             // (cs + i sn) wp and (cs - i sn) wm
             accp.x = fmaf(cs0, wp.x, fmaf(-sn0, wp.y, accp.x));
             accp.y = fmaf(cs0, wp.y, fmaf(sn0, wp.x, accp.y));
@@ -523,28 +527,51 @@ __global__ void k_aggregate(const LevelsArgs *__restrict__ A, const float4 *__re
         out[p + h] = accm;
     }
     if (T.red < 0) return;
-    // split cluster: the last of its tasks to finish sums the partial rows
-    // in row order into M_c
+    // split cluster: its blocks are (element chunks) x (pair ranges); the
+    // last one to finish sums the partial rows in row order into M_c
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const int ntask = f.red_ptr[T.red + 1] - f.red_ptr[T.red];
+        const int npb = (h + kAggThreads - 1) / kAggThreads;
+        const int ntask = (f.red_ptr[T.red + 1] - f.red_ptr[T.red]) * npb;
         last = atomicAdd(&A->red_cnt[T.gred], 1u) == (unsigned)(ntask - 1);
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
     const int r0 = f.red_ptr[T.red], r1 = f.red_ptr[T.red + 1];
-    float2 *__restrict__ dst = f.M + (int64_t)T.c * f.nd;
-    for (int nu = threadIdx.x; nu < f.nd; nu += blockDim.x) {
-        float2 acc = make_float2(0.f, 0.f);
-        for (int rr = r0; rr < r1; ++rr) {
-            const volatile float2 *src = f.M + (int64_t)rr * f.nd + nu;
-            acc.x += src->x;
-            acc.y += src->y;
+    const int nd = f.nd;
+    float2 *__restrict__ dst = f.M + (int64_t)T.c * nd;
+    // each thread sums kRedDirs directions at a time and loads kRedRows rows
+    // of them together (L2 loads of other blocks' rows, all in flight at
+    // once); every direction still adds its rows in row order
+    constexpr int kRedDirs = 4, kRedRows = 4;
+    for (int nb = threadIdx.x; nb < nd; nb += kAggThreads * kRedDirs) {
+        float2 acc[kRedDirs];
+#pragma unroll
+        for (int b = 0; b < kRedDirs; ++b) acc[b] = make_float2(0.f, 0.f);
+        for (int rr = r0; rr < r1; rr += kRedRows) {
+            float2 v[kRedRows][kRedDirs];
+#pragma unroll
+            for (int a = 0; a < kRedRows; ++a)
+#pragma unroll
+                for (int b = 0; b < kRedDirs; ++b) {
+                    const int nu = nb + b * kAggThreads;
+                    v[a][b] = (rr + a < r1 && nu < nd) ? __ldcg(f.M + (int64_t)(rr + a) * nd + nu)
+                                                       : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+            for (int a = 0; a < kRedRows; ++a)
+#pragma unroll
+                for (int b = 0; b < kRedDirs; ++b) {
+                    acc[b].x += v[a][b].x;
+                    acc[b].y += v[a][b].y;
+                }
         }
-        dst[nu] = acc;
+#pragma unroll
+        for (int b = 0; b < kRedDirs; ++b)
+            if (nb + b * kAggThreads < nd) dst[nb + b * kAggThreads] = acc[b];
     }
     if (threadIdx.x == 0) A->red_cnt[T.gred] = 0;
 }
@@ -622,9 +649,10 @@ __global__ void __launch_bounds__(256) k_transfer_split(const LevelsArgs *__rest
 // (when ynear is given; else y receives the far part alone):
 //   y_i = near_i + (ik/16 pi^2) sum_l sum_nu w_nu (1 + s_nu.n_i)
 //                   e^{ik (x_i - z_t).s_nu} Lambda_t(nu).
-// One block per leaf: the elements of a leaf share their cluster at every
-// level, so the weighted Lambda rows of the leaf's ancestors and the
-// directions are staged in shared memory once.  Threads take antipodal
+// One block per task (at most kDisTask elements of one leaf; large leaves
+// are split so that no block is much longer than the others): the elements
+// of a leaf share their cluster at every level, so the weighted Lambda rows
+// of the leaf's ancestors and the directions are staged in shared memory.  Threads take antipodal
 // direction pairs (s_p, -s_p) of all levels (one phase and its conjugate),
 // each for a chunk of kDisChunk elements held in registers; the block then
 // sums each element's partials in a fixed order and writes y[perm[i]]
@@ -642,8 +670,8 @@ __global__ void __launch_bounds__(128, 8) k_disaggregate(DisaggArgs a, const flo
     __shared__ float4 dzs[kDisChunk][kMaxFarLevels];   // -k/(2 pi) (z_c - x_i) per active level
     __shared__ float4 ns[kDisChunk];
     __shared__ float2 red[32][kDisChunk];
-    const int t = blockIdx.x;
-    const int64_t e0 = a.leaf_start[t], e1 = a.leaf_start[t + 1];
+    const int2 tk = a.tasks[blockIdx.x];
+    const int64_t e0 = tk.x, e1 = tk.y;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) {
         // active levels (the leaf's cluster has an interaction list there)

@@ -63,8 +63,12 @@ struct PrepArgs {
     float k;
 };
 
-// Aggregation work item: `ne` elements from e0 of cluster c, written to row
-// `row` of the multipole buffer (row c when the cluster is a single task).
+// Aggregation work item: `ne` (at most kAggChunk) elements from e0 of
+// cluster c and the antipodal direction pairs [p0, p0 + kAggThreads),
+// written to row `row` of the multipole buffer (row c when the cluster is
+// one element chunk).
+constexpr int kAggThreads = 64;
+constexpr int kAggChunk = 32;
 struct AggTask {
     int c, row;
     int64_t e0;
@@ -72,7 +76,11 @@ struct AggTask {
     int lev;                 // index of the level (in LevelsArgs) the task belongs to
     int red;                 // split cluster: index of its partial-row range (in FarArgs), else -1
     int gred;                // split cluster: index of its arrival counter, else -1
+    int p0;                  // first direction pair
 };
+
+// Disaggregation work item: elements [x, y) of one leaf, at most kDisTask.
+constexpr int kDisTask = 16;
 
 struct FarArgs {
     int nd;                  // 2 L^2 directions
@@ -113,7 +121,7 @@ struct DisaggArgs {
     const int64_t *perm;     // optional
     float k;
     int nlev;
-    const int64_t *leaf_start;  // leaves (+1): element ranges
+    const int2 *tasks;       // element ranges [x, y) within one leaf, one per block
     int sum_nd;              // sum of nd over the levels (shared-memory rows)
     FarArgs lev[kMaxFarLevels];
 };

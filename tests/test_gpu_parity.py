@@ -89,6 +89,30 @@ def test_fmm_matvec_matches_oracle(bem):
     assert errs[6.0] < 1e-4, errs
 
 
+def test_fmm_matvec_after_frequency_change(bem):
+    """A mesh that has planned 2000 Hz reuses its frequency-independent lists
+    at 3100 Hz, where the coarsest far level needs a longer expansion (L = 8
+    -> 10): the product there must still match the oracle's dense operator,
+    i.e. every per-L work decomposition is rebuilt for the new lengths."""
+    nodes, tris = inputs.icosphere(4, 0.1)
+    n = tris.shape[0]
+    x = inputs.random_complex(n, 23)
+    mesh = bem.Mesh(nodes, tris, trunc_factor=5.0)
+    xt = torch.tensor(x, dtype=torch.complex64, device="cuda")
+    mesh.matvec(2000.0, xt, c=C, rho=RHO)
+    L0 = mesh.stats(2000.0, c=C)["L"]
+    freq = 3100.0
+    st = mesh.stats(freq, c=C)
+    assert st["levels"] >= 2 and st["L"] != L0, (L0, st["L"])
+    y = mesh.matvec(freq, xt, c=C, rho=RHO)
+    k = 2 * np.pi * freq / C
+    cp, cq, _, _ = oracle.column_coeffs(np.full(n, bem.VELO, np.int32), k, C, RHO)
+    yo = oracle.assemble(nodes, tris, k, cp, cq) @ x
+    err = _rel(y.cpu().numpy(), yo)
+    mesh.close()
+    assert err < 2e-4, err
+
+
 def test_solve_and_field_match_oracle(bem):
     nodes, tris = inputs.icosphere(3, 0.1)
     freq = 1000.0
