@@ -1017,7 +1017,7 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     if (A.ntargets > 0) {
         if (A.ntgroups > 0) {
             KTimer kt_("k_transfer", sf);
-            k_transfer_split<<<A.ntgroups, 256, 0, sf>>>(P.largs.p, skip);
+            k_transfer_split<<<A.ntgroups, 32 * kTransferWarps, 0, sf>>>(P.largs.p, skip);
         }
         ck_launch("k_transfer");
     }

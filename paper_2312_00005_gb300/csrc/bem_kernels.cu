@@ -590,15 +590,17 @@ __global__ void k_selftest_sincos(const float *__restrict__ x, int64_t n, float4
 // Diagonal transfer (Sec. 3.3.3, matrix D(l)): for every target cluster t
 // with an interaction list (Sec. 3.3.4),
 //   Lambda_t(nu) = sum_{s in I(t)} D_L(z_t - z_s, s_nu) M_s(nu).
-// Each target's interaction list is split among the warps of a block: a
-// block takes one target and kTransferDirs
-// directions (lanes), its 8 warps take every 8th entry, and the partial sums
-// are added in warp order.  Short dependent load chains per warp and many
-// blocks keep enough D and M loads in flight to cover the L2 latency.
-__global__ void __launch_bounds__(256) k_transfer_split(const LevelsArgs *__restrict__ A, const int *skip)
+// A block takes one target and kTransferDirs directions (lanes); its
+// kTransferWarps warps take every kTransferWarps-th list entry, each with
+// kTransferUnroll entries (their D and M loads) in flight, and the partial
+// sums are added in warp order.  Few warps per target with deep load
+// batches hold fewer registers and warps of an SM for the same L2 traffic,
+// which leaves room for the near-field product running beside.
+__global__ void __launch_bounds__(32 * kTransferWarps) k_transfer_split(const LevelsArgs *__restrict__ A,
+                                                                        const int *skip)
 {
     if (skip_now(skip)) return;
-    __shared__ float2 part[8][kTransferDirs];
+    __shared__ float2 part[kTransferWarps][kTransferDirs];
     __shared__ int2 s_ent[kTransferEntries];      // (source cluster, offset) of the list entries
     const int4 T = A->tgroups[blockIdx.x];
     const FarArgs &f = A->lev[T.x];
@@ -608,6 +610,8 @@ __global__ void __launch_bounds__(256) k_transfer_split(const LevelsArgs *__rest
     const bool live = nu < nd;
     const int b = f.il_ptr[t], e = f.il_ptr[t + 1];
     float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+    constexpr int kW = kTransferWarps, kU = kTransferUnroll;
+    static_assert(kU % 2 == 0, "entries are added in pairs");
     for (int c0 = b; c0 < e; c0 += kTransferEntries) {
         const int cnt = min(kTransferEntries, e - c0);
         __syncthreads();
@@ -616,20 +620,21 @@ __global__ void __launch_bounds__(256) k_transfer_split(const LevelsArgs *__rest
         __syncthreads();
         if (!live) continue;
         int q = warp;
-        for (; q + 24 < cnt; q += 32) {
-            float2 dv[4], mv[4];
+        for (; q + kW * (kU - 1) < cnt; q += kW * kU) {
+            float2 dv[kU], mv[kU];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int2 en = s_ent[q + 8 * u];
+            for (int u = 0; u < kU; ++u) {
+                const int2 en = s_ent[q + kW * u];
                 dv[u] = __ldg(f.D + (int64_t)en.y * nd + nu);
                 mv[u] = f.M[(int64_t)en.x * nd + nu];
             }
-            acc0 = cfma(dv[0], mv[0], acc0);
-            acc1 = cfma(dv[1], mv[1], acc1);
-            acc0 = cfma(dv[2], mv[2], acc0);
-            acc1 = cfma(dv[3], mv[3], acc1);
+#pragma unroll
+            for (int u = 0; u < kU; u += 2) {
+                acc0 = cfma(dv[u], mv[u], acc0);
+                acc1 = cfma(dv[u + 1], mv[u + 1], acc1);
+            }
         }
-        for (; q < cnt; q += 8) {
+        for (; q < cnt; q += kW) {
             const int2 en = s_ent[q];
             acc0 = cfma(__ldg(f.D + (int64_t)en.y * nd + nu), f.M[(int64_t)en.x * nd + nu], acc0);
         }
@@ -639,7 +644,7 @@ __global__ void __launch_bounds__(256) k_transfer_split(const LevelsArgs *__rest
     if (warp == 0 && live) {
         float2 sum = part[0][lane];
 #pragma unroll
-        for (int w = 1; w < 8; ++w) sum = cadd(sum, part[w][lane]);
+        for (int w = 1; w < kW; ++w) sum = cadd(sum, part[w][lane]);
         f.Lam[(int64_t)t * nd + nu] = sum;
     }
 }

@@ -148,9 +148,11 @@ __global__ void k_near_fused(NearArgs a, const float2 *x, float2 *y, int *err, c
 __global__ void k_prep(PrepArgs a, const int *skip);
 __global__ void k_aggregate(const LevelsArgs *A, const float4 *wts, const float4 *nrm, const int *skip);
 __global__ void k_selftest_sincos(const float *x, int64_t n, float4 *out);
-// Transfer with the interaction list of one target split among 8 warps:
-// one block per (target, kTransferDirs directions).
+// Transfer with the interaction list of one target split among
+// kTransferWarps warps: one block per (target, kTransferDirs directions).
 constexpr int kTransferDirs = 32;
+constexpr int kTransferWarps = 2;          // warps sharing one target's list
+constexpr int kTransferUnroll = 8;         // list entries per warp in flight
 constexpr int kTransferEntries = 512;     // interaction-list entries staged per pass
 __global__ void k_transfer_split(const LevelsArgs *A, const int *skip);
 __global__ void k_disaggregate(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
