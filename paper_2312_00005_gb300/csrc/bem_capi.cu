@@ -330,6 +330,10 @@ struct bem_mesh_impl {
     // side stream and events of the GMRES Givens steps inside one graph
     cudaStream_t s_giv = nullptr;
     cudaEvent_t ev_orth[kStepsPerGraph] = {}, ev_giv[kStepsPerGraph] = {};
+    // GMRES status after each graph: two pinned host copies and their events,
+    // so that the next graph is queued before the host waits for a status
+    GmresState *h_st = nullptr;
+    cudaEvent_t ev_st[2] = {};
     std::vector<float> coef_key;
 
     ElemDev elem() const
@@ -346,6 +350,9 @@ struct bem_mesh_impl {
             if (ev_orth[t]) cudaEventDestroy(ev_orth[t]);
             if (ev_giv[t]) cudaEventDestroy(ev_giv[t]);
         }
+        for (int t = 0; t < 2; ++t)
+            if (ev_st[t]) cudaEventDestroy(ev_st[t]);
+        if (h_st) cudaFreeHost(h_st);
         if (s_giv) cudaStreamDestroy(s_giv);
         if (s_setup) cudaStreamDestroy(s_setup);
         if (ev_fork) cudaEventDestroy(ev_fork);
@@ -1348,6 +1355,8 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
                 ck(cudaEventCreateWithFlags(&M->ev_orth[t], cudaEventDisableTiming), "event");
                 ck(cudaEventCreateWithFlags(&M->ev_giv[t], cudaEventDisableTiming), "event");
             }
+            for (int t = 0; t < 2; ++t) ck(cudaEventCreateWithFlags(&M->ev_st[t], cudaEventDisableTiming), "event");
+            ck(cudaMallocHost(&M->h_st, 2 * sizeof(GmresState)), "cudaMallocHost");
         }
         const int64_t n = n_tris;
         std::vector<float4> chi(n), clo(n), nr(n), va(n), e1(n), e2(n);
@@ -1651,23 +1660,42 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
         bool converged = false;
         GmresState h;
         for (;;) {
-            // Arnoldi cycle
-            for (int guard = 0; guard < m + batch; guard += batch) {
+            // Arnoldi cycle.  With graphs, graph g + 1 is queued before the
+            // host waits for the status copied after graph g, so the GPU
+            // does not idle while the host reads it; a graph queued after
+            // the cycle ended runs its steps as skips.
+            const int max_graphs = (m + batch + batch - 1) / batch;
+            int launched = 0, checked = 0;
+            auto launch_graph = [&]() {
                 if (use_graph) {
                     ck(cudaGraphLaunch(gexec, s), "graph launch");
                     g_launches.fetch_add(per_graph);
                 } else {
                     arnoldi_steps(1);
                 }
-                ck(cudaMemcpyAsync(&h, M.st.p, sizeof h, cudaMemcpyDeviceToHost, s), "D2H st");
-                ck(cudaStreamSynchronize(s), "sync");
+                GmresState *dst = M.h_st + (launched & 1);
+                ck(cudaMemcpyAsync(dst, M.st.p, sizeof *dst, cudaMemcpyDeviceToHost, s), "D2H st");
+                ck(cudaEventRecord(M.ev_st[launched & 1], s), "record st");
+                ++launched;
+            };
+            launch_graph();
+            for (;;) {
+                if (use_graph && launched < max_graphs) launch_graph();
+                ck(cudaEventSynchronize(M.ev_st[checked & 1]), "sync st");
+                h = M.h_st[checked & 1];
+                ++checked;
                 if (h.fault) {
+                    ck(cudaStreamSynchronize(s), "sync");
                     if (gexec) cudaGraphExecDestroy(gexec);
                     if (graph) cudaGraphDestroy(graph);
                     throw Fail{set_err(BEM_E_TIMEOUT, "GMRES: a grid barrier wait of the fused Gram-Schmidt "
                                                       "step gave up")};
                 }
                 if (h.done) break;
+                if (checked == launched) {
+                    if (launched >= max_graphs) break;
+                    launch_graph();
+                }
             }
             {
                 KTimer kt_("k_gm_backsolve", s);
