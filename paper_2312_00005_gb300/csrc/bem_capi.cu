@@ -1075,7 +1075,7 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
                                               " directions over all levels exceed the disaggregation kernel's "
                                               "shared-memory staging")};
         if (P.lists->n_dis_tasks > 0)
-            k_disaggregate<<<P.lists->n_dis_tasks, 128, smem, sd>>>(da, far_only ? nullptr : M.ynear.p, y, skip);
+            k_disaggregate<<<P.lists->n_dis_tasks, kDisThreads, smem, sd>>>(da, far_only ? nullptr : M.ynear.p, y, skip);
     }
     ck_launch("k_disaggregate");
     if (fork && far_only) {

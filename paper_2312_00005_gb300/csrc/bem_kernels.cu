@@ -654,30 +654,34 @@ __global__ void __launch_bounds__(32 * kTransferWarps) k_transfer_split(const Le
 // (when ynear is given; else y receives the far part alone):
 //   y_i = near_i + (ik/16 pi^2) sum_l sum_nu w_nu (1 + s_nu.n_i)
 //                   e^{ik (x_i - z_t).s_nu} Lambda_t(nu).
-// One block per task (at most kDisTask elements of one leaf; large leaves
-// are split so that no block is much longer than the others): the elements
-// of a leaf share their cluster at every level, so the weighted Lambda rows
-// of the leaf's ancestors and the directions are staged in shared memory.  Threads take antipodal
-// direction pairs (s_p, -s_p) of all levels (one phase and its conjugate),
-// each for a chunk of kDisChunk elements held in registers; the block then
-// sums each element's partials in a fixed order and writes y[perm[i]]
-// (caller order) or y[i].
+// One block of kDisThreads per task (at most kDisTask elements of one leaf;
+// large leaves are split so that no block is much longer than the others):
+// the elements of a leaf share their cluster at every level, so the
+// weighted Lambda rows of the leaf's ancestors, the directions and the
+// task's element data are staged in shared memory once.  Threads take
+// antipodal direction pairs (s_p, -s_p) of all levels (one phase and its
+// conjugate), each for a chunk of kDisChunk elements held in registers;
+// every warp leaves its sum per element in shared memory without waiting
+// for the others, and after one barrier the block adds the warps' sums in
+// warp order and writes y[perm[i]] (caller order) or y[i].
 constexpr int kDisChunk = 8;
-__global__ void __launch_bounds__(128, 8) k_disaggregate(DisaggArgs a, const float2 *__restrict__ ynear, float2 *__restrict__ y,
-                               const int *skip)
+__global__ void __launch_bounds__(kDisThreads, 16) k_disaggregate(DisaggArgs a, const float2 *__restrict__ ynear,
+                                                                  float2 *__restrict__ y, const int *skip)
 {
     if (skip_now(skip)) return;
     extern __shared__ float4 dsm[];   // [sum_nd / 2] first-half directions, then [sum_nd / 2] (A, B) pairs
     float4 *dir_s = dsm;
     float4 *ab_s = dsm + a.sum_nd / 2;
+    constexpr int kNW = kDisThreads / 32;
     __shared__ int s_lev[kMaxFarLevels], s_poff[kMaxFarLevels + 1];
     __shared__ int s_nact;
-    __shared__ float4 dzs[kDisChunk][kMaxFarLevels];   // -k/(2 pi) (z_c - x_i) per active level
-    __shared__ float4 ns[kDisChunk];
-    __shared__ float2 red[32][kDisChunk];
+    __shared__ float4 dzs[kDisTask][kMaxFarLevels];   // -k/(2 pi) (z_c - x_i) per active level
+    __shared__ float4 ns[kDisTask];
+    __shared__ float2 red[kNW][kDisTask];
     const int2 tk = a.tasks[blockIdx.x];
     const int64_t e0 = tk.x, e1 = tk.y;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int cnt_all = (int)min((int64_t)kDisTask, e1 - e0);   // the host never makes larger tasks
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         // active levels (the leaf's cluster has an interaction list there)
         int na = 0, poff = 0;
@@ -710,17 +714,17 @@ __global__ void __launch_bounds__(128, 8) k_disaggregate(DisaggArgs a, const flo
             ab_s[s_poff[u] + q] = make_float4(lp.x + lm.x, lp.y + lm.y, lp.x - lm.x, lp.y - lm.y);
         }
     }
-    for (int64_t c0 = e0; c0 < e1; c0 += kDisChunk) {
-        const int cnt = (int)min((int64_t)kDisChunk, e1 - c0);
-        for (int v = threadIdx.x; v < cnt * na; v += blockDim.x) {
-            const int q = v / na, u = v % na;
-            const FarArgs &f = a.lev[s_lev[u]];
-            const float kt = -f.k * 0.15915494309189535f;
-            const float4 dz = f.dz[c0 + q];              // z_c - x_i
-            dzs[q][u] = make_float4(kt * dz.x, kt * dz.y, kt * dz.z, 0.f);
-        }
-        for (int q = threadIdx.x; q < cnt; q += blockDim.x) ns[q] = a.nrm[c0 + q];
-        __syncthreads();
+    for (int v = threadIdx.x; v < cnt_all * na; v += blockDim.x) {
+        const int q = v / na, u = v % na;
+        const FarArgs &f = a.lev[s_lev[u]];
+        const float kt = -f.k * 0.15915494309189535f;
+        const float4 dz = f.dz[e0 + q];              // z_c - x_i
+        dzs[q][u] = make_float4(kt * dz.x, kt * dz.y, kt * dz.z, 0.f);
+    }
+    for (int q = threadIdx.x; q < cnt_all; q += blockDim.x) ns[q] = a.nrm[e0 + q];
+    __syncthreads();
+    for (int q0 = 0; q0 < cnt_all; q0 += kDisChunk) {
+        const int cnt = min(kDisChunk, cnt_all - q0);
         float2 acc[kDisChunk];
 #pragma unroll
         for (int q = 0; q < kDisChunk; ++q) acc[q] = make_float2(0.f, 0.f);
@@ -731,7 +735,7 @@ __global__ void __launch_bounds__(128, 8) k_disaggregate(DisaggArgs a, const flo
 #pragma unroll
             for (int q = 0; q < kDisChunk; ++q) {
                 if (q < cnt) {
-                    const float4 d = dzs[q][u], n = ns[q];
+                    const float4 d = dzs[q0 + q][u], n = ns[q0 + q];
                     float sn0, cs0;
                     sincos_turns(fmaf(d.x, sv.x, fmaf(d.y, sv.y, d.z * sv.z)), &sn0, &cs0);
                     const float tn = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
@@ -746,22 +750,22 @@ __global__ void __launch_bounds__(128, 8) k_disaggregate(DisaggArgs a, const flo
 #pragma unroll
         for (int q = 0; q < kDisChunk; ++q) {
             const float2 v = warp_sum(acc[q]);
-            if (lane == 0) red[warp][q] = v;
+            if (lane == 0 && q < cnt) red[warp][q0 + q] = v;
         }
-        __syncthreads();
-        if (threadIdx.x < cnt) {
-            const int q = threadIdx.x;
-            float2 v = red[0][q];
-            for (int w = 1; w < nw; ++w) v = cadd(v, red[w][q]);
-            const int64_t i = c0 + q;
-            // (ik / 16 pi^2) v
-            const float sc = a.k * 0.00633257397764611f;   // k / (16 pi^2)
-            const float2 far = make_float2(-sc * v.y, sc * v.x);
-            const float2 out = ynear ? cadd(ynear[i], far) : far;
-            if (a.perm) y[a.perm[i]] = out;
-            else y[i] = out;
-        }
-        __syncthreads();
+    }
+    __syncthreads();
+    if (threadIdx.x < cnt_all) {
+        const int q = threadIdx.x;
+        float2 v = red[0][q];
+#pragma unroll
+        for (int w = 1; w < kNW; ++w) v = cadd(v, red[w][q]);
+        const int64_t i = e0 + q;
+        // (ik / 16 pi^2) v
+        const float sc = a.k * 0.00633257397764611f;   // k / (16 pi^2)
+        const float2 far = make_float2(-sc * v.y, sc * v.x);
+        const float2 out = ynear ? cadd(ynear[i], far) : far;
+        if (a.perm) y[a.perm[i]] = out;
+        else y[i] = out;
     }
 }
 

@@ -79,8 +79,10 @@ struct AggTask {
     int p0;                  // first direction pair
 };
 
-// Disaggregation work item: elements [x, y) of one leaf, at most kDisTask.
+// Disaggregation work item: elements [x, y) of one leaf, at most kDisTask,
+// one block of kDisThreads threads each.
 constexpr int kDisTask = 16;
+constexpr int kDisThreads = 64;
 
 struct FarArgs {
     int nd;                  // 2 L^2 directions
