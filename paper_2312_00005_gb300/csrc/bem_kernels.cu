@@ -1173,16 +1173,26 @@ __global__ void __launch_bounds__(kOrthoThreads) k_gm_ortho(OrthoArgs a)
 {
     const GmresArgs &g = a.g;
     GmresState *st = g.st;
-    const int done = *(volatile int *)&st->done;
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->skip_prod = done;
-    if (done || *(volatile int *)a.err) return;
-    const int j = *(volatile int *)&st->j;
     const int G = gridDim.x, b = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = kOrthoThreads / 32;
     constexpr int kRowsPerPass = 128, kCg = kOrthoThreads / kRowsPerPass;
     const int64_t r0 = (int64_t)b * a.rows;
     const int64_t rem = g.n - r0;
     const int R = rem <= 0 ? 0 : (int)(rem < a.rows ? rem : (int64_t)a.rows);
+    // w = A v_j (far part g.w + near part) and the state (j, done; fault)
+    // are loaded together: one memory round trip before any decision
+    constexpr int kWr = kOrthoMaxRows / kOrthoThreads;
+    float2 wv[kWr];
+#pragma unroll
+    for (int u = 0; u < kWr; ++u) {
+        const int i = threadIdx.x + u * kOrthoThreads;
+        wv[u] = i < R ? cadd(g.w[r0 + i], a.wnear[r0 + i]) : make_float2(0.f, 0.f);
+    }
+    const int2 jd = __ldcv(reinterpret_cast<const int2 *>(&st->j));   // (j, done)
+    const int fault = __ldcv(a.err);
+    const int j = jd.x, done = jd.y;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->skip_prod = done;
+    if (done || fault) return;
     float2 *part = (float2 *)g.part;              // [m + 1][G]
     float2 *npart = (float2 *)g.normpart;         // [G] (x: ||w||^2 partial)
     __shared__ float2 ws[kOrthoMaxRows];
@@ -1191,8 +1201,11 @@ __global__ void __launch_bounds__(kOrthoThreads) k_gm_ortho(OrthoArgs a)
     __shared__ float red[kOrthoThreads / 32];
     __shared__ float s_hh;
     __shared__ double s_nn;
-    // w = A v_j: far part (g.w) + near part
-    for (int i = threadIdx.x; i < R; i += kOrthoThreads) ws[i] = cadd(g.w[r0 + i], a.wnear[r0 + i]);
+#pragma unroll
+    for (int u = 0; u < kWr; ++u) {
+        const int i = threadIdx.x + u * kOrthoThreads;
+        if (i < R) ws[i] = wv[u];
+    }
     __syncthreads();
     double nn = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
