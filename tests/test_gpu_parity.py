@@ -131,6 +131,24 @@ def test_solve_and_field_match_oracle(bem):
     assert np.allclose(q.cpu().numpy(), 0)
 
 
+@pytest.mark.parametrize("restart", [4, 6, 7])
+def test_restarted_gmres_matches_oracle(bem, restart):
+    """GMRES restarted every 4, 6 or 7 steps (the Arnoldi steps run as
+    graphs of four, and the next graph is queued before the previous one's
+    status is read, so cycles end inside and at the end of graphs): several
+    restarts, and the solution still matches the oracle's."""
+    nodes, tris = inputs.icosphere(3, 0.1)
+    freq = 1000.0
+    mesh = bem.Mesh(nodes, tris, restart=restart)
+    src = [bem.plane_wave((0, 0, 1))]
+    p, q, info = mesh.solve(freq, src, tol=1e-7, c=C, rho=RHO)
+    mesh.close()
+    assert info["converged"] and info["restarts"] >= 1, info
+    po, qo, _ = oracle.solve(nodes, tris, freq, c=C, rho=RHO, sources=[("plane", (0, 0, 1.0), 1.0)])
+    ep = _rel(p.cpu().numpy(), po)
+    assert ep < 1e-4, ep
+
+
 def test_mixed_boundary_solve_matches_oracle(bem):
     nodes, tris = inputs.icosphere(3, 0.1)
     n = tris.shape[0]
