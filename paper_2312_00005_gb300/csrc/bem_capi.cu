@@ -319,6 +319,7 @@ struct bem_mesh_impl {
     DevArr<float2> spare_val;
     std::vector<std::unique_ptr<DevArr<float2>>> spare_bufs;
     DevArr<SourceDev> srcbuf;
+    DevArr<float2> fieldpart;     // per-point partial sums of the field (point-major)
     DevArr<double> ptsbuf;
     std::map<int, std::unique_ptr<DepthDev>> depth_dev;
     std::map<int, double> growth_root;                 // x*(L) of the Hankel stability test
@@ -1700,7 +1701,7 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
             {
                 KTimer kt_("k_gm_backsolve", s);
                 const int tri_cols = std::min(m, 100);
-                k_gm_backsolve<<<1, 32, (size_t)tri_cols * tri_cols * sizeof(double2), s>>>(M.st.p, M.H.p, M.g_.p,
+                k_gm_backsolve<<<1, 256, (size_t)tri_cols * tri_cols * sizeof(double2), s>>>(M.st.p, M.H.p, M.g_.p,
                                                                                            M.yv.p, m, tri_cols);
             }
             ck_launch("k_gm_backsolve");
@@ -1953,12 +1954,30 @@ int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem
         sdev.upload(sv, s);
         reset_err(M);
         const double k = wavenumber(freq_hz, c);
+        // each point's element sum split over S blocks when the points alone
+        // would leave SMs idle (partials added in slice order)
+        int nsm = 0;
+        ck(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, M.device), "attribute");
+        const int64_t want = 8 * (int64_t)nsm;
+        const int S = (int)std::max<int64_t>(1, std::min<int64_t>({16, (want + M_pts - 1) / M_pts,
+                                                                   (n + 255) / 256}));
+        if (S > 1) M.fieldpart.alloc((size_t)M_pts * S);
         {
             KTimer kt_("k_field", s);
-            k_field<<<(unsigned)M_pts, 256, 0, s>>>(M.elem(), M.Q.p, dp.p, M_pts, (float)k, M.tmp.p, M.tmp2.p, sdev.p,
-                                              n_src, (float2 *)out_dev, fr(M).err.p);
+            k_field<<<dim3((unsigned)M_pts, (unsigned)S), 256, 0, s>>>(M.elem(), M.Q.p, dp.p, M_pts, (float)k,
+                                                                      M.tmp.p, M.tmp2.p, sdev.p, n_src,
+                                                                      M.fieldpart.p, (float2 *)out_dev,
+                                                                      fr(M).err.p);
         }
         ck_launch("k_field");
+        if (S > 1) {
+            {
+                KTimer kt_("k_field", s);
+                k_field_finish<<<nblocks(M_pts, 128), 128, 0, s>>>(dp.p, M_pts, S, (float)k, sdev.p, n_src,
+                                                                  M.fieldpart.p, (float2 *)out_dev);
+            }
+            ck_launch("k_field_finish");
+        }
         check_err(M);
         join_streams(s, us);
         resolve_timing();

@@ -887,13 +887,39 @@ __global__ void k_rhs(const double *__restrict__ cd, const float4 *__restrict__ 
 }
 
 // ------------------------------------------------------------------ field evaluation
-// p(x) = p_inc(x) + sum_j [H(x)_j p_j - G(x)_j q_j] (Eq. BIE_I, lambda = 1);
-// one block per field point, threads over elements.
+// p(x) = p_inc(x) + sum_j [H(x)_j p_j - G(x)_j q_j] (Eq. BIE_I, lambda = 1).
+// Block (m, s) takes field point m and every S-th slice of blockDim
+// elements from slice s, threads over elements.  With S = 1 the block adds
+// the incident field and writes p(x_m); otherwise it leaves its partial sum
+// in part[m S + s] and k_field_finish adds the S partials in slice order.
+__device__ void field_incident(const double *xd, float k, const SourceDev *__restrict__ src, int nsrc, double &br,
+                               double &bi)
+{
+    for (int s = 0; s < nsrc; ++s) {
+        const SourceDev S = src[s];
+        double sn, cs, gr, gi;
+        if (S.kind == 0) {
+            sincos((double)k * (S.v[0] * xd[0] + S.v[1] * xd[1] + S.v[2] * xd[2]), &sn, &cs);
+            gr = cs; gi = sn;
+        } else {
+            const double d0 = xd[0] - S.v[0], d1 = xd[1] - S.v[1], d2 = xd[2] - S.v[2];
+            const double R = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+            sincos((double)k * R, &sn, &cs);
+            gr = cs / (4.0 * 3.14159265358979323846 * R);
+            gi = sn / (4.0 * 3.14159265358979323846 * R);
+        }
+        br += S.amp[0] * gr - S.amp[1] * gi;
+        bi += S.amp[0] * gi + S.amp[1] * gr;
+    }
+}
+
 __global__ void k_field(ElemDev E, const QuadTables *__restrict__ Qp, const double *__restrict__ pts, int64_t M,
                         float k, const float2 *__restrict__ p, const float2 *__restrict__ q,
-                        const SourceDev *__restrict__ src, int nsrc, float2 *__restrict__ out, int *err)
+                        const SourceDev *__restrict__ src, int nsrc, float2 *__restrict__ part,
+                        float2 *__restrict__ out, int *err)
 {
     const int64_t m = blockIdx.x;
+    const int S = gridDim.y, sl = blockIdx.y;
     if (m >= M) return;
     const QuadTables &Q = *Qp;
     const double xd[3] = {pts[3 * m], pts[3 * m + 1], pts[3 * m + 2]};
@@ -901,7 +927,7 @@ __global__ void k_field(ElemDev E, const QuadTables *__restrict__ Qp, const doub
     const float3 xlo = make_float3((float)(xd[0] - (double)xhi.x), (float)(xd[1] - (double)xhi.y),
                                    (float)(xd[2] - (double)xhi.z));
     float2 acc = make_float2(0.f, 0.f);
-    for (int64_t j = threadIdx.x; j < E.n; j += blockDim.x) {
+    for (int64_t j = (int64_t)sl * blockDim.x + threadIdx.x; j < E.n; j += (int64_t)S * blockDim.x) {
         float2 G = make_float2(0.f, 0.f), H = make_float2(0.f, 0.f);
         if (!integrate_regular<true>(E, j, xhi, xlo, xd, make_float3(0.f, 0.f, 1.f), k, 1.0f / k, Q, G, H)) {
             atomicMin(err, (int)j);
@@ -917,26 +943,31 @@ __global__ void k_field(ElemDev E, const QuadTables *__restrict__ Qp, const doub
         float2 v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : make_float2(0.f, 0.f);
         v = warp_sum(v);
         if (threadIdx.x == 0) {
-            double br = v.x, bi = v.y;
-            for (int s = 0; s < nsrc; ++s) {
-                const SourceDev S = src[s];
-                double sn, cs, gr, gi;
-                if (S.kind == 0) {
-                    sincos((double)k * (S.v[0] * xd[0] + S.v[1] * xd[1] + S.v[2] * xd[2]), &sn, &cs);
-                    gr = cs; gi = sn;
-                } else {
-                    const double d0 = xd[0] - S.v[0], d1 = xd[1] - S.v[1], d2 = xd[2] - S.v[2];
-                    const double R = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-                    sincos((double)k * R, &sn, &cs);
-                    gr = cs / (4.0 * 3.14159265358979323846 * R);
-                    gi = sn / (4.0 * 3.14159265358979323846 * R);
-                }
-                br += S.amp[0] * gr - S.amp[1] * gi;
-                bi += S.amp[0] * gi + S.amp[1] * gr;
+            if (S > 1) {
+                part[m * S + sl] = v;
+            } else {
+                double br = v.x, bi = v.y;
+                field_incident(xd, k, src, nsrc, br, bi);
+                out[m] = make_float2((float)br, (float)bi);
             }
-            out[m] = make_float2((float)br, (float)bi);
         }
     }
+}
+
+// The S partial sums of each field point in slice order, plus the incident
+// field; one thread per point.
+__global__ void k_field_finish(const double *__restrict__ pts, int64_t M, int S, float k,
+                               const SourceDev *__restrict__ src, int nsrc, const float2 *__restrict__ part,
+                               float2 *__restrict__ out)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    float2 v = part[m * S];
+    for (int s = 1; s < S; ++s) v = cadd(v, part[m * S + s]);
+    const double xd[3] = {pts[3 * m], pts[3 * m + 1], pts[3 * m + 2]};
+    double br = v.x, bi = v.y;
+    field_incident(xd, k, src, nsrc, br, bi);
+    out[m] = make_float2((float)br, (float)bi);
 }
 
 // ------------------------------------------------------------------ vector helpers
@@ -1339,28 +1370,37 @@ __global__ void k_gm_givens(GmresArgs a)
 }
 
 // Back substitution y = R^{-1} g over ncols columns (FP64), one warp:
-// column-oriented, each step divides one entry and the lanes update the rest.
-// The triangle is staged in shared memory when it fits (smem_cols columns).
+// column-oriented, each step scales one entry by the reciprocal of its
+// diagonal and the lanes update the rest.  The reciprocals 1 / R_ll are
+// formed first, all in parallel, so the sequential chain of steps holds no
+// division (FP64 division is a long dependent sequence on this part).  The
+// triangle is staged in shared memory when it fits (smem_cols columns).
 __global__ void k_gm_backsolve(const GmresState *st, const double2 *__restrict__ H, const double2 *__restrict__ g,
                                double2 *__restrict__ y, int m, int smem_cols)
 {
-    extern __shared__ double2 tri[];       // [nc][nc] when nc <= smem_cols
+    extern __shared__ double2 tri[];       // [nc][nc] when nc <= smem_cols (upper triangle filled)
     __shared__ double2 sv[kMaxRestart + 1];
+    __shared__ double2 rinv[kMaxRestart + 1];
     const int nc = st->ncols;
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const bool in_smem = nc <= smem_cols;
-    for (int l = lane; l < nc; l += 32) sv[l] = g[l];
+    // staging by the whole block (its loads independent of one another),
+    // then warp 0 alone runs the sequential steps
+    for (int l = threadIdx.x; l < nc; l += blockDim.x) {
+        sv[l] = g[l];
+        const double2 d = H[(int64_t)l * m + l];
+        const double inv = 1.0 / (d.x * d.x + d.y * d.y);
+        rinv[l] = make_double2(d.x * inv, -d.y * inv);   // conj(d) / |d|^2
+    }
     if (in_smem)
-        for (int q = lane; q < nc * nc; q += 32) {
-            const int r = q / nc, c = q % nc;
-            tri[q] = H[(int64_t)r * m + c];
-        }
-    __syncwarp();
+        for (int r = threadIdx.x / 32; r < nc; r += blockDim.x / 32)
+            for (int c = r + lane; c < nc; c += 32) tri[r * nc + c] = H[(int64_t)r * m + c];
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
     for (int l = nc - 1; l >= 0; --l) {
-        const double2 d = in_smem ? tri[l * nc + l] : H[(int64_t)l * m + l];
-        const double dd = d.x * d.x + d.y * d.y;
+        const double2 ri = rinv[l];
         const double2 sl = sv[l];
-        const double2 yl = make_double2((sl.x * d.x + sl.y * d.y) / dd, (sl.y * d.x - sl.x * d.y) / dd);
+        const double2 yl = make_double2(sl.x * ri.x - sl.y * ri.y, sl.x * ri.y + sl.y * ri.x);
         if (lane == 0) y[l] = yl;
         for (int r = lane; r < l; r += 32) {
             const double2 h = in_smem ? tri[r * nc + l] : H[(int64_t)r * m + l];
