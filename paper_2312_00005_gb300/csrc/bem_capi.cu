@@ -642,19 +642,32 @@ void finish_plan(bem_mesh_impl &M, Plan &Pl)
         take_spare(M, D->D, (size_t)D->noff * D->nd);
         take_spare(M, D->M, (size_t)(D->nc + D->ll->nextra) * D->nd);
         take_spare(M, D->Lam, (size_t)D->nc * D->nd);
-        const int64_t tot = (int64_t)D->noff * D->nd;
-        if (tot > 0) {
+        if ((int64_t)D->noff * D->nd > 0 && D->L > kMaxTableL)
+            throw Fail{set_err(BEM_E_ARG, "far field: expansion length " + std::to_string(D->L) +
+                                              " exceeds the translation-table limit " + std::to_string(kMaxTableL))};
+        P->lev.push_back(std::move(D));
+    }
+    {
+        // translation tables of every level in one launch
+        DTableArgs ta;
+        memset(&ta, 0, sizeof ta);
+        ta.k = k;
+        int nb = 0;
+        for (const auto &D : P->lev) {
+            if ((int64_t)D->noff * D->nd == 0) continue;
+            ta.start[ta.nlev] = nb;
+            ta.lev[ta.nlev] = DTableLevel{D->ll->offs.p, D->dirs_d.p, D->D.p, D->nd, D->L};
+            nb += D->noff;
+            ++ta.nlev;
+        }
+        ta.start[ta.nlev] = nb;
+        if (nb > 0) {
             {
                 KTimer kt_("k_dtable", s);
-                if (D->L > kMaxTableL)
-                    throw Fail{set_err(BEM_E_ARG, "far field: expansion length " + std::to_string(D->L) +
-                                                      " exceeds the translation-table limit " +
-                                                      std::to_string(kMaxTableL))};
-                k_dtable<<<D->noff, 128, 0, s>>>(D->ll->offs.p, D->noff, D->dirs_d.p, D->nd, D->L, k, D->D.p);
+                k_dtable<<<nb, 128, 0, s>>>(ta);
             }
             ck_launch("k_dtable");
         }
-        P->lev.push_back(std::move(D));
     }
     LevelsArgs &A = P->hargs;
     memset(&A, 0, sizeof A);

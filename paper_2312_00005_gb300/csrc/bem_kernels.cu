@@ -771,9 +771,10 @@ __global__ void __launch_bounds__(kDisThreads, 16) k_disaggregate(DisaggArgs a, 
 
 // Translation table per distinct offset X (Eq. FMMBase):
 //   D_L(X, s_nu) = sum_{n=0}^{L} i^n (2n+1) h_n(k|X|) P_n(X.s_nu / |X|),
-// FP64, spherical Hankel functions by upward recursion (Sec. 4.2).
-__global__ void k_dtable(const double *__restrict__ offs, int noff, const double *__restrict__ dirs, int nd,
-                         int L, double k, float2 *__restrict__ D)
+// FP64, spherical Hankel functions by upward recursion (Sec. 4.2).  The
+// offsets of every far level in one launch (each block's work is a short
+// serial FP64 chain, so the levels' blocks run side by side).
+__global__ void k_dtable(DTableArgs a)
 {
     // one block per offset X: the coefficients c_n = (2n+1) i^n h_n(k|X|)
     // depend on X only and are formed once (thread 0, upward recursion);
@@ -782,7 +783,15 @@ __global__ void k_dtable(const double *__restrict__ offs, int noff, const double
     // D(X, s) = E + O and D(X, -s) = E - O.
     __shared__ double2 cn[kMaxTableL + 1];
     __shared__ double inv[kMaxTableL + 1];
-    const int o = blockIdx.x;
+    int lv = 0;
+    while (lv + 1 < a.nlev && (int)blockIdx.x >= a.start[lv + 1]) ++lv;
+    const DTableLevel &T = a.lev[lv];
+    const int o = blockIdx.x - a.start[lv];
+    const double *__restrict__ offs = T.offs;
+    const double *__restrict__ dirs = T.dirs;
+    const int nd = T.nd, L = T.L;
+    const double k = a.k;
+    float2 *__restrict__ D = T.D;
     const double X0 = offs[3 * o], X1 = offs[3 * o + 1], X2 = offs[3 * o + 2];
     const double R = sqrt(X0 * X0 + X1 * X1 + X2 * X2);
     if (threadIdx.x == 0) {

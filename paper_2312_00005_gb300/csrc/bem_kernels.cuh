@@ -160,7 +160,21 @@ __global__ void k_transfer_split(const LevelsArgs *A, const int *skip);
 __global__ void k_disaggregate(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
 // largest expansion length of the translation tables (shared-memory rows)
 constexpr int kMaxTableL = 255;
-__global__ void k_dtable(const double *offs, int noff, const double *dirs, int nd, int L, double k, float2 *D);
+// Translation tables of every far level: block b serves offset
+// b - start[l] of the level l with start[l] <= b < start[l + 1].
+struct DTableLevel {
+    const double *offs;      // [noff][3] offsets z_t - z_s
+    const double *dirs;      // [nd][3] directions (first half: one of each antipodal pair)
+    float2 *D;               // [noff][nd]
+    int nd, L;
+};
+struct DTableArgs {
+    int nlev;
+    double k;
+    int start[kMaxFarLevels + 1];
+    DTableLevel lev[kMaxFarLevels];
+};
+__global__ void k_dtable(DTableArgs a);
 __global__ void k_rhs(const double *cd, const float4 *nrm, int64_t n, double k, const SourceDev *src, int nsrc,
                       float2 *b);
 __global__ void k_field(ElemDev E, const QuadTables *Q, const double *pts, int64_t M, float k, const float2 *p,
