@@ -96,7 +96,9 @@ __global__ void k_near_classify(NearArgs a, int2 *__restrict__ heavy, unsigned l
 // thread holds its column's element data in registers and walks the leaf's
 // rows, whose data sit in shared memory (broadcast reads); the 32 columns of
 // a warp then write 32 consecutive values of one row.  r~ is compared in
-// squared form (FP64 when within 2e-5 of a threshold).
+// squared form (FP64 when within 2e-5 of a threshold).  Four blocks per SM
+// (64 registers, a few spilled) keep more warps issuing than two blocks
+// with every value in registers.
 constexpr int kLightRows = 64;
 // the general rule out of line, so that the common path keeps few registers
 __device__ __noinline__ bool general_entry(const ElemDev &E, int64_t i, int64_t j, float3 xhi, float3 xlo,
@@ -121,7 +123,7 @@ __device__ __forceinline__ float2 order23_entry(const ElemDev &E, int j, float3 
     return cadd(cmul(cpj, Kp), cmul(cqj, Kq));
 }
 
-__global__ void __launch_bounds__(256) k_near_store_light(NearArgs a, float2 *__restrict__ val,
+__global__ void __launch_bounds__(256, 4) k_near_store_light(NearArgs a, float2 *__restrict__ val,
                                                           int *__restrict__ err)
 {
     __shared__ float4 s_hi[kLightRows], s_lo[kLightRows], s_n[kLightRows];
