@@ -309,7 +309,9 @@ __global__ void k_near_spmv(NearArgs a, const float2 *__restrict__ val, const fl
 // range of rows of one leaf; the leaf's near columns x are staged in shared
 // memory (kept while consecutive items share the leaf) and the item's values
 // (rows x ncol, contiguous) are split evenly among the warps, which stream
-// them from HBM (evict-first, 16 loads per lane in flight).  Each warp
+// them from HBM (evict-first, 8 loads per lane in flight: enough for
+// the bandwidth with 8 blocks per SM, and few registers, which the far-field
+// kernels running beside need).  Each warp
 // leaves a partial per row it touched; the block sums them in warp order.
 // One block per item: items are small, so the block scheduler balances the
 // work across SMs (and shares them with the far-field kernels running
@@ -324,12 +326,12 @@ __device__ __forceinline__ float2 spmv_segment(const float2 *__restrict__ v, con
     float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
     int q = (c0 >> 1) + lane;
     const int qe = c1 >> 1;
-    for (; q + 480 < qe; q += 512) {
-        float4 vv[16];
+    for (; q + 224 < qe; q += 256) {
+        float4 vv[8];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) vv[u] = __ldcs(v4 + q + 32 * u);
+        for (int u = 0; u < 8; ++u) vv[u] = __ldcs(v4 + q + 32 * u);
 #pragma unroll
-        for (int u = 0; u < 16; u += 2) {
+        for (int u = 0; u < 8; u += 2) {
             const float4 xa = x4[q + 32 * u], xb = x4[q + 32 * (u + 1)];
             acc0 = cfma(make_float2(vv[u].x, vv[u].y), make_float2(xa.x, xa.y), acc0);
             acc1 = cfma(make_float2(vv[u].z, vv[u].w), make_float2(xa.z, xa.w), acc1);
