@@ -68,7 +68,7 @@ struct PrepArgs {
 // written to row `row` of the multipole buffer (row c when the cluster is
 // one element chunk).
 constexpr int kAggThreads = 64;
-constexpr int kAggChunk = 32;
+constexpr int kAggChunk = 64;
 struct AggTask {
     int c, row;
     int64_t e0;
