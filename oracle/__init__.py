@@ -27,7 +27,7 @@ __all__ = [
     "lib", "build", "VELO", "PRES", "ADMI", "geometry", "gauss_legendre", "gauss_jacobi10",
     "triangle_rule", "quad_order", "kernels", "element_integrals", "duffy_G", "edge_fp",
     "column_coeffs", "assemble", "matvec_rows", "matvec_dense", "gmres", "incident", "rhs",
-    "solve", "field", "sph_hankel", "sphere_grid", "translation", "fmm_pair", "num_threads",
+    "solve", "field", "field_velocity", "sph_hankel", "sphere_grid", "translation", "fmm_pair", "num_threads",
     "OracleError",
 ]
 
@@ -82,6 +82,7 @@ def lib():
                 "orc_gmres": (i, [P, l, P, P, d, i, i, P, P]),
                 "orc_incident": (None, [P, P, l, d, i, P, P, P, P]),
                 "orc_field": (i, [P, P, l, d, P, P, P, P, l, P, P]),
+                "orc_field_grad": (i, [P, P, l, d, P, P, P, P, l, P, P]),
                 "orc_sph_hankel": (None, [i, d, P]),
                 "orc_sphere_grid": (i, [i, P, P]),
                 "orc_translation": (None, [i, d, P, P, i, P]),
@@ -363,6 +364,34 @@ def field(nodes, tris, freq, p, q, pts, c=343.0, sources=(), params=None):
         pi, _ = incident(pts, None, k, kind, vec, amp)
         out += pi
     return out
+
+
+def field_velocity(nodes, tris, freq, p, q, pts, c=343.0, rho=1.21, sources=(), params=None):
+    """Particle velocity at exterior points, v = grad p / (i w rho)
+    (Eq. utopandv), with grad p = grad p_inc + sum_j [grad H_j p_j - grad G_j q_j]
+    (Eq. BIE_I, lambda = 1, differentiated under the integral; the component
+    along an axis e uses the kernels H' and E of Eq. dBIE with n_x = e).
+    Returns complex [npts, 3]."""
+    nodes, tris = _f64(nodes), _i32(tris)
+    n = tris.shape[0]
+    pts = _f64(pts, (-1, 3))
+    k = 2.0 * np.pi * freq / c
+    grad = np.zeros((pts.shape[0], 3), np.complex128)
+    bad = ctypes.c_long(-1)
+    pr = _params(params)
+    st = lib().orc_field_grad(_p(nodes), _p(tris), n, float(k), _p(_c128(p)), _p(_c128(q)), _pp(pr),
+                              _p(pts), pts.shape[0], _p(grad), ctypes.byref(bad))
+    if st:
+        raise OracleError("number of subdivisions exceeds the limit at element %d" % bad.value,
+                          bad.value)
+    for (kind, vec, amp) in sources:
+        for ax in range(3):
+            e = np.zeros_like(pts)
+            e[:, ax] = 1.0
+            _, dpi = incident(pts, e, k, kind, vec, amp)
+            grad[:, ax] += dpi
+    omega = 2.0 * np.pi * freq
+    return grad / (1j * omega * rho)
 
 
 # ---------------------------------------------------------------- FMM pieces (unit tests)

@@ -25,7 +25,8 @@
  *     per-column coefficients that fold in the boundary conditions;
  *   - a dense O(N^2) matrix-vector product and restarted GMRES;
  *   - the field at exterior points from the representation formula with
- *     lambda = 1 (Eq. BIE_I);
+ *     lambda = 1 (Eq. BIE_I), and its gradient (the particle velocity of
+ *     Eq. utopandv) from the same formula differentiated under the integral;
  *   - the pieces of the plane-wave expansion of Eq. FMMBase (spherical Hankel
  *     functions by upward recursion, Legendre polynomials, the unit-sphere
  *     grid of Sec. 3.3.1, the translation D_L and the single-pair expansion)
@@ -846,6 +847,54 @@ int orc_field(const double *nodes, const int *tris, long n, double k, const doub
         }
         out[2 * r] = creal(s);
         out[2 * r + 1] = cimag(s);
+    }
+    free(cen); free(nrm); free(area);
+    if (bad_elem) *bad_elem = bad;
+    return bad >= 0 ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of the scattered field at exterior points, for the particle     */
+/* velocity of Eq. utopandv (v = grad p / (i w rho)) that the paper writes   */
+/* per field point (appendix Output): differentiating Eq. BIE_I (lambda = 1) */
+/* under the integral (x is off the surface), the component along a unit     */
+/* vector e is                                                               */
+/*   e . grad p_s(x) = sum_j [ E(x)_j p_j - H'(x)_j q_j ],                   */
+/* where H' = dG/dn_x and E = d2G/dn_x dn_y are the kernels of Eq. dBIE with */
+/* n_x = e.  Same element rules as orc_field.  out: [npts][3] complex (the   */
+/* x, y, z components).  Returns 0 or -1 (subdivision limit).                */
+/* ------------------------------------------------------------------------ */
+int orc_field_grad(const double *nodes, const int *tris, long n, double k, const double *p,
+                   const double *q, const double *params, const double *pts, long npts, double *out,
+                   long *bad_elem)
+{
+    ensure_rules();
+    orc_params P;
+    read_params(params, &P);
+    double *cen = (double *)malloc(sizeof(double) * 3 * n), *nrm = (double *)malloc(sizeof(double) * 3 * n),
+           *area = (double *)malloc(sizeof(double) * n);
+    orc_geometry(nodes, tris, n, cen, nrm, area);
+    const cplx *pv = (const cplx *)p, *qv = (const cplx *)q;
+    long bad = -1;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long r = 0; r < npts; ++r) {
+        for (int ax = 0; ax < 3; ++ax) {
+            double e[3] = {0.0, 0.0, 0.0};
+            e[ax] = 1.0;
+            cplx s = 0.0;
+            for (long j = 0; j < n; ++j) {
+                const double *a = nodes + 3 * tris[3 * j], *b = nodes + 3 * tris[3 * j + 1],
+                             *c = nodes + 3 * tris[3 * j + 2];
+                cplx o[4] = {0.0, 0.0, 0.0, 0.0};
+                if (regular_integrals(pts + 3 * r, e, a, b, c, nrm + 3 * j, k, 0, &P, o)) {
+#pragma omp critical
+                    { if (bad < 0 || j < bad) bad = j; }
+                }
+                s += o[3] * pv[j] - o[2] * qv[j];
+            }
+            out[6 * r + 2 * ax] = creal(s);
+            out[6 * r + 2 * ax + 1] = cimag(s);
+        }
     }
     free(cen); free(nrm); free(area);
     if (bad_elem) *bad_elem = bad;
