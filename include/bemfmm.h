@@ -209,6 +209,19 @@ int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem
                  int32_t n_src, const void *p_dev, const void *q_dev, const double *pts,
                  int64_t M, void *out_dev, void *stream);
 
+/* Particle velocity at M exterior points (Eq. utopandv: v = grad p / (i w
+ * rho); the paper writes its x, y and z components per evaluation point,
+ * appendix Output, file vEvalGrid): grad p(x) = grad p_inc(x) +
+ * sum_j [grad H(x)_j p_j - grad G(x)_j q_j], i.e. Eq. BIE_I (lambda = 1)
+ * differentiated under the integral, with the element rules of
+ * bem_evaluate.  rho from medium.  p_dev, q_dev: device cf32 [n_tris]
+ * (caller order, as written by bem_solve).  pts: host double [M][3].
+ * v_out_dev: device cf32 [M][3] (x, y, z components of each point).
+ * Errors as for bem_evaluate. */
+int bem_evaluate_velocity(void *mesh, double freq_hz, const bem_medium *medium, const bem_source *srcs,
+                          int32_t n_src, const void *p_dev, const void *q_dev, const double *pts, int64_t M,
+                          void *v_out_dev, void *stream);
+
 /* Plan statistics for a frequency (builds the plan if needed). */
 int bem_mesh_stats(void *mesh, double freq_hz, const bem_medium *medium, bem_plan_stats *out);
 

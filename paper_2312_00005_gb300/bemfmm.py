@@ -108,6 +108,8 @@ def lib():
                                             i64, P, P]),
             "bem_solve_sweep": (ctypes.c_int, [P, P, i32, ctypes.POINTER(Medium), P, i32, ctypes.POINTER(Source), i32,
                                                d, i32, P, P, P, i64, P, ctypes.POINTER(SolveInfo), P]),
+            "bem_evaluate_velocity": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), ctypes.POINTER(Source), i32, P,
+                                                     P, P, i64, P, P]),
             "bem_mesh_stats": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), ctypes.POINTER(PlanStats)]),
             "bem_plan_stats_host": (ctypes.c_int, [P, i64, P, i64, ctypes.POINTER(Params), d, d,
                                                    ctypes.POINTER(PlanStats)]),
@@ -390,6 +392,21 @@ class Mesh:
         _check(lib().bem_evaluate(self._h, float(freq), ctypes.byref(med), srcs, len(sources), _dptr(p, self.n),
                                   _dptr(q, self.n), pts.ctypes.data_as(ctypes.c_void_p), m, _dptr(out, m),
                                   _stream_ptr(stream)))
+        return out
+
+    def evaluate_velocity(self, freq, p, q, points, sources=(), c=343.0, rho=1.21, out=None, stream=None):
+        """Particle velocity v = grad p / (i w rho) at exterior points
+        (Eq. utopandv with Eq. BIE_I differentiated); complex64 [M, 3]."""
+        import torch
+        pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 3))
+        m = pts.shape[0]
+        if out is None:
+            out = torch.empty((m, 3), dtype=torch.complex64, device=p.device)
+        srcs = (Source * max(1, len(sources)))(*sources)
+        med = self._medium(c, rho)
+        _check(lib().bem_evaluate_velocity(self._h, float(freq), ctypes.byref(med), srcs, len(sources),
+                                           _dptr(p, self.n), _dptr(q, self.n), pts.ctypes.data_as(ctypes.c_void_p),
+                                           m, _dptr(out, 3 * m), _stream_ptr(stream)))
         return out
 
     def release_plan(self):

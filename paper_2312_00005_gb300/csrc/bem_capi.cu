@@ -2000,6 +2000,74 @@ int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem
     }
 }
 
+int bem_evaluate_velocity(void *mesh, double freq_hz, const bem_medium *medium, const bem_source *srcs,
+                          int32_t n_src, const void *p_dev, const void *q_dev, const double *pts, int64_t M_pts,
+                          void *v_out_dev, void *stream)
+{
+    if (!mesh || !p_dev || !q_dev || !pts || M_pts < 0 || !v_out_dev || n_src < 0 || (n_src > 0 && !srcs))
+        return set_err(BEM_E_ARG, "bad argument");
+    if (M_pts == 0) return BEM_OK;
+    auto &M = *(bem_mesh_impl *)mesh;
+    try {
+        double c, rho;
+        medium_of(medium, c, rho);
+        if (!(freq_hz > 0)) return set_err(BEM_E_ARG, "frequency must be positive");
+        ck(cudaSetDevice(M.device), "cudaSetDevice");
+        ensure_work(M);
+        cudaStream_t us = (cudaStream_t)stream;
+        join_streams(us, M.s);
+        cudaStream_t s = M.s;
+        const int64_t n = M.n;
+        {
+            KTimer kt_("k_gather", s);
+            k_gather<<<nblocks(n, 256), 256, 0, s>>>((const float2 *)p_dev, M.perm.p, n, M.tmp.p);
+        }
+        ck_launch("k_gather");
+        {
+            KTimer kt_("k_gather", s);
+            k_gather<<<nblocks(n, 256), 256, 0, s>>>((const float2 *)q_dev, M.perm.p, n, M.tmp2.p);
+        }
+        ck_launch("k_gather");
+        std::vector<double> hp(pts, pts + 3 * M_pts);
+        DevArr<double> &dp = M.ptsbuf;
+        dp.upload(hp, s);
+        std::vector<SourceDev> sv = sources_of(srcs, n_src);
+        DevArr<SourceDev> &sdev = M.srcbuf;
+        sdev.upload(sv, s);
+        reset_err(M);
+        const double k = wavenumber(freq_hz, c);
+        const float inv_omega_rho = (float)(1.0 / (2.0 * 3.14159265358979323846 * freq_hz * rho));
+        // blocks per point as for the field (partials added in slice order)
+        int nsm = 0;
+        ck(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, M.device), "attribute");
+        const int64_t want = 8 * (int64_t)nsm;
+        const int S = (int)std::max<int64_t>(1, std::min<int64_t>({16, (want + M_pts - 1) / M_pts,
+                                                                   (n + 255) / 256}));
+        if (S > 1) M.fieldpart.alloc((size_t)M_pts * S * 3);
+        {
+            KTimer kt_("k_field_velocity", s);
+            k_field_velocity<<<dim3((unsigned)M_pts, (unsigned)S), 256, 0, s>>>(
+                M.elem(), M.Q.p, dp.p, M_pts, (float)k, inv_omega_rho, M.tmp.p, M.tmp2.p, sdev.p, n_src,
+                M.fieldpart.p, (float2 *)v_out_dev, fr(M).err.p);
+        }
+        ck_launch("k_field_velocity");
+        if (S > 1) {
+            {
+                KTimer kt_("k_field_velocity", s);
+                k_field_velocity_finish<<<nblocks(M_pts, 128), 128, 0, s>>>(
+                    dp.p, M_pts, S, (float)k, inv_omega_rho, sdev.p, n_src, M.fieldpart.p, (float2 *)v_out_dev);
+            }
+            ck_launch("k_field_velocity_finish");
+        }
+        check_err(M);
+        join_streams(s, us);
+        resolve_timing();
+        return BEM_OK;
+    } catch (Fail &f) {
+        return f.code;
+    }
+}
+
 int bem_selftest_sincos(const void *x_dev, int64_t n, void *out_dev, void *stream)
 {
     if (!x_dev || !out_dev || n < 0) return set_err(BEM_E_ARG, "bad argument");

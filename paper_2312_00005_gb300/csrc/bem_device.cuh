@@ -123,6 +123,39 @@ __device__ __forceinline__ void gh_point(float3 d, float3 ny, float k, float w, 
 }
 
 
+// grad_x G and grad_x H (H = dG/dn_y) at one quadrature point, d = y - x,
+// for the particle velocity at field points (Eq. utopandv, with Eq. BIE_I
+// differentiated under the integral).  With f = G (ik - 1/r) / r:
+//   grad_x G = -f d,
+//   grad_x H = -f'(r) (d.ny / r) d - f ny,
+//   f'(r) = G (-k^2 / r - 3ik / r^2 + 3 / r^3);
+// their components along a unit vector e are the kernels H' and E of
+// Eq. dBIE with n_x = e.
+__device__ __forceinline__ void grad_point(float3 d, float3 ny, float k, float w, float2 *gG, float2 *gH)
+{
+    const float r2 = dot3f(d, d);
+    const float ir = rsqrtf(r2);
+    const float r = r2 * ir;
+    float s, c;
+    sincos_turns(k * r * 0.15915494309189535f, &s, &c);
+    const float g = w * ir * kInv4Pi;
+    const float2 G = make_float2(c * g, s * g);
+    const float2 Ga = cmul(G, make_float2(-ir, k));          // G (ik - 1/r)
+    const float2 f = make_float2(Ga.x * ir, Ga.y * ir);
+    const float ir2 = ir * ir;
+    const float2 fp = cmul(G, make_float2(-k * k * ir + 3.0f * ir2 * ir, -3.0f * k * ir2));
+    const float dn = dot3f(d, ny) * ir;
+    const float2 cd = make_float2(-fp.x * dn, -fp.y * dn);   // grad_x H = cd d - f ny
+    const float dv[3] = {d.x, d.y, d.z}, nv[3] = {ny.x, ny.y, ny.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        gG[a].x = fmaf(-f.x, dv[a], gG[a].x);
+        gG[a].y = fmaf(-f.y, dv[a], gG[a].y);
+        gH[a].x = fmaf(cd.x, dv[a], fmaf(-f.x, nv[a], gH[a].x));
+        gH[a].y = fmaf(cd.y, dv[a], fmaf(-f.y, nv[a], gH[a].y));
+    }
+}
+
 // Rule code for a (sub)element: 0 = subdivide, m >= 1 = regular order m.
 __device__ __forceinline__ int rule_from_rt(float rt, const QuadTables &Q)
 {
@@ -174,15 +207,15 @@ struct SubTri {
     int depth;
 };
 
-// Integrate the Burton-Miller kernels (or G/H for a field point) over element
-// j from point x (high/low parts xhi, xlo; FP64 copy xd), with the
-// subdivision of Sec. 3.1.3 and the regular rule of Sec. 3.1.4.
-// Quadrature points are y = a + xi (b - a) + eta (c - a); every distance is
-// formed from local offsets so FP32 keeps its relative accuracy.
-// Returns false if the subdivision limit is exceeded.
-template <bool kField>
-__device__ bool integrate_regular(const ElemDev &E, int64_t j, float3 xhi, float3 xlo, const double *xd,
-                                  float3 nx, float k, float ik_inv, const QuadTables &Q, float2 &A0, float2 &A1)
+// Integrate kernels over element j from point x (high/low parts xhi, xlo;
+// FP64 copy xd), with the subdivision of Sec. 3.1.3 and the regular rule of
+// Sec. 3.1.4: acc.point(d, ny, w) adds the kernels at each quadrature point
+// (d = y - x, weight w).  Quadrature points are y = a + xi (b - a) +
+// eta (c - a); every distance is formed from local offsets so FP32 keeps its
+// relative accuracy.  Returns false if the subdivision limit is exceeded.
+template <class Acc>
+__device__ bool integrate_regular_acc(const ElemDev &E, int64_t j, float3 xhi, float3 xlo, const double *xd,
+                                      const QuadTables &Q, Acc &acc)
 {
     const float4 ch = E.chi[j], cl = E.clo[j];
     const float3 D0 = add3(sub3f(f3(ch), xhi), sub3f(f3(cl), xlo));   // x_j - x
@@ -195,8 +228,7 @@ __device__ bool integrate_regular(const ElemDev &E, int64_t j, float3 xhi, float
     if (Q.m_max > 1) {
         const float rt0 = sqrtf(dot3f(D0, D0) / area);
         if (rt0 > Q.R[1] * (1.0f + 1e-5f)) {
-            if (kField) gh_point(D0, ny, k, area, A0, A1);
-            else bm_point(D0, nx, ny, k, ik_inv, area, A0, A1);
+            acc.point(D0, ny, area);
             return true;
         }
     }
@@ -220,8 +252,7 @@ __device__ bool integrate_regular(const ElemDev &E, int64_t j, float3 xhi, float
             for (int q = 0; q < nq; ++q) {
                 const float3 d = mad3(Q.tri_eta[code][q], e2, mad3(Q.tri_xi[code][q], e1, base));
                 const float w = 2.0f * area * Q.tri_w[code][q];
-                if (kField) gh_point(d, ny, k, w, A0, A1);
-                else bm_point(d, nx, ny, k, ik_inv, w, A0, A1);
+                acc.point(d, ny, w);
             }
             return true;
         }
@@ -271,10 +302,48 @@ __device__ bool integrate_regular(const ElemDev &E, int64_t j, float3 xhi, float
             const float px = s.x0 + u * sx1 + v * sx2, py = s.y0 + u * sy1 + v * sy2;
             const float3 d = mad3(py, e2, mad3(px, e1, base));
             const float w = 2.0f * sa * Q.tri_w[code][q];
-            if (kField) gh_point(d, ny, k, w, A0, A1);
-            else bm_point(d, nx, ny, k, ik_inv, w, A0, A1);
+            acc.point(d, ny, w);
         }
     }
+    return ok;
+}
+
+// Point accumulators for integrate_regular_acc.
+struct BmAcc {        // Burton-Miller column kernels Kp, Kq (bm_point)
+    float3 nx;
+    float k, ik_inv;
+    float2 A0, A1;
+    __device__ __forceinline__ void point(float3 d, float3 ny, float w) { bm_point(d, nx, ny, k, ik_inv, w, A0, A1); }
+};
+struct GhAcc {        // G and H of a field point (gh_point)
+    float k;
+    float2 A0, A1;
+    __device__ __forceinline__ void point(float3 d, float3 ny, float w) { gh_point(d, ny, k, w, A0, A1); }
+};
+struct GradAcc {      // grad_x G and grad_x H of a field point (grad_point)
+    float k;
+    float2 gG[3], gH[3];
+    __device__ __forceinline__ void point(float3 d, float3 ny, float w) { grad_point(d, ny, k, w, gG, gH); }
+};
+
+// The Burton-Miller kernels (kField false) or G and H of a field point
+// (kField true) integrated over element j; see integrate_regular_acc.
+template <bool kField>
+__device__ __forceinline__ bool integrate_regular(const ElemDev &E, int64_t j, float3 xhi, float3 xlo,
+                                                  const double *xd, float3 nx, float k, float ik_inv,
+                                                  const QuadTables &Q, float2 &A0, float2 &A1)
+{
+    if (kField) {
+        GhAcc a{k, A0, A1};
+        const bool ok = integrate_regular_acc(E, j, xhi, xlo, xd, Q, a);
+        A0 = a.A0;
+        A1 = a.A1;
+        return ok;
+    }
+    BmAcc a{nx, k, ik_inv, A0, A1};
+    const bool ok = integrate_regular_acc(E, j, xhi, xlo, xd, Q, a);
+    A0 = a.A0;
+    A1 = a.A1;
     return ok;
 }
 

@@ -983,6 +983,122 @@ __global__ void k_field_finish(const double *__restrict__ pts, int64_t M, int S,
     out[m] = make_float2((float)br, (float)bi);
 }
 
+// Gradient of the incident fields at x (FP64): plane wave grad p = ik d p,
+// point source grad p = p (ik - 1/R) (x - x0) / R.
+__device__ void incident_grad(const double *xd, float k, const SourceDev *__restrict__ src, int nsrc, double *gr,
+                              double *gi)
+{
+    for (int s = 0; s < nsrc; ++s) {
+        const SourceDev S = src[s];
+        double sn, cs;
+        if (S.kind == 0) {
+            sincos((double)k * (S.v[0] * xd[0] + S.v[1] * xd[1] + S.v[2] * xd[2]), &sn, &cs);
+            // p = A e^{i phi}; ik d p = k d (i p): i p = (-p_i, p_r)
+            const double pr = S.amp[0] * cs - S.amp[1] * sn, pi = S.amp[0] * sn + S.amp[1] * cs;
+            for (int a = 0; a < 3; ++a) {
+                gr[a] += -(double)k * S.v[a] * pi;
+                gi[a] += (double)k * S.v[a] * pr;
+            }
+        } else {
+            const double d[3] = {xd[0] - S.v[0], xd[1] - S.v[1], xd[2] - S.v[2]};
+            const double R = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            sincos((double)k * R, &sn, &cs);
+            const double g = 1.0 / (4.0 * 3.14159265358979323846 * R);
+            const double pr = (S.amp[0] * cs - S.amp[1] * sn) * g, pi = (S.amp[0] * sn + S.amp[1] * cs) * g;
+            // p (ik - 1/R) = (-pr/R - k pi) + i (k pr - pi/R)
+            const double fr = -pr / R - (double)k * pi, fi = (double)k * pr - pi / R;
+            for (int a = 0; a < 3; ++a) {
+                gr[a] += fr * d[a] / R;
+                gi[a] += fi * d[a] / R;
+            }
+        }
+    }
+}
+
+// Particle velocity at field points, v = grad p / (i w rho) (Eq. utopandv),
+// with grad p = grad p_inc + sum_j [grad H(x)_j p_j - grad G(x)_j q_j]
+// (Eq. BIE_I, lambda = 1, differentiated under the integral; the element
+// rules of the field).  Blocks as in k_field: block (m, s) takes field point
+// m and every S-th slice of blockDim elements from slice s; with S = 1 it
+// writes v(x_m), otherwise its partial gradient part[(m S + s) 3 + a] for
+// k_field_velocity_finish.  out: [M][3] (x, y, z components).
+__global__ void k_field_velocity(ElemDev E, const QuadTables *__restrict__ Qp, const double *__restrict__ pts,
+                                 int64_t M, float k, float inv_omega_rho, const float2 *__restrict__ p,
+                                 const float2 *__restrict__ q, const SourceDev *__restrict__ src, int nsrc,
+                                 float2 *__restrict__ part, float2 *__restrict__ out, int *err)
+{
+    const int64_t m = blockIdx.x;
+    const int S = gridDim.y, sl = blockIdx.y;
+    if (m >= M) return;
+    const QuadTables &Q = *Qp;
+    const double xd[3] = {pts[3 * m], pts[3 * m + 1], pts[3 * m + 2]};
+    const float3 xhi = make_float3((float)xd[0], (float)xd[1], (float)xd[2]);
+    const float3 xlo = make_float3((float)(xd[0] - (double)xhi.x), (float)(xd[1] - (double)xhi.y),
+                                   (float)(xd[2] - (double)xhi.z));
+    float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    for (int64_t j = (int64_t)sl * blockDim.x + threadIdx.x; j < E.n; j += (int64_t)S * blockDim.x) {
+        GradAcc g;
+        g.k = k;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) g.gG[a] = g.gH[a] = make_float2(0.f, 0.f);
+        if (!integrate_regular_acc(E, j, xhi, xlo, xd, Q, g)) {
+            atomicMin(err, (int)j);
+            continue;
+        }
+        const float2 pj = p[j], qj = q[j];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[a] = cadd(acc[a], csub(cmul(g.gH[a], pj), cmul(g.gG[a], qj)));
+    }
+    __shared__ float2 red[3][32];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float2 v = warp_sum(acc[a]);
+        if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double gr[3], gi[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float2 v = threadIdx.x < (blockDim.x >> 5) ? red[a][threadIdx.x] : make_float2(0.f, 0.f);
+            v = warp_sum(v);
+            gr[a] = v.x;
+            gi[a] = v.y;
+        }
+        if (threadIdx.x == 0) {
+            if (S > 1) {
+                for (int a = 0; a < 3; ++a) part[(m * S + sl) * 3 + a] = make_float2((float)gr[a], (float)gi[a]);
+            } else {
+                incident_grad(xd, k, src, nsrc, gr, gi);
+                // v = grad p / (i w rho) = -i grad p / (w rho)
+                for (int a = 0; a < 3; ++a)
+                    out[3 * m + a] = make_float2((float)(gi[a] * inv_omega_rho), (float)(-gr[a] * inv_omega_rho));
+            }
+        }
+    }
+}
+
+// The S partial gradients of each field point in slice order, the incident
+// gradient and the scaling to the velocity; one thread per point.
+__global__ void k_field_velocity_finish(const double *__restrict__ pts, int64_t M, int S, float k,
+                                        float inv_omega_rho, const SourceDev *__restrict__ src, int nsrc,
+                                        const float2 *__restrict__ part, float2 *__restrict__ out)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double gr[3], gi[3];
+    for (int a = 0; a < 3; ++a) {
+        float2 v = part[(m * S) * 3 + a];
+        for (int s = 1; s < S; ++s) v = cadd(v, part[(m * S + s) * 3 + a]);
+        gr[a] = v.x;
+        gi[a] = v.y;
+    }
+    const double xd[3] = {pts[3 * m], pts[3 * m + 1], pts[3 * m + 2]};
+    incident_grad(xd, k, src, nsrc, gr, gi);
+    for (int a = 0; a < 3; ++a)
+        out[3 * m + a] = make_float2((float)(gi[a] * inv_omega_rho), (float)(-gr[a] * inv_omega_rho));
+}
+
 // ------------------------------------------------------------------ vector helpers
 __global__ void k_gather(const float2 *__restrict__ x, const int64_t *__restrict__ perm, int64_t n,
                          float2 *__restrict__ y)

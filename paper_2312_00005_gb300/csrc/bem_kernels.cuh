@@ -181,6 +181,11 @@ __global__ void k_field(ElemDev E, const QuadTables *Q, const double *pts, int64
                         const float2 *q, const SourceDev *src, int nsrc, float2 *part, float2 *out, int *err);
 __global__ void k_field_finish(const double *pts, int64_t M, int S, float k, const SourceDev *src, int nsrc,
                                const float2 *part, float2 *out);
+__global__ void k_field_velocity(ElemDev E, const QuadTables *Q, const double *pts, int64_t M, float k,
+                                 float inv_omega_rho, const float2 *p, const float2 *q, const SourceDev *src, int nsrc,
+                                 float2 *part, float2 *out, int *err);
+__global__ void k_field_velocity_finish(const double *pts, int64_t M, int S, float k, float inv_omega_rho,
+                                        const SourceDev *src, int nsrc, const float2 *part, float2 *out);
 __global__ void k_gather(const float2 *x, const int64_t *perm, int64_t n, float2 *y);
 __global__ void k_scatter(const float2 *x, const int64_t *perm, int64_t n, float2 *y);
 __global__ void k_sub(float2 *b, const float2 *y, int64_t n);
