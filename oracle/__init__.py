@@ -117,9 +117,9 @@ def _i32(a):
 def _params(params):
     if params is None:
         return None
-    keys = ["quad_tol", "m_max", "rt_subdiv", "max_depth", "n_duffy", "edge_parts", "edge_gauss"]
+    keys = ["quad_tol", "m_max", "rt_subdiv", "max_depth", "n_duffy", "edge_parts", "edge_gauss", "tau"]
     dflt = {"quad_tol": 1e-3, "m_max": 6, "rt_subdiv": 1.3, "max_depth": 15, "n_duffy": 4,
-            "edge_parts": 4, "edge_gauss": 3}
+            "edge_parts": 4, "edge_gauss": 3, "tau": 1.0}
     dflt.update(params)
     return np.array([float(dflt[k]) for k in keys], dtype=np.float64)
 

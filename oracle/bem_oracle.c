@@ -24,8 +24,10 @@
  *   - the dense Burton-Miller system of Eq. SystemI with gamma = i/k, with
  *     per-column coefficients that fold in the boundary conditions;
  *   - a dense O(N^2) matrix-vector product and restarted GMRES;
+ *   - the interior problem (tau = -1 in Eq. BIE_I and Eq. SystemI: the sign
+ *     of every integral operator) as a parameter, tau = +1 by default;
  *   - the field at exterior points from the representation formula with
- *     lambda = 1 (Eq. BIE_I), and its gradient (the particle velocity of
+ *     lambda = 1 (Eq. BIE_I; interior points when tau = -1), and its gradient (the particle velocity of
  *     Eq. utopandv) from the same formula differentiated under the integral;
  *   - the pieces of the plane-wave expansion of Eq. FMMBase (spherical Hankel
  *     functions by upward recursion, Legendre polynomials, the unit-sphere
@@ -63,6 +65,7 @@ typedef struct {
     int    n_duffy;       /* Gauss points per direction in the Duffy rule, 4 */
     int    edge_parts;    /* parts per edge in the hypersingular rule, 4 */
     int    edge_gauss;    /* Gauss points per part, 3 */
+    double tau;           /* +1 exterior problem, -1 interior problem (Eq. BIE_I) */
 } orc_params;
 
 static void default_params(orc_params *p)
@@ -74,6 +77,7 @@ static void default_params(orc_params *p)
     p->n_duffy = 4;
     p->edge_parts = 4;
     p->edge_gauss = 3;
+    p->tau = 1.0;
 }
 
 static int clamp_rule(int n);
@@ -90,6 +94,7 @@ static void read_params(const double *pp, orc_params *p)
     p->n_duffy = (int)pp[4];
     p->edge_parts = (int)pp[5];
     p->edge_gauss = (int)pp[6];
+    p->tau = pp[7] < 0.0 ? -1.0 : 1.0;
     p->m_max = clamp_rule(p->m_max);
     p->n_duffy = clamp_rule(p->n_duffy);
     p->edge_gauss = clamp_rule(p->edge_gauss);
@@ -569,7 +574,8 @@ static int row_entry(const mesh_ctx *M, long i, long j, cplx *aij)
                           &M->P, o))
         return -1;
     cplx gamma = I / M->k;
-    cplx v = M->cp[j] * (-(o[1] - gamma * o[3])) + M->cq[j] * (o[0] - gamma * o[2]);
+    /* Eq. SystemI: tau on every integral operator, not on the identity halves */
+    cplx v = M->P.tau * (M->cp[j] * (-(o[1] - gamma * o[3])) + M->cq[j] * (o[0] - gamma * o[2]));
     if (i == j) v += 0.5 * (M->cp[i] - gamma * M->cq[i]);
     *aij = v;
     return 0;
@@ -845,6 +851,7 @@ int orc_field(const double *nodes, const int *tris, long n, double k, const doub
             }
             s += o[1] * pv[j] - o[0] * qv[j];
         }
+        s *= P.tau;
         out[2 * r] = creal(s);
         out[2 * r + 1] = cimag(s);
     }
@@ -892,6 +899,7 @@ int orc_field_grad(const double *nodes, const int *tris, long n, double k, const
                 }
                 s += o[3] * pv[j] - o[2] * qv[j];
             }
+            s *= P.tau;
             out[6 * r + 2 * ax] = creal(s);
             out[6 * r + 2 * ax + 1] = cimag(s);
         }

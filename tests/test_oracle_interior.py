@@ -1,0 +1,56 @@
+"""Pins of the oracle's interior problem (tau = -1 in Eq. BIE_I and
+Eq. SystemI: the sign of every integral operator, not of the identity
+halves): a plane wave inside a closed sphere, produced by the normal
+velocity it induces on the surface and no source, must come back at the
+element midpoints and at interior field points; the exterior formulation
+(tau = +1) with the same data must not."""
+import numpy as np
+
+import oracle
+from paper_2312_00005_gb300 import inputs
+
+C, RHO = 343.0, 1.21
+
+
+def _interior_plane_wave(freq, level=3):
+    nodes, tris = inputs.icosphere(level, 0.1)
+    n = tris.shape[0]
+    k = 2 * np.pi * freq / C
+    cen, nrm, _ = oracle.geometry(nodes, tris)
+    d = np.array([0.3, 0.4, 0.866])
+    d /= np.linalg.norm(d)
+    p_ex = np.exp(1j * k * cen @ d)
+    # q = dp/dn = ik (d.n) p, and q = i w rho v (Eq. utopandv): v = (d.n) p / (rho c)
+    v = (nrm @ d) * p_ex / (RHO * C)
+    return nodes, tris, n, k, d, p_ex, v
+
+
+def test_interior_plane_wave_in_a_sphere():
+    # ka = 1: away from the interior Neumann resonances of the sphere (j_n'(ka) = 0: ka = 2.08, 3.34, ...)
+    freq = 546.0
+    nodes, tris, n, k, d, p_ex, v = _interior_plane_wave(freq)
+    bct = np.full(n, oracle.VELO, np.int32)
+    p, q, info = oracle.solve(nodes, tris, freq, c=C, rho=RHO, bc_type=bct, bc_value=v, params={"tau": -1.0})
+    err = np.linalg.norm(p - p_ex) / np.linalg.norm(p_ex)
+    assert err < 3e-2, err      # 1.8% at N = 1280 (constant elements, first order)
+    pts = np.array([[0.0, 0.0, 0.0], [0.03, -0.02, 0.01], [-0.05, 0.02, 0.04], [0.0, 0.06, -0.05]])
+    f = oracle.field(nodes, tris, freq, p, q, pts, c=C, params={"tau": -1.0})
+    f_ex = np.exp(1j * k * pts @ d)
+    ef = np.abs(f - f_ex).max()
+    assert ef < 3e-2, ef        # 1.7% (|p| = 1); the tau = +1 formula gives about 2
+    # the same boundary data read as an exterior problem give another field
+    p2, _, _ = oracle.solve(nodes, tris, freq, c=C, rho=RHO, bc_type=bct, bc_value=v)
+    assert np.linalg.norm(p2 - p_ex) / np.linalg.norm(p_ex) > 0.2
+
+
+def test_interior_error_falls_with_refinement():
+    """Constant elements: the midpoint error of the interior plane wave
+    drops when the sphere is refined (N = 320 -> 1280)."""
+    freq = 546.0
+    errs = []
+    for level in (2, 3):
+        nodes, tris, n, k, d, p_ex, v = _interior_plane_wave(freq, level)
+        bct = np.full(n, oracle.VELO, np.int32)
+        p, _, _ = oracle.solve(nodes, tris, freq, c=C, rho=RHO, bc_type=bct, bc_value=v, params={"tau": -1.0})
+        errs.append(np.linalg.norm(p - p_ex) / np.linalg.norm(p_ex))
+    assert errs[1] < 0.6 * errs[0], errs
