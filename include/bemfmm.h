@@ -17,8 +17,9 @@
  *     N + sum_l S(l) D(l) T(l)).
  *
  * Variables are pressures: p on the surface and q = dp/dn = i w rho v, with
- * n the outward normal (pointing into the fluid, App. A) and time factor
- * e^{-i w t}.  Complex numbers are interleaved (re, im): float2 ("cf32") on
+ * n the outward normal (pointing away from the enclosed volume: into the
+ * fluid for the exterior problem, App. A, out of it for the interior problem
+ * of bem_params.tau = -1) and time factor e^{-i w t}.  Complex numbers are interleaved (re, im): float2 ("cf32") on
  * the device, double[2] on the host.
  *
  * Ownership: every entry point copies what it needs from host arrays before
@@ -84,6 +85,10 @@ typedef struct bem_params {
     int32_t restart;        /* GMRES restart length, 100                                       */
     int32_t autotune;       /* 1: choose the leaf size by timing candidates on the GPU at the
                                mesh's first plan (when leaf_edge is 0; default); 0: off       */
+    double  tau;            /* +1: exterior problem (default); -1: interior problem, the field
+                               inside the closed surface (Eq. BIE_I, Eq. SystemI: the sign of
+                               every integral operator).  Normals point away from the enclosed
+                               volume in both cases (Sec. 2.1).  Other values: BEM_E_ARG.    */
 } bem_params;
 
 typedef struct bem_medium {

@@ -808,6 +808,7 @@ NearArgs near_args(const bem_mesh_impl &M, const Plan &P, const float2 *cp, cons
     a.Q = M.Q.p;
     a.k = (float)P.k;
     a.ik_inv = (float)(1.0 / P.k);
+    a.tau = M.prm.tau < 0 ? -1.f : 1.f;
     a.cp = cp;
     a.cq = cq;
     return a;
@@ -844,6 +845,17 @@ void make_coeffs(bem_mesh_impl &M, double k, double omega, double c, double rho,
         }
         if (C.z[i].x != 0.f || C.z[i].y != 0.f) C.known_nonzero = true;
     }
+    // tau (Eq. SystemI: +1 exterior, -1 interior) multiplies every integral
+    // operator: it is folded into the column coefficients of the unknowns
+    // and of the known data (the self entry takes it out of its identity
+    // half again); aq, the physical relation q = a p, keeps its sign
+    if (M.prm.tau < 0)
+        for (int64_t i = 0; i < n; ++i) {
+            C.cp[i] = make_float2(-C.cp[i].x, -C.cp[i].y);
+            C.cq[i] = make_float2(-C.cq[i].x, -C.cq[i].y);
+            C.cp0[i] = make_float2(-C.cp0[i].x, -C.cp0[i].y);
+            C.cq0[i] = make_float2(-C.cq0[i].x, -C.cq0[i].y);
+        }
 }
 
 void upload_coeffs(bem_mesh_impl &M, const Coeffs &C)
@@ -1303,6 +1315,7 @@ void bem_params_default(bem_params *p)
     p->near_store = 1;
     p->restart = 100;
     p->autotune = 1;
+    p->tau = 1.0;
 }
 
 const char *bem_last_error(void) { return g_err.c_str(); }
@@ -1323,6 +1336,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
     if (p.m_max < 1 || p.m_max > kMaxRule) return set_err(BEM_E_ARG, "m_max must be in 1..6");
     if (p.max_depth < 0 || p.max_depth > 15) return set_err(BEM_E_ARG, "max_depth must be in 0..15");
     if (p.restart < 2 || p.restart > kMaxRestart) return set_err(BEM_E_ARG, "restart must be in 2..256");
+    if (!(p.tau == 1.0 || p.tau == -1.0)) return set_err(BEM_E_ARG, "tau must be +1 (exterior) or -1 (interior)");
     if (!(p.quad_tol > 0) || !(p.rt_subdiv > 0) || !(p.admissibility > 0) || p.L_min < 1 || p.L_min > 200)
         return set_err(BEM_E_ARG, "invalid parameter");
     try {
@@ -1978,7 +1992,8 @@ int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem
         {
             KTimer kt_("k_field", s);
             k_field<<<dim3((unsigned)M_pts, (unsigned)S), 256, 0, s>>>(M.elem(), M.Q.p, dp.p, M_pts, (float)k,
-                                                                      M.tmp.p, M.tmp2.p, sdev.p, n_src,
+                                                                      (float)M.prm.tau, M.tmp.p, M.tmp2.p,
+                                                                      sdev.p, n_src,
                                                                       M.fieldpart.p, (float2 *)out_dev,
                                                                       fr(M).err.p);
         }
@@ -2047,7 +2062,8 @@ int bem_evaluate_velocity(void *mesh, double freq_hz, const bem_medium *medium, 
         {
             KTimer kt_("k_field_velocity", s);
             k_field_velocity<<<dim3((unsigned)M_pts, (unsigned)S), 256, 0, s>>>(
-                M.elem(), M.Q.p, dp.p, M_pts, (float)k, inv_omega_rho, M.tmp.p, M.tmp2.p, sdev.p, n_src,
+                M.elem(), M.Q.p, dp.p, M_pts, (float)k, (float)M.prm.tau, inv_omega_rho, M.tmp.p, M.tmp2.p,
+                sdev.p, n_src,
                 M.fieldpart.p, (float2 *)v_out_dev, fr(M).err.p);
         }
         ck_launch("k_field_velocity");

@@ -413,9 +413,11 @@ __device__ __forceinline__ void self_term(const ElemDev &E, int64_t j, float k, 
 }
 
 // Entry A_ij of the Burton-Miller matrix for columns with coefficients
-// (cp_j, cq_j): A_ij = cp_j Kp_ij + cq_j Kq_ij + delta_ij (cp_i - gamma cq_i)/2.
+// (cp_j, cq_j) that already carry tau (Eq. SystemI: +1 exterior, -1
+// interior, on every integral operator): A_ij = cp_j Kp_ij + cq_j Kq_ij +
+// delta_ij tau (cp_i - gamma cq_i)/2, the identity half without tau.
 __device__ __forceinline__ bool bm_entry(const ElemDev &E, int64_t i, int64_t j, float3 xhi, float3 xlo,
-                                         const double *xd, float3 nx, float k, float ik_inv,
+                                         const double *xd, float3 nx, float k, float ik_inv, float tau,
                                          const QuadTables &Q, float2 cpj, float2 cqj, float2 &out)
 {
     if (i == j) {
@@ -424,9 +426,9 @@ __device__ __forceinline__ bool bm_entry(const ElemDev &E, int64_t i, int64_t j,
         // Kp = gamma E_ii (H_ii = 0), Kq = G_ii (H'_ii = 0); gamma = i/k
         const float2 gE = make_float2(-Eii.y * ik_inv, Eii.x * ik_inv);
         float2 v = cadd(cmul(cpj, gE), cmul(cqj, Gii));
-        // (cp - gamma cq)/2
+        // (cp - gamma cq)/2 of the coefficients without tau
         const float2 gcq = make_float2(-cqj.y * ik_inv, cqj.x * ik_inv);
-        v = cadd(v, cscale(csub(cpj, gcq), 0.5f));
+        v = cadd(v, cscale(csub(cpj, gcq), 0.5f * tau));
         out = v;
         return true;
     }

@@ -46,7 +46,7 @@ __global__ void k_near_store(NearArgs a, float2 *__restrict__ val, int *__restri
     for (int p = lane; p < nc; p += 32) {
         const int j = near_col(a.N, r_end, r, p);
         float2 v;
-        if (!bm_entry(a.E, i, j, xhi, xlo, xd, nx, a.k, a.ik_inv, Q, a.cp[j], a.cq[j], v)) {
+        if (!bm_entry(a.E, i, j, xhi, xlo, xd, nx, a.k, a.ik_inv, a.tau, Q, a.cp[j], a.cq[j], v)) {
             atomicMin(err, j);
             v = make_float2(0.f, 0.f);
         }
@@ -102,10 +102,10 @@ __global__ void k_near_classify(NearArgs a, int2 *__restrict__ heavy, unsigned l
 constexpr int kLightRows = 64;
 // the general rule out of line, so that the common path keeps few registers
 __device__ __noinline__ bool general_entry(const ElemDev &E, int64_t i, int64_t j, float3 xhi, float3 xlo,
-                                           const double *xd, float3 nx, float k, float ik_inv, const QuadTables &Q,
-                                           float2 cpj, float2 cqj, float2 *out)
+                                           const double *xd, float3 nx, float k, float ik_inv, float tau,
+                                           const QuadTables &Q, float2 cpj, float2 cqj, float2 *out)
 {
-    return bm_entry(E, i, j, xhi, xlo, xd, nx, k, ik_inv, Q, cpj, cqj, *out);
+    return bm_entry(E, i, j, xhi, xlo, xd, nx, k, ik_inv, tau, Q, cpj, cqj, *out);
 }
 // Entry A_ij of order 2 or 3 over the whole element j (no subdivision).
 __device__ __forceinline__ float2 order23_entry(const ElemDev &E, int j, float3 D0, float3 nx, float k, float ik_inv,
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256, 4) k_near_store_light(NearArgs a, float2 
                 // off, m_max <= 3): the general rule
                 const double xd[3] = {s_xd[q][0], s_xd[q][1], s_xd[q][2]};
                 float2 v;
-                if (!general_entry(a.E, i, j, f3(s_hi[q]), f3(s_lo[q]), xd, f3(s_n[q]), a.k, a.ik_inv, Q, cpj,
+                if (!general_entry(a.E, i, j, f3(s_hi[q]), f3(s_lo[q]), xd, f3(s_n[q]), a.k, a.ik_inv, a.tau, Q, cpj,
                                    cqj, &v)) {
                     atomicMin(err, j);
                     v = make_float2(0.f, 0.f);
@@ -267,7 +267,7 @@ __global__ void k_near_store_heavy(NearArgs a, const int2 *__restrict__ heavy, i
     int r = a.N.run_ptr[t];
     const int j = near_col(a.N, a.N.run_ptr[t + 1], r, ip.y);
     float2 v;
-    if (!bm_entry(a.E, i, j, xhi, xlo, xd, nx, a.k, a.ik_inv, Q, a.cp[j], a.cq[j], v)) {
+    if (!bm_entry(a.E, i, j, xhi, xlo, xd, nx, a.k, a.ik_inv, a.tau, Q, a.cp[j], a.cq[j], v)) {
         atomicMin(err, j);
         v = make_float2(0.f, 0.f);
     }
@@ -442,7 +442,7 @@ __global__ void k_near_fused(NearArgs a, const float2 *__restrict__ x, float2 *_
         const float2 cp = a.cp[j], cq = a.cq[j];
         if (cp.x == 0.f && cp.y == 0.f && cq.x == 0.f && cq.y == 0.f) continue;
         float2 v;
-        if (!bm_entry(a.E, i, j, xhi, xlo, xd, nx, a.k, a.ik_inv, Q, cp, cq, v)) {
+        if (!bm_entry(a.E, i, j, xhi, xlo, xd, nx, a.k, a.ik_inv, a.tau, Q, cp, cq, v)) {
             atomicMin(err, j);
             continue;
         }
@@ -900,9 +900,10 @@ __global__ void k_rhs(const double *__restrict__ cd, const float4 *__restrict__ 
 }
 
 // ------------------------------------------------------------------ field evaluation
-// p(x) = p_inc(x) + sum_j [H(x)_j p_j - G(x)_j q_j] (Eq. BIE_I, lambda = 1).
-// Block (m, s) takes field point m and every S-th slice of blockDim
-// elements from slice s, threads over elements.  With S = 1 the block adds
+// p(x) = p_inc(x) + tau sum_j [H(x)_j p_j - G(x)_j q_j] (Eq. BIE_I, lambda =
+// 1; tau = +1 at exterior points, -1 at interior points).  Block (m, s)
+// takes field point m and every S-th slice of blockDim elements from slice
+// s, threads over elements.  With S = 1 the block adds
 // the incident field and writes p(x_m); otherwise it leaves its partial sum
 // in part[m S + s] and k_field_finish adds the S partials in slice order.
 __device__ void field_incident(const double *xd, float k, const SourceDev *__restrict__ src, int nsrc, double &br,
@@ -927,7 +928,7 @@ __device__ void field_incident(const double *xd, float k, const SourceDev *__res
 }
 
 __global__ void k_field(ElemDev E, const QuadTables *__restrict__ Qp, const double *__restrict__ pts, int64_t M,
-                        float k, const float2 *__restrict__ p, const float2 *__restrict__ q,
+                        float k, float tau, const float2 *__restrict__ p, const float2 *__restrict__ q,
                         const SourceDev *__restrict__ src, int nsrc, float2 *__restrict__ part,
                         float2 *__restrict__ out, int *err)
 {
@@ -955,6 +956,7 @@ __global__ void k_field(ElemDev E, const QuadTables *__restrict__ Qp, const doub
     if (threadIdx.x < 32) {
         float2 v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : make_float2(0.f, 0.f);
         v = warp_sum(v);
+        v = cscale(v, tau);      // tau on the integral part (Eq. BIE_I)
         if (threadIdx.x == 0) {
             if (S > 1) {
                 part[m * S + sl] = v;
@@ -1016,14 +1018,14 @@ __device__ void incident_grad(const double *xd, float k, const SourceDev *__rest
 }
 
 // Particle velocity at field points, v = grad p / (i w rho) (Eq. utopandv),
-// with grad p = grad p_inc + sum_j [grad H(x)_j p_j - grad G(x)_j q_j]
+// with grad p = grad p_inc + tau sum_j [grad H(x)_j p_j - grad G(x)_j q_j]
 // (Eq. BIE_I, lambda = 1, differentiated under the integral; the element
 // rules of the field).  Blocks as in k_field: block (m, s) takes field point
 // m and every S-th slice of blockDim elements from slice s; with S = 1 it
 // writes v(x_m), otherwise its partial gradient part[(m S + s) 3 + a] for
 // k_field_velocity_finish.  out: [M][3] (x, y, z components).
 __global__ void k_field_velocity(ElemDev E, const QuadTables *__restrict__ Qp, const double *__restrict__ pts,
-                                 int64_t M, float k, float inv_omega_rho, const float2 *__restrict__ p,
+                                 int64_t M, float k, float tau, float inv_omega_rho, const float2 *__restrict__ p,
                                  const float2 *__restrict__ q, const SourceDev *__restrict__ src, int nsrc,
                                  float2 *__restrict__ part, float2 *__restrict__ out, int *err)
 {
@@ -1062,8 +1064,8 @@ __global__ void k_field_velocity(ElemDev E, const QuadTables *__restrict__ Qp, c
         for (int a = 0; a < 3; ++a) {
             float2 v = threadIdx.x < (blockDim.x >> 5) ? red[a][threadIdx.x] : make_float2(0.f, 0.f);
             v = warp_sum(v);
-            gr[a] = v.x;
-            gi[a] = v.y;
+            gr[a] = tau * v.x;   // tau on the integral part (Eq. BIE_I)
+            gi[a] = tau * v.y;
         }
         if (threadIdx.x == 0) {
             if (S > 1) {

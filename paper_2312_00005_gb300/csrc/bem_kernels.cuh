@@ -34,6 +34,7 @@ struct NearArgs {
     NearDev N;
     const QuadTables *Q;
     float k, ik_inv;
+    float tau;               // +1 exterior, -1 interior problem; cp, cq below already carry it
     const float2 *cp, *cq;   // column coefficients (internal order)
 };
 
@@ -177,11 +178,12 @@ struct DTableArgs {
 __global__ void k_dtable(DTableArgs a);
 __global__ void k_rhs(const double *cd, const float4 *nrm, int64_t n, double k, const SourceDev *src, int nsrc,
                       float2 *b);
-__global__ void k_field(ElemDev E, const QuadTables *Q, const double *pts, int64_t M, float k, const float2 *p,
-                        const float2 *q, const SourceDev *src, int nsrc, float2 *part, float2 *out, int *err);
+__global__ void k_field(ElemDev E, const QuadTables *Q, const double *pts, int64_t M, float k, float tau,
+                        const float2 *p, const float2 *q, const SourceDev *src, int nsrc, float2 *part, float2 *out,
+                        int *err);
 __global__ void k_field_finish(const double *pts, int64_t M, int S, float k, const SourceDev *src, int nsrc,
                                const float2 *part, float2 *out);
-__global__ void k_field_velocity(ElemDev E, const QuadTables *Q, const double *pts, int64_t M, float k,
+__global__ void k_field_velocity(ElemDev E, const QuadTables *Q, const double *pts, int64_t M, float k, float tau,
                                  float inv_omega_rho, const float2 *p, const float2 *q, const SourceDev *src, int nsrc,
                                  float2 *part, float2 *out, int *err);
 __global__ void k_field_velocity_finish(const double *pts, int64_t M, int S, float k, float inv_omega_rho,

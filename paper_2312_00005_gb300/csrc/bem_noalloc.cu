@@ -223,6 +223,7 @@ extern "C" int bem_matvec_direct_noalloc(const double *nodes_dev, int64_t n_node
     a.Q = (const QuadTables *)(base + lay.Q);
     a.k = (float)k;
     a.ik_inv = (float)(1.0 / k);
+    a.tau = 1.f;             // exterior problem
     a.cp = (const float2 *)(base + lay.cp);
     a.cq = (const float2 *)(base + lay.cq);
     k_near_fused<<<(unsigned)((n_tris + 7) / 8), 256, 0, s>>>(a, (const float2 *)x_dev, (float2 *)y_dev,

@@ -173,6 +173,41 @@ def test_field_velocity_matches_oracle(bem):
     mesh.close()
 
 
+@pytest.mark.parametrize("mode,level,freq", [("direct", 3, 546.0), ("fmm", 4, 1474.0)])
+def test_interior_problem_matches_oracle(bem, mode, level, freq):
+    """Interior problem (tau = -1): a plane wave inside a closed sphere from
+    the normal velocity it induces, no source (ka = 1 and 2.7, away from the
+    sphere's interior Neumann resonances).  Surface pressure, interior field
+    and interior velocity against the oracle's tau = -1 solution, which is
+    itself within 2% of the plane wave."""
+    nodes, tris = inputs.icosphere(level, 0.1)
+    n = tris.shape[0]
+    k = 2 * np.pi * freq / C
+    cen, nrm, _ = oracle.geometry(nodes, tris)
+    d = np.array([0.3, 0.4, 0.866])
+    d /= np.linalg.norm(d)
+    v = (nrm @ d) * np.exp(1j * k * cen @ d) / (RHO * C)
+    bct = np.full(n, bem.VELO, np.int32)
+    kw = {"mode": bem.MODE_DIRECT} if mode == "direct" else {"trunc_factor": 6.0}
+    mesh = bem.Mesh(nodes, tris, bc_type=bct, bc_value=v, tau=-1.0, **kw)
+    if mode == "fmm":
+        assert mesh.stats(freq, c=C)["levels"] >= 1
+    p, q, info = mesh.solve(freq, [], tol=1e-7, c=C, rho=RHO)
+    assert info["converged"], info
+    po, qo, _ = oracle.solve(nodes, tris, freq, c=C, rho=RHO, bc_type=bct, bc_value=v, params={"tau": -1.0})
+    ep = _rel(p.cpu().numpy(), po)
+    assert ep < (1e-4 if mode == "direct" else 2e-4), ep
+    pts = np.array([[0.0, 0.0, 0.0], [0.03, -0.02, 0.01], [-0.05, 0.02, 0.04], [0.0, 0.06, -0.05]])
+    f = mesh.evaluate(freq, p, q, pts, [], c=C, rho=RHO).cpu().numpy()
+    fo = oracle.field(nodes, tris, freq, po, qo, pts, c=C, params={"tau": -1.0})
+    assert _rel(f, fo) < 2e-4, _rel(f, fo)
+    assert np.abs(fo - np.exp(1j * k * pts @ d)).max() < 3e-2
+    vel = mesh.evaluate_velocity(freq, p, q, pts, [], c=C, rho=RHO).cpu().numpy()
+    vo = oracle.field_velocity(nodes, tris, freq, po, qo, pts, c=C, rho=RHO, params={"tau": -1.0})
+    assert _rel(vel, vo) < 2e-4, _rel(vel, vo)
+    mesh.close()
+
+
 def test_mixed_boundary_solve_matches_oracle(bem):
     nodes, tris = inputs.icosphere(3, 0.1)
     n = tris.shape[0]
