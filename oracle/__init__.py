@@ -202,11 +202,14 @@ def geometry(nodes, tris):
 
 
 # ---------------------------------------------------------------- system
-def column_coeffs(bc_type, k, c, rho, beta=None):
+def column_coeffs(bc_type, k, c, rho, beta=None, tau=1.0):
     """Column coefficients (cp, cq) of the unknown vector and (cp0, cq0) of the
     known-data vector (Eq. SystemI, pressure form).
 
-    beta = rho c Y per element (only used on ADMI elements)."""
+    beta = rho c Y per element (only used on ADMI elements), Y the velocity
+    into the wall over p: along the normal for the interior problem
+    (tau = -1, normals out of the fluid), against it for the exterior
+    problem, so q = dp/dn = -tau i k beta p."""
     bc_type = np.asarray(bc_type)
     n = bc_type.shape[0]
     cp = np.zeros(n, np.complex128)
@@ -217,7 +220,7 @@ def column_coeffs(bc_type, k, c, rho, beta=None):
     cp[pu] = 1.0
     adm = bc_type == ADMI
     if adm.any():
-        cq[adm] = -1j * k * np.asarray(beta)[adm]
+        cq[adm] = -1j * k * tau * np.asarray(beta)[adm]
     cq[~pu] = 1.0
     cq0[pu] = 1.0          # known q-part g on VELO / ADMI elements
     cp0[~pu] = 1.0         # known p on PRES elements
@@ -326,7 +329,8 @@ def solve(nodes, tris, freq, c=343.0, rho=1.21, sources=(), bc_type=None, bc_val
     omega = 2.0 * np.pi * freq
     bc_type = np.zeros(n, np.int32) if bc_type is None else np.asarray(bc_type, np.int32)
     bc_value = np.zeros(n, np.complex128) if bc_value is None else _c128(bc_value)
-    cp, cq, cp0, cq0 = column_coeffs(bc_type, k, c, rho, beta)
+    tau = -1.0 if params is not None and params.get("tau", 1.0) < 0 else 1.0
+    cp, cq, cp0, cq0 = column_coeffs(bc_type, k, c, rho, beta, tau)
     cen, nrm, _ = geometry(nodes, tris)
     b = rhs(cen, nrm, k, sources)
     z = known_data(bc_type, bc_value, omega, rho)

@@ -837,8 +837,11 @@ void make_coeffs(bem_mesh_impl &M, double k, double omega, double c, double rho,
             if (ty == BEM_ADMI) {
                 const int r = M.region[e];
                 const double yr = adm[2 * r], yi = adm[2 * r + 1];
-                // a = -i k beta, beta = rho c Y
-                const double br = rho * c * yr, bi = rho * c * yi;
+                // a = -tau i k beta, beta = rho c Y, Y = velocity into the
+                // wall / p (the wall lies along the normal for the interior
+                // problem, against it for the exterior problem)
+                const double t = M.prm.tau < 0 ? -1.0 : 1.0;
+                const double br = t * rho * c * yr, bi = t * rho * c * yi;
                 C.cq[i] = make_float2((float)(k * bi), (float)(-k * br));
                 C.aq[i] = C.cq[i];
             }

@@ -17,7 +17,7 @@ import math
 import numpy as np
 
 __all__ = [
-    "icosahedron", "icosphere", "geodesic_sphere", "bumpy_ellipsoid", "fibonacci_sphere",
+    "icosahedron", "icosphere", "geodesic_sphere", "bumpy_ellipsoid", "duct", "fibonacci_sphere",
     "random_complex", "workload",
 ]
 
@@ -128,6 +128,45 @@ def bumpy_ellipsoid(nu: int, axes=(0.09, 0.075, 0.11), n_bumps: int = 24, seed: 
     disp = (a[None, :] * np.exp(-0.5 * (ang / s[None, :]) ** 2)).sum(axis=1)
     nodes = e + disp[:, None] * u
     return nodes, _orient_outward(nodes, tris)
+
+
+def duct(length: float = 3.4, width: float = 0.2, h: float = 0.05):
+    """Closed duct [0, length] x [-width/2, width/2]^2 (the paper's duct
+    benchmark, Sec. 5.3): every face cut into squares of edge about h, each
+    square into two triangles, wound so that (b - a) x (c - a) points out of
+    the enclosed volume.  Returns (nodes float64 [Nv,3], tris int32 [N,3])."""
+    nx = max(1, int(round(length / h)))
+    ny = max(1, int(round(width / h)))
+    xs = np.linspace(0.0, length, nx + 1)
+    ys = np.linspace(-width / 2, width / 2, ny + 1)
+    centre = np.array([length / 2, 0.0, 0.0])
+    nodes, tris = [], []
+
+    def face(us, vs, point):
+        base = len(nodes)
+        for u in us:
+            for v in vs:
+                nodes.append(point(u, v))
+        m = len(vs)
+        for a in range(len(us) - 1):
+            for b in range(m - 1):
+                i00, i01 = base + a * m + b, base + a * m + b + 1
+                i10, i11 = base + (a + 1) * m + b, base + (a + 1) * m + b + 1
+                tris.append([i00, i10, i11])
+                tris.append([i00, i11, i01])
+
+    face(ys, ys, lambda u, v: (0.0, u, v))
+    face(ys, ys, lambda u, v: (length, u, v))
+    face(xs, ys, lambda u, v: (u, -width / 2, v))
+    face(xs, ys, lambda u, v: (u, width / 2, v))
+    face(xs, ys, lambda u, v: (u, v, -width / 2))
+    face(xs, ys, lambda u, v: (u, v, width / 2))
+    nodes = np.array(nodes, dtype=np.float64)
+    tris = np.array(tris, dtype=np.int32)
+    a, b, c = nodes[tris[:, 0]], nodes[tris[:, 1]], nodes[tris[:, 2]]
+    out = np.einsum("ij,ij->i", np.cross(b - a, c - a), (a + b + c) / 3.0 - centre) < 0
+    tris[out] = tris[out][:, [0, 2, 1]]
+    return nodes, tris
 
 
 def fibonacci_sphere(m: int, radius: float = 1.0, center=(0.0, 0.0, 0.0)):

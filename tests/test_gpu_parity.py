@@ -208,6 +208,38 @@ def test_interior_problem_matches_oracle(bem, mode, level, freq):
     mesh.close()
 
 
+def test_duct_matches_oracle(bem):
+    """The paper's duct benchmark (Sec. 5.3; interior problem with velocity,
+    admittance and sound-hard elements, 2240 elements, 240 Hz) through the
+    FMM path: surface pressure and the field along the axis against the
+    oracle's tau = -1 solution."""
+    c, rho, f = 340.0, 1.3, 240.0
+    nodes, tris = inputs.duct(3.4, 0.2, 0.05)
+    n = tris.shape[0]
+    cen, _, _ = oracle.geometry(nodes, tris)
+    bct = np.full(n, bem.VELO, np.int32)
+    bcv = np.zeros(n, complex)
+    bcv[cen[:, 0] < 1e-9] = 1.0
+    end = cen[:, 0] > 3.4 - 1e-9
+    bct[end] = bem.ADMI
+    region = end.astype(np.int32)
+    adm = np.array([0.0, 1.0 / (rho * c)], complex)
+    mesh = bem.Mesh(nodes, tris, bc_type=bct, bc_value=bcv, region=region, tau=-1.0, trunc_factor=6.0)
+    p, q, info = mesh.solve(f, [], admittance=adm, tol=1e-7, c=c, rho=rho)
+    assert info["converged"], info
+    beta = np.where(end, 1.0, 0.0).astype(complex)
+    po, qo, _ = oracle.solve(nodes, tris, f, c=c, rho=rho, bc_type=bct, bc_value=bcv, beta=beta,
+                             params={"tau": -1.0})
+    ep = _rel(p.cpu().numpy(), po)
+    assert ep < 2e-4, ep
+    xs = np.linspace(0.2, 3.2, 7)
+    pts = np.stack([xs, 0 * xs, 0 * xs], 1)
+    fld = mesh.evaluate(f, p, q, pts, [], c=c, rho=rho).cpu().numpy()
+    fo = oracle.field(nodes, tris, f, po, qo, pts, c=c, params={"tau": -1.0})
+    assert _rel(fld, fo) < 2e-4, _rel(fld, fo)
+    mesh.close()
+
+
 def test_mixed_boundary_solve_matches_oracle(bem):
     nodes, tris = inputs.icosphere(3, 0.1)
     n = tris.shape[0]
