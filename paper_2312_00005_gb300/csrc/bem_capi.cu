@@ -1655,15 +1655,20 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
             }
             ck_launch("k_gm_givens");
         };
-        // nsteps Arnoldi steps: product of v_j (inputs already formed), the
-        // fused Gram-Schmidt step (which also forms v_{j+1}'s inputs), then
-        // the Givens step.  In the graph the Givens step of step t runs on a
-        // side stream beside the product of step t + 1, which does not need
-        // it; step t + 1's Gram-Schmidt waits for it.
+        // the product of the current basis vector (its inputs already formed)
+        auto product = [&]() {
+            matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, nullptr, nullptr, false, M.w.p, false, done, s, true, true);
+        };
+        // nsteps Arnoldi steps, each the fused Gram-Schmidt step of column j
+        // (which also forms v_{j+1}'s product inputs), the Givens step and
+        // the product of v_{j+1}; a cycle's first product runs before its
+        // first steps.  In the graph the Givens step runs on a side stream
+        // beside the product, which does not need it, and the next
+        // Gram-Schmidt step waits for it; the last Givens step of a graph
+        // ends beside its last product, so it does not delay the next graph.
         auto arnoldi_steps = [&](int nsteps) {
             const bool side = use_graph;
             for (int t = 0; t < nsteps; ++t) {
-                matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, nullptr, nullptr, false, M.w.p, false, done, s, true, true);
                 if (side && t > 0) ck(cudaStreamWaitEvent(s, M.ev_giv[t - 1], 0), "wait givens");
                 ortho();
                 if (side) {
@@ -1674,6 +1679,7 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
                 } else {
                     givens(s);
                 }
+                product();
             }
             if (side) ck(cudaStreamWaitEvent(s, M.ev_giv[nsteps - 1], 0), "join givens");
         };
@@ -1697,6 +1703,7 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
             // the cycle ended runs its steps as skips.
             const int max_graphs = (m + batch + batch - 1) / batch;
             int launched = 0, checked = 0;
+            product();
             auto launch_graph = [&]() {
                 if (use_graph) {
                     ck(cudaGraphLaunch(gexec, s), "graph launch");
