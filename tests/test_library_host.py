@@ -43,6 +43,16 @@ def test_params_default_are_the_papers(lib):
     assert p.quad_tol == 1e-3 and p.m_max == 6 and p.rt_subdiv == 1.3 and p.max_depth == 15
     assert p.trunc_factor == 1.8 and p.L_min == 8
     assert abs(p.admissibility - 2 / np.sqrt(3)) < 1e-15
+    assert p.tau == 1.0          # exterior problem unless asked otherwise
+
+
+@pytest.mark.parametrize("tau", [0.0, 0.5, -2.0, float("nan")])
+def test_tau_other_than_plus_or_minus_one_is_rejected(lib, tau):
+    """tau selects the exterior (+1) or interior (-1) problem of Eq. BIE_I;
+    anything else is an argument error, raised before any device work."""
+    nodes, tris = inputs.icosphere(1, 0.1)
+    with pytest.raises(bemfmm.BemError):
+        bemfmm.Mesh(nodes, tris, tau=tau)
 
 
 @pytest.mark.parametrize("lev,freq", [(3, 1000.0), (4, 2000.0), (5, 4000.0)])
