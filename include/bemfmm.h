@@ -262,7 +262,8 @@ int bem_selftest_sincos(const void *x_dev, int64_t n, void *out_dev, void *strea
  * start-up, or hosts whose own allocator owns the device, and that therefore
  * cannot create a mesh handle).  Computes y = A x, A the conventional dense
  * Burton-Miller matrix (every pair by the quadrature of Sec. 3.1, no FMM) of
- * a sound-hard surface (all elements VELO with v = 0, unknown p).
+ * a sound-hard surface (all elements VELO with v = 0, unknown p) for the
+ * exterior problem (tau = +1).
  *   nodes_dev: device double [n_nodes][3]; tris_dev: device int32 [n_tris][3]
  *   (counter-clockwise); x_dev, y_dev: device cf32 [n_tris]; medium may be
  *   NULL (c = 343 m/s).
