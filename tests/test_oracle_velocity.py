@@ -30,17 +30,17 @@ def test_plane_wave_velocity_is_pressure_over_impedance():
 
 def test_velocity_matches_central_differences_of_the_field():
     """Seeded surface data p, q (both terms of Eq. BIE_I matter), a plane
-    wave, points from 0.16 m to 0.9 m off a 0.1 m sphere (regular rules of
-    order 1 to 3): the analytic gradient of the oracle's field equals its
-    central difference with step 1e-6 m (truncation and rounding both far
-    below the tolerance)."""
+    wave and a point source, points from 0.16 m to 0.9 m off a 0.1 m sphere
+    (regular rules of order 1 to 3): the analytic gradient of the oracle's
+    field equals its central difference with step 1e-6 m (truncation and
+    rounding both far below the tolerance)."""
     nodes, tris = inputs.icosphere(2, 0.1)
     n = tris.shape[0]
     f = 800.0
     rng = np.random.default_rng(5)
     p = rng.normal(size=n) + 1j * rng.normal(size=n)
     q = (rng.normal(size=n) + 1j * rng.normal(size=n)) * 10.0
-    src = [("plane", (0.0, 0.6, 0.8), 1.0 + 0.5j)]
+    src = [("plane", (0.0, 0.6, 0.8), 1.0 + 0.5j), ("point", (0.02, -0.01, 0.03), 0.4 - 0.3j)]
     pts = np.array([[0.6, 0.3, 0.7], [0.0, -0.25, 0.12], [0.13, 0.1, -0.2]])
     v = oracle.field_velocity(nodes, tris, f, p, q, pts, c=C, rho=RHO, sources=src)
     grad = v * (1j * 2 * np.pi * f * RHO)
