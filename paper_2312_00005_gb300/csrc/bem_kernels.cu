@@ -27,33 +27,6 @@ __device__ __forceinline__ double2 warp_sum_d(double2 v)
 __device__ __forceinline__ bool skip_now(const int *skip) { return skip != nullptr && *(volatile const int *)skip != 0; }
 
 // ------------------------------------------------------------------ near field
-// Stored near field (Sec. 3.3.3, matrix N): one warp per collocation row i,
-// lanes over the row's near columns (the elements of the near leaves of i's
-// leaf, concatenated); writes A_ij for the unknowns' column coefficients.
-__global__ void k_near_store(NearArgs a, float2 *__restrict__ val, int *__restrict__ err)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= a.E.n) return;
-    const QuadTables &Q = *a.Q;
-    const float4 ch = a.E.chi[i], cl = a.E.clo[i];
-    const float3 xhi = f3(ch), xlo = f3(cl), nx = f3(a.E.nrm[i]);
-    const double xd[3] = {a.E.cd[3 * i], a.E.cd[3 * i + 1], a.E.cd[3 * i + 2]};
-    const int t = a.N.leaf_of[i];
-    const int r_end = a.N.run_ptr[t + 1], nc = a.N.ncol[t];
-    int r = a.N.run_ptr[t];
-    const int64_t base = a.N.row_ptr[i];
-    for (int p = lane; p < nc; p += 32) {
-        const int j = near_col(a.N, r_end, r, p);
-        float2 v;
-        if (!bm_entry(a.E, i, j, xhi, xlo, xd, nx, a.k, a.ik_inv, a.tau, Q, a.cp[j], a.cq[j], v)) {
-            atomicMin(err, j);
-            v = make_float2(0.f, 0.f);
-        }
-        val[base + p] = v;
-    }
-}
-
 // Expensive pairs (heavy_rt2) of the stored near field, listed by kind so
 // that the warps of k_near_store_heavy take pairs of one kind: 0 = self term,
 // 1 = subdivided element, 1 + m = regular order m >= 4 (a sorting hint from
@@ -1107,12 +1080,6 @@ __global__ void k_gather(const float2 *__restrict__ x, const int64_t *__restrict
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = x[perm[i]];
-}
-__global__ void k_scatter(const float2 *__restrict__ x, const int64_t *__restrict__ perm, int64_t n,
-                          float2 *__restrict__ y)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[perm[i]] = x[i];
 }
 // b <- b - y
 __global__ void k_sub(float2 *__restrict__ b, const float2 *__restrict__ y, int64_t n)

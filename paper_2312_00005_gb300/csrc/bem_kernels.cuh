@@ -135,7 +135,6 @@ struct SourceDev {
     double amp[2];
 };
 
-__global__ void k_near_store(NearArgs a, float2 *val, int *err);
 constexpr int kHeavyKinds = 8;          // self, subdivided, orders 2 .. 6 (see k_near_classify)
 __global__ void k_near_classify(NearArgs a, int2 *heavy, unsigned long long *count, const unsigned long long *off);
 __global__ void k_near_store_light(NearArgs a, float2 *val, int *err);
@@ -189,7 +188,6 @@ __global__ void k_field_velocity(ElemDev E, const QuadTables *Q, const double *p
 __global__ void k_field_velocity_finish(const double *pts, int64_t M, int S, float k, float inv_omega_rho,
                                         const SourceDev *src, int nsrc, const float2 *part, float2 *out);
 __global__ void k_gather(const float2 *x, const int64_t *perm, int64_t n, float2 *y);
-__global__ void k_scatter(const float2 *x, const int64_t *perm, int64_t n, float2 *y);
 __global__ void k_sub(float2 *b, const float2 *y, int64_t n);
 __global__ void k_rsub(float2 *w, const float2 *b, int64_t n);
 __global__ void k_pq(const float2 *u, const float2 *z, const float2 *aq, const int *type, const int64_t *perm,
