@@ -6,8 +6,8 @@
  * code for solving acoustic scattering problems", arXiv 2312.00005.
  *   - constant elements on flat triangles, collocation at the element
  *     midpoints (Sec. 2.2, 2.3);
- *   - exterior problem (tau = 1) with Burton-Miller coupling gamma = i/k,
- *     Eq. SystemI;
+ *   - exterior (tau = +1) or interior (tau = -1, bem_params.tau) problem
+ *     with Burton-Miller coupling gamma = i/k, Eq. SystemI;
  *   - near field by the quadrature of Sec. 3.1 (Duffy singular rule,
  *     edge-integral hypersingular rule, subdivision while r~ < 1.3, regular
  *     order from the a-priori estimates, m <= 6);
@@ -19,16 +19,18 @@
  * Variables are pressures: p on the surface and q = dp/dn = i w rho v, with
  * n the outward normal (pointing away from the enclosed volume: into the
  * fluid for the exterior problem, App. A, out of it for the interior problem
- * of bem_params.tau = -1) and time factor e^{-i w t}.  Complex numbers are interleaved (re, im): float2 ("cf32") on
- * the device, double[2] on the host.
+ * of bem_params.tau = -1) and time factor e^{-i w t}.  Complex numbers are
+ * interleaved (re, im): float2 ("cf32") on the device, double[2] on the
+ * host.
  *
  * Ownership: every entry point copies what it needs from host arrays before
  * it returns.  Device buffers passed in belong to the caller and must hold the
  * stated number of elements; the library never frees them.  Work is
  * enqueued on the caller's CUDA stream (a cudaStream_t passed as void*;
  * NULL = the legacy default stream) and is stream-ordered.  bem_solve,
- * bem_matvec_host and bem_mesh_stats synchronise the stream before they
- * return; bem_matvec and bem_evaluate do not.
+ * bem_solve_sweep, bem_matvec_host and bem_mesh_stats synchronise the stream
+ * before they return; bem_matvec, bem_evaluate and bem_evaluate_velocity do
+ * not.
  *
  * Errors: every function returns BEM_OK (0), a negative error code, or a
  * positive warning code with all outputs written.  bem_last_error() gives a
@@ -142,8 +144,9 @@ typedef struct bem_plan_stats {
 void bem_params_default(bem_params *p);
 
 /* Create a mesh (App. A): nodes [n_nodes][3] in metres, tris [n_tris][3]
- * 0-based node indices in counter-clockwise order seen from the fluid
- * (outward normal; not checked, Sec. 2.1).  bc_type [n_tris] (NULL = all
+ * 0-based node indices in counter-clockwise order seen from outside the
+ * enclosed volume (outward normal: into the fluid for the exterior problem,
+ * out of it for the interior one; not checked, Sec. 2.1).  bc_type [n_tris] (NULL = all
  * BEM_VELO), bc_value [n_tris][2] complex (NULL = 0): p for PRES, v for
  * VELO, the extra velocity for ADMI.  region [n_tris] (NULL = 0) selects the
  * admittance entry of ADMI elements.  params NULL = defaults.  Geometry,
@@ -155,11 +158,12 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
 
 int bem_mesh_destroy(void *mesh);
 
-/* y = A x for n_rhs right-hand sides (Eq. SystemI, tau = 1), where A is the
+/* y = A x for n_rhs right-hand sides (Eq. SystemI with the mesh's tau), where A is the
  * Burton-Miller matrix in the unknowns u (p on VELO / ADMI elements, q on
  * PRES elements) with the boundary conditions folded in: column j enters as
  * p_j = c^p_j u_j and q_j = c^q_j u_j with (c^p, c^q) = (1, 0) for VELO,
- * (1, -ik rho c Y) for ADMI and (0, 1) for PRES.
+ * (1, -tau ik rho c Y) for ADMI (Y = velocity into the wall / p) and (0, 1)
+ * for PRES.
  * x_dev, y_dev: device cf32 [n_rhs][n_tris] in the caller's element order.
  * admittance: host double [n_regions][2] (Y in m/(Pa s)); may be NULL when
  * no element is ADMI.  Builds (or reuses) the plan for this frequency. */
@@ -174,7 +178,8 @@ int bem_matvec_host(void *mesh, double freq_hz, const bem_medium *medium,
 
 /* Solve Eq. SystemI at one frequency for the incident field of n_src
  * sources and the mesh's boundary data, with restarted GMRES on the device
- * (FP64 orthogonalisation and Givens rotations; FP32 products).  Writes the
+ * (classical Gram-Schmidt with compensated FP32 sums, FP64 Hessenberg
+ * matrix and Givens rotations; FP32 products).  Writes the
  * surface pressure p_dev and q_dev = dp/dn (device cf32 [n_tris] each, caller
  * order; q_dev may be NULL).  tol: relative residual target (e.g. 1e-6).
  * max_iter: cap on products.  info may be NULL.  Returns BEM_OK,
@@ -194,9 +199,9 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
  * buffers, so that work overlaps the solve.
  *   p_dev, q_dev: device cf32 [n_freq][n_tris] (q_dev may be NULL when
  *   n_pts = 0); pts: host double [n_pts][3] field points (may be NULL with
- *   n_pts = 0); field_dev: device cf32 [n_freq][n_pts], the exterior field
- *   (Eq. BIE_I with lambda = 1) at each frequency; infos: host [n_freq] or
- *   NULL.
+ *   n_pts = 0); field_dev: device cf32 [n_freq][n_pts], the field (Eq. BIE_I
+ *   with lambda = 1, as bem_evaluate) at each frequency; infos: host
+ *   [n_freq] or NULL.
  * Returns on the first error (the outputs of earlier frequencies are
  * written); otherwise BEM_OK or the first warning met (its message in
  * bem_last_error).  The caller's stream is joined and synchronised. */
@@ -205,8 +210,9 @@ int bem_solve_sweep(void *mesh, const double *freqs_hz, int32_t n_freq, const be
                     double tol, int32_t max_iter, void *p_dev, void *q_dev, const double *pts,
                     int64_t n_pts, void *field_dev, bem_solve_info *infos, void *stream);
 
-/* Total pressure at M exterior points (Eq. BIE_I with lambda = 1):
- * p(x) = p_inc(x) + sum_j [H(x)_j p_j - G(x)_j q_j], element integrals by
+/* Total pressure at M field points (Eq. BIE_I with lambda = 1), outside the
+ * surface for the exterior problem, inside it for the interior one:
+ * p(x) = p_inc(x) + tau sum_j [H(x)_j p_j - G(x)_j q_j], element integrals by
  * the regular / quasi-singular rules measured from x.  p_dev, q_dev: device
  * cf32 [n_tris] (caller order, as written by bem_solve).  pts: host double
  * [M][3].  out_dev: device cf32 [M]. */
@@ -214,10 +220,10 @@ int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem
                  int32_t n_src, const void *p_dev, const void *q_dev, const double *pts,
                  int64_t M, void *out_dev, void *stream);
 
-/* Particle velocity at M exterior points (Eq. utopandv: v = grad p / (i w
+/* Particle velocity at M field points (Eq. utopandv: v = grad p / (i w
  * rho); the paper writes its x, y and z components per evaluation point,
  * appendix Output, file vEvalGrid): grad p(x) = grad p_inc(x) +
- * sum_j [grad H(x)_j p_j - grad G(x)_j q_j], i.e. Eq. BIE_I (lambda = 1)
+ * tau sum_j [grad H(x)_j p_j - grad G(x)_j q_j], i.e. Eq. BIE_I (lambda = 1)
  * differentiated under the integral, with the element rules of
  * bem_evaluate.  rho from medium.  p_dev, q_dev: device cf32 [n_tris]
  * (caller order, as written by bem_solve).  pts: host double [M][3].
