@@ -113,6 +113,31 @@ def test_fmm_matvec_after_frequency_change(bem):
     assert err < 2e-4, err
 
 
+@pytest.mark.parametrize("tau", [1.0, -1.0])
+def test_recomputed_near_field_matches_stored_and_oracle(bem, tau):
+    """near_store = 0 (every near-field entry recomputed inside each product
+    by its own kernel, self terms included) gives the stored path's product,
+    and both match the oracle's operator; exterior and interior problems
+    (the self entry's identity half, the admittance sign), mixed boundary
+    conditions."""
+    nodes, tris = inputs.icosphere(4, 0.1)
+    n = tris.shape[0]
+    freq = 2000.0
+    k = 2 * np.pi * freq / C
+    bct, region, adm = _mixed_bc(n, 7)
+    x = inputs.random_complex(n, 24)
+    xt = torch.tensor(x, dtype=torch.complex64, device="cuda")
+    ys = {}
+    for ns in (1, 0):
+        mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region, trunc_factor=6.0, near_store=ns, tau=tau)
+        ys[ns] = mesh.matvec(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy()
+        mesh.close()
+    assert _rel(ys[0], ys[1]) < 1e-5, _rel(ys[0], ys[1])
+    cp, cq, _, _ = oracle.column_coeffs(bct, k, C, RHO, RHO * C * adm[region], tau)
+    yo = oracle.assemble(nodes, tris, k, cp, cq, params={"tau": tau}) @ x
+    assert _rel(ys[0], yo) < 1e-4, _rel(ys[0], yo)
+
+
 def test_solve_and_field_match_oracle(bem):
     nodes, tris = inputs.icosphere(3, 0.1)
     freq = 1000.0
