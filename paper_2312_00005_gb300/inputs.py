@@ -7,8 +7,9 @@ kernels or quadrature), so the CUDA path and the oracle can both be fed from
 it without sharing any of the method.
 
 Workloads follow the shapes the paper benchmarks (Sec. 5.1: icosahedron-based
-sphere meshes; Sec. 5.2: a head-like closed surface) with the sizes of the
-configurations this library is measured on.
+sphere meshes; Sec. 5.2: a head-like closed surface; Sec. 5.3: a closed duct
+for the interior problem) with the sizes of the configurations this library
+is measured on.
 """
 from __future__ import annotations
 
