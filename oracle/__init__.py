@@ -27,7 +27,7 @@ __all__ = [
     "lib", "build", "VELO", "PRES", "ADMI", "geometry", "gauss_legendre", "gauss_jacobi10",
     "triangle_rule", "quad_order", "kernels", "element_integrals", "duffy_G", "edge_fp",
     "column_coeffs", "assemble", "matvec_rows", "matvec_dense", "gmres", "incident", "rhs",
-    "solve", "field", "field_velocity", "sph_hankel", "sphere_grid", "translation", "fmm_pair", "num_threads",
+    "solve", "field", "field_velocity", "field_matrices", "admittance_gradient", "sph_hankel", "sphere_grid", "translation", "fmm_pair", "num_threads",
     "OracleError",
 ]
 
@@ -83,6 +83,7 @@ def lib():
                 "orc_incident": (None, [P, P, l, d, i, P, P, P, P]),
                 "orc_field": (i, [P, P, l, d, P, P, P, P, l, P, P]),
                 "orc_field_grad": (i, [P, P, l, d, P, P, P, P, l, P, P]),
+                "orc_field_mats": (i, [P, P, l, d, P, P, l, P, P, P]),
                 "orc_sph_hankel": (None, [i, d, P]),
                 "orc_sphere_grid": (i, [i, P, P]),
                 "orc_translation": (None, [i, d, P, P, i, P]),
@@ -396,6 +397,98 @@ def field_velocity(nodes, tris, freq, p, q, pts, c=343.0, rho=1.21, sources=(), 
             grad[:, ax] += dpi
     omega = 2.0 * np.pi * freq
     return grad / (1j * omega * rho)
+
+
+def field_matrices(nodes, tris, freq, pts, c=343.0, params=None):
+    """(Gm, Hm): the element integrals G(x_r)_j and H(x_r)_j of the
+    representation formula (Eq. BIE_I, lambda = 1) as dense [npts, N]
+    matrices, without the tau sign (the field is p_inc + tau (Hm p - Gm q))."""
+    nodes, tris = _f64(nodes), _i32(tris)
+    n = tris.shape[0]
+    pts = _f64(pts, (-1, 3))
+    k = 2.0 * np.pi * freq / c
+    Gm = np.zeros((pts.shape[0], n), np.complex128)
+    Hm = np.zeros((pts.shape[0], n), np.complex128)
+    bad = ctypes.c_long(-1)
+    st = lib().orc_field_mats(_p(nodes), _p(tris), n, float(k), _pp(_params(params)), _p(pts), pts.shape[0],
+                              _p(Gm), _p(Hm), ctypes.byref(bad))
+    if st:
+        raise OracleError("number of subdivisions exceeds the limit at element %d" % bad.value,
+                          bad.value)
+    return Gm, Hm
+
+
+def admittance_gradient(nodes, tris, freq, pts, region, Y, sources=(), bc_type=None, bc_value=None,
+                        c=343.0, rho=1.21, params=None, tol=1e-12):
+    """Field loss L = sum_m |p(x_m)|^2 at the points x_m and its gradient with
+    respect to the region admittances Y_r, by the adjoint of the discrete
+    system (a derived quantity: the paper solves the forward problem only).
+
+    region: per element, the admittance region (index into Y) or -1; an
+    element with region >= 0 is ADMI (bc_type may also be given), with
+    beta_j = rho c Y_region(j) and the column coefficient
+    cq_j = -tau i k beta_j of the admittance condition.
+    Returns (L, grad, info) with grad_r = dL/d(Re Y_r) + i dL/d(Im Y_r).
+
+    Steps (pressure form, Eq. SystemI and Eq. BIE_I):
+      1. A is linear in the column coefficients: A = Ap diag(cp) + Aq diag(cq),
+         Ap the operator on p-unknowns (cp = 1, cq = 0), Aq on q-unknowns.
+      2. Forward: A u = b; p = cp u + cp0 z, q = cq u + cq0 z.
+      3. Field f = p_inc + tau (Hm p - Gm q) = p_inc + F u + const with
+         F = tau (Hm diag(cp) - Gm diag(cq)); L = f^H f.
+      4. u and f are holomorphic in Y; with s_r = f^H df/dY_r the real
+         gradient is 2 conj(s_r).
+      5. df/dY_r = -tau Gm (d_r o u) - F A^-1 Aq (d_r o u), d_r = dcq/dY_r
+         = -tau i k rho c on ADMI elements of region r, 0 elsewhere.
+      6. Adjoint: A^T lam = F^T conj(f), so that f^H F A^-1 = lam^T; then
+         s_r = sum over elements j of region r of
+               d_j u_j [ -tau (Gm^T conj f)_j - (Aq^T lam)_j ]."""
+    nodes, tris = _f64(nodes), _i32(tris)
+    n = tris.shape[0]
+    k = 2.0 * np.pi * freq / c
+    omega = 2.0 * np.pi * freq
+    tau = -1.0 if params is not None and params.get("tau", 1.0) < 0 else 1.0
+    region = np.asarray(region, np.int64).reshape(n)
+    Y = np.asarray(Y, np.complex128).reshape(-1)
+    if bc_type is None:
+        bc_type = np.where(region >= 0, ADMI, VELO).astype(np.int32)
+    bc_type = np.asarray(bc_type, np.int32)
+    adm = bc_type == ADMI
+    if np.any(region[adm] < 0) or np.any(region >= Y.shape[0]):
+        raise ValueError("every ADMI element needs a region index into Y")
+    bc_value = np.zeros(n, np.complex128) if bc_value is None else _c128(bc_value)
+    beta = np.zeros(n, np.complex128)
+    beta[adm] = rho * c * Y[region[adm]]
+    cp, cq, cp0, cq0 = column_coeffs(bc_type, k, c, rho, beta, tau)
+    cen, nrm, _ = geometry(nodes, tris)
+    b = rhs(cen, nrm, k, sources)
+    z = known_data(bc_type, bc_value, omega, rho)
+    if np.any(z != 0):
+        b = b - assemble(nodes, tris, k, cp0, cq0, params) @ z
+    ones, zeros = np.ones(n, np.complex128), np.zeros(n, np.complex128)
+    Ap = assemble(nodes, tris, k, ones, zeros, params)
+    Aq = assemble(nodes, tris, k, zeros, ones, params)
+    A = Ap * cp[None, :] + Aq * cq[None, :]
+    del Ap
+    u, info_f = gmres(A, b, tol=tol, maxit=4 * n + 100, restart=min(n, 300))
+    p = cp * u + cp0 * z
+    q = cq * u + cq0 * z
+    Gm, Hm = field_matrices(nodes, tris, freq, pts, c, params)
+    f = tau * (Hm @ p - Gm @ q)
+    for (kind, vec, amp) in sources:
+        pi, _ = incident(pts, None, k, kind, vec, amp)
+        f = f + pi
+    L = float(np.real(np.vdot(f, f)))
+    F = tau * (Hm * cp[None, :] - Gm * cq[None, :])
+    lam, info_a = gmres(np.ascontiguousarray(A.T), F.T @ np.conj(f), tol=tol, maxit=4 * n + 100,
+                        restart=min(n, 300))
+    d = np.where(adm, -tau * 1j * k * rho * c, 0.0)
+    t = d * u * (-tau * (Gm.T @ np.conj(f)) - Aq.T @ lam)
+    s = np.zeros(Y.shape[0], np.complex128)
+    np.add.at(s, region[adm], t[adm])
+    grad = 2.0 * np.conj(s)
+    info = {"forward": info_f, "adjoint": info_a, "p": p, "q": q, "field": f}
+    return L, grad, info
 
 
 # ---------------------------------------------------------------- FMM pieces (unit tests)

@@ -29,6 +29,10 @@
  *   - the field at exterior points from the representation formula with
  *     lambda = 1 (Eq. BIE_I; interior points when tau = -1), and its gradient (the particle velocity of
  *     Eq. utopandv) from the same formula differentiated under the integral;
+ *   - the field-point integrals G(x)_j, H(x)_j as dense matrices, for the
+ *     adjoint gradient of a field loss with respect to the admittances (a
+ *     derived quantity the paper does not compute; its steps are in the
+ *     Python wrapper);
  *   - the pieces of the plane-wave expansion of Eq. FMMBase (spherical Hankel
  *     functions by upward recursion, Legendre polynomials, the unit-sphere
  *     grid of Sec. 3.3.1, the translation D_L and the single-pair expansion)
@@ -854,6 +858,47 @@ int orc_field(const double *nodes, const int *tris, long n, double k, const doub
         s *= P.tau;
         out[2 * r] = creal(s);
         out[2 * r + 1] = cimag(s);
+    }
+    free(cen); free(nrm); free(area);
+    if (bad_elem) *bad_elem = bad;
+    return bad >= 0 ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The element integrals of the representation formula (Eq. BIE_I with      */
+/* lambda = 1) as dense matrices, Gm[r][j] = G(x_r)_j and Hm[r][j] = H(x_r)_j */
+/* (row-major [npts][n] complex), without the tau sign: the field is         */
+/* p_inc + tau (Hm p - Gm q).  Same rules as orc_field.  Used by the adjoint  */
+/* gradient, which needs the transposed field operator.  Returns 0 or -1     */
+/* (subdivision limit) with *bad_elem.                                       */
+/* ------------------------------------------------------------------------ */
+int orc_field_mats(const double *nodes, const int *tris, long n, double k, const double *params,
+                   const double *pts, long npts, double *Gm, double *Hm, long *bad_elem)
+{
+    ensure_rules();
+    orc_params P;
+    read_params(params, &P);
+    double *cen = (double *)malloc(sizeof(double) * 3 * n), *nrm = (double *)malloc(sizeof(double) * 3 * n),
+           *area = (double *)malloc(sizeof(double) * n);
+    orc_geometry(nodes, tris, n, cen, nrm, area);
+    long bad = -1;
+    double nx0[3] = {0.0, 0.0, 1.0}; /* H' and E are not used here */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long r = 0; r < npts; ++r) {
+        for (long j = 0; j < n; ++j) {
+            const double *a = nodes + 3 * tris[3 * j], *b = nodes + 3 * tris[3 * j + 1],
+                         *c = nodes + 3 * tris[3 * j + 2];
+            cplx o[4] = {0.0, 0.0, 0.0, 0.0};
+            if (regular_integrals(pts + 3 * r, nx0, a, b, c, nrm + 3 * j, k, 0, &P, o)) {
+#pragma omp critical
+                { if (bad < 0 || j < bad) bad = j; }
+            }
+            size_t e = 2 * ((size_t)r * n + j);
+            Gm[e] = creal(o[0]);
+            Gm[e + 1] = cimag(o[0]);
+            Hm[e] = creal(o[1]);
+            Hm[e + 1] = cimag(o[1]);
+        }
     }
     free(cen); free(nrm); free(area);
     if (bad_elem) *bad_elem = bad;

@@ -46,6 +46,29 @@ def sphere_plane_wave(points, k, a, beta=0.0, nmax=None):
     return p
 
 
+def sphere_plane_wave_dbeta(points, k, a, beta, nmax=None):
+    """Derivative dp/d(beta) of the exterior field of sphere_plane_wave (points
+    with r > a).  Only b_n depends on beta; by the quotient rule
+    db_n/dbeta = -i [j_n (h_n' + i beta h_n) - h_n (j_n' + i beta j_n)]
+                 / (h_n' + i beta h_n)^2   (Bessel values at ka)."""
+    pts = np.asarray(points, dtype=np.float64).reshape(-1, 3)
+    r = np.linalg.norm(pts, axis=1)
+    if np.any(r <= a):
+        raise ValueError("exterior points only")
+    ct = pts[:, 2] / r
+    ka = k * a
+    if nmax is None:
+        nmax = int(ka + 30 + 2 * np.max(k * r))
+    dp = np.zeros(pts.shape[0], np.complex128)
+    for n in range(nmax + 1):
+        jn_a, djn_a = spherical_jn(n, ka), spherical_jn(n, ka, True)
+        hn_a, dhn_a = _h(n, ka), _h(n, ka, True)
+        den = dhn_a + 1j * beta * hn_a
+        dbn = -1j * (jn_a * den - hn_a * (djn_a + 1j * beta * jn_a)) / (den * den)
+        dp += (1j ** n) * (2 * n + 1) * dbn * _h(n, k * r) * eval_legendre(n, ct)
+    return dp
+
+
 def monopole(points, x0, k, amp=1.0):
     """Free-field point source amp e^{ikR}/(4 pi R) and its gradient."""
     pts = np.asarray(points, dtype=np.float64).reshape(-1, 3)
