@@ -91,6 +91,11 @@ typedef struct bem_params {
                                inside the closed surface (Eq. BIE_I, Eq. SystemI: the sign of
                                every integral operator).  Normals point away from the enclosed
                                volume in both cases (Sec. 2.1).  Other values: BEM_E_ARG.    */
+    int32_t row_scaling;    /* 1: row-scaling preconditioner of the iterative solver (Sec. 3.2):
+                               bem_solve / bem_solve_sweep run GMRES on D^-1 A u = D^-1 b with
+                               D = diag(A) (the self entries), and tol and relres refer to
+                               that scaled residual; the solution is that of A u = b.
+                               0: off (default).  Other values: BEM_E_ARG.                    */
 } bem_params;
 
 typedef struct bem_medium {
@@ -107,7 +112,8 @@ typedef struct bem_source {
 typedef struct bem_solve_info {
     int32_t iterations;       /* matrix-vector products in GMRES              */
     int32_t restarts;
-    double  relres;           /* final ||b - A u|| / ||b|| (GMRES estimate)    */
+    double  relres;           /* final ||b - A u|| / ||b|| (GMRES estimate; of the
+                                 row-scaled system when row_scaling is on)     */
     double  seconds;          /* wall time of the call                         */
     int32_t levels;           /* FMM levels with interaction lists             */
     int32_t L[16];            /* expansion length per used level, finest last  */

@@ -317,12 +317,16 @@ def rhs(cen, nrm, k, sources):
 
 
 def solve(nodes, tris, freq, c=343.0, rho=1.21, sources=(), bc_type=None, bc_value=None,
-          beta=None, tol=1e-8, maxit=2000, restart=300, params=None, return_system=False):
+          beta=None, tol=1e-8, maxit=2000, restart=300, params=None, return_system=False,
+          row_scaling=False):
     """Dense collocation BEM solve (Eq. SystemI) with GMRES.
 
     sources: iterable of (kind, vector, complex amplitude).
     bc_type / bc_value: per element (default all VELO with v = 0).
     beta: per-element rho c Y for ADMI elements.
+    row_scaling: GMRES on D^-1 A u = D^-1 b with D = diag(A), the solver's
+    row-scaling preconditioner (Sec. 3.2); tol then applies to the scaled
+    residual.
     Returns (p, q, info) at the element midpoints."""
     tris = _i32(tris)
     n = tris.shape[0]
@@ -340,7 +344,11 @@ def solve(nodes, tris, freq, c=343.0, rho=1.21, sources=(), bc_type=None, bc_val
         b = b - A0 @ z
         del A0
     A = assemble(nodes, tris, k, cp, cq, params)
-    u, info = gmres(A, b, tol=tol, maxit=maxit, restart=restart)
+    if row_scaling:
+        dinv = 1.0 / np.diag(A)
+        u, info = gmres(A * dinv[:, None], b * dinv, tol=tol, maxit=maxit, restart=restart)
+    else:
+        u, info = gmres(A, b, tol=tol, maxit=maxit, restart=restart)
     pu = bc_type != PRES
     p = np.where(pu, u, z)
     # on VELO / ADMI elements q = a u + g (cq holds a = -ik beta, zero for VELO)

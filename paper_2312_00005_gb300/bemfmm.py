@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
         ("rt_subdiv", ctypes.c_double), ("max_depth", ctypes.c_int32), ("trunc_factor", ctypes.c_double),
         ("L_min", ctypes.c_int32), ("admissibility", ctypes.c_double), ("leaf_edge", ctypes.c_double),
         ("stability_max", ctypes.c_double), ("near_store", ctypes.c_int32), ("restart", ctypes.c_int32),
-        ("autotune", ctypes.c_int32), ("tau", ctypes.c_double),
+        ("autotune", ctypes.c_int32), ("tau", ctypes.c_double), ("row_scaling", ctypes.c_int32),
     ]
 
 

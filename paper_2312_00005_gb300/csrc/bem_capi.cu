@@ -298,6 +298,7 @@ struct bem_mesh_impl {
     DevArr<QuadTables> Q;
     DevArr<int> type;
     DevArr<float2> xint, ynear, tmp, tmp2, bvec, uvec;
+    DevArr<float2> dinv;         // row scaling 1 / A_ii (internal order) when row_scaling is on
     DevArr<float4> wts;          // far-field weights (alpha, c) per element
     // GMRES workspace
     DevArr<float2> V, w;
@@ -1319,6 +1320,7 @@ void bem_params_default(bem_params *p)
     p->restart = 100;
     p->autotune = 1;
     p->tau = 1.0;
+    p->row_scaling = 0;
 }
 
 const char *bem_last_error(void) { return g_err.c_str(); }
@@ -1340,6 +1342,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
     if (p.max_depth < 0 || p.max_depth > 15) return set_err(BEM_E_ARG, "max_depth must be in 0..15");
     if (p.restart < 2 || p.restart > kMaxRestart) return set_err(BEM_E_ARG, "restart must be in 2..256");
     if (!(p.tau == 1.0 || p.tau == -1.0)) return set_err(BEM_E_ARG, "tau must be +1 (exterior) or -1 (interior)");
+    if (p.row_scaling != 0 && p.row_scaling != 1) return set_err(BEM_E_ARG, "row_scaling must be 0 or 1");
     if (!(p.quad_tol > 0) || !(p.rt_subdiv > 0) || !(p.admissibility > 0) || p.L_min < 1 || p.L_min > 200)
         return set_err(BEM_E_ARG, "invalid parameter");
     try {
@@ -1540,6 +1543,22 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
             }
             ck_launch("k_sub");
         }
+        // row scaling (Sec. 3.2): GMRES on D^-1 A u = D^-1 b, D = diag(A)
+        const bool rscale = M.prm.row_scaling != 0;
+        if (rscale) {
+            M.dinv.alloc(n);
+            NearArgs na = near_args(M, P, fr(M).cp.p, fr(M).cq.p);
+            {
+                KTimer kt_("k_row_scale_init", s);
+                k_row_scale_init<<<nblocks(n, 128), 128, 0, s>>>(na, M.dinv.p, fr(M).err.p);
+            }
+            ck_launch("k_row_scale_init");
+            {
+                KTimer kt_("k_row_scale", s);
+                k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(M.bvec.p, nullptr, M.dinv.p, n, nullptr);
+            }
+            ck_launch("k_row_scale");
+        }
         ck(cudaStreamSynchronize(s), "sync");
         auto t_rhs = std::chrono::steady_clock::now();
         // GMRES workspace
@@ -1655,9 +1674,17 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
             }
             ck_launch("k_gm_givens");
         };
-        // the product of the current basis vector (its inputs already formed)
+        // the product of the current basis vector (its inputs already formed),
+        // row-scaled when row scaling is on (both parts that k_gm_ortho adds)
         auto product = [&]() {
             matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, nullptr, nullptr, false, M.w.p, false, done, s, true, true);
+            if (rscale) {
+                {
+                    KTimer kt_("k_row_scale", s);
+                    k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.ynear.p, M.dinv.p, n, done);
+                }
+                ck_launch("k_row_scale");
+            }
         };
         // nsteps Arnoldi steps, each the fused Gram-Schmidt step of column j
         // (which also forms v_{j+1}'s product inputs), the Givens step and
@@ -1752,7 +1779,14 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
             // restart: r = b - A x
             ++restarts;
             matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, M.uvec.p, nullptr, false, M.w.p, false, nullptr, s);
-            k_rsub<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.bvec.p, n);   // w = b - A x
+            if (rscale) {
+                {
+                    KTimer kt_("k_row_scale", s);
+                    k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, nullptr, M.dinv.p, n, nullptr);
+                }
+                ck_launch("k_row_scale");
+            }
+            k_rsub<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.bvec.p, n);   // w = b - A x (row-scaled: D^-1 (b - A x))
             ck_launch("k_rsub");
             {
                 KTimer kt_("k_norm_part", s);

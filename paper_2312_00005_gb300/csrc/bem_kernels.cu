@@ -425,6 +425,39 @@ __global__ void k_near_fused(NearArgs a, const float2 *__restrict__ x, float2 *_
     if (lane == 0) y[i] = acc;
 }
 
+// Row scaling of Eq. SystemI (Sec. 3.2, the solver's row-scaling
+// preconditioner): dinv_i = 1 / A_ii, the self entry of row i with the
+// element's own column coefficients (the value the stored near field holds).
+__global__ void k_row_scale_init(NearArgs a, float2 *__restrict__ dinv, int *__restrict__ err)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.E.n) return;
+    const float4 ch = a.E.chi[i], cl = a.E.clo[i];
+    const float3 xhi = f3(ch), xlo = f3(cl), nx = f3(a.E.nrm[i]);
+    const double xd[3] = {a.E.cd[3 * i], a.E.cd[3 * i + 1], a.E.cd[3 * i + 2]};
+    float2 v;
+    if (!bm_entry(a.E, i, i, xhi, xlo, xd, nx, a.k, a.ik_inv, a.tau, *a.Q, a.cp[i], a.cq[i], v)) {
+        atomicMin(err, (int)i);
+        v = make_float2(1.f, 0.f);
+    }
+    const float m2 = v.x * v.x + v.y * v.y;
+    dinv[i] = m2 > 0.f ? make_float2(v.x / m2, -v.y / m2) : make_float2(1.f, 0.f);
+}
+
+// y_i *= dinv_i, and y2_i *= dinv_i when y2 is given (the two parts of a
+// product that the Gram-Schmidt step adds): the row scaling of a product or
+// of the right-hand side.  Skips with the product kernels.
+__global__ void k_row_scale(float2 *__restrict__ y, float2 *__restrict__ y2, const float2 *__restrict__ dinv,
+                            int64_t n, const int *skip)
+{
+    if (skip_now(skip)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 d = dinv[i];
+    y[i] = cmul(y[i], d);
+    if (y2) y2[i] = cmul(y2[i], d);
+}
+
 // ------------------------------------------------------------------ far field
 // Per product: gather x into the internal order (x_int[i] = x[perm[i]] or
 // x = xbase + jidx * n) and form the aggregation weights of the centroid

@@ -188,6 +188,8 @@ __global__ void k_field_velocity(ElemDev E, const QuadTables *Q, const double *p
 __global__ void k_field_velocity_finish(const double *pts, int64_t M, int S, float k, float inv_omega_rho,
                                         const SourceDev *src, int nsrc, const float2 *part, float2 *out);
 __global__ void k_gather(const float2 *x, const int64_t *perm, int64_t n, float2 *y);
+__global__ void k_row_scale_init(NearArgs a, float2 *dinv, int *err);
+__global__ void k_row_scale(float2 *y, float2 *y2, const float2 *dinv, int64_t n, const int *skip);
 __global__ void k_sub(float2 *b, const float2 *y, int64_t n);
 __global__ void k_rsub(float2 *w, const float2 *b, int64_t n);
 __global__ void k_pq(const float2 *u, const float2 *z, const float2 *aq, const int *type, const int64_t *perm,

@@ -44,6 +44,14 @@ def test_params_default_are_the_papers(lib):
     assert p.trunc_factor == 1.8 and p.L_min == 8
     assert abs(p.admissibility - 2 / np.sqrt(3)) < 1e-15
     assert p.tau == 1.0          # exterior problem unless asked otherwise
+    assert p.row_scaling == 0    # no preconditioner unless asked (Sec. 3.2: an option)
+
+
+@pytest.mark.parametrize("rs", [-1, 2])
+def test_row_scaling_other_than_zero_or_one_is_rejected(lib, rs):
+    nodes, tris = inputs.icosphere(1, 0.1)
+    with pytest.raises(bemfmm.BemError):
+        bemfmm.Mesh(nodes, tris, row_scaling=rs)
 
 
 @pytest.mark.parametrize("tau", [0.0, 0.5, -2.0, float("nan")])

@@ -159,3 +159,29 @@ def test_gmres_and_matvecs_against_library(sphere1280):
     # GMRES reports non-convergence when capped (cf. the CGS warning, Sec. 3.2)
     xs, info = oracle.gmres(A_, b, tol=1e-12, maxit=3)
     assert not info["converged"] and info["iterations"] == 3
+
+
+def test_row_scaling_same_solution_fewer_iterations(sphere1280):
+    """The row-scaling preconditioner of the iterative solver (Sec. 3.2),
+    read as D^-1 A u = D^-1 b with D = diag(A): the same solution, and on a
+    sphere with pressure data on its upper half and velocity data on its
+    lower half (pressure rows have a diagonal near gamma/2 = i/(2k), two
+    orders below the others at 4 kHz) GMRES needs far fewer products; on
+    the sound-hard sphere the count hardly changes."""
+    nodes, tris = sphere1280
+    n = tris.shape[0]
+    f = 4000.0
+    cen, _, _ = oracle.geometry(nodes, tris)
+    bct = np.where(cen[:, 2] > 0, oracle.PRES, oracle.VELO).astype(np.int32)
+    rng = np.random.default_rng(3)
+    bcv = np.where(bct == oracle.PRES, 1.0, 1e-3) * (rng.normal(size=n) + 1j * rng.normal(size=n))
+    kw = dict(c=C, rho=RHO, sources=PLANE_Z, bc_type=bct, bc_value=bcv, tol=1e-10, restart=1000)
+    p0, q0, i0 = oracle.solve(nodes, tris, f, **kw)
+    p1, q1, i1 = oracle.solve(nodes, tris, f, row_scaling=True, **kw)
+    assert i0["converged"] and i1["converged"]
+    assert _relerr(p1, p0)[0] < 1e-7 and np.linalg.norm(q1 - q0) < 1e-7 * np.linalg.norm(q0)
+    assert 2 * i1["iterations"] < i0["iterations"], (i0, i1)
+    h0 = oracle.solve(nodes, tris, f, c=C, rho=RHO, sources=PLANE_Z, tol=1e-10, restart=1000)
+    h1 = oracle.solve(nodes, tris, f, c=C, rho=RHO, sources=PLANE_Z, tol=1e-10, restart=1000, row_scaling=True)
+    assert _relerr(h1[0], h0[0])[0] < 1e-7
+    assert abs(h1[2]["iterations"] - h0[2]["iterations"]) <= 0.2 * h0[2]["iterations"]
