@@ -239,6 +239,29 @@ int bem_evaluate_velocity(void *mesh, double freq_hz, const bem_medium *medium, 
                           int32_t n_src, const void *p_dev, const void *q_dev, const double *pts, int64_t M,
                           void *v_out_dev, void *stream);
 
+/* Gradient of a field loss with respect to the region admittances, by the
+ * adjoint of the discrete system (a derived quantity: the paper solves the
+ * forward problem of Eq. SystemI only).  L = sum_m |p(x_m)|^2 with p the
+ * total pressure of Eq. BIE_I (lambda = 1, as bem_evaluate) at the n_pts
+ * points pts (host double [n_pts][3]); the parameters are the admittances
+ * Y_r of the regions (admittance: host double [n_regions][2], as for
+ * bem_solve), entering column j of an ADMI element as c^q_j = -tau ik rho c
+ * Y_r.  Steps: the forward solve (as bem_solve: p_dev, q_dev receive p and
+ * q, device cf32 [n_tris], caller order; info its statistics), the field
+ * f at the points, one adjoint GMRES solve A^T lambda = F^T conj(f) (F the
+ * map from the unknowns to the field), and per element of region r the term
+ * d u_j (-tau (G_f^T conj f)_j - (A_q^T lambda)_j), d = -tau ik rho c, A_q
+ * the operator on q-unknowns.  Writes *loss = L and grad (host double
+ * [n_regions][2]) = dL/dRe Y_r + i dL/dIm Y_r.
+ * Needs mode BEM_MODE_DIRECT (the transposed product recomputes every pair
+ * by quadrature; the transposed far-field product is not built): other
+ * modes return BEM_E_ARG.  Returns BEM_OK, BEM_W_NOT_CONVERGED (either
+ * solve; outputs filled from the last iterates) or an error. */
+int bem_admittance_gradient(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
+                            int32_t n_regions, const bem_source *srcs, int32_t n_src, const double *pts,
+                            int64_t n_pts, double tol, int32_t max_iter, void *p_dev, void *q_dev, double *loss,
+                            double *grad, bem_solve_info *info, void *stream);
+
 /* Plan statistics for a frequency (builds the plan if needed). */
 int bem_mesh_stats(void *mesh, double freq_hz, const bem_medium *medium, bem_plan_stats *out);
 

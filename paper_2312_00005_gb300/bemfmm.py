@@ -110,6 +110,9 @@ def lib():
                                                d, i32, P, P, P, i64, P, ctypes.POINTER(SolveInfo), P]),
             "bem_evaluate_velocity": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), ctypes.POINTER(Source), i32, P,
                                                      P, P, i64, P, P]),
+            "bem_admittance_gradient": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), P, i32, ctypes.POINTER(Source),
+                                                       i32, P, i64, d, i32, P, P, ctypes.POINTER(d), P,
+                                                       ctypes.POINTER(SolveInfo), P]),
             "bem_mesh_stats": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), ctypes.POINTER(PlanStats)]),
             "bem_plan_stats_host": (ctypes.c_int, [P, i64, P, i64, ctypes.POINTER(Params), d, d,
                                                    ctypes.POINTER(PlanStats)]),
@@ -408,6 +411,39 @@ class Mesh:
                                            _dptr(p, self.n), _dptr(q, self.n), pts.ctypes.data_as(ctypes.c_void_p),
                                            m, _dptr(out, 3 * m), _stream_ptr(stream)))
         return out
+
+    def admittance_gradient(self, freq, sources, admittance, points, tol=1e-7, max_iter=1000, c=343.0, rho=1.21,
+                            p=None, q=None, stream=None):
+        """Loss L = sum_m |p(x_m)|^2 of the total pressure at the points and
+        its gradient dL/dRe Y_r + i dL/dIm Y_r with respect to the region
+        admittances, by the adjoint of Eq. SystemI (direct mode only).
+        Returns (L, grad complex128 [n_regions], p, q, info), p and q the
+        forward solution (complex64 CUDA tensors, caller order)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if p is None:
+            p = torch.empty(self.n, dtype=torch.complex64, device=dev)
+        if q is None:
+            q = torch.empty(self.n, dtype=torch.complex64, device=dev)
+        adm, nreg = _admittance(admittance)
+        if adm is None:
+            raise ValueError("admittance per region is required")
+        pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 3))
+        srcs = (Source * max(1, len(sources)))(*sources)
+        med = self._medium(c, rho)
+        info = SolveInfo()
+        loss = ctypes.c_double(0.0)
+        grad = np.zeros(2 * nreg, dtype=np.float64)
+        code = lib().bem_admittance_gradient(self._h, float(freq), ctypes.byref(med),
+                                             adm.ctypes.data_as(ctypes.c_void_p), nreg, srcs, len(sources),
+                                             pts.ctypes.data_as(ctypes.c_void_p), pts.shape[0], float(tol),
+                                             int(max_iter), _dptr(p, self.n), _dptr(q, self.n), ctypes.byref(loss),
+                                             grad.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info),
+                                             _stream_ptr(stream))
+        _check(code)
+        d = {"iterations": info.iterations, "restarts": info.restarts, "relres": info.relres,
+             "status": code, "converged": code != W_NOT_CONVERGED}
+        return loss.value, grad[0::2] + 1j * grad[1::2], p, q, d
 
     def release_plan(self):
         """Free the per-frequency plan; the next call rebuilds it."""

@@ -299,6 +299,11 @@ struct bem_mesh_impl {
     DevArr<int> type;
     DevArr<float2> xint, ynear, tmp, tmp2, bvec, uvec;
     DevArr<float2> dinv;         // row scaling 1 / A_ii (internal order) when row_scaling is on
+    // admittance gradient: forward u, field at the points, G_f^T conj(f),
+    // coefficients of the q-operator, region per element, accumulators
+    DevArr<float2> uadj, fadj, gadj, adj_cp, adj_cq;
+    DevArr<int> adjreg;
+    DevArr<double> adjacc;
     DevArr<float4> wts;          // far-field weights (alpha, c) per element
     // GMRES workspace
     DevArr<float2> V, w;
@@ -1507,6 +1512,296 @@ int bem_matvec_host(void *mesh, double freq_hz, const bem_medium *medium, const 
 
 namespace {
 
+struct GmresResult {
+    int total_iters = 0, restarts = 0;
+    bool converged = false;
+    GmresState h;
+};
+
+// Restarted GMRES on A u = b, or on A^T u = b when transposed (direct mode
+// only: the transposed product recomputes every pair by quadrature), with b
+// in M.bvec and u in M.uvec (internal order), for the current frame's plan
+// and column coefficients.  Row-scaled when row_scaling is on (the forward
+// system only; the caller has scaled b).  Throws Fail.
+GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool transposed)
+{
+    cudaStream_t s = M.s;
+    const int64_t n = M.n;
+    const int m = M.prm.restart;
+    const bool rscale = M.prm.row_scaling != 0 && !transposed;
+    GmresResult R;
+    // y = A^T x_int (x_int formed by k_prep or k_gm_ortho); zero (may be
+    // null) is cleared, for the part of the product k_gm_ortho adds to y
+    auto product_t = [&](float2 *y, float2 *zero, const int *skip) {
+        NearArgs na = near_args(M, *fr(M).plan, fr(M).cp.p, fr(M).cq.p);
+        {
+            KTimer kt_("k_direct_product_t", s);
+            k_direct_product_t<<<nblocks(n, 8), 256, 0, s>>>(na, M.xint.p, y, zero, fr(M).err.p, skip);
+        }
+        ck_launch("k_direct_product_t");
+    };
+    // GMRES workspace
+    M.V.alloc((size_t)(m + 1) * n);
+    M.w.alloc(n);
+    M.H.alloc((size_t)(m + 1) * m);
+    M.cs.alloc(m);
+    M.sn.alloc(m);
+    M.g_.alloc(m + 1);
+    M.hcol.alloc(m + 1);
+    M.yv.alloc(m + 1);
+    // the fused Gram-Schmidt step: one cooperative launch, block b owns
+    // rows [b R, b R + R) with R <= kOrthoMaxRows; all blocks co-resident
+    int nblk = 0;
+    {
+        int per_sm = 0, nsm = 0;
+        ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gm_ortho, kOrthoThreads, 0), "occupancy");
+        ck(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, M.device), "attribute");
+        const int64_t cap = std::min<int64_t>((int64_t)per_sm * nsm, kOrthoMaxBlocks);
+        const int64_t want = std::max<int64_t>(1, (n + 63) / 64);
+        nblk = (int)std::min(cap, want);
+        if ((n + nblk - 1) / nblk > kOrthoMaxRows)
+            throw Fail{set_err(BEM_E_ARG, "GMRES: " + std::to_string(n) + " unknowns exceed the fused "
+                                              "Gram-Schmidt step's limit of " +
+                                              std::to_string(cap * kOrthoMaxRows))};
+    }
+    const int orows = (int)((n + nblk - 1) / nblk);
+    M.part.alloc((size_t)(m + 1) * nblk);
+    const int nnorm = (int)nblocks(n, 256);
+    M.normpart.alloc(std::max(nnorm, nblk));
+    M.st.alloc(1);
+    M.gbar.alloc(2);
+    ck(cudaMemsetAsync(M.gbar.p, 0, 2 * sizeof(unsigned int), s), "memset barrier");
+    GmresState hs;
+    memset(&hs, 0, sizeof hs);
+    hs.tol = tol;
+    hs.maxit = max_iter;
+    ck(cudaMemcpyAsync(M.st.p, &hs, sizeof hs, cudaMemcpyHostToDevice, s), "H2D st");
+    ck(cudaMemsetAsync(M.uvec.p, 0, n * sizeof(float2), s), "memset x");
+    ck(cudaMemsetAsync(M.H.p, 0, M.H.bytes(), s), "memset H");
+    // the product inputs of v_0 (later basis vectors get theirs from
+    // k_gm_ortho)
+    auto prep_v0 = [&]() {
+        PrepArgs pa = prep_args(M, fr(M).cp.p, fr(M).cq.p, M.V.p);
+        {
+            KTimer kt_("k_prep", s);
+            k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, nullptr);
+        }
+        ck_launch("k_prep");
+    };
+    // start: r0 = b
+    {
+        KTimer kt_("k_norm_part", s);
+        k_norm_part<<<nnorm, 256, 0, s>>>(M.bvec.p, n, M.normpart.p);
+    }
+    ck_launch("k_norm_part");
+    {
+        KTimer kt_("k_gm_start", s);
+        k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.bvec.p, n, M.normpart.p, nnorm, M.g_.p, m, 1);
+    }
+    ck_launch("k_gm_start");
+    prep_v0();
+    // one Arnoldi step, captured once as a graph and replayed
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const int *done = &M.st.p->skip_prod;   // uniform within every product launch
+    OrthoArgs oa;
+    GmresArgs &ga = oa.g;
+    ga.V = M.V.p;
+    ga.w = M.w.p;
+    ga.n = n;
+    ga.st = M.st.p;
+    ga.part = M.part.p;
+    ga.nblk = nblk;
+    ga.H = M.H.p;
+    ga.hcol = M.hcol.p;
+    ga.cs = M.cs.p;
+    ga.sn = M.sn.p;
+    ga.g = M.g_.p;
+    ga.normpart = M.normpart.p;
+    ga.m = m;
+    oa.next = prep_args(M, fr(M).cp.p, fr(M).cq.p, nullptr);
+    oa.wnear = M.ynear.p;
+    oa.bar = M.gbar.p;
+    oa.err = &M.st.p->fault;
+    oa.rows = orows;
+    // one Arnoldi step: product of v_j (inputs already formed), then the
+    // fused Gram-Schmidt / Givens step, which also forms v_{j+1}
+    const bool use_graph = !g_timing;
+    // Arnoldi steps per graph (and per status read).  With event timing
+    // on, one step per read and every kernel on one stream, so that each
+    // kernel is timed alone and no timed launch is a skipped one.
+    const int batch = use_graph ? kStepsPerGraph : 1;
+    auto ortho = [&]() {
+        KTimer kt_("k_gm_ortho", s);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(nblk);
+        cfg.blockDim = dim3(kOrthoThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        ck(cudaLaunchKernelEx(&cfg, k_gm_ortho, oa), "k_gm_ortho");
+        g_launches.fetch_add(1);
+    };
+    auto givens = [&](cudaStream_t gs) {
+        {
+            KTimer kt_("k_gm_givens", gs);
+            k_gm_givens<<<1, 32, 0, gs>>>(ga);
+        }
+        ck_launch("k_gm_givens");
+    };
+    // the product of the current basis vector (its inputs already formed),
+    // row-scaled when row scaling is on (both parts that k_gm_ortho adds)
+    auto product = [&]() {
+        if (transposed) {
+            product_t(M.w.p, M.ynear.p, done);
+            return;
+        }
+        matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, nullptr, nullptr, false, M.w.p, false, done, s, true, true);
+        if (rscale) {
+            {
+                KTimer kt_("k_row_scale", s);
+                k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.ynear.p, M.dinv.p, n, done);
+            }
+            ck_launch("k_row_scale");
+        }
+    };
+    // nsteps Arnoldi steps, each the fused Gram-Schmidt step of column j
+    // (which also forms v_{j+1}'s product inputs), the Givens step and
+    // the product of v_{j+1}; a cycle's first product runs before its
+    // first steps.  In the graph the Givens step runs on a side stream
+    // beside the product, which does not need it, and the next
+    // Gram-Schmidt step waits for it; the last Givens step of a graph
+    // ends beside its last product, so it does not delay the next graph.
+    auto arnoldi_steps = [&](int nsteps) {
+        const bool side = use_graph;
+        for (int t = 0; t < nsteps; ++t) {
+            if (side && t > 0) ck(cudaStreamWaitEvent(s, M.ev_giv[t - 1], 0), "wait givens");
+            ortho();
+            if (side) {
+                ck(cudaEventRecord(M.ev_orth[t], s), "record ortho");
+                ck(cudaStreamWaitEvent(M.s_giv, M.ev_orth[t], 0), "wait ortho");
+                givens(M.s_giv);
+                ck(cudaEventRecord(M.ev_giv[t], M.s_giv), "record givens");
+            } else {
+                givens(s);
+            }
+            product();
+        }
+        if (side) ck(cudaStreamWaitEvent(s, M.ev_giv[nsteps - 1], 0), "join givens");
+    };
+    uint64_t per_graph = 0;
+    if (use_graph) {
+        const uint64_t before = g_launches.load();
+        ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
+        arnoldi_steps(batch);
+        ck(cudaStreamEndCapture(s, &graph), "end capture");
+        per_graph = g_launches.load() - before;
+        g_launches.fetch_sub(per_graph);   // captured, not launched
+        ck(cudaGraphInstantiate(&gexec, graph, 0), "instantiate");
+    }
+    int &restarts = R.restarts, &total_iters = R.total_iters;
+    bool &converged = R.converged;
+    GmresState &h = R.h;
+    for (;;) {
+        // Arnoldi cycle.  With graphs, graph g + 1 is queued before the
+        // host waits for the status copied after graph g, so the GPU
+        // does not idle while the host reads it; a graph queued after
+        // the cycle ended runs its steps as skips.
+        const int max_graphs = (m + batch + batch - 1) / batch;
+        int launched = 0, checked = 0;
+        product();
+        auto launch_graph = [&]() {
+            if (use_graph) {
+                ck(cudaGraphLaunch(gexec, s), "graph launch");
+                g_launches.fetch_add(per_graph);
+            } else {
+                arnoldi_steps(1);
+            }
+            GmresState *dst = M.h_st + (launched & 1);
+            ck(cudaMemcpyAsync(dst, M.st.p, sizeof *dst, cudaMemcpyDeviceToHost, s), "D2H st");
+            ck(cudaEventRecord(M.ev_st[launched & 1], s), "record st");
+            ++launched;
+        };
+        launch_graph();
+        for (;;) {
+            if (use_graph && launched < max_graphs) launch_graph();
+            ck(cudaEventSynchronize(M.ev_st[checked & 1]), "sync st");
+            h = M.h_st[checked & 1];
+            ++checked;
+            if (h.fault) {
+                ck(cudaStreamSynchronize(s), "sync");
+                if (gexec) cudaGraphExecDestroy(gexec);
+                if (graph) cudaGraphDestroy(graph);
+                throw Fail{set_err(BEM_E_TIMEOUT, "GMRES: a grid barrier wait of the fused Gram-Schmidt "
+                                                  "step gave up")};
+            }
+            if (h.done) break;
+            if (checked == launched) {
+                if (launched >= max_graphs) break;
+                launch_graph();
+            }
+        }
+        {
+            KTimer kt_("k_gm_backsolve", s);
+            const int tri_cols = std::min(m, 100);
+            k_gm_backsolve<<<1, 256, (size_t)tri_cols * tri_cols * sizeof(double2), s>>>(M.st.p, M.H.p, M.g_.p,
+                                                                                       M.yv.p, m, tri_cols);
+        }
+        ck_launch("k_gm_backsolve");
+        {
+            KTimer kt_("k_gm_xupdate", s);
+            k_gm_xupdate<<<nblocks(n, 256), 256, 0, s>>>(M.uvec.p, M.V.p, n, M.st.p, M.yv.p);
+        }
+        ck_launch("k_gm_xupdate");
+        total_iters = h.iters;
+        if (h.converged || h.iters >= max_iter) { converged = h.converged; break; }
+        // restart: r = b - A x
+        ++restarts;
+        if (transposed) {
+            PrepArgs pa = prep_args(M, fr(M).cp.p, fr(M).cq.p, M.uvec.p);
+            {
+                KTimer kt_("k_prep", s);
+                k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, nullptr);
+            }
+            ck_launch("k_prep");
+            product_t(M.w.p, nullptr, nullptr);
+        } else {
+            matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, M.uvec.p, nullptr, false, M.w.p, false, nullptr, s);
+        }
+        if (rscale) {
+            {
+                KTimer kt_("k_row_scale", s);
+                k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, nullptr, M.dinv.p, n, nullptr);
+            }
+            ck_launch("k_row_scale");
+        }
+        k_rsub<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.bvec.p, n);   // w = b - A x (row-scaled: D^-1 (b - A x))
+        ck_launch("k_rsub");
+        {
+            KTimer kt_("k_norm_part", s);
+            k_norm_part<<<nnorm, 256, 0, s>>>(M.w.p, n, M.normpart.p);
+        }
+        ck_launch("k_norm_part");
+        {
+            KTimer kt_("k_gm_start", s);
+            k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.w.p, n, M.normpart.p, nnorm, M.g_.p, m, 0);
+        }
+        ck_launch("k_gm_start");
+        prep_v0();
+        ck(cudaMemsetAsync(M.H.p, 0, M.H.bytes(), s), "memset H");
+        ck(cudaMemcpyAsync(&h, M.st.p, sizeof h, cudaMemcpyDeviceToHost, s), "D2H st");
+        ck(cudaStreamSynchronize(s), "sync");
+        if (h.done) { converged = true; total_iters = h.iters; break; }
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    return R;
+}
+
 // Solve with the current frame's plan (prepared for freq_hz): right-hand
 // side, GMRES, p and q in the caller's order.  Throws Fail.
 int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, const bem_source *srcs, int32_t n_src,
@@ -1561,251 +1856,10 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
         }
         ck(cudaStreamSynchronize(s), "sync");
         auto t_rhs = std::chrono::steady_clock::now();
-        // GMRES workspace
-        M.V.alloc((size_t)(m + 1) * n);
-        M.w.alloc(n);
-        M.H.alloc((size_t)(m + 1) * m);
-        M.cs.alloc(m);
-        M.sn.alloc(m);
-        M.g_.alloc(m + 1);
-        M.hcol.alloc(m + 1);
-        M.yv.alloc(m + 1);
-        // the fused Gram-Schmidt step: one cooperative launch, block b owns
-        // rows [b R, b R + R) with R <= kOrthoMaxRows; all blocks co-resident
-        int nblk = 0;
-        {
-            int per_sm = 0, nsm = 0;
-            ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gm_ortho, kOrthoThreads, 0), "occupancy");
-            ck(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, M.device), "attribute");
-            const int64_t cap = std::min<int64_t>((int64_t)per_sm * nsm, kOrthoMaxBlocks);
-            const int64_t want = std::max<int64_t>(1, (n + 63) / 64);
-            nblk = (int)std::min(cap, want);
-            if ((n + nblk - 1) / nblk > kOrthoMaxRows)
-                throw Fail{set_err(BEM_E_ARG, "GMRES: " + std::to_string(n) + " unknowns exceed the fused "
-                                                  "Gram-Schmidt step's limit of " +
-                                                  std::to_string(cap * kOrthoMaxRows))};
-        }
-        const int orows = (int)((n + nblk - 1) / nblk);
-        M.part.alloc((size_t)(m + 1) * nblk);
-        const int nnorm = (int)nblocks(n, 256);
-        M.normpart.alloc(std::max(nnorm, nblk));
-        M.st.alloc(1);
-        M.gbar.alloc(2);
-        ck(cudaMemsetAsync(M.gbar.p, 0, 2 * sizeof(unsigned int), s), "memset barrier");
-        GmresState hs;
-        memset(&hs, 0, sizeof hs);
-        hs.tol = tol;
-        hs.maxit = max_iter;
-        ck(cudaMemcpyAsync(M.st.p, &hs, sizeof hs, cudaMemcpyHostToDevice, s), "H2D st");
-        ck(cudaMemsetAsync(M.uvec.p, 0, n * sizeof(float2), s), "memset x");
-        ck(cudaMemsetAsync(M.H.p, 0, M.H.bytes(), s), "memset H");
-        // the product inputs of v_0 (later basis vectors get theirs from
-        // k_gm_ortho)
-        auto prep_v0 = [&]() {
-            PrepArgs pa = prep_args(M, fr(M).cp.p, fr(M).cq.p, M.V.p);
-            {
-                KTimer kt_("k_prep", s);
-                k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, nullptr);
-            }
-            ck_launch("k_prep");
-        };
-        // start: r0 = b
-        {
-            KTimer kt_("k_norm_part", s);
-            k_norm_part<<<nnorm, 256, 0, s>>>(M.bvec.p, n, M.normpart.p);
-        }
-        ck_launch("k_norm_part");
-        {
-            KTimer kt_("k_gm_start", s);
-            k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.bvec.p, n, M.normpart.p, nnorm, M.g_.p, m, 1);
-        }
-        ck_launch("k_gm_start");
-        prep_v0();
-        // one Arnoldi step, captured once as a graph and replayed
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t gexec = nullptr;
-        const int *done = &M.st.p->skip_prod;   // uniform within every product launch
-        OrthoArgs oa;
-        GmresArgs &ga = oa.g;
-        ga.V = M.V.p;
-        ga.w = M.w.p;
-        ga.n = n;
-        ga.st = M.st.p;
-        ga.part = M.part.p;
-        ga.nblk = nblk;
-        ga.H = M.H.p;
-        ga.hcol = M.hcol.p;
-        ga.cs = M.cs.p;
-        ga.sn = M.sn.p;
-        ga.g = M.g_.p;
-        ga.normpart = M.normpart.p;
-        ga.m = m;
-        oa.next = prep_args(M, fr(M).cp.p, fr(M).cq.p, nullptr);
-        oa.wnear = M.ynear.p;
-        oa.bar = M.gbar.p;
-        oa.err = &M.st.p->fault;
-        oa.rows = orows;
-        // one Arnoldi step: product of v_j (inputs already formed), then the
-        // fused Gram-Schmidt / Givens step, which also forms v_{j+1}
-        const bool use_graph = !g_timing;
-        // Arnoldi steps per graph (and per status read).  With event timing
-        // on, one step per read and every kernel on one stream, so that each
-        // kernel is timed alone and no timed launch is a skipped one.
-        const int batch = use_graph ? kStepsPerGraph : 1;
-        auto ortho = [&]() {
-            KTimer kt_("k_gm_ortho", s);
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(nblk);
-            cfg.blockDim = dim3(kOrthoThreads);
-            cfg.dynamicSmemBytes = 0;
-            cfg.stream = s;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeCooperative;
-            attr[0].val.cooperative = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            ck(cudaLaunchKernelEx(&cfg, k_gm_ortho, oa), "k_gm_ortho");
-            g_launches.fetch_add(1);
-        };
-        auto givens = [&](cudaStream_t gs) {
-            {
-                KTimer kt_("k_gm_givens", gs);
-                k_gm_givens<<<1, 32, 0, gs>>>(ga);
-            }
-            ck_launch("k_gm_givens");
-        };
-        // the product of the current basis vector (its inputs already formed),
-        // row-scaled when row scaling is on (both parts that k_gm_ortho adds)
-        auto product = [&]() {
-            matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, nullptr, nullptr, false, M.w.p, false, done, s, true, true);
-            if (rscale) {
-                {
-                    KTimer kt_("k_row_scale", s);
-                    k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.ynear.p, M.dinv.p, n, done);
-                }
-                ck_launch("k_row_scale");
-            }
-        };
-        // nsteps Arnoldi steps, each the fused Gram-Schmidt step of column j
-        // (which also forms v_{j+1}'s product inputs), the Givens step and
-        // the product of v_{j+1}; a cycle's first product runs before its
-        // first steps.  In the graph the Givens step runs on a side stream
-        // beside the product, which does not need it, and the next
-        // Gram-Schmidt step waits for it; the last Givens step of a graph
-        // ends beside its last product, so it does not delay the next graph.
-        auto arnoldi_steps = [&](int nsteps) {
-            const bool side = use_graph;
-            for (int t = 0; t < nsteps; ++t) {
-                if (side && t > 0) ck(cudaStreamWaitEvent(s, M.ev_giv[t - 1], 0), "wait givens");
-                ortho();
-                if (side) {
-                    ck(cudaEventRecord(M.ev_orth[t], s), "record ortho");
-                    ck(cudaStreamWaitEvent(M.s_giv, M.ev_orth[t], 0), "wait ortho");
-                    givens(M.s_giv);
-                    ck(cudaEventRecord(M.ev_giv[t], M.s_giv), "record givens");
-                } else {
-                    givens(s);
-                }
-                product();
-            }
-            if (side) ck(cudaStreamWaitEvent(s, M.ev_giv[nsteps - 1], 0), "join givens");
-        };
-        uint64_t per_graph = 0;
-        if (use_graph) {
-            const uint64_t before = g_launches.load();
-            ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
-            arnoldi_steps(batch);
-            ck(cudaStreamEndCapture(s, &graph), "end capture");
-            per_graph = g_launches.load() - before;
-            g_launches.fetch_sub(per_graph);   // captured, not launched
-            ck(cudaGraphInstantiate(&gexec, graph, 0), "instantiate");
-        }
-        int restarts = 0, total_iters = 0;
-        bool converged = false;
-        GmresState h;
-        for (;;) {
-            // Arnoldi cycle.  With graphs, graph g + 1 is queued before the
-            // host waits for the status copied after graph g, so the GPU
-            // does not idle while the host reads it; a graph queued after
-            // the cycle ended runs its steps as skips.
-            const int max_graphs = (m + batch + batch - 1) / batch;
-            int launched = 0, checked = 0;
-            product();
-            auto launch_graph = [&]() {
-                if (use_graph) {
-                    ck(cudaGraphLaunch(gexec, s), "graph launch");
-                    g_launches.fetch_add(per_graph);
-                } else {
-                    arnoldi_steps(1);
-                }
-                GmresState *dst = M.h_st + (launched & 1);
-                ck(cudaMemcpyAsync(dst, M.st.p, sizeof *dst, cudaMemcpyDeviceToHost, s), "D2H st");
-                ck(cudaEventRecord(M.ev_st[launched & 1], s), "record st");
-                ++launched;
-            };
-            launch_graph();
-            for (;;) {
-                if (use_graph && launched < max_graphs) launch_graph();
-                ck(cudaEventSynchronize(M.ev_st[checked & 1]), "sync st");
-                h = M.h_st[checked & 1];
-                ++checked;
-                if (h.fault) {
-                    ck(cudaStreamSynchronize(s), "sync");
-                    if (gexec) cudaGraphExecDestroy(gexec);
-                    if (graph) cudaGraphDestroy(graph);
-                    throw Fail{set_err(BEM_E_TIMEOUT, "GMRES: a grid barrier wait of the fused Gram-Schmidt "
-                                                      "step gave up")};
-                }
-                if (h.done) break;
-                if (checked == launched) {
-                    if (launched >= max_graphs) break;
-                    launch_graph();
-                }
-            }
-            {
-                KTimer kt_("k_gm_backsolve", s);
-                const int tri_cols = std::min(m, 100);
-                k_gm_backsolve<<<1, 256, (size_t)tri_cols * tri_cols * sizeof(double2), s>>>(M.st.p, M.H.p, M.g_.p,
-                                                                                           M.yv.p, m, tri_cols);
-            }
-            ck_launch("k_gm_backsolve");
-            {
-                KTimer kt_("k_gm_xupdate", s);
-                k_gm_xupdate<<<nblocks(n, 256), 256, 0, s>>>(M.uvec.p, M.V.p, n, M.st.p, M.yv.p);
-            }
-            ck_launch("k_gm_xupdate");
-            total_iters = h.iters;
-            if (h.converged || h.iters >= max_iter) { converged = h.converged; break; }
-            // restart: r = b - A x
-            ++restarts;
-            matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, M.uvec.p, nullptr, false, M.w.p, false, nullptr, s);
-            if (rscale) {
-                {
-                    KTimer kt_("k_row_scale", s);
-                    k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, nullptr, M.dinv.p, n, nullptr);
-                }
-                ck_launch("k_row_scale");
-            }
-            k_rsub<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.bvec.p, n);   // w = b - A x (row-scaled: D^-1 (b - A x))
-            ck_launch("k_rsub");
-            {
-                KTimer kt_("k_norm_part", s);
-                k_norm_part<<<nnorm, 256, 0, s>>>(M.w.p, n, M.normpart.p);
-            }
-            ck_launch("k_norm_part");
-            {
-                KTimer kt_("k_gm_start", s);
-                k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.w.p, n, M.normpart.p, nnorm, M.g_.p, m, 0);
-            }
-            ck_launch("k_gm_start");
-            prep_v0();
-            ck(cudaMemsetAsync(M.H.p, 0, M.H.bytes(), s), "memset H");
-            ck(cudaMemcpyAsync(&h, M.st.p, sizeof h, cudaMemcpyDeviceToHost, s), "D2H st");
-            ck(cudaStreamSynchronize(s), "sync");
-            if (h.done) { converged = true; total_iters = h.iters; break; }
-        }
-        if (gexec) cudaGraphExecDestroy(gexec);
-        if (graph) cudaGraphDestroy(graph);
+        GmresResult R = run_gmres(M, tol, max_iter, false);
+        const int total_iters = R.total_iters, restarts = R.restarts;
+        const bool converged = R.converged;
+        const GmresState &h = R.h;
         auto t_gmres = std::chrono::steady_clock::now();
         // p and q in the caller's order
         {
@@ -2124,6 +2178,113 @@ int bem_evaluate_velocity(void *mesh, double freq_hz, const bem_medium *medium, 
         resolve_timing();
         return BEM_OK;
     } catch (Fail &f) {
+        return f.code;
+    }
+}
+
+int bem_admittance_gradient(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
+                            int32_t n_regions, const bem_source *srcs, int32_t n_src, const double *pts,
+                            int64_t n_pts, double tol, int32_t max_iter, void *p_dev, void *q_dev, double *loss,
+                            double *grad, bem_solve_info *info, void *stream)
+{
+    if (!mesh || !admittance || n_regions < 1 || n_src < 0 || (n_src > 0 && !srcs) || !pts || n_pts < 1 ||
+        !(tol > 0) || max_iter < 1 || !p_dev || !q_dev || !loss || !grad)
+        return set_err(BEM_E_ARG, "bad argument");
+    auto &M = *(bem_mesh_impl *)mesh;
+    if (M.prm.mode != BEM_MODE_DIRECT)
+        return set_err(BEM_E_ARG, "the admittance gradient needs mode BEM_MODE_DIRECT (the transposed "
+                                  "far-field product is not built)");
+    // forward problem: u, p, q (Eq. SystemI) and the field at the points
+    const int fwd = bem_solve(mesh, freq_hz, medium, admittance, n_regions, srcs, n_src, tol, max_iter, p_dev,
+                              q_dev, info, stream);
+    if (fwd < 0) return fwd;
+    const std::string fwd_msg = g_err;
+    try {
+        double c, rho;
+        medium_of(medium, c, rho);
+        cudaStream_t us = (cudaStream_t)stream;
+        cudaStream_t s = M.s;
+        const int64_t n = M.n;
+        const double k = wavenumber(freq_hz, c);
+        const float tau = M.prm.tau < 0 ? -1.f : 1.f;
+        M.uadj.alloc(n);
+        M.fadj.alloc(n_pts);
+        M.gadj.alloc(n);
+        join_streams(us, s);
+        ck(cudaMemcpyAsync(M.uadj.p, M.uvec.p, n * sizeof(float2), cudaMemcpyDeviceToDevice, s), "D2D u");
+        join_streams(s, us);
+        const int ev = bem_evaluate(mesh, freq_hz, medium, srcs, n_src, p_dev, q_dev, pts, n_pts, M.fadj.p, stream);
+        if (ev < 0) return ev;
+        join_streams(us, s);
+        reset_err(M);
+        // adjoint right-hand side F^T conj(f) into b, and G_f^T conj(f)
+        std::vector<double> hp(pts, pts + 3 * n_pts);
+        M.ptsbuf.upload(hp, s);
+        M.bvec.alloc(n);
+        {
+            KTimer kt_("k_field_t", s);
+            k_field_t<<<nblocks(n, 8), 256, 0, s>>>(M.elem(), M.Q.p, M.ptsbuf.p, n_pts, (float)k, M.fadj.p,
+                                                     fr(M).cp.p, fr(M).cq.p, M.gadj.p, M.bvec.p, fr(M).err.p);
+        }
+        ck_launch("k_field_t");
+        // adjoint solve A^T lambda = F^T conj(f) (lambda in uvec)
+        GmresResult R = run_gmres(M, tol, max_iter, true);
+        // aq = A_q^T lambda: the transposed product with c^p = 0 and c^q = 1
+        // (tau folded in as for the unknowns' coefficients)
+        std::vector<float2> h0((size_t)n, make_float2(0.f, 0.f)), hq((size_t)n, make_float2(tau, 0.f));
+        M.adj_cp.upload(h0, s);
+        M.adj_cq.upload(hq, s);
+        PrepArgs pa = prep_args(M, M.adj_cp.p, M.adj_cq.p, M.uvec.p);
+        {
+            KTimer kt_("k_prep", s);
+            k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, nullptr);
+        }
+        ck_launch("k_prep");
+        NearArgs na = near_args(M, *fr(M).plan, M.adj_cp.p, M.adj_cq.p);
+        {
+            KTimer kt_("k_direct_product_t", s);
+            k_direct_product_t<<<nblocks(n, 8), 256, 0, s>>>(na, M.xint.p, M.w.p, nullptr, fr(M).err.p, nullptr);
+        }
+        ck_launch("k_direct_product_t");
+        // per-region sums and the loss
+        std::vector<int> reg((size_t)n);
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t e = M.t.perm[i];
+            reg[i] = M.bct[e] == BEM_ADMI ? M.region[e] : -1;
+        }
+        M.adjreg.upload(reg, s);
+        const int nacc = 2 * n_regions + 1;
+        M.adjacc.alloc(nacc);
+        ck(cudaMemsetAsync(M.adjacc.p, 0, nacc * sizeof(double), s), "memset acc");
+        {
+            KTimer kt_("k_adjoint_reduce", s);
+            k_adjoint_reduce<<<nblocks(std::max<int64_t>(n, n_pts), 256), 256, 0, s>>>(
+                M.uadj.p, M.gadj.p, M.w.p, M.adjreg.p, n, tau, 0.0, -(double)tau * k * rho * c, M.fadj.p, n_pts,
+                n_regions, M.adjacc.p);
+        }
+        ck_launch("k_adjoint_reduce");
+        std::vector<double> hacc(nacc);
+        ck(cudaMemcpyAsync(hacc.data(), M.adjacc.p, nacc * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H acc");
+        check_err(M);
+        join_streams(s, us);
+        ck(cudaStreamSynchronize(s), "sync");
+        resolve_timing();
+        *loss = hacc[2 * n_regions];
+        for (int r = 0; r < 2 * n_regions; ++r) grad[r] = hacc[r];
+        if (fwd != BEM_OK) {
+            g_err = fwd_msg;
+            return fwd;
+        }
+        if (!R.converged) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "adjoint GMRES: relative residual %.3g after %d products (tol %.3g)",
+                     R.h.resid, R.total_iters, tol);
+            g_err = buf;
+            return BEM_W_NOT_CONVERGED;
+        }
+        return BEM_OK;
+    } catch (Fail &f) {
+        abandon_capture(M);
         return f.code;
     }
 }

@@ -458,6 +458,113 @@ __global__ void k_row_scale(float2 *__restrict__ y, float2 *__restrict__ y2, con
     if (y2) y2[i] = cmul(y2[i], d);
 }
 
+// ------------------------------------------------------------------ adjoint
+// Transposed product of the direct operator (every pair by quadrature,
+// Eq. SystemI): y_j = sum_i A_ij x_i with A_ij the entry bm_entry gives for
+// row i and column j (the same entries as the forward product, so this is
+// its exact transpose).  One warp per column j, lanes over the rows.  zero
+// (may be null): also cleared at j (the second part of a product that the
+// Gram-Schmidt step adds).
+__global__ void k_direct_product_t(NearArgs a, const float2 *__restrict__ x, float2 *__restrict__ y,
+                                   float2 *__restrict__ zero, int *__restrict__ err, const int *skip)
+{
+    if (skip_now(skip)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= a.E.n) return;
+    const QuadTables &Q = *a.Q;
+    const float2 cp = a.cp[j], cq = a.cq[j];
+    float2 acc = make_float2(0.f, 0.f);
+    if (cp.x != 0.f || cp.y != 0.f || cq.x != 0.f || cq.y != 0.f) {
+        for (int64_t i = lane; i < a.E.n; i += 32) {
+            const float4 ch = a.E.chi[i], cl = a.E.clo[i];
+            const float3 xhi = f3(ch), xlo = f3(cl), nx = f3(a.E.nrm[i]);
+            const double xd[3] = {a.E.cd[3 * i], a.E.cd[3 * i + 1], a.E.cd[3 * i + 2]};
+            float2 v;
+            if (!bm_entry(a.E, i, j, xhi, xlo, xd, nx, a.k, a.ik_inv, a.tau, Q, cp, cq, v)) {
+                atomicMin(err, (int)j);
+                continue;
+            }
+            acc = cfma(v, x[i], acc);
+        }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        y[j] = acc;
+        if (zero) zero[j] = make_float2(0.f, 0.f);
+    }
+}
+
+// Transposed field operator of the representation formula (Eq. BIE_I with
+// lambda = 1, the element rules of k_field): for each element j,
+//   g_j = sum_m G(x_m)_j conj(f_m),  h_j = sum_m H(x_m)_j conj(f_m),
+// and the adjoint right-hand side r_j = cp_j h_j - cq_j g_j (the column
+// coefficients carry tau, so r = F^T conj(f) with F the map from the
+// unknowns to the field).  One warp per element, lanes over the points.
+__global__ void k_field_t(ElemDev E, const QuadTables *__restrict__ Qp, const double *__restrict__ pts, int64_t M,
+                          float k, const float2 *__restrict__ f, const float2 *__restrict__ cp,
+                          const float2 *__restrict__ cq, float2 *__restrict__ g_out, float2 *__restrict__ r_out,
+                          int *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= E.n) return;
+    const QuadTables &Q = *Qp;
+    float2 ga = make_float2(0.f, 0.f), ha = make_float2(0.f, 0.f);
+    for (int64_t m = lane; m < M; m += 32) {
+        const double xd[3] = {pts[3 * m], pts[3 * m + 1], pts[3 * m + 2]};
+        const float3 xhi = make_float3((float)xd[0], (float)xd[1], (float)xd[2]);
+        const float3 xlo = make_float3((float)(xd[0] - (double)xhi.x), (float)(xd[1] - (double)xhi.y),
+                                       (float)(xd[2] - (double)xhi.z));
+        float2 G = make_float2(0.f, 0.f), H = make_float2(0.f, 0.f);
+        if (!integrate_regular<true>(E, j, xhi, xlo, xd, make_float3(0.f, 0.f, 1.f), k, 1.0f / k, Q, G, H)) {
+            atomicMin(err, (int)j);
+            continue;
+        }
+        const float2 w = make_float2(f[m].x, -f[m].y);
+        ga = cfma(G, w, ga);
+        ha = cfma(H, w, ha);
+    }
+    ga = warp_sum(ga);
+    ha = warp_sum(ha);
+    if (lane == 0) {
+        g_out[j] = ga;
+        r_out[j] = csub(cmul(cp[j], ha), cmul(cq[j], ga));
+    }
+}
+
+// Gradient of L = sum_m |f_m|^2 with respect to the region admittances Y_r,
+// from the forward solution u, the adjoint solution lambda of
+// A^T lambda = F^T conj(f), g = G_f^T conj(f) and aq = A_q^T lambda (A_q the
+// operator on q-unknowns, c^p = 0 and c^q = 1): element j of region r adds
+//   t_j = d u_j (-tau g_j - aq_j),  d = dc^q_j / dY_r = -tau i k rho c,
+// and grad_r = 2 conj(sum_j t_j) = dL/dRe Y_r + i dL/dIm Y_r.  acc
+// (zeroed by the caller): [n_regions][2] gradient, then L.  region: per
+// element (internal order), -1 when the element is not ADMI.
+__global__ void k_adjoint_reduce(const float2 *__restrict__ u, const float2 *__restrict__ g,
+                                 const float2 *__restrict__ aq, const int *__restrict__ region, int64_t n,
+                                 float tau, double dre, double dim, const float2 *__restrict__ f, int64_t M,
+                                 int nreg, double *acc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const int r = region[i];
+        if (r >= 0 && r < nreg) {
+            const double gr = g[i].x, gi = g[i].y, ar = aq[i].x, ai = aq[i].y;
+            const double br = -tau * gr - ar, bi = -tau * gi - ai;      // -tau g_j - aq_j
+            const double ur = u[i].x, ui = u[i].y;
+            const double cr = ur * br - ui * bi, ci = ur * bi + ui * br; // u_j (...)
+            const double tr = dre * cr - dim * ci, ti = dre * ci + dim * cr;
+            atomicAdd(&acc[2 * r], 2.0 * tr);
+            atomicAdd(&acc[2 * r + 1], -2.0 * ti);
+        }
+    }
+    if (i < M) {
+        const double fr_ = f[i].x, fi = f[i].y;
+        atomicAdd(&acc[2 * nreg], fr_ * fr_ + fi * fi);
+    }
+}
+
 // ------------------------------------------------------------------ far field
 // Per product: gather x into the internal order (x_int[i] = x[perm[i]] or
 // x = xbase + jidx * n) and form the aggregation weights of the centroid

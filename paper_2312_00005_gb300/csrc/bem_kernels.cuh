@@ -188,6 +188,12 @@ __global__ void k_field_velocity(ElemDev E, const QuadTables *Q, const double *p
 __global__ void k_field_velocity_finish(const double *pts, int64_t M, int S, float k, float inv_omega_rho,
                                         const SourceDev *src, int nsrc, const float2 *part, float2 *out);
 __global__ void k_gather(const float2 *x, const int64_t *perm, int64_t n, float2 *y);
+__global__ void k_direct_product_t(NearArgs a, const float2 *x, float2 *y, float2 *zero, int *err, const int *skip);
+__global__ void k_field_t(ElemDev E, const QuadTables *Qp, const double *pts, int64_t M, float k, const float2 *f,
+                          const float2 *cp, const float2 *cq, float2 *g_out, float2 *r_out, int *err);
+__global__ void k_adjoint_reduce(const float2 *u, const float2 *g, const float2 *aq, const int *region, int64_t n,
+                                 float tau, double dre, double dim, const float2 *f, int64_t M, int nreg,
+                                 double *acc);
 __global__ void k_row_scale_init(NearArgs a, float2 *dinv, int *err);
 __global__ void k_row_scale(float2 *y, float2 *y2, const float2 *dinv, int64_t n, const int *skip);
 __global__ void k_sub(float2 *b, const float2 *y, int64_t n);

@@ -315,6 +315,73 @@ def test_row_scaling_solve_matches_oracle(bem, mode, level):
     assert _rel(q1, qo) < 2 * tol, _rel(q1, qo)
 
 
+def _octant_regions(cen):
+    return ((cen[:, 0] > 0) + 2 * (cen[:, 1] > 0) + 4 * (cen[:, 2] > 0)).astype(np.int32)
+
+
+def test_admittance_gradient_matches_oracle_exterior(bem):
+    """Adjoint gradient of L = sum |p|^2 at 20 points on a 1 m sphere with
+    respect to eight octant admittances (passive, seeded) on a 320-element
+    sphere, plane wave plus point source, direct mode: loss and gradient
+    against the oracle's adjoint (itself pinned by finite differences)."""
+    nodes, tris = inputs.icosphere(2, 0.1)
+    n = tris.shape[0]
+    f = 1000.0
+    cen, _, _ = oracle.geometry(nodes, tris)
+    region = _octant_regions(cen)
+    rng = np.random.default_rng(2312)
+    Y = rng.uniform(0.0, 0.5, 8) * np.exp(1j * rng.uniform(-np.pi / 2, np.pi / 2, 8)) / (RHO * C)
+    bct = np.full(n, bem.ADMI, np.int32)
+    pts = inputs.fibonacci_sphere(20, 1.0)
+    src_o = [("plane", (0.0, 0.0, 1.0), 1.0), ("point", (0.0, 0.13, 0.02), 0.5 - 0.2j)]
+    src = [bem.plane_wave((0, 0, 1)), bem.point_source((0.0, 0.13, 0.02), 0.5 - 0.2j)]
+    mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region, mode=bem.MODE_DIRECT)
+    L, g, p, q, info = mesh.admittance_gradient(f, src, Y, pts, tol=1e-7, c=C, rho=RHO)
+    mesh.close()
+    assert info["converged"], info
+    Lo, go, io = oracle.admittance_gradient(nodes, tris, f, pts, region, Y, sources=src_o, c=C, rho=RHO)
+    assert abs(L - Lo) < 1e-4 * Lo, (L, Lo)
+    eg = np.max(np.abs(g - go)) / np.max(np.abs(go))
+    assert eg < 1e-3, eg
+    assert _rel(p.cpu().numpy(), io["p"]) < 1e-4
+
+
+def test_admittance_gradient_matches_oracle_interior(bem):
+    """The same for the interior problem (tau = -1) in a short closed duct
+    with a driven end and three admittance regions."""
+    c, rho, f = 340.0, 1.3, 240.0
+    nodes, tris = inputs.duct(0.6, 0.2, 0.1)
+    cen, _, _ = oracle.geometry(nodes, tris)
+    drive = cen[:, 0] < 1e-9
+    far = cen[:, 0] > 0.6 - 1e-9
+    region = np.where(far, 0, np.where(cen[:, 2] < 0, 1, 2)).astype(np.int32)
+    region[drive] = 0
+    bct = np.where(drive, bem.VELO, bem.ADMI).astype(np.int32)
+    bcv = np.where(drive, 1.0, 0.0).astype(np.complex128)
+    Y = np.array([1.0 / (rho * c), 0.2 / (rho * c) * np.exp(0.3j), 0.1 / (rho * c) * np.exp(-0.5j)])
+    xs = np.linspace(0.1, 0.5, 5)
+    pts = np.stack([xs, 0 * xs + 0.01, 0 * xs - 0.02], 1)
+    mesh = bem.Mesh(nodes, tris, bc_type=bct, bc_value=bcv, region=region, mode=bem.MODE_DIRECT, tau=-1.0)
+    L, g, p, q, info = mesh.admittance_gradient(f, [], Y, pts, tol=1e-7, c=c, rho=rho)
+    mesh.close()
+    assert info["converged"], info
+    oreg = np.where(drive, -1, region)
+    Lo, go, io = oracle.admittance_gradient(nodes, tris, f, pts, oreg, Y, bc_type=bct, bc_value=bcv, c=c,
+                                            rho=rho, params={"tau": -1.0})
+    assert abs(L - Lo) < 1e-4 * Lo, (L, Lo)
+    eg = np.max(np.abs(g - go)) / np.max(np.abs(go))
+    assert eg < 1e-3, eg
+
+
+def test_admittance_gradient_needs_direct_mode(bem):
+    nodes, tris = inputs.icosphere(2, 0.1)
+    n = tris.shape[0]
+    mesh = bem.Mesh(nodes, tris, bc_type=np.full(n, bem.ADMI, np.int32))
+    with pytest.raises(bem.BemError):
+        mesh.admittance_gradient(1000.0, [bem.plane_wave((0, 0, 1))], [0.001], inputs.fibonacci_sphere(4, 1.0))
+    mesh.close()
+
+
 def test_subdivision_limit_is_reported(bem):
     nodes, tris = inputs.icosphere(1, 0.1)
     tris = np.vstack([tris, tris[5:6]])
