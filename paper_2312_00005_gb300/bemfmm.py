@@ -15,7 +15,7 @@ import numpy as np
 __all__ = [
     "VELO", "PRES", "ADMI", "MODE_FMM", "MODE_DIRECT", "BemError", "Params", "Medium", "Source",
     "SolveInfo", "PlanStats", "Mesh", "lib", "launch_count", "plane_wave", "point_source", "timing_enable",
-    "timing_get", "plan_stats_host", "default_params",
+    "timing_get", "plan_stats_host", "default_params", "admittance_loss",
 ]
 
 VELO, PRES, ADMI = 0, 1, 2
@@ -454,3 +454,43 @@ class Mesh:
         med = self._medium(c, rho)
         _check(lib().bem_mesh_stats(self._h, float(freq), ctypes.byref(med), ctypes.byref(st)))
         return st.as_dict()
+
+
+def _admittance_loss_fn():
+    import torch
+
+    class AdmittanceLoss(torch.autograd.Function):
+        """L(Y) = sum_m |p(x_m)|^2 as a differentiable function of the region
+        admittances Y (complex tensor [n_regions]); the backward pass returns
+        the adjoint gradient bem_admittance_gradient computed with the
+        forward one (PyTorch's convention for a real function of complex
+        inputs: dL/dRe Y + i dL/dIm Y)."""
+
+        @staticmethod
+        def forward(ctx, Y, mesh, freq, sources, points, tol, c, rho):
+            y = Y.detach().cpu().numpy().astype(np.complex128)
+            L, g, _, _, info = mesh.admittance_gradient(freq, sources, y, points, tol=tol, c=c, rho=rho)
+            if not info["converged"]:
+                raise BemError(W_NOT_CONVERGED, lib().bem_last_error().decode(errors="replace"))
+            ctx.save_for_backward(torch.as_tensor(g, dtype=Y.dtype, device=Y.device))
+            return torch.as_tensor(L, dtype=Y.real.dtype, device=Y.device)
+
+        @staticmethod
+        def backward(ctx, gL):
+            (g,) = ctx.saved_tensors
+            return gL * g, None, None, None, None, None, None, None
+
+    return AdmittanceLoss
+
+
+def admittance_loss(mesh, Y, freq, sources, points, tol=1e-7, c=343.0, rho=1.21):
+    """Differentiable field loss sum_m |p(x_m)|^2 of the region admittances
+    Y (complex torch tensor [n_regions], e.g. with requires_grad); the mesh
+    must be in direct mode (see Mesh.admittance_gradient)."""
+    global _AdmittanceLoss
+    if _AdmittanceLoss is None:
+        _AdmittanceLoss = _admittance_loss_fn()
+    return _AdmittanceLoss.apply(Y, mesh, float(freq), tuple(sources), points, float(tol), float(c), float(rho))
+
+
+_AdmittanceLoss = None

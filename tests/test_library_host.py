@@ -106,3 +106,27 @@ def test_bad_arguments_are_rejected(lib):
     deg[0, 1] = deg[0, 0]
     with pytest.raises(bemfmm.BemError):
         bemfmm.plan_stats_host(nodes, deg, 1000.0)
+
+
+def test_admittance_loss_autograd_convention():
+    """bemfmm.admittance_loss hands the library's gradient (dL/dRe Y +
+    i dL/dIm Y) to torch.autograd: with a stand-in mesh whose loss is
+    sum |Y - Y0|^2 (gradient 2 (Y - Y0) in that convention), Y.grad equals
+    what torch's own autograd gives for the same function, also through a
+    chain rule factor."""
+    torch = pytest.importorskip("torch")
+    Y0 = np.array([0.3 + 0.1j, -0.2 + 0.5j, 0.05 - 0.4j])
+
+    class FakeMesh:
+        def admittance_gradient(self, freq, sources, y, points, tol, c, rho):
+            return float(np.sum(np.abs(y - Y0) ** 2)), 2.0 * (y - Y0), None, None, {"converged": True}
+
+    y = np.array([1.0 - 0.5j, 0.25 + 0.75j, -0.6 + 0.1j])
+    Y = torch.tensor(y, dtype=torch.complex128, requires_grad=True)
+    L = 3.0 * bemfmm.admittance_loss(FakeMesh(), Y, 1000.0, [], np.zeros((1, 3)))
+    L.backward()
+    Y2 = torch.tensor(y, dtype=torch.complex128, requires_grad=True)
+    L2 = 3.0 * ((Y2 - torch.tensor(Y0)).abs() ** 2).sum()
+    L2.backward()
+    assert abs(L.item() - L2.item()) < 1e-12
+    assert torch.allclose(Y.grad, Y2.grad, atol=1e-12)
