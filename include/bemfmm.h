@@ -176,6 +176,18 @@ int bem_mesh_destroy(void *mesh);
 int bem_matvec(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
                int32_t n_regions, const void *x_dev, void *y_dev, int32_t n_rhs, void *stream);
 
+/* y = A^T x (the transpose of bem_matvec's A, one right-hand side), the
+ * product of the adjoint solve in bem_admittance_gradient.  Near part: the
+ * same entries as A, recomputed by quadrature in every call (not the stored
+ * ones).  Far part (FMM mode): the antipodal symmetry of the sphere grid of
+ * Sec. 3.3.3 and D(-X, s) = D(X, -s) in Eq. FMMBase make it the forward
+ * aggregation of x with the source factor 1 - s.n, the forward transfer and
+ * a disaggregation with A's column factor A_j (c^q_j - ik c^p_j s.n_j) as
+ * its row factor.  x_dev, y_dev: device cf32 [n_tris], caller order.
+ * Arguments and errors as bem_matvec. */
+int bem_matvec_transpose(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
+                         int32_t n_regions, const void *x_dev, void *y_dev, void *stream);
+
 /* As bem_matvec with host buffers x_host, y_host (cf32 [n_rhs][n_tris]):
  * copies in, multiplies, copies out, synchronises. */
 int bem_matvec_host(void *mesh, double freq_hz, const bem_medium *medium,
@@ -253,10 +265,9 @@ int bem_evaluate_velocity(void *mesh, double freq_hz, const bem_medium *medium, 
  * d u_j (-tau (G_f^T conj f)_j - (A_q^T lambda)_j), d = -tau ik rho c, A_q
  * the operator on q-unknowns.  Writes *loss = L and grad (host double
  * [n_regions][2]) = dL/dRe Y_r + i dL/dIm Y_r.
- * Needs mode BEM_MODE_DIRECT (the transposed product recomputes every pair
- * by quadrature; the transposed far-field product is not built): other
- * modes return BEM_E_ARG.  Returns BEM_OK, BEM_W_NOT_CONVERGED (either
- * solve; outputs filled from the last iterates) or an error. */
+ * The adjoint solve uses the transposed product of bem_matvec_transpose
+ * (FMM or direct, as the mesh's mode).  Returns BEM_OK, BEM_W_NOT_CONVERGED
+ * (either solve; outputs filled from the last iterates) or an error. */
 int bem_admittance_gradient(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
                             int32_t n_regions, const bem_source *srcs, int32_t n_src, const double *pts,
                             int64_t n_pts, double tol, int32_t max_iter, void *p_dev, void *q_dev, double *loss,

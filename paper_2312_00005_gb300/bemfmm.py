@@ -102,6 +102,7 @@ def lib():
             "bem_mesh_destroy": (ctypes.c_int, [P]),
             "bem_matvec": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), P, i32, P, P, i32, P]),
             "bem_matvec_host": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), P, i32, P, P, i32, P]),
+            "bem_matvec_transpose": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), P, i32, P, P, P]),
             "bem_solve": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), P, i32, ctypes.POINTER(Source), i32, d, i32,
                                          P, P, ctypes.POINTER(SolveInfo), P]),
             "bem_evaluate": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), ctypes.POINTER(Source), i32, P, P, P,
@@ -301,6 +302,19 @@ class Mesh:
         _check(code)
         return y
 
+    def matvec_transpose(self, freq, x, y=None, admittance=None, c=343.0, rho=1.21, stream=None):
+        """y = A^T x (the adjoint solve's product); x: complex64 CUDA tensor
+        [n] in the caller's element order."""
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        adm, nreg = _admittance(admittance)
+        med = self._medium(c, rho)
+        _check(lib().bem_matvec_transpose(self._h, float(freq), ctypes.byref(med),
+                                          None if adm is None else adm.ctypes.data_as(ctypes.c_void_p), nreg,
+                                          _dptr(x, self.n), _dptr(y, self.n), _stream_ptr(stream)))
+        return y
+
     def matvec_host(self, freq, x, admittance=None, c=343.0, rho=1.21):
         """As matvec with host arrays (copies inside the call)."""
         xh = np.ascontiguousarray(np.asarray(x, dtype=np.complex64))
@@ -416,7 +430,7 @@ class Mesh:
                             p=None, q=None, stream=None):
         """Loss L = sum_m |p(x_m)|^2 of the total pressure at the points and
         its gradient dL/dRe Y_r + i dL/dIm Y_r with respect to the region
-        admittances, by the adjoint of Eq. SystemI (direct mode only).
+        admittances, by the adjoint of Eq. SystemI.
         Returns (L, grad complex128 [n_regions], p, q, info), p and q the
         forward solution (complex64 CUDA tensors, caller order)."""
         import torch
@@ -485,8 +499,8 @@ def _admittance_loss_fn():
 
 def admittance_loss(mesh, Y, freq, sources, points, tol=1e-7, c=343.0, rho=1.21):
     """Differentiable field loss sum_m |p(x_m)|^2 of the region admittances
-    Y (complex torch tensor [n_regions], e.g. with requires_grad); the mesh
-    must be in direct mode (see Mesh.admittance_gradient)."""
+    Y (complex torch tensor [n_regions], e.g. with requires_grad); see
+    Mesh.admittance_gradient."""
     global _AdmittanceLoss
     if _AdmittanceLoss is None:
         _AdmittanceLoss = _admittance_loss_fn()

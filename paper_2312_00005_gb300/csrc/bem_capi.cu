@@ -302,6 +302,7 @@ struct bem_mesh_impl {
     // admittance gradient: forward u, field at the points, G_f^T conj(f),
     // coefficients of the q-operator, region per element, accumulators
     DevArr<float2> uadj, fadj, gadj, adj_cp, adj_cq;
+    DevArr<float4> rowf;         // transposed product: row factor (a, b) per element
     DevArr<int> adjreg;
     DevArr<double> adjacc;
     DevArr<float4> wts;          // far-field weights (alpha, c) per element
@@ -1093,6 +1094,7 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     da.perm = perm_out ? M.perm.p : nullptr;
     da.k = (float)P.k;
     da.nlev = (int)P.lev.size();
+    da.rowf = nullptr;
     if (fork && !far_only) {
         ck(cudaEventRecord(M.ev_join, sf), "record join");
         ck(cudaStreamWaitEvent(s, M.ev_join, 0), "wait join");
@@ -1117,6 +1119,82 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
         ck(cudaEventRecord(M.ev_join, sf), "record join");
         ck(cudaStreamWaitEvent(s, M.ev_join, 0), "wait join");
     }
+}
+
+// y = A^T x with the given column coefficients (the adjoint solve): the
+// near part by k_near_fused_t (entries recomputed), the far part by the
+// forward aggregation and transfer kernels on the weights k_prep_t forms
+// and k_disaggregate_t.  x: internal order, or null when x_int already
+// holds x (formed by k_gm_ortho).  y: caller order when perm_out, else
+// internal.  far_only: y receives the far part alone and the near part
+// stays in M.ynear (the Gram-Schmidt step adds them).
+void matvec_t_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, const float2 *x, float2 *y,
+                       bool perm_out, bool far_only, const int *skip, cudaStream_t s)
+{
+    Plan &P = *fr(M).plan;
+    const int64_t n = M.n;
+    const bool far = !P.lev.empty();
+    M.rowf.alloc(n);   // no-op when run_gmres allocated it before a graph capture
+    {
+        KTimer kt_("k_prep_t", s);
+        k_prep_t<<<nblocks(n, 256), 256, 0, s>>>(n, x, M.xint.p, far ? M.wts.p : nullptr, M.rowf.p, M.chi.p, cp, cq,
+                                                 (float)P.k, skip);
+    }
+    ck_launch("k_prep_t");
+    const LevelsArgs &A = P.hargs;
+    const bool fork = !g_timing && (A.ntasks > 0 || A.ntargets > 0);
+    cudaStream_t sf = fork ? M.s_far : s;
+    if (fork) {
+        ck(cudaEventRecord(M.ev_fork, s), "record fork");
+        ck(cudaStreamWaitEvent(sf, M.ev_fork, 0), "wait fork");
+    }
+    if (A.ntasks > 0) {
+        {
+            KTimer kt_("k_aggregate", sf);
+            k_aggregate<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, M.nrm.p, skip);
+        }
+        ck_launch("k_aggregate");
+    }
+    if (A.ntargets > 0 && A.ntgroups > 0) {
+        {
+            KTimer kt_("k_transfer", sf);
+            k_transfer_split<<<A.ntgroups, 32 * kTransferWarps, 0, sf>>>(P.largs.p, skip);
+        }
+        ck_launch("k_transfer");
+    }
+    NearArgs na = near_args(M, P, cp, cq);
+    {
+        KTimer kt_("k_near_fused_t", s);
+        k_near_fused_t<<<nblocks(n, 8), 256, 0, s>>>(na, M.xint.p, M.ynear.p, nullptr, fr(M).err.p, skip);
+    }
+    ck_launch("k_near_fused_t");
+    if (fork) {
+        ck(cudaEventRecord(M.ev_join, sf), "record join");
+        ck(cudaStreamWaitEvent(s, M.ev_join, 0), "wait join");
+    }
+    DisaggArgs da;
+    da.n = n;
+    da.nrm = M.nrm.p;
+    da.perm = perm_out ? M.perm.p : nullptr;
+    da.k = (float)P.k;
+    da.nlev = (int)P.lev.size();
+    da.rowf = M.rowf.p;
+    for (int l = 0; l < A.nlev; ++l) da.lev[l] = A.lev[l];
+    da.tasks = P.lists->dis_tasks.p;
+    da.sum_nd = 0;
+    for (int l = 0; l < A.nlev; ++l) da.sum_nd += A.lev[l].nd;
+    {
+        KTimer kt_("k_disaggregate_t", s);
+        const size_t smem = (size_t)std::max(2, da.sum_nd) / 2 * sizeof(float4) + (size_t)da.sum_nd * sizeof(float2);
+        if (smem > kDisaggSmem)
+            throw Fail{set_err(BEM_E_ARG, "far field: " + std::to_string(da.sum_nd) +
+                                              " directions over all levels exceed the disaggregation kernel's "
+                                              "shared-memory staging")};
+        if (P.lists->n_dis_tasks > 0)
+            k_disaggregate_t<<<P.lists->n_dis_tasks, kDisThreads, smem, s>>>(da, far_only ? nullptr : M.ynear.p, y,
+                                                                             skip);
+    }
+    ck_launch("k_disaggregate_t");
 }
 
 // Leaf-size autotuner: builds the geometric lists for the automatic leaf
@@ -1487,6 +1565,32 @@ int bem_matvec(void *mesh, double freq_hz, const bem_medium *medium, const doubl
     }
 }
 
+int bem_matvec_transpose(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
+                         int32_t n_regions, const void *x_dev, void *y_dev, void *stream)
+{
+    if (!mesh || !x_dev || !y_dev) return set_err(BEM_E_ARG, "bad argument");
+    auto &M = *(bem_mesh_impl *)mesh;
+    try {
+        cudaStream_t us = (cudaStream_t)stream;
+        Coeffs C;
+        join_streams(us, M.s);
+        prepare(M, freq_hz, medium, admittance, n_regions, C);
+        reset_err(M);
+        M.tmp.alloc(M.n);
+        {
+            KTimer kt_("k_gather", M.s);
+            k_gather<<<nblocks(M.n, 256), 256, 0, M.s>>>((const float2 *)x_dev, M.perm.p, M.n, M.tmp.p);
+        }
+        ck_launch("k_gather");
+        matvec_t_internal(M, fr(M).cp.p, fr(M).cq.p, M.tmp.p, (float2 *)y_dev, true, false, nullptr, M.s);
+        check_err(M);
+        join_streams(M.s, us);
+        return resolution_warning(M, freq_hz, medium);
+    } catch (Fail &f) {
+        return f.code;
+    }
+}
+
 int bem_matvec_host(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
                     int32_t n_regions, const void *x_host, void *y_host, int32_t n_rhs, void *stream)
 {
@@ -1518,8 +1622,8 @@ struct GmresResult {
     GmresState h;
 };
 
-// Restarted GMRES on A u = b, or on A^T u = b when transposed (direct mode
-// only: the transposed product recomputes every pair by quadrature), with b
+// Restarted GMRES on A u = b, or on A^T u = b when transposed (the adjoint
+// solve; matvec_t_internal), with b
 // in M.bvec and u in M.uvec (internal order), for the current frame's plan
 // and column coefficients.  Row-scaled when row_scaling is on (the forward
 // system only; the caller has scaled b).  Throws Fail.
@@ -1530,16 +1634,7 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     const int m = M.prm.restart;
     const bool rscale = M.prm.row_scaling != 0 && !transposed;
     GmresResult R;
-    // y = A^T x_int (x_int formed by k_prep or k_gm_ortho); zero (may be
-    // null) is cleared, for the part of the product k_gm_ortho adds to y
-    auto product_t = [&](float2 *y, float2 *zero, const int *skip) {
-        NearArgs na = near_args(M, *fr(M).plan, fr(M).cp.p, fr(M).cq.p);
-        {
-            KTimer kt_("k_direct_product_t", s);
-            k_direct_product_t<<<nblocks(n, 8), 256, 0, s>>>(na, M.xint.p, y, zero, fr(M).err.p, skip);
-        }
-        ck_launch("k_direct_product_t");
-    };
+    if (transposed) M.rowf.alloc(n);   // before the Arnoldi steps are captured (no allocation in a capture)
     // GMRES workspace
     M.V.alloc((size_t)(m + 1) * n);
     M.w.alloc(n);
@@ -1657,7 +1752,7 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     // row-scaled when row scaling is on (both parts that k_gm_ortho adds)
     auto product = [&]() {
         if (transposed) {
-            product_t(M.w.p, M.ynear.p, done);
+            matvec_t_internal(M, fr(M).cp.p, fr(M).cq.p, nullptr, M.w.p, false, true, done, s);
             return;
         }
         matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, nullptr, nullptr, false, M.w.p, false, done, s, true, true);
@@ -1762,13 +1857,7 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
         // restart: r = b - A x
         ++restarts;
         if (transposed) {
-            PrepArgs pa = prep_args(M, fr(M).cp.p, fr(M).cq.p, M.uvec.p);
-            {
-                KTimer kt_("k_prep", s);
-                k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, nullptr);
-            }
-            ck_launch("k_prep");
-            product_t(M.w.p, nullptr, nullptr);
+            matvec_t_internal(M, fr(M).cp.p, fr(M).cq.p, M.uvec.p, M.w.p, false, false, nullptr, s);
         } else {
             matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, M.uvec.p, nullptr, false, M.w.p, false, nullptr, s);
         }
@@ -2191,9 +2280,6 @@ int bem_admittance_gradient(void *mesh, double freq_hz, const bem_medium *medium
         !(tol > 0) || max_iter < 1 || !p_dev || !q_dev || !loss || !grad)
         return set_err(BEM_E_ARG, "bad argument");
     auto &M = *(bem_mesh_impl *)mesh;
-    if (M.prm.mode != BEM_MODE_DIRECT)
-        return set_err(BEM_E_ARG, "the admittance gradient needs mode BEM_MODE_DIRECT (the transposed "
-                                  "far-field product is not built)");
     // forward problem: u, p, q (Eq. SystemI) and the field at the points
     const int fwd = bem_solve(mesh, freq_hz, medium, admittance, n_regions, srcs, n_src, tol, max_iter, p_dev,
                               q_dev, info, stream);
@@ -2234,18 +2320,7 @@ int bem_admittance_gradient(void *mesh, double freq_hz, const bem_medium *medium
         std::vector<float2> h0((size_t)n, make_float2(0.f, 0.f)), hq((size_t)n, make_float2(tau, 0.f));
         M.adj_cp.upload(h0, s);
         M.adj_cq.upload(hq, s);
-        PrepArgs pa = prep_args(M, M.adj_cp.p, M.adj_cq.p, M.uvec.p);
-        {
-            KTimer kt_("k_prep", s);
-            k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, nullptr);
-        }
-        ck_launch("k_prep");
-        NearArgs na = near_args(M, *fr(M).plan, M.adj_cp.p, M.adj_cq.p);
-        {
-            KTimer kt_("k_direct_product_t", s);
-            k_direct_product_t<<<nblocks(n, 8), 256, 0, s>>>(na, M.xint.p, M.w.p, nullptr, fr(M).err.p, nullptr);
-        }
-        ck_launch("k_direct_product_t");
+        matvec_t_internal(M, M.adj_cp.p, M.adj_cq.p, M.uvec.p, M.w.p, false, false, nullptr, s);
         // per-region sums and the loss
         std::vector<int> reg((size_t)n);
         for (int64_t i = 0; i < n; ++i) {

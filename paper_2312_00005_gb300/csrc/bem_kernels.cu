@@ -459,14 +459,15 @@ __global__ void k_row_scale(float2 *__restrict__ y, float2 *__restrict__ y2, con
 }
 
 // ------------------------------------------------------------------ adjoint
-// Transposed product of the direct operator (every pair by quadrature,
-// Eq. SystemI): y_j = sum_i A_ij x_i with A_ij the entry bm_entry gives for
-// row i and column j (the same entries as the forward product, so this is
-// its exact transpose).  One warp per column j, lanes over the rows.  zero
-// (may be null): also cleared at j (the second part of a product that the
-// Gram-Schmidt step adds).
-__global__ void k_direct_product_t(NearArgs a, const float2 *__restrict__ x, float2 *__restrict__ y,
-                                   float2 *__restrict__ zero, int *__restrict__ err, const int *skip)
+// Near part of the transposed product, y_j = sum_{i near j} A_ij x_i with
+// the entries recomputed by bm_entry (row i, column j; the forward product's
+// entries).  The near relation is symmetric (it pairs leaves: i is near j
+// when leaf(i) is in leaf(j)'s near list and the lists are symmetric), so
+// the rows i of column j are the near columns listed for j's own leaf.
+// One warp per column j, lanes over those rows.  zero (may be null): also
+// cleared at j.
+__global__ void k_near_fused_t(NearArgs a, const float2 *__restrict__ x, float2 *__restrict__ y,
+                               float2 *__restrict__ zero, int *__restrict__ err, const int *skip)
 {
     if (skip_now(skip)) return;
     const int lane = threadIdx.x & 31;
@@ -476,7 +477,11 @@ __global__ void k_direct_product_t(NearArgs a, const float2 *__restrict__ x, flo
     const float2 cp = a.cp[j], cq = a.cq[j];
     float2 acc = make_float2(0.f, 0.f);
     if (cp.x != 0.f || cp.y != 0.f || cq.x != 0.f || cq.y != 0.f) {
-        for (int64_t i = lane; i < a.E.n; i += 32) {
+        const int t = a.N.leaf_of[j];
+        const int r_end = a.N.run_ptr[t + 1], nc = a.N.ncol[t];
+        int r = a.N.run_ptr[t];
+        for (int p = lane; p < nc; p += 32) {
+            const int64_t i = near_col(a.N, r_end, r, p);
             const float4 ch = a.E.chi[i], cl = a.E.clo[i];
             const float3 xhi = f3(ch), xlo = f3(cl), nx = f3(a.E.nrm[i]);
             const double xd[3] = {a.E.cd[3 * i], a.E.cd[3 * i + 1], a.E.cd[3 * i + 2]};
@@ -493,6 +498,28 @@ __global__ void k_direct_product_t(NearArgs a, const float2 *__restrict__ x, flo
         y[j] = acc;
         if (zero) zero[j] = make_float2(0.f, 0.f);
     }
+}
+
+// Inputs of the transposed product's far field.  With the antipodal
+// symmetry of the sphere grid and D(-X, s) = D(X, -s) (Eq. FMMBase), the far
+// part of A^T x is the forward aggregation of the weights (alpha, c) =
+// (x_i, -x_i) (row operator 1 - s.n_i on the source side), the forward
+// transfer, and a disaggregation with the row factor A_i (cq_i - ik cp_i
+// (s.n_i)) = a_i + b_i (s.n_i) (the column factor of the forward product).
+// x: internal order, or null to use x_int as it stands.
+__global__ void k_prep_t(int64_t n, const float2 *__restrict__ x, float2 *__restrict__ xint,
+                         float4 *__restrict__ wts, float4 *__restrict__ rowf, const float4 *__restrict__ chi,
+                         const float2 *__restrict__ cp, const float2 *__restrict__ cq, float k, const int *skip)
+{
+    if (skip_now(skip)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 xv = x ? x[i] : xint[i];
+    if (x) xint[i] = xv;
+    if (wts) wts[i] = make_float4(xv.x, xv.y, -xv.x, -xv.y);
+    const float A = chi[i].w;
+    const float2 av = cscale(cq[i], A), t = cscale(cp[i], A);
+    rowf[i] = make_float4(av.x, av.y, k * t.y, -k * t.x);   // (A cq, -ik A cp)
 }
 
 // Transposed field operator of the representation formula (Eq. BIE_I with
@@ -781,11 +808,14 @@ __global__ void __launch_bounds__(32 * kTransferWarps) k_transfer_split(const Le
 // every warp leaves its sum per element in shared memory without waiting
 // for the others, and after one barrier the block adds the warps' sums in
 // warp order and writes y[perm[i]] (caller order) or y[i].
+// kRowF: the row factor a_i + b_i (s.n_i) with per-element (a, b) = a.rowf[i]
+// in place of 1 + s.n_i (the transposed product: two sums per element,
+// S0 = sum (1-part) and S1 = sum (s.n-part), combined as a S0 + b S1).
 constexpr int kDisChunk = 8;
-__global__ void __launch_bounds__(kDisThreads, 16) k_disaggregate(DisaggArgs a, const float2 *__restrict__ ynear,
-                                                                  float2 *__restrict__ y, const int *skip)
+template <bool kRowF>
+__device__ __forceinline__ void disaggregate_body(const DisaggArgs &a, const float2 *__restrict__ ynear,
+                                                  float2 *__restrict__ y)
 {
-    if (skip_now(skip)) return;
     extern __shared__ float4 dsm[];   // [sum_nd / 2] first-half directions, then [sum_nd / 2] (A, B) pairs
     float4 *dir_s = dsm;
     float4 *ab_s = dsm + a.sum_nd / 2;
@@ -795,6 +825,7 @@ __global__ void __launch_bounds__(kDisThreads, 16) k_disaggregate(DisaggArgs a, 
     __shared__ float4 dzs[kDisTask][kMaxFarLevels];   // -k/(2 pi) (z_c - x_i) per active level
     __shared__ float4 ns[kDisTask];
     __shared__ float2 red[kNW][kDisTask];
+    __shared__ float2 red1[kRowF ? kNW : 1][kRowF ? kDisTask : 1];
     const int2 tk = a.tasks[blockIdx.x];
     const int64_t e0 = tk.x, e1 = tk.y;
     const int cnt_all = (int)min((int64_t)kDisTask, e1 - e0);   // the host never makes larger tasks
@@ -842,9 +873,11 @@ __global__ void __launch_bounds__(kDisThreads, 16) k_disaggregate(DisaggArgs a, 
     __syncthreads();
     for (int q0 = 0; q0 < cnt_all; q0 += kDisChunk) {
         const int cnt = min(kDisChunk, cnt_all - q0);
-        float2 acc[kDisChunk];
+        float2 acc[kDisChunk], acc1[kRowF ? kDisChunk : 1];
 #pragma unroll
         for (int q = 0; q < kDisChunk; ++q) acc[q] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < (kRowF ? kDisChunk : 1); ++q) acc1[q] = make_float2(0.f, 0.f);
         for (int pf = threadIdx.x; pf < HP; pf += blockDim.x) {
             const float4 sv = dir_s[pf];
             const int u = __float_as_int(sv.w);
@@ -856,11 +889,19 @@ __global__ void __launch_bounds__(kDisThreads, 16) k_disaggregate(DisaggArgs a, 
                     float sn0, cs0;
                     sincos_turns(fmaf(d.x, sv.x, fmaf(d.y, sv.y, d.z * sv.z)), &sn0, &cs0);
                     const float tn = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
-                    // (cs + i sn)(1 + t) lp + (cs - i sn)(1 - t) lm = cs sp + i sn dm
-                    const float spx = fmaf(tn, ab.z, ab.x), spy = fmaf(tn, ab.w, ab.y);
-                    const float dmx = fmaf(tn, ab.x, ab.z), dmy = fmaf(tn, ab.y, ab.w);
-                    acc[q].x = fmaf(cs0, spx, fmaf(-sn0, dmy, acc[q].x));
-                    acc[q].y = fmaf(cs0, spy, fmaf(sn0, dmx, acc[q].y));
+                    if (kRowF) {
+                        // S0 += cs A + i sn B, S1 += t (cs B + i sn A)
+                        acc[q].x = fmaf(cs0, ab.x, fmaf(-sn0, ab.w, acc[q].x));
+                        acc[q].y = fmaf(cs0, ab.y, fmaf(sn0, ab.z, acc[q].y));
+                        acc1[q].x = fmaf(tn, fmaf(cs0, ab.z, -sn0 * ab.y), acc1[q].x);
+                        acc1[q].y = fmaf(tn, fmaf(cs0, ab.w, sn0 * ab.x), acc1[q].y);
+                    } else {
+                        // (cs + i sn)(1 + t) lp + (cs - i sn)(1 - t) lm = cs sp + i sn dm
+                        const float spx = fmaf(tn, ab.z, ab.x), spy = fmaf(tn, ab.w, ab.y);
+                        const float dmx = fmaf(tn, ab.x, ab.z), dmy = fmaf(tn, ab.y, ab.w);
+                        acc[q].x = fmaf(cs0, spx, fmaf(-sn0, dmy, acc[q].x));
+                        acc[q].y = fmaf(cs0, spy, fmaf(sn0, dmx, acc[q].y));
+                    }
                 }
             }
         }
@@ -868,6 +909,10 @@ __global__ void __launch_bounds__(kDisThreads, 16) k_disaggregate(DisaggArgs a, 
         for (int q = 0; q < kDisChunk; ++q) {
             const float2 v = warp_sum(acc[q]);
             if (lane == 0 && q < cnt) red[warp][q0 + q] = v;
+            if (kRowF) {
+                const float2 v1 = warp_sum(acc1[kRowF ? q : 0]);
+                if (lane == 0 && q < cnt) red1[kRowF ? warp : 0][kRowF ? q0 + q : 0] = v1;
+            }
         }
     }
     __syncthreads();
@@ -877,6 +922,13 @@ __global__ void __launch_bounds__(kDisThreads, 16) k_disaggregate(DisaggArgs a, 
 #pragma unroll
         for (int w = 1; w < kNW; ++w) v = cadd(v, red[w][q]);
         const int64_t i = e0 + q;
+        if (kRowF) {
+            float2 v1 = red1[0][kRowF ? q : 0];
+#pragma unroll
+            for (int w = 1; w < kNW; ++w) v1 = cadd(v1, red1[kRowF ? w : 0][kRowF ? q : 0]);
+            const float4 f = a.rowf[i];
+            v = cadd(cmul(make_float2(f.x, f.y), v), cmul(make_float2(f.z, f.w), v1));
+        }
         // (ik / 16 pi^2) v
         const float sc = a.k * 0.00633257397764611f;   // k / (16 pi^2)
         const float2 far = make_float2(-sc * v.y, sc * v.x);
@@ -884,6 +936,22 @@ __global__ void __launch_bounds__(kDisThreads, 16) k_disaggregate(DisaggArgs a, 
         if (a.perm) y[a.perm[i]] = out;
         else y[i] = out;
     }
+}
+
+__global__ void __launch_bounds__(kDisThreads, 16) k_disaggregate(DisaggArgs a, const float2 *__restrict__ ynear,
+                                                                  float2 *__restrict__ y, const int *skip)
+{
+    if (skip_now(skip)) return;
+    disaggregate_body<false>(a, ynear, y);
+}
+
+// The disaggregation of the transposed product: row factor a_i + b_i (s.n_i)
+// from a.rowf (see k_prep_t).
+__global__ void __launch_bounds__(kDisThreads, 16) k_disaggregate_t(DisaggArgs a, const float2 *__restrict__ ynear,
+                                                                    float2 *__restrict__ y, const int *skip)
+{
+    if (skip_now(skip)) return;
+    disaggregate_body<true>(a, ynear, y);
 }
 
 // Translation table per distinct offset X (Eq. FMMBase):

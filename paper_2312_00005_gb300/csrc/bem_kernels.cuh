@@ -126,6 +126,7 @@ struct DisaggArgs {
     int nlev;
     const int2 *tasks;       // element ranges [x, y) within one leaf, one per block
     int sum_nd;              // sum of nd over the levels (shared-memory rows)
+    const float4 *rowf;      // k_disaggregate_t: per-element row factor (a, b); else unused
     FarArgs lev[kMaxFarLevels];
 };
 
@@ -158,6 +159,7 @@ constexpr int kTransferUnroll = 8;         // list entries per warp in flight
 constexpr int kTransferEntries = 512;     // interaction-list entries staged per pass
 __global__ void k_transfer_split(const LevelsArgs *A, const int *skip);
 __global__ void k_disaggregate(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
+__global__ void k_disaggregate_t(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
 // largest expansion length of the translation tables (shared-memory rows)
 constexpr int kMaxTableL = 255;
 // Translation tables of every far level: block b serves offset
@@ -188,7 +190,9 @@ __global__ void k_field_velocity(ElemDev E, const QuadTables *Q, const double *p
 __global__ void k_field_velocity_finish(const double *pts, int64_t M, int S, float k, float inv_omega_rho,
                                         const SourceDev *src, int nsrc, const float2 *part, float2 *out);
 __global__ void k_gather(const float2 *x, const int64_t *perm, int64_t n, float2 *y);
-__global__ void k_direct_product_t(NearArgs a, const float2 *x, float2 *y, float2 *zero, int *err, const int *skip);
+__global__ void k_near_fused_t(NearArgs a, const float2 *x, float2 *y, float2 *zero, int *err, const int *skip);
+__global__ void k_prep_t(int64_t n, const float2 *x, float2 *xint, float4 *wts, float4 *rowf, const float4 *chi,
+                         const float2 *cp, const float2 *cq, float k, const int *skip);
 __global__ void k_field_t(ElemDev E, const QuadTables *Qp, const double *pts, int64_t M, float k, const float2 *f,
                           const float2 *cp, const float2 *cq, float2 *g_out, float2 *r_out, int *err);
 __global__ void k_adjoint_reduce(const float2 *u, const float2 *g, const float2 *aq, const int *region, int64_t n,

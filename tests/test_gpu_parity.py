@@ -384,13 +384,62 @@ def test_admittance_gradient_matches_oracle_interior(bem):
     assert eg < 2e-5, eg
 
 
-def test_admittance_gradient_needs_direct_mode(bem):
-    nodes, tris = inputs.icosphere(2, 0.1)
+@pytest.mark.parametrize("mode", ["direct", "fmm"])
+def test_transposed_product_matches_oracle(bem, mode):
+    """y = A^T x (the adjoint solve's product) against the oracle's dense
+    A^T x with mixed boundary conditions: direct (1280 elements, 1.5 kHz)
+    within FP32 rounding; FMM (5120 elements, 2 kHz, three levels) within
+    the plane-wave truncation, as the forward product."""
+    lev, freq = (3, 1500.0) if mode == "direct" else (4, 2000.0)
+    nodes, tris = inputs.icosphere(lev, 0.1)
     n = tris.shape[0]
-    mesh = bem.Mesh(nodes, tris, bc_type=np.full(n, bem.ADMI, np.int32))
-    with pytest.raises(bem.BemError):
-        mesh.admittance_gradient(1000.0, [bem.plane_wave((0, 0, 1))], [0.001], inputs.fibonacci_sphere(4, 1.0))
+    k = 2 * np.pi * freq / C
+    bct, region, adm = _mixed_bc(n, 7)
+    x = inputs.random_complex(n, 23)
+    cp, cq = _oracle_coeffs(bct, region, adm, k)
+    yo = oracle.assemble(nodes, tris, k, cp, cq).T @ x
+    xt = torch.tensor(x, dtype=torch.complex64, device="cuda")
+    if mode == "direct":
+        mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region, mode=bem.MODE_DIRECT)
+        err = _rel(mesh.matvec_transpose(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy(), yo)
+        mesh.close()
+        assert err < 2e-5, err
+        return
+    errs = {}
+    for tf in (1.8, 6.0):
+        mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region, trunc_factor=tf)
+        assert mesh.stats(freq, c=C)["levels"] >= 2
+        errs[tf] = _rel(mesh.matvec_transpose(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy(), yo)
+        mesh.close()
+    print("transposed fmm rel err", errs)
+    assert errs[1.8] < 2e-3, errs
+    assert errs[6.0] < 1e-4, errs
+
+
+def test_admittance_gradient_fmm_matches_oracle(bem):
+    """The adjoint gradient through the FMM (5120 elements, 2 kHz, eight
+    octant regions, truncation factor 6) against the oracle's dense adjoint:
+    both solves and the transposed product carry the FMM truncation error."""
+    nodes, tris = inputs.icosphere(4, 0.1)
+    n = tris.shape[0]
+    f = 2000.0
+    cen, _, _ = oracle.geometry(nodes, tris)
+    region = _octant_regions(cen)
+    rng = np.random.default_rng(2312)
+    Y = rng.uniform(0.0, 0.5, 8) * np.exp(1j * rng.uniform(-np.pi / 2, np.pi / 2, 8)) / (RHO * C)
+    bct = np.full(n, bem.ADMI, np.int32)
+    pts = inputs.fibonacci_sphere(20, 1.0)
+    mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region, trunc_factor=6.0)
+    assert mesh.stats(f, c=C)["levels"] >= 2
+    L, g, p, q, info = mesh.admittance_gradient(f, [bem.plane_wave((0, 0, 1))], Y, pts, tol=1e-7, c=C, rho=RHO)
     mesh.close()
+    assert info["converged"], info
+    Lo, go, _ = oracle.admittance_gradient(nodes, tris, f, pts, region, Y, sources=[("plane", (0, 0, 1.0), 1.0)],
+                                           c=C, rho=RHO)
+    eg = np.max(np.abs(g - go)) / np.max(np.abs(go))
+    print("fmm adjoint: loss rel err", abs(L - Lo) / Lo, "grad rel err", eg)
+    assert abs(L - Lo) < 1e-4 * Lo, (L, Lo)
+    assert eg < 2e-3, eg
 
 
 def test_subdivision_limit_is_reported(bem):
