@@ -2346,10 +2346,8 @@ int bem_admittance_gradient(void *mesh, double freq_hz, const bem_medium *medium
         resolve_timing();
         *loss = hacc[2 * n_regions];
         for (int r = 0; r < 2 * n_regions; ++r) grad[r] = hacc[r];
-        if (fwd != BEM_OK) {
-            g_err = fwd_msg;
-            return fwd;
-        }
+        // the adjoint's non-convergence first: it makes the gradient itself
+        // approximate; then the forward warning, if any
         if (!R.converged) {
             char buf[160];
             snprintf(buf, sizeof buf, "adjoint GMRES: relative residual %.3g after %d products (tol %.3g)",
@@ -2357,7 +2355,8 @@ int bem_admittance_gradient(void *mesh, double freq_hz, const bem_medium *medium
             g_err = buf;
             return BEM_W_NOT_CONVERGED;
         }
-        return BEM_OK;
+        if (fwd != BEM_OK) g_err = fwd_msg;
+        return fwd;
     } catch (Fail &f) {
         abandon_capture(M);
         return f.code;

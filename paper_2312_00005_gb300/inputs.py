@@ -119,6 +119,13 @@ def bumpy_ellipsoid(nu: int, axes=(0.09, 0.075, 0.11), n_bumps: int = 24, seed: 
     ellipsoid with the given semi-axes, plus seeded smooth Gaussian radial bumps
     (amplitude and angular width drawn uniformly from the given ranges)."""
     u, tris = geodesic_sphere(nu)
+    nodes = _head_map(u, axes, n_bumps, seed, amp, sigma)
+    return nodes, _orient_outward(nodes, tris)
+
+
+def _head_map(u, axes=(0.09, 0.075, 0.11), n_bumps=24, seed=2312, amp=(0.002, 0.006), sigma=(0.15, 0.35)):
+    """The head-like surface as a map of unit vectors u [M, 3]: ellipsoid
+    point plus the seeded radial bumps."""
     rng = np.random.default_rng(seed)
     cen = rng.normal(size=(n_bumps, 3))
     cen /= np.linalg.norm(cen, axis=1, keepdims=True)
@@ -127,8 +134,43 @@ def bumpy_ellipsoid(nu: int, axes=(0.09, 0.075, 0.11), n_bumps: int = 24, seed: 
     e = u * np.asarray(axes, dtype=np.float64)[None, :]
     ang = np.arccos(np.clip(u @ cen.T, -1.0, 1.0))
     disp = (a[None, :] * np.exp(-0.5 * (ang / s[None, :]) ** 2)).sum(axis=1)
-    nodes = e + disp[:, None] * u
-    return nodes, _orient_outward(nodes, tris)
+    return e + disp[:, None] * u
+
+
+def head_point_source(offset: float = 0.001):
+    """Position of the batched-frequency workload's point source: offset
+    metres outside the head-like surface at the image of +y (its +y
+    extremum), along +y."""
+    y = _head_map(np.array([[0.0, 1.0, 0.0]]))[0]
+    return y + np.array([0.0, offset, 0.0])
+
+
+def head_bands(n_freq: int = 64, f_lo: float = 200.0, f_hi: float = 16000.0, c: float = 343.0,
+               per_wavelength: float = 10.7, h_max: float = 0.011, step: float = 1.15):
+    """The batched-frequency workload on the head-like surface: n_freq
+    frequencies f_i = f_lo (f_hi / f_lo)^(i / (n_freq - 1)), each wanting a
+    mean element edge h_i = min(lambda_i / per_wavelength, h_max).  The mean
+    edge of bumpy_ellipsoid(nu) is kappa / nu (kappa measured on nu = 10);
+    each frequency takes the smallest nu of the ladder ceil(nu_0 step^j)
+    with kappa / nu <= h_i, so frequencies share meshes in bands of uneven
+    N = 20 nu^2.  Returns [(nu, [freqs])] in increasing frequency."""
+    nodes, tris = bumpy_ellipsoid(10)
+    e = np.concatenate([np.linalg.norm(nodes[tris[:, a]] - nodes[tris[:, b]], axis=1)
+                        for a, b in ((0, 1), (1, 2), (2, 0))])
+    kappa = float(e.mean()) * 10
+    freqs = f_lo * (f_hi / f_lo) ** (np.arange(n_freq) / (n_freq - 1))
+    need = np.ceil(kappa / np.minimum(c / freqs / per_wavelength, h_max)).astype(int)
+    ladder = [int(need.min())]
+    while ladder[-1] < need.max():
+        ladder.append(max(ladder[-1] + 1, int(np.ceil(ladder[0] * step ** len(ladder)))))
+    bands = []
+    for f, nd in zip(freqs, need):
+        nu = next(v for v in ladder if v >= nd)
+        if bands and bands[-1][0] == nu:
+            bands[-1][1].append(float(f))
+        else:
+            bands.append((nu, [float(f)]))
+    return bands
 
 
 def duct(length: float = 3.4, width: float = 0.2, h: float = 0.05):
@@ -192,6 +234,7 @@ def workload(name: str):
 
     sphere1280_1k  : sound-hard sphere r = 0.1 m, icosphere of 1280 triangles,
                      plane wave along +z at 1 kHz (small oracle case).
+    sphere5120_2k  : the same sphere as an icosphere of 5120 triangles at 2 kHz.
     sphere20480_4k : the same sphere as an icosphere of 20480 triangles, plane
                      wave along +z at 4 kHz, 100 field points on a 1 m sphere.
     """

@@ -442,6 +442,29 @@ def test_admittance_gradient_fmm_matches_oracle(bem):
     assert eg < 2e-3, eg
 
 
+def test_head_band_sweep_matches_oracle(bem):
+    """The first band of the batched-frequency workload (head-like surface,
+    2420 elements, point source 1 mm off the surface): a sweep over the
+    band's last two frequencies through the FMM (truncation factor 6); the
+    last one's surface pressure and field against the oracle."""
+    nu, freqs = inputs.head_bands()[0]
+    nodes, tris = inputs.bumpy_ellipsoid(nu)
+    xs = inputs.head_point_source()
+    pts = inputs.fibonacci_sphere(20, 1.0)
+    mesh = bem.Mesh(nodes, tris, trunc_factor=6.0)
+    fs = freqs[-2:]
+    p, q, fl, infos = mesh.solve_sweep(fs, [bem.point_source(xs, 1.0)], tol=1e-7, c=C, rho=RHO, points=pts)
+    mesh.close()
+    assert all(i["converged"] for i in infos), infos
+    src_o = [("point", tuple(xs), 1.0)]
+    po, qo, _ = oracle.solve(nodes, tris, fs[-1], c=C, rho=RHO, sources=src_o)
+    fo = oracle.field(nodes, tris, fs[-1], po, qo, pts, c=C, sources=src_o)
+    ep = _rel(p[-1].cpu().numpy(), po)
+    ef = _rel(fl[-1].cpu().numpy(), fo)
+    assert ep < 2e-4, ep
+    assert ef < 2e-4, ef
+
+
 def test_subdivision_limit_is_reported(bem):
     nodes, tris = inputs.icosphere(1, 0.1)
     tris = np.vstack([tris, tris[5:6]])
