@@ -96,6 +96,10 @@ typedef struct bem_params {
                                D = diag(A) (the self entries), and tol and relres refer to
                                that scaled residual; the solution is that of A u = b.
                                0: off (default).  Other values: BEM_E_ARG.                    */
+    int32_t check_orientation; /* 1: bem_mesh_create rejects (BEM_E_ARG, before any device work)
+                               a mesh that is not closed and consistently wound or whose normals
+                               point into the enclosed volume (bem_mesh_check_host); the paper
+                               leaves this to the user (Sec. 2.1).  0: off (default).         */
 } bem_params;
 
 typedef struct bem_medium {
@@ -272,6 +276,20 @@ int bem_admittance_gradient(void *mesh, double freq_hz, const bem_medium *medium
                             int32_t n_regions, const bem_source *srcs, int32_t n_src, const double *pts,
                             int64_t n_pts, double tol, int32_t max_iter, void *p_dev, void *q_dev, double *loss,
                             double *grad, bem_solve_info *info, void *stream);
+
+/* Orientation diagnostics of a closed triangle surface, host only (no
+ * device work).  The paper requires the normals to point away from the
+ * scatterer, into the fluid of an exterior problem, and leaves the check to
+ * the user (Sec. 2.1: inward normals swap the interior and exterior
+ * problems; App. A).  volume: the signed enclosed volume
+ * (1/3) sum_j A_j (x_j . n_j), x_j the midpoint, n_j = (b - a) x (c - a) / |.|
+ * (divergence theorem; positive when every normal points out of the
+ * enclosed volume); open_edges: edges not shared by exactly two triangles;
+ * misoriented_edges: shared edges that both triangles traverse in the same
+ * direction.  Any output may be NULL.  Errors: BEM_E_ARG (bad index,
+ * degenerate triangle), BEM_E_OOM. */
+int bem_mesh_check_host(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tris, double *volume,
+                        int64_t *open_edges, int64_t *misoriented_edges);
 
 /* Plan statistics for a frequency (builds the plan if needed). */
 int bem_mesh_stats(void *mesh, double freq_hz, const bem_medium *medium, bem_plan_stats *out);

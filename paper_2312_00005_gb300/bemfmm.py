@@ -15,7 +15,7 @@ import numpy as np
 __all__ = [
     "VELO", "PRES", "ADMI", "MODE_FMM", "MODE_DIRECT", "BemError", "Params", "Medium", "Source",
     "SolveInfo", "PlanStats", "Mesh", "lib", "launch_count", "plane_wave", "point_source", "timing_enable",
-    "timing_get", "plan_stats_host", "default_params", "admittance_loss",
+    "timing_get", "plan_stats_host", "mesh_check_host", "default_params", "admittance_loss",
 ]
 
 VELO, PRES, ADMI = 0, 1, 2
@@ -41,6 +41,7 @@ class Params(ctypes.Structure):
         ("L_min", ctypes.c_int32), ("admissibility", ctypes.c_double), ("leaf_edge", ctypes.c_double),
         ("stability_max", ctypes.c_double), ("near_store", ctypes.c_int32), ("restart", ctypes.c_int32),
         ("autotune", ctypes.c_int32), ("tau", ctypes.c_double), ("row_scaling", ctypes.c_int32),
+        ("check_orientation", ctypes.c_int32),
     ]
 
 
@@ -115,6 +116,8 @@ def lib():
                                                        i32, P, i64, d, i32, P, P, ctypes.POINTER(d), P,
                                                        ctypes.POINTER(SolveInfo), P]),
             "bem_mesh_stats": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), ctypes.POINTER(PlanStats)]),
+            "bem_mesh_check_host": (ctypes.c_int, [P, i64, P, i64, ctypes.POINTER(d), ctypes.POINTER(i64),
+                                                   ctypes.POINTER(i64)]),
             "bem_plan_stats_host": (ctypes.c_int, [P, i64, P, i64, ctypes.POINTER(Params), d, d,
                                                    ctypes.POINTER(PlanStats)]),
             "bem_mesh_release_plan": (ctypes.c_int, [P]),
@@ -235,6 +238,19 @@ def _admittance(adm):
     a = np.asarray(adm, dtype=np.complex128).reshape(-1)
     buf = np.ascontiguousarray(np.stack([a.real, a.imag], axis=1))
     return buf, a.shape[0]
+
+
+def mesh_check_host(nodes, tris) -> dict:
+    """Orientation diagnostics of a closed surface (host only): signed
+    enclosed volume (positive for normals out of the volume), open edges,
+    inconsistently wound edges."""
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    vol, op, mis = ctypes.c_double(0.0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().bem_mesh_check_host(nodes.ctypes.data_as(ctypes.c_void_p), nodes.shape[0],
+                                     tris.ctypes.data_as(ctypes.c_void_p), tris.shape[0], ctypes.byref(vol),
+                                     ctypes.byref(op), ctypes.byref(mis)))
+    return {"volume": vol.value, "open_edges": op.value, "misoriented_edges": mis.value}
 
 
 def plan_stats_host(nodes, tris, freq, c=343.0, params=None) -> dict:

@@ -1404,6 +1404,7 @@ void bem_params_default(bem_params *p)
     p->autotune = 1;
     p->tau = 1.0;
     p->row_scaling = 0;
+    p->check_orientation = 0;
 }
 
 const char *bem_last_error(void) { return g_err.c_str(); }
@@ -1426,8 +1427,34 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
     if (p.restart < 2 || p.restart > kMaxRestart) return set_err(BEM_E_ARG, "restart must be in 2..256");
     if (!(p.tau == 1.0 || p.tau == -1.0)) return set_err(BEM_E_ARG, "tau must be +1 (exterior) or -1 (interior)");
     if (p.row_scaling != 0 && p.row_scaling != 1) return set_err(BEM_E_ARG, "row_scaling must be 0 or 1");
+    if (p.check_orientation != 0 && p.check_orientation != 1)
+        return set_err(BEM_E_ARG, "check_orientation must be 0 or 1");
     if (!(p.quad_tol > 0) || !(p.rt_subdiv > 0) || !(p.admissibility > 0) || p.L_min < 1 || p.L_min > 200)
         return set_err(BEM_E_ARG, "invalid parameter");
+    if (p.check_orientation) {
+        // host only, before any device work
+        try {
+            Geometry g;
+            std::string e = compute_geometry(nodes, n_nodes, tris, n_tris, g);
+            if (!e.empty()) return set_err(BEM_E_ARG, e);
+            const MeshCheck mc = check_mesh(g, nodes, n_nodes, tris, n_tris);
+            char buf[200];
+            if (mc.open_edges || mc.misoriented_edges) {
+                snprintf(buf, sizeof buf, "orientation check: %lld edges not shared by two triangles, %lld shared "
+                                          "edges wound the same way by both",
+                         (long long)mc.open_edges, (long long)mc.misoriented_edges);
+                return set_err(BEM_E_ARG, buf);
+            }
+            if (!(mc.volume > 0)) {
+                snprintf(buf, sizeof buf, "orientation check: the normals point into the enclosed volume (signed "
+                                          "volume %.6g m^3); reverse the winding of every triangle",
+                         mc.volume);
+                return set_err(BEM_E_ARG, buf);
+            }
+        } catch (std::bad_alloc &) {
+            return set_err(BEM_E_OOM, "host allocation failed");
+        }
+    }
     try {
         auto M = std::make_unique<bem_mesh_impl>();
         M->prm = p;
@@ -2415,6 +2442,24 @@ int bem_timing_get(const char *name, double *total_ms, int64_t *launches)
     *total_ms = it->second.first;
     *launches = it->second.second;
     return BEM_OK;
+}
+
+int bem_mesh_check_host(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tris, double *volume,
+                        int64_t *open_edges, int64_t *misoriented_edges)
+{
+    if (!nodes || !tris || n_nodes < 3 || n_tris < 1) return set_err(BEM_E_ARG, "bad argument");
+    try {
+        Geometry g;
+        std::string e = compute_geometry(nodes, n_nodes, tris, n_tris, g);
+        if (!e.empty()) return set_err(BEM_E_ARG, e);
+        const MeshCheck mc = check_mesh(g, nodes, n_nodes, tris, n_tris);
+        if (volume) *volume = mc.volume;
+        if (open_edges) *open_edges = mc.open_edges;
+        if (misoriented_edges) *misoriented_edges = mc.misoriented_edges;
+        return BEM_OK;
+    } catch (std::bad_alloc &) {
+        return set_err(BEM_E_OOM, "host allocation failed");
+    }
 }
 
 int bem_plan_stats_host(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tris,

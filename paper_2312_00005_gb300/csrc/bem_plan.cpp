@@ -516,4 +516,50 @@ void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k,
         }
 }
 
+MeshCheck check_mesh(const Geometry &g, const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n)
+{
+    MeshCheck r;
+    // weld coincident vertices: id[v] = first vertex with the same rounded position
+    double ext = 0.0;
+    for (int d = 0; d < 3; ++d) ext = std::max(ext, g.vmax[d] - g.vmin[d]);
+    const double q = ext > 0 ? 1e-9 * ext : 1.0;
+    std::vector<std::tuple<int64_t, int64_t, int64_t, int32_t>> key((size_t)n_nodes);
+    for (int64_t v = 0; v < n_nodes; ++v)
+        key[v] = std::make_tuple((int64_t)std::llround((nodes[3 * v] - g.vmin[0]) / q),
+                                 (int64_t)std::llround((nodes[3 * v + 1] - g.vmin[1]) / q),
+                                 (int64_t)std::llround((nodes[3 * v + 2] - g.vmin[2]) / q), (int32_t)v);
+    std::sort(key.begin(), key.end());
+    std::vector<int32_t> id((size_t)n_nodes);
+    for (size_t i = 0; i < key.size(); ++i) {
+        const bool same = i > 0 && std::get<0>(key[i]) == std::get<0>(key[i - 1]) &&
+                          std::get<1>(key[i]) == std::get<1>(key[i - 1]) && std::get<2>(key[i]) == std::get<2>(key[i - 1]);
+        id[std::get<3>(key[i])] = same ? id[std::get<3>(key[i - 1])] : std::get<3>(key[i]);
+    }
+    for (int64_t j = 0; j < n; ++j)
+        r.volume += g.area[j] * (g.cen[3 * j] * g.nrm[3 * j] + g.cen[3 * j + 1] * g.nrm[3 * j + 1] +
+                                 g.cen[3 * j + 2] * g.nrm[3 * j + 2]) / 3.0;
+    // undirected edge (lo, hi) -> traversals lo -> hi and hi -> lo
+    std::vector<std::tuple<int32_t, int32_t, int>> ed;
+    ed.reserve(3 * n);
+    for (int64_t j = 0; j < n; ++j)
+        for (int e = 0; e < 3; ++e) {
+            const int32_t a = id[tris[3 * j + e]], b = id[tris[3 * j + (e + 1) % 3]];
+            ed.emplace_back(std::min(a, b), std::max(a, b), a < b ? 1 : 0);
+        }
+    std::sort(ed.begin(), ed.end());
+    for (size_t i = 0; i < ed.size();) {
+        size_t k = i;
+        int fwd = 0;
+        while (k < ed.size() && std::get<0>(ed[k]) == std::get<0>(ed[i]) && std::get<1>(ed[k]) == std::get<1>(ed[i])) {
+            fwd += std::get<2>(ed[k]);
+            ++k;
+        }
+        const size_t cnt = k - i;
+        if (cnt != 2) ++r.open_edges;
+        else if (fwd != 1) ++r.misoriented_edges;
+        i = k;
+    }
+    return r;
+}
+
 }  // namespace bem

@@ -36,6 +36,20 @@ struct Geometry {
 std::string compute_geometry(const double *nodes, int64_t n_nodes, const int32_t *tris,
                              int64_t n, Geometry &g);
 
+// Orientation diagnostics of a closed triangle surface (Sec. 2.1: the normals
+// must point away from the scatterer): the signed enclosed volume
+// (1/3) sum_j A_j (x_j . n_j) by the divergence theorem, positive when every
+// normal points out of the enclosed volume; the edges not shared by exactly
+// two triangles; the shared edges that both triangles traverse in the same
+// direction (inconsistent winding).  Vertices closer than 1e-9 of the
+// bounding box are one vertex for the edge count (node lists may repeat a
+// point).
+struct MeshCheck {
+    double volume = 0.0;
+    int64_t open_edges = 0, misoriented_edges = 0;
+};
+MeshCheck check_mesh(const Geometry &g, const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n);
+
 // ---------------------------------------------------------------- quadrature tables
 // Gauss rules by the Golub-Welsch eigenvalue method (Jacobi rotations on the
 // symmetric tridiagonal Jacobi matrix of the three-term recurrence).

@@ -130,3 +130,44 @@ def test_admittance_loss_autograd_convention():
     L2.backward()
     assert abs(L.item() - L2.item()) < 1e-12
     assert torch.allclose(Y.grad, Y2.grad, atol=1e-12)
+
+
+def _tet_volume(nodes, tris):
+    a, b, c = nodes[tris[:, 0]], nodes[tris[:, 1]], nodes[tris[:, 2]]
+    return float(np.einsum("ij,ij->i", a, np.cross(b, c)).sum() / 6.0)
+
+
+def test_mesh_check_closed_outward_surfaces(lib):
+    """Signed volume against the sum of signed tetrahedra a.(b x c)/6 (the same
+    divergence-theorem integral written per vertex triple), no open or
+    inconsistently wound edges; the duct's volume is its box's."""
+    for nodes, tris in (inputs.icosphere(3, 0.1), inputs.bumpy_ellipsoid(10)):
+        r = bemfmm.mesh_check_host(nodes, tris)
+        assert r["open_edges"] == 0 and r["misoriented_edges"] == 0
+        assert abs(r["volume"] - _tet_volume(nodes, tris)) < 1e-12 * abs(r["volume"])
+        assert r["volume"] > 0
+    nodes, tris = inputs.duct(0.6, 0.2, 0.1)
+    r = bemfmm.mesh_check_host(nodes, tris)
+    assert abs(r["volume"] - 0.6 * 0.2 * 0.2) < 1e-12 and r["open_edges"] == 0 and r["misoriented_edges"] == 0
+
+
+def test_mesh_check_finds_reversed_flipped_and_open(lib):
+    nodes, tris = inputs.icosphere(2, 0.1)
+    v = bemfmm.mesh_check_host(nodes, tris)["volume"]
+    rev = bemfmm.mesh_check_host(nodes, tris[:, [0, 2, 1]])
+    assert abs(rev["volume"] + v) < 1e-15 and rev["misoriented_edges"] == 0
+    one = tris.copy()
+    one[5] = one[5][[0, 2, 1]]
+    assert bemfmm.mesh_check_host(nodes, one)["misoriented_edges"] == 3
+    assert bemfmm.mesh_check_host(nodes, tris[1:])["open_edges"] == 3
+
+
+def test_mesh_create_orientation_check_rejects_before_device_work(lib):
+    """check_orientation = 1: an inward-wound or inconsistent mesh is an
+    argument error raised on the host (this runs without a GPU)."""
+    nodes, tris = inputs.icosphere(2, 0.1)
+    for bad in (tris[:, [0, 2, 1]], np.concatenate([tris[:5], tris[5:6, [0, 2, 1]], tris[6:]])):
+        with pytest.raises(bemfmm.BemError, match="orientation check"):
+            bemfmm.Mesh(nodes, bad, check_orientation=1)
+    with pytest.raises(bemfmm.BemError):
+        bemfmm.Mesh(nodes, tris, check_orientation=2)
