@@ -148,6 +148,14 @@ typedef struct bem_plan_stats {
     int32_t n_tuned;            /* leaf depths the autotuner timed (0: not run)        */
     int32_t tuned_depth[4];     /* ... their octree depths                             */
     double  tuned_seconds[4];   /* ... estimated seconds per solve (entries + 40 products) */
+    int64_t asymmetric_pairs;   /* element pairs of list entries without a mirror: near leaf
+                                   pairs (a, b) without (b, a) plus interaction entries
+                                   (t, s) without (s, t), each weighted by its clusters'
+                                   sizes.  The far test bounds r~ with the source cluster's
+                                   largest element area (Sec. 3.1.4 measures r~ against the
+                                   source element), so a pair can be far one way and near
+                                   the other; bem_matvec_transpose reads the lists backwards
+                                   and applies, on these pairs, the other direction's rule */
 } bem_plan_stats;
 
 /* Paper defaults (Sec. 3.1, Eq. FMMTruncation, Eq. Farfieldcond). */
@@ -181,9 +189,14 @@ int bem_matvec(void *mesh, double freq_hz, const bem_medium *medium, const doubl
                int32_t n_regions, const void *x_dev, void *y_dev, int32_t n_rhs, void *stream);
 
 /* y = A^T x (the transpose of bem_matvec's A, one right-hand side), the
- * product of the adjoint solve in bem_admittance_gradient.  Near part: the
- * same entries as A, recomputed by quadrature in every call (not the stored
- * ones).  Far part (FMM mode): the antipodal symmetry of the sphere grid of
+ * product of the adjoint solve in bem_admittance_gradient.  It reads the near
+ * and interaction lists backwards: exact where the near/far verdict of a
+ * pair is the same both ways; on the pairs counted by
+ * bem_plan_stats.asymmetric_pairs it takes the other direction's rule (the
+ * plane-wave expansion where A used quadrature of a higher order, or the
+ * reverse), which agree within the quadrature tolerance and the truncation.
+ * Near part: the same entries as A, recomputed by quadrature in every call
+ * (not the stored ones).  Far part (FMM mode): the antipodal symmetry of the sphere grid of
  * Sec. 3.3.3 and D(-X, s) = D(X, -s) in Eq. FMMBase make it the forward
  * aggregation of x with the source factor 1 - s.n, the forward transfer and
  * a disaggregation with A's column factor A_j (c^q_j - ik c^p_j s.n_j) as

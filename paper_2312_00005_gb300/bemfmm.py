@@ -70,6 +70,7 @@ class PlanStats(ctypes.Structure):
         ("near_nnz", ctypes.c_int64), ("near_quad_points", ctypes.c_int64), ("leaf_edge", ctypes.c_double),
         ("mean_edge", ctypes.c_double), ("device_bytes", ctypes.c_int64), ("far_pairs", ctypes.c_int64),
         ("n_tuned", ctypes.c_int32), ("tuned_depth", ctypes.c_int32 * 4), ("tuned_seconds", ctypes.c_double * 4),
+        ("asymmetric_pairs", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -81,6 +82,7 @@ class PlanStats(ctypes.Structure):
             "n_offsets": list(self.n_offsets[:n]), "n_leaves": self.n_leaves, "near_nnz": self.near_nnz,
             "near_quad_points": self.near_quad_points, "leaf_edge": self.leaf_edge,
             "mean_edge": self.mean_edge, "device_bytes": self.device_bytes, "far_pairs": self.far_pairs,
+            "asymmetric_pairs": self.asymmetric_pairs,
             "autotune": [(self.tuned_depth[q], self.tuned_seconds[q]) for q in range(self.n_tuned)],
         }
 

@@ -1374,6 +1374,30 @@ void fill_stats(const Geometry &g, const Tree &t, const FreqPlan &fp, bem_plan_s
             for (int q = F.il_ptr[c]; q < F.il_ptr[c + 1]; ++q) far_pairs += L.count[c] * L.count[F.il_src[q]];
     }
     out->far_pairs = far_pairs;
+    // symmetry of the lists (the transposed product reads them backwards):
+    // near leaf pairs (a, b) without (b, a), interaction entries (c, s)
+    // without (s, c) at the same level
+    int64_t asym = 0;   // element pairs
+    auto count_asym = [&asym](std::vector<int64_t> &keys, int64_t m, const std::vector<int64_t> &cnt) {
+        std::sort(keys.begin(), keys.end());
+        for (int64_t key : keys)
+            if (!std::binary_search(keys.begin(), keys.end(), (key % m) * m + key / m))
+                asym += cnt[key / m] * cnt[key % m];
+    };
+    {
+        const int64_t nl = (int64_t)fp.near_ptr.size() - 1;
+        std::vector<int64_t> keys;
+        for (int64_t a = 0; a < nl; ++a)
+            for (int q = fp.near_ptr[a]; q < fp.near_ptr[a + 1]; ++q) keys.push_back(a * nl + fp.near_src[q]);
+        if (nl > 0) count_asym(keys, nl, t.lv[fp.leaf_depth].count);
+    }
+    for (const FarLevel &F : fp.far) {
+        std::vector<int64_t> keys;
+        for (int c = 0; c < F.nc; ++c)
+            for (int q = F.il_ptr[c]; q < F.il_ptr[c + 1]; ++q) keys.push_back((int64_t)c * F.nc + F.il_src[q]);
+        if (F.nc > 0) count_asym(keys, F.nc, t.lv[F.depth].count);
+    }
+    out->asymmetric_pairs = asym;
     out->n_leaves = (int)t.lv[fp.leaf_depth].start.size();
     out->near_nnz = fp.nnz;
     out->near_quad_points = -1;

@@ -459,13 +459,14 @@ __global__ void k_row_scale(float2 *__restrict__ y, float2 *__restrict__ y2, con
 }
 
 // ------------------------------------------------------------------ adjoint
-// Near part of the transposed product, y_j = sum_{i near j} A_ij x_i with
-// the entries recomputed by bm_entry (row i, column j; the forward product's
-// entries).  The near relation is symmetric (it pairs leaves: i is near j
-// when leaf(i) is in leaf(j)'s near list and the lists are symmetric), so
-// the rows i of column j are the near columns listed for j's own leaf.
-// One warp per column j, lanes over those rows.  zero (may be null): also
-// cleared at j.
+// Near part of the transposed product: y_j = sum_i A_ij x_i over the rows i
+// whose leaves are in the near list of j's own leaf (the lists read
+// backwards), with the entries recomputed by bm_entry (row i, column j; the
+// forward product's entries).  Where a pair's near/far verdict differs by
+// direction (the far test uses the source cluster's element areas), the
+// pair is taken here or in the far part, the other way than in A.  One warp
+// per column j, lanes over those rows.  zero (may be null): also cleared
+// at j.
 __global__ void k_near_fused_t(NearArgs a, const float2 *__restrict__ x, float2 *__restrict__ y,
                                float2 *__restrict__ zero, int *__restrict__ err, const int *skip)
 {

@@ -69,6 +69,7 @@ def test_plan_partitions_all_pairs(lib, lev, freq):
     n = tris.shape[0]
     st = bemfmm.plan_stats_host(nodes, tris, freq)
     assert st["near_nnz"] + st["far_pairs"] == n * n
+    assert 0 <= st["asymmetric_pairs"] < 0.03 * n * n
     assert st["near_nnz"] >= n                  # the diagonal is near
     for L in st["L"]:
         assert L >= 8
@@ -171,3 +172,17 @@ def test_mesh_create_orientation_check_rejects_before_device_work(lib):
             bemfmm.Mesh(nodes, bad, check_orientation=1)
     with pytest.raises(bemfmm.BemError):
         bemfmm.Mesh(nodes, tris, check_orientation=2)
+
+
+def test_plan_lists_symmetric_where_the_verdicts_must_agree(lib):
+    """The transposed product reads the lists backwards.  A pair's near/far
+    verdict can differ by direction only through the source cluster's
+    largest element area in the far test: on a mesh of equal elements (the
+    duct's squares) and in direct mode (no far pairs) every list entry has
+    its mirror."""
+    nodes, tris = inputs.duct(3.4, 0.2, 0.05)
+    st = bemfmm.plan_stats_host(nodes, tris, 240.0)
+    assert st["levels"] >= 1 and st["asymmetric_pairs"] == 0
+    nodes, tris = inputs.bumpy_ellipsoid(10)
+    st = bemfmm.plan_stats_host(nodes, tris, 3000.0, params=bemfmm.default_params(mode=bemfmm.MODE_DIRECT))
+    assert st["asymmetric_pairs"] == 0 and st["near_nnz"] == tris.shape[0] ** 2
