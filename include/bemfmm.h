@@ -100,6 +100,12 @@ typedef struct bem_params {
                                a mesh that is not closed and consistently wound or whose normals
                                point into the enclosed volume (bem_mesh_check_host); the paper
                                leaves this to the user (Sec. 2.1).  0: off (default).         */
+    int32_t symmetric_far;  /* 1: a cluster pair is far only if r~ > R_1 holds with the larger
+                               of the two clusters' element areas, so its verdict is the same
+                               both ways and bem_matvec_transpose is the exact transpose of
+                               bem_matvec (asymmetric_pairs = 0) at the cost of a few more
+                               near pairs; 0 (default): the source cluster's area, the bound
+                               r~ of Sec. 3.1.4 needs.  Other values: BEM_E_ARG.              */
 } bem_params;
 
 typedef struct bem_medium {

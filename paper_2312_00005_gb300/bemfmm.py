@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
         ("L_min", ctypes.c_int32), ("admissibility", ctypes.c_double), ("leaf_edge", ctypes.c_double),
         ("stability_max", ctypes.c_double), ("near_store", ctypes.c_int32), ("restart", ctypes.c_int32),
         ("autotune", ctypes.c_int32), ("tau", ctypes.c_double), ("row_scaling", ctypes.c_int32),
-        ("check_orientation", ctypes.c_int32),
+        ("check_orientation", ctypes.c_int32), ("symmetric_far", ctypes.c_int32),
     ]
 
 

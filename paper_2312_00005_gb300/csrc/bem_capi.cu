@@ -1429,6 +1429,7 @@ void bem_params_default(bem_params *p)
     p->tau = 1.0;
     p->row_scaling = 0;
     p->check_orientation = 0;
+    p->symmetric_far = 0;
 }
 
 const char *bem_last_error(void) { return g_err.c_str(); }
@@ -1453,6 +1454,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
     if (p.row_scaling != 0 && p.row_scaling != 1) return set_err(BEM_E_ARG, "row_scaling must be 0 or 1");
     if (p.check_orientation != 0 && p.check_orientation != 1)
         return set_err(BEM_E_ARG, "check_orientation must be 0 or 1");
+    if (p.symmetric_far != 0 && p.symmetric_far != 1) return set_err(BEM_E_ARG, "symmetric_far must be 0 or 1");
     if (!(p.quad_tol > 0) || !(p.rt_subdiv > 0) || !(p.admissibility > 0) || p.L_min < 1 || p.L_min > 200)
         return set_err(BEM_E_ARG, "invalid parameter");
     if (p.check_orientation) {

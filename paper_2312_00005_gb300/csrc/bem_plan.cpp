@@ -462,8 +462,13 @@ void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k,
                         }
                         if (st != -1) {
                             const double dist = off_dist[key];
+                            // r~ of every element pair above R_1: bounded with the
+                            // source cluster's largest area, or with the larger
+                            // of both clusters' (symmetric_far: the same verdict
+                            // both ways, so the lists have mirrors)
+                            const double rb = p.symmetric_far ? std::max(r1sq[c], r1sq[s]) : r1sq[s];
                             far = dist > p.admissibility * (L.rad[c] + L.rad[s]) &&
-                                  dist - L.crad[c] - L.crad[s] > r1sq[s];
+                                  dist - L.crad[c] - L.crad[s] > rb;
                             if (far && st == -3) {
                                 // first far use of this offset: give it a translation row
                                 st = (int32_t)(F.offsets.size() / 3);

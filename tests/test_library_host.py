@@ -186,3 +186,18 @@ def test_plan_lists_symmetric_where_the_verdicts_must_agree(lib):
     nodes, tris = inputs.bumpy_ellipsoid(10)
     st = bemfmm.plan_stats_host(nodes, tris, 3000.0, params=bemfmm.default_params(mode=bemfmm.MODE_DIRECT))
     assert st["asymmetric_pairs"] == 0 and st["near_nnz"] == tris.shape[0] ** 2
+
+
+@pytest.mark.parametrize("mesh,freq", [("ico5", 4000.0), ("head20", 5000.0)])
+def test_symmetric_far_test_gives_mirrored_lists(lib, mesh, freq):
+    """symmetric_far = 1 bounds r~ with the larger of the two clusters'
+    element areas: every list entry then has its mirror (the transposed
+    product is then the exact transpose), the lists still partition all
+    pairs, and only pairs move from the far to the near field."""
+    nodes, tris = inputs.icosphere(5, 0.1) if mesh == "ico5" else inputs.bumpy_ellipsoid(20)
+    n = tris.shape[0]
+    a = bemfmm.plan_stats_host(nodes, tris, freq)
+    b = bemfmm.plan_stats_host(nodes, tris, freq, params=bemfmm.default_params(symmetric_far=1))
+    assert a["asymmetric_pairs"] > 0 and b["asymmetric_pairs"] == 0
+    assert b["near_nnz"] + b["far_pairs"] == n * n
+    assert a["near_nnz"] <= b["near_nnz"] <= 1.5 * a["near_nnz"], (a["near_nnz"], b["near_nnz"])
