@@ -318,7 +318,7 @@ def rhs(cen, nrm, k, sources):
 
 def solve(nodes, tris, freq, c=343.0, rho=1.21, sources=(), bc_type=None, bc_value=None,
           beta=None, tol=1e-8, maxit=2000, restart=300, params=None, return_system=False,
-          row_scaling=False):
+          row_scaling=False, blocks=None):
     """Dense collocation BEM solve (Eq. SystemI) with GMRES.
 
     sources: iterable of (kind, vector, complex amplitude).
@@ -327,6 +327,9 @@ def solve(nodes, tris, freq, c=343.0, rho=1.21, sources=(), bc_type=None, bc_val
     row_scaling: GMRES on D^-1 A u = D^-1 b with D = diag(A), the solver's
     row-scaling preconditioner (Sec. 3.2); tol then applies to the scaled
     residual.
+    blocks: per element a block index; GMRES on P A u = P b with P the
+    inverse of A's block diagonal over those blocks (block-Jacobi, the block
+    form of row scaling; singleton blocks are row scaling).
     Returns (p, q, info) at the element midpoints."""
     tris = _i32(tris)
     n = tris.shape[0]
@@ -347,6 +350,15 @@ def solve(nodes, tris, freq, c=343.0, rho=1.21, sources=(), bc_type=None, bc_val
     if row_scaling:
         dinv = 1.0 / np.diag(A)
         u, info = gmres(A * dinv[:, None], b * dinv, tol=tol, maxit=maxit, restart=restart)
+    elif blocks is not None:
+        blocks = np.asarray(blocks)
+        PA, Pb = np.empty_like(A), np.empty_like(b)
+        for c in np.unique(blocks):
+            idx = np.where(blocks == c)[0]
+            lu = np.linalg.inv(A[np.ix_(idx, idx)])
+            PA[idx] = lu @ A[idx]
+            Pb[idx] = lu @ b[idx]
+        u, info = gmres(PA, Pb, tol=tol, maxit=maxit, restart=restart)
     else:
         u, info = gmres(A, b, tol=tol, maxit=maxit, restart=restart)
     pu = bc_type != PRES
