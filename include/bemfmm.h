@@ -14,7 +14,12 @@
  *   - far field by the plane-wave expansion of Eq. FMMBase with the
  *     truncation of Eq. FMMTruncation and the admissibility of
  *     Eq. Farfieldcond, per level (Sec. 3.3.4: operator
- *     N + sum_l S(l) D(l) T(l)).
+ *     N + sum_l S(l) D(l) T(l));
+ *   - restarted GMRES on the device, optionally row-scaled (Sec. 3.2);
+ *   - beyond the paper: the transposed product and the adjoint gradient of a
+ *     field loss with respect to the region admittances
+ *     (bem_matvec_transpose, bem_admittance_gradient), and an opt-in check
+ *     of the normals' orientation (bem_mesh_check_host).
  *
  * Variables are pressures: p on the surface and q = dp/dn = i w rho v, with
  * n the outward normal (pointing away from the enclosed volume: into the
@@ -28,9 +33,10 @@
  * stated number of elements; the library never frees them.  Work is
  * enqueued on the caller's CUDA stream (a cudaStream_t passed as void*;
  * NULL = the legacy default stream) and is stream-ordered.  bem_solve,
- * bem_solve_sweep, bem_matvec_host and bem_mesh_stats synchronise the stream
- * before they return; bem_matvec, bem_evaluate and bem_evaluate_velocity do
- * not.
+ * bem_solve_sweep, bem_admittance_gradient, bem_matvec_host and
+ * bem_mesh_stats synchronise the stream before they return, and
+ * bem_matvec_transpose waits for its own work (it checks the quadrature's
+ * error flag); bem_matvec, bem_evaluate and bem_evaluate_velocity do not.
  *
  * Errors: every function returns BEM_OK (0), a negative error code, or a
  * positive warning code with all outputs written.  bem_last_error() gives a
