@@ -34,9 +34,10 @@
  * enqueued on the caller's CUDA stream (a cudaStream_t passed as void*;
  * NULL = the legacy default stream) and is stream-ordered.  bem_solve,
  * bem_solve_sweep, bem_admittance_gradient, bem_matvec_host and
- * bem_mesh_stats synchronise the stream before they return, and
- * bem_matvec_transpose waits for its own work (it checks the quadrature's
- * error flag); bem_matvec, bem_evaluate and bem_evaluate_velocity do not.
+ * bem_mesh_stats synchronise the stream before they return;
+ * bem_matvec_transpose, bem_evaluate and bem_evaluate_velocity wait for
+ * their own work (they read the quadrature's error flag) but leave the
+ * caller's stream to its own order; bem_matvec does not wait.
  *
  * Errors: every function returns BEM_OK (0), a negative error code, or a
  * positive warning code with all outputs written.  bem_last_error() gives a
