@@ -47,13 +47,15 @@ def test_combine_ranks_single_process_is_identity():
     assert bench.combine_ranks(1.5, 2.5, 3.0, 4.0) == (1.5, 2.5, 3.0, 4.0)
 
 
-def test_band_workload_reference_arm_reports_unavailable():
-    """The batched-frequency workload has no bounded oracle sample: its
-    reference arm prints one JSON line with "unavailable" and exits 0."""
+@pytest.mark.parametrize("workload", ["head_bands_c3", "head_adjoint_c4"])
+def test_extra_workloads_reference_arm_reports_unavailable(workload):
+    """The batched-frequency and adjoint workloads have no bounded oracle
+    sample: their reference arm prints one JSON line with "unavailable" and
+    exits 0."""
     import json
     import subprocess
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
-                        "head_bands_c3"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+                        workload], capture_output=True, text=True, timeout=300, cwd=ROOT)
     assert r.returncode == 0, r.stderr
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and "unavailable" in line
