@@ -169,6 +169,17 @@ typedef struct bem_plan_stats {
                                    source element), so a pair can be far one way and near
                                    the other; bem_matvec_transpose reads the lists backwards
                                    and applies, on these pairs, the other direction's rule */
+    double  order_R[8];         /* the order thresholds of Sec. 3.1.4 the plan uses: the
+                                   regular order is m when r~ > order_R[m] (m = 1 .. m_max - 1,
+                                   smallest such m), else m_max; order_R[0] = rt_subdiv      */
+    int64_t near_light_entries; /* near pairs under one regular rule of order 1..3 over the
+                                   whole element (the light entry kernel) ...               */
+    int64_t near_light_points;  /* ... and their quadrature points (m^2 each)              */
+    int64_t near_heavy_entries; /* self terms, subdivided pairs and orders 4..6 ...         */
+    int64_t near_heavy_points;  /* ... and their kernel evaluations: a self term takes
+                                   6 x 16 Duffy points and 3 x 4 x 3 edge points, a
+                                   subdivided pair m^2 points per leaf subelement;
+                                   near_quad_points = near_light_points + near_heavy_points */
 } bem_plan_stats;
 
 /* Paper defaults (Sec. 3.1, Eq. FMMTruncation, Eq. Farfieldcond). */
@@ -361,11 +372,15 @@ int bem_selftest_sincos(const void *x_dev, int64_t n, void *out_dev, void *strea
  * compiled into the library (held on every GPU that loads the library until
  * the process exits), so n_tris is limited to 32768; larger meshes are
  * rejected with BEM_E_ARG and a message.  It calls no allocating routine.
- * The first call on a device looks up that array's device address (make it
- * before any stream capture).  All calls on a device share the array and
- * each call overwrites it: calls that overlap on the GPU race.  Work is
- * enqueued on `stream`; the call synchronises that stream before it returns
- * (to report degenerate elements or the subdivision limit). */
+ * The first call on a device (and the first after that device's CUDA
+ * context was replaced, e.g. by cudaDeviceReset) looks up that array's
+ * device address in the current context; later calls reuse it.  All calls on
+ * a device share the array and each call overwrites it: calls that overlap on
+ * the GPU race.  Work is enqueued on `stream`; the call synchronises that
+ * stream before it returns (to report degenerate elements or the subdivision
+ * limit), so it must not be called while that stream is being captured into
+ * a CUDA graph.  medium as for the mesh entry points (NULL, or c <= 0: 343
+ * m/s). */
 int bem_matvec_direct_noalloc(const double *nodes_dev, int64_t n_nodes, const int32_t *tris_dev, int64_t n_tris,
                               double freq_hz, const bem_medium *medium, const void *x_dev, void *y_dev,
                               void *stream);

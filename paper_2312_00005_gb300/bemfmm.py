@@ -70,7 +70,9 @@ class PlanStats(ctypes.Structure):
         ("near_nnz", ctypes.c_int64), ("near_quad_points", ctypes.c_int64), ("leaf_edge", ctypes.c_double),
         ("mean_edge", ctypes.c_double), ("device_bytes", ctypes.c_int64), ("far_pairs", ctypes.c_int64),
         ("n_tuned", ctypes.c_int32), ("tuned_depth", ctypes.c_int32 * 4), ("tuned_seconds", ctypes.c_double * 4),
-        ("asymmetric_pairs", ctypes.c_int64),
+        ("asymmetric_pairs", ctypes.c_int64), ("order_R", ctypes.c_double * 8),
+        ("near_light_entries", ctypes.c_int64), ("near_light_points", ctypes.c_int64),
+        ("near_heavy_entries", ctypes.c_int64), ("near_heavy_points", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -82,7 +84,9 @@ class PlanStats(ctypes.Structure):
             "n_offsets": list(self.n_offsets[:n]), "n_leaves": self.n_leaves, "near_nnz": self.near_nnz,
             "near_quad_points": self.near_quad_points, "leaf_edge": self.leaf_edge,
             "mean_edge": self.mean_edge, "device_bytes": self.device_bytes, "far_pairs": self.far_pairs,
-            "asymmetric_pairs": self.asymmetric_pairs,
+            "asymmetric_pairs": self.asymmetric_pairs, "order_R": list(self.order_R),
+            "near_light_entries": self.near_light_entries, "near_light_points": self.near_light_points,
+            "near_heavy_entries": self.near_heavy_entries, "near_heavy_points": self.near_heavy_points,
             "autotune": [(self.tuned_depth[q], self.tuned_seconds[q]) for q in range(self.n_tuned)],
         }
 
@@ -172,12 +176,26 @@ def selftest_sincos(x):
 def matvec_direct_noalloc(nodes_dev, tris_dev, freq, x, y, c=343.0, rho=1.21, stream=None):
     """Direct sound-hard product that allocates no device memory (see the
     header): nodes_dev float64 [n_nodes, 3], tris_dev int32 [n, 3], x and y
-    complex64 [n], all CUDA tensors owned by the caller."""
+    complex64 [n], all contiguous CUDA tensors on the current device, owned
+    by the caller.  The C entry point cannot see the tensors' shapes, so they
+    are checked here: a wrong shape would make its kernels read past the
+    caller's buffers."""
     import torch
-    for t, dt in ((nodes_dev, torch.float64), (tris_dev, torch.int32)):
+    dev = torch.cuda.current_device()
+    for name, t, dt in (("nodes_dev", nodes_dev, torch.float64), ("tris_dev", tris_dev, torch.int32)):
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
-            raise TypeError("nodes_dev must be float64 and tris_dev int32 contiguous CUDA tensors")
+            raise TypeError("%s must be a contiguous %s CUDA tensor" % (name, dt))
+        if t.dim() != 2 or t.shape[1] != 3:
+            raise ValueError("%s must have shape [*, 3], got %s" % (name, tuple(t.shape)))
     n = tris_dev.shape[0]
+    for name, t in (("x", x), ("y", y)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex64 and t.is_contiguous()):
+            raise TypeError("%s must be a contiguous complex64 CUDA tensor" % name)
+        if t.numel() != n:
+            raise ValueError("%s has %d elements, the mesh %d triangles" % (name, t.numel(), n))
+    for name, t in (("nodes_dev", nodes_dev), ("tris_dev", tris_dev), ("x", x), ("y", y)):
+        if t.device.index != dev:
+            raise ValueError("%s is on cuda:%d, the current device is cuda:%d" % (name, t.device.index, dev))
     med = Medium(float(c), float(rho))
     return _check(lib().bem_matvec_direct_noalloc(ctypes.c_void_p(nodes_dev.data_ptr()), nodes_dev.shape[0],
                                                   ctypes.c_void_p(tris_dev.data_ptr()), n, float(freq),

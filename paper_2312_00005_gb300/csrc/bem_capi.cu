@@ -51,6 +51,48 @@ static std::map<std::string, std::pair<double, int64_t>> g_tacc;
 namespace bem {
 // Sets the calling thread's message returned by bem_last_error.
 void set_last_error(const std::string &msg) { g_err = msg; }
+
+// ------------------------------------------------------------------ tables
+QuadTables make_tables(const bem_params &p)
+{
+    QuadTables Q;
+    memset(&Q, 0, sizeof Q);
+    for (int m = 1; m <= kMaxRule; ++m) {
+        std::vector<double> xi, eta, w;
+        conical_rule(m, xi, eta, w);
+        for (int q = 0; q < m * m; ++q) {
+            Q.tri_xi[m][q] = (float)xi[q];
+            Q.tri_eta[m][q] = (float)eta[q];
+            Q.tri_w[m][q] = (float)w[q];
+        }
+    }
+    std::vector<double> x, w;
+    gauss_legendre01(4, x, w);
+    for (int i = 0; i < 4; ++i) { Q.gl4_x[i] = (float)x[i]; Q.gl4_w[i] = (float)w[i]; }
+    gauss_legendre01(3, x, w);
+    for (int i = 0; i < 3; ++i) { Q.gl3_x[i] = (float)x[i]; Q.gl3_w[i] = (float)w[i]; }
+    double R[kMaxRule + 1] = {0};
+    order_thresholds(p.quad_tol, p.m_max, R);
+    for (int m = 1; m < p.m_max; ++m) {
+        Q.R[m] = (float)R[m];
+        Q.Rd[m] = R[m];
+        Q.R2[m] = (float)(R[m] * R[m]);
+    }
+    Q.heavy_rt2 = p.m_max > 3 ? (float)((R[3] * (1.0 + 1e-5)) * (R[3] * (1.0 + 1e-5))) : 0.f;
+    Q.rt_sub = (float)p.rt_subdiv;
+    Q.rt_sub_d = p.rt_subdiv;
+    Q.m_max = p.m_max;
+    Q.max_depth = p.max_depth;
+    Q.edge_parts = 4;
+    return Q;
+}
+
+// c and rho of a medium (NULL or non-positive values: 343 m/s, 1.21 kg/m^3)
+void medium_of(const bem_medium *m, double &c, double &rho)
+{
+    c = (m && m->c > 0) ? m->c : 343.0;
+    rho = (m && m->rho > 0) ? m->rho : 1.21;
+}
 }  // namespace bem
 
 namespace {
@@ -377,48 +419,7 @@ static inline Frame &fr(bem_mesh_impl &M) { return t_frame ? *t_frame : M.cur; }
 
 namespace {
 
-// ------------------------------------------------------------------ tables
-QuadTables make_tables(const bem_params &p)
-{
-    QuadTables Q;
-    memset(&Q, 0, sizeof Q);
-    for (int m = 1; m <= kMaxRule; ++m) {
-        std::vector<double> xi, eta, w;
-        conical_rule(m, xi, eta, w);
-        for (int q = 0; q < m * m; ++q) {
-            Q.tri_xi[m][q] = (float)xi[q];
-            Q.tri_eta[m][q] = (float)eta[q];
-            Q.tri_w[m][q] = (float)w[q];
-        }
-    }
-    std::vector<double> x, w;
-    gauss_legendre01(4, x, w);
-    for (int i = 0; i < 4; ++i) { Q.gl4_x[i] = (float)x[i]; Q.gl4_w[i] = (float)w[i]; }
-    gauss_legendre01(3, x, w);
-    for (int i = 0; i < 3; ++i) { Q.gl3_x[i] = (float)x[i]; Q.gl3_w[i] = (float)w[i]; }
-    double R[kMaxRule + 1] = {0};
-    order_thresholds(p.quad_tol, p.m_max, R);
-    for (int m = 1; m < p.m_max; ++m) {
-        Q.R[m] = (float)R[m];
-        Q.Rd[m] = R[m];
-        Q.R2[m] = (float)(R[m] * R[m]);
-    }
-    Q.heavy_rt2 = p.m_max > 3 ? (float)((R[3] * (1.0 + 1e-5)) * (R[3] * (1.0 + 1e-5))) : 0.f;
-    Q.rt_sub = (float)p.rt_subdiv;
-    Q.rt_sub_d = p.rt_subdiv;
-    Q.m_max = p.m_max;
-    Q.max_depth = p.max_depth;
-    Q.edge_parts = 4;
-    return Q;
-}
-
 double wavenumber(double f, double c) { return 2.0 * M_PI * f / c; }
-
-void medium_of(const bem_medium *m, double &c, double &rho)
-{
-    c = (m && m->c > 0) ? m->c : 343.0;
-    rho = (m && m->rho > 0) ? m->rho : 1.21;
-}
 
 // ------------------------------------------------------------------ plan
 std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
@@ -1355,9 +1356,15 @@ void join_streams(cudaStream_t from, cudaStream_t to)
 }
 
 
-void fill_stats(const Geometry &g, const Tree &t, const FreqPlan &fp, bem_plan_stats *out)
+void fill_stats(const Geometry &g, const Tree &t, const FreqPlan &fp, const bem_params &p, bem_plan_stats *out)
 {
     memset(out, 0, sizeof *out);
+    {
+        double R[kMaxRule + 1] = {0};
+        order_thresholds(p.quad_tol, std::max(2, p.m_max), R);
+        out->order_R[0] = p.rt_subdiv;
+        for (int m = 1; m < p.m_max && m < 8; ++m) out->order_R[m] = R[m];
+    }
     out->n_elements = g.n;
     out->leaf_level = fp.leaf_depth;
     out->levels = (int)fp.far.size();
@@ -1400,7 +1407,12 @@ void fill_stats(const Geometry &g, const Tree &t, const FreqPlan &fp, bem_plan_s
     out->asymmetric_pairs = asym;
     out->n_leaves = (int)t.lv[fp.leaf_depth].start.size();
     out->near_nnz = fp.nnz;
-    out->near_quad_points = -1;
+    const NearCount nc = count_near_points(g, t, fp, p);
+    out->near_light_entries = nc.light_entries;
+    out->near_light_points = nc.light_points;
+    out->near_heavy_entries = nc.heavy_entries;
+    out->near_heavy_points = nc.heavy_points;
+    out->near_quad_points = nc.light_points + nc.heavy_points;
     out->leaf_edge = t.lv[fp.leaf_depth].box;
     out->mean_edge = g.mean_edge;
 }
@@ -2505,7 +2517,7 @@ int bem_plan_stats_host(const double *nodes, int64_t n_nodes, const int32_t *tri
         build_tree(g, leaf, t);
         FreqPlan fp;
         build_plan(g, t, p, wavenumber(freq_hz, c > 0 ? c : 343.0), fp);
-        fill_stats(g, t, fp, out);
+        fill_stats(g, t, fp, p, out);
         return BEM_OK;
     } catch (std::bad_alloc &) {
         return set_err(BEM_E_OOM, "host allocation failed");
@@ -2525,7 +2537,7 @@ int bem_mesh_stats(void *mesh, double freq_hz, const bem_medium *medium, bem_pla
         build_plan_dev(M, freq_hz, c);
         ck(cudaStreamSynchronize(M.s), "sync");
         Plan &P = *fr(M).plan;
-        fill_stats(M.g, M.t, P.fp(), out);
+        fill_stats(M.g, M.t, P.fp(), M.prm, out);
         for (size_t l = 0; l < P.lev.size() && l < 16; ++l) out->L[l] = P.lev[l]->L;
         out->n_tuned = (int)std::min<size_t>(4, M.tune_log.size());
         for (int q = 0; q < out->n_tuned; ++q) {

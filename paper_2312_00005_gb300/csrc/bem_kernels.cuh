@@ -1,6 +1,7 @@
 // bem_kernels.cuh -- kernel argument blocks and kernel declarations.
 #pragma once
 
+#include "../../include/bemfmm.h"
 #include "bem_device.cuh"
 
 namespace bem {
@@ -239,5 +240,11 @@ __global__ void k_gm_xupdate(float2 *x, const float2 *V, int64_t n, const GmresS
 __global__ void k_gm_start(GmresState *st, float2 *V, const float2 *r, int64_t n, const double *normpart, int nblk,
                            double2 *g, int m, int first);
 __global__ void k_norm_part(const float2 *r, int64_t n, double *part);
+
+// Host helpers shared by the translation units (bem_capi.cu): the
+// quadrature tables of a parameter set (conical rules m = 1..6, the Duffy and
+// edge rules, the order thresholds of Sec. 3.1.4) and the medium defaults.
+QuadTables make_tables(const bem_params &p);
+void medium_of(const bem_medium *m, double &c, double &rho);
 
 }  // namespace bem

@@ -37,7 +37,17 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
+// The scratch address of each device, with the id of the CUDA context it
+// was looked up in: a context created anew (after cudaDeviceReset, or a
+// different primary context) loads the module again, and the symbol may then
+// live elsewhere, so the address is looked up again whenever the current
+// context's id differs from the cached one.
+struct ScratchAddr {
+    unsigned long long ctx_id = 0;
+    bool valid = false;
+    void *p = nullptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
 
 // messages go to the library's per-thread error text (bem_last_error)
 int fail(int code, const std::string &msg)
@@ -128,19 +138,54 @@ __global__ void k_noalloc_clear(int *err, QuadTables q, QuadTables *out)
     }
 }
 
-// Device address of the scratch array on the current device; looked up once
-// per device (the first call on a device does this).
+// Id of the calling thread's current CUDA context (driver entry points
+// queried through the runtime, so the library needs no link to the driver
+// library); false when there is none yet or the query is unavailable.
+bool current_context_id(unsigned long long *id)
+{
+    typedef int (*GetCurrentFn)(void **);
+    typedef int (*GetIdFn)(void *, unsigned long long *);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f0 = nullptr, *f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) == cudaSuccess &&
+            q0 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess) {
+            get_current = (GetCurrentFn)f0;
+            get_id = (GetIdFn)f1;
+        }
+    }
+    if (!get_current || !get_id) return false;
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
+
+// Device address of the scratch array on the current device (which the
+// caller has made current).  Looked up once per device and context: the
+// first call on a device, and the first after its context changed, call
+// cudaGetSymbolAddress; later calls reuse the address.
 int scratch_address(int dev, unsigned char **out)
 {
     if (dev < 0 || dev >= kMaxDevices) return fail(BEM_E_ARG, "device index out of range");
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchAddr &c = g_scratch_addr[dev];
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
+    if (!(have_id && c.valid && c.ctx_id == id)) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) return fail(BEM_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_scratch_ptr[dev] = p;
+        c.p = p;
+        // the lookup made a context current if there was none
+        c.valid = current_context_id(&c.ctx_id);
     }
-    *out = (unsigned char *)g_scratch_ptr[dev];
+    *out = (unsigned char *)c.p;
     return BEM_OK;
 }
 
@@ -167,37 +212,14 @@ extern "C" int bem_matvec_direct_noalloc(const double *nodes_dev, int64_t n_node
     unsigned char *base = nullptr;
     int st = scratch_address(dev, &base);
     if (st != BEM_OK) return st;
-    const double c = (medium && medium->c > 0) ? medium->c : 343.0;
+    double c = 343.0, rho = 1.21;
+    medium_of(medium, c, rho);
     const double k = 2.0 * M_PI * freq_hz / c;
     bem_params prm;
     bem_params_default(&prm);
-    // quadrature tables of the paper's default rules (host generator, copied in)
-    QuadTables Q;
-    {
-        std::vector<double> xi, eta, w;
-        memset(&Q, 0, sizeof Q);
-        for (int m = 1; m <= kMaxRule; ++m) {
-            conical_rule(m, xi, eta, w);
-            for (int q = 0; q < m * m; ++q) {
-                Q.tri_xi[m][q] = (float)xi[q];
-                Q.tri_eta[m][q] = (float)eta[q];
-                Q.tri_w[m][q] = (float)w[q];
-            }
-        }
-        std::vector<double> x, wt;
-        gauss_legendre01(4, x, wt);
-        for (int i = 0; i < 4; ++i) { Q.gl4_x[i] = (float)x[i]; Q.gl4_w[i] = (float)wt[i]; }
-        gauss_legendre01(3, x, wt);
-        for (int i = 0; i < 3; ++i) { Q.gl3_x[i] = (float)x[i]; Q.gl3_w[i] = (float)wt[i]; }
-        double R[kMaxRule + 1] = {0};
-        order_thresholds(prm.quad_tol, prm.m_max, R);
-        for (int m = 1; m < prm.m_max; ++m) { Q.R[m] = (float)R[m]; Q.Rd[m] = R[m]; }
-        Q.rt_sub = (float)prm.rt_subdiv;
-        Q.rt_sub_d = prm.rt_subdiv;
-        Q.m_max = prm.m_max;
-        Q.max_depth = prm.max_depth;
-        Q.edge_parts = 4;
-    }
+    // quadrature tables of the paper's default rules (the mesh set-up's
+    // generator), copied into the scratch array by value
+    const QuadTables Q = make_tables(prm);
     cudaStream_t s = (cudaStream_t)stream;
     k_noalloc_clear<<<1, 32, 0, s>>>((int *)(base + lay.err), Q, (QuadTables *)(base + lay.Q));
     k_noalloc_geometry<<<(unsigned)((n_tris + 255) / 256), 256, 0, s>>>(nodes_dev, n_nodes, tris_dev, n_tris, base,

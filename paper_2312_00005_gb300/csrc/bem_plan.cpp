@@ -521,6 +521,85 @@ void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k,
         }
 }
 
+// Kernel evaluations of one near pair (row element at x, column element e):
+// the whole element under one regular rule, or the subdivision of Sec. 3.1.3
+// into four children (midpoint, vertex, edge midpoints) while r~ < rt_sub.
+static int64_t pair_points(const Geometry &g, const double *x, int64_t e, const double *R, const bem_params &p)
+{
+    auto order = [&](double rt) {
+        for (int m = 1; m < p.m_max; ++m)
+            if (rt > R[m]) return m;
+        return p.m_max;
+    };
+    struct Sub { double x0, y0, x1, y1, x2, y2; int depth; };
+    std::vector<Sub> st{{0.0, 0.0, 1.0, 0.0, 0.0, 1.0, 0}};
+    int64_t pts = 0;
+    while (!st.empty()) {
+        const Sub s = st.back();
+        st.pop_back();
+        const double cx = (s.x0 + s.x1 + s.x2) / 3.0, cy = (s.y0 + s.y1 + s.y2) / 3.0;
+        double d[3];
+        for (int q = 0; q < 3; ++q)
+            d[q] = g.cen[3 * e + q] + g.va[3 * e + q] + cx * g.e1[3 * e + q] + cy * g.e2[3 * e + q] - x[q];
+        const double rt = norm3(d) / std::sqrt(g.area[e] * std::ldexp(1.0, -2 * s.depth));
+        if (rt >= p.rt_subdiv || s.depth >= p.max_depth) {
+            const int m = order(rt);
+            pts += (int64_t)m * m;
+            continue;
+        }
+        const double mx01 = 0.5 * (s.x0 + s.x1), my01 = 0.5 * (s.y0 + s.y1);
+        const double mx12 = 0.5 * (s.x1 + s.x2), my12 = 0.5 * (s.y1 + s.y2);
+        const double mx20 = 0.5 * (s.x2 + s.x0), my20 = 0.5 * (s.y2 + s.y0);
+        const int dd = s.depth + 1;
+        st.push_back({mx01, my01, mx12, my12, mx20, my20, dd});
+        st.push_back({mx20, my20, mx12, my12, s.x2, s.y2, dd});
+        st.push_back({mx01, my01, s.x1, s.y1, mx12, my12, dd});
+        st.push_back({s.x0, s.y0, mx01, my01, mx20, my20, dd});
+    }
+    return pts;
+}
+
+NearCount count_near_points(const Geometry &g, const Tree &t, const FreqPlan &fp, const bem_params &p)
+{
+    NearCount c;
+    double R[kMaxRule + 1] = {0};
+    order_thresholds(p.quad_tol, std::max(2, p.m_max), R);
+    // the light / heavy split of the entry kernels: light when r~ is above
+    // R_3 (1 + 1e-5), so that one rule of order 1..3 covers the element
+    const double heavy_rt2 = p.m_max > 3 ? (R[3] * (1.0 + 1e-5)) * (R[3] * (1.0 + 1e-5)) : 0.0;
+    const Level &Lf = t.lv[fp.leaf_depth];
+    const int nl = (int)Lf.start.size();
+    for (int a = 0; a < nl; ++a) {
+        for (int64_t ii = Lf.start[a]; ii < Lf.start[a] + Lf.count[a]; ++ii) {
+            const int64_t ei = t.perm[ii];
+            const double *x = &g.cen[3 * ei];
+            for (int q = fp.near_ptr[a]; q < fp.near_ptr[a + 1]; ++q) {
+                const int b = fp.near_src[q];
+                for (int64_t jj = Lf.start[b]; jj < Lf.start[b] + Lf.count[b]; ++jj) {
+                    const int64_t ej = t.perm[jj];
+                    if (ej == ei) {
+                        c.heavy_entries += 1;
+                        c.heavy_points += 6 * 16 + 3 * 4 * 3;
+                        continue;
+                    }
+                    double d[3];
+                    sub3(&g.cen[3 * ej], x, d);
+                    const double rt2 = dot3(d, d) / g.area[ej];
+                    if (p.m_max > 3 && !(rt2 > heavy_rt2)) {
+                        c.heavy_entries += 1;
+                        c.heavy_points += pair_points(g, x, ej, R, p);
+                    } else {
+                        const int m = rt2 > R[1] * R[1] ? 1 : (rt2 > R[2] * R[2] ? 2 : 3);
+                        c.light_entries += 1;
+                        c.light_points += (int64_t)m * m;
+                    }
+                }
+            }
+        }
+    }
+    return c;
+}
+
 MeshCheck check_mesh(const Geometry &g, const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n)
 {
     MeshCheck r;

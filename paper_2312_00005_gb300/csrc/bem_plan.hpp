@@ -127,6 +127,17 @@ struct FreqPlan {
     int max_L = 0;
 };
 
+// Quadrature work of the near field of a plan (the rules of Sec. 3.1 as the
+// entry kernels apply them): entries under one regular rule of order 1..3
+// over the whole element ("light") and the rest (self terms, subdivided
+// pairs, orders 4..6: "heavy"), with their kernel evaluations.  Rule
+// decisions in FP64 (the device decides in FP32 with an FP64 fallback within
+// 1e-5 of a threshold, so both agree).
+struct NearCount {
+    int64_t light_entries = 0, light_points = 0, heavy_entries = 0, heavy_points = 0;
+};
+NearCount count_near_points(const Geometry &g, const Tree &t, const FreqPlan &fp, const bem_params &p);
+
 // Sets the calling thread's message returned by bem_last_error.
 void set_last_error(const std::string &msg);
 

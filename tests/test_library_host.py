@@ -201,3 +201,45 @@ def test_symmetric_far_test_gives_mirrored_lists(lib, mesh, freq):
     assert a["asymmetric_pairs"] > 0 and b["asymmetric_pairs"] == 0
     assert b["near_nnz"] + b["far_pairs"] == n * n
     assert a["near_nnz"] <= b["near_nnz"] <= 1.5 * a["near_nnz"], (a["near_nnz"], b["near_nnz"])
+
+
+def _golden_thresholds():
+    path = os.path.join(ROOT, "tests", "golden", "order_thresholds.txt")
+    rows = []
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            tol, m, _, R = line.split()
+            rows.append((float(tol), int(m), float(R)))
+    return rows
+
+
+@pytest.mark.parametrize("tol", [1e-3, 1e-6])
+def test_library_order_thresholds_match_hand_derived_values(lib, tol):
+    """The library's order thresholds (its own Golub-Welsch / order code,
+    independent of the oracle's) against the values derived by hand from
+    the three a-priori estimates of Sec. 3.1.4 (tests/golden/order_thresholds.txt).
+    The oracle is pinned to the same file, so a misreading both shared would
+    fail here.  R_1 at 1e-3 is also the library's far-field bound."""
+    nodes, tris = inputs.icosphere(2, 0.1)
+    p = bemfmm.default_params(quad_tol=tol)
+    st = bemfmm.plan_stats_host(nodes, tris, 1000.0, params=p)
+    R = st["order_R"]
+    assert R[0] == 1.3                    # the subdivision bound of Sec. 3.1.3
+    for t, m, Rm in _golden_thresholds():
+        if t == tol:
+            assert abs(R[m] - Rm) < 2e-6 * Rm, (tol, m, R[m], Rm)
+
+
+def test_near_quadrature_counts_cover_the_near_field(lib):
+    """The near-field work counts (rules of Sec. 3.1 per near pair) add up
+    to the near pairs; every element's self term is heavy (Duffy + edge
+    rule: 132 kernel evaluations); light entries take 1, 4 or 9 points."""
+    nodes, tris = inputs.icosphere(4, 0.1)
+    n = tris.shape[0]
+    st = bemfmm.plan_stats_host(nodes, tris, 2000.0)
+    assert st["near_light_entries"] + st["near_heavy_entries"] == st["near_nnz"]
+    assert st["near_heavy_entries"] >= n
+    assert st["near_heavy_points"] >= 132 * n
+    assert st["near_light_entries"] <= st["near_light_points"] <= 9 * st["near_light_entries"]
+    assert st["near_quad_points"] == st["near_light_points"] + st["near_heavy_points"]

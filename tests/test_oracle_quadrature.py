@@ -1,6 +1,7 @@
 """Pins of the oracle's quadrature and kernels against closed forms, library
 routines and brute force (CPU only)."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -60,6 +61,39 @@ def test_quad_order_monotone_and_capped():
     assert ms[0] == 6 and ms[-1] == 1
     assert all(a >= b for a, b in zip(ms, ms[1:]))
     assert oracle.quad_order(0.5) == 6          # capped
+
+
+def order_thresholds_golden():
+    """(tol, m, binding estimate, R_m) rows of tests/golden/order_thresholds.txt:
+    the r~ above which order m meets all three a-priori estimates of
+    Sec. 3.1.4, derived by hand there from the printed formulas."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "order_thresholds.txt")
+    rows = []
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        tol, m, est, R = line.split()
+        rows.append((float(tol), int(m), est, float(R)))
+    return rows
+
+
+@pytest.mark.parametrize("tol,m,est,R", order_thresholds_golden())
+def test_quad_order_switches_at_the_hand_derived_thresholds(tol, m, est, R):
+    """Just above R_m order m suffices, just below it order m + 1 is needed.
+    Each estimate binds in some row (eps_G at m = 1, eps_H at m = 2, eps_E at
+    m = 3..5 for tol 1e-3; eps_G at m = 2 and eps_H at m = 3 for tol 1e-6),
+    so a wrong constant or exponent in any of the three moves a threshold by
+    far more than the 1e-5 margin used here."""
+    assert oracle.quad_order(R * (1 + 1e-5), tol) == m, (tol, m, est)
+    assert oracle.quad_order(R * (1 - 1e-5), tol) == m + 1, (tol, m, est)
+
+
+def test_quad_order_cap_at_six():
+    """Below R_5 the estimates would ask for m = 7 and more; the paper caps m at 6."""
+    R5 = [r for (t, m, _, r) in order_thresholds_golden() if t == 1e-3 and m == 5][0]
+    for rt in (R5 * (1 - 1e-5), 1.5, 1.31):
+        assert oracle.quad_order(rt) == 6
 
 
 # ------------------------------------------------------------------ kernels
