@@ -413,11 +413,14 @@ def residual_vs_fp64(W, p, args, nrows=48):
     return {"fp64_residual_sampled_rows": float(np.linalg.norm(Ap - b) / np.linalg.norm(b)), "rows": nrows}
 
 
-# DRAM traffic of one k_near_spmv_items launch (dram__bytes_read.sum +
-# dram__bytes_write.sum) from an ncu capture of this workload with the tree
-# the timed run chooses; valid only while the kernel's source and launch and
-# the plan (near_nnz) are the ones captured.  The capture command and its
-# figures are in profiles/k_near_spmv_items_sphere20480_4k.md.
+# DRAM traffic of one k_near_spmv_items launch from an ncu capture of this
+# workload with the tree the timed run chooses (leaf depth 4):
+# dram__bytes_read.sum 288.49 MB + dram__bytes_write.sum 3.15 MB = 291.64 MB,
+# 1.014 x the algorithmic 287.7 MB, taken with
+#   ncu --set full --clock-control none -k regex:k_near_spmv_items -s 45 -c 1 \
+#       python bench.py --steps 1 --warmup 3 --no-cpu-baseline --leaf-edge 0.0126
+# Valid only while the kernel's source and launch and the plan (near_nnz)
+# are the ones captured (the source hash below guards it).
 SPMV_TRAFFIC = {"source_sha256": "32082caf313f0d59cf420cac3dee7d59af1bd02e739ef517ed2c5684672ba875",
                 "near_nnz": 35925668, "bytes": 291635968}
 

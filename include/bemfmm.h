@@ -385,6 +385,22 @@ int bem_matvec_direct_noalloc(const double *nodes_dev, int64_t n_nodes, const in
                               double freq_hz, const bem_medium *medium, const void *x_dev, void *y_dev,
                               void *stream);
 
+/* Test hooks for the library's own failure paths (no counterpart in the
+ * paper), so that tests reach them without a GPU fault.  Process-wide; each
+ * call sets both hooks.
+ *   alloc_fail_after >= 0: that many further device allocations succeed and
+ *     the next one is refused without calling cudaMalloc (the entry point
+ *     returns BEM_E_OOM and frees what it had allocated); < 0: off.
+ *   barrier_polls > 0: the grid barriers of the GMRES Gram-Schmidt step
+ *     withhold their release and every wait gives up after barrier_polls
+ *     polls, as a block that never arrives would make it (bem_solve returns
+ *     BEM_E_TIMEOUT; the mesh stays usable); 0: off (the waits give up after
+ *     2^23 polls, which a healthy launch never reaches).
+ *   live_device_bytes (may be NULL): bytes the library holds in device
+ *     allocations (every mesh's buffers) at the time of the call.
+ * Errors: BEM_E_ARG (barrier_polls < 0). */
+int bem_test_hooks(int64_t alloc_fail_after, int32_t barrier_polls, int64_t *live_device_bytes);
+
 /* Number of kernels this library has launched in this process. */
 uint64_t bem_launch_count(void);
 

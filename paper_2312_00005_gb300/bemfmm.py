@@ -132,6 +132,7 @@ def lib():
                                               ctypes.POINTER(ctypes.c_int64)]),
             "bem_selftest_sincos": (ctypes.c_int, [P, i64, P, P]),
             "bem_matvec_direct_noalloc": (ctypes.c_int, [P, i64, P, i64, d, ctypes.POINTER(Medium), P, P, P]),
+            "bem_test_hooks": (ctypes.c_int, [i64, i32, ctypes.POINTER(i64)]),
             "bem_launch_count": (ctypes.c_uint64, []),
             "bem_last_error": (ctypes.c_char_p, []),
         }
@@ -141,6 +142,14 @@ def lib():
             f.argtypes = args
         _lib = L
     return _lib
+
+
+def test_hooks(alloc_fail_after=-1, barrier_polls=0) -> int:
+    """Set the failure-path test hooks (see bem_test_hooks in the header);
+    returns the bytes the library holds in device allocations."""
+    live = ctypes.c_int64(0)
+    _check(lib().bem_test_hooks(int(alloc_fail_after), int(barrier_polls), ctypes.byref(live)))
+    return live.value
 
 
 def launch_count() -> int:
@@ -181,7 +190,6 @@ def matvec_direct_noalloc(nodes_dev, tris_dev, freq, x, y, c=343.0, rho=1.21, st
     are checked here: a wrong shape would make its kernels read past the
     caller's buffers."""
     import torch
-    dev = torch.cuda.current_device()
     for name, t, dt in (("nodes_dev", nodes_dev, torch.float64), ("tris_dev", tris_dev, torch.int32)):
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
             raise TypeError("%s must be a contiguous %s CUDA tensor" % (name, dt))
@@ -193,6 +201,7 @@ def matvec_direct_noalloc(nodes_dev, tris_dev, freq, x, y, c=343.0, rho=1.21, st
             raise TypeError("%s must be a contiguous complex64 CUDA tensor" % name)
         if t.numel() != n:
             raise ValueError("%s has %d elements, the mesh %d triangles" % (name, t.numel(), n))
+    dev = torch.cuda.current_device()
     for name, t in (("nodes_dev", nodes_dev), ("tris_dev", tris_dev), ("x", x), ("y", y)):
         if t.device.index != dev:
             raise ValueError("%s is on cuda:%d, the current device is cuda:%d" % (name, t.device.index, dev))

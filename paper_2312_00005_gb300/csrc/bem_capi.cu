@@ -180,6 +180,29 @@ void resolve_timing()
 // Device array with grow-only capacity: alloc() reuses the allocation when
 // it is large enough, so buffers handed from one plan to the next are not
 // reallocated.
+// Test hooks (bem_test_hooks): the number of device allocations still
+// allowed before one is reported as failed (-1: no limit), and the bytes the
+// library holds in device allocations.
+std::atomic<int64_t> g_alloc_budget{-1};
+std::atomic<int64_t> g_live_bytes{0};
+// polls of a Gram-Schmidt grid-barrier wait with the release withheld (0: off)
+std::atomic<int32_t> g_barrier_polls{0};
+
+void dev_malloc(void **p, size_t bytes)
+{
+    for (;;) {
+        int64_t b = g_alloc_budget.load();
+        if (b < 0) break;
+        if (b == 0) {
+            g_err = "device allocation of " + std::to_string(bytes) + " bytes refused by the test hook";
+            throw Fail{BEM_E_OOM};
+        }
+        if (g_alloc_budget.compare_exchange_weak(b, b - 1)) break;
+    }
+    ck(cudaMalloc(p, bytes), "cudaMalloc");
+    g_live_bytes += (int64_t)bytes;
+}
+
 template <typename T>
 struct DevArr {
     T *p = nullptr;
@@ -190,7 +213,10 @@ struct DevArr {
     ~DevArr() { release(); }
     void release()
     {
-        if (p) cudaFree(p);
+        if (p) {
+            cudaFree(p);
+            g_live_bytes -= (int64_t)(cap * sizeof(T));
+        }
         p = nullptr;
         n = cap = 0;
     }
@@ -199,7 +225,7 @@ struct DevArr {
         if (count <= cap && p) { n = count; return; }
         release();
         if (count == 0) return;
-        ck(cudaMalloc((void **)&p, count * sizeof(T)), "cudaMalloc");
+        dev_malloc((void **)&p, count * sizeof(T));
         n = cap = count;
     }
     void swap(DevArr &o)
@@ -1214,10 +1240,17 @@ void autotune_leaf_depth(bem_mesh_impl &M, double k)
     tcq.upload(h0, M.s);
     tx.upload(hx, M.s);
     ty.alloc(n);
-    cudaEvent_t e0, e1, e2;
-    ck(cudaEventCreate(&e0), "event");
-    ck(cudaEventCreate(&e1), "event");
-    ck(cudaEventCreate(&e2), "event");
+    // events destroyed on every exit (a failed allocation throws from here)
+    struct Events {
+        cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+        ~Events()
+        {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    for (cudaEvent_t &x : ev.e) ck(cudaEventCreate(&x), "event");
+    cudaEvent_t e0 = ev.e[0], e1 = ev.e[1], e2 = ev.e[2];
     std::vector<std::tuple<int, double, std::shared_ptr<Lists>>> cand;
     for (int d = M.leaf_depth - 1; d <= M.leaf_depth + 1; ++d) {
         if (d < 1 || d > M.t.leaf_depth) continue;
@@ -1231,8 +1264,14 @@ void autotune_leaf_depth(bem_mesh_impl &M, double k)
         P->k = k;
         P->lists = lists;
         finish_plan(M, *P);
-        std::unique_ptr<Plan> keep;
-        keep.swap(fr(M).plan);
+        // the frame's plan is the candidate while it is timed; the guard
+        // puts the previous one back on every exit
+        struct Restore {
+            std::unique_ptr<Plan> &slot;
+            std::unique_ptr<Plan> keep;
+            ~Restore() { slot.swap(keep); }
+        } restore{fr(M).plan, nullptr};
+        restore.keep.swap(fr(M).plan);
         fr(M).plan = std::move(P);
         fr(M).plan->val.alloc((size_t)fr(M).plan->nnz());
         ck(cudaEventRecord(e0, M.s), "record");
@@ -1257,12 +1296,7 @@ void autotune_leaf_depth(bem_mesh_impl &M, double k)
         const double cost = 1e-3 * (ms_store + 40.0 * ms_mv / 3.0);
         M.tune_log.push_back({d, cost});
         cand.emplace_back(d, cost, lists);
-        fr(M).plan.reset();
-        fr(M).plan.swap(keep);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaEventDestroy(e2);
     // Another depth replaces the automatic one only when it is at least 3%
     // faster, so that near ties do not flip between runs.
     std::shared_ptr<Lists> best;
@@ -1784,6 +1818,11 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     oa.bar = M.gbar.p;
     oa.err = &M.st.p->fault;
     oa.rows = orows;
+    {
+        const int32_t polls = g_barrier_polls.load();
+        oa.spin_limit = polls > 0 ? (unsigned int)polls : kSpinLimit;
+        oa.hold_release = polls > 0 ? 1 : 0;
+    }
     // one Arnoldi step: product of v_j (inputs already formed), then the
     // fused Gram-Schmidt / Givens step, which also forms v_{j+1}
     const bool use_graph = !g_timing;
@@ -2479,6 +2518,15 @@ int bem_timing_get(const char *name, double *total_ms, int64_t *launches)
     if (it == g_tacc.end()) { *total_ms = 0.0; *launches = 0; return set_err(BEM_E_ARG, "kernel never timed"); }
     *total_ms = it->second.first;
     *launches = it->second.second;
+    return BEM_OK;
+}
+
+int bem_test_hooks(int64_t alloc_fail_after, int32_t barrier_polls, int64_t *live_device_bytes)
+{
+    if (barrier_polls < 0) return set_err(BEM_E_ARG, "barrier_polls must be >= 0");
+    g_alloc_budget.store(alloc_fail_after < 0 ? -1 : alloc_fail_after);
+    g_barrier_polls.store(barrier_polls);
+    if (live_device_bytes) *live_device_bytes = g_live_bytes.load();
     return BEM_OK;
 }
 

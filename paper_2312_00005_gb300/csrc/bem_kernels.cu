@@ -1407,16 +1407,17 @@ __device__ void gm_givens_warp(const GmresArgs &a, double nn, int j)
 
 // Grid barrier of a cooperative launch.  Thread 0 of each block arrives on
 // bar[0]; the last arrival resets it and advances the generation bar[1].
-// A wait gives up after kSpinLimit polls and sets *err, so a lost block can
-// never hang the GPU (the host reports the error).
-constexpr unsigned int kSpinLimit = 1u << 23;
+// A wait gives up after `limit` polls (kSpinLimit unless a test shortens it)
+// and sets *err, so a lost block can never hang the GPU (the host reports
+// the error).  hold: the last arrival does not advance the generation (a
+// release that never comes, for the test of the give-up path).
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
 {
     unsigned int v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void grid_barrier(unsigned int *bar, int *err)
+__device__ __forceinline__ void grid_barrier(unsigned int *bar, int *err, unsigned int limit, int hold)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1425,13 +1426,13 @@ __device__ __forceinline__ void grid_barrier(unsigned int *bar, int *err)
         if (atomicAdd(bar, 1u) == gridDim.x - 1) {
             atomicExch(bar, 0u);
             __threadfence();
-            atomicAdd(bar + 1, 1u);
+            if (!hold) atomicAdd(bar + 1, 1u);
         } else {
             // polls are plain acquire loads (served by L2 without
             // serialising behind the arrivals, unlike atomics)
             unsigned int it = 0;
             while (ld_acquire_gpu(bar + 1) == g0) {
-                if (++it > kSpinLimit || *(volatile int *)err) {
+                if (++it > limit || *(volatile int *)err) {
                     atomicExch(err, 1);
                     break;
                 }
@@ -1569,7 +1570,7 @@ __global__ void __launch_bounds__(kOrthoThreads) k_gm_ortho(OrthoArgs a)
                 if (lane == 0 && l0 + u <= j) part[(int64_t)(l0 + u) * G + b] = d;
             }
         }
-        grid_barrier(a.bar, a.err);
+        grid_barrier(a.bar, a.err, a.spin_limit, a.hold_release);
         // block b reduces columns b, b + G, ... (<= j)
         if (warp == 0)
             for (int l = b; l <= j; l += G) {
@@ -1583,7 +1584,7 @@ __global__ void __launch_bounds__(kOrthoThreads) k_gm_ortho(OrthoArgs a)
                     else { const double2 h0 = __ldcg(hp); *hp = make_double2(h0.x + h.x, h0.y + h.y); }
                 }
             }
-        grid_barrier(a.bar, a.err);
+        grid_barrier(a.bar, a.err, a.spin_limit, a.hold_release);
         for (int l = threadIdx.x; l <= j; l += kOrthoThreads) {
             const double2 h = __ldcg(g.hcol + l);
             hs[l] = make_float2((float)h.x, (float)h.y);
@@ -1639,7 +1640,7 @@ __global__ void __launch_bounds__(kOrthoThreads) k_gm_ortho(OrthoArgs a)
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) npart[b] = make_float2(v, 0.f);
         }
-        grid_barrier(a.bar, a.err);
+        grid_barrier(a.bar, a.err, a.spin_limit, a.hold_release);
         if (warp == 0) {
             const FF v = warp_sum_ff(npart, G);
             if (lane == 0) s_nn = (double)v.hi.x + (double)v.lo.x;

@@ -228,7 +228,12 @@ struct OrthoArgs {
     unsigned int *bar;       // [2] grid barrier: arrivals, generation (zero at the first launch)
     int *err;                // &st->fault
     int rows;                // rows of the basis per block
+    unsigned int spin_limit; // polls after which a barrier wait gives up (kSpinLimit)
+    int hold_release;        // test hook: the last arrival never releases the others, so
+                             // every wait runs out after spin_limit polls (0: off)
 };
+// polls of a grid-barrier wait before it gives up and sets the fault flag
+constexpr unsigned int kSpinLimit = 1u << 23;
 constexpr int kOrthoThreads = 256;
 constexpr int kOrthoMaxBlocks = 512;   // partials per reduction: 32 lanes x 16 loads
 constexpr int kOrthoMaxRows = 1024;    // rows per block staged in shared memory

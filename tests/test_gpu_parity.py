@@ -36,6 +36,41 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def _elem(a, b):
+    """max_i |a_i - b_i| / max(|b_i|, 1e-3 max_j |b_j|): the largest error of
+    one element relative to its own size (floored at 1e-3 of the largest
+    element, so that an element near zero by cancellation is not divided by
+    almost nothing).  A wrong entry confined to a few rows shows here at its
+    own size, where the l2 norm would dilute it by sqrt(N)."""
+    a = np.asarray(a, np.complex128)
+    b = np.asarray(b, np.complex128)
+    s = np.maximum(np.abs(b), 1e-3 * np.abs(b).max())
+    return float(np.max(np.abs(a - b) / s))
+
+
+def _check(a, b, l2, el, what=""):
+    """Relative l2 error below l2 and per-element error (_elem) below el."""
+    e2, ee = _rel(a, b), _elem(a, b)
+    print("%s: rel l2 %.3g (bound %.0e), per element %.3g (bound %.0e)" % (what, e2, l2, ee, el))
+    assert e2 < l2, (what, e2, l2)
+    assert ee < el, (what, ee, el)
+    return e2, ee
+
+
+def _rt_min(nodes, tris):
+    """Per row: the smallest r~ = |x_i - x_j| / sqrt(A_j) over j != i (Sec.
+    3.1.3; below 1.3 the pair is subdivided)."""
+    cen, _, area = oracle.geometry(nodes, tris)
+    n = cen.shape[0]
+    out = np.empty(n)
+    for i0 in range(0, n, 512):
+        d = np.linalg.norm(cen[i0:i0 + 512, None, :] - cen[None, :, :], axis=2) / np.sqrt(area)[None, :]
+        for r in range(d.shape[0]):
+            d[r, i0 + r] = np.inf
+        out[i0:i0 + 512] = d.min(axis=1)
+    return out
+
+
 def _mixed_bc(n, seed):
     rng = np.random.default_rng(seed)
     bct = rng.integers(0, 3, n).astype(np.int32)
@@ -62,8 +97,15 @@ def test_direct_matvec_matches_oracle(bem, lev, freq):
     cp, cq = _oracle_coeffs(bct, region, adm, k)
     A = oracle.assemble(nodes, tris, k, cp, cq)
     yo = A @ x
-    err = _rel(y.cpu().numpy(), yo)
-    assert err < 2e-5, err
+    yn = y.cpu().numpy()
+    _check(yn, yo, 2e-5, 2e-4, "direct product")
+    # rows whose near field holds a subdivided pair (r~ < 1.3, Sec. 3.1.3) and
+    # rows of each boundary type, each group on its own
+    sub = _rt_min(nodes, tris) < 1.3
+    assert sub.sum() > n // 2
+    _check(yn[sub], yo[sub], 2e-5, 2e-4, "rows with subdivided pairs")
+    for t in (0, 1, 2):
+        _check(yn[bct == t], yo[bct == t], 2e-5, 2e-4, "rows of boundary type %d" % t)
 
 
 def test_fmm_matvec_matches_oracle(bem):
@@ -79,17 +121,13 @@ def test_fmm_matvec_matches_oracle(bem):
     cp, cq = _oracle_coeffs(bct, region, adm, k)
     A = oracle.assemble(nodes, tris, k, cp, cq)
     yo = A @ x
-    errs = {}
-    for tf in (1.8, 6.0):
+    for tf, l2, el in ((1.8, 2e-3, 2e-2), (6.0, 1e-4, 1e-3)):
         mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region, trunc_factor=tf)
         st = mesh.stats(freq, c=C)
         assert st["levels"] >= 2
         y = mesh.matvec(freq, torch.tensor(x, dtype=torch.complex64, device="cuda"), admittance=adm, c=C, rho=RHO)
-        errs[tf] = _rel(y.cpu().numpy(), yo)
+        _check(y.cpu().numpy(), yo, l2, el, "fmm product, factor %g" % tf)
         mesh.close()
-    print("fmm matvec rel err", errs)
-    assert errs[1.8] < 2e-3, errs
-    assert errs[6.0] < 1e-4, errs
 
 
 def test_fmm_matvec_after_frequency_change(bem):
@@ -111,9 +149,8 @@ def test_fmm_matvec_after_frequency_change(bem):
     k = 2 * np.pi * freq / C
     cp, cq, _, _ = oracle.column_coeffs(np.full(n, bem.VELO, np.int32), k, C, RHO)
     yo = oracle.assemble(nodes, tris, k, cp, cq) @ x
-    err = _rel(y.cpu().numpy(), yo)
     mesh.close()
-    assert err < 2e-4, err
+    _check(y.cpu().numpy(), yo, 2e-4, 2e-3, "fmm product after a frequency change")
 
 
 @pytest.mark.parametrize("tau", [1.0, -1.0])
@@ -135,10 +172,10 @@ def test_recomputed_near_field_matches_stored_and_oracle(bem, tau):
         mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region, trunc_factor=6.0, near_store=ns, tau=tau)
         ys[ns] = mesh.matvec(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy()
         mesh.close()
-    assert _rel(ys[0], ys[1]) < 1e-5, _rel(ys[0], ys[1])
+    _check(ys[0], ys[1], 1e-5, 1e-4, "recomputed vs stored near field")
     cp, cq, _, _ = oracle.column_coeffs(bct, k, C, RHO, RHO * C * adm[region], tau)
     yo = oracle.assemble(nodes, tris, k, cp, cq, params={"tau": tau}) @ x
-    assert _rel(ys[0], yo) < 1e-4, _rel(ys[0], yo)
+    _check(ys[0], yo, 1e-4, 1e-3, "recomputed near field vs oracle")
 
 
 def test_solve_and_field_match_oracle(bem):
@@ -152,10 +189,8 @@ def test_solve_and_field_match_oracle(bem):
     fld = mesh.evaluate(freq, p, q, pts, src, c=C, rho=RHO)
     po, qo, _ = oracle.solve(nodes, tris, freq, c=C, rho=RHO, sources=[("plane", (0, 0, 1.0), 1.0)])
     fo = oracle.field(nodes, tris, freq, po, qo, pts, c=C, sources=[("plane", (0, 0, 1.0), 1.0)])
-    ep = _rel(p.cpu().numpy(), po)
-    ef = _rel(fld.cpu().numpy(), fo)
-    assert ep < 1e-4, ep
-    assert ef < 1e-4, ef
+    _check(p.cpu().numpy(), po, 1e-4, 1e-3, "surface pressure")
+    _check(fld.cpu().numpy(), fo, 1e-4, 1e-3, "field")
     assert np.allclose(q.cpu().numpy(), 0)
 
 
@@ -173,8 +208,7 @@ def test_restarted_gmres_matches_oracle(bem, restart):
     mesh.close()
     assert info["converged"] and info["restarts"] >= 1, info
     po, qo, _ = oracle.solve(nodes, tris, freq, c=C, rho=RHO, sources=[("plane", (0, 0, 1.0), 1.0)])
-    ep = _rel(p.cpu().numpy(), po)
-    assert ep < 1e-4, ep
+    _check(p.cpu().numpy(), po, 1e-4, 1e-3, "restarted GMRES(%d)" % restart)
 
 
 def test_field_velocity_matches_oracle(bem):
@@ -196,8 +230,7 @@ def test_field_velocity_matches_oracle(bem):
     for pts in (np.concatenate([near, far]), inputs.fibonacci_sphere(2000, 0.9)[:1500]):
         v = mesh.evaluate_velocity(freq, p, q, pts, src, c=C, rho=RHO).cpu().numpy()
         vo = oracle.field_velocity(nodes, tris, freq, pn, qn, pts, c=C, rho=RHO, sources=osrc)
-        err = _rel(v.astype(np.complex128), vo)
-        assert err < 1e-5, (pts.shape, err)
+        _check(v.astype(np.complex128).ravel(), vo.ravel(), 1e-5, 1e-4, "velocity at %d points" % len(pts))
     mesh.close()
 
 
@@ -223,16 +256,16 @@ def test_interior_problem_matches_oracle(bem, mode, level, freq):
     p, q, info = mesh.solve(freq, [], tol=1e-7, c=C, rho=RHO)
     assert info["converged"], info
     po, qo, _ = oracle.solve(nodes, tris, freq, c=C, rho=RHO, bc_type=bct, bc_value=v, params={"tau": -1.0})
-    ep = _rel(p.cpu().numpy(), po)
-    assert ep < (1e-4 if mode == "direct" else 2e-4), ep
+    tol = 1e-4 if mode == "direct" else 2e-4
+    _check(p.cpu().numpy(), po, tol, 10 * tol, "interior surface pressure")
     pts = np.array([[0.0, 0.0, 0.0], [0.03, -0.02, 0.01], [-0.05, 0.02, 0.04], [0.0, 0.06, -0.05]])
     f = mesh.evaluate(freq, p, q, pts, [], c=C, rho=RHO).cpu().numpy()
     fo = oracle.field(nodes, tris, freq, po, qo, pts, c=C, params={"tau": -1.0})
-    assert _rel(f, fo) < 2e-4, _rel(f, fo)
+    _check(f, fo, 2e-4, 2e-3, "interior field")
     assert np.abs(fo - np.exp(1j * k * pts @ d)).max() < 3e-2
     vel = mesh.evaluate_velocity(freq, p, q, pts, [], c=C, rho=RHO).cpu().numpy()
     vo = oracle.field_velocity(nodes, tris, freq, po, qo, pts, c=C, rho=RHO, params={"tau": -1.0})
-    assert _rel(vel, vo) < 2e-4, _rel(vel, vo)
+    _check(vel.ravel(), vo.ravel(), 2e-4, 2e-3, "interior velocity")
     mesh.close()
 
 
@@ -258,13 +291,12 @@ def test_duct_matches_oracle(bem):
     beta = np.where(end, 1.0, 0.0).astype(complex)
     po, qo, _ = oracle.solve(nodes, tris, f, c=c, rho=rho, bc_type=bct, bc_value=bcv, beta=beta,
                              params={"tau": -1.0})
-    ep = _rel(p.cpu().numpy(), po)
-    assert ep < 2e-4, ep
+    _check(p.cpu().numpy(), po, 2e-4, 2e-3, "duct surface pressure")
     xs = np.linspace(0.2, 3.2, 7)
     pts = np.stack([xs, 0 * xs, 0 * xs], 1)
     fld = mesh.evaluate(f, p, q, pts, [], c=c, rho=rho).cpu().numpy()
     fo = oracle.field(nodes, tris, f, po, qo, pts, c=c, params={"tau": -1.0})
-    assert _rel(fld, fo) < 2e-4, _rel(fld, fo)
+    _check(fld, fo, 2e-4, 2e-3, "duct field")
     mesh.close()
 
 
@@ -282,8 +314,8 @@ def test_mixed_boundary_solve_matches_oracle(bem):
     p, q, info = mesh.solve(freq, src, admittance=adm, tol=1e-7, c=C, rho=RHO)
     po, qo, _ = oracle.solve(nodes, tris, freq, c=C, rho=RHO, sources=[("point", (0.3, 0.1, -0.2), 2.0 + 1.0j)],
                              bc_type=bct, bc_value=bcv, beta=RHO * C * adm[region])
-    assert _rel(p.cpu().numpy(), po) < 1e-4
-    assert _rel(q.cpu().numpy(), qo) < 2e-4
+    _check(p.cpu().numpy(), po, 1e-4, 1e-3, "mixed-boundary p")
+    _check(q.cpu().numpy(), qo, 2e-4, 2e-3, "mixed-boundary q")
 
 
 @pytest.mark.parametrize("mode,level", [("direct", 3), ("fmm", 4)])
@@ -314,8 +346,8 @@ def test_row_scaling_solve_matches_oracle(bem, mode, level):
     po, qo, _ = oracle.solve(nodes, tris, freq, c=C, rho=RHO, sources=[("plane", (0, 0, 1.0), 1.0)],
                              bc_type=bct, bc_value=bcv, row_scaling=True)
     tol = 1e-4 if mode == "direct" else 2e-4
-    assert _rel(p1, po) < tol, _rel(p1, po)
-    assert _rel(q1, qo) < 2 * tol, _rel(q1, qo)
+    _check(p1, po, tol, 10 * tol, "row-scaled p")
+    _check(q1, qo, 2 * tol, 20 * tol, "row-scaled q")
 
 
 def _octant_regions(cen):
@@ -346,7 +378,7 @@ def test_admittance_gradient_matches_oracle_exterior(bem):
     assert abs(L - Lo) < 1e-6 * Lo, (L, Lo)           # measured 1.4e-8
     eg = np.max(np.abs(g - go)) / np.max(np.abs(go))
     assert eg < 2e-5, eg                               # measured 9e-7
-    assert _rel(p.cpu().numpy(), io["p"]) < 1e-4
+    _check(p.cpu().numpy(), io["p"], 1e-4, 1e-3, "forward p of the gradient")
     # the same through torch.autograd
     mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region, mode=bem.MODE_DIRECT)
     Yt = torch.tensor(Y, dtype=torch.complex128, requires_grad=True)
@@ -401,19 +433,16 @@ def test_transposed_product_matches_oracle(bem, mode):
     xt = torch.tensor(x, dtype=torch.complex64, device="cuda")
     if mode == "direct":
         mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region, mode=bem.MODE_DIRECT)
-        err = _rel(mesh.matvec_transpose(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy(), yo)
+        yt = mesh.matvec_transpose(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy()
         mesh.close()
-        assert err < 2e-5, err
+        _check(yt, yo, 2e-5, 2e-4, "transposed direct product")
         return
-    errs = {}
-    for tf in (1.8, 6.0):
+    for tf, l2, el in ((1.8, 2e-3, 2e-2), (6.0, 1e-4, 1e-3)):
         mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region, trunc_factor=tf)
         assert mesh.stats(freq, c=C)["levels"] >= 2
-        errs[tf] = _rel(mesh.matvec_transpose(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy(), yo)
+        yt = mesh.matvec_transpose(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy()
         mesh.close()
-    print("transposed fmm rel err", errs)
-    assert errs[1.8] < 2e-3, errs
-    assert errs[6.0] < 1e-4, errs
+        _check(yt, yo, l2, el, "transposed fmm product, factor %g" % tf)
 
 
 def test_admittance_gradient_fmm_matches_oracle(bem):
@@ -459,10 +488,8 @@ def test_head_band_sweep_matches_oracle(bem):
     src_o = [("point", tuple(xs), 1.0)]
     po, qo, _ = oracle.solve(nodes, tris, fs[-1], c=C, rho=RHO, sources=src_o)
     fo = oracle.field(nodes, tris, fs[-1], po, qo, pts, c=C, sources=src_o)
-    ep = _rel(p[-1].cpu().numpy(), po)
-    ef = _rel(fl[-1].cpu().numpy(), fo)
-    assert ep < 2e-4, ep
-    assert ef < 2e-4, ef
+    _check(p[-1].cpu().numpy(), po, 2e-4, 2e-3, "head band surface pressure")
+    _check(fl[-1].cpu().numpy(), fo, 2e-4, 2e-3, "head band field")
 
 
 def test_subdivision_limit_is_reported(bem):
@@ -501,10 +528,11 @@ def test_fmm_truncation_error_is_measurable(bem):
         assert st["far_pairs"] > 0.5 * n * n
         y = mesh.matvec(freq, torch.tensor(x, dtype=torch.complex64, device="cuda"), c=C, rho=RHO)
         errs[L_min] = _rel(y.cpu().numpy(), yo)
+        if L_min == 8:
+            _check(y.cpu().numpy(), yo, 2e-5, 2e-4, "fmm product, paper's truncation")
         mesh.close()
     print("truncation", errs)
     assert errs[3] > 1e-5 and errs[3] > 10 * errs[8], errs
-    assert errs[8] < 2e-5, errs
 
 
 def test_head_like_surface_fmm_matvec(bem):
@@ -520,7 +548,7 @@ def test_head_like_surface_fmm_matvec(bem):
     x = inputs.random_complex(n, 24)
     mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region)
     y = mesh.matvec(freq, torch.tensor(x, dtype=torch.complex64, device="cuda"), admittance=adm, c=C, rho=RHO)
-    assert _rel(y.cpu().numpy(), A @ x) < 2e-5
+    _check(y.cpu().numpy(), A @ x, 2e-5, 2e-4, "head-like surface fmm product")
 
 
 @pytest.fixture(scope="module")
@@ -545,8 +573,7 @@ def test_full_size_matvec_sampled_rows(bem, big_sphere):
     rows = np.random.default_rng(2).choice(n, size=96, replace=False)
     rows = np.concatenate([rows, [0, n - 1]])
     yo = oracle.matvec_rows(nodes, tris, k, np.ones(n, complex), np.zeros(n, complex), x, rows)
-    err = _rel(y[rows], yo)
-    assert err < 2e-5, err
+    _check(y[rows], yo, 2e-5, 2e-4, "full-size sampled rows")
 
 
 def test_full_size_smooth_vector_truncation(bem, big_sphere):
@@ -560,21 +587,20 @@ def test_full_size_smooth_vector_truncation(bem, big_sphere):
     x = np.exp(1j * k * cen[:, 2])
     rows = np.random.default_rng(5).choice(n, size=96, replace=False)
     yo = oracle.matvec_rows(nodes, tris, k, np.ones(n, complex), np.zeros(n, complex), x, rows)
-    errs = {}
-    for tf in (1.8, 5.0):
+    for tf, l2, el in ((1.8, 1e-3, 1e-2), (5.0, 1e-4, 1e-3), (8.0, 2e-5, 2e-4)):
         mesh = bem.Mesh(nodes, tris, trunc_factor=tf)
         y = mesh.matvec(f, torch.tensor(x, dtype=torch.complex64, device="cuda"), c=C, rho=RHO).cpu().numpy()
-        errs[tf] = _rel(y[rows], yo)
         mesh.close()
-    print("smooth-vector FMM error by truncation factor", errs)
-    assert errs[1.8] < 1e-3 and errs[5.0] < 1e-4, errs
+        _check(y[rows], yo, l2, el, "full-size smooth vector, factor %g" % tf)
 
 
-@pytest.mark.parametrize("tf,tol", [(1.8, 1e-3), (5.0, 1e-4)])
+@pytest.mark.parametrize("tf,tol", [(1.8, 1e-3), (5.0, 1e-4), (8.0, 1e-5)])
 def test_full_size_solve_residual_and_series(bem, big_sphere, tf, tol):
     """Bench workload solve: FP64 residual of the GPU solution on sampled
     rows of the paper's dense operator (FMM truncation + FP32), and the
-    sphere series (discretisation error)."""
+    sphere series (discretisation error).  Factor 8 is the bench's setting:
+    there the FMM error falls below the GMRES tolerance (1e-6), so the
+    residual is bounded by 1e-5."""
     from closed_forms import sphere_plane_wave
     W = big_sphere
     nodes, tris, f = W["nodes"], W["tris"], W["freq"]
