@@ -110,47 +110,33 @@ def _workload(name):
 
 
 # ---------------------------------------------------------------------- oracle CPU legs
-def oracle_sample(W, seconds=15.0, gmres_iters=40):
-    """Time the FP64 oracle on a bounded sample of the same workload and scale
-    it to matvecs/s of a full dense solve: assembly of all N rows (rows are
-    computed on the fly, sample timed) + gmres_iters dense products (a dense
-    row block, sample timed).  Returns (matvecs/s, description, threads)."""
+def oracle_solve(W, tol=1e-6, restart=100):
+    """One complete solve of the workload by the FP64 oracle on the host
+    cores, timed as it runs (nothing extrapolated): dense assembly of all
+    N x N entries with the paper's quadrature, the right-hand side, and
+    GMRES(restart) with dense O(N^2) products to the relative residual tol.
+    Returns (matvecs/s, description, threads, seconds, products)."""
     import oracle
-    nodes, tris, f, c, rho = W["nodes"], W["tris"], W["freq"], W["c"], W["rho"]
+    nodes, tris, f, c = W["nodes"], W["tris"], W["freq"], W["c"]
     n = tris.shape[0]
     k = 2 * math.pi * f / c
-    cp = np.ones(n, np.complex128)
-    cq = np.zeros(n, np.complex128)
-    x = np.ones(n, np.complex128)
-    rng = np.random.default_rng(0)
     oracle.lib()
     threads = oracle.num_threads()
-    # calibrate
-    rows = rng.choice(n, size=min(n, 2 * threads), replace=False)
     t0 = time.perf_counter()
-    oracle.matvec_rows(nodes, tris, k, cp, cq, x, rows)
-    dt = time.perf_counter() - t0
-    per_row = dt / len(rows)
-    nrows = int(max(len(rows), min(n, 0.7 * seconds / max(per_row, 1e-9))))
-    rows = rng.choice(n, size=nrows, replace=False)
-    t0 = time.perf_counter()
-    oracle.matvec_rows(nodes, tris, k, cp, cq, x, rows)
-    t_rows = time.perf_counter() - t0
-    t_assemble = t_rows / nrows * n
-    # dense product on a row block of a stored matrix
-    blk = int(min(n, max(256, (64 << 20) // (16 * n))))
-    A = (rng.normal(size=(blk, n)) + 1j * rng.normal(size=(blk, n))).astype(np.complex128)
-    xv = np.ascontiguousarray(x)
-    reps = 3
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        oracle.matvec_dense_block(A, xv)
-    t_mv = (time.perf_counter() - t0) / reps * (n / blk)
-    total = t_assemble + gmres_iters * t_mv
-    desc = ("oracle (FP64 C, OpenMP) on %d sampled rows of the %d x %d operator with the paper's quadrature "
-            "(%.2f s) -> assembly %.1f s; dense product on a %d-row block -> %.3f s per product; "
-            "solve = assembly + %d products" % (nrows, n, n, t_rows, t_assemble, blk, t_mv, gmres_iters))
-    return gmres_iters / total, desc, threads, total
+    A = oracle.assemble(nodes, tris, k, np.ones(n, np.complex128), np.zeros(n, np.complex128))
+    t_asm = time.perf_counter() - t0
+    cen, nrm, _ = oracle.geometry(nodes, tris)
+    b = oracle.rhs(cen, nrm, k, [("plane", tuple(W["plane_dir"]), W["amp"])])
+    t1 = time.perf_counter()
+    _, info = oracle.gmres(A, b, tol=tol, maxit=1000, restart=restart)
+    t_gm = time.perf_counter() - t1
+    del A
+    total = time.perf_counter() - t0
+    its = int(info["iterations"])
+    desc = ("oracle (FP64 C, OpenMP, %d threads), whole workload, measured: dense assembly of the %d x %d "
+            "operator with the paper's quadrature %.2f s, right-hand side and GMRES(%d) to %.0e with %d dense "
+            "products %.2f s" % (threads, n, n, t_asm, restart, tol, its, t_gm))
+    return its / total, desc, threads, total, its
 
 
 def combine_ranks(t_ms, e_ms, mvs, e_mvs, device="cpu"):
@@ -362,6 +348,7 @@ def run_ours(args):
                                        "leaf_edge", "leaf_level", "autotune")},
         "kernels": kernels,
         "roofline": roof,
+        "rooflines": extra_rooflines(kernels, stats, peaks),
         "clocks": clocks,
         "gpu_launches": int(launches),
         "e2e": {"value": round(e2e, 2), "unit": UNIT,
@@ -369,9 +356,9 @@ def run_ours(args):
                 "d2h_bytes_per_step": int((2 * n + pts.shape[0]) * 8)},
     }
     if ws == 1 and not args.no_cpu_baseline:
-        v, desc, thr, tot = oracle_sample(W, seconds=args.cpu_seconds, gmres_iters=max(1, int(round(mvs / args.steps))))
+        v, desc, thr, tot, its = oracle_solve(W, tol=args.tol)
         out["cpu_baseline"] = {"value": round(v, 4), "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc,
-                               "solve_s_per_frequency_est": round(tot, 2)}
+                               "solve_s_per_frequency": round(tot, 3), "products": its}
     print(json.dumps(out))
     sys.stdout.flush()
     mesh.close()
@@ -464,33 +451,98 @@ def roofline(kernels, stats, n, peaks, peak_src):
             "traffic": None, "avg_us": kernels[name]["avg_us"], "peak_source": peak_src}
 
 
+# FP32 flops of one regular quadrature point of the near-field entries
+# (bm_point with the point's position and weight): |d|^2, r, the phase
+# k r / 2 pi and its exact reduction, G, the three dot products, the two
+# Burton-Miller factors and the two complex multiply-adds (an FMA counts
+# two); plus rsqrt, sin and cos on the SFU.  The self terms' Duffy and edge
+# points cost about the same with CUDA's accurate sincosf.  Per entry, the
+# column coefficients add two complex products and a sum.
+FLOPS_PER_POINT = 80
+FLOPS_PER_ENTRY = 14
+SMS = 152
+# L2 bandwidth of this GB300 derived from ncu (k_transfer_split read 341 MB
+# in 26.2 us = 13.0 TB/s at lts__throughput 45.7 % of peak): about 28.5 TB/s
+L2_GBS_NCU = 28500.0
+
+
+def extra_rooflines(kernels, stats, peaks):
+    """Rooflines of the kernels after the dominant one: the near-field entry
+    kernels against the FP32 peak (their algorithmic flops counted from the
+    plan's quadrature points), the aggregation against the SFU peak (one sine
+    and one cosine per element and antipodal direction pair), the transfer
+    against L2 bandwidth (D and M, 8 B each per list entry and direction)."""
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32 = SMS * 128 * 2 * mhz * 1e6 / 1e12     # TFLOP/s
+    sfu = SMS * 16 * mhz * 1e6 / 1e12           # Tops/s
+    out = {}
+
+    def avg_s(name):
+        k = kernels.get(name)
+        return k["avg_us"] * 1e-6 if k else None
+
+    t = avg_s("k_near_store")
+    if t:
+        fl = stats["near_light_points"] * FLOPS_PER_POINT + stats["near_light_entries"] * FLOPS_PER_ENTRY
+        out["k_near_store_light"] = {"bound": "alu", "achieved": round(fl / t / 1e12, 2), "peak": round(fp32, 1),
+                                     "unit": "TFLOP/s", "frac": round(fl / t / 1e12 / fp32, 4),
+                                     "flops_per_launch": fl, "points": stats["near_light_points"],
+                                     "entries": stats["near_light_entries"],
+                                     "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
+    t = avg_s("k_near_store_heavy")
+    if t:
+        fl = stats["near_heavy_points"] * FLOPS_PER_POINT + stats["near_heavy_entries"] * FLOPS_PER_ENTRY
+        out["k_near_store_heavy"] = {"bound": "alu", "achieved": round(fl / t / 1e12, 2), "peak": round(fp32, 1),
+                                     "unit": "TFLOP/s", "frac": round(fl / t / 1e12 / fp32, 4),
+                                     "flops_per_launch": fl, "points": stats["near_heavy_points"],
+                                     "entries": stats["near_heavy_entries"],
+                                     "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
+    t = avg_s("k_aggregate")
+    if t:
+        terms = sum(ns * L * L for ns, L in zip(stats["n_src_elements"], stats["L"]))
+        ops = 2 * terms
+        out["k_aggregate"] = {"bound": "sfu", "achieved": round(ops / t / 1e12, 3), "peak": round(sfu, 3),
+                              "unit": "Tops/s", "frac": round(ops / t / 1e12 / sfu, 4), "pair_terms": terms,
+                              "peak_source": "152 SMs x 16 SFU ops/clk x max SM clock"}
+    t = avg_s("k_transfer")
+    if t:
+        byts = sum(16 * ni * 2 * L * L for ni, L in zip(stats["n_interactions"], stats["L"]))
+        out["k_transfer"] = {"bound": "l2", "achieved": round(byts / t / 1e9, 1), "peak": L2_GBS_NCU,
+                             "unit": "GB/s", "frac": round(byts / t / 1e9 / L2_GBS_NCU, 4), "bytes": byts,
+                             "peak_source": "ncu-derived (k_transfer_split achieved / lts__throughput %)"}
+    return out
+
+
 # ---------------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on the host cores.
+    A step is one whole solve of the workload (oracle_solve: dense assembly
+    and GMRES to the bench's tolerance), timed as it runs; value = the
+    oracle's products over the timed steps' seconds."""
     ws, rank, local = _dist()
     if rank != 0:
         return
     W = _workload(args.workload)
     n = W["tris"].shape[0]
-    per = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle_sample(W, seconds=per)
-    vals, descs, tots = [], [], []
+        oracle_solve(W, tol=args.tol)
+    descs, tots, prods = [], [], []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, d, thr, tot = oracle_sample(W, seconds=per)
-        vals.append(v)
+        v, d, thr, tot, its = oracle_solve(W, tol=args.tol)
         descs.append(d)
         tots.append(tot)
+        prods.append(its)
     wall = time.perf_counter() - t0
-    v = float(np.mean(vals))
+    v = float(sum(prods) / sum(tots))
     out = {
         "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * float(np.mean(tots)), 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": W["name"], "n_elements": n, "freq_hz": W["freq"]},
+        "config": {"workload": W["name"], "n_elements": n, "freq_hz": W["freq"], "gmres_tol": args.tol},
         "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": thr, "kind": "oracle", "sample": descs[-1]},
         "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "sample_wall_s": round(wall, 2),
+        "timed_wall_s": round(wall, 2),
     }
     print(json.dumps(out))
 
@@ -637,7 +689,6 @@ def main():
     ap.add_argument("--max-iter", type=int, default=1000)
     ap.add_argument("--restart", type=int, default=0,
                     help="GMRES restart length (default: 100 for the sphere, 256 for head_bands_c3)")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true",
                     help="one bem_solve call per frequency (default: the steps as one bem_solve_sweep call)")

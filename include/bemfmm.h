@@ -180,6 +180,11 @@ typedef struct bem_plan_stats {
                                    6 x 16 Duffy points and 3 x 4 x 3 edge points, a
                                    subdivided pair m^2 points per leaf subelement;
                                    near_quad_points = near_light_points + near_heavy_points */
+    int64_t n_src_elements[16]; /* per used level: elements of the clusters that are
+                                   interaction sources (aggregated: L^2 antipodal direction
+                                   pairs each, Sec. 3.3.3 T(l))                             */
+    int64_t n_tgt_elements[16]; /* per used level: elements of the clusters with an
+                                   interaction list (disaggregated, S(l))                   */
 } bem_plan_stats;
 
 /* Paper defaults (Sec. 3.1, Eq. FMMTruncation, Eq. Farfieldcond). */

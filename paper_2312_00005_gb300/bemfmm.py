@@ -73,6 +73,7 @@ class PlanStats(ctypes.Structure):
         ("asymmetric_pairs", ctypes.c_int64), ("order_R", ctypes.c_double * 8),
         ("near_light_entries", ctypes.c_int64), ("near_light_points", ctypes.c_int64),
         ("near_heavy_entries", ctypes.c_int64), ("near_heavy_points", ctypes.c_int64),
+        ("n_src_elements", ctypes.c_int64 * 16), ("n_tgt_elements", ctypes.c_int64 * 16),
     ]
 
     def as_dict(self):
@@ -87,6 +88,7 @@ class PlanStats(ctypes.Structure):
             "asymmetric_pairs": self.asymmetric_pairs, "order_R": list(self.order_R),
             "near_light_entries": self.near_light_entries, "near_light_points": self.near_light_points,
             "near_heavy_entries": self.near_heavy_entries, "near_heavy_points": self.near_heavy_points,
+            "n_src_elements": list(self.n_src_elements[:n]), "n_tgt_elements": list(self.n_tgt_elements[:n]),
             "autotune": [(self.tuned_depth[q], self.tuned_seconds[q]) for q in range(self.n_tuned)],
         }
 

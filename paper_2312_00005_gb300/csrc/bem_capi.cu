@@ -1411,8 +1411,16 @@ void fill_stats(const Geometry &g, const Tree &t, const FreqPlan &fp, const bem_
         out->n_clusters[l] = F.nc;
         out->n_interactions[l] = F.n_inter;
         out->n_offsets[l] = (int)(F.offsets.size() / 3);
+        std::vector<char> src(F.nc, 0);
+        for (int c = 0; c < F.nc; ++c) {
+            for (int q = F.il_ptr[c]; q < F.il_ptr[c + 1]; ++q) {
+                far_pairs += L.count[c] * L.count[F.il_src[q]];
+                src[F.il_src[q]] = 1;
+            }
+            if (F.il_ptr[c + 1] > F.il_ptr[c]) out->n_tgt_elements[l] += L.count[c];
+        }
         for (int c = 0; c < F.nc; ++c)
-            for (int q = F.il_ptr[c]; q < F.il_ptr[c + 1]; ++q) far_pairs += L.count[c] * L.count[F.il_src[q]];
+            if (src[c]) out->n_src_elements[l] += L.count[c];
     }
     out->far_pairs = far_pairs;
     // symmetry of the lists (the transposed product reads them backwards):
