@@ -60,7 +60,8 @@ extern "C" {
                                      message names the element */
 #define BEM_E_CUDA            -3  /* a CUDA call failed */
 #define BEM_E_OOM             -4  /* device allocation failed */
-#define BEM_E_TIMEOUT         -5  /* a device loop exhausted its iteration budget */
+#define BEM_E_TIMEOUT         -5  /* reserved: no device code of this library waits on another
+                                     block or launch, so no call returns it */
 #define BEM_E_INTERNAL        -6
 #define BEM_W_NOT_CONVERGED    1  /* GMRES stopped at max_iter above tol (cf. Sec. 3.2 warning) */
 #define BEM_W_UNDERRESOLVED    2  /* mean edge longer than a sixth of the wavelength (Sec. 2.2) */
@@ -91,7 +92,7 @@ typedef struct bem_params {
     double  stability_max;  /* far only if sum_n (2n+1)|h_n(kX)| / |h_0(kX)| <= this, 1e3     */
     int32_t near_store;     /* 1: store near-field entries per frequency (default);
                                0: recompute them inside every product                         */
-    int32_t restart;        /* GMRES restart length, 100                                       */
+    int32_t restart;        /* GMRES restart length, 100 (2..1024)                             */
     int32_t autotune;       /* 1: choose the leaf size by timing candidates on the GPU at the
                                mesh's first plan (when leaf_edge is 0; default); 0: off       */
     double  tau;            /* +1: exterior problem (default); -1: interior problem, the field
@@ -390,21 +391,15 @@ int bem_matvec_direct_noalloc(const double *nodes_dev, int64_t n_nodes, const in
                               double freq_hz, const bem_medium *medium, const void *x_dev, void *y_dev,
                               void *stream);
 
-/* Test hooks for the library's own failure paths (no counterpart in the
- * paper), so that tests reach them without a GPU fault.  Process-wide; each
- * call sets both hooks.
+/* Test hook for the library's own allocation-failure path (no counterpart
+ * in the paper), so that tests reach it without exhausting the device.
+ * Process-wide.
  *   alloc_fail_after >= 0: that many further device allocations succeed and
  *     the next one is refused without calling cudaMalloc (the entry point
  *     returns BEM_E_OOM and frees what it had allocated); < 0: off.
- *   barrier_polls > 0: the grid barriers of the GMRES Gram-Schmidt step
- *     withhold their release and every wait gives up after barrier_polls
- *     polls, as a block that never arrives would make it (bem_solve returns
- *     BEM_E_TIMEOUT; the mesh stays usable); 0: off (the waits give up after
- *     2^23 polls, which a healthy launch never reaches).
  *   live_device_bytes (may be NULL): bytes the library holds in device
- *     allocations (every mesh's buffers) at the time of the call.
- * Errors: BEM_E_ARG (barrier_polls < 0). */
-int bem_test_hooks(int64_t alloc_fail_after, int32_t barrier_polls, int64_t *live_device_bytes);
+ *     allocations (every mesh's buffers) at the time of the call. */
+int bem_test_hooks(int64_t alloc_fail_after, int64_t *live_device_bytes);
 
 /* Number of kernels this library has launched in this process. */
 uint64_t bem_launch_count(void);

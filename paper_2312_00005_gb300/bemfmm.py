@@ -134,7 +134,7 @@ def lib():
                                               ctypes.POINTER(ctypes.c_int64)]),
             "bem_selftest_sincos": (ctypes.c_int, [P, i64, P, P]),
             "bem_matvec_direct_noalloc": (ctypes.c_int, [P, i64, P, i64, d, ctypes.POINTER(Medium), P, P, P]),
-            "bem_test_hooks": (ctypes.c_int, [i64, i32, ctypes.POINTER(i64)]),
+            "bem_test_hooks": (ctypes.c_int, [i64, ctypes.POINTER(i64)]),
             "bem_launch_count": (ctypes.c_uint64, []),
             "bem_last_error": (ctypes.c_char_p, []),
         }
@@ -146,11 +146,11 @@ def lib():
     return _lib
 
 
-def test_hooks(alloc_fail_after=-1, barrier_polls=0) -> int:
-    """Set the failure-path test hooks (see bem_test_hooks in the header);
-    returns the bytes the library holds in device allocations."""
+def test_hooks(alloc_fail_after=-1) -> int:
+    """Set the allocation-failure test hook (see bem_test_hooks in the
+    header); returns the bytes the library holds in device allocations."""
     live = ctypes.c_int64(0)
-    _check(lib().bem_test_hooks(int(alloc_fail_after), int(barrier_polls), ctypes.byref(live)))
+    _check(lib().bem_test_hooks(int(alloc_fail_after), ctypes.byref(live)))
     return live.value
 
 

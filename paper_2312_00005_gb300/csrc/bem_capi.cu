@@ -185,8 +185,6 @@ void resolve_timing()
 // library holds in device allocations.
 std::atomic<int64_t> g_alloc_budget{-1};
 std::atomic<int64_t> g_live_bytes{0};
-// polls of a Gram-Schmidt grid-barrier wait with the release withheld (0: off)
-std::atomic<int32_t> g_barrier_polls{0};
 
 void dev_malloc(void **p, size_t bytes)
 {
@@ -378,7 +376,7 @@ struct bem_mesh_impl {
     DevArr<float2> V, w;
     DevArr<double2> H, cs, sn, g_, hcol, part, yv;
     DevArr<double> normpart;
-    DevArr<unsigned int> gbar;   // grid barrier of the fused Gram-Schmidt step
+    DevArr<unsigned int> gbar;   // arrival counter of the Gram-Schmidt reductions
     DevArr<GmresState> st;
     // frequency state: cur serves the products and the solve; next is filled
     // by the setup thread of a frequency sweep for the following frequency
@@ -1152,7 +1150,7 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
 // near part by k_near_fused_t (entries recomputed), the far part by the
 // forward aggregation and transfer kernels on the weights k_prep_t forms
 // and k_disaggregate_t.  x: internal order, or null when x_int already
-// holds x (formed by k_gm_ortho).  y: caller order when perm_out, else
+// holds x (formed by k_gs_finish).  y: caller order when perm_out, else
 // internal.  far_only: y receives the far part alone and the near part
 // stays in M.ynear (the Gram-Schmidt step adds them).
 void matvec_t_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, const float2 *x, float2 *y,
@@ -1503,7 +1501,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
     if (params) p = *params;
     if (p.m_max < 1 || p.m_max > kMaxRule) return set_err(BEM_E_ARG, "m_max must be in 1..6");
     if (p.max_depth < 0 || p.max_depth > 15) return set_err(BEM_E_ARG, "max_depth must be in 0..15");
-    if (p.restart < 2 || p.restart > kMaxRestart) return set_err(BEM_E_ARG, "restart must be in 2..256");
+    if (p.restart < 2 || p.restart > kMaxRestart) return set_err(BEM_E_ARG, "restart must be in 2..1024");
     if (!(p.tau == 1.0 || p.tau == -1.0)) return set_err(BEM_E_ARG, "tau must be +1 (exterior) or -1 (interior)");
     if (p.row_scaling != 0 && p.row_scaling != 1) return set_err(BEM_E_ARG, "row_scaling must be 0 or 1");
     if (p.check_orientation != 0 && p.check_orientation != 1)
@@ -1751,28 +1749,26 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     M.g_.alloc(m + 1);
     M.hcol.alloc(m + 1);
     M.yv.alloc(m + 1);
-    // the fused Gram-Schmidt step: one cooperative launch, block b owns
-    // rows [b R, b R + R) with R <= kOrthoMaxRows; all blocks co-resident
+    // the Gram-Schmidt step: block b owns rows [b R, b R + R), R <= kGsMaxRows;
+    // about 128 rows per block (a short reduction for the last block), at
+    // most 256 blocks unless the rows need more
     int nblk = 0;
     {
-        int per_sm = 0, nsm = 0;
-        ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gm_ortho, kOrthoThreads, 0), "occupancy");
-        ck(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, M.device), "attribute");
-        const int64_t cap = std::min<int64_t>((int64_t)per_sm * nsm, kOrthoMaxBlocks);
-        const int64_t want = std::max<int64_t>(1, (n + 63) / 64);
-        nblk = (int)std::min(cap, want);
-        if ((n + nblk - 1) / nblk > kOrthoMaxRows)
-            throw Fail{set_err(BEM_E_ARG, "GMRES: " + std::to_string(n) + " unknowns exceed the fused "
-                                              "Gram-Schmidt step's limit of " +
-                                              std::to_string(cap * kOrthoMaxRows))};
+        const int64_t want = std::min<int64_t>((n + 127) / 128, 256);
+        const int64_t need = (n + kGsMaxRows - 1) / kGsMaxRows;
+        nblk = (int)std::max<int64_t>(1, std::max(want, need));
+        if (nblk > kGsMaxBlocks)
+            throw Fail{set_err(BEM_E_ARG, "GMRES: " + std::to_string(n) + " unknowns exceed the Gram-Schmidt "
+                                              "step's limit of " +
+                                              std::to_string((int64_t)kGsMaxBlocks * kGsMaxRows))};
     }
     const int orows = (int)((n + nblk - 1) / nblk);
     M.part.alloc((size_t)(m + 1) * nblk);
     const int nnorm = (int)nblocks(n, 256);
     M.normpart.alloc(std::max(nnorm, nblk));
     M.st.alloc(1);
-    M.gbar.alloc(2);
-    ck(cudaMemsetAsync(M.gbar.p, 0, 2 * sizeof(unsigned int), s), "memset barrier");
+    M.gbar.alloc(1);
+    ck(cudaMemsetAsync(M.gbar.p, 0, sizeof(unsigned int), s), "memset counter");
     GmresState hs;
     memset(&hs, 0, sizeof hs);
     hs.tol = tol;
@@ -1781,7 +1777,7 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     ck(cudaMemsetAsync(M.uvec.p, 0, n * sizeof(float2), s), "memset x");
     ck(cudaMemsetAsync(M.H.p, 0, M.H.bytes(), s), "memset H");
     // the product inputs of v_0 (later basis vectors get theirs from
-    // k_gm_ortho)
+    // k_gs_finish)
     auto prep_v0 = [&]() {
         PrepArgs pa = prep_args(M, fr(M).cp.p, fr(M).cq.p, M.V.p);
         {
@@ -1806,7 +1802,7 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     const int *done = &M.st.p->skip_prod;   // uniform within every product launch
-    OrthoArgs oa;
+    GsArgs oa;
     GmresArgs &ga = oa.g;
     ga.V = M.V.p;
     ga.w = M.w.p;
@@ -1823,14 +1819,8 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     ga.m = m;
     oa.next = prep_args(M, fr(M).cp.p, fr(M).cq.p, nullptr);
     oa.wnear = M.ynear.p;
-    oa.bar = M.gbar.p;
-    oa.err = &M.st.p->fault;
+    oa.cnt = M.gbar.p;
     oa.rows = orows;
-    {
-        const int32_t polls = g_barrier_polls.load();
-        oa.spin_limit = polls > 0 ? (unsigned int)polls : kSpinLimit;
-        oa.hold_release = polls > 0 ? 1 : 0;
-    }
     // one Arnoldi step: product of v_j (inputs already formed), then the
     // fused Gram-Schmidt / Givens step, which also forms v_{j+1}
     const bool use_graph = !g_timing;
@@ -1839,19 +1829,21 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     // kernel is timed alone and no timed launch is a skipped one.
     const int batch = use_graph ? kStepsPerGraph : 1;
     auto ortho = [&]() {
-        KTimer kt_("k_gm_ortho", s);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(nblk);
-        cfg.blockDim = dim3(kOrthoThreads);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        ck(cudaLaunchKernelEx(&cfg, k_gm_ortho, oa), "k_gm_ortho");
-        g_launches.fetch_add(1);
+        {
+            KTimer kt_("k_gs_dots", s);
+            k_gs_dots<<<nblk, kGsThreads, 0, s>>>(oa);
+        }
+        ck_launch("k_gs_dots");
+        {
+            KTimer kt_("k_gs_update", s);
+            k_gs_update<<<nblk, kGsThreads, 0, s>>>(oa);
+        }
+        ck_launch("k_gs_update");
+        {
+            KTimer kt_("k_gs_finish", s);
+            k_gs_finish<<<nblk, kGsThreads, 0, s>>>(oa);
+        }
+        ck_launch("k_gs_finish");
     };
     auto givens = [&](cudaStream_t gs) {
         {
@@ -1861,7 +1853,7 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
         ck_launch("k_gm_givens");
     };
     // the product of the current basis vector (its inputs already formed),
-    // row-scaled when row scaling is on (both parts that k_gm_ortho adds)
+    // row-scaled when row scaling is on (both parts that k_gs_dots adds)
     auto product = [&]() {
         if (transposed) {
             matvec_t_internal(M, fr(M).cp.p, fr(M).cq.p, nullptr, M.w.p, false, true, done, s);
@@ -1939,13 +1931,6 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
             ck(cudaEventSynchronize(M.ev_st[checked & 1]), "sync st");
             h = M.h_st[checked & 1];
             ++checked;
-            if (h.fault) {
-                ck(cudaStreamSynchronize(s), "sync");
-                if (gexec) cudaGraphExecDestroy(gexec);
-                if (graph) cudaGraphDestroy(graph);
-                throw Fail{set_err(BEM_E_TIMEOUT, "GMRES: a grid barrier wait of the fused Gram-Schmidt "
-                                                  "step gave up")};
-            }
             if (h.done) break;
             if (checked == launched) {
                 if (launched >= max_graphs) break;
@@ -2529,11 +2514,9 @@ int bem_timing_get(const char *name, double *total_ms, int64_t *launches)
     return BEM_OK;
 }
 
-int bem_test_hooks(int64_t alloc_fail_after, int32_t barrier_polls, int64_t *live_device_bytes)
+int bem_test_hooks(int64_t alloc_fail_after, int64_t *live_device_bytes)
 {
-    if (barrier_polls < 0) return set_err(BEM_E_ARG, "barrier_polls must be >= 0");
     g_alloc_budget.store(alloc_fail_after < 0 ? -1 : alloc_fail_after);
-    g_barrier_polls.store(barrier_polls);
     if (live_device_bytes) *live_device_bytes = g_live_bytes.load();
     return BEM_OK;
 }

@@ -1405,45 +1405,6 @@ __device__ void gm_givens_warp(const GmresArgs &a, double nn, int j)
     for (int l = lane; l <= j + 1; l += 32) a.H[(int64_t)l * m + j] = shr[l];
 }
 
-// Grid barrier of a cooperative launch.  Thread 0 of each block arrives on
-// bar[0]; the last arrival resets it and advances the generation bar[1].
-// A wait gives up after `limit` polls (kSpinLimit unless a test shortens it)
-// and sets *err, so a lost block can never hang the GPU (the host reports
-// the error).  hold: the last arrival does not advance the generation (a
-// release that never comes, for the test of the give-up path).
-__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
-{
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void grid_barrier(unsigned int *bar, int *err, unsigned int limit, int hold)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned int g0 = ld_acquire_gpu(bar + 1);
-        __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            if (!hold) atomicAdd(bar + 1, 1u);
-        } else {
-            // polls are plain acquire loads (served by L2 without
-            // serialising behind the arrivals, unlike atomics)
-            unsigned int it = 0;
-            while (ld_acquire_gpu(bar + 1) == g0) {
-                if (++it > limit || *(volatile int *)err) {
-                    atomicExch(err, 1);
-                    break;
-                }
-                __nanosleep(20);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-}
-
 // Compensated FP32 ("float-float") sums: s + e holds the running sum to
 // about 2^-44 relative.  The reductions below are issued by every block in
 // a fixed order, so all blocks derive identical values without FP64, whose
@@ -1471,7 +1432,7 @@ __device__ __forceinline__ void ff_add(FF &a, const FF &b)
     ff_add1(a.hi.y, a.lo.y, b.hi.y, b.lo.y);
 }
 // sum of p[0..n), n <= 32 kFFLoads (float2, written by other blocks before
-// a grid barrier: read through L2) by one warp: lane order, then a fixed
+// the reduction: read through L2) by one warp: lane order, then a fixed
 // xor tree.  All loads are issued before the first add.
 constexpr int kFFLoads = 16;
 __device__ __forceinline__ FF warp_sum_ff(const float2 *p, int n)
@@ -1502,178 +1463,280 @@ __device__ __forceinline__ FF warp_sum_ff(const float2 *p, int n)
     return v;
 }
 
-// Classical Gram-Schmidt with selective reorthogonalisation (second pass
-// when ||w_after|| < 0.1 ||w_before||), then the next basis vector
-// v_{j+1} = w / ||w|| with its product inputs; the Givens step follows in
-// k_gm_givens.  Block b owns rows [b R, b R + R) of every vector: FP32
-// within a block, compensated FP32 across blocks, every reduction in a
-// fixed order, so all blocks derive identical values.
-__global__ void __launch_bounds__(kOrthoThreads) k_gm_ortho(OrthoArgs a)
+// ------------------------------------------------------------------ Gram-Schmidt
+// Classical Gram-Schmidt with selective reorthogonalisation (DGKS: a second
+// pass when ||w_1|| < 0.1 ||w||) for Arnoldi column j, in three launches with
+// no block ever waiting for another:
+//   k_gs_dots    w = (far + near part of A v_j); partial dots V_l^H w and
+//                ||w||^2 per block; the last block to finish reduces them:
+//                h = V^H w (column j of H), ||w||^2;
+//   k_gs_update  w_1 = w - V h; partial ||w_1||^2 and V_l^H w_1 per block; the
+//                last block reduces them and applies the DGKS test: without a
+//                second pass nn = ||w_1||^2, with one h_2 = V^H w_1 is added
+//                to column j of H and nn = ||w_1||^2 - |h_2|^2 (accurate: h_2
+//                is small against w_1);
+//   k_gs_finish  v_{j+1} = (w_1 [- V h_2]) / sqrt(nn) and the next product's
+//                inputs.
+// Block b owns rows [b R, b R + R) of every vector: FP32 sums within a block,
+// compensated FP32 across blocks in a fixed order (so the result does not
+// depend on which block finishes last).  The Givens step (k_gm_givens)
+// follows on a side stream.
+__device__ __forceinline__ int gs_rows(const GsArgs &a, int64_t &r0)
+{
+    r0 = (int64_t)blockIdx.x * a.rows;
+    const int64_t rem = a.g.n - r0;
+    return rem <= 0 ? 0 : (int)(rem < a.rows ? rem : (int64_t)a.rows);
+}
+
+// Partial dots part[l G + b] = sum_{i in block} conj(V_l[i]) ws[i], l <= j,
+// and npart[b] = sum_{i in block} |ws[i]|^2.
+__device__ void gs_partials(const GsArgs &a, const float2 *ws, int R, int64_t r0, int j)
+{
+    const GmresArgs &g = a.g;
+    const int G = gridDim.x, b = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int nwarp = kGsThreads / 32;
+    float2 *part = (float2 *)g.part;
+    for (int l0 = warp * 8; l0 <= j; l0 += nwarp * 8) {
+        float2 acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int i = lane; i < R; i += 32) {
+            const float2 y = ws[i];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (l0 + u <= j) {
+                    const float2 x = __ldcg(g.V + (int64_t)(l0 + u) * g.n + r0 + i);
+                    acc[u].x = fmaf(x.x, y.x, fmaf(x.y, y.y, acc[u].x));
+                    acc[u].y = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc[u].y));
+                }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float2 d = warp_sum(acc[u]);
+            if (lane == 0 && l0 + u <= j) part[(int64_t)(l0 + u) * G + b] = d;
+        }
+    }
+    __shared__ float red[nwarp];
+    float nrm = 0.f;
+    for (int i = threadIdx.x; i < R; i += kGsThreads) nrm = fmaf(ws[i].x, ws[i].x, fmaf(ws[i].y, ws[i].y, nrm));
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    if (lane == 0) red[warp] = nrm;
+    __syncthreads();
+    if (warp == 0) {
+        float v = lane < nwarp ? red[lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) ((float2 *)g.normpart)[b] = make_float2(v, 0.f);
+    }
+}
+
+// Arrival of a block whose partials are written: true in the last block to
+// arrive (it then sees every block's partials), which also re-arms the
+// counter for the next use.
+__device__ __forceinline__ bool gs_last_block(unsigned int *cnt)
+{
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+        if (s_last) *cnt = 0u;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
+}
+
+// Last block: sums the G partials of every dot (h_l, l <= j) and of the norm
+// in a fixed order; writes hcol = h (and column j of H when set_H), and
+// returns (in every thread) ||.||^2 and sum_l |h_l|^2.
+__device__ void gs_reduce(const GsArgs &a, int j, bool set_H, double *ww_out, double *hh_out)
+{
+    const GmresArgs &g = a.g;
+    const int G = gridDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int nwarp = kGsThreads / 32;
+    const float2 *part = (const float2 *)g.part;
+    __shared__ double s_hh[nwarp];
+    __shared__ double s_ww;
+    double hh = 0.0;
+    for (int l = warp; l <= j; l += nwarp) {
+        const FF sum = warp_sum_ff(part + (int64_t)l * G, G);
+        const double2 h = make_double2((double)sum.hi.x + (double)sum.lo.x, (double)sum.hi.y + (double)sum.lo.y);
+        hh += h.x * h.x + h.y * h.y;
+        if (lane == 0) {
+            g.hcol[l] = h;
+            if (set_H) g.H[(int64_t)l * g.m + j] = h;
+        }
+    }
+    if (lane == 0) s_hh[warp] = hh;
+    if (warp == 0) {
+        const FF v = warp_sum_ff((const float2 *)g.normpart, G);
+        if (lane == 0) s_ww = (double)v.hi.x + (double)v.lo.x;
+    }
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < nwarp; ++w) t += s_hh[w];
+    *hh_out = t;
+    *ww_out = s_ww;
+}
+
+// w_1 = ws - V h (h = hcol as FP32 in hs), written back into ws.
+__device__ void gs_update(const GsArgs &a, float2 *ws, const float2 *hs, int R, int64_t r0, int j)
+{
+    const GmresArgs &g = a.g;
+    constexpr int kRowsPerPass = 128, kCg = kGsThreads / kRowsPerPass;
+    __shared__ float2 cpart[kGsThreads];
+    const int cg = threadIdx.x / kRowsPerPass, rr = threadIdx.x % kRowsPerPass;
+    for (int i0 = 0; i0 < R; i0 += kRowsPerPass) {
+        const int i = i0 + rr;
+        float2 acc = make_float2(0.f, 0.f);
+        if (i < R) {
+            const float2 *vp = g.V + r0 + i;
+#pragma unroll 8
+            for (int l = cg; l <= j; l += kCg) {
+                const float2 v = __ldcg(vp + (int64_t)l * g.n);
+                const float2 h = hs[l];
+                acc.x = fmaf(h.x, v.x, fmaf(-h.y, v.y, acc.x));
+                acc.y = fmaf(h.x, v.y, fmaf(h.y, v.x, acc.y));
+            }
+        }
+        cpart[threadIdx.x] = acc;
+        __syncthreads();
+        if (cg == 0 && i < R) {
+            float2 c = cpart[rr];
+#pragma unroll
+            for (int q = 1; q < kCg; ++q) {
+                c.x += cpart[rr + q * kRowsPerPass].x;
+                c.y += cpart[rr + q * kRowsPerPass].y;
+            }
+            ws[i] = make_float2(ws[i].x - c.x, ws[i].y - c.y);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void gs_load_h(const GmresArgs &g, float2 *hs, int j)
+{
+    for (int l = threadIdx.x; l <= j; l += kGsThreads) {
+        const double2 h = __ldcg(g.hcol + l);
+        hs[l] = make_float2((float)h.x, (float)h.y);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kGsThreads) k_gs_dots(GsArgs a)
 {
     const GmresArgs &g = a.g;
     GmresState *st = g.st;
-    const int G = gridDim.x, b = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = kOrthoThreads / 32;
-    constexpr int kRowsPerPass = 128, kCg = kOrthoThreads / kRowsPerPass;
-    const int64_t r0 = (int64_t)b * a.rows;
-    const int64_t rem = g.n - r0;
-    const int R = rem <= 0 ? 0 : (int)(rem < a.rows ? rem : (int64_t)a.rows);
-    // w = A v_j (far part g.w + near part) and the state (j, done; fault)
-    // are loaded together: one memory round trip before any decision
-    constexpr int kWr = kOrthoMaxRows / kOrthoThreads;
+    int64_t r0;
+    const int R = gs_rows(a, r0);
+    // w = A v_j (far part g.w + near part) and the state (j, done) are
+    // loaded together: one memory round trip before any decision
+    constexpr int kWr = kGsMaxRows / kGsThreads;
     float2 wv[kWr];
 #pragma unroll
     for (int u = 0; u < kWr; ++u) {
-        const int i = threadIdx.x + u * kOrthoThreads;
+        const int i = threadIdx.x + u * kGsThreads;
         wv[u] = i < R ? cadd(g.w[r0 + i], a.wnear[r0 + i]) : make_float2(0.f, 0.f);
     }
     const int2 jd = __ldcv(reinterpret_cast<const int2 *>(&st->j));   // (j, done)
-    const int fault = __ldcv(a.err);
     const int j = jd.x, done = jd.y;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->skip_prod = done;
-    if (done || fault) return;
-    float2 *part = (float2 *)g.part;              // [m + 1][G]
-    float2 *npart = (float2 *)g.normpart;         // [G] (x: ||w||^2 partial)
-    __shared__ float2 ws[kOrthoMaxRows];
-    __shared__ float2 hs[kMaxRestart + 1];
-    __shared__ float2 cpart[kOrthoThreads];
-    __shared__ float red[kOrthoThreads / 32];
-    __shared__ float s_hh;
-    __shared__ double s_nn;
+    if (done) return;
+    __shared__ float2 ws[kGsMaxRows];
 #pragma unroll
     for (int u = 0; u < kWr; ++u) {
-        const int i = threadIdx.x + u * kOrthoThreads;
-        if (i < R) ws[i] = wv[u];
+        const int i = threadIdx.x + u * kGsThreads;
+        if (i < R) {
+            ws[i] = wv[u];
+            g.w[r0 + i] = wv[u];
+        }
     }
     __syncthreads();
-    double nn = 0.0;
-    for (int pass = 0; pass < 2; ++pass) {
-        // dots: warp handles columns l0 .. l0 + 7, lanes stride the rows
-        for (int l0 = warp * 8; l0 <= j; l0 += nwarp * 8) {
-            float2 acc[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.f, 0.f);
-#pragma unroll 4
-            for (int i = lane; i < R; i += 32) {
-                const float2 y = ws[i];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (l0 + u <= j) {
-                        const float2 x = __ldcg(g.V + (int64_t)(l0 + u) * g.n + r0 + i);
-                        acc[u].x = fmaf(x.x, y.x, fmaf(x.y, y.y, acc[u].x));
-                        acc[u].y = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc[u].y));
-                    }
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const float2 d = warp_sum(acc[u]);
-                if (lane == 0 && l0 + u <= j) part[(int64_t)(l0 + u) * G + b] = d;
-            }
+    gs_partials(a, ws, R, r0, j);
+    if (!gs_last_block(a.cnt)) return;
+    double ww, hh;
+    gs_reduce(a, j, true, &ww, &hh);
+    if (threadIdx.x == 0) st->ww = ww;
+}
+
+__global__ void __launch_bounds__(kGsThreads) k_gs_update(GsArgs a)
+{
+    const GmresArgs &g = a.g;
+    GmresState *st = g.st;
+    const int2 jd = __ldcv(reinterpret_cast<const int2 *>(&st->j));
+    const int j = jd.x;
+    if (jd.y) return;
+    int64_t r0;
+    const int R = gs_rows(a, r0);
+    __shared__ float2 ws[kGsMaxRows];
+    __shared__ float2 hs[kMaxRestart + 1];
+    for (int i = threadIdx.x; i < R; i += kGsThreads) ws[i] = g.w[r0 + i];
+    gs_load_h(g, hs, j);
+    gs_update(a, ws, hs, R, r0, j);
+    for (int i = threadIdx.x; i < R; i += kGsThreads) g.w[r0 + i] = ws[i];
+    // ||w_1||^2 and the dots of a possible second pass
+    gs_partials(a, ws, R, r0, j);
+    if (!gs_last_block(a.cnt)) return;
+    // the second pass's dots h_2 go to hcol only; column j of H takes them
+    // below if the test asks for the pass
+    double ww1, hh2;
+    gs_reduce(a, j, false, &ww1, &hh2);
+    // DGKS: second pass when ||w_1|| < 0.1 ||w||
+    const bool need = ww1 < 0.01 * st->ww;
+    if (need) {
+        for (int l = threadIdx.x; l <= j; l += kGsThreads) {
+            const double2 h = g.hcol[l];
+            double2 *hp = g.H + (int64_t)l * g.m + j;
+            const double2 h0 = *hp;
+            *hp = make_double2(h0.x + h.x, h0.y + h.y);
         }
-        grid_barrier(a.bar, a.err, a.spin_limit, a.hold_release);
-        // block b reduces columns b, b + G, ... (<= j)
-        if (warp == 0)
-            for (int l = b; l <= j; l += G) {
-                const FF sum = warp_sum_ff(part + (int64_t)l * G, G);
-                if (lane == 0) {
-                    const double2 h = make_double2((double)sum.hi.x + (double)sum.lo.x,
-                                                   (double)sum.hi.y + (double)sum.lo.y);
-                    g.hcol[l] = h;
-                    double2 *hp = g.H + (int64_t)l * g.m + j;
-                    if (pass == 0) *hp = h;
-                    else { const double2 h0 = __ldcg(hp); *hp = make_double2(h0.x + h.x, h0.y + h.y); }
-                }
-            }
-        grid_barrier(a.bar, a.err, a.spin_limit, a.hold_release);
-        for (int l = threadIdx.x; l <= j; l += kOrthoThreads) {
-            const double2 h = __ldcg(g.hcol + l);
-            hs[l] = make_float2((float)h.x, (float)h.y);
-        }
-        __syncthreads();
-        if (warp == 0) {
-            float hh = 0.f;
-            for (int l = lane; l <= j; l += 32) hh = fmaf(hs[l].x, hs[l].x, fmaf(hs[l].y, hs[l].y, hh));
-            for (int o = 16; o > 0; o >>= 1) hh += __shfl_xor_sync(0xffffffffu, hh, o);
-            if (lane == 0) s_hh = hh;
-        }
-        // update: w_i -= sum_l h_l v_l[i]; kCg column groups per row
-        float nrm = 0.f;
-        {
-            const int cg = threadIdx.x / kRowsPerPass, rr = threadIdx.x % kRowsPerPass;
-            for (int i0 = 0; i0 < R; i0 += kRowsPerPass) {
-                const int i = i0 + rr;
-                float2 acc = make_float2(0.f, 0.f);
-                if (i < R) {
-                    const float2 *vp = g.V + r0 + i;
-#pragma unroll 8
-                    for (int l = cg; l <= j; l += kCg) {
-                        const float2 v = __ldcg(vp + (int64_t)l * g.n);
-                        const float2 h = hs[l];
-                        acc.x = fmaf(h.x, v.x, fmaf(-h.y, v.y, acc.x));
-                        acc.y = fmaf(h.x, v.y, fmaf(h.y, v.x, acc.y));
-                    }
-                }
-                cpart[threadIdx.x] = acc;
-                __syncthreads();
-                if (cg == 0 && i < R) {
-                    float2 c = cpart[rr];
-#pragma unroll
-                    for (int q = 1; q < kCg; ++q) {
-                        c.x += cpart[rr + q * kRowsPerPass].x;
-                        c.y += cpart[rr + q * kRowsPerPass].y;
-                    }
-                    float2 wv = ws[i];
-                    wv.x -= c.x;
-                    wv.y -= c.y;
-                    ws[i] = wv;
-                    g.w[r0 + i] = wv;
-                    nrm = fmaf(wv.x, wv.x, fmaf(wv.y, wv.y, nrm));
-                }
-                __syncthreads();
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-        if (lane == 0) red[warp] = nrm;
-        __syncthreads();
-        if (warp == 0) {
-            float v = lane < nwarp ? red[lane] : 0.f;
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) npart[b] = make_float2(v, 0.f);
-        }
-        grid_barrier(a.bar, a.err, a.spin_limit, a.hold_release);
-        if (warp == 0) {
-            const FF v = warp_sum_ff(npart, G);
-            if (lane == 0) s_nn = (double)v.hi.x + (double)v.lo.x;
-        }
-        __syncthreads();
-        nn = s_nn;
-        if (pass == 1) break;
-        // ||w_before||^2 = ||w_after||^2 + sum |h_l|^2; second pass when
-        // ||w_after|| < 0.1 ||w_before||
-        const bool need = (float)nn * 0.99f < 0.01f * s_hh;
-        if (b == 0 && threadIdx.x == 0) {
-            st->reorth = need;
-            st->n_reorth += need;
-        }
-        if (!need) break;
     }
-    if (b == 0 && threadIdx.x == 0) st->nn = nn;
+    if (threadIdx.x == 0) {
+        st->reorth = need;
+        st->n_reorth += need;
+        st->nn = need ? fmax(ww1 - hh2, 0.0) : ww1;
+    }
+}
+
+__global__ void __launch_bounds__(kGsThreads) k_gs_finish(GsArgs a)
+{
+    const GmresArgs &g = a.g;
+    GmresState *st = g.st;
+    const int2 jd = __ldcv(reinterpret_cast<const int2 *>(&st->j));
+    const int j = jd.x;
+    if (jd.y) return;
+    const int reorth = __ldcv(&st->reorth);
+    const double nn = __ldcv(&st->nn);
+    int64_t r0;
+    const int R = gs_rows(a, r0);
+    __shared__ float2 ws[kGsMaxRows];
+    __shared__ float2 hs[kMaxRestart + 1];
+    for (int i = threadIdx.x; i < R; i += kGsThreads) ws[i] = g.w[r0 + i];
+    if (reorth) {
+        gs_load_h(g, hs, j);
+        gs_update(a, ws, hs, R, r0, j);
+    } else {
+        __syncthreads();
+    }
     // next basis vector and the product inputs (unused when the cycle ends)
     const float nf = (float)nn;
     const float sc = nf > 0.f ? 1.f / sqrtf(nf) : 0.f;
     float2 *vn = g.V + (int64_t)(j + 1) * g.n;
-    for (int i = threadIdx.x; i < R; i += kOrthoThreads) {
+    for (int i = threadIdx.x; i < R; i += kGsThreads) {
         const float2 xv = cscale(ws[i], sc);
         vn[r0 + i] = xv;
         prep_store(a.next, r0 + i, xv);
     }
 }
 
-// Givens step of the column k_gm_ortho just formed (one warp).
+// Givens step of the column the Gram-Schmidt kernels just formed (one warp).
 __global__ void k_gm_givens(GmresArgs a)
 {
     GmresState *st = a.st;
-    if (*(volatile int *)&st->done || st->fault) return;
+    if (*(volatile int *)&st->done) return;
     gm_givens_warp(a, st->nn, st->j);
 }
 

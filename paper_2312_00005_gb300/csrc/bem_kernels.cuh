@@ -6,7 +6,7 @@
 
 namespace bem {
 
-constexpr int kMaxRestart = 256;
+constexpr int kMaxRestart = 1024;
 constexpr int kMaxFarLevels = 16;
 
 // Near columns of a leaf: runs of consecutive elements (the elements of
@@ -44,9 +44,10 @@ struct GmresState {
     double bnorm, beta, resid, tol, hn;
     int reorth;              // second Gram-Schmidt pass needed for the current column
     int n_reorth;            // columns that needed it
-    int fault;               // a grid barrier wait gave up (never reset by a restart)
-    double nn;               // ||w||^2 after orthogonalisation (k_gm_ortho -> k_gm_givens)
-    // Skip flag of the product kernels: a copy of done taken by k_gm_ortho
+    int fault;               // unused (kept zero)
+    double nn;               // ||w||^2 after orthogonalisation (k_gs_update -> k_gs_finish, k_gm_givens)
+    double ww;               // ||w||^2 before it (k_gs_dots -> k_gs_update)
+    // Skip flag of the product kernels: a copy of done taken by k_gs_dots
     // (in stream order before the next product).  done itself is set by
     // k_gm_givens on a side stream while that product runs, so reading it
     // there could differ between the threads of one block.
@@ -216,28 +217,22 @@ struct GmresArgs {
     int m;
 };
 
-// One Gram-Schmidt step of the Arnoldi process in a single cooperative
-// launch (all blocks co-resident): dots, update, norm and the next
-// product's inputs, separated by grid barriers whose waits give up after a
-// bounded number of polls (err = 1).  k_gm_givens then takes the Givens
-// step.  Partials are stored as float2 inside the part / normpart buffers.
-struct OrthoArgs {
-    GmresArgs g;             // g.nblk = gridDim.x; g.part [m + 1][nblk], g.normpart [nblk]
+// One Gram-Schmidt step of the Arnoldi process in three launches
+// (k_gs_dots, k_gs_update, k_gs_finish) with no waits between blocks: each
+// reduction is finished by the last block to arrive.
+struct GsArgs {
+    GmresArgs g;             // g.nblk = gridDim.x; g.part [m + 1][nblk], g.normpart [nblk] (float2 partials)
     PrepArgs next;           // inputs of the next product, formed from V_{j+1}
     const float2 *wnear;     // near-field part of the product (g.w holds the far part)
-    unsigned int *bar;       // [2] grid barrier: arrivals, generation (zero at the first launch)
-    int *err;                // &st->fault
+    unsigned int *cnt;       // arrival counter of the last-block reductions (zero between uses)
     int rows;                // rows of the basis per block
-    unsigned int spin_limit; // polls after which a barrier wait gives up (kSpinLimit)
-    int hold_release;        // test hook: the last arrival never releases the others, so
-                             // every wait runs out after spin_limit polls (0: off)
 };
-// polls of a grid-barrier wait before it gives up and sets the fault flag
-constexpr unsigned int kSpinLimit = 1u << 23;
-constexpr int kOrthoThreads = 256;
-constexpr int kOrthoMaxBlocks = 512;   // partials per reduction: 32 lanes x 16 loads
-constexpr int kOrthoMaxRows = 1024;    // rows per block staged in shared memory
-__global__ void k_gm_ortho(OrthoArgs a);
+constexpr int kGsThreads = 256;
+constexpr int kGsMaxBlocks = 512;   // partials per reduction: 32 lanes x 16 loads
+constexpr int kGsMaxRows = 1024;    // rows per block staged in shared memory
+__global__ void k_gs_dots(GsArgs a);
+__global__ void k_gs_update(GsArgs a);
+__global__ void k_gs_finish(GsArgs a);
 __global__ void k_gm_givens(GmresArgs a);
 __global__ void k_gm_backsolve(const GmresState *st, const double2 *H, const double2 *g, double2 *y, int m,
                                int smem_cols);
