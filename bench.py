@@ -571,10 +571,13 @@ def run_bands(args):
     stream = torch.cuda.current_stream()
     kw = dict(tol=args.tol, max_iter=args.max_iter, points=pts)
     # GMRES(100) stalls on this surface above about 5 kHz (the FP64 oracle
-    # too: 398 products against 128 unrestarted at 8000 elements, 5.3 kHz);
-    # the band workload runs GMRES(256) unless --restart says otherwise
-    restart = args.restart if args.restart > 0 else 256
-    mkw = dict(trunc_factor=args.trunc_factor, restart=restart)
+    # too: 398 products against 128 unrestarted at 8000 elements, 5.3 kHz):
+    # the band workload runs GMRES without restarts up to max_iter (1000)
+    # products and the block-Jacobi preconditioner over the leaf boxes
+    # (the block form of the paper's row scaling, Sec. 3.2), unless
+    # --restart / --no-block-jacobi say otherwise
+    restart = args.restart if args.restart > 0 else min(1024, args.max_iter)
+    mkw = dict(trunc_factor=args.trunc_factor, restart=restart, block_jacobi=0 if args.no_block_jacobi else 1)
     nodes, tris = inputs.bumpy_ellipsoid(bands[0][0])
     mesh = bemfmm.Mesh(nodes, tris, **mkw)
     mesh.solve_sweep(bands[0][1][:args.warmup], src, **kw)
@@ -610,7 +613,7 @@ def run_bands(args):
         "max_relres": worst,
         "config": {"workload": "head_bands_c3", "frequencies": nfreq, "f_hz": [bands[0][1][0], bands[-1][1][-1]],
                    "bands": rows, "source": "point, 1 mm off the surface at +y", "tol": args.tol,
-                   "gmres_restart": restart,
+                   "gmres_restart": restart, "block_jacobi": mkw["block_jacobi"],
                    "trunc_factor": args.trunc_factor, "field_points": int(pts.shape[0]),
                    "l2": "not flushed; every frequency computes fresh near-field entries"},
     }))
@@ -690,6 +693,8 @@ def main():
     ap.add_argument("--restart", type=int, default=0,
                     help="GMRES restart length (default: 100 for the sphere, 256 for head_bands_c3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-block-jacobi", action="store_true",
+                    help="head_bands_c3: no block-Jacobi preconditioner")
     ap.add_argument("--no-sweep", action="store_true",
                     help="one bem_solve call per frequency (default: the steps as one bem_solve_sweep call)")
     ap.add_argument("--leaf-edge", type=float, default=0.0,

@@ -114,6 +114,14 @@ typedef struct bem_params {
                                bem_matvec (asymmetric_pairs = 0) at the cost of a few more
                                near pairs; 0 (default): the source cluster's area, the bound
                                r~ of Sec. 3.1.4 needs.  Other values: BEM_E_ARG.              */
+    int32_t block_jacobi;   /* 1: block-Jacobi preconditioner, the block form of the row scaling
+                               of Sec. 3.2: bem_solve / bem_solve_sweep run GMRES on
+                               P A u = P b with P the inverse of A's block diagonal over the
+                               leaf boxes of the plan (each split into runs of at most 64
+                               elements; bem_mesh_blocks lists them), and tol and relres refer
+                               to that preconditioned residual; the solution is that of
+                               A u = b.  0: off (default).  Not together with row_scaling;
+                               other values: BEM_E_ARG.                                        */
 } bem_params;
 
 typedef struct bem_medium {
@@ -336,6 +344,13 @@ int bem_mesh_check_host(const double *nodes, int64_t n_nodes, const int32_t *tri
 
 /* Plan statistics for a frequency (builds the plan if needed). */
 int bem_mesh_stats(void *mesh, double freq_hz, const bem_medium *medium, bem_plan_stats *out);
+
+/* The sub-blocks of the block-Jacobi preconditioner (bem_params.block_jacobi)
+ * in the plan for a frequency: block_of (host int32 [n_tris], caller order)
+ * receives each element's sub-block index.  Sub-blocks are the leaf boxes of
+ * the plan's octree, each split into runs of at most 64 elements of its
+ * Morton-ordered element list.  Builds the plan if needed. */
+int bem_mesh_blocks(void *mesh, double freq_hz, const bem_medium *medium, int32_t *block_of);
 
 /* The same statistics computed on the host only (no CUDA call): geometry,
  * clustering and the near / interaction lists of Sec. 3.3.4 for the given

@@ -42,6 +42,7 @@ class Params(ctypes.Structure):
         ("stability_max", ctypes.c_double), ("near_store", ctypes.c_int32), ("restart", ctypes.c_int32),
         ("autotune", ctypes.c_int32), ("tau", ctypes.c_double), ("row_scaling", ctypes.c_int32),
         ("check_orientation", ctypes.c_int32), ("symmetric_far", ctypes.c_int32),
+        ("block_jacobi", ctypes.c_int32),
     ]
 
 
@@ -129,6 +130,7 @@ def lib():
             "bem_plan_stats_host": (ctypes.c_int, [P, i64, P, i64, ctypes.POINTER(Params), d, d,
                                                    ctypes.POINTER(PlanStats)]),
             "bem_mesh_release_plan": (ctypes.c_int, [P]),
+            "bem_mesh_blocks": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), P]),
             "bem_timing_enable": (ctypes.c_int, [ctypes.c_int]),
             "bem_timing_get": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int64)]),
@@ -505,6 +507,14 @@ class Mesh:
         d = {"iterations": info.iterations, "restarts": info.restarts, "relres": info.relres,
              "status": code, "converged": code != W_NOT_CONVERGED}
         return loss.value, grad[0::2] + 1j * grad[1::2], p, q, d
+
+    def blocks(self, freq, c=343.0, rho=1.21):
+        """Sub-block index of each element (caller order) of the block-Jacobi
+        preconditioner in the plan for freq (int32 numpy array [n])."""
+        out = np.empty(self.n, dtype=np.int32)
+        med = self._medium(c, rho)
+        _check(lib().bem_mesh_blocks(self._h, float(freq), ctypes.byref(med), out.ctypes.data_as(ctypes.c_void_p)))
+        return out
 
     def release_plan(self):
         """Free the per-frequency plan; the next call rebuilds it."""

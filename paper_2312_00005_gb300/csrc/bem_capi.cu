@@ -275,6 +275,10 @@ struct Lists {
     // expensive near pairs (row, position), listed on first use
     DevArr<int2> heavy;
     int64_t n_heavy = -1;
+    // block-Jacobi sub-blocks (first element, size, offset of the inverse)
+    std::vector<int4> h_bj;
+    DevArr<int4> bj;
+    int64_t bj_entries = 0;
 };
 
 // Per-depth element data (frequency independent).
@@ -365,6 +369,7 @@ struct bem_mesh_impl {
     DevArr<int> type;
     DevArr<float2> xint, ynear, tmp, tmp2, bvec, uvec;
     DevArr<float2> dinv;         // row scaling 1 / A_ii (internal order) when row_scaling is on
+    DevArr<float2> bjinv;        // block-Jacobi inverses of the diagonal sub-blocks when block_jacobi is on
     // admittance gradient: forward u, field at the points, G_f^T conj(f),
     // coefficients of the q-operator, region per element, accumulators
     DevArr<float2> uadj, fadj, gadj, adj_cp, adj_cq;
@@ -374,9 +379,10 @@ struct bem_mesh_impl {
     DevArr<float4> wts;          // far-field weights (alpha, c) per element
     // GMRES workspace
     DevArr<float2> V, w;
-    DevArr<double2> H, cs, sn, g_, hcol, part, yv;
+    DevArr<double2> H, cs, sn, g_, yv;
     DevArr<double> normpart;
-    DevArr<unsigned int> gbar;   // arrival counter of the Gram-Schmidt reductions
+    DevArr<double> gsacc;        // Gram-Schmidt norm sums [2][2] (per parity of the column)
+    DevArr<double2> gsh2;        // Gram-Schmidt second-pass dots [2][m + 1]
     DevArr<GmresState> st;
     // frequency state: cur serves the products and the solve; next is filled
     // by the setup thread of a frequency sweep for the following frequency
@@ -494,6 +500,24 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
         std::stable_sort(dt.begin(), dt.end(), [](int2 u, int2 v) { return u.y - u.x > v.y - v.x; });
         Ls->n_dis_tasks = (int)dt.size();
         Ls->dis_tasks.upload(dt, s);
+    }
+    {
+        // block-Jacobi sub-blocks: each leaf split into ceil(count / kBjMax)
+        // runs of consecutive elements of nearly equal size
+        int64_t off = 0;
+        for (int t = 0; t < nl; ++t) {
+            const int64_t a = leaf_start[t], cnt = leaf_start[t + 1] - a;
+            const int64_t nsub = (cnt + kBjMax - 1) / kBjMax;
+            for (int64_t q = 0; q < nsub; ++q) {
+                const int64_t b0 = a + cnt * q / nsub, b1 = a + cnt * (q + 1) / nsub;
+                const int nb = (int)(b1 - b0);
+                Ls->h_bj.push_back(make_int4((int)b0, nb, (int)off, 0));
+                off += (int64_t)nb * nb;
+            }
+        }
+        if (off > INT_MAX) throw Fail{set_err(BEM_E_ARG, "block-Jacobi blocks exceed the 32-bit offset range")};
+        Ls->bj_entries = off;
+        Ls->bj.upload(Ls->h_bj, s);
     }
     Ls->nnz = row_ptr[M.n];
     Ls->leaf_of.upload(leaf_of, s);
@@ -1482,6 +1506,7 @@ void bem_params_default(bem_params *p)
     p->row_scaling = 0;
     p->check_orientation = 0;
     p->symmetric_far = 0;
+    p->block_jacobi = 0;
 }
 
 const char *bem_last_error(void) { return g_err.c_str(); }
@@ -1507,6 +1532,9 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
     if (p.check_orientation != 0 && p.check_orientation != 1)
         return set_err(BEM_E_ARG, "check_orientation must be 0 or 1");
     if (p.symmetric_far != 0 && p.symmetric_far != 1) return set_err(BEM_E_ARG, "symmetric_far must be 0 or 1");
+    if (p.block_jacobi != 0 && p.block_jacobi != 1) return set_err(BEM_E_ARG, "block_jacobi must be 0 or 1");
+    if (p.block_jacobi && p.row_scaling)
+        return set_err(BEM_E_ARG, "row_scaling and block_jacobi are alternatives: set at most one");
     if (!(p.quad_tol > 0) || !(p.rt_subdiv > 0) || !(p.admissibility > 0) || p.L_min < 1 || p.L_min > 200)
         return set_err(BEM_E_ARG, "invalid parameter");
     if (p.check_orientation) {
@@ -1738,6 +1766,8 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     const int64_t n = M.n;
     const int m = M.prm.restart;
     const bool rscale = M.prm.row_scaling != 0 && !transposed;
+    const bool bjac = M.prm.block_jacobi != 0 && !transposed;
+    const Lists &Lb = *fr(M).plan->lists;
     GmresResult R;
     if (transposed) M.rowf.alloc(n);   // before the Arnoldi steps are captured (no allocation in a capture)
     // GMRES workspace
@@ -1747,28 +1777,22 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     M.cs.alloc(m);
     M.sn.alloc(m);
     M.g_.alloc(m + 1);
-    M.hcol.alloc(m + 1);
     M.yv.alloc(m + 1);
-    // the Gram-Schmidt step: block b owns rows [b R, b R + R), R <= kGsMaxRows;
-    // about 128 rows per block (a short reduction for the last block), at
-    // most 256 blocks unless the rows need more
+    // the Gram-Schmidt step: block b owns rows [b R, b R + R), R <= kGsMaxRows
+    // (staged in shared memory); about 256 rows per block, so that each sum
+    // takes few atomic additions, at most 256 blocks unless the rows need more
     int nblk = 0;
     {
-        const int64_t want = std::min<int64_t>((n + 127) / 128, 256);
+        const int64_t want = std::min<int64_t>((n + 255) / 256, 256);
         const int64_t need = (n + kGsMaxRows - 1) / kGsMaxRows;
         nblk = (int)std::max<int64_t>(1, std::max(want, need));
-        if (nblk > kGsMaxBlocks)
-            throw Fail{set_err(BEM_E_ARG, "GMRES: " + std::to_string(n) + " unknowns exceed the Gram-Schmidt "
-                                              "step's limit of " +
-                                              std::to_string((int64_t)kGsMaxBlocks * kGsMaxRows))};
     }
     const int orows = (int)((n + nblk - 1) / nblk);
-    M.part.alloc((size_t)(m + 1) * nblk);
+    M.gsacc.alloc(4);
+    M.gsh2.alloc((size_t)2 * (m + 1));
     const int nnorm = (int)nblocks(n, 256);
     M.normpart.alloc(std::max(nnorm, nblk));
     M.st.alloc(1);
-    M.gbar.alloc(1);
-    ck(cudaMemsetAsync(M.gbar.p, 0, sizeof(unsigned int), s), "memset counter");
     GmresState hs;
     memset(&hs, 0, sizeof hs);
     hs.tol = tol;
@@ -1794,7 +1818,8 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     ck_launch("k_norm_part");
     {
         KTimer kt_("k_gm_start", s);
-        k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.bvec.p, n, M.normpart.p, nnorm, M.g_.p, m, 1);
+        k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.bvec.p, n, M.normpart.p, nnorm, M.g_.p, m, 1,
+                                                   M.gsacc.p, M.gsh2.p);
     }
     ck_launch("k_gm_start");
     prep_v0();
@@ -1808,10 +1833,8 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     ga.w = M.w.p;
     ga.n = n;
     ga.st = M.st.p;
-    ga.part = M.part.p;
     ga.nblk = nblk;
     ga.H = M.H.p;
-    ga.hcol = M.hcol.p;
     ga.cs = M.cs.p;
     ga.sn = M.sn.p;
     ga.g = M.g_.p;
@@ -1819,7 +1842,8 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     ga.m = m;
     oa.next = prep_args(M, fr(M).cp.p, fr(M).cq.p, nullptr);
     oa.wnear = M.ynear.p;
-    oa.cnt = M.gbar.p;
+    oa.acc = M.gsacc.p;
+    oa.h2 = M.gsh2.p;
     oa.rows = orows;
     // one Arnoldi step: product of v_j (inputs already formed), then the
     // fused Gram-Schmidt / Givens step, which also forms v_{j+1}
@@ -1866,6 +1890,14 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
                 k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.ynear.p, M.dinv.p, n, done);
             }
             ck_launch("k_row_scale");
+        }
+        if (bjac) {
+            // w <- P (far + near), the near part cleared
+            {
+                KTimer kt_("k_bj_apply", s);
+                k_bj_apply<<<(unsigned)Lb.h_bj.size(), kBjMax, 0, s>>>(Lb.bj.p, M.bjinv.p, M.w.p, M.ynear.p, done);
+            }
+            ck_launch("k_bj_apply");
         }
     };
     // nsteps Arnoldi steps, each the fused Gram-Schmidt step of column j
@@ -1965,7 +1997,14 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
             }
             ck_launch("k_row_scale");
         }
-        k_rsub<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.bvec.p, n);   // w = b - A x (row-scaled: D^-1 (b - A x))
+        if (bjac) {
+            {
+                KTimer kt_("k_bj_apply", s);
+                k_bj_apply<<<(unsigned)Lb.h_bj.size(), kBjMax, 0, s>>>(Lb.bj.p, M.bjinv.p, M.w.p, nullptr, nullptr);
+            }
+            ck_launch("k_bj_apply");
+        }
+        k_rsub<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.bvec.p, n);   // w = b - A x (preconditioned: P (b - A x))
         ck_launch("k_rsub");
         {
             KTimer kt_("k_norm_part", s);
@@ -1974,7 +2013,8 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
         ck_launch("k_norm_part");
         {
             KTimer kt_("k_gm_start", s);
-            k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.w.p, n, M.normpart.p, nnorm, M.g_.p, m, 0);
+            k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.w.p, n, M.normpart.p, nnorm, M.g_.p, m, 0,
+                                                       M.gsacc.p, M.gsh2.p);
         }
         ck_launch("k_gm_start");
         prep_v0();
@@ -2039,6 +2079,25 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
                 k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(M.bvec.p, nullptr, M.dinv.p, n, nullptr);
             }
             ck_launch("k_row_scale");
+        }
+        // block-Jacobi (the block form of the row scaling of Sec. 3.2):
+        // GMRES on P A u = P b, P the inverse of A's block diagonal
+        if (M.prm.block_jacobi) {
+            const Lists &Lb = *P.lists;
+            M.bjinv.alloc((size_t)std::max<int64_t>(1, Lb.bj_entries));
+            reset_err(M);
+            NearArgs na = near_args(M, P, fr(M).cp.p, fr(M).cq.p);
+            {
+                KTimer kt_("k_bj_factor", s);
+                k_bj_factor<<<(unsigned)Lb.h_bj.size(), 256, 0, s>>>(na, Lb.bj.p, M.bjinv.p, fr(M).err.p);
+            }
+            ck_launch("k_bj_factor");
+            check_err(M);
+            {
+                KTimer kt_("k_bj_apply", s);
+                k_bj_apply<<<(unsigned)Lb.h_bj.size(), kBjMax, 0, s>>>(Lb.bj.p, M.bjinv.p, M.bvec.p, nullptr, nullptr);
+            }
+            ck_launch("k_bj_apply");
         }
         ck(cudaStreamSynchronize(s), "sync");
         auto t_rhs = std::chrono::steady_clock::now();
@@ -2560,6 +2619,29 @@ int bem_plan_stats_host(const double *nodes, int64_t n_nodes, const int32_t *tri
         return BEM_OK;
     } catch (std::bad_alloc &) {
         return set_err(BEM_E_OOM, "host allocation failed");
+    }
+}
+
+int bem_mesh_blocks(void *mesh, double freq_hz, const bem_medium *medium, int32_t *block_of)
+{
+    if (!mesh || !block_of) return set_err(BEM_E_ARG, "bad argument");
+    auto &M = *(bem_mesh_impl *)mesh;
+    try {
+        double c, rho;
+        medium_of(medium, c, rho);
+        if (!(freq_hz > 0)) return set_err(BEM_E_ARG, "frequency must be positive");
+        ck(cudaSetDevice(M.device), "cudaSetDevice");
+        ensure_work(M);
+        build_plan_dev(M, freq_hz, c);
+        ck(cudaStreamSynchronize(M.s), "sync");
+        const Lists &L = *fr(M).plan->lists;
+        for (size_t b = 0; b < L.h_bj.size(); ++b) {
+            const int4 B = L.h_bj[b];
+            for (int r = 0; r < B.y; ++r) block_of[M.t.perm[B.x + r]] = (int32_t)b;
+        }
+        return BEM_OK;
+    } catch (Fail &f) {
+        return f.code;
     }
 }
 

@@ -458,6 +458,149 @@ __global__ void k_row_scale(float2 *__restrict__ y, float2 *__restrict__ y2, con
     if (y2) y2[i] = cmul(y2[i], d);
 }
 
+// Block-Jacobi preconditioner (the block form of the solver's row scaling,
+// Sec. 3.2): P = inverse of the block diagonal of A over sub-blocks of at
+// most kBjMax consecutive elements of one leaf (blocks[b] = (first element,
+// size, offset of its inverse, 0)).  One CUDA block per sub-block: the
+// entries A_ij of the sub-block (bm_entry, the stored near field's values),
+// then Gauss-Jordan inversion in place with partial pivoting in shared
+// memory (FP32 complex).  The inverse is stored column-major so that the
+// apply kernel's threads (one per row) read consecutive entries.  A zero
+// pivot leaves the sub-block's inverse the identity (no preconditioning
+// there); err takes the subdivision limit of the entries, as for the stored
+// near field.
+__global__ void __launch_bounds__(256) k_bj_factor(NearArgs a, const int4 *__restrict__ blocks, float2 *__restrict__ binv,
+                                                   int *__restrict__ err)
+{
+    __shared__ float2 A[kBjMax][kBjMax + 1];
+    __shared__ int piv[kBjMax];
+    __shared__ int s_p;
+    __shared__ bool s_bad;
+    const int4 B = blocks[blockIdx.x];
+    const int64_t e0 = B.x;
+    const int nb = B.y;
+    const QuadTables &Q = *a.Q;
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+        const int r = idx / nb, c = idx % nb;
+        const int64_t i = e0 + r, j = e0 + c;
+        const float4 ch = a.E.chi[i], cl = a.E.clo[i];
+        const double xd[3] = {a.E.cd[3 * i], a.E.cd[3 * i + 1], a.E.cd[3 * i + 2]};
+        float2 v;
+        if (!bm_entry(a.E, i, j, f3(ch), f3(cl), xd, f3(a.E.nrm[i]), a.k, a.ik_inv, a.tau, Q, a.cp[j], a.cq[j], v)) {
+            atomicMin(err, (int)j);
+            v = make_float2(r == c ? 1.f : 0.f, 0.f);
+        }
+        A[r][c] = v;
+    }
+    if (threadIdx.x == 0) s_bad = false;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < nb; ++k) {
+        // pivot: the largest |A[i][k]|, i >= k (warp 0)
+        if (warp == 0) {
+            float best = -1.f;
+            int bi = k;
+            for (int i = k + lane; i < nb; i += 32) {
+                const float m = A[i][k].x * A[i][k].x + A[i][k].y * A[i][k].y;
+                if (m > best) { best = m; bi = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) {
+                s_p = bi;
+                piv[k] = bi;
+                if (!(best > 0.f)) s_bad = true;
+            }
+        }
+        __syncthreads();
+        if (s_bad) break;
+        const int p = s_p;
+        if (p != k)
+            for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+                const float2 t = A[k][c];
+                A[k][c] = A[p][c];
+                A[p][c] = t;
+            }
+        __syncthreads();
+        const float2 d = A[k][k];
+        const float dm = 1.f / (d.x * d.x + d.y * d.y);
+        const float2 inv = make_float2(d.x * dm, -d.y * dm);
+        __syncthreads();
+        // row k /= pivot (the pivot's own place becomes 1 / pivot)
+        for (int c = threadIdx.x; c < nb; c += blockDim.x) A[k][c] = c == k ? inv : cmul(A[k][c], inv);
+        __syncthreads();
+        // eliminate column k from the other rows (their column k becomes -f / pivot)
+        for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+            const int i = idx / nb, c = idx % nb;
+            if (i == k) continue;
+            const float2 f = A[i][k];
+            if (c == k) continue;
+            A[i][c] = csub(A[i][c], cmul(f, A[k][c]));
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb; i += blockDim.x)
+            if (i != k) A[i][k] = make_float2(-(A[i][k].x * inv.x - A[i][k].y * inv.y),
+                                              -(A[i][k].x * inv.y + A[i][k].y * inv.x));
+        __syncthreads();
+    }
+    if (s_bad) {
+        for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x)
+            binv[B.z + idx] = make_float2((idx / nb) == (idx % nb) ? 1.f : 0.f, 0.f);
+        return;
+    }
+    // undo the row exchanges as column exchanges, last first
+    for (int k = nb - 1; k >= 0; --k) {
+        const int p = piv[k];
+        if (p != k)
+            for (int r = threadIdx.x; r < nb; r += blockDim.x) {
+                const float2 t = A[r][k];
+                A[r][k] = A[r][p];
+                A[r][p] = t;
+            }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+        const int c = idx / nb, r = idx % nb;      // column-major
+        binv[B.z + idx] = A[r][c];
+    }
+}
+
+// w <- P (w + wnear) over the sub-blocks (wnear, when given, is cleared):
+// the preconditioner applied to a product whose two parts the Gram-Schmidt
+// step would add, or to a right-hand side / residual (wnear null).  One block
+// of kBjMax threads per sub-block, one thread per row.  Skips with the
+// product kernels.
+__global__ void __launch_bounds__(kBjMax) k_bj_apply(const int4 *__restrict__ blocks, const float2 *__restrict__ binv,
+                                                     float2 *__restrict__ w, float2 *__restrict__ wnear,
+                                                     const int *skip)
+{
+    if (skip_now(skip)) return;
+    __shared__ float2 xs[kBjMax];
+    const int4 B = blocks[blockIdx.x];
+    const int nb = B.y;
+    const int r = threadIdx.x;
+    if (r < nb) {
+        float2 v = w[B.x + r];
+        if (wnear) v = cadd(v, wnear[B.x + r]);
+        xs[r] = v;
+    }
+    __syncthreads();
+    if (r >= nb) return;
+    const float2 *__restrict__ col = binv + B.z + r;
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+    int c = 0;
+    for (; c + 1 < nb; c += 2) {
+        acc0 = cfma(col[(int64_t)c * nb], xs[c], acc0);
+        acc1 = cfma(col[(int64_t)(c + 1) * nb], xs[c + 1], acc1);
+    }
+    if (c < nb) acc0 = cfma(col[(int64_t)c * nb], xs[c], acc0);
+    w[B.x + r] = cadd(acc0, acc1);
+    if (wnear) wnear[B.x + r] = make_float2(0.f, 0.f);
+}
+
 // ------------------------------------------------------------------ adjoint
 // Near part of the transposed product: y_j = sum_i A_ij x_i over the rows i
 // whose leaves are in the near list of j's own leaf (the lists read
@@ -1467,20 +1610,23 @@ __device__ __forceinline__ FF warp_sum_ff(const float2 *p, int n)
 // Classical Gram-Schmidt with selective reorthogonalisation (DGKS: a second
 // pass when ||w_1|| < 0.1 ||w||) for Arnoldi column j, in three launches with
 // no block ever waiting for another:
-//   k_gs_dots    w = (far + near part of A v_j); partial dots V_l^H w and
-//                ||w||^2 per block; the last block to finish reduces them:
-//                h = V^H w (column j of H), ||w||^2;
-//   k_gs_update  w_1 = w - V h; partial ||w_1||^2 and V_l^H w_1 per block; the
-//                last block reduces them and applies the DGKS test: without a
-//                second pass nn = ||w_1||^2, with one h_2 = V^H w_1 is added
-//                to column j of H and nn = ||w_1||^2 - |h_2|^2 (accurate: h_2
-//                is small against w_1);
-//   k_gs_finish  v_{j+1} = (w_1 [- V h_2]) / sqrt(nn) and the next product's
-//                inputs.
-// Block b owns rows [b R, b R + R) of every vector: FP32 sums within a block,
-// compensated FP32 across blocks in a fixed order (so the result does not
-// depend on which block finishes last).  The Givens step (k_gm_givens)
-// follows on a side stream.
+//   k_gs_dots    w = (far + near part of A v_j); each block adds its partial
+//                dots V_l^H w into column j of H and its partial ||w||^2
+//                into acc (FP64 atomics);
+//   k_gs_update  w_1 = w - V h; partial ||w_1||^2 and V_l^H w_1 (the dots of
+//                a possible second pass) added into acc and h2;
+//   k_gs_finish  every block takes the same DGKS decision from the sums;
+//                without a second pass nn = ||w_1||^2, with one h_2 is added
+//                to column j of H, w_2 = w_1 - V h_2 and nn = ||w_1||^2 -
+//                |h_2|^2 (accurate: h_2 is small against w_1); v_{j+1} =
+//                w / sqrt(nn) and the next product's inputs.
+// Block b owns rows [b R, b R + R) of every vector, with FP32 sums within a
+// block.  The FP64 sums of the blocks' FP32 partials are exact whenever the
+// partials span fewer than 29 binary orders of magnitude, so they do not
+// depend on the order in which the blocks add them.  acc and h2 alternate
+// between two copies by the parity of j: k_gs_finish clears the copy of
+// step j + 1 (k_gm_start clears both at the start of a cycle, where H is
+// cleared too).  The Givens step (k_gm_givens) follows on a side stream.
 __device__ __forceinline__ int gs_rows(const GsArgs &a, int64_t &r0)
 {
     r0 = (int64_t)blockIdx.x * a.rows;
@@ -1488,15 +1634,20 @@ __device__ __forceinline__ int gs_rows(const GsArgs &a, int64_t &r0)
     return rem <= 0 ? 0 : (int)(rem < a.rows ? rem : (int64_t)a.rows);
 }
 
-// Partial dots part[l G + b] = sum_{i in block} conj(V_l[i]) ws[i], l <= j,
-// and npart[b] = sum_{i in block} |ws[i]|^2.
-__device__ void gs_partials(const GsArgs &a, const float2 *ws, int R, int64_t r0, int j)
+__device__ __forceinline__ void atomic_add_c(double2 *p, float2 v)
+{
+    atomicAdd(&p->x, (double)v.x);
+    atomicAdd(&p->y, (double)v.y);
+}
+
+// Partial dots sum_{i in block} conj(V_l[i]) ws[i], l <= j, added into
+// dst[l * stride], and the partial sum_{i in block} |ws[i]|^2 added into *nrm.
+__device__ void gs_partials(const GsArgs &a, const float2 *ws, int R, int64_t r0, int j, double2 *dst,
+                            int64_t stride, double *nrm)
 {
     const GmresArgs &g = a.g;
-    const int G = gridDim.x, b = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nwarp = kGsThreads / 32;
-    float2 *part = (float2 *)g.part;
     for (int l0 = warp * 8; l0 <= j; l0 += nwarp * 8) {
         float2 acc[8];
 #pragma unroll
@@ -1515,74 +1666,23 @@ __device__ void gs_partials(const GsArgs &a, const float2 *ws, int R, int64_t r0
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const float2 d = warp_sum(acc[u]);
-            if (lane == 0 && l0 + u <= j) part[(int64_t)(l0 + u) * G + b] = d;
+            if (lane == u && l0 + u <= j) atomic_add_c(dst + (int64_t)(l0 + u) * stride, d);
         }
     }
     __shared__ float red[nwarp];
-    float nrm = 0.f;
-    for (int i = threadIdx.x; i < R; i += kGsThreads) nrm = fmaf(ws[i].x, ws[i].x, fmaf(ws[i].y, ws[i].y, nrm));
-    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-    if (lane == 0) red[warp] = nrm;
+    float v2 = 0.f;
+    for (int i = threadIdx.x; i < R; i += kGsThreads) v2 = fmaf(ws[i].x, ws[i].x, fmaf(ws[i].y, ws[i].y, v2));
+    for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+    if (lane == 0) red[warp] = v2;
     __syncthreads();
     if (warp == 0) {
         float v = lane < nwarp ? red[lane] : 0.f;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) ((float2 *)g.normpart)[b] = make_float2(v, 0.f);
+        if (lane == 0) atomicAdd(nrm, (double)v);
     }
 }
 
-// Arrival of a block whose partials are written: true in the last block to
-// arrive (it then sees every block's partials), which also re-arms the
-// counter for the next use.
-__device__ __forceinline__ bool gs_last_block(unsigned int *cnt)
-{
-    __shared__ bool s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
-        if (s_last) *cnt = 0u;
-    }
-    __syncthreads();
-    if (s_last) __threadfence();
-    return s_last;
-}
-
-// Last block: sums the G partials of every dot (h_l, l <= j) and of the norm
-// in a fixed order; writes hcol = h (and column j of H when set_H), and
-// returns (in every thread) ||.||^2 and sum_l |h_l|^2.
-__device__ void gs_reduce(const GsArgs &a, int j, bool set_H, double *ww_out, double *hh_out)
-{
-    const GmresArgs &g = a.g;
-    const int G = gridDim.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int nwarp = kGsThreads / 32;
-    const float2 *part = (const float2 *)g.part;
-    __shared__ double s_hh[nwarp];
-    __shared__ double s_ww;
-    double hh = 0.0;
-    for (int l = warp; l <= j; l += nwarp) {
-        const FF sum = warp_sum_ff(part + (int64_t)l * G, G);
-        const double2 h = make_double2((double)sum.hi.x + (double)sum.lo.x, (double)sum.hi.y + (double)sum.lo.y);
-        hh += h.x * h.x + h.y * h.y;
-        if (lane == 0) {
-            g.hcol[l] = h;
-            if (set_H) g.H[(int64_t)l * g.m + j] = h;
-        }
-    }
-    if (lane == 0) s_hh[warp] = hh;
-    if (warp == 0) {
-        const FF v = warp_sum_ff((const float2 *)g.normpart, G);
-        if (lane == 0) s_ww = (double)v.hi.x + (double)v.lo.x;
-    }
-    __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < nwarp; ++w) t += s_hh[w];
-    *hh_out = t;
-    *ww_out = s_ww;
-}
-
-// w_1 = ws - V h (h = hcol as FP32 in hs), written back into ws.
+// w_1 = ws - V h (h as FP32 in hs), written back into ws.
 __device__ void gs_update(const GsArgs &a, float2 *ws, const float2 *hs, int R, int64_t r0, int j)
 {
     const GmresArgs &g = a.g;
@@ -1617,15 +1717,6 @@ __device__ void gs_update(const GsArgs &a, float2 *ws, const float2 *hs, int R, 
     }
 }
 
-__device__ __forceinline__ void gs_load_h(const GmresArgs &g, float2 *hs, int j)
-{
-    for (int l = threadIdx.x; l <= j; l += kGsThreads) {
-        const double2 h = __ldcg(g.hcol + l);
-        hs[l] = make_float2((float)h.x, (float)h.y);
-    }
-    __syncthreads();
-}
-
 __global__ void __launch_bounds__(kGsThreads) k_gs_dots(GsArgs a)
 {
     const GmresArgs &g = a.g;
@@ -1655,11 +1746,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_dots(GsArgs a)
         }
     }
     __syncthreads();
-    gs_partials(a, ws, R, r0, j);
-    if (!gs_last_block(a.cnt)) return;
-    double ww, hh;
-    gs_reduce(a, j, true, &ww, &hh);
-    if (threadIdx.x == 0) st->ww = ww;
+    gs_partials(a, ws, R, r0, j, g.H + j, g.m, a.acc + 2 * (j & 1));
 }
 
 __global__ void __launch_bounds__(kGsThreads) k_gs_update(GsArgs a)
@@ -1674,31 +1761,15 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_update(GsArgs a)
     __shared__ float2 ws[kGsMaxRows];
     __shared__ float2 hs[kMaxRestart + 1];
     for (int i = threadIdx.x; i < R; i += kGsThreads) ws[i] = g.w[r0 + i];
-    gs_load_h(g, hs, j);
+    for (int l = threadIdx.x; l <= j; l += kGsThreads) {
+        const double2 h = __ldcg(g.H + (int64_t)l * g.m + j);
+        hs[l] = make_float2((float)h.x, (float)h.y);
+    }
+    __syncthreads();
     gs_update(a, ws, hs, R, r0, j);
     for (int i = threadIdx.x; i < R; i += kGsThreads) g.w[r0 + i] = ws[i];
     // ||w_1||^2 and the dots of a possible second pass
-    gs_partials(a, ws, R, r0, j);
-    if (!gs_last_block(a.cnt)) return;
-    // the second pass's dots h_2 go to hcol only; column j of H takes them
-    // below if the test asks for the pass
-    double ww1, hh2;
-    gs_reduce(a, j, false, &ww1, &hh2);
-    // DGKS: second pass when ||w_1|| < 0.1 ||w||
-    const bool need = ww1 < 0.01 * st->ww;
-    if (need) {
-        for (int l = threadIdx.x; l <= j; l += kGsThreads) {
-            const double2 h = g.hcol[l];
-            double2 *hp = g.H + (int64_t)l * g.m + j;
-            const double2 h0 = *hp;
-            *hp = make_double2(h0.x + h.x, h0.y + h.y);
-        }
-    }
-    if (threadIdx.x == 0) {
-        st->reorth = need;
-        st->n_reorth += need;
-        st->nn = need ? fmax(ww1 - hh2, 0.0) : ww1;
-    }
+    gs_partials(a, ws, R, r0, j, a.h2 + (int64_t)(j & 1) * (g.m + 1), 1, a.acc + 2 * (j & 1) + 1);
 }
 
 __global__ void __launch_bounds__(kGsThreads) k_gs_finish(GsArgs a)
@@ -1708,15 +1779,33 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_finish(GsArgs a)
     const int2 jd = __ldcv(reinterpret_cast<const int2 *>(&st->j));
     const int j = jd.x;
     if (jd.y) return;
-    const int reorth = __ldcv(&st->reorth);
-    const double nn = __ldcv(&st->nn);
+    const double ww = __ldcg(a.acc + 2 * (j & 1)), w1 = __ldcg(a.acc + 2 * (j & 1) + 1);
+    // DGKS: second pass when ||w_1|| < 0.1 ||w||
+    const bool need = w1 < 0.01 * ww;
+    const double2 *h2 = a.h2 + (int64_t)(j & 1) * (g.m + 1);
     int64_t r0;
     const int R = gs_rows(a, r0);
     __shared__ float2 ws[kGsMaxRows];
     __shared__ float2 hs[kMaxRestart + 1];
+    __shared__ double s_hh;
     for (int i = threadIdx.x; i < R; i += kGsThreads) ws[i] = g.w[r0 + i];
-    if (reorth) {
-        gs_load_h(g, hs, j);
+    double nn = w1;
+    if (need) {
+        for (int l = threadIdx.x; l <= j; l += kGsThreads) {
+            const double2 h = __ldcg(h2 + l);
+            hs[l] = make_float2((float)h.x, (float)h.y);
+        }
+        if (threadIdx.x < 32) {
+            double hh = 0.0;
+            for (int l = threadIdx.x; l <= j; l += 32) {
+                const double2 h = __ldcg(h2 + l);
+                hh += h.x * h.x + h.y * h.y;
+            }
+            for (int o = 16; o > 0; o >>= 1) hh += __shfl_xor_sync(0xffffffffu, hh, o);
+            if (threadIdx.x == 0) s_hh = hh;
+        }
+        __syncthreads();
+        nn = fmax(w1 - s_hh, 0.0);
         gs_update(a, ws, hs, R, r0, j);
     } else {
         __syncthreads();
@@ -1729,6 +1818,24 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_finish(GsArgs a)
         const float2 xv = cscale(ws[i], sc);
         vn[r0 + i] = xv;
         prep_store(a.next, r0 + i, xv);
+    }
+    if (blockIdx.x == 0) {
+        if (need)
+            for (int l = threadIdx.x; l <= j; l += kGsThreads) {
+                double2 *hp = g.H + (int64_t)l * g.m + j;
+                const double2 h = h2[l], h0 = *hp;
+                *hp = make_double2(h0.x + h.x, h0.y + h.y);
+            }
+        // the other parity's sums, for step j + 1
+        double2 *h2n = a.h2 + (int64_t)((j + 1) & 1) * (g.m + 1);
+        for (int l = threadIdx.x; l <= j + 1 && l <= g.m; l += kGsThreads) h2n[l] = make_double2(0.0, 0.0);
+        if (threadIdx.x == 0) {
+            a.acc[2 * ((j + 1) & 1)] = 0.0;
+            a.acc[2 * ((j + 1) & 1) + 1] = 0.0;
+            st->reorth = need;
+            st->n_reorth += need;
+            st->nn = nn;
+        }
     }
 }
 
@@ -1800,8 +1907,14 @@ __global__ void k_gm_xupdate(float2 *__restrict__ x, const float2 *__restrict__ 
 // r = b - A x is formed by the caller; here: V_0 = r / ||r|| with ||r|| from
 // normpart, and the cycle state is reset.
 __global__ void k_gm_start(GmresState *st, float2 *__restrict__ V, const float2 *__restrict__ r, int64_t n,
-                           const double *__restrict__ normpart, int nblk, double2 *__restrict__ g, int m, int first)
+                           const double *__restrict__ normpart, int nblk, double2 *__restrict__ g, int m, int first,
+                           double *__restrict__ gs_acc, double2 *__restrict__ gs_h2)
 {
+    if (blockIdx.x == 0) {
+        // the Gram-Schmidt sums of both parities (see k_gs_dots)
+        for (int l = threadIdx.x; l < 2 * (m + 1); l += blockDim.x) gs_h2[l] = make_double2(0.0, 0.0);
+        if (threadIdx.x < 4) gs_acc[threadIdx.x] = 0.0;
+    }
     __shared__ double beta_s;
     if (threadIdx.x == 0) {
         double nn = 0.0;

@@ -45,8 +45,7 @@ struct GmresState {
     int reorth;              // second Gram-Schmidt pass needed for the current column
     int n_reorth;            // columns that needed it
     int fault;               // unused (kept zero)
-    double nn;               // ||w||^2 after orthogonalisation (k_gs_update -> k_gs_finish, k_gm_givens)
-    double ww;               // ||w||^2 before it (k_gs_dots -> k_gs_update)
+    double nn;               // ||w||^2 after orthogonalisation (k_gs_finish -> k_gm_givens)
     // Skip flag of the product kernels: a copy of done taken by k_gs_dots
     // (in stream order before the next product).  done itself is set by
     // k_gm_givens on a side stream while that product runs, so reading it
@@ -200,6 +199,10 @@ __global__ void k_field_t(ElemDev E, const QuadTables *Qp, const double *pts, in
 __global__ void k_adjoint_reduce(const float2 *u, const float2 *g, const float2 *aq, const int *region, int64_t n,
                                  float tau, double dre, double dim, const float2 *f, int64_t M, int nreg,
                                  double *acc);
+// block-Jacobi sub-blocks: at most kBjMax consecutive elements of one leaf
+constexpr int kBjMax = 64;
+__global__ void k_bj_factor(NearArgs a, const int4 *blocks, float2 *binv, int *err);
+__global__ void k_bj_apply(const int4 *blocks, const float2 *binv, float2 *w, float2 *wnear, const int *skip);
 __global__ void k_row_scale_init(NearArgs a, float2 *dinv, int *err);
 __global__ void k_row_scale(float2 *y, float2 *y2, const float2 *dinv, int64_t n, const int *skip);
 __global__ void k_sub(float2 *b, const float2 *y, int64_t n);
@@ -210,9 +213,8 @@ struct GmresArgs {
     float2 *V, *w;
     int64_t n;
     GmresState *st;
-    double2 *part;           // [m + 1][nblk] dot partials
     int nblk;
-    double2 *H, *hcol, *cs, *sn, *g;
+    double2 *H, *cs, *sn, *g;
     double *normpart;        // [nblk] norm partials
     int m;
 };
@@ -221,14 +223,14 @@ struct GmresArgs {
 // (k_gs_dots, k_gs_update, k_gs_finish) with no waits between blocks: each
 // reduction is finished by the last block to arrive.
 struct GsArgs {
-    GmresArgs g;             // g.nblk = gridDim.x; g.part [m + 1][nblk], g.normpart [nblk] (float2 partials)
+    GmresArgs g;             // g.nblk = gridDim.x
     PrepArgs next;           // inputs of the next product, formed from V_{j+1}
     const float2 *wnear;     // near-field part of the product (g.w holds the far part)
-    unsigned int *cnt;       // arrival counter of the last-block reductions (zero between uses)
+    double *acc;             // [2][2] per parity of j: ||w||^2, ||w_1||^2
+    double2 *h2;             // [2][m + 1] per parity of j: second-pass dots V^H w_1
     int rows;                // rows of the basis per block
 };
 constexpr int kGsThreads = 256;
-constexpr int kGsMaxBlocks = 512;   // partials per reduction: 32 lanes x 16 loads
 constexpr int kGsMaxRows = 1024;    // rows per block staged in shared memory
 __global__ void k_gs_dots(GsArgs a);
 __global__ void k_gs_update(GsArgs a);
@@ -238,7 +240,7 @@ __global__ void k_gm_backsolve(const GmresState *st, const double2 *H, const dou
                                int smem_cols);
 __global__ void k_gm_xupdate(float2 *x, const float2 *V, int64_t n, const GmresState *st, const double2 *y);
 __global__ void k_gm_start(GmresState *st, float2 *V, const float2 *r, int64_t n, const double *normpart, int nblk,
-                           double2 *g, int m, int first);
+                           double2 *g, int m, int first, double *gs_acc, double2 *gs_h2);
 __global__ void k_norm_part(const float2 *r, int64_t n, double *part);
 
 // Host helpers shared by the translation units (bem_capi.cu): the
