@@ -261,6 +261,24 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
               int32_t n_regions, const bem_source *srcs, int32_t n_src, double tol,
               int32_t max_iter, void *p_dev, void *q_dev, bem_solve_info *info, void *stream);
 
+/* Several right-hand sides at one frequency (the paper's input can list
+ * several plane waves and point sources, App. C.4; here each source is its
+ * own right-hand side instead of one summed incident field): solves
+ * Eq. SystemI for n_rhs (1..4) systems A u_r = b_r that share the matrix, as
+ * n_rhs calls of bem_solve with srcs + r would, with GMRES on the device for
+ * all of them in lockstep: every product takes the n_rhs basis vectors in
+ * one pass (the stored near field streamed once, one phase per element and
+ * direction pair for all of them), while each system keeps its own Krylov
+ * basis, Hessenberg matrix and convergence test.
+ *   srcs: host [n_rhs], source r makes right-hand side r (the mesh's
+ *   boundary data enter every one); p_dev, q_dev: device cf32
+ *   [n_rhs][n_tris] (q_dev may be NULL); infos: host [n_rhs] or NULL.
+ * Returns BEM_OK, BEM_W_NOT_CONVERGED (some system stopped at max_iter; its
+ * info says which), BEM_W_UNDERRESOLVED or an error. */
+int bem_solve_multi(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
+                    int32_t n_regions, const bem_source *srcs, int32_t n_rhs, double tol, int32_t max_iter,
+                    void *p_dev, void *q_dev, bem_solve_info *infos, void *stream);
+
 /* Frequency sweep (the paper solves the frequencies of a sweep
  * independently and splits sweeps into frequency ranges, appendix
  * "Command-line parameters", subsection Parallelization; the overlap below

@@ -117,6 +117,8 @@ def lib():
                                          P, P, ctypes.POINTER(SolveInfo), P]),
             "bem_evaluate": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), ctypes.POINTER(Source), i32, P, P, P,
                                             i64, P, P]),
+            "bem_solve_multi": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), P, i32, ctypes.POINTER(Source), i32, d,
+                                               i32, P, P, ctypes.POINTER(SolveInfo), P]),
             "bem_solve_sweep": (ctypes.c_int, [P, P, i32, ctypes.POINTER(Medium), P, i32, ctypes.POINTER(Source), i32,
                                                d, i32, P, P, P, i64, P, ctypes.POINTER(SolveInfo), P]),
             "bem_evaluate_velocity": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), ctypes.POINTER(Source), i32, P,
@@ -402,6 +404,34 @@ class Mesh:
              "setup_seconds": info.setup_seconds, "rhs_seconds": info.rhs_seconds,
              "gmres_seconds": info.gmres_seconds}
         return p, q, d
+
+    def solve_multi(self, freq, sources, admittance=None, tol=1e-6, max_iter=1000, c=343.0, rho=1.21, p=None,
+                    q=None, stream=None):
+        """One system per source (1..4 of them), solved together (see
+        bem_solve_multi); returns (p, q, infos) with p, q complex64 CUDA
+        tensors [n_rhs, n_tris] in the caller's element order."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        nr = len(sources)
+        if p is None:
+            p = torch.empty((nr, self.n), dtype=torch.complex64, device=dev)
+        if q is None:
+            q = torch.empty((nr, self.n), dtype=torch.complex64, device=dev)
+        srcs = (Source * nr)(*sources)
+        adm, nreg = _admittance(admittance)
+        med = self._medium(c, rho)
+        infos = (SolveInfo * nr)()
+        code = lib().bem_solve_multi(self._h, float(freq), ctypes.byref(med),
+                                     None if adm is None else adm.ctypes.data_as(ctypes.c_void_p), nreg, srcs, nr,
+                                     float(tol), int(max_iter), _dptr(p, nr * self.n), _dptr(q, nr * self.n), infos,
+                                     _stream_ptr(stream))
+        _check(code)
+        out = []
+        for info in infos:
+            out.append({"iterations": info.iterations, "restarts": info.restarts, "relres": info.relres,
+                        "status": info.status, "converged": info.status != W_NOT_CONVERGED,
+                        "seconds": info.seconds, "gmres_seconds": info.gmres_seconds})
+        return p, q, out
 
     def solve_sweep(self, freqs, sources=(), admittance=None, tol=1e-6, max_iter=1000, c=343.0, rho=1.21,
                     points=None, p=None, q=None, field=None, stream=None):

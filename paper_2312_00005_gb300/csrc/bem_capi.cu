@@ -322,6 +322,7 @@ struct LevelDev {
 };
 
 struct Plan {
+    int planes = 1;               // right-hand sides the M and Lambda buffers hold
     DevArr<int4> tgroups;         // transfer blocks (level, target, first direction)
     DevArr<AggTask> agg_tasks;    // aggregation blocks (element chunk, first direction pair)
     double freq = -1.0, c = -1.0, k = 0.0;
@@ -413,6 +414,7 @@ struct bem_mesh_impl {
     // GMRES status after each graph: two pinned host copies and their events,
     // so that the next graph is queued before the host waits for a status
     GmresState *h_st = nullptr;
+    int h_st_planes = 0;                       // planes h_st holds per copy (two copies)
     cudaEvent_t ev_st[2] = {};
     std::vector<float> coef_key;
 
@@ -760,6 +762,8 @@ void finish_plan(bem_mesh_impl &M, Plan &Pl)
     for (size_t l = 0; l < P->lev.size(); ++l) {
         A.lev[l] = P->lev[l]->args();
         A.lev[l].k = (float)k;
+        A.lev[l].mplane = (int64_t)(P->lev[l]->nc + P->lev[l]->ll->nextra) * P->lev[l]->nd;
+        A.lev[l].lplane = (int64_t)P->lev[l]->nc * P->lev[l]->nd;
     }
     std::vector<LevelsArgs> hv(1, A);
     P->largs.upload(hv, s);
@@ -1061,7 +1065,34 @@ PrepArgs prep_args(bem_mesh_impl &M, const float2 *cp, const float2 *cq, const f
     pa.cp = cp;
     pa.cq = cq;
     pa.k = (float)fr(M).plan->k;
+    pa.plane = 0;
+    pa.xplane = 0;
     return pa;
+}
+
+// Room for nr right-hand sides in the current plan's M and Lambda buffers
+// and in the product's work vectors (xint, ynear, wts: nr planes of n).
+void ensure_planes(bem_mesh_impl &M, int nr)
+{
+    Plan &P = *fr(M).plan;
+    if (M.xint.cap < (size_t)M.n * nr) {
+        M.xint.alloc((size_t)M.n * nr);
+        M.ynear.alloc((size_t)M.n * nr);
+        M.wts.alloc((size_t)M.n * nr);
+    }
+    if (P.planes >= nr) return;
+    LevelsArgs &A = P.hargs;
+    for (size_t l = 0; l < P.lev.size(); ++l) {
+        LevelDev &D = *P.lev[l];
+        D.M.alloc((size_t)(D.nc + D.ll->nextra) * D.nd * nr);
+        D.Lam.alloc((size_t)D.nc * D.nd * nr);
+        A.lev[l].M = D.M.p;
+        A.lev[l].Lam = D.Lam.p;
+    }
+    std::vector<LevelsArgs> hv(1, A);
+    P.largs.upload(hv, fr(M).s);
+    ck(cudaStreamSynchronize(fr(M).s), "sync");
+    P.planes = nr;
 }
 
 // y = A x with the given column coefficients.  x: caller order when
@@ -1074,17 +1105,20 @@ PrepArgs prep_args(bem_mesh_impl &M, const float2 *cp, const float2 *cq, const f
 // stream beside the near-field product.
 void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool use_store, const float2 *x,
                      const int *jidx, bool perm_in, float2 *y, bool perm_out, const int *skip, cudaStream_t s,
-                     bool prepared = false, bool far_only = false)
+                     bool prepared = false, bool far_only = false, int nr = 1)
 {
     Plan &P = *fr(M).plan;
     const int64_t n = M.n;
+    if (nr > 1) ensure_planes(M, nr);
     if (!prepared) {
         PrepArgs pa = prep_args(M, cp, cq, x);
         pa.jidx = jidx;
         pa.perm = perm_in ? M.perm.p : nullptr;
+        pa.plane = n;
+        pa.xplane = n;
         {
             KTimer kt_("k_prep", s);
-            k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, skip);
+            k_prep<<<dim3(nblocks(n, 256), nr), 256, 0, s>>>(pa, skip);
         }
         ck_launch("k_prep");
     }
@@ -1102,19 +1136,61 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     if (A.ntasks > 0) {
         {
             KTimer kt_("k_aggregate", sf);
-            k_aggregate<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, M.nrm.p, skip);
+            switch (nr) {
+                case 1: k_aggregate_1<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, n, M.nrm.p, skip); break;
+                case 2: k_aggregate_2<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, n, M.nrm.p, skip); break;
+                case 3: k_aggregate_3<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, n, M.nrm.p, skip); break;
+                default: k_aggregate_4<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, n, M.nrm.p, skip); break;
+            }
         }
         ck_launch("k_aggregate");
     }
     if (A.ntargets > 0) {
         if (A.ntgroups > 0) {
             KTimer kt_("k_transfer", sf);
-            k_transfer_split<<<A.ntgroups, 32 * kTransferWarps, 0, sf>>>(P.largs.p, skip);
+            k_transfer_split<<<dim3(A.ntgroups, nr), 32 * kTransferWarps, 0, sf>>>(P.largs.p, skip);
         }
         ck_launch("k_transfer");
     }
     NearArgs na = near_args(M, P, cp, cq);
-    if (use_store && M.prm.near_store && !P.fp().direct) {
+    if (nr > 1 && use_store && M.prm.near_store && !P.fp().direct &&
+        (size_t)nr * (((size_t)P.lists->max_ncol + 1) & ~(size_t)1) * sizeof(float2) <= 160 * 1024) {
+        // all right-hand sides in one pass over the stored values
+        const size_t xs_bytes = (size_t)nr * (((size_t)P.lists->max_ncol + 1) & ~(size_t)1) * sizeof(float2);
+        if (P.lists->n_spmv_items > 0) {
+            KTimer kt_("k_near_spmv", s);
+            k_near_spmv_items_multi<<<P.lists->n_spmv_items, kSpmvThreads, xs_bytes, s>>>(
+                na, P.lists->spmv_items.p, P.val.p, M.xint.p, M.ynear.p, nr, n, skip);
+        }
+        ck_launch("k_near_spmv");
+    } else if (nr > 1) {
+        // one right-hand side at a time (the values are streamed nr times)
+        for (int r = 0; r < nr; ++r) {
+            if (use_store && M.prm.near_store && !P.fp().direct &&
+                (size_t)P.lists->max_ncol * sizeof(float2) <= 160 * 1024) {
+                if (P.lists->n_spmv_items > 0) {
+                    KTimer kt_("k_near_spmv", s);
+                    k_near_spmv_items<<<P.lists->n_spmv_items, kSpmvThreads,
+                                        (size_t)P.lists->max_ncol * sizeof(float2), s>>>(
+                        na, P.lists->spmv_items.p, P.val.p, M.xint.p + r * n, M.ynear.p + r * n, skip);
+                }
+                ck_launch("k_near_spmv");
+            } else if (use_store && M.prm.near_store && !P.fp().direct) {
+                {
+                    KTimer kt_("k_near_spmv", s);
+                    k_near_spmv<<<nblocks(n, 8), 256, 0, s>>>(na, P.val.p, M.xint.p + r * n, M.ynear.p + r * n, skip);
+                }
+                ck_launch("k_near_spmv");
+            } else {
+                {
+                    KTimer kt_("k_near_fused", s);
+                    k_near_fused<<<nblocks(n, 8), 256, 0, s>>>(na, M.xint.p + r * n, M.ynear.p + r * n, fr(M).err.p,
+                                                                skip);
+                }
+                ck_launch("k_near_fused");
+            }
+        }
+    } else if (use_store && M.prm.near_store && !P.fp().direct) {
         const size_t xs_bytes = (size_t)P.lists->max_ncol * sizeof(float2);
         if (xs_bytes <= 160 * 1024) {
             if (P.lists->n_spmv_items > 0) {
@@ -1161,7 +1237,8 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
                                               " directions over all levels exceed the disaggregation kernel's "
                                               "shared-memory staging")};
         if (P.lists->n_dis_tasks > 0)
-            k_disaggregate<<<P.lists->n_dis_tasks, kDisThreads, smem, sd>>>(da, far_only ? nullptr : M.ynear.p, y, skip);
+            k_disaggregate<<<dim3(P.lists->n_dis_tasks, nr), kDisThreads, smem, sd>>>(da, far_only ? nullptr : M.ynear.p,
+                                                                                    y, skip);
     }
     ck_launch("k_disaggregate");
     if (fork && far_only) {
@@ -1200,7 +1277,7 @@ void matvec_t_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, con
     if (A.ntasks > 0) {
         {
             KTimer kt_("k_aggregate", sf);
-            k_aggregate<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, M.nrm.p, skip);
+            k_aggregate_1<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, n, M.nrm.p, skip);
         }
         ck_launch("k_aggregate");
     }
@@ -1344,9 +1421,11 @@ void autotune_leaf_depth(bem_mesh_impl &M, double k)
 
 void ensure_work(bem_mesh_impl &M)
 {
-    M.xint.alloc(M.n);
-    M.ynear.alloc(M.n);
-    M.wts.alloc(M.n);
+    // (ensure_planes may have given xint, ynear and wts room for several
+    // right-hand sides; alloc keeps a larger capacity)
+    M.xint.alloc(std::max<size_t>(M.xint.n, M.n));
+    M.ynear.alloc(std::max<size_t>(M.ynear.n, M.n));
+    M.wts.alloc(std::max<size_t>(M.wts.n, M.n));
     M.tmp.alloc(M.n);
     M.tmp2.alloc(M.n);
 }
@@ -1607,6 +1686,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
             }
             for (int t = 0; t < 2; ++t) ck(cudaEventCreateWithFlags(&M->ev_st[t], cudaEventDisableTiming), "event");
             ck(cudaMallocHost(&M->h_st, 2 * sizeof(GmresState)), "cudaMallocHost");
+            M->h_st_planes = 1;
         }
         const int64_t n = n_tris;
         std::vector<float4> chi(n), clo(n), nr(n), va(n), e1(n), e2(n);
@@ -1686,10 +1766,14 @@ int bem_matvec(void *mesh, double freq_hz, const bem_medium *medium, const doubl
         Coeffs C;
         join_streams(us, M.s);
         prepare(M, freq_hz, medium, admittance, n_regions, C);
-        for (int r = 0; r < n_rhs; ++r) {
+        // up to kMaxPlanes right-hand sides per pass: one stream of the stored
+        // near field and one phase per element and direction for all of them
+        for (int r = 0; r < n_rhs; r += kMaxPlanes) {
+            const int nr = std::min(kMaxPlanes, n_rhs - r);
             const float2 *x = (const float2 *)x_dev + (int64_t)r * M.n;
             float2 *y = (float2 *)y_dev + (int64_t)r * M.n;
-            matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, x, nullptr, true, y, true, nullptr, M.s);
+            matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, x, nullptr, true, y, true, nullptr, M.s, false, false,
+                            nr);
         }
         join_streams(M.s, us);
         return resolution_warning(M, freq_hz, medium);
@@ -1750,17 +1834,23 @@ int bem_matvec_host(void *mesh, double freq_hz, const bem_medium *medium, const 
 namespace {
 
 struct GmresResult {
-    int total_iters = 0, restarts = 0;
+    int total_iters = 0, restarts = 0;   // plane 0 (the only one unless nr > 1)
     bool converged = false;
     GmresState h;
+    std::vector<GmresState> hp;          // final state of every plane
+    std::vector<int> iters;              // products of every plane
+    std::vector<char> conv;              // convergence of every plane
 };
 
 // Restarted GMRES on A u = b, or on A^T u = b when transposed (the adjoint
-// solve; matvec_t_internal), with b
-// in M.bvec and u in M.uvec (internal order), for the current frame's plan
-// and column coefficients.  Row-scaled when row_scaling is on (the forward
-// system only; the caller has scaled b).  Throws Fail.
-GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool transposed)
+// solve; matvec_t_internal), for nr right-hand sides at once (nr systems in
+// lockstep, each with its own Krylov basis, Hessenberg matrix and state,
+// sharing every product: the product takes all planes in one pass), with b
+// in M.bvec and u in M.uvec (nr planes of n, internal order), for the
+// current frame's plan and column coefficients.  Preconditioned (row scaling
+// or block-Jacobi) when the mesh asks for it (the forward system only; the
+// caller has preconditioned b).  Throws Fail.
+GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool transposed, int nr = 1)
 {
     cudaStream_t s = M.s;
     const int64_t n = M.n;
@@ -1770,137 +1860,183 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     const Lists &Lb = *fr(M).plan->lists;
     GmresResult R;
     if (transposed) M.rowf.alloc(n);   // before the Arnoldi steps are captured (no allocation in a capture)
-    // GMRES workspace
-    M.V.alloc((size_t)(m + 1) * n);
-    M.w.alloc(n);
-    M.H.alloc((size_t)(m + 1) * m);
-    M.cs.alloc(m);
-    M.sn.alloc(m);
-    M.g_.alloc(m + 1);
-    M.yv.alloc(m + 1);
+    if (nr > 1) ensure_planes(M, nr);
+    // GMRES workspace, nr planes of each
+    const int64_t vplane = (int64_t)(m + 1) * n, hplane = (int64_t)(m + 1) * m;
+    M.V.alloc((size_t)nr * vplane);
+    M.w.alloc((size_t)nr * n);
+    M.H.alloc((size_t)nr * hplane);
+    M.cs.alloc((size_t)nr * m);
+    M.sn.alloc((size_t)nr * m);
+    M.g_.alloc((size_t)nr * (m + 1));
+    M.yv.alloc((size_t)nr * (m + 1));
     // the Gram-Schmidt step: block b owns rows [b R, b R + R), R <= kGsMaxRows
-    // (staged in shared memory); about 256 rows per block, so that each sum
-    // takes few atomic additions, at most 256 blocks unless the rows need more
+    // (staged in shared memory); 64 rows per block, so that many blocks keep
+    // many loads of the basis in flight, and more when that would exceed
+    // about 1024 blocks (each block adds its partial sums atomically)
     int nblk = 0;
     {
-        const int64_t want = std::min<int64_t>((n + 255) / 256, 256);
-        const int64_t need = (n + kGsMaxRows - 1) / kGsMaxRows;
-        nblk = (int)std::max<int64_t>(1, std::max(want, need));
+        const int64_t rows = std::max<int64_t>(64, (n + 1023) / 1024);
+        nblk = (int)std::max<int64_t>(1, (n + rows - 1) / rows);
     }
     const int orows = (int)((n + nblk - 1) / nblk);
-    M.gsacc.alloc(4);
-    M.gsh2.alloc((size_t)2 * (m + 1));
+    M.gsacc.alloc((size_t)4 * nr);
+    M.gsh2.alloc((size_t)2 * (m + 1) * nr);
     const int nnorm = (int)nblocks(n, 256);
-    M.normpart.alloc(std::max(nnorm, nblk));
-    M.st.alloc(1);
-    GmresState hs;
-    memset(&hs, 0, sizeof hs);
-    hs.tol = tol;
-    hs.maxit = max_iter;
-    ck(cudaMemcpyAsync(M.st.p, &hs, sizeof hs, cudaMemcpyHostToDevice, s), "H2D st");
-    ck(cudaMemsetAsync(M.uvec.p, 0, n * sizeof(float2), s), "memset x");
+    const int npart = std::max(nnorm, nblk);
+    M.normpart.alloc((size_t)npart * nr);
+    M.st.alloc(nr);
+    if (M.h_st_planes < nr) {
+        if (M.h_st) cudaFreeHost(M.h_st);
+        M.h_st = nullptr;
+        M.h_st_planes = 0;
+        ck(cudaMallocHost(&M.h_st, 2 * nr * sizeof(GmresState)), "cudaMallocHost");
+        M.h_st_planes = nr;
+    }
+    {
+        std::vector<GmresState> hs(nr);
+        memset(hs.data(), 0, nr * sizeof(GmresState));
+        for (auto &h : hs) {
+            h.tol = tol;
+            h.maxit = max_iter;
+        }
+        ck(cudaMemcpyAsync(M.st.p, hs.data(), nr * sizeof(GmresState), cudaMemcpyHostToDevice, s), "H2D st");
+    }
+    ck(cudaMemsetAsync(M.uvec.p, 0, (size_t)nr * n * sizeof(float2), s), "memset x");
     ck(cudaMemsetAsync(M.H.p, 0, M.H.bytes(), s), "memset H");
-    // the product inputs of v_0 (later basis vectors get theirs from
-    // k_gs_finish)
+    // per-plane pointers of the Gram-Schmidt and Givens kernels
+    std::vector<GsArgs> oa(nr);
+    for (int r = 0; r < nr; ++r) {
+        GmresArgs &ga = oa[r].g;
+        ga.V = M.V.p + r * vplane;
+        ga.w = M.w.p + r * n;
+        ga.n = n;
+        ga.st = M.st.p + r;
+        ga.nblk = nblk;
+        ga.H = M.H.p + r * hplane;
+        ga.cs = M.cs.p + (int64_t)r * m;
+        ga.sn = M.sn.p + (int64_t)r * m;
+        ga.g = M.g_.p + (int64_t)r * (m + 1);
+        ga.normpart = M.normpart.p + (int64_t)r * npart;
+        ga.m = m;
+        oa[r].next = prep_args(M, fr(M).cp.p, fr(M).cq.p, nullptr);
+        oa[r].next.xint = M.xint.p + r * n;
+        if (oa[r].next.wts) oa[r].next.wts = M.wts.p + r * n;
+        oa[r].wnear = M.ynear.p + r * n;
+        oa[r].acc = M.gsacc.p + 4 * r;
+        oa[r].h2 = M.gsh2.p + (int64_t)2 * (m + 1) * r;
+        oa[r].rows = orows;
+    }
+    // the product inputs of every plane's v_0 (later basis vectors get
+    // theirs from k_gs_finish)
     auto prep_v0 = [&]() {
         PrepArgs pa = prep_args(M, fr(M).cp.p, fr(M).cq.p, M.V.p);
+        pa.plane = n;
+        pa.xplane = vplane;
         {
             KTimer kt_("k_prep", s);
-            k_prep<<<nblocks(n, 256), 256, 0, s>>>(pa, nullptr);
+            k_prep<<<dim3(nblocks(n, 256), nr), 256, 0, s>>>(pa, nullptr);
         }
         ck_launch("k_prep");
     };
-    // start: r0 = b
-    {
-        KTimer kt_("k_norm_part", s);
-        k_norm_part<<<nnorm, 256, 0, s>>>(M.bvec.p, n, M.normpart.p);
-    }
-    ck_launch("k_norm_part");
-    {
-        KTimer kt_("k_gm_start", s);
-        k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.bvec.p, n, M.normpart.p, nnorm, M.g_.p, m, 1,
-                                                   M.gsacc.p, M.gsh2.p);
-    }
-    ck_launch("k_gm_start");
-    prep_v0();
+    // r0 = b, V_0 = r0 / ||r0||, cycle state reset (every plane)
+    auto start = [&](const float2 *r0, int first) {
+        for (int r = 0; r < nr; ++r) {
+            {
+                KTimer kt_("k_norm_part", s);
+                k_norm_part<<<nnorm, 256, 0, s>>>(r0 + r * n, n, oa[r].g.normpart);
+            }
+            ck_launch("k_norm_part");
+            {
+                KTimer kt_("k_gm_start", s);
+                k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(oa[r].g.st, oa[r].g.V, r0 + r * n, n, oa[r].g.normpart,
+                                                           nnorm, oa[r].g.g, m, first, oa[r].acc, oa[r].h2);
+            }
+            ck_launch("k_gm_start");
+        }
+        prep_v0();
+    };
+    start(M.bvec.p, 1);
     // one Arnoldi step, captured once as a graph and replayed
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    const int *done = &M.st.p->skip_prod;   // uniform within every product launch
-    GsArgs oa;
-    GmresArgs &ga = oa.g;
-    ga.V = M.V.p;
-    ga.w = M.w.p;
-    ga.n = n;
-    ga.st = M.st.p;
-    ga.nblk = nblk;
-    ga.H = M.H.p;
-    ga.cs = M.cs.p;
-    ga.sn = M.sn.p;
-    ga.g = M.g_.p;
-    ga.normpart = M.normpart.p;
-    ga.m = m;
-    oa.next = prep_args(M, fr(M).cp.p, fr(M).cq.p, nullptr);
-    oa.wnear = M.ynear.p;
-    oa.acc = M.gsacc.p;
-    oa.h2 = M.gsh2.p;
-    oa.rows = orows;
+    // skip flag of the product kernels: uniform within every launch; with
+    // several planes the product runs until every plane is done
+    const int *done = nr == 1 ? &M.st.p->skip_prod : &M.st.p->skip_all;
     // one Arnoldi step: product of v_j (inputs already formed), then the
-    // fused Gram-Schmidt / Givens step, which also forms v_{j+1}
+    // Gram-Schmidt / Givens step, which also forms v_{j+1}
     const bool use_graph = !g_timing;
     // Arnoldi steps per graph (and per status read).  With event timing
     // on, one step per read and every kernel on one stream, so that each
     // kernel is timed alone and no timed launch is a skipped one.
     const int batch = use_graph ? kStepsPerGraph : 1;
     auto ortho = [&]() {
-        {
-            KTimer kt_("k_gs_dots", s);
-            k_gs_dots<<<nblk, kGsThreads, 0, s>>>(oa);
+        for (int r = 0; r < nr; ++r) {
+            {
+                KTimer kt_("k_gs_dots", s);
+                k_gs_dots<<<nblk, kGsThreads, 0, s>>>(oa[r]);
+            }
+            ck_launch("k_gs_dots");
+            {
+                KTimer kt_("k_gs_update", s);
+                k_gs_update<<<nblk, kGsThreads, 0, s>>>(oa[r]);
+            }
+            ck_launch("k_gs_update");
+            {
+                KTimer kt_("k_gs_finish", s);
+                k_gs_finish<<<nblk, kGsThreads, 0, s>>>(oa[r]);
+            }
+            ck_launch("k_gs_finish");
         }
-        ck_launch("k_gs_dots");
-        {
-            KTimer kt_("k_gs_update", s);
-            k_gs_update<<<nblk, kGsThreads, 0, s>>>(oa);
+        if (nr > 1) {
+            k_gm_skip_all<<<1, 32, 0, s>>>(M.st.p, nr);
+            ck_launch("k_gm_skip_all");
         }
-        ck_launch("k_gs_update");
-        {
-            KTimer kt_("k_gs_finish", s);
-            k_gs_finish<<<nblk, kGsThreads, 0, s>>>(oa);
-        }
-        ck_launch("k_gs_finish");
     };
     auto givens = [&](cudaStream_t gs) {
-        {
-            KTimer kt_("k_gm_givens", gs);
-            k_gm_givens<<<1, 32, 0, gs>>>(ga);
+        for (int r = 0; r < nr; ++r) {
+            {
+                KTimer kt_("k_gm_givens", gs);
+                k_gm_givens<<<1, 32, 0, gs>>>(oa[r].g);
+            }
+            ck_launch("k_gm_givens");
         }
-        ck_launch("k_gm_givens");
     };
-    // the product of the current basis vector (its inputs already formed),
-    // row-scaled when row scaling is on (both parts that k_gs_dots adds)
+    // the preconditioner on every plane of w (and of the near part, which
+    // the Gram-Schmidt step would add, when wnear is given)
+    auto precond = [&](float2 *w, float2 *wnear, const int *skip) {
+        for (int r = 0; r < nr; ++r) {
+            if (rscale) {
+                {
+                    KTimer kt_("k_row_scale", s);
+                    k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(w + r * n, wnear ? wnear + r * n : nullptr, M.dinv.p,
+                                                                n, skip);
+                }
+                ck_launch("k_row_scale");
+            }
+            if (bjac) {
+                // w <- P (w + wnear), the near part cleared
+                {
+                    KTimer kt_("k_bj_apply", s);
+                    k_bj_apply<<<(unsigned)Lb.h_bj.size(), kBjMax, 0, s>>>(Lb.bj.p, M.bjinv.p, w + r * n,
+                                                                           wnear ? wnear + r * n : nullptr, skip);
+                }
+                ck_launch("k_bj_apply");
+            }
+        }
+    };
+    // the product of the current basis vectors (their inputs already
+    // formed), preconditioned when the mesh asks for it
     auto product = [&]() {
         if (transposed) {
             matvec_t_internal(M, fr(M).cp.p, fr(M).cq.p, nullptr, M.w.p, false, true, done, s);
             return;
         }
-        matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, nullptr, nullptr, false, M.w.p, false, done, s, true, true);
-        if (rscale) {
-            {
-                KTimer kt_("k_row_scale", s);
-                k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.ynear.p, M.dinv.p, n, done);
-            }
-            ck_launch("k_row_scale");
-        }
-        if (bjac) {
-            // w <- P (far + near), the near part cleared
-            {
-                KTimer kt_("k_bj_apply", s);
-                k_bj_apply<<<(unsigned)Lb.h_bj.size(), kBjMax, 0, s>>>(Lb.bj.p, M.bjinv.p, M.w.p, M.ynear.p, done);
-            }
-            ck_launch("k_bj_apply");
-        }
+        matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, nullptr, nullptr, false, M.w.p, false, done, s, true, true,
+                        nr);
+        precond(M.w.p, M.ynear.p, done);
     };
-    // nsteps Arnoldi steps, each the fused Gram-Schmidt step of column j
+    // nsteps Arnoldi steps, each the Gram-Schmidt step of column j
     // (which also forms v_{j+1}'s product inputs), the Givens step and
     // the product of v_{j+1}; a cycle's first product runs before its
     // first steps.  In the graph the Givens step runs on a side stream
@@ -1934,9 +2070,7 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
         g_launches.fetch_sub(per_graph);   // captured, not launched
         ck(cudaGraphInstantiate(&gexec, graph, 0), "instantiate");
     }
-    int &restarts = R.restarts, &total_iters = R.total_iters;
-    bool &converged = R.converged;
-    GmresState &h = R.h;
+    R.hp.assign(nr, GmresState());
     for (;;) {
         // Arnoldi cycle.  With graphs, graph g + 1 is queued before the
         // host waits for the status copied after graph g, so the GPU
@@ -1952,8 +2086,8 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
             } else {
                 arnoldi_steps(1);
             }
-            GmresState *dst = M.h_st + (launched & 1);
-            ck(cudaMemcpyAsync(dst, M.st.p, sizeof *dst, cudaMemcpyDeviceToHost, s), "D2H st");
+            GmresState *dst = M.h_st + (launched & 1) * nr;
+            ck(cudaMemcpyAsync(dst, M.st.p, nr * sizeof *dst, cudaMemcpyDeviceToHost, s), "D2H st");
             ck(cudaEventRecord(M.ev_st[launched & 1], s), "record st");
             ++launched;
         };
@@ -1961,78 +2095,82 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
         for (;;) {
             if (use_graph && launched < max_graphs) launch_graph();
             ck(cudaEventSynchronize(M.ev_st[checked & 1]), "sync st");
-            h = M.h_st[checked & 1];
+            bool all_done = true;
+            for (int r = 0; r < nr; ++r) {
+                R.hp[r] = M.h_st[(checked & 1) * nr + r];
+                all_done = all_done && R.hp[r].done;
+            }
             ++checked;
-            if (h.done) break;
+            if (all_done) break;
             if (checked == launched) {
                 if (launched >= max_graphs) break;
                 launch_graph();
             }
         }
-        {
-            KTimer kt_("k_gm_backsolve", s);
-            const int tri_cols = std::min(m, 100);
-            k_gm_backsolve<<<1, 256, (size_t)tri_cols * tri_cols * sizeof(double2), s>>>(M.st.p, M.H.p, M.g_.p,
-                                                                                       M.yv.p, m, tri_cols);
+        for (int r = 0; r < nr; ++r) {
+            {
+                KTimer kt_("k_gm_backsolve", s);
+                const int tri_cols = std::min(m, 100);
+                k_gm_backsolve<<<1, 256, (size_t)tri_cols * tri_cols * sizeof(double2), s>>>(
+                    oa[r].g.st, oa[r].g.H, oa[r].g.g, M.yv.p + (int64_t)r * (m + 1), m, tri_cols);
+            }
+            ck_launch("k_gm_backsolve");
+            {
+                KTimer kt_("k_gm_xupdate", s);
+                k_gm_xupdate<<<nblocks(n, 256), 256, 0, s>>>(M.uvec.p + r * n, oa[r].g.V, n, oa[r].g.st,
+                                                             M.yv.p + (int64_t)r * (m + 1));
+            }
+            ck_launch("k_gm_xupdate");
         }
-        ck_launch("k_gm_backsolve");
-        {
-            KTimer kt_("k_gm_xupdate", s);
-            k_gm_xupdate<<<nblocks(n, 256), 256, 0, s>>>(M.uvec.p, M.V.p, n, M.st.p, M.yv.p);
+        bool all_conv = true, at_max = false;
+        for (int r = 0; r < nr; ++r) {
+            all_conv = all_conv && R.hp[r].converged;
+            at_max = at_max || R.hp[r].iters >= max_iter;
         }
-        ck_launch("k_gm_xupdate");
-        total_iters = h.iters;
-        if (h.converged || h.iters >= max_iter) { converged = h.converged; break; }
-        // restart: r = b - A x
-        ++restarts;
+        if (all_conv || at_max) break;
+        // restart (every plane): r = b - A x
+        ++R.restarts;
         if (transposed) {
             matvec_t_internal(M, fr(M).cp.p, fr(M).cq.p, M.uvec.p, M.w.p, false, false, nullptr, s);
         } else {
-            matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, M.uvec.p, nullptr, false, M.w.p, false, nullptr, s);
+            matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, M.uvec.p, nullptr, false, M.w.p, false, nullptr, s, false,
+                            false, nr);
         }
-        if (rscale) {
-            {
-                KTimer kt_("k_row_scale", s);
-                k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, nullptr, M.dinv.p, n, nullptr);
-            }
-            ck_launch("k_row_scale");
-        }
-        if (bjac) {
-            {
-                KTimer kt_("k_bj_apply", s);
-                k_bj_apply<<<(unsigned)Lb.h_bj.size(), kBjMax, 0, s>>>(Lb.bj.p, M.bjinv.p, M.w.p, nullptr, nullptr);
-            }
-            ck_launch("k_bj_apply");
-        }
-        k_rsub<<<nblocks(n, 256), 256, 0, s>>>(M.w.p, M.bvec.p, n);   // w = b - A x (preconditioned: P (b - A x))
+        precond(M.w.p, nullptr, nullptr);
+        k_rsub<<<nblocks((int64_t)nr * n, 256), 256, 0, s>>>(M.w.p, M.bvec.p, (int64_t)nr * n);   // w = P (b - A x)
         ck_launch("k_rsub");
-        {
-            KTimer kt_("k_norm_part", s);
-            k_norm_part<<<nnorm, 256, 0, s>>>(M.w.p, n, M.normpart.p);
-        }
-        ck_launch("k_norm_part");
-        {
-            KTimer kt_("k_gm_start", s);
-            k_gm_start<<<nblocks(n, 256), 256, 0, s>>>(M.st.p, M.V.p, M.w.p, n, M.normpart.p, nnorm, M.g_.p, m, 0,
-                                                       M.gsacc.p, M.gsh2.p);
-        }
-        ck_launch("k_gm_start");
-        prep_v0();
+        start(M.w.p, 0);
         ck(cudaMemsetAsync(M.H.p, 0, M.H.bytes(), s), "memset H");
-        ck(cudaMemcpyAsync(&h, M.st.p, sizeof h, cudaMemcpyDeviceToHost, s), "D2H st");
+        ck(cudaMemcpyAsync(M.h_st, M.st.p, nr * sizeof(GmresState), cudaMemcpyDeviceToHost, s), "D2H st");
         ck(cudaStreamSynchronize(s), "sync");
-        if (h.done) { converged = true; total_iters = h.iters; break; }
+        bool all_done = true;
+        for (int r = 0; r < nr; ++r) all_done = all_done && M.h_st[r].done;
+        if (all_done) {
+            for (int r = 0; r < nr; ++r) R.hp[r] = M.h_st[r];
+            break;
+        }
     }
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
+    R.iters.resize(nr);
+    R.conv.resize(nr);
+    for (int r = 0; r < nr; ++r) {
+        R.iters[r] = R.hp[r].iters;
+        R.conv[r] = R.hp[r].converged;
+    }
+    R.h = R.hp[0];
+    R.total_iters = R.hp[0].iters;
+    R.converged = R.hp[0].converged;
     return R;
 }
 
 // Solve with the current frame's plan (prepared for freq_hz): right-hand
-// side, GMRES, p and q in the caller's order.  Throws Fail.
+// side, GMRES, p and q in the caller's order.  nr = 1: one right-hand side,
+// the incident field of all n_src sources; nr > 1 (= n_src): one system per
+// source, solved together (planes of p_dev, q_dev and info).  Throws Fail.
 int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, const bem_source *srcs, int32_t n_src,
                 double tol, int32_t max_iter, void *p_dev, void *q_dev, bem_solve_info *info, cudaStream_t us,
-                std::chrono::steady_clock::time_point t0, std::chrono::steady_clock::time_point t_setup)
+                std::chrono::steady_clock::time_point t0, std::chrono::steady_clock::time_point t_setup, int nr = 1)
 {
     {
         Plan &P = *fr(M).plan;
@@ -2043,9 +2181,18 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
         std::vector<SourceDev> sv = sources_of(srcs, n_src);
         DevArr<SourceDev> &sdev = M.srcbuf;
         sdev.upload(sv, s);
-        M.bvec.alloc(n);
-        M.uvec.alloc(n);
-        if (n_src > 0) {
+        M.bvec.alloc((size_t)nr * n);
+        M.uvec.alloc((size_t)nr * n);
+        if (nr > 1) {
+            // one source per right-hand side
+            for (int r = 0; r < nr; ++r) {
+                {
+                    KTimer kt_("k_rhs", s);
+                    k_rhs<<<nblocks(n, 256), 256, 0, s>>>(M.cd.p, M.nrm.p, n, P.k, sdev.p + r, 1, M.bvec.p + r * n);
+                }
+                ck_launch("k_rhs");
+            }
+        } else if (n_src > 0) {
             {
                 KTimer kt_("k_rhs", s);
                 k_rhs<<<nblocks(n, 256), 256, 0, s>>>(M.cd.p, M.nrm.p, n, P.k, sdev.p, n_src, M.bvec.p);
@@ -2058,11 +2205,13 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
             reset_err(M);
             matvec_internal(M, fr(M).cp0.p, fr(M).cq0.p, false, fr(M).z.p, nullptr, false, M.tmp2.p, false, nullptr, s);
             check_err(M);
-            {
-                KTimer kt_("k_sub", s);
-                k_sub<<<nblocks(n, 256), 256, 0, s>>>(M.bvec.p, M.tmp2.p, n);
+            for (int r = 0; r < nr; ++r) {
+                {
+                    KTimer kt_("k_sub", s);
+                    k_sub<<<nblocks(n, 256), 256, 0, s>>>(M.bvec.p + r * n, M.tmp2.p, n);
+                }
+                ck_launch("k_sub");
             }
-            ck_launch("k_sub");
         }
         // row scaling (Sec. 3.2): GMRES on D^-1 A u = D^-1 b, D = diag(A)
         const bool rscale = M.prm.row_scaling != 0;
@@ -2074,11 +2223,13 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
                 k_row_scale_init<<<nblocks(n, 128), 128, 0, s>>>(na, M.dinv.p, fr(M).err.p);
             }
             ck_launch("k_row_scale_init");
-            {
-                KTimer kt_("k_row_scale", s);
-                k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(M.bvec.p, nullptr, M.dinv.p, n, nullptr);
+            for (int r = 0; r < nr; ++r) {
+                {
+                    KTimer kt_("k_row_scale", s);
+                    k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(M.bvec.p + r * n, nullptr, M.dinv.p, n, nullptr);
+                }
+                ck_launch("k_row_scale");
             }
-            ck_launch("k_row_scale");
         }
         // block-Jacobi (the block form of the row scaling of Sec. 3.2):
         // GMRES on P A u = P b, P the inverse of A's block diagonal
@@ -2093,52 +2244,61 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
             }
             ck_launch("k_bj_factor");
             check_err(M);
-            {
-                KTimer kt_("k_bj_apply", s);
-                k_bj_apply<<<(unsigned)Lb.h_bj.size(), kBjMax, 0, s>>>(Lb.bj.p, M.bjinv.p, M.bvec.p, nullptr, nullptr);
+            for (int r = 0; r < nr; ++r) {
+                {
+                    KTimer kt_("k_bj_apply", s);
+                    k_bj_apply<<<(unsigned)Lb.h_bj.size(), kBjMax, 0, s>>>(Lb.bj.p, M.bjinv.p, M.bvec.p + r * n,
+                                                                           nullptr, nullptr);
+                }
+                ck_launch("k_bj_apply");
             }
-            ck_launch("k_bj_apply");
         }
         ck(cudaStreamSynchronize(s), "sync");
         auto t_rhs = std::chrono::steady_clock::now();
-        GmresResult R = run_gmres(M, tol, max_iter, false);
-        const int total_iters = R.total_iters, restarts = R.restarts;
-        const bool converged = R.converged;
-        const GmresState &h = R.h;
+        GmresResult R = run_gmres(M, tol, max_iter, false, nr);
         auto t_gmres = std::chrono::steady_clock::now();
         // p and q in the caller's order
-        {
-            KTimer kt_("k_pq", s);
-            k_pq<<<nblocks(n, 256), 256, 0, s>>>(M.uvec.p, fr(M).z.p, fr(M).aq.p, M.type.p, M.perm.p, n, (float2 *)p_dev,
-                                             (float2 *)q_dev);
+        for (int r = 0; r < nr; ++r) {
+            {
+                KTimer kt_("k_pq", s);
+                k_pq<<<nblocks(n, 256), 256, 0, s>>>(M.uvec.p + r * n, fr(M).z.p, fr(M).aq.p, M.type.p, M.perm.p, n,
+                                                     (float2 *)p_dev + r * n, q_dev ? (float2 *)q_dev + r * n : nullptr);
+            }
+            ck_launch("k_pq");
         }
-        ck_launch("k_pq");
         check_err(M);
         join_streams(s, us);
         ck(cudaStreamSynchronize(us), "sync");
         resolve_timing();
-        int status = converged ? BEM_OK : BEM_W_NOT_CONVERGED;
-        if (!converged) {
-            char buf[160];
-            snprintf(buf, sizeof buf, "GMRES: relative residual %.3g after %d products (tol %.3g)", h.resid,
-                     total_iters, tol);
+        bool all_conv = true;
+        for (int r = 0; r < nr; ++r) all_conv = all_conv && R.conv[r];
+        int status = all_conv ? BEM_OK : BEM_W_NOT_CONVERGED;
+        if (!all_conv) {
+            char buf[200];
+            for (int r = 0; r < nr; ++r)
+                if (!R.conv[r]) {
+                    snprintf(buf, sizeof buf, "GMRES: relative residual %.3g after %d products (tol %.3g)%s",
+                             R.hp[r].resid, R.iters[r], tol, nr > 1 ? " for a right-hand side" : "");
+                    break;
+                }
             g_err = buf;
         } else if (resolution_warning(M, freq_hz, medium) != BEM_OK) {
             status = BEM_W_UNDERRESOLVED;
         }
-        if (info) {
-            memset(info, 0, sizeof *info);
-            info->iterations = total_iters;
-            info->restarts = restarts;
-            info->relres = h.resid;
-            info->levels = (int)P.lev.size();
-            for (size_t l = 0; l < P.lev.size() && l < 16; ++l) info->L[l] = P.lev[l]->L;
-            info->near_nnz = P.nnz();
-            info->status = status;
-            info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-            info->setup_seconds = std::chrono::duration<double>(t_setup - t0).count();
-            info->rhs_seconds = std::chrono::duration<double>(t_rhs - t_setup).count();
-            info->gmres_seconds = std::chrono::duration<double>(t_gmres - t_rhs).count();
+        for (int r = 0; info && r < nr; ++r) {
+            bem_solve_info *ir = info + r;
+            memset(ir, 0, sizeof *ir);
+            ir->iterations = R.iters[r];
+            ir->restarts = R.restarts;
+            ir->relres = R.hp[r].resid;
+            ir->levels = (int)P.lev.size();
+            for (size_t l = 0; l < P.lev.size() && l < 16; ++l) ir->L[l] = P.lev[l]->L;
+            ir->near_nnz = P.nnz();
+            ir->status = R.conv[r] ? (status == BEM_W_NOT_CONVERGED ? BEM_OK : status) : BEM_W_NOT_CONVERGED;
+            ir->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            ir->setup_seconds = std::chrono::duration<double>(t_setup - t0).count();
+            ir->rhs_seconds = std::chrono::duration<double>(t_rhs - t_setup).count();
+            ir->gmres_seconds = std::chrono::duration<double>(t_gmres - t_rhs).count();
         }
         return status;
     }
@@ -2189,6 +2349,28 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
         ck(cudaStreamSynchronize(M.s), "sync");
         return solve_frame(M, freq_hz, medium, srcs, n_src, tol, max_iter, p_dev, q_dev, info, us, t0,
                            std::chrono::steady_clock::now());
+    } catch (Fail &f) {
+        abandon_capture(M);
+        return f.code;
+    }
+}
+
+int bem_solve_multi(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
+                    int32_t n_regions, const bem_source *srcs, int32_t n_rhs, double tol, int32_t max_iter,
+                    void *p_dev, void *q_dev, bem_solve_info *infos, void *stream)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (!mesh || !p_dev || n_rhs < 1 || n_rhs > kMaxPlanes || !srcs || !(tol > 0) || max_iter < 1)
+        return set_err(BEM_E_ARG, "bad argument (n_rhs must be in 1..4)");
+    auto &M = *(bem_mesh_impl *)mesh;
+    try {
+        cudaStream_t us = (cudaStream_t)stream;
+        Coeffs C;
+        join_streams(us, M.s);
+        prepare(M, freq_hz, medium, admittance, n_regions, C);
+        ck(cudaStreamSynchronize(M.s), "sync");
+        return solve_frame(M, freq_hz, medium, srcs, n_rhs, tol, max_iter, p_dev, q_dev, infos, us, t0,
+                           std::chrono::steady_clock::now(), n_rhs);
     } catch (Fail &f) {
         abandon_capture(M);
         return f.code;

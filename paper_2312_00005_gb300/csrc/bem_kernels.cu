@@ -393,6 +393,110 @@ __global__ void __launch_bounds__(kSpmvThreads) k_near_spmv_items(NearArgs a, co
     }
 }
 
+// sum_{c0 <= c < c1} v[c] xs_r[c] for the planes r < nr of xs (ncp floats2
+// apart), as spmv_segment for one plane: each 16-byte load of v serves all
+// planes.
+__device__ __forceinline__ void spmv_segment_multi(const float2 *__restrict__ v, const float2 *__restrict__ xs, int ncp,
+                                                   int c0, int c1, int lane, int nr, float2 out[kMaxPlanes])
+{
+    const float4 *__restrict__ v4 = reinterpret_cast<const float4 *>(v);
+    float2 acc0[kMaxPlanes], acc1[kMaxPlanes];
+#pragma unroll
+    for (int r = 0; r < kMaxPlanes; ++r) acc0[r] = acc1[r] = make_float2(0.f, 0.f);
+    int q = (c0 >> 1) + lane;
+    const int qe = c1 >> 1;
+    for (; q + 96 < qe; q += 128) {
+        float4 vv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) vv[u] = __ldcs(v4 + q + 32 * u);
+#pragma unroll
+        for (int r = 0; r < kMaxPlanes; ++r) {
+            if (r >= nr) break;
+            const float4 *__restrict__ x4 = reinterpret_cast<const float4 *>(xs + (int64_t)r * ncp);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 xa = x4[q + 32 * u];
+                acc0[r] = cfma(make_float2(vv[u].x, vv[u].y), make_float2(xa.x, xa.y), acc0[r]);
+                acc1[r] = cfma(make_float2(vv[u].z, vv[u].w), make_float2(xa.z, xa.w), acc1[r]);
+            }
+        }
+    }
+    for (; q < qe; q += 32) {
+        const float4 vv = __ldcs(v4 + q);
+#pragma unroll
+        for (int r = 0; r < kMaxPlanes; ++r) {
+            if (r >= nr) break;
+            const float4 xa = reinterpret_cast<const float4 *>(xs + (int64_t)r * ncp)[q];
+            acc0[r] = cfma(make_float2(vv.x, vv.y), make_float2(xa.x, xa.y), acc0[r]);
+            acc1[r] = cfma(make_float2(vv.z, vv.w), make_float2(xa.z, xa.w), acc1[r]);
+        }
+    }
+    if ((c1 & 1) && lane == 0) {
+        const float2 vl = v[c1 - 1];
+#pragma unroll
+        for (int r = 0; r < kMaxPlanes; ++r)
+            if (r < nr) acc0[r] = cfma(vl, xs[(int64_t)r * ncp + c1 - 1], acc0[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < kMaxPlanes; ++r) out[r] = warp_sum(cadd(acc0[r], acc1[r]));
+}
+
+__global__ void __launch_bounds__(kSpmvThreads) k_near_spmv_items_multi(NearArgs a, const int4 *__restrict__ items,
+                                                                        const float2 *__restrict__ val,
+                                                                        const float2 *__restrict__ x,
+                                                                        float2 *__restrict__ y, int nr, int64_t plane,
+                                                                        const int *skip)
+{
+    if (skip_now(skip)) return;
+    extern __shared__ float2 xs[];            // [nr][ncp]
+    constexpr int kW = kSpmvThreads / 32;
+    __shared__ float2 part[kMaxPlanes][kSpmvMaxItemRows][kW];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int4 W = items[blockIdx.x];
+    const int t = W.x;
+    const int nc = a.N.ncol[t];
+    const int ncp = (nc + 1) & ~1;
+    {
+        const int r0 = a.N.run_ptr[t], r1 = a.N.run_ptr[t + 1];
+        for (int r = r0 + warp; r < r1; r += kW) {
+            const int2 rr = a.N.runs[r];
+            const int end = (r + 1 < r1) ? a.N.runs[r + 1].y : nc;
+            for (int p = rr.y + lane; p < end; p += 32)
+                for (int pl = 0; pl < nr; ++pl) xs[(int64_t)pl * ncp + p] = x[pl * plane + rr.x + (p - rr.y)];
+        }
+    }
+    for (int q = threadIdx.x; q < kMaxPlanes * kSpmvMaxItemRows * kW; q += kSpmvThreads)
+        (&part[0][0][0])[q] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int64_t i0 = a.N.leaf_start[t] + W.y;
+    const int nrow = min(W.z - W.y, kSpmvMaxItemRows);
+    const int64_t total = (int64_t)nrow * ncp;
+    int64_t qa = (total * warp / kW) & ~(int64_t)1;
+    const int64_t qb = warp == kW - 1 ? total : (total * (warp + 1) / kW) & ~(int64_t)1;
+    while (qa < qb) {
+        const int r = (int)(qa / ncp);
+        const int c0 = (int)(qa - (int64_t)r * ncp);
+        const int c1 = (int)min((int64_t)ncp, (int64_t)c0 + (qb - qa));
+        const int c1r = min(c1, nc);
+        if (c0 < c1r) {
+            float2 acc[kMaxPlanes];
+            spmv_segment_multi(val + a.N.row_ptr[i0 + r], xs, ncp, c0, c1r, lane, nr, acc);
+            if (lane == 0)
+#pragma unroll
+                for (int pl = 0; pl < kMaxPlanes; ++pl) part[pl][r][warp] = acc[pl];
+        }
+        qa += c1 - c0;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nrow * nr; q += kSpmvThreads) {
+        const int row = q % nrow, pl = q / nrow;
+        float2 sum = part[pl][row][0];
+#pragma unroll
+        for (int w = 1; w < kW; ++w) sum = cadd(sum, part[pl][row][w]);
+        y[pl * plane + i0 + row] = sum;
+    }
+}
+
 // Near-field product with the entries recomputed on the fly (no storage);
 // also the conventional dense BEM product when the near list is everything.
 __global__ void k_near_fused(NearArgs a, const float2 *__restrict__ x, float2 *__restrict__ y,
@@ -759,6 +863,13 @@ __global__ void k_prep(PrepArgs a, const int *skip)
     if (i >= a.n) return;
     const float2 *xb = a.x;
     if (a.jidx) xb += (int64_t)(*a.jidx) * a.n;
+    if (blockIdx.y) {
+        // right-hand side blockIdx.y: its planes of x, xint and wts
+        const int64_t o = (int64_t)blockIdx.y * a.plane;
+        xb += (int64_t)blockIdx.y * a.xplane;
+        a.xint += o;
+        if (a.wts) a.wts += o;
+    }
     prep_store(a, i, a.perm ? xb[a.perm[i]] : xb[i]);
 }
 
@@ -771,22 +882,22 @@ __global__ void k_prep(PrepArgs a, const int *skip)
 // sets the kernel's length.  For a cluster split into several element
 // chunks, the last of its blocks to finish sums the chunks' partial rows in
 // row order.
-__global__ void __launch_bounds__(kAggThreads) k_aggregate(const LevelsArgs *__restrict__ A,
-                                                           const float4 *__restrict__ wts,
-                                                           const float4 *__restrict__ nrm, const int *skip)
+template <int NR>
+__device__ __forceinline__ void aggregate_body(const LevelsArgs *__restrict__ A, const float4 *__restrict__ wts,
+                                               int64_t wplane, const float4 *__restrict__ nrm)
 {
-    if (skip_now(skip)) return;
     const AggTask T = A->tasks[blockIdx.x];
     const FarArgs &f = A->lev[T.lev];
     __shared__ float4 sd[kAggChunk];       // (z_c - x_j) k / (2 pi)
-    __shared__ float4 sw[kAggChunk];       // (alpha_j, c_j)
+    __shared__ float4 sw[NR][kAggChunk];   // (alpha_j, c_j) per right-hand side
     __shared__ float4 sn[kAggChunk];       // n_j
     const float kt = f.k * 0.15915494309189535f;
     for (int q = threadIdx.x; q < T.ne; q += blockDim.x) {
         const int64_t j = T.e0 + q;
         const float4 d = f.dz[j];
         sd[q] = make_float4(kt * d.x, kt * d.y, kt * d.z, 0.f);
-        sw[q] = wts[j];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) sw[r][q] = wts[r * wplane + j];
         sn[q] = nrm[j];
     }
     __syncthreads();
@@ -797,22 +908,31 @@ __global__ void __launch_bounds__(kAggThreads) k_aggregate(const LevelsArgs *__r
     const int p = T.p0 + threadIdx.x;
     if (p < h) {
         const float4 sv = f.dirs[p];
-        float2 accp = make_float2(0.f, 0.f), accm = accp;
+        float2 accp[NR], accm[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) accp[r] = accm[r] = make_float2(0.f, 0.f);
         for (int q = 0; q < T.ne; ++q) {
-            const float4 d = sd[q], w = sw[q], n = sn[q];
+            const float4 d = sd[q], n = sn[q];
             float sn0, cs0;
             sincos_turns(fmaf(d.x, sv.x, fmaf(d.y, sv.y, d.z * sv.z)), &sn0, &cs0);
             const float t = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
-            const float2 wp = make_float2(fmaf(w.z, t, w.x), fmaf(w.w, t, w.y));
-            const float2 wm = make_float2(fmaf(-w.z, t, w.x), fmaf(-w.w, t, w.y));
-            // (cs + i sn) wp and (cs - i sn) wm
-            accp.x = fmaf(cs0, wp.x, fmaf(-sn0, wp.y, accp.x));
-            accp.y = fmaf(cs0, wp.y, fmaf(sn0, wp.x, accp.y));
-            accm.x = fmaf(cs0, wm.x, fmaf(sn0, wm.y, accm.x));
-            accm.y = fmaf(cs0, wm.y, fmaf(-sn0, wm.x, accm.y));
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float4 w = sw[r][q];
+                const float2 wp = make_float2(fmaf(w.z, t, w.x), fmaf(w.w, t, w.y));
+                const float2 wm = make_float2(fmaf(-w.z, t, w.x), fmaf(-w.w, t, w.y));
+                // (cs + i sn) wp and (cs - i sn) wm
+                accp[r].x = fmaf(cs0, wp.x, fmaf(-sn0, wp.y, accp[r].x));
+                accp[r].y = fmaf(cs0, wp.y, fmaf(sn0, wp.x, accp[r].y));
+                accm[r].x = fmaf(cs0, wm.x, fmaf(sn0, wm.y, accm[r].x));
+                accm[r].y = fmaf(cs0, wm.y, fmaf(-sn0, wm.x, accm[r].y));
+            }
         }
-        out[p] = accp;
-        out[p + h] = accm;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            out[r * f.mplane + p] = accp[r];
+            out[r * f.mplane + p + h] = accm[r];
+        }
     }
     if (T.red < 0) return;
     // split cluster: its blocks are (element chunks) x (pair ranges); the
@@ -830,7 +950,9 @@ __global__ void __launch_bounds__(kAggThreads) k_aggregate(const LevelsArgs *__r
     __threadfence();
     const int r0 = f.red_ptr[T.red], r1 = f.red_ptr[T.red + 1];
     const int nd = f.nd;
-    float2 *__restrict__ dst = f.M + (int64_t)T.c * nd;
+    for (int pl = 0; pl < NR; ++pl) {
+    const float2 *__restrict__ Mp = f.M + pl * f.mplane;
+    float2 *__restrict__ dst = f.M + pl * f.mplane + (int64_t)T.c * nd;
     // each thread sums kRedDirs directions at a time and loads kRedRows rows
     // of them together (L2 loads of other blocks' rows, all in flight at
     // once); every direction still adds its rows in row order
@@ -846,7 +968,7 @@ __global__ void __launch_bounds__(kAggThreads) k_aggregate(const LevelsArgs *__r
 #pragma unroll
                 for (int b = 0; b < kRedDirs; ++b) {
                     const int nu = nb + b * kAggThreads;
-                    v[a][b] = (rr + a < r1 && nu < nd) ? __ldcg(f.M + (int64_t)(rr + a) * nd + nu)
+                    v[a][b] = (rr + a < r1 && nu < nd) ? __ldcg(Mp + (int64_t)(rr + a) * nd + nu)
                                                        : make_float2(0.f, 0.f);
                 }
 #pragma unroll
@@ -861,8 +983,23 @@ __global__ void __launch_bounds__(kAggThreads) k_aggregate(const LevelsArgs *__r
         for (int b = 0; b < kRedDirs; ++b)
             if (nb + b * kAggThreads < nd) dst[nb + b * kAggThreads] = acc[b];
     }
+    }
     if (threadIdx.x == 0) A->red_cnt[T.gred] = 0;
 }
+
+#define BEM_AGGREGATE_KERNEL(NR)                                                                                      \
+    __global__ void __launch_bounds__(kAggThreads)                                                                   \
+        k_aggregate_##NR(const LevelsArgs *__restrict__ A, const float4 *__restrict__ wts, int64_t wplane,           \
+                         const float4 *__restrict__ nrm, const int *skip)                                            \
+    {                                                                                                                 \
+        if (skip_now(skip)) return;                                                                                   \
+        aggregate_body<NR>(A, wts, wplane, nrm);                                                                     \
+    }
+BEM_AGGREGATE_KERNEL(1)
+BEM_AGGREGATE_KERNEL(2)
+BEM_AGGREGATE_KERNEL(3)
+BEM_AGGREGATE_KERNEL(4)
+#undef BEM_AGGREGATE_KERNEL
 
 // sin / cos of 2 pi x by sincos_turns and by sincospif, for the unit tests.
 __global__ void k_selftest_sincos(const float *__restrict__ x, int64_t n, float4 *__restrict__ out)
@@ -893,6 +1030,9 @@ __global__ void __launch_bounds__(32 * kTransferWarps) k_transfer_split(const Le
     const int4 T = A->tgroups[blockIdx.x];
     const FarArgs &f = A->lev[T.x];
     const int t = T.y, nu0 = T.z, nd = f.nd;
+    // right-hand side blockIdx.y: its M and Lambda planes
+    const float2 *__restrict__ Mp = f.M + blockIdx.y * f.mplane;
+    float2 *__restrict__ Lp = f.Lam + blockIdx.y * f.lplane;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nu = nu0 + lane;
     const bool live = nu < nd;
@@ -914,7 +1054,7 @@ __global__ void __launch_bounds__(32 * kTransferWarps) k_transfer_split(const Le
             for (int u = 0; u < kU; ++u) {
                 const int2 en = s_ent[q + kW * u];
                 dv[u] = __ldg(f.D + (int64_t)en.y * nd + nu);
-                mv[u] = f.M[(int64_t)en.x * nd + nu];
+                mv[u] = Mp[(int64_t)en.x * nd + nu];
             }
 #pragma unroll
             for (int u = 0; u < kU; u += 2) {
@@ -924,7 +1064,7 @@ __global__ void __launch_bounds__(32 * kTransferWarps) k_transfer_split(const Le
         }
         for (; q < cnt; q += kW) {
             const int2 en = s_ent[q];
-            acc0 = cfma(__ldg(f.D + (int64_t)en.y * nd + nu), f.M[(int64_t)en.x * nd + nu], acc0);
+            acc0 = cfma(__ldg(f.D + (int64_t)en.y * nd + nu), Mp[(int64_t)en.x * nd + nu], acc0);
         }
     }
     part[warp][lane] = cadd(acc0, acc1);
@@ -933,7 +1073,7 @@ __global__ void __launch_bounds__(32 * kTransferWarps) k_transfer_split(const Le
         float2 sum = part[0][lane];
 #pragma unroll
         for (int w = 1; w < kW; ++w) sum = cadd(sum, part[w][lane]);
-        f.Lam[(int64_t)t * nd + nu] = sum;
+        Lp[(int64_t)t * nd + nu] = sum;
     }
 }
 
@@ -972,6 +1112,12 @@ __device__ __forceinline__ void disaggregate_body(const DisaggArgs &a, const flo
     __shared__ float2 red1[kRowF ? kNW : 1][kRowF ? kDisTask : 1];
     const int2 tk = a.tasks[blockIdx.x];
     const int64_t e0 = tk.x, e1 = tk.y;
+    // right-hand side blockIdx.y: its Lambda planes and rows of ynear and y
+    const int64_t pl = blockIdx.y;
+    if (pl) {
+        if (ynear) ynear += pl * a.n;
+        y += pl * a.n;
+    }
     const int cnt_all = (int)min((int64_t)kDisTask, e1 - e0);   // the host never makes larger tasks
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
@@ -997,7 +1143,7 @@ __device__ __forceinline__ void disaggregate_body(const DisaggArgs &a, const flo
     // (1 + t) lp - (1 - t) lm = B + t A
     for (int u = 0; u < na; ++u) {
         const FarArgs &f = a.lev[s_lev[u]];
-        const float2 *__restrict__ src = f.Lam + (int64_t)f.elem_cl[e0] * f.nd;
+        const float2 *__restrict__ src = f.Lam + pl * f.lplane + (int64_t)f.elem_cl[e0] * f.nd;
         const int h = f.nd / 2;
         for (int q = threadIdx.x; q < h; q += blockDim.x) {
             const float4 d = f.dirs[q];
@@ -1613,20 +1759,27 @@ __device__ __forceinline__ FF warp_sum_ff(const float2 *p, int n)
 //   k_gs_dots    w = (far + near part of A v_j); each block adds its partial
 //                dots V_l^H w into column j of H and its partial ||w||^2
 //                into acc (FP64 atomics);
-//   k_gs_update  w_1 = w - V h; partial ||w_1||^2 and V_l^H w_1 (the dots of
-//                a possible second pass) added into acc and h2;
-//   k_gs_finish  every block takes the same DGKS decision from the sums;
-//                without a second pass nn = ||w_1||^2, with one h_2 is added
-//                to column j of H, w_2 = w_1 - V h_2 and nn = ||w_1||^2 -
-//                |h_2|^2 (accurate: h_2 is small against w_1); v_{j+1} =
-//                w / sqrt(nn) and the next product's inputs.
-// Block b owns rows [b R, b R + R) of every vector, with FP32 sums within a
-// block.  The FP64 sums of the blocks' FP32 partials are exact whenever the
-// partials span fewer than 29 binary orders of magnitude, so they do not
-// depend on the order in which the blocks add them.  acc and h2 alternate
-// between two copies by the parity of j: k_gs_finish clears the copy of
-// step j + 1 (k_gm_start clears both at the start of a cycle, where H is
-// cleared too).  The Givens step (k_gm_givens) follows on a side stream.
+//   k_gs_update  w_1 = w - V h and its partial ||w_1||^2; the DGKS test on
+//                the sums (||w_1||^2 = ||w||^2 - |h|^2 by Pythagoras; exact
+//                enough to decide, since the sums are) asks for a second pass
+//                rarely, and only then the block adds the dots V_l^H w_1;
+//   k_gs_finish  the decision read from the state (k_gs_update's block 0
+//                leaves it there); without a second pass nn = ||w_1||^2
+//                (summed, not estimated); with one h_2 is added to column j
+//                of H, w_2 = w_1 - V h_2 and nn = ||w_1||^2 - |h_2|^2
+//                (accurate: h_2 is small against w_1); v_{j+1} = w / sqrt(nn)
+//                and the next product's inputs.
+// Every block of k_gs_update takes the same decision from the same FP64
+// sums.  Block b owns
+// rows [b R, b R + R) of every vector (R about 64: the basis comes from HBM,
+// since each product streams the stored near field through L2, so many
+// blocks keep many loads in flight), with FP32 sums within a block.  The
+// FP64 sums of the blocks' FP32 partials are exact whenever the partials span
+// fewer than 29 binary orders of magnitude, so they do not depend on the
+// order in which the blocks add them.  acc and h2 alternate between two
+// copies by the parity of j: k_gs_finish clears the copy of step j + 1
+// (k_gm_start clears both at the start of a cycle, where H is cleared too).
+// The Givens step (k_gm_givens) follows on a side stream.
 __device__ __forceinline__ int gs_rows(const GsArgs &a, int64_t &r0)
 {
     r0 = (int64_t)blockIdx.x * a.rows;
@@ -1641,34 +1794,45 @@ __device__ __forceinline__ void atomic_add_c(double2 *p, float2 v)
 }
 
 // Partial dots sum_{i in block} conj(V_l[i]) ws[i], l <= j, added into
-// dst[l * stride], and the partial sum_{i in block} |ws[i]|^2 added into *nrm.
-__device__ void gs_partials(const GsArgs &a, const float2 *ws, int R, int64_t r0, int j, double2 *dst,
-                            int64_t stride, double *nrm)
+// dst[l * stride]: warp w takes the columns l = w (mod 8), four at a time,
+// its lanes the rows, so that every warp keeps several independent loads in
+// flight.
+__device__ void gs_dots_part(const GsArgs &a, const float2 *ws, int R, int64_t r0, int j, double2 *dst, int64_t stride)
 {
     const GmresArgs &g = a.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nwarp = kGsThreads / 32;
-    for (int l0 = warp * 8; l0 <= j; l0 += nwarp * 8) {
-        float2 acc[8];
+    for (int l0 = warp; l0 <= j; l0 += 4 * nwarp) {
+        float2 acc[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.f, 0.f);
-#pragma unroll 4
+        for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
+#pragma unroll 2
         for (int i = lane; i < R; i += 32) {
             const float2 y = ws[i];
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (l0 + u <= j) {
-                    const float2 x = __ldcg(g.V + (int64_t)(l0 + u) * g.n + r0 + i);
+            for (int u = 0; u < 4; ++u) {
+                const int l = l0 + u * nwarp;
+                if (l <= j) {
+                    const float2 x = __ldcg(g.V + (int64_t)l * g.n + r0 + i);
                     acc[u].x = fmaf(x.x, y.x, fmaf(x.y, y.y, acc[u].x));
                     acc[u].y = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc[u].y));
                 }
+            }
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 4; ++u) {
+            const int l = l0 + u * nwarp;
             const float2 d = warp_sum(acc[u]);
-            if (lane == u && l0 + u <= j) atomic_add_c(dst + (int64_t)(l0 + u) * stride, d);
+            if (lane == u && l <= j) atomic_add_c(dst + (int64_t)l * stride, d);
         }
     }
+}
+
+// The block's sum_{i in block} |ws[i]|^2 added into *nrm.
+__device__ void gs_norm_part(const float2 *ws, int R, double *nrm)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int nwarp = kGsThreads / 32;
     __shared__ float red[nwarp];
     float v2 = 0.f;
     for (int i = threadIdx.x; i < R; i += kGsThreads) v2 = fmaf(ws[i].x, ws[i].x, fmaf(ws[i].y, ws[i].y, v2));
@@ -1682,11 +1846,12 @@ __device__ void gs_partials(const GsArgs &a, const float2 *ws, int R, int64_t r0
     }
 }
 
-// w_1 = ws - V h (h as FP32 in hs), written back into ws.
+// w_1 = ws - V h (h as FP32 in hs), written back into ws: thread (row rr,
+// column group cg) sums the columns l = cg (mod kCg) of its row.
 __device__ void gs_update(const GsArgs &a, float2 *ws, const float2 *hs, int R, int64_t r0, int j)
 {
     const GmresArgs &g = a.g;
-    constexpr int kRowsPerPass = 128, kCg = kGsThreads / kRowsPerPass;
+    constexpr int kRowsPerPass = 64, kCg = kGsThreads / kRowsPerPass;
     __shared__ float2 cpart[kGsThreads];
     const int cg = threadIdx.x / kRowsPerPass, rr = threadIdx.x % kRowsPerPass;
     for (int i0 = 0; i0 < R; i0 += kRowsPerPass) {
@@ -1717,6 +1882,31 @@ __device__ void gs_update(const GsArgs &a, float2 *ws, const float2 *hs, int R, 
     }
 }
 
+// h_l (l <= j) of a column sum as FP32 into hs, and sum_l |h_l|^2 (FP64, the
+// same order in every block) returned to every thread.
+__device__ double gs_load_h(const double2 *src, int64_t stride, float2 *hs, int j)
+{
+    __shared__ double s_hh;
+    for (int l = threadIdx.x; l <= j; l += kGsThreads) {
+        const double2 h = __ldcg(src + (int64_t)l * stride);
+        hs[l] = make_float2((float)h.x, (float)h.y);
+    }
+    if (threadIdx.x < 32) {
+        double hh = 0.0;
+        for (int l = threadIdx.x; l <= j; l += 32) {
+            const double2 h = __ldcg(src + (int64_t)l * stride);
+            hh += h.x * h.x + h.y * h.y;
+        }
+        for (int o = 16; o > 0; o >>= 1) hh += __shfl_xor_sync(0xffffffffu, hh, o);
+        if (threadIdx.x == 0) s_hh = hh;
+    }
+    __syncthreads();
+    return s_hh;
+}
+
+// DGKS test from the FP64 sums: ||w_1||^2 = ||w||^2 - |h|^2 < 0.01 ||w||^2.
+__device__ __forceinline__ bool gs_second_pass(double ww, double hh) { return ww - hh < 0.01 * ww; }
+
 __global__ void __launch_bounds__(kGsThreads) k_gs_dots(GsArgs a)
 {
     const GmresArgs &g = a.g;
@@ -1746,7 +1936,8 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_dots(GsArgs a)
         }
     }
     __syncthreads();
-    gs_partials(a, ws, R, r0, j, g.H + j, g.m, a.acc + 2 * (j & 1));
+    gs_dots_part(a, ws, R, r0, j, g.H + j, g.m);
+    gs_norm_part(ws, R, a.acc + 2 * (j & 1));
 }
 
 __global__ void __launch_bounds__(kGsThreads) k_gs_update(GsArgs a)
@@ -1761,15 +1952,15 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_update(GsArgs a)
     __shared__ float2 ws[kGsMaxRows];
     __shared__ float2 hs[kMaxRestart + 1];
     for (int i = threadIdx.x; i < R; i += kGsThreads) ws[i] = g.w[r0 + i];
-    for (int l = threadIdx.x; l <= j; l += kGsThreads) {
-        const double2 h = __ldcg(g.H + (int64_t)l * g.m + j);
-        hs[l] = make_float2((float)h.x, (float)h.y);
-    }
-    __syncthreads();
+    const double hh = gs_load_h(g.H + j, g.m, hs, j);
+    const double ww = __ldcg(a.acc + 2 * (j & 1));
     gs_update(a, ws, hs, R, r0, j);
     for (int i = threadIdx.x; i < R; i += kGsThreads) g.w[r0 + i] = ws[i];
-    // ||w_1||^2 and the dots of a possible second pass
-    gs_partials(a, ws, R, r0, j, a.h2 + (int64_t)(j & 1) * (g.m + 1), 1, a.acc + 2 * (j & 1) + 1);
+    gs_norm_part(ws, R, a.acc + 2 * (j & 1) + 1);
+    const bool need = gs_second_pass(ww, hh);
+    // the decision for k_gs_finish (whose block 0 changes column j of H)
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->reorth = need;
+    if (need) gs_dots_part(a, ws, R, r0, j, a.h2 + (int64_t)(j & 1) * (g.m + 1), 1);
 }
 
 __global__ void __launch_bounds__(kGsThreads) k_gs_finish(GsArgs a)
@@ -1779,36 +1970,19 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_finish(GsArgs a)
     const int2 jd = __ldcv(reinterpret_cast<const int2 *>(&st->j));
     const int j = jd.x;
     if (jd.y) return;
-    const double ww = __ldcg(a.acc + 2 * (j & 1)), w1 = __ldcg(a.acc + 2 * (j & 1) + 1);
-    // DGKS: second pass when ||w_1|| < 0.1 ||w||
-    const bool need = w1 < 0.01 * ww;
-    const double2 *h2 = a.h2 + (int64_t)(j & 1) * (g.m + 1);
     int64_t r0;
     const int R = gs_rows(a, r0);
     __shared__ float2 ws[kGsMaxRows];
     __shared__ float2 hs[kMaxRestart + 1];
-    __shared__ double s_hh;
     for (int i = threadIdx.x; i < R; i += kGsThreads) ws[i] = g.w[r0 + i];
+    const double w1 = __ldcg(a.acc + 2 * (j & 1) + 1);
+    const bool need = __ldcv(&st->reorth) != 0;      // k_gs_update's decision
+    const double2 *h2 = a.h2 + (int64_t)(j & 1) * (g.m + 1);
     double nn = w1;
     if (need) {
-        for (int l = threadIdx.x; l <= j; l += kGsThreads) {
-            const double2 h = __ldcg(h2 + l);
-            hs[l] = make_float2((float)h.x, (float)h.y);
-        }
-        if (threadIdx.x < 32) {
-            double hh = 0.0;
-            for (int l = threadIdx.x; l <= j; l += 32) {
-                const double2 h = __ldcg(h2 + l);
-                hh += h.x * h.x + h.y * h.y;
-            }
-            for (int o = 16; o > 0; o >>= 1) hh += __shfl_xor_sync(0xffffffffu, hh, o);
-            if (threadIdx.x == 0) s_hh = hh;
-        }
-        __syncthreads();
-        nn = fmax(w1 - s_hh, 0.0);
+        const double hh2 = gs_load_h(h2, 1, hs, j);
+        nn = fmax(w1 - hh2, 0.0);
         gs_update(a, ws, hs, R, r0, j);
-    } else {
-        __syncthreads();
     }
     // next basis vector and the product inputs (unused when the cycle ends)
     const float nf = (float)nn;
@@ -1832,7 +2006,6 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_finish(GsArgs a)
         if (threadIdx.x == 0) {
             a.acc[2 * ((j + 1) & 1)] = 0.0;
             a.acc[2 * ((j + 1) & 1) + 1] = 0.0;
-            st->reorth = need;
             st->n_reorth += need;
             st->nn = nn;
         }
@@ -1845,6 +2018,16 @@ __global__ void k_gm_givens(GmresArgs a)
     GmresState *st = a.st;
     if (*(volatile int *)&st->done) return;
     gm_givens_warp(a, st->nn, st->j);
+}
+
+// st[0].skip_all = every plane's skip_prod (the product kernels of several
+// right-hand sides skip only when all systems are done).
+__global__ void k_gm_skip_all(GmresState *st, int nr)
+{
+    if (threadIdx.x != 0) return;
+    int all = 1;
+    for (int r = 0; r < nr; ++r) all &= __ldcv(&st[r].skip_prod) != 0;
+    st[0].skip_all = all;
 }
 
 // Back substitution y = R^{-1} g over ncols columns (FP64), one warp:

@@ -51,6 +51,9 @@ struct GmresState {
     // k_gm_givens on a side stream while that product runs, so reading it
     // there could differ between the threads of one block.
     int skip_prod;
+    // With several right-hand sides (plane 0's state only): the product
+    // kernels skip once every plane's skip_prod is set (k_gm_skip_all).
+    int skip_all;
 };
 
 struct PrepArgs {
@@ -63,6 +66,8 @@ struct PrepArgs {
     const float4 *chi, *nrm;
     const float2 *cp, *cq;
     float k;
+    int64_t plane;           // element stride between the right-hand sides of xint and wts
+    int64_t xplane;          // ... and of x (launch grid.y = number of right-hand sides)
 };
 
 // Aggregation work item: `ne` (at most kAggChunk) elements from e0 of
@@ -102,6 +107,7 @@ struct FarArgs {
     const int *is_src;       // [nc]
     const float4 *dz;        // per element: z_c - x_j
     const int *elem_cl;      // per element: cluster at this level
+    int64_t mplane, lplane;  // stride (in float2) between the right-hand sides' M and Lam planes
 };
 
 // All far levels of a plan, for the kernels that run every level in one launch.
@@ -148,9 +154,19 @@ constexpr int kSpmvThreads = 128;
 constexpr int kSpmvMaxItemRows = 32;
 __global__ void k_near_spmv_items(NearArgs a, const int4 *items, const float2 *val, const float2 *x, float2 *y,
                                   const int *skip);
+// The same for nr <= kMaxPlanes right-hand sides (planes `plane` elements
+// apart in x and y): the stored values are streamed once for all of them.
+__global__ void k_near_spmv_items_multi(NearArgs a, const int4 *items, const float2 *val, const float2 *x, float2 *y,
+                                        int nr, int64_t plane, const int *skip);
 __global__ void k_near_fused(NearArgs a, const float2 *x, float2 *y, int *err, const int *skip);
 __global__ void k_prep(PrepArgs a, const int *skip);
-__global__ void k_aggregate(const LevelsArgs *A, const float4 *wts, const float4 *nrm, const int *skip);
+// Aggregation of NR right-hand sides at once (one phase per element and
+// direction pair serves all of them); wts holds NR planes of n elements.
+__global__ void k_aggregate_1(const LevelsArgs *A, const float4 *wts, int64_t wplane, const float4 *nrm, const int *skip);
+__global__ void k_aggregate_2(const LevelsArgs *A, const float4 *wts, int64_t wplane, const float4 *nrm, const int *skip);
+__global__ void k_aggregate_3(const LevelsArgs *A, const float4 *wts, int64_t wplane, const float4 *nrm, const int *skip);
+__global__ void k_aggregate_4(const LevelsArgs *A, const float4 *wts, int64_t wplane, const float4 *nrm, const int *skip);
+constexpr int kMaxPlanes = 4;            // right-hand sides per multi-plane launch
 __global__ void k_selftest_sincos(const float *x, int64_t n, float4 *out);
 // Transfer with the interaction list of one target split among
 // kTransferWarps warps: one block per (target, kTransferDirs directions).
@@ -236,6 +252,7 @@ __global__ void k_gs_dots(GsArgs a);
 __global__ void k_gs_update(GsArgs a);
 __global__ void k_gs_finish(GsArgs a);
 __global__ void k_gm_givens(GmresArgs a);
+__global__ void k_gm_skip_all(GmresState *st, int nr);
 __global__ void k_gm_backsolve(const GmresState *st, const double2 *H, const double2 *g, double2 *y, int m,
                                int smem_cols);
 __global__ void k_gm_xupdate(float2 *x, const float2 *V, int64_t n, const GmresState *st, const double2 *y);
