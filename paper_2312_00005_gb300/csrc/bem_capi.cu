@@ -382,7 +382,7 @@ struct bem_mesh_impl {
     DevArr<float2> V, w;
     DevArr<double2> H, cs, sn, g_, yv;
     DevArr<double> normpart;
-    DevArr<double> gsacc;        // Gram-Schmidt norm sums [2][2] (per parity of the column)
+    DevArr<double> gsacc;        // Gram-Schmidt norm sums [2][4] (per parity of the column)
     DevArr<double2> gsh2;        // Gram-Schmidt second-pass dots [2][m + 1]
     DevArr<GmresState> st;
     // frequency state: cur serves the products and the solve; next is filled
@@ -1721,6 +1721,8 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         M->type.upload(ty, s);
         ck(cudaFuncSetAttribute(k_near_spmv_items, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024),
            "cudaFuncSetAttribute");
+        ck(cudaFuncSetAttribute(k_near_spmv_items_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024),
+           "cudaFuncSetAttribute");
 
         ck(cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 100 * 16),
            "cudaFuncSetAttribute");
@@ -1880,7 +1882,7 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
         nblk = (int)std::max<int64_t>(1, (n + rows - 1) / rows);
     }
     const int orows = (int)((n + nblk - 1) / nblk);
-    M.gsacc.alloc((size_t)4 * nr);
+    M.gsacc.alloc((size_t)8 * nr);
     M.gsh2.alloc((size_t)2 * (m + 1) * nr);
     const int nnorm = (int)nblocks(n, 256);
     const int npart = std::max(nnorm, nblk);
@@ -1923,7 +1925,7 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
         oa[r].next.xint = M.xint.p + r * n;
         if (oa[r].next.wts) oa[r].next.wts = M.wts.p + r * n;
         oa[r].wnear = M.ynear.p + r * n;
-        oa[r].acc = M.gsacc.p + 4 * r;
+        oa[r].acc = M.gsacc.p + 8 * r;
         oa[r].h2 = M.gsh2.p + (int64_t)2 * (m + 1) * r;
         oa[r].rows = orows;
     }
@@ -1987,6 +1989,11 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
                 k_gs_finish<<<nblk, kGsThreads, 0, s>>>(oa[r]);
             }
             ck_launch("k_gs_finish");
+            {
+                KTimer kt_("k_gs_scale", s);
+                k_gs_scale<<<nblk, kGsThreads, 0, s>>>(oa[r]);
+            }
+            ck_launch("k_gs_scale");
         }
         if (nr > 1) {
             k_gm_skip_all<<<1, 32, 0, s>>>(M.st.p, nr);

@@ -1764,11 +1764,15 @@ __device__ __forceinline__ FF warp_sum_ff(const float2 *p, int n)
 //                enough to decide, since the sums are) asks for a second pass
 //                rarely, and only then the block adds the dots V_l^H w_1;
 //   k_gs_finish  the decision read from the state (k_gs_update's block 0
-//                leaves it there); without a second pass nn = ||w_1||^2
-//                (summed, not estimated); with one h_2 is added to column j
-//                of H, w_2 = w_1 - V h_2 and nn = ||w_1||^2 - |h_2|^2
-//                (accurate: h_2 is small against w_1); v_{j+1} = w / sqrt(nn)
-//                and the next product's inputs.
+//                leaves it there); without a second pass v_{j+1} = w_1 /
+//                ||w_1|| and the next product's inputs; with one h_2 is
+//                added to column j of H, w_2 = w_1 - V h_2 and its partial
+//                ||w_2||^2 are formed, and
+//   k_gs_scale   (a second pass only) v_{j+1} = w_2 / ||w_2|| and the next
+//                product's inputs.
+// Every norm is summed from the vector itself, never estimated (when w_1 is
+// mostly rounding noise inside span(V), ||w_1||^2 - |h_2|^2 would cancel to
+// nothing and fake a breakdown of the Arnoldi process).
 // Every block of k_gs_update takes the same decision from the same FP64
 // sums.  Block b owns
 // rows [b R, b R + R) of every vector (R about 64: the basis comes from HBM,
@@ -1776,8 +1780,9 @@ __device__ __forceinline__ FF warp_sum_ff(const float2 *p, int n)
 // blocks keep many loads in flight), with FP32 sums within a block.  The
 // FP64 sums of the blocks' FP32 partials are exact whenever the partials span
 // fewer than 29 binary orders of magnitude, so they do not depend on the
-// order in which the blocks add them.  acc and h2 alternate between two
-// copies by the parity of j: k_gs_finish clears the copy of step j + 1
+// order in which the blocks add them.  acc ([4]: ||w||^2, ||w_1||^2,
+// ||w_2||^2) and h2 alternate between two copies by the parity of j: the
+// normalising kernel clears the copy of step j + 1
 // (k_gm_start clears both at the start of a cycle, where H is cleared too).
 // The Givens step (k_gm_givens) follows on a side stream.
 __device__ __forceinline__ int gs_rows(const GsArgs &a, int64_t &r0)
@@ -1937,7 +1942,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_dots(GsArgs a)
     }
     __syncthreads();
     gs_dots_part(a, ws, R, r0, j, g.H + j, g.m);
-    gs_norm_part(ws, R, a.acc + 2 * (j & 1));
+    gs_norm_part(ws, R, a.acc + 4 * (j & 1));
 }
 
 __global__ void __launch_bounds__(kGsThreads) k_gs_update(GsArgs a)
@@ -1953,14 +1958,48 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_update(GsArgs a)
     __shared__ float2 hs[kMaxRestart + 1];
     for (int i = threadIdx.x; i < R; i += kGsThreads) ws[i] = g.w[r0 + i];
     const double hh = gs_load_h(g.H + j, g.m, hs, j);
-    const double ww = __ldcg(a.acc + 2 * (j & 1));
+    const double ww = __ldcg(a.acc + 4 * (j & 1));
     gs_update(a, ws, hs, R, r0, j);
     for (int i = threadIdx.x; i < R; i += kGsThreads) g.w[r0 + i] = ws[i];
-    gs_norm_part(ws, R, a.acc + 2 * (j & 1) + 1);
+    gs_norm_part(ws, R, a.acc + 4 * (j & 1) + 1);
     const bool need = gs_second_pass(ww, hh);
     // the decision for k_gs_finish (whose block 0 changes column j of H)
     if (blockIdx.x == 0 && threadIdx.x == 0) st->reorth = need;
     if (need) gs_dots_part(a, ws, R, r0, j, a.h2 + (int64_t)(j & 1) * (g.m + 1), 1);
+}
+
+// v_{j+1} = ws / sqrt(nn) over the block's rows, with the next product's
+// inputs; block 0 keeps the books of step j: H column j takes the second
+// pass's h_2 (when there was one), nn goes to the state, and the other
+// parity's sums are cleared for step j + 1.
+__device__ void gs_normalise(const GsArgs &a, const float2 *ws, int R, int64_t r0, int j, double nn, bool need)
+{
+    const GmresArgs &g = a.g;
+    GmresState *st = g.st;
+    const float nf = (float)nn;
+    const float sc = nf > 0.f ? 1.f / sqrtf(nf) : 0.f;
+    float2 *vn = g.V + (int64_t)(j + 1) * g.n;
+    for (int i = threadIdx.x; i < R; i += kGsThreads) {
+        const float2 xv = cscale(ws[i], sc);
+        vn[r0 + i] = xv;
+        prep_store(a.next, r0 + i, xv);
+    }
+    if (blockIdx.x == 0) {
+        const double2 *h2 = a.h2 + (int64_t)(j & 1) * (g.m + 1);
+        if (need)
+            for (int l = threadIdx.x; l <= j; l += kGsThreads) {
+                double2 *hp = g.H + (int64_t)l * g.m + j;
+                const double2 h = h2[l], h0 = *hp;
+                *hp = make_double2(h0.x + h.x, h0.y + h.y);
+            }
+        double2 *h2n = a.h2 + (int64_t)((j + 1) & 1) * (g.m + 1);
+        for (int l = threadIdx.x; l <= j + 1 && l <= g.m; l += kGsThreads) h2n[l] = make_double2(0.0, 0.0);
+        if (threadIdx.x < 4) a.acc[4 * ((j + 1) & 1) + threadIdx.x] = 0.0;
+        if (threadIdx.x == 0) {
+            st->n_reorth += need;
+            st->nn = nn;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kGsThreads) k_gs_finish(GsArgs a)
@@ -1975,41 +2014,34 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_finish(GsArgs a)
     __shared__ float2 ws[kGsMaxRows];
     __shared__ float2 hs[kMaxRestart + 1];
     for (int i = threadIdx.x; i < R; i += kGsThreads) ws[i] = g.w[r0 + i];
-    const double w1 = __ldcg(a.acc + 2 * (j & 1) + 1);
     const bool need = __ldcv(&st->reorth) != 0;      // k_gs_update's decision
-    const double2 *h2 = a.h2 + (int64_t)(j & 1) * (g.m + 1);
-    double nn = w1;
-    if (need) {
-        const double hh2 = gs_load_h(h2, 1, hs, j);
-        nn = fmax(w1 - hh2, 0.0);
-        gs_update(a, ws, hs, R, r0, j);
+    if (!need) {
+        // ||w_1||^2 summed by k_gs_update
+        gs_normalise(a, ws, R, r0, j, __ldcg(a.acc + 4 * (j & 1) + 1), false);
+        return;
     }
-    // next basis vector and the product inputs (unused when the cycle ends)
-    const float nf = (float)nn;
-    const float sc = nf > 0.f ? 1.f / sqrtf(nf) : 0.f;
-    float2 *vn = g.V + (int64_t)(j + 1) * g.n;
-    for (int i = threadIdx.x; i < R; i += kGsThreads) {
-        const float2 xv = cscale(ws[i], sc);
-        vn[r0 + i] = xv;
-        prep_store(a.next, r0 + i, xv);
-    }
-    if (blockIdx.x == 0) {
-        if (need)
-            for (int l = threadIdx.x; l <= j; l += kGsThreads) {
-                double2 *hp = g.H + (int64_t)l * g.m + j;
-                const double2 h = h2[l], h0 = *hp;
-                *hp = make_double2(h0.x + h.x, h0.y + h.y);
-            }
-        // the other parity's sums, for step j + 1
-        double2 *h2n = a.h2 + (int64_t)((j + 1) & 1) * (g.m + 1);
-        for (int l = threadIdx.x; l <= j + 1 && l <= g.m; l += kGsThreads) h2n[l] = make_double2(0.0, 0.0);
-        if (threadIdx.x == 0) {
-            a.acc[2 * ((j + 1) & 1)] = 0.0;
-            a.acc[2 * ((j + 1) & 1) + 1] = 0.0;
-            st->n_reorth += need;
-            st->nn = nn;
-        }
-    }
+    // second pass: w_2 = w_1 - V h_2 and its partial ||w_2||^2 (summed, as
+    // every norm here: when w_1 is mostly rounding noise inside span(V),
+    // ||w_1||^2 - |h_2|^2 would cancel to nothing); k_gs_scale normalises
+    gs_load_h(a.h2 + (int64_t)(j & 1) * (g.m + 1), 1, hs, j);
+    gs_update(a, ws, hs, R, r0, j);
+    for (int i = threadIdx.x; i < R; i += kGsThreads) g.w[r0 + i] = ws[i];
+    gs_norm_part(ws, R, a.acc + 4 * (j & 1) + 2);
+}
+
+// After a second pass only: v_{j+1} = w_2 / ||w_2||.
+__global__ void __launch_bounds__(kGsThreads) k_gs_scale(GsArgs a)
+{
+    const GmresArgs &g = a.g;
+    GmresState *st = g.st;
+    const int2 jd = __ldcv(reinterpret_cast<const int2 *>(&st->j));
+    const int j = jd.x;
+    if (jd.y || !__ldcv(&st->reorth)) return;
+    int64_t r0;
+    const int R = gs_rows(a, r0);
+    __shared__ float2 ws[kGsMaxRows];
+    for (int i = threadIdx.x; i < R; i += kGsThreads) ws[i] = g.w[r0 + i];
+    gs_normalise(a, ws, R, r0, j, __ldcg(a.acc + 4 * (j & 1) + 2), true);
 }
 
 // Givens step of the column the Gram-Schmidt kernels just formed (one warp).
@@ -2096,7 +2128,7 @@ __global__ void k_gm_start(GmresState *st, float2 *__restrict__ V, const float2 
     if (blockIdx.x == 0) {
         // the Gram-Schmidt sums of both parities (see k_gs_dots)
         for (int l = threadIdx.x; l < 2 * (m + 1); l += blockDim.x) gs_h2[l] = make_double2(0.0, 0.0);
-        if (threadIdx.x < 4) gs_acc[threadIdx.x] = 0.0;
+        if (threadIdx.x < 8) gs_acc[threadIdx.x] = 0.0;
     }
     __shared__ double beta_s;
     if (threadIdx.x == 0) {
