@@ -296,7 +296,7 @@ def run_ours(args):
     k_ms, k_mvs, _ = timed(args.steps)
     kernels = {}
     for name in ["k_near_spmv", "k_near_store", "k_near_store_heavy", "k_near_classify", "k_aggregate", "k_transfer", "k_disaggregate", "k_prep",
-                 "k_gs_dots", "k_gs_update", "k_gs_finish", "k_gs_scale", "k_gm_givens", "k_dtable", "k_rhs",
+                 "k_gs_dots", "k_gs_update", "k_gs_finish", "k_gm_givens", "k_dtable", "k_rhs",
                  "k_field", "k_gm_xupdate", "k_gm_backsolve", "k_pq", "k_gm_start", "k_norm_part", "k_gather"]:
         ms, cnt = bemfmm.timing_get(name)
         if cnt:

@@ -1989,11 +1989,7 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
                 k_gs_finish<<<nblk, kGsThreads, 0, s>>>(oa[r]);
             }
             ck_launch("k_gs_finish");
-            {
-                KTimer kt_("k_gs_scale", s);
-                k_gs_scale<<<nblk, kGsThreads, 0, s>>>(oa[r]);
-            }
-            ck_launch("k_gs_scale");
+
         }
         if (nr > 1) {
             k_gm_skip_all<<<1, 32, 0, s>>>(M.st.p, nr);

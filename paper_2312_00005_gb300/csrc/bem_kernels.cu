@@ -1767,9 +1767,9 @@ __device__ __forceinline__ FF warp_sum_ff(const float2 *p, int n)
 //                leaves it there); without a second pass v_{j+1} = w_1 /
 //                ||w_1|| and the next product's inputs; with one h_2 is
 //                added to column j of H, w_2 = w_1 - V h_2 and its partial
-//                ||w_2||^2 are formed, and
-//   k_gs_scale   (a second pass only) v_{j+1} = w_2 / ||w_2|| and the next
-//                product's inputs.
+//                ||w_2||^2 are formed, and the last block to finish (an
+//                arrival counter) forms v_{j+1} = w_2 / ||w_2|| for every
+//                row (second passes are rare).
 // Every norm is summed from the vector itself, never estimated (when w_1 is
 // mostly rounding noise inside span(V), ||w_1||^2 - |h_2|^2 would cancel to
 // nothing and fake a breakdown of the Arnoldi process).
@@ -1781,8 +1781,8 @@ __device__ __forceinline__ FF warp_sum_ff(const float2 *p, int n)
 // FP64 sums of the blocks' FP32 partials are exact whenever the partials span
 // fewer than 29 binary orders of magnitude, so they do not depend on the
 // order in which the blocks add them.  acc ([4]: ||w||^2, ||w_1||^2,
-// ||w_2||^2) and h2 alternate between two copies by the parity of j: the
-// normalising kernel clears the copy of step j + 1
+// ||w_2||^2, arrival counter) and h2 alternate between two copies by the
+// parity of j: the normalising block clears the copy of step j + 1
 // (k_gm_start clears both at the start of a cycle, where H is cleared too).
 // The Givens step (k_gm_givens) follows on a side stream.
 __device__ __forceinline__ int gs_rows(const GsArgs &a, int64_t &r0)
@@ -1984,7 +1984,7 @@ __device__ void gs_normalise(const GsArgs &a, const float2 *ws, int R, int64_t r
         vn[r0 + i] = xv;
         prep_store(a.next, r0 + i, xv);
     }
-    if (blockIdx.x == 0) {
+    if (need || blockIdx.x == 0) {   // after a second pass: the last block (the only caller)
         const double2 *h2 = a.h2 + (int64_t)(j & 1) * (g.m + 1);
         if (need)
             for (int l = threadIdx.x; l <= j; l += kGsThreads) {
@@ -2022,26 +2022,34 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_finish(GsArgs a)
     }
     // second pass: w_2 = w_1 - V h_2 and its partial ||w_2||^2 (summed, as
     // every norm here: when w_1 is mostly rounding noise inside span(V),
-    // ||w_1||^2 - |h_2|^2 would cancel to nothing); k_gs_scale normalises
+    // ||w_1||^2 - |h_2|^2 would cancel to nothing); the last block to finish
+    // normalises every row (second passes are rare, so this keeps a launch
+    // off the common path)
     gs_load_h(a.h2 + (int64_t)(j & 1) * (g.m + 1), 1, hs, j);
     gs_update(a, ws, hs, R, r0, j);
     for (int i = threadIdx.x; i < R; i += kGsThreads) g.w[r0 + i] = ws[i];
     gs_norm_part(ws, R, a.acc + 4 * (j & 1) + 2);
-}
-
-// After a second pass only: v_{j+1} = w_2 / ||w_2||.
-__global__ void __launch_bounds__(kGsThreads) k_gs_scale(GsArgs a)
-{
-    const GmresArgs &g = a.g;
-    GmresState *st = g.st;
-    const int2 jd = __ldcv(reinterpret_cast<const int2 *>(&st->j));
-    const int j = jd.x;
-    if (jd.y || !__ldcv(&st->reorth)) return;
-    int64_t r0;
-    const int R = gs_rows(a, r0);
-    __shared__ float2 ws[kGsMaxRows];
-    for (int i = threadIdx.x; i < R; i += kGsThreads) ws[i] = g.w[r0 + i];
-    gs_normalise(a, ws, R, r0, j, __ldcg(a.acc + 4 * (j & 1) + 2), true);
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int *cnt = reinterpret_cast<unsigned int *>(a.acc + 4 * (j & 1) + 3);
+        s_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const double nn = __ldcg(a.acc + 4 * (j & 1) + 2);
+    const float nf = (float)nn;
+    const float sc = nf > 0.f ? 1.f / sqrtf(nf) : 0.f;
+    float2 *vn = g.V + (int64_t)(j + 1) * g.n;
+    for (int64_t i = threadIdx.x; i < g.n; i += kGsThreads) {
+        const float2 xv = cscale(__ldcg(g.w + i), sc);
+        vn[i] = xv;
+        prep_store(a.next, i, xv);
+    }
+    // the books of block 0 in gs_normalise, with no rows of its own
+    gs_normalise(a, ws, 0, 0, j, nn, true);
 }
 
 // Givens step of the column the Gram-Schmidt kernels just formed (one warp).

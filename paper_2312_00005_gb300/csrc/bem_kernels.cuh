@@ -242,7 +242,7 @@ struct GsArgs {
     GmresArgs g;             // g.nblk = gridDim.x
     PrepArgs next;           // inputs of the next product, formed from V_{j+1}
     const float2 *wnear;     // near-field part of the product (g.w holds the far part)
-    double *acc;             // [2][4] per parity of j: ||w||^2, ||w_1||^2, ||w_2||^2, unused
+    double *acc;             // [2][4] per parity of j: ||w||^2, ||w_1||^2, ||w_2||^2, arrival counter
     double2 *h2;             // [2][m + 1] per parity of j: second-pass dots V^H w_1
     int rows;                // rows of the basis per block
 };
@@ -251,7 +251,6 @@ constexpr int kGsMaxRows = 1024;    // rows per block staged in shared memory
 __global__ void k_gs_dots(GsArgs a);
 __global__ void k_gs_update(GsArgs a);
 __global__ void k_gs_finish(GsArgs a);
-__global__ void k_gs_scale(GsArgs a);
 __global__ void k_gm_givens(GmresArgs a);
 __global__ void k_gm_skip_all(GmresState *st, int nr);
 __global__ void k_gm_backsolve(const GmresState *st, const double2 *H, const double2 *g, double2 *y, int m,

