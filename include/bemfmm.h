@@ -122,6 +122,12 @@ typedef struct bem_params {
                                to that preconditioned residual; the solution is that of
                                A u = b.  0: off (default).  Not together with row_scaling;
                                other values: BEM_E_ARG.                                        */
+    int32_t far_precision;  /* arithmetic of the aggregation T(l) (Sec. 3.3.3) in the forward
+                               products: 0 (default) FP32 on the CUDA cores; 1 split BF16 on
+                               the tensor cores (every operand as a sum of two BF16 parts,
+                               three products accumulated in FP32; a few 1e-6 relative, see
+                               bem_solve_multi for the refinement that recovers the FP32
+                               form's accuracy).  Other values: BEM_E_ARG.                     */
 } bem_params;
 
 typedef struct bem_medium {

@@ -1,6 +1,6 @@
 """Build the in-tree CUDA library ``_bemfmm.so`` for sm_103a with nvcc.
 
-Four translation units are compiled in parallel and linked into one shared
+Five translation units are compiled in parallel and linked into one shared
 object next to this file (git-ignored).  Run ``python -m
 paper_2312_00005_gb300.build`` or call ``build()``.
 """
@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_bemfmm.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
-SOURCES = ["bem_plan.cpp", "bem_kernels.cu", "bem_capi.cu", "bem_noalloc.cu"]
+SOURCES = ["bem_plan.cpp", "bem_kernels.cu", "bem_capi.cu", "bem_noalloc.cu", "bem_tc.cu"]
 HEADERS = ["bem_plan.hpp", "bem_device.cuh", "bem_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -325,6 +325,8 @@ struct Plan {
     int planes = 1;               // right-hand sides the M and Lambda buffers hold
     DevArr<int4> tgroups;         // transfer blocks (level, target, first direction)
     DevArr<AggTask> agg_tasks;    // aggregation blocks (element chunk, first direction pair)
+    DevArr<AggTask> agg_tasks_tc; // the same with kTcPairs pairs per block (tensor-core aggregation)
+    int n_tc_tasks = 0;
     double freq = -1.0, c = -1.0, k = 0.0;
     std::shared_ptr<Lists> lists;
     bool shared_lists = false;
@@ -378,6 +380,10 @@ struct bem_mesh_impl {
     DevArr<int> adjreg;
     DevArr<double> adjacc;
     DevArr<float4> wts;          // far-field weights (alpha, c) per element
+    DevArr<int> tc_fault;        // set when a tensor-core aggregation's wait ran out
+    bool force_fp32 = false;     // products with the FP32 aggregation (the refinement's residuals)
+    DevArr<float2> bsave, xcur, rtmp;   // refinement: right-hand side, current solution, A x
+    DevArr<double2> x64;         // refinement: solution in FP64
     // GMRES workspace
     DevArr<float2> V, w;
     DevArr<double2> H, cs, sn, g_, yv;
@@ -743,6 +749,17 @@ void finish_plan(bem_mesh_impl &M, Plan &Pl)
         P->agg_tasks.upload(at, s);
         A.tasks = P->agg_tasks.p;
         A.ntasks = (int)at.size();
+        if (M.prm.far_precision == 1) {
+            std::vector<AggTask> tt;
+            for (const AggTask &t : P->lists->h_tasks)
+                for (int p0 = 0; p0 < P->lev[t.lev]->nd / 2; p0 += kTcPairs) {
+                    AggTask u = t;
+                    u.p0 = p0;
+                    tt.push_back(u);
+                }
+            P->agg_tasks_tc.upload(tt, s);
+            P->n_tc_tasks = (int)tt.size();
+        }
     }
     A.reds = P->lists->all_reds.p;
     A.nreds = P->lists->n_reds;
@@ -947,6 +964,21 @@ void check_err(bem_mesh_impl &M)
     }
 }
 
+// Reports (BEM_E_TIMEOUT) a tensor-core aggregation whose wait for the
+// tensor cores ran out since the last check; waits for the mesh's stream.
+void check_tc_fault(bem_mesh_impl &M)
+{
+    if (M.prm.far_precision != 1) return;
+    int f = 0;
+    ck(cudaMemcpyAsync(&f, M.tc_fault.p, sizeof(int), cudaMemcpyDeviceToHost, M.s), "D2H fault");
+    ck(cudaStreamSynchronize(M.s), "sync");
+    if (f) {
+        ck(cudaMemsetAsync(M.tc_fault.p, 0, sizeof(int), M.s), "memset");
+        g_err = "tensor-core aggregation: the wait for the tensor cores gave up";
+        throw Fail{BEM_E_TIMEOUT};
+    }
+}
+
 void reset_err(bem_mesh_impl &M)
 {
     const int v = INT_MAX;
@@ -1133,7 +1165,15 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
         ck(cudaEventRecord(M.ev_fork, s), "record fork");
         ck(cudaStreamWaitEvent(sf, M.ev_fork, 0), "wait fork");
     }
-    if (A.ntasks > 0) {
+    if (A.ntasks > 0 && M.prm.far_precision == 1 && !M.force_fp32) {
+        {
+            KTimer kt_("k_aggregate_tc", sf);
+            if (P.n_tc_tasks > 0)
+                k_aggregate_tc<<<P.n_tc_tasks, kTcThreads, kTcSmemBytes, sf>>>(P.largs.p, P.agg_tasks_tc.p, M.wts.p, n,
+                                                                               M.nrm.p, nr, M.tc_fault.p, skip);
+        }
+        ck_launch("k_aggregate_tc");
+    } else if (A.ntasks > 0) {
         {
             KTimer kt_("k_aggregate", sf);
             switch (nr) {
@@ -1586,6 +1626,7 @@ void bem_params_default(bem_params *p)
     p->check_orientation = 0;
     p->symmetric_far = 0;
     p->block_jacobi = 0;
+    p->far_precision = 0;
 }
 
 const char *bem_last_error(void) { return g_err.c_str(); }
@@ -1612,6 +1653,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         return set_err(BEM_E_ARG, "check_orientation must be 0 or 1");
     if (p.symmetric_far != 0 && p.symmetric_far != 1) return set_err(BEM_E_ARG, "symmetric_far must be 0 or 1");
     if (p.block_jacobi != 0 && p.block_jacobi != 1) return set_err(BEM_E_ARG, "block_jacobi must be 0 or 1");
+    if (p.far_precision != 0 && p.far_precision != 1) return set_err(BEM_E_ARG, "far_precision must be 0 or 1");
     if (p.block_jacobi && p.row_scaling)
         return set_err(BEM_E_ARG, "row_scaling and block_jacobi are alternatives: set at most one");
     if (!(p.quad_tol > 0) || !(p.rt_subdiv > 0) || !(p.admissibility > 0) || p.L_min < 1 || p.L_min > 200)
@@ -1726,6 +1768,12 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
 
         ck(cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 100 * 16),
            "cudaFuncSetAttribute");
+        if (p.far_precision == 1) {
+            ck(cudaFuncSetAttribute(k_aggregate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes),
+               "cudaFuncSetAttribute");
+        }
+        M->tc_fault.alloc(1);
+        ck(cudaMemsetAsync(M->tc_fault.p, 0, sizeof(int), s), "memset");
         ck(cudaFuncSetAttribute(k_disaggregate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDisaggSmem),
            "cudaFuncSetAttribute");
 
@@ -1777,6 +1825,7 @@ int bem_matvec(void *mesh, double freq_hz, const bem_medium *medium, const doubl
             matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, x, nullptr, true, y, true, nullptr, M.s, false, false,
                             nr);
         }
+        check_tc_fault(M);
         join_streams(M.s, us);
         return resolution_warning(M, freq_hz, medium);
     } catch (Fail &f) {
@@ -2167,6 +2216,127 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     return R;
 }
 
+// The solver's preconditioner (row scaling or block-Jacobi, when the mesh
+// asks for one) applied to nr planes of b in place.
+void precondition_rhs(bem_mesh_impl &M, float2 *b, int nr)
+{
+    cudaStream_t s = M.s;
+    const int64_t n = M.n;
+    const Lists &Lb = *fr(M).plan->lists;
+    for (int r = 0; r < nr; ++r) {
+        if (M.prm.row_scaling) {
+            {
+                KTimer kt_("k_row_scale", s);
+                k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(b + r * n, nullptr, M.dinv.p, n, nullptr);
+            }
+            ck_launch("k_row_scale");
+        }
+        if (M.prm.block_jacobi) {
+            {
+                KTimer kt_("k_bj_apply", s);
+                k_bj_apply<<<(unsigned)Lb.h_bj.size(), kBjMax, 0, s>>>(Lb.bj.p, M.bjinv.p, b + r * n, nullptr, nullptr);
+            }
+            ck_launch("k_bj_apply");
+        }
+    }
+}
+
+// Iterative refinement of a solve whose products aggregate in split BF16 on
+// the tensor cores (far_precision 1): the solution is kept in FP64 (x64), the
+// residual r = b - A x is formed with the FP32 products and differenced in
+// FP64, and each inner GMRES (the mixed-precision products, preconditioned
+// as the mesh asks) solves A d = r to a relative 1e-3 (or less when the
+// target is closer), x64 += d, until ||r|| <= tol ||b|| for every plane.  b:
+// M.bvec (nr planes, not preconditioned); the solution ends in M.uvec.
+// Products: inner products plus one FP32 product per outer step.
+GmresResult run_refined(bem_mesh_impl &M, double tol, int32_t max_iter, int nr)
+{
+    cudaStream_t s = M.s;
+    const int64_t n = M.n;
+    const size_t pn = (size_t)nr * n;
+    M.bsave.alloc(pn);
+    M.xcur.alloc(pn);
+    M.rtmp.alloc(pn);
+    M.x64.alloc(pn);
+    ck(cudaMemcpyAsync(M.bsave.p, M.bvec.p, pn * sizeof(float2), cudaMemcpyDeviceToDevice, s), "D2D b");
+    ck(cudaMemsetAsync(M.x64.p, 0, pn * sizeof(double2), s), "memset x64");
+    ck(cudaMemsetAsync(M.xcur.p, 0, pn * sizeof(float2), s), "memset x");
+    const int nparts = 152;
+    DevArr<double> part;
+    part.alloc((size_t)nparts * nr);
+    std::vector<double> hp((size_t)nparts * nr), bn(nr, 0.0), rn(nr, 0.0);
+    // out[r] = ||b_r - y_r|| for y = A x (FP32 products); M.bvec receives b - y
+    auto norms = [&](const float2 *y, std::vector<double> &out) {
+        for (int r = 0; r < nr; ++r) {
+            k_refine_residual<<<nparts, 256, 0, s>>>(M.bsave.p + r * n, y + r * n, M.bvec.p + r * n, n,
+                                                     part.p + (int64_t)r * nparts);
+            ck_launch("k_refine_residual");
+        }
+        ck(cudaMemcpyAsync(hp.data(), part.p, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H norms");
+        ck(cudaStreamSynchronize(s), "sync");
+        for (int r = 0; r < nr; ++r) {
+            double v = 0.0;
+            for (int q = 0; q < nparts; ++q) v += hp[(size_t)r * nparts + q];
+            out[r] = std::sqrt(v);
+        }
+    };
+    norms(M.xcur.p, bn);        // x = 0: the residual is b
+    GmresResult R;
+    R.hp.assign(nr, GmresState());
+    R.iters.assign(nr, 0);
+    R.conv.assign(nr, 0);
+    int total = 0;
+    rn = bn;
+    for (int outer = 0; outer < 30; ++outer) {
+        if (outer > 0) {
+            // r = b - A x with the FP32 products, differenced in FP64
+            M.force_fp32 = true;
+            try {
+                matvec_internal(M, fr(M).cp.p, fr(M).cq.p, true, M.xcur.p, nullptr, false, M.rtmp.p, false, nullptr,
+                                s, false, false, nr);
+            } catch (...) {
+                M.force_fp32 = false;
+                throw;
+            }
+            M.force_fp32 = false;
+            total += 1;
+            norms(M.rtmp.p, rn);
+        }
+        bool all = true;
+        double worst = 0.0;
+        for (int r = 0; r < nr; ++r) {
+            const double rel = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
+            R.hp[r].resid = rel;
+            R.conv[r] = rel <= tol;
+            all = all && R.conv[r];
+            worst = std::max(worst, rel);
+        }
+        if (all || total >= max_iter) break;
+        // inner solve of A d = r with the mixed-precision products
+        precondition_rhs(M, M.bvec.p, nr);
+        const double inner = std::min(0.5, std::max(1e-3, 0.5 * tol / std::max(worst, 1e-300)));
+        GmresResult G = run_gmres(M, inner, std::max(1, max_iter - total), false, nr);
+        int most = 0;
+        for (int r = 0; r < nr; ++r) most = std::max(most, G.iters[r]);
+        total += most;
+        R.restarts += G.restarts + 1;
+        for (int r = 0; r < nr; ++r) {
+            k_refine_update<<<nblocks(n, 256), 256, 0, s>>>(M.x64.p + r * n, M.uvec.p + r * n, M.xcur.p + r * n, n);
+            ck_launch("k_refine_update");
+        }
+    }
+    ck(cudaMemcpyAsync(M.uvec.p, M.xcur.p, pn * sizeof(float2), cudaMemcpyDeviceToDevice, s), "D2D x");
+    for (int r = 0; r < nr; ++r) {
+        R.iters[r] = total;
+        R.hp[r].iters = total;
+        R.hp[r].converged = R.conv[r];
+    }
+    R.h = R.hp[0];
+    R.total_iters = total;
+    R.converged = R.conv[0];
+    return R;
+}
+
 // Solve with the current frame's plan (prepared for freq_hz): right-hand
 // side, GMRES, p and q in the caller's order.  nr = 1: one right-hand side,
 // the incident field of all n_src sources; nr > 1 (= n_src): one system per
@@ -2226,13 +2396,6 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
                 k_row_scale_init<<<nblocks(n, 128), 128, 0, s>>>(na, M.dinv.p, fr(M).err.p);
             }
             ck_launch("k_row_scale_init");
-            for (int r = 0; r < nr; ++r) {
-                {
-                    KTimer kt_("k_row_scale", s);
-                    k_row_scale<<<nblocks(n, 256), 256, 0, s>>>(M.bvec.p + r * n, nullptr, M.dinv.p, n, nullptr);
-                }
-                ck_launch("k_row_scale");
-            }
         }
         // block-Jacobi (the block form of the row scaling of Sec. 3.2):
         // GMRES on P A u = P b, P the inverse of A's block diagonal
@@ -2247,18 +2410,15 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
             }
             ck_launch("k_bj_factor");
             check_err(M);
-            for (int r = 0; r < nr; ++r) {
-                {
-                    KTimer kt_("k_bj_apply", s);
-                    k_bj_apply<<<(unsigned)Lb.h_bj.size(), kBjMax, 0, s>>>(Lb.bj.p, M.bjinv.p, M.bvec.p + r * n,
-                                                                           nullptr, nullptr);
-                }
-                ck_launch("k_bj_apply");
-            }
         }
+        // the preconditioned right-hand side (the refinement of a
+        // mixed-precision solve preconditions each inner residual instead)
+        if (M.prm.far_precision != 1) precondition_rhs(M, M.bvec.p, nr);
         ck(cudaStreamSynchronize(s), "sync");
         auto t_rhs = std::chrono::steady_clock::now();
-        GmresResult R = run_gmres(M, tol, max_iter, false, nr);
+        GmresResult R = M.prm.far_precision == 1 ? run_refined(M, tol, max_iter, nr)
+                                                 : run_gmres(M, tol, max_iter, false, nr);
+        check_tc_fault(M);
         auto t_gmres = std::chrono::steady_clock::now();
         // p and q in the caller's order
         for (int r = 0; r < nr; ++r) {

@@ -24,7 +24,6 @@ __device__ __forceinline__ double2 warp_sum_d(double2 v)
     return v;
 }
 
-__device__ __forceinline__ bool skip_now(const int *skip) { return skip != nullptr && *(volatile const int *)skip != 0; }
 
 // ------------------------------------------------------------------ near field
 // Expensive pairs (heavy_rt2) of the stored near field, listed by kind so
@@ -934,57 +933,7 @@ __device__ __forceinline__ void aggregate_body(const LevelsArgs *__restrict__ A,
             out[r * f.mplane + p + h] = accm[r];
         }
     }
-    if (T.red < 0) return;
-    // split cluster: its blocks are (element chunks) x (pair ranges); the
-    // last one to finish sums the partial rows in row order into M_c
-    __shared__ bool last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const int npb = (h + kAggThreads - 1) / kAggThreads;
-        const int ntask = (f.red_ptr[T.red + 1] - f.red_ptr[T.red]) * npb;
-        last = atomicAdd(&A->red_cnt[T.gred], 1u) == (unsigned)(ntask - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    const int r0 = f.red_ptr[T.red], r1 = f.red_ptr[T.red + 1];
-    const int nd = f.nd;
-    for (int pl = 0; pl < NR; ++pl) {
-    const float2 *__restrict__ Mp = f.M + pl * f.mplane;
-    float2 *__restrict__ dst = f.M + pl * f.mplane + (int64_t)T.c * nd;
-    // each thread sums kRedDirs directions at a time and loads kRedRows rows
-    // of them together (L2 loads of other blocks' rows, all in flight at
-    // once); every direction still adds its rows in row order
-    constexpr int kRedDirs = 4, kRedRows = 4;
-    for (int nb = threadIdx.x; nb < nd; nb += kAggThreads * kRedDirs) {
-        float2 acc[kRedDirs];
-#pragma unroll
-        for (int b = 0; b < kRedDirs; ++b) acc[b] = make_float2(0.f, 0.f);
-        for (int rr = r0; rr < r1; rr += kRedRows) {
-            float2 v[kRedRows][kRedDirs];
-#pragma unroll
-            for (int a = 0; a < kRedRows; ++a)
-#pragma unroll
-                for (int b = 0; b < kRedDirs; ++b) {
-                    const int nu = nb + b * kAggThreads;
-                    v[a][b] = (rr + a < r1 && nu < nd) ? __ldcg(Mp + (int64_t)(rr + a) * nd + nu)
-                                                       : make_float2(0.f, 0.f);
-                }
-#pragma unroll
-            for (int a = 0; a < kRedRows; ++a)
-#pragma unroll
-                for (int b = 0; b < kRedDirs; ++b) {
-                    acc[b].x += v[a][b].x;
-                    acc[b].y += v[a][b].y;
-                }
-        }
-#pragma unroll
-        for (int b = 0; b < kRedDirs; ++b)
-            if (nb + b * kAggThreads < nd) dst[nb + b * kAggThreads] = acc[b];
-    }
-    }
-    if (threadIdx.x == 0) A->red_cnt[T.gred] = 0;
+    aggregate_reduce(A, T, f, kAggThreads, NR);
 }
 
 #define BEM_AGGREGATE_KERNEL(NR)                                                                                      \
@@ -1579,6 +1528,40 @@ __global__ void k_gather(const float2 *__restrict__ x, const int64_t *__restrict
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = x[perm[i]];
 }
+// Iterative refinement of a mixed-precision solve: r = b - y in FP64 from the
+// FP32 right-hand side and product (y = A x with the FP32 products), stored
+// as FP32 in r; part[blockIdx.x] = the block's ||r||^2 in FP64.
+__global__ void k_refine_residual(const float2 *__restrict__ b, const float2 *__restrict__ y, float2 *__restrict__ r,
+                                  int64_t n, double *__restrict__ part)
+{
+    double v = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double rx = (double)b[i].x - (double)y[i].x, ry = (double)b[i].y - (double)y[i].y;
+        r[i] = make_float2((float)rx, (float)ry);
+        v += rx * rx + ry * ry;
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = s;
+    }
+}
+
+// x64 += d (the refinement's FP64 solution) and x = x64 rounded to FP32.
+__global__ void k_refine_update(double2 *__restrict__ x64, const float2 *__restrict__ d, float2 *__restrict__ x,
+                                int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 v = make_double2(x64[i].x + (double)d[i].x, x64[i].y + (double)d[i].y);
+    x64[i] = v;
+    x[i] = make_float2((float)v.x, (float)v.y);
+}
+
 // b <- b - y
 __global__ void k_sub(float2 *__restrict__ b, const float2 *__restrict__ y, int64_t n)
 {

@@ -160,6 +160,70 @@ __global__ void k_near_spmv_items_multi(NearArgs a, const int4 *items, const flo
                                         int nr, int64_t plane, const int *skip);
 __global__ void k_near_fused(NearArgs a, const float2 *x, float2 *y, int *err, const int *skip);
 __global__ void k_prep(PrepArgs a, const int *skip);
+// True when the product kernels of a finished GMRES cycle should skip.
+__device__ __forceinline__ bool skip_now(const int *skip) { return skip != nullptr && *(volatile const int *)skip != 0; }
+
+// Split cluster (T.red >= 0) of an aggregation launch whose blocks take ppb
+// direction pairs each: its blocks are (element chunks) x (pair ranges), and
+// the last one to finish sums the partial rows in row order into row T.c of
+// every plane (nplanes right-hand sides).  Called by every thread of the
+// block after its own rows are written.
+__device__ __forceinline__ void aggregate_reduce(const LevelsArgs *A, const AggTask &T, const FarArgs &f, int ppb,
+                                                 int nplanes)
+{
+    if (T.red < 0) return;
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int h = f.nd / 2;
+        const int npb = (h + ppb - 1) / ppb;
+        const int ntask = (f.red_ptr[T.red + 1] - f.red_ptr[T.red]) * npb;
+        last = atomicAdd(&A->red_cnt[T.gred], 1u) == (unsigned)(ntask - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int r0 = f.red_ptr[T.red], r1 = f.red_ptr[T.red + 1];
+    const int nd = f.nd;
+    const int nt = blockDim.x;
+    for (int pl = 0; pl < nplanes; ++pl) {
+        const float2 *__restrict__ Mp = f.M + pl * f.mplane;
+        float2 *__restrict__ dst = f.M + pl * f.mplane + (int64_t)T.c * nd;
+        // each thread sums kRedDirs directions at a time and loads kRedRows
+        // rows of them together (L2 loads of other blocks' rows, all in
+        // flight at once); every direction still adds its rows in row order
+        constexpr int kRedDirs = 4, kRedRows = 4;
+        for (int nb = threadIdx.x; nb < nd; nb += nt * kRedDirs) {
+            float2 acc[kRedDirs];
+#pragma unroll
+            for (int b = 0; b < kRedDirs; ++b) acc[b] = make_float2(0.f, 0.f);
+            for (int rr = r0; rr < r1; rr += kRedRows) {
+                float2 v[kRedRows][kRedDirs];
+#pragma unroll
+                for (int a = 0; a < kRedRows; ++a)
+#pragma unroll
+                    for (int b = 0; b < kRedDirs; ++b) {
+                        const int nu = nb + b * nt;
+                        v[a][b] = (rr + a < r1 && nu < nd) ? __ldcg(Mp + (int64_t)(rr + a) * nd + nu)
+                                                           : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                for (int a = 0; a < kRedRows; ++a)
+#pragma unroll
+                    for (int b = 0; b < kRedDirs; ++b) {
+                        acc[b].x += v[a][b].x;
+                        acc[b].y += v[a][b].y;
+                    }
+            }
+#pragma unroll
+            for (int b = 0; b < kRedDirs; ++b)
+                if (nb + b * nt < nd) dst[nb + b * nt] = acc[b];
+        }
+    }
+    if (threadIdx.x == 0) A->red_cnt[T.gred] = 0;
+}
+
 // Aggregation of NR right-hand sides at once (one phase per element and
 // direction pair serves all of them); wts holds NR planes of n elements.
 __global__ void k_aggregate_1(const LevelsArgs *A, const float4 *wts, int64_t wplane, const float4 *nrm, const int *skip);
@@ -167,6 +231,15 @@ __global__ void k_aggregate_2(const LevelsArgs *A, const float4 *wts, int64_t wp
 __global__ void k_aggregate_3(const LevelsArgs *A, const float4 *wts, int64_t wplane, const float4 *nrm, const int *skip);
 __global__ void k_aggregate_4(const LevelsArgs *A, const float4 *wts, int64_t wplane, const float4 *nrm, const int *skip);
 constexpr int kMaxPlanes = 4;            // right-hand sides per multi-plane launch
+// Aggregation on the tensor cores (bem_tc.cu): tasks of one element chunk
+// and kTcPairs direction pairs, split-BF16 operands, FP32 accumulation;
+// fault is set when the wait for the tensor cores runs out.
+constexpr int kTcThreads = 256;
+constexpr int kTcPairs = 128;
+constexpr size_t kTcSmemBytes = 2 * (size_t)kTcPairs * 4 * kAggChunk * 2 + 2 * (size_t)4 * kMaxPlanes * 4 * kAggChunk * 2 +
+                                1024;
+__global__ void k_aggregate_tc(const LevelsArgs *A, const AggTask *tasks, const float4 *wts, int64_t wplane,
+                               const float4 *nrm, int nr, int *fault, const int *skip);
 __global__ void k_selftest_sincos(const float *x, int64_t n, float4 *out);
 // Transfer with the interaction list of one target split among
 // kTransferWarps warps: one block per (target, kTransferDirs directions).
@@ -222,6 +295,8 @@ __global__ void k_bj_apply(const int4 *blocks, const float2 *binv, float2 *w, fl
 __global__ void k_row_scale_init(NearArgs a, float2 *dinv, int *err);
 __global__ void k_row_scale(float2 *y, float2 *y2, const float2 *dinv, int64_t n, const int *skip);
 __global__ void k_sub(float2 *b, const float2 *y, int64_t n);
+__global__ void k_refine_residual(const float2 *b, const float2 *y, float2 *r, int64_t n, double *part);
+__global__ void k_refine_update(double2 *x64, const float2 *d, float2 *x, int64_t n);
 __global__ void k_rsub(float2 *w, const float2 *b, int64_t n);
 __global__ void k_pq(const float2 *u, const float2 *z, const float2 *aq, const int *type, const int64_t *perm,
                      int64_t n, float2 *p, float2 *q);
