@@ -2245,8 +2245,9 @@ void precondition_rhs(bem_mesh_impl &M, float2 *b, int nr)
 // the tensor cores (far_precision 1): the solution is kept in FP64 (x64), the
 // residual r = b - A x is formed with the FP32 products and differenced in
 // FP64, and each inner GMRES (the mixed-precision products, preconditioned
-// as the mesh asks) solves A d = r to a relative 1e-3 (or less when the
-// target is closer), x64 += d, until ||r|| <= tol ||b|| for every plane.  b:
+// as the mesh asks) solves A d = r to half the remaining target, x64 += d,
+// until ||r|| <= tol ||b|| for every plane (the true residual of the FP32
+// operator, not the GMRES estimate of the mixed-precision one).  b:
 // M.bvec (nr planes, not preconditioned); the solution ends in M.uvec.
 // Products: inner products plus one FP32 product per outer step.
 GmresResult run_refined(bem_mesh_impl &M, double tol, int32_t max_iter, int nr)
@@ -2312,9 +2313,12 @@ GmresResult run_refined(bem_mesh_impl &M, double tol, int32_t max_iter, int nr)
             worst = std::max(worst, rel);
         }
         if (all || total >= max_iter) break;
-        // inner solve of A d = r with the mixed-precision products
+        // inner solve of A d = r with the mixed-precision products, aimed at
+        // the target (with a margin of two): the split-BF16 products carry
+        // errors near the FP32 products' own, so one inner solve usually
+        // suffices and the FP32 residual only confirms it
         precondition_rhs(M, M.bvec.p, nr);
-        const double inner = std::min(0.5, std::max(1e-3, 0.5 * tol / std::max(worst, 1e-300)));
+        const double inner = std::min(0.5, 0.5 * tol / std::max(worst, 1e-300));
         GmresResult G = run_gmres(M, inner, std::max(1, max_iter - total), false, nr);
         int most = 0;
         for (int r = 0; r < nr; ++r) most = std::max(most, G.iters[r]);
