@@ -229,6 +229,13 @@ def random_complex(n: int, seed: int, shape=None):
     return rng.normal(size=shp) + 1j * rng.normal(size=shp)
 
 
+def tetrahedral_directions():
+    """The four unit directions (+-1, +-1, +-1) / sqrt(3) with an even number
+    of minus signs (the vertices of a regular tetrahedron)."""
+    d = np.array([[1.0, 1.0, 1.0], [1.0, -1.0, -1.0], [-1.0, 1.0, -1.0], [-1.0, -1.0, 1.0]])
+    return d / np.sqrt(3.0)
+
+
 def workload(name: str):
     """The synthetic workloads the library is checked and measured on.
 
@@ -237,6 +244,11 @@ def workload(name: str):
     sphere5120_2k  : the same sphere as an icosphere of 5120 triangles at 2 kHz.
     sphere20480_4k : the same sphere as an icosphere of 20480 triangles, plane
                      wave along +z at 4 kHz, 100 field points on a 1 m sphere.
+    bumpy158k_20k  : the head-like bumpy ellipsoid (bumpy_ellipsoid) at
+                     geodesic frequency 89 (158420 triangles, mean edge 1.3 mm,
+                     about a thirteenth of the wavelength) at 20 kHz, four
+                     plane waves along the tetrahedral directions (one
+                     right-hand side each).
     """
     if name == "sphere1280_1k":
         nodes, tris = icosphere(3, 0.1)
@@ -247,10 +259,16 @@ def workload(name: str):
     elif name == "sphere20480_4k":
         nodes, tris = icosphere(5, 0.1)
         freq = 4000.0
+    elif name == "bumpy158k_20k":
+        nodes, tris = bumpy_ellipsoid(89)
+        freq = 20000.0
     else:
         raise KeyError(name)
-    return {
+    out = {
         "name": name, "nodes": nodes, "tris": tris, "freq": freq, "c": 343.0, "rho": 1.21,
         "plane_dir": (0.0, 0.0, 1.0), "amp": 1.0 + 0.0j,
         "field_points": fibonacci_sphere(100, 1.0),
     }
+    if name == "bumpy158k_20k":
+        out["plane_dirs"] = tetrahedral_directions()
+    return out
