@@ -815,8 +815,15 @@ void build_plan_dev(bem_mesh_impl &M, double freq, double c)
     auto stable_from = [&](int L) {
         auto it = M.growth_root.find(L);
         if (it != M.growth_root.end()) return it->second;
+        // as x grows every |h_n(x)| tends to 1/x, so the growth tends to
+        // sum_{n<=L} (2n+1) = (L+1)^2 from above: beyond the bound no offset
+        // is ever stable
+        if ((double)(L + 1) * (L + 1) > M.prm.stability_max) {
+            M.growth_root[L] = HUGE_VAL;
+            return HUGE_VAL;
+        }
         double lo = 1e-9, hi = 1.0;
-        while (!(hankel_growth(hi, L) <= M.prm.stability_max)) hi *= 2.0;
+        for (int it2 = 0; it2 < 64 && !(hankel_growth(hi, L) <= M.prm.stability_max); ++it2) hi *= 2.0;
         for (int it2 = 0; it2 < 200 && hi - lo > 1e-13 * hi; ++it2) {
             const double mid = 0.5 * (lo + hi);
             if (hankel_growth(mid, L) <= M.prm.stability_max) hi = mid;

@@ -765,3 +765,22 @@ def test_multi_rhs_solve_matches_single_solves_and_oracle(bem, precond):
         _check(P[r].cpu().numpy(), po, 2e-4, 2e-3, "multi-rhs p vs oracle, rhs %d" % r)
         _check(Q[r].cpu().numpy(), qo, 2e-4, 2e-3, "multi-rhs q vs oracle, rhs %d" % r)
     mesh.close()
+
+
+def test_plan_with_levels_that_can_never_be_stable(bem):
+    """At a frequency where a coarse level's expansion length reaches L >= 31,
+    the stability sum (2n+1)|h_n|/|h_0| stays above (L+1)^2 > 1e3 at every
+    distance: that level can have no far pairs (its pairs stay near) and the
+    plan must say so instead of searching for a stable distance forever.
+    1280 elements at 25 kHz (under-resolved, which only warns): the product
+    still matches the oracle."""
+    nodes, tris = inputs.icosphere(3, 0.1)
+    n = tris.shape[0]
+    freq = 25000.0
+    k = 2 * np.pi * freq / C
+    x = inputs.random_complex(n, 77)
+    mesh = bem.Mesh(nodes, tris, trunc_factor=8.0)
+    y = mesh.matvec(freq, torch.tensor(x, dtype=torch.complex64, device="cuda"), c=C, rho=RHO).cpu().numpy()
+    mesh.close()
+    yo = oracle.assemble(nodes, tris, k, np.ones(n, complex), np.zeros(n, complex)) @ x
+    _check(y, yo, 2e-5, 2e-4, "product at 25 kHz (coarse levels never stable)")
