@@ -1200,16 +1200,21 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
         ck_launch("k_transfer");
     }
     NearArgs na = near_args(M, P, cp, cq);
-    if (nr > 1 && use_store && M.prm.near_store && !P.fp().direct &&
-        (size_t)nr * (((size_t)P.lists->max_ncol + 1) & ~(size_t)1) * sizeof(float2) <= 160 * 1024) {
-        // all right-hand sides in one pass over the stored values
-        const size_t xs_bytes = (size_t)nr * (((size_t)P.lists->max_ncol + 1) & ~(size_t)1) * sizeof(float2);
-        if (P.lists->n_spmv_items > 0) {
-            KTimer kt_("k_near_spmv", s);
-            k_near_spmv_items_multi<<<P.lists->n_spmv_items, kSpmvThreads, xs_bytes, s>>>(
-                na, P.lists->spmv_items.p, P.val.p, M.xint.p, M.ynear.p, nr, n, skip);
+    // right-hand sides per pass of the multi-plane near-field product: as many
+    // as the staged columns of the largest leaf allow in shared memory
+    const size_t plane_bytes = (((size_t)P.lists->max_ncol + 1) & ~(size_t)1) * sizeof(float2);
+    const int fit = (int)std::min<size_t>(kMaxPlanes, kSpmvMultiSmem / std::max<size_t>(plane_bytes, 1));
+    if (nr > 1 && use_store && M.prm.near_store && !P.fp().direct && fit >= 2) {
+        // the right-hand sides in ceil(nr / fit) passes over the stored values
+        for (int r0 = 0; r0 < nr; r0 += fit) {
+            const int g = std::min(fit, nr - r0);
+            if (P.lists->n_spmv_items > 0) {
+                KTimer kt_("k_near_spmv", s);
+                k_near_spmv_items_multi<<<P.lists->n_spmv_items, kSpmvThreads, (size_t)g * plane_bytes, s>>>(
+                    na, P.lists->spmv_items.p, P.val.p, M.xint.p + r0 * n, M.ynear.p + r0 * n, g, n, skip);
+            }
+            ck_launch("k_near_spmv");
         }
-        ck_launch("k_near_spmv");
     } else if (nr > 1) {
         // one right-hand side at a time (the values are streamed nr times)
         for (int r = 0; r < nr; ++r) {
@@ -1283,9 +1288,29 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
             throw Fail{set_err(BEM_E_ARG, "far field: " + std::to_string(da.sum_nd) +
                                               " directions over all levels exceed the disaggregation kernel's "
                                               "shared-memory staging")};
-        if (P.lists->n_dis_tasks > 0)
-            k_disaggregate<<<dim3(P.lists->n_dis_tasks, nr), kDisThreads, smem, sd>>>(da, far_only ? nullptr : M.ynear.p,
-                                                                                    y, skip);
+        if (P.lists->n_dis_tasks > 0) {
+            if (nr == 1) {
+                k_disaggregate<<<P.lists->n_dis_tasks, kDisThreads, smem, sd>>>(da, far_only ? nullptr : M.ynear.p, y,
+                                                                                skip);
+            } else {
+                // the planes in groups of four (or two): one phase per element
+                // and direction pair serves a whole group
+                const size_t unit = (size_t)std::max(2, da.sum_nd) / 2 * sizeof(float4);
+                for (int r0 = 0; r0 < nr;) {
+                    int g = nr - r0 >= 4 ? 4 : (nr - r0 >= 2 ? 2 : 1);
+                    while (g > 1 && unit * (1 + g) > kDisaggSmem) g /= 2;
+                    DisaggArgs dg = da;
+                    for (int l = 0; l < A.nlev; ++l) dg.lev[l].Lam = A.lev[l].Lam + r0 * A.lev[l].lplane;
+                    const float2 *yn = far_only ? nullptr : M.ynear.p + r0 * n;
+                    float2 *yo = y + r0 * n;
+                    const size_t sm = (size_t)std::max(2, da.sum_nd) / 2 * sizeof(float4) * (1 + g);
+                    if (g == 4) k_disaggregate_m4<<<P.lists->n_dis_tasks, kDisThreads, sm, sd>>>(dg, yn, yo, skip);
+                    else if (g == 2) k_disaggregate_m2<<<P.lists->n_dis_tasks, kDisThreads, sm, sd>>>(dg, yn, yo, skip);
+                    else k_disaggregate<<<P.lists->n_dis_tasks, kDisThreads, smem, sd>>>(dg, yn, yo, skip);
+                    r0 += g;
+                }
+            }
+        }
     }
     ck_launch("k_disaggregate");
     if (fork && far_only) {
@@ -1770,7 +1795,8 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         M->type.upload(ty, s);
         ck(cudaFuncSetAttribute(k_near_spmv_items, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024),
            "cudaFuncSetAttribute");
-        ck(cudaFuncSetAttribute(k_near_spmv_items_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024),
+        ck(cudaFuncSetAttribute(k_near_spmv_items_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSpmvMultiSmem),
            "cudaFuncSetAttribute");
 
         ck(cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 100 * 16),
@@ -1782,6 +1808,10 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         M->tc_fault.alloc(1);
         ck(cudaMemsetAsync(M->tc_fault.p, 0, sizeof(int), s), "memset");
         ck(cudaFuncSetAttribute(k_disaggregate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDisaggSmem),
+           "cudaFuncSetAttribute");
+        ck(cudaFuncSetAttribute(k_disaggregate_m2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDisaggSmem),
+           "cudaFuncSetAttribute");
+        ck(cudaFuncSetAttribute(k_disaggregate_m4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDisaggSmem),
            "cudaFuncSetAttribute");
 
         std::vector<QuadTables> qt(1, make_tables(p));

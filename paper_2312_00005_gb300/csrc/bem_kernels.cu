@@ -1177,6 +1177,134 @@ __device__ __forceinline__ void disaggregate_body(const DisaggArgs &a, const flo
     }
 }
 
+// The disaggregation of NR right-hand sides at once (forward row factor
+// 1 + s.n_i): the same blocks and staging as disaggregate_body, with the
+// weighted rows (A, B) of every plane in shared memory, so that one phase per
+// element and direction pair serves all planes; chunks of 8 / NR elements
+// keep the accumulators in registers.  Planes are n apart in ynear and y.
+template <int NR>
+__device__ __forceinline__ void disaggregate_multi_body(const DisaggArgs &a, const float2 *__restrict__ ynear,
+                                                        float2 *__restrict__ y)
+{
+    constexpr int kCh = kDisChunk / NR;
+    extern __shared__ float4 dsm[];   // [HP] first-half directions, then [NR][HP] (A, B) pairs
+    float4 *dir_s = dsm;
+    constexpr int kNW = kDisThreads / 32;
+    __shared__ int s_lev[kMaxFarLevels], s_poff[kMaxFarLevels + 1];
+    __shared__ int s_nact;
+    __shared__ float4 dzs[kDisTask][kMaxFarLevels];
+    __shared__ float4 ns[kDisTask];
+    __shared__ float2 red[NR][kNW][kDisTask];
+    const int2 tk = a.tasks[blockIdx.x];
+    const int64_t e0 = tk.x, e1 = tk.y;
+    const int cnt_all = (int)min((int64_t)kDisTask, e1 - e0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        int na = 0, poff = 0;
+        for (int l = 0; l < a.nlev; ++l) {
+            const FarArgs &f = a.lev[l];
+            const int c = f.elem_cl[e0];
+            if (f.il_ptr[c] == f.il_ptr[c + 1]) continue;
+            s_lev[na] = l;
+            s_poff[na] = poff;
+            poff += f.nd / 2;
+            ++na;
+        }
+        s_poff[na] = poff;
+        s_nact = na;
+    }
+    __syncthreads();
+    const int na = s_nact, HP = s_poff[na];
+    float4 *ab_s = dsm + a.sum_nd / 2;   // plane r at ab_s + r * (sum_nd / 2)
+    const int abp = a.sum_nd / 2;
+    for (int u = 0; u < na; ++u) {
+        const FarArgs &f = a.lev[s_lev[u]];
+        const int h = f.nd / 2;
+        for (int q = threadIdx.x; q < h; q += blockDim.x) {
+            const float4 d = f.dirs[q];
+            dir_s[s_poff[u] + q] = make_float4(d.x, d.y, d.z, __int_as_float(u));
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float2 *__restrict__ src = f.Lam + r * f.lplane + (int64_t)f.elem_cl[e0] * f.nd;
+                const float2 lp = cscale(src[q], d.w), lm = cscale(src[q + h], d.w);
+                ab_s[r * abp + s_poff[u] + q] = make_float4(lp.x + lm.x, lp.y + lm.y, lp.x - lm.x, lp.y - lm.y);
+            }
+        }
+    }
+    for (int v = threadIdx.x; v < cnt_all * na; v += blockDim.x) {
+        const int q = v / na, u = v % na;
+        const FarArgs &f = a.lev[s_lev[u]];
+        const float kt = -f.k * 0.15915494309189535f;
+        const float4 dz = f.dz[e0 + q];
+        dzs[q][u] = make_float4(kt * dz.x, kt * dz.y, kt * dz.z, 0.f);
+    }
+    for (int q = threadIdx.x; q < cnt_all; q += blockDim.x) ns[q] = a.nrm[e0 + q];
+    __syncthreads();
+    for (int q0 = 0; q0 < cnt_all; q0 += kCh) {
+        const int cnt = min(kCh, cnt_all - q0);
+        float2 acc[kCh][NR];
+#pragma unroll
+        for (int q = 0; q < kCh; ++q)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[q][r] = make_float2(0.f, 0.f);
+        for (int pf = threadIdx.x; pf < HP; pf += blockDim.x) {
+            const float4 sv = dir_s[pf];
+            const int u = __float_as_int(sv.w);
+            float4 ab[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) ab[r] = ab_s[r * abp + pf];
+#pragma unroll
+            for (int q = 0; q < kCh; ++q) {
+                if (q < cnt) {
+                    const float4 d = dzs[q0 + q][u], n = ns[q0 + q];
+                    float sn0, cs0;
+                    sincos_turns(fmaf(d.x, sv.x, fmaf(d.y, sv.y, d.z * sv.z)), &sn0, &cs0);
+                    const float tn = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        // (cs + i sn)(1 + t) lp + (cs - i sn)(1 - t) lm = cs sp + i sn dm
+                        const float spx = fmaf(tn, ab[r].z, ab[r].x), spy = fmaf(tn, ab[r].w, ab[r].y);
+                        const float dmx = fmaf(tn, ab[r].x, ab[r].z), dmy = fmaf(tn, ab[r].y, ab[r].w);
+                        acc[q][r].x = fmaf(cs0, spx, fmaf(-sn0, dmy, acc[q][r].x));
+                        acc[q][r].y = fmaf(cs0, spy, fmaf(sn0, dmx, acc[q][r].y));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kCh; ++q)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float2 v = warp_sum(acc[q][r]);
+                if (lane == 0 && q < cnt) red[r][warp][q0 + q] = v;
+            }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt_all * NR; t += blockDim.x) {
+        const int q = t % cnt_all, r = t / cnt_all;
+        float2 v = red[r][0][q];
+#pragma unroll
+        for (int w = 1; w < kNW; ++w) v = cadd(v, red[r][w][q]);
+        const int64_t i = e0 + q;
+        const float sc = a.k * 0.00633257397764611f;   // k / (16 pi^2)
+        const float2 far = make_float2(-sc * v.y, sc * v.x);
+        const float2 out = ynear ? cadd(ynear[r * a.n + i], far) : far;
+        if (a.perm) y[r * a.n + a.perm[i]] = out;
+        else y[r * a.n + i] = out;
+    }
+}
+
+#define BEM_DISAGG_MULTI_KERNEL(NR)                                                                                 \
+    __global__ void __launch_bounds__(kDisThreads) k_disaggregate_m##NR(DisaggArgs a, const float2 *__restrict__ ynear, \
+                                                                        float2 *__restrict__ y, const int *skip)     \
+    {                                                                                                               \
+        if (skip_now(skip)) return;                                                                                 \
+        disaggregate_multi_body<NR>(a, ynear, y);                                                                   \
+    }
+BEM_DISAGG_MULTI_KERNEL(2)
+BEM_DISAGG_MULTI_KERNEL(4)
+#undef BEM_DISAGG_MULTI_KERNEL
+
 __global__ void __launch_bounds__(kDisThreads, 16) k_disaggregate(DisaggArgs a, const float2 *__restrict__ ynear,
                                                                   float2 *__restrict__ y, const int *skip)
 {

@@ -156,6 +156,9 @@ __global__ void k_near_spmv_items(NearArgs a, const int4 *items, const float2 *v
                                   const int *skip);
 // The same for nr <= kMaxPlanes right-hand sides (planes `plane` elements
 // apart in x and y): the stored values are streamed once for all of them.
+// Dynamic shared memory: nr planes of the leaf's columns, at most
+// kSpmvMultiSmem bytes (the kernel's static part takes 4 KB of the 227 KB).
+constexpr size_t kSpmvMultiSmem = 216 * 1024;
 __global__ void k_near_spmv_items_multi(NearArgs a, const int4 *items, const float2 *val, const float2 *x, float2 *y,
                                         int nr, int64_t plane, const int *skip);
 __global__ void k_near_fused(NearArgs a, const float2 *x, float2 *y, int *err, const int *skip);
@@ -249,6 +252,10 @@ constexpr int kTransferUnroll = 8;         // list entries per warp in flight
 constexpr int kTransferEntries = 512;     // interaction-list entries staged per pass
 __global__ void k_transfer_split(const LevelsArgs *A, const int *skip);
 __global__ void k_disaggregate(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
+// 2 or 4 right-hand sides at once (one phase per element and pair for all);
+// dynamic shared memory (sum_nd / 2) (1 + NR) float4
+__global__ void k_disaggregate_m2(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
+__global__ void k_disaggregate_m4(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
 __global__ void k_disaggregate_t(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
 // largest expansion length of the translation tables (shared-memory rows)
 constexpr int kMaxTableL = 255;
