@@ -173,7 +173,7 @@ def run_ours(args):
     n = tris.shape[0]
     pts = W["field_points"]
     src = [bemfmm.plane_wave(W["plane_dir"], W["amp"])]
-    mkw = {"trunc_factor": args.trunc_factor}
+    mkw = {"trunc_factor": args.trunc_factor, "near_chunk": args.near_chunk}
     if args.restart > 0:
         mkw["restart"] = args.restart
     if args.leaf_edge > 0:
@@ -332,7 +332,7 @@ def run_ours(args):
         "config": {"workload": W["name"], "n_elements": n, "freq_hz": f, "sweep_step_hz": 0.25,
                    "mesh": "icosphere r=0.1 m",
                    "source": "plane wave +z", "field_points": int(pts.shape[0]), "gmres_tol": args.tol,
-                   "trunc_factor": args.trunc_factor,
+                   "trunc_factor": args.trunc_factor, "near_chunk": args.near_chunk,
                    "l2_flush": ("256 MB write between steps" if args.no_sweep else
                                 "256 MB write before the sweep; per step the stored near field (8 B x near_nnz, "
                                 "> L2) is streamed again"),
@@ -713,7 +713,7 @@ def run_multi(args):
     budget = args.max_iter if args.max_iter != 1000 else 200
     restart = args.restart if args.restart > 0 else min(1024, budget)
     mkw = {"trunc_factor": args.trunc_factor, "far_precision": args.far_precision, "restart": restart,
-           "block_jacobi": 0 if args.no_block_jacobi else 1}
+           "block_jacobi": 0 if args.no_block_jacobi else 1, "near_chunk": args.near_chunk}
     t_mesh = time.perf_counter()
     mesh = bemfmm.Mesh(nodes, tris, **mkw)
     st = mesh.stats(f, c=c)
@@ -779,7 +779,7 @@ def run_multi(args):
                    "rhs": "4 plane waves, tetrahedral directions", "gmres_budget_products": budget,
                    "gmres_restart": restart, "block_jacobi": mkw["block_jacobi"], "gmres_tol": args.tol,
                    "trunc_factor": args.trunc_factor, "far_precision": args.far_precision,
-                   "solve_call": "bem_solve_multi (4 right-hand sides together)"},
+                   "near_chunk": args.near_chunk, "solve_call": "bem_solve_multi (4 right-hand sides together)"},
     }))
 
 
@@ -809,6 +809,8 @@ def main():
                     help="bumpy158k_20k: oracle rows per right-hand side for the product check")
     ap.add_argument("--no-sweep", action="store_true",
                     help="one bem_solve call per frequency (default: the steps as one bem_solve_sweep call)")
+    ap.add_argument("--near-chunk", type=int, default=0,
+                    help="columns staged per pass of the stored near-field product (0: the library's choice)")
     ap.add_argument("--leaf-edge", type=float, default=0.0,
                     help="fixed leaf box edge in m (default: automatic, autotuned)")
     args = ap.parse_args()

@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
         ("stability_max", ctypes.c_double), ("near_store", ctypes.c_int32), ("restart", ctypes.c_int32),
         ("autotune", ctypes.c_int32), ("tau", ctypes.c_double), ("row_scaling", ctypes.c_int32),
         ("check_orientation", ctypes.c_int32), ("symmetric_far", ctypes.c_int32),
-        ("block_jacobi", ctypes.c_int32), ("far_precision", ctypes.c_int32),
+        ("block_jacobi", ctypes.c_int32), ("far_precision", ctypes.c_int32), ("near_chunk", ctypes.c_int32),
     ]
 
 

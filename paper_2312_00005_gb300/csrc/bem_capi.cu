@@ -1200,21 +1200,17 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
         ck_launch("k_transfer");
     }
     NearArgs na = near_args(M, P, cp, cq);
-    // right-hand sides per pass of the multi-plane near-field product: as many
-    // as the staged columns of the largest leaf allow in shared memory
-    const size_t plane_bytes = (((size_t)P.lists->max_ncol + 1) & ~(size_t)1) * sizeof(float2);
-    const int fit = (int)std::min<size_t>(kMaxPlanes, kSpmvMultiSmem / std::max<size_t>(plane_bytes, 1));
-    if (nr > 1 && use_store && M.prm.near_store && !P.fp().direct && fit >= 2) {
-        // the right-hand sides in ceil(nr / fit) passes over the stored values
-        for (int r0 = 0; r0 < nr; r0 += fit) {
-            const int g = std::min(fit, nr - r0);
-            if (P.lists->n_spmv_items > 0) {
-                KTimer kt_("k_near_spmv", s);
-                k_near_spmv_items_multi<<<P.lists->n_spmv_items, kSpmvThreads, (size_t)g * plane_bytes, s>>>(
-                    na, P.lists->spmv_items.p, P.val.p, M.xint.p + r0 * n, M.ynear.p + r0 * n, g, n, skip);
-            }
-            ck_launch("k_near_spmv");
+    if ((nr > 1 || M.prm.near_chunk > 0) && use_store && M.prm.near_store && !P.fp().direct) {
+        // all right-hand sides in one pass over the stored values, the leaf's
+        // columns staged in chunks
+        const int ncp = (P.lists->max_ncol + 1) & ~1;
+        const int cw = std::max(2, std::min(ncp, M.prm.near_chunk > 0 ? M.prm.near_chunk : kSpmvMultiChunk));
+        if (P.lists->n_spmv_items > 0) {
+            KTimer kt_("k_near_spmv", s);
+            k_near_spmv_items_multi<<<P.lists->n_spmv_items, kSpmvThreads, (size_t)nr * cw * sizeof(float2), s>>>(
+                na, P.lists->spmv_items.p, P.val.p, M.xint.p, M.ynear.p, nr, n, cw, skip);
         }
+        ck_launch("k_near_spmv");
     } else if (nr > 1) {
         // one right-hand side at a time (the values are streamed nr times)
         for (int r = 0; r < nr; ++r) {
@@ -1659,6 +1655,7 @@ void bem_params_default(bem_params *p)
     p->symmetric_far = 0;
     p->block_jacobi = 0;
     p->far_precision = 0;
+    p->near_chunk = 0;
 }
 
 const char *bem_last_error(void) { return g_err.c_str(); }
@@ -1686,6 +1683,8 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
     if (p.symmetric_far != 0 && p.symmetric_far != 1) return set_err(BEM_E_ARG, "symmetric_far must be 0 or 1");
     if (p.block_jacobi != 0 && p.block_jacobi != 1) return set_err(BEM_E_ARG, "block_jacobi must be 0 or 1");
     if (p.far_precision != 0 && p.far_precision != 1) return set_err(BEM_E_ARG, "far_precision must be 0 or 1");
+    if (p.near_chunk != 0 && (p.near_chunk < 64 || p.near_chunk > 4096 || (p.near_chunk & 1)))
+        return set_err(BEM_E_ARG, "near_chunk must be 0 or an even number in 64..4096");
     if (p.block_jacobi && p.row_scaling)
         return set_err(BEM_E_ARG, "row_scaling and block_jacobi are alternatives: set at most one");
     if (!(p.quad_tol > 0) || !(p.rt_subdiv > 0) || !(p.admissibility > 0) || p.L_min < 1 || p.L_min > 200)
@@ -1796,7 +1795,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         ck(cudaFuncSetAttribute(k_near_spmv_items, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024),
            "cudaFuncSetAttribute");
         ck(cudaFuncSetAttribute(k_near_spmv_items_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kSpmvMultiSmem),
+                                (int)(kMaxPlanes * 4096 * sizeof(float2))),
            "cudaFuncSetAttribute");
 
         ck(cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 100 * 16),

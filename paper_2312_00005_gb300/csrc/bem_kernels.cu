@@ -444,10 +444,10 @@ __global__ void __launch_bounds__(kSpmvThreads) k_near_spmv_items_multi(NearArgs
                                                                         const float2 *__restrict__ val,
                                                                         const float2 *__restrict__ x,
                                                                         float2 *__restrict__ y, int nr, int64_t plane,
-                                                                        const int *skip)
+                                                                        int cw, const int *skip)
 {
     if (skip_now(skip)) return;
-    extern __shared__ float2 xs[];            // [nr][ncp]
+    extern __shared__ float2 xs[];            // [nr][cw]: one chunk of the leaf's columns
     constexpr int kW = kSpmvThreads / 32;
     __shared__ float2 part[kMaxPlanes][kSpmvMaxItemRows][kW];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -455,36 +455,43 @@ __global__ void __launch_bounds__(kSpmvThreads) k_near_spmv_items_multi(NearArgs
     const int t = W.x;
     const int nc = a.N.ncol[t];
     const int ncp = (nc + 1) & ~1;
-    {
-        const int r0 = a.N.run_ptr[t], r1 = a.N.run_ptr[t + 1];
-        for (int r = r0 + warp; r < r1; r += kW) {
-            const int2 rr = a.N.runs[r];
-            const int end = (r + 1 < r1) ? a.N.runs[r + 1].y : nc;
-            for (int p = rr.y + lane; p < end; p += 32)
-                for (int pl = 0; pl < nr; ++pl) xs[(int64_t)pl * ncp + p] = x[pl * plane + rr.x + (p - rr.y)];
-        }
-    }
+    const int run0 = a.N.run_ptr[t], run1 = a.N.run_ptr[t + 1];
     for (int q = threadIdx.x; q < kMaxPlanes * kSpmvMaxItemRows * kW; q += kSpmvThreads)
         (&part[0][0][0])[q] = make_float2(0.f, 0.f);
-    __syncthreads();
     const int64_t i0 = a.N.leaf_start[t] + W.y;
     const int nrow = min(W.z - W.y, kSpmvMaxItemRows);
-    const int64_t total = (int64_t)nrow * ncp;
-    int64_t qa = (total * warp / kW) & ~(int64_t)1;
-    const int64_t qb = warp == kW - 1 ? total : (total * (warp + 1) / kW) & ~(int64_t)1;
-    while (qa < qb) {
-        const int r = (int)(qa / ncp);
-        const int c0 = (int)(qa - (int64_t)r * ncp);
-        const int c1 = (int)min((int64_t)ncp, (int64_t)c0 + (qb - qa));
-        const int c1r = min(c1, nc);
-        if (c0 < c1r) {
-            float2 acc[kMaxPlanes];
-            spmv_segment_multi(val + a.N.row_ptr[i0 + r], xs, ncp, c0, c1r, lane, nr, acc);
-            if (lane == 0)
-#pragma unroll
-                for (int pl = 0; pl < kMaxPlanes; ++pl) part[pl][r][warp] = acc[pl];
+    // the columns in chunks of cw (even, so every chunk's rows start on a
+    // 16-byte boundary); each warp keeps its partial sums of a row in its
+    // own slot of part across the chunks
+    for (int cb = 0; cb < ncp; cb += cw) {
+        const int cwp = min(cw, ncp - cb);
+        const int ce = min(cb + cwp, nc);
+        if (cb > 0) __syncthreads();          // the previous chunk's columns are no longer read
+        for (int r = run0 + warp; r < run1; r += kW) {
+            const int2 rr = a.N.runs[r];
+            const int end = (r + 1 < run1) ? a.N.runs[r + 1].y : nc;
+            const int lo = max(rr.y, cb), hi = min(end, ce);
+            for (int p = lo + lane; p < hi; p += 32)
+                for (int pl = 0; pl < nr; ++pl) xs[pl * cw + (p - cb)] = x[pl * plane + rr.x + (p - rr.y)];
         }
-        qa += c1 - c0;
+        __syncthreads();
+        const int64_t total = (int64_t)nrow * cwp;
+        int64_t qa = (total * warp / kW) & ~(int64_t)1;
+        const int64_t qb = warp == kW - 1 ? total : (total * (warp + 1) / kW) & ~(int64_t)1;
+        while (qa < qb) {
+            const int r = (int)(qa / cwp);
+            const int c0 = (int)(qa - (int64_t)r * cwp);
+            const int c1 = (int)min((int64_t)cwp, (int64_t)c0 + (qb - qa));
+            const int c1r = min(c1, ce - cb);
+            if (c0 < c1r) {
+                float2 acc[kMaxPlanes];
+                spmv_segment_multi(val + a.N.row_ptr[i0 + r] + cb, xs, cw, c0, c1r, lane, nr, acc);
+                if (lane == 0)
+#pragma unroll
+                    for (int pl = 0; pl < kMaxPlanes; ++pl) part[pl][r][warp] = cadd(part[pl][r][warp], acc[pl]);
+            }
+            qa += c1 - c0;
+        }
     }
     __syncthreads();
     for (int q = threadIdx.x; q < nrow * nr; q += kSpmvThreads) {

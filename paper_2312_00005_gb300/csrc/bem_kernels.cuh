@@ -156,11 +156,11 @@ __global__ void k_near_spmv_items(NearArgs a, const int4 *items, const float2 *v
                                   const int *skip);
 // The same for nr <= kMaxPlanes right-hand sides (planes `plane` elements
 // apart in x and y): the stored values are streamed once for all of them.
-// Dynamic shared memory: nr planes of the leaf's columns, at most
-// kSpmvMultiSmem bytes (the kernel's static part takes 4 KB of the 227 KB).
-constexpr size_t kSpmvMultiSmem = 216 * 1024;
+// The leaf's columns are staged in chunks of cw (even) columns: dynamic
+// shared memory nr * cw * 8 bytes, small enough for several blocks per SM.
+constexpr int kSpmvMultiChunk = 1024;
 __global__ void k_near_spmv_items_multi(NearArgs a, const int4 *items, const float2 *val, const float2 *x, float2 *y,
-                                        int nr, int64_t plane, const int *skip);
+                                        int nr, int64_t plane, int cw, const int *skip);
 __global__ void k_near_fused(NearArgs a, const float2 *x, float2 *y, int *err, const int *skip);
 __global__ void k_prep(PrepArgs a, const int *skip);
 // True when the product kernels of a finished GMRES cycle should skip.

