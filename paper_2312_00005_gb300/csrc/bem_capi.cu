@@ -27,9 +27,6 @@ using namespace bem;
 constexpr int kStepsPerGraph = 4;
 // values per work item of the stored near-field product
 constexpr int64_t kSpmvItemEntries = 65536;
-// dynamic shared memory of k_disaggregate: first-half directions and
-// weighted Lambda rows of every level (16 bytes per direction)
-constexpr size_t kDisaggSmem = 200 * 1024;
 
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_err;
@@ -1195,7 +1192,9 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     if (A.ntargets > 0) {
         if (A.ntgroups > 0) {
             KTimer kt_("k_transfer", sf);
-            k_transfer_split<<<dim3(A.ntgroups, nr), 32 * kTransferWarps, 0, sf>>>(P.largs.p, skip);
+            if (nr == 4) k_transfer_m4<<<A.ntgroups, 32 * kTransferWarps, 0, sf>>>(P.largs.p, skip);
+            else if (nr == 2) k_transfer_m2<<<A.ntgroups, 32 * kTransferWarps, 0, sf>>>(P.largs.p, skip);
+            else k_transfer_split<<<dim3(A.ntgroups, nr), 32 * kTransferWarps, 0, sf>>>(P.largs.p, skip);
         }
         ck_launch("k_transfer");
     }
@@ -1275,34 +1274,24 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     cudaStream_t sd = far_only ? sf : s;
     for (int l = 0; l < A.nlev; ++l) da.lev[l] = A.lev[l];
     da.tasks = P.lists->dis_tasks.p;
-    da.sum_nd = 0;
-    for (int l = 0; l < A.nlev; ++l) da.sum_nd += A.lev[l].nd;
     {
         KTimer kt_("k_disaggregate", sd);
-        const size_t smem = (size_t)std::max(2, da.sum_nd) / 2 * sizeof(float4) + (size_t)da.sum_nd * sizeof(float2);
-        if (smem > kDisaggSmem)
-            throw Fail{set_err(BEM_E_ARG, "far field: " + std::to_string(da.sum_nd) +
-                                              " directions over all levels exceed the disaggregation kernel's "
-                                              "shared-memory staging")};
         if (P.lists->n_dis_tasks > 0) {
             if (nr == 1) {
-                k_disaggregate<<<P.lists->n_dis_tasks, kDisThreads, smem, sd>>>(da, far_only ? nullptr : M.ynear.p, y,
-                                                                                skip);
+                k_disaggregate_m1<<<P.lists->n_dis_tasks, kDisThreads, 0, sd>>>(da, far_only ? nullptr : M.ynear.p, y,
+                                                                               skip);
             } else {
                 // the planes in groups of four (or two): one phase per element
                 // and direction pair serves a whole group
-                const size_t unit = (size_t)std::max(2, da.sum_nd) / 2 * sizeof(float4);
                 for (int r0 = 0; r0 < nr;) {
-                    int g = nr - r0 >= 4 ? 4 : (nr - r0 >= 2 ? 2 : 1);
-                    while (g > 1 && unit * (1 + g) > kDisaggSmem) g /= 2;
+                    const int g = nr - r0 >= 4 ? 4 : (nr - r0 >= 2 ? 2 : 1);
                     DisaggArgs dg = da;
                     for (int l = 0; l < A.nlev; ++l) dg.lev[l].Lam = A.lev[l].Lam + r0 * A.lev[l].lplane;
                     const float2 *yn = far_only ? nullptr : M.ynear.p + r0 * n;
                     float2 *yo = y + r0 * n;
-                    const size_t sm = (size_t)std::max(2, da.sum_nd) / 2 * sizeof(float4) * (1 + g);
-                    if (g == 4) k_disaggregate_m4<<<P.lists->n_dis_tasks, kDisThreads, sm, sd>>>(dg, yn, yo, skip);
-                    else if (g == 2) k_disaggregate_m2<<<P.lists->n_dis_tasks, kDisThreads, sm, sd>>>(dg, yn, yo, skip);
-                    else k_disaggregate<<<P.lists->n_dis_tasks, kDisThreads, smem, sd>>>(dg, yn, yo, skip);
+                    if (g == 4) k_disaggregate_m4<<<P.lists->n_dis_tasks, kDisThreads, 0, sd>>>(dg, yn, yo, skip);
+                    else if (g == 2) k_disaggregate_m2<<<P.lists->n_dis_tasks, kDisThreads, 0, sd>>>(dg, yn, yo, skip);
+                    else k_disaggregate_m1<<<P.lists->n_dis_tasks, kDisThreads, 0, sd>>>(dg, yn, yo, skip);
                     r0 += g;
                 }
             }
@@ -1375,18 +1364,11 @@ void matvec_t_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, con
     da.rowf = M.rowf.p;
     for (int l = 0; l < A.nlev; ++l) da.lev[l] = A.lev[l];
     da.tasks = P.lists->dis_tasks.p;
-    da.sum_nd = 0;
-    for (int l = 0; l < A.nlev; ++l) da.sum_nd += A.lev[l].nd;
     {
         KTimer kt_("k_disaggregate_t", s);
-        const size_t smem = (size_t)std::max(2, da.sum_nd) / 2 * sizeof(float4) + (size_t)da.sum_nd * sizeof(float2);
-        if (smem > kDisaggSmem)
-            throw Fail{set_err(BEM_E_ARG, "far field: " + std::to_string(da.sum_nd) +
-                                              " directions over all levels exceed the disaggregation kernel's "
-                                              "shared-memory staging")};
         if (P.lists->n_dis_tasks > 0)
-            k_disaggregate_t<<<P.lists->n_dis_tasks, kDisThreads, smem, s>>>(da, far_only ? nullptr : M.ynear.p, y,
-                                                                             skip);
+            k_disaggregate_t<<<P.lists->n_dis_tasks, kDisThreads, 0, s>>>(da, far_only ? nullptr : M.ynear.p, y,
+                                                                          skip);
     }
     ck_launch("k_disaggregate_t");
 }
@@ -1806,12 +1788,6 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         }
         M->tc_fault.alloc(1);
         ck(cudaMemsetAsync(M->tc_fault.p, 0, sizeof(int), s), "memset");
-        ck(cudaFuncSetAttribute(k_disaggregate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDisaggSmem),
-           "cudaFuncSetAttribute");
-        ck(cudaFuncSetAttribute(k_disaggregate_m2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDisaggSmem),
-           "cudaFuncSetAttribute");
-        ck(cudaFuncSetAttribute(k_disaggregate_m4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDisaggSmem),
-           "cudaFuncSetAttribute");
 
         std::vector<QuadTables> qt(1, make_tables(p));
         M->Q.upload(qt, s);

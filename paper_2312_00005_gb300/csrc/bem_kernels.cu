@@ -1033,266 +1033,185 @@ __global__ void __launch_bounds__(32 * kTransferWarps) k_transfer_split(const Le
     }
 }
 
+// The transfer for NR right-hand sides at once: the same blocks and list
+// order as k_transfer_split, each D value loaded once for all planes (the
+// M and Lambda planes are mplane and lplane apart).
+template <int NR>
+__device__ __forceinline__ void transfer_multi_body(const LevelsArgs *__restrict__ A)
+{
+    constexpr int kW = kTransferWarps, kU = 8 / NR;
+    __shared__ float2 part[NR][kW][kTransferDirs];
+    __shared__ int2 s_ent[kTransferEntries];
+    const int4 T = A->tgroups[blockIdx.x];
+    const FarArgs &f = A->lev[T.x];
+    const int t = T.y, nu0 = T.z, nd = f.nd;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nu = nu0 + lane;
+    const bool live = nu < nd;
+    const int b = f.il_ptr[t], e = f.il_ptr[t + 1];
+    float2 acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = make_float2(0.f, 0.f);
+    for (int c0 = b; c0 < e; c0 += kTransferEntries) {
+        const int cnt = min(kTransferEntries, e - c0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x)
+            s_ent[q] = make_int2(f.il_src[c0 + q], f.il_off[c0 + q]);
+        __syncthreads();
+        if (!live) continue;
+        int q = warp;
+        for (; q + kW * (kU - 1) < cnt; q += kW * kU) {
+            float2 dv[kU], mv[kU][NR];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int2 en = s_ent[q + kW * u];
+                dv[u] = __ldg(f.D + (int64_t)en.y * nd + nu);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) mv[u][r] = f.M[r * f.mplane + (int64_t)en.x * nd + nu];
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[r] = cfma(dv[u], mv[u][r], acc[r]);
+        }
+        for (; q < cnt; q += kW) {
+            const int2 en = s_ent[q];
+            const float2 dv = __ldg(f.D + (int64_t)en.y * nd + nu);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[r] = cfma(dv, f.M[r * f.mplane + (int64_t)en.x * nd + nu], acc[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) part[r][warp][lane] = acc[r];
+    __syncthreads();
+    if (warp == 0 && live) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            float2 sum = part[r][0][lane];
+#pragma unroll
+            for (int w = 1; w < kW; ++w) sum = cadd(sum, part[r][w][lane]);
+            f.Lam[r * f.lplane + (int64_t)t * nd + nu] = sum;
+        }
+    }
+}
+
+#define BEM_TRANSFER_MULTI_KERNEL(NR)                                                                               \
+    __global__ void __launch_bounds__(32 * kTransferWarps) k_transfer_m##NR(const LevelsArgs *__restrict__ A,      \
+                                                                            const int *skip)                       \
+    {                                                                                                               \
+        if (skip_now(skip)) return;                                                                                 \
+        transfer_multi_body<NR>(A);                                                                                 \
+    }
+BEM_TRANSFER_MULTI_KERNEL(2)
+BEM_TRANSFER_MULTI_KERNEL(4)
+#undef BEM_TRANSFER_MULTI_KERNEL
+
 // Disaggregation over all levels (Sec. 3.3.3, matrix S(l), with the
 // Burton-Miller row operator 1 + s.n_i) and the sum with the near field
 // (when ynear is given; else y receives the far part alone):
 //   y_i = near_i + (ik/16 pi^2) sum_l sum_nu w_nu (1 + s_nu.n_i)
-//                   e^{ik (x_i - z_t).s_nu} Lambda_t(nu).
+//                   e^{ik (x_i - z_t).s_nu} Lambda_t(nu),
+// for NR right-hand sides at once (one phase per element and direction serves
+// all of them; planes n apart in ynear and y, lplane apart in Lambda).
 // One block of kDisThreads per task (at most kDisTask elements of one leaf;
-// large leaves are split so that no block is much longer than the others):
-// the elements of a leaf share their cluster at every level, so the
-// weighted Lambda rows of the leaf's ancestors, the directions and the
-// task's element data are staged in shared memory once.  Threads take
-// antipodal direction pairs (s_p, -s_p) of all levels (one phase and its
-// conjugate), each for a chunk of kDisChunk elements held in registers;
-// every warp leaves its sum per element in shared memory without waiting
-// for the others, and after one barrier the block adds the warps' sums in
-// warp order and writes y[perm[i]] (caller order) or y[i].
-// kRowF: the row factor a_i + b_i (s.n_i) with per-element (a, b) = a.rowf[i]
-// in place of 1 + s.n_i (the transposed product: two sums per element,
-// S0 = sum (1-part) and S1 = sum (s.n-part), combined as a S0 + b S1).
-constexpr int kDisChunk = 8;
-template <bool kRowF>
+// large leaves are split so that no block is much longer than the others).
+// Element-major: thread t takes element t % cnt of the task and every nsl-th
+// antipodal direction pair (s_p, -s_p) (one phase and its conjugate; nsl =
+// kDisThreads / cnt slices).  The leaf shares its cluster at every level, so
+// the direction pairs and the weighted rows (A, B) of every plane are staged
+// in shared memory in chunks of kDisPairChunk pairs, level by level, and read
+// by all the task's elements at once; each thread keeps its element's sums in
+// registers, and the slices' sums are added in slice order.
+// kRowF (NR = 1): the row factor a_i + b_i (s.n_i) with per-element (a, b) =
+// a.rowf[i] in place of 1 + s.n_i (the transposed product: two sums per
+// element, S0 = sum (1-part) and S1 = sum (s.n-part), combined as a S0 + b S1).
+constexpr int kDisPairChunk = 256;
+template <int NR, bool kRowF>
 __device__ __forceinline__ void disaggregate_body(const DisaggArgs &a, const float2 *__restrict__ ynear,
                                                   float2 *__restrict__ y)
 {
-    extern __shared__ float4 dsm[];   // [sum_nd / 2] first-half directions, then [sum_nd / 2] (A, B) pairs
-    float4 *dir_s = dsm;
-    float4 *ab_s = dsm + a.sum_nd / 2;
-    constexpr int kNW = kDisThreads / 32;
-    __shared__ int s_lev[kMaxFarLevels], s_poff[kMaxFarLevels + 1];
-    __shared__ int s_nact;
-    __shared__ float4 dzs[kDisTask][kMaxFarLevels];   // -k/(2 pi) (z_c - x_i) per active level
-    __shared__ float4 ns[kDisTask];
-    __shared__ float2 red[kNW][kDisTask];
-    __shared__ float2 red1[kRowF ? kNW : 1][kRowF ? kDisTask : 1];
+    static_assert(!kRowF || NR == 1, "the transposed product has one right-hand side");
+    constexpr int kS = kRowF ? 2 : 1;           // sums per element and plane
+    __shared__ float4 dir_s[kDisPairChunk];
+    __shared__ float4 ab_s[NR][kDisPairChunk];
+    __shared__ float2 red[kDisThreads][NR * kS];
     const int2 tk = a.tasks[blockIdx.x];
     const int64_t e0 = tk.x, e1 = tk.y;
-    // right-hand side blockIdx.y: its Lambda planes and rows of ynear and y
-    const int64_t pl = blockIdx.y;
-    if (pl) {
-        if (ynear) ynear += pl * a.n;
-        y += pl * a.n;
-    }
-    const int cnt_all = (int)min((int64_t)kDisTask, e1 - e0);   // the host never makes larger tasks
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
-        // active levels (the leaf's cluster has an interaction list there)
-        int na = 0, poff = 0;
-        for (int l = 0; l < a.nlev; ++l) {
-            const FarArgs &f = a.lev[l];
-            const int c = f.elem_cl[e0];
-            if (f.il_ptr[c] == f.il_ptr[c + 1]) continue;
-            s_lev[na] = l;
-            s_poff[na] = poff;
-            poff += f.nd / 2;
-            ++na;
-        }
-        s_poff[na] = poff;
-        s_nact = na;
-    }
-    __syncthreads();
-    const int na = s_nact, HP = s_poff[na];
-    // per antipodal pair p of each active level: the direction s_p and, with
-    // the weighted rows lp = w Lambda(s_p), lm = w Lambda(-s_p), A = lp + lm
-    // and B = lp - lm, so that (1 + t) lp + (1 - t) lm = A + t B and
-    // (1 + t) lp - (1 - t) lm = B + t A
-    for (int u = 0; u < na; ++u) {
-        const FarArgs &f = a.lev[s_lev[u]];
-        const float2 *__restrict__ src = f.Lam + pl * f.lplane + (int64_t)f.elem_cl[e0] * f.nd;
+    const int cnt = (int)min((int64_t)kDisTask, e1 - e0);   // the host makes tasks of 1..kDisTask elements
+    if (cnt <= 0) return;
+    const int nsl = kDisThreads / cnt;
+    const int q = threadIdx.x % cnt, sl = threadIdx.x / cnt;
+    const bool act = sl < nsl;
+    const float4 n = a.nrm[e0 + q];
+    float2 acc[NR * kS];
+#pragma unroll
+    for (int r = 0; r < NR * kS; ++r) acc[r] = make_float2(0.f, 0.f);
+    for (int l = 0; l < a.nlev; ++l) {
+        const FarArgs &f = a.lev[l];
+        const int c = f.elem_cl[e0];
+        if (f.il_ptr[c] == f.il_ptr[c + 1]) continue;   // no interaction list at this level
         const int h = f.nd / 2;
-        for (int q = threadIdx.x; q < h; q += blockDim.x) {
-            const float4 d = f.dirs[q];
-            const float2 lp = cscale(src[q], d.w), lm = cscale(src[q + h], d.w);
-            dir_s[s_poff[u] + q] = make_float4(d.x, d.y, d.z, __int_as_float(u));
-            ab_s[s_poff[u] + q] = make_float4(lp.x + lm.x, lp.y + lm.y, lp.x - lm.x, lp.y - lm.y);
-        }
-    }
-    for (int v = threadIdx.x; v < cnt_all * na; v += blockDim.x) {
-        const int q = v / na, u = v % na;
-        const FarArgs &f = a.lev[s_lev[u]];
         const float kt = -f.k * 0.15915494309189535f;
-        const float4 dz = f.dz[e0 + q];              // z_c - x_i
-        dzs[q][u] = make_float4(kt * dz.x, kt * dz.y, kt * dz.z, 0.f);
-    }
-    for (int q = threadIdx.x; q < cnt_all; q += blockDim.x) ns[q] = a.nrm[e0 + q];
-    __syncthreads();
-    for (int q0 = 0; q0 < cnt_all; q0 += kDisChunk) {
-        const int cnt = min(kDisChunk, cnt_all - q0);
-        float2 acc[kDisChunk], acc1[kRowF ? kDisChunk : 1];
+        const float4 dz = f.dz[e0 + q];                  // z_c - x_i
+        const float dx = kt * dz.x, dy = kt * dz.y, dzz = kt * dz.z;
+        for (int p0 = 0; p0 < h; p0 += kDisPairChunk) {
+            const int np = min(kDisPairChunk, h - p0);
+            __syncthreads();
+            // per antipodal pair: s_p and, with lp = w Lambda(s_p), lm =
+            // w Lambda(-s_p), A = lp + lm and B = lp - lm, so that
+            // (1 + t) lp + (1 - t) lm = A + t B and (1 + t) lp - (1 - t) lm = B + t A
+            for (int i = threadIdx.x; i < np; i += blockDim.x) {
+                const float4 d = f.dirs[p0 + i];
+                dir_s[i] = d;
 #pragma unroll
-        for (int q = 0; q < kDisChunk; ++q) acc[q] = make_float2(0.f, 0.f);
+                for (int r = 0; r < NR; ++r) {
+                    const float2 *__restrict__ src = f.Lam + r * f.lplane + (int64_t)c * f.nd;
+                    const float2 lp = cscale(src[p0 + i], d.w), lm = cscale(src[p0 + i + h], d.w);
+                    ab_s[r][i] = make_float4(lp.x + lm.x, lp.y + lm.y, lp.x - lm.x, lp.y - lm.y);
+                }
+            }
+            __syncthreads();
+            if (!act) continue;
+            for (int i = sl; i < np; i += nsl) {
+                const float4 sv = dir_s[i];
+                float sn0, cs0;
+                sincos_turns(fmaf(dx, sv.x, fmaf(dy, sv.y, dzz * sv.z)), &sn0, &cs0);
+                const float tn = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
 #pragma unroll
-        for (int q = 0; q < (kRowF ? kDisChunk : 1); ++q) acc1[q] = make_float2(0.f, 0.f);
-        for (int pf = threadIdx.x; pf < HP; pf += blockDim.x) {
-            const float4 sv = dir_s[pf];
-            const int u = __float_as_int(sv.w);
-            const float4 ab = ab_s[pf];
-#pragma unroll
-            for (int q = 0; q < kDisChunk; ++q) {
-                if (q < cnt) {
-                    const float4 d = dzs[q0 + q][u], n = ns[q0 + q];
-                    float sn0, cs0;
-                    sincos_turns(fmaf(d.x, sv.x, fmaf(d.y, sv.y, d.z * sv.z)), &sn0, &cs0);
-                    const float tn = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
+                for (int r = 0; r < NR; ++r) {
+                    const float4 ab = ab_s[r][i];
                     if (kRowF) {
                         // S0 += cs A + i sn B, S1 += t (cs B + i sn A)
-                        acc[q].x = fmaf(cs0, ab.x, fmaf(-sn0, ab.w, acc[q].x));
-                        acc[q].y = fmaf(cs0, ab.y, fmaf(sn0, ab.z, acc[q].y));
-                        acc1[q].x = fmaf(tn, fmaf(cs0, ab.z, -sn0 * ab.y), acc1[q].x);
-                        acc1[q].y = fmaf(tn, fmaf(cs0, ab.w, sn0 * ab.x), acc1[q].y);
+                        acc[0].x = fmaf(cs0, ab.x, fmaf(-sn0, ab.w, acc[0].x));
+                        acc[0].y = fmaf(cs0, ab.y, fmaf(sn0, ab.z, acc[0].y));
+                        acc[kS - 1].x = fmaf(tn, fmaf(cs0, ab.z, -sn0 * ab.y), acc[kS - 1].x);
+                        acc[kS - 1].y = fmaf(tn, fmaf(cs0, ab.w, sn0 * ab.x), acc[kS - 1].y);
                     } else {
                         // (cs + i sn)(1 + t) lp + (cs - i sn)(1 - t) lm = cs sp + i sn dm
                         const float spx = fmaf(tn, ab.z, ab.x), spy = fmaf(tn, ab.w, ab.y);
                         const float dmx = fmaf(tn, ab.x, ab.z), dmy = fmaf(tn, ab.y, ab.w);
-                        acc[q].x = fmaf(cs0, spx, fmaf(-sn0, dmy, acc[q].x));
-                        acc[q].y = fmaf(cs0, spy, fmaf(sn0, dmx, acc[q].y));
+                        acc[r].x = fmaf(cs0, spx, fmaf(-sn0, dmy, acc[r].x));
+                        acc[r].y = fmaf(cs0, spy, fmaf(sn0, dmx, acc[r].y));
                     }
                 }
             }
         }
-#pragma unroll
-        for (int q = 0; q < kDisChunk; ++q) {
-            const float2 v = warp_sum(acc[q]);
-            if (lane == 0 && q < cnt) red[warp][q0 + q] = v;
-            if (kRowF) {
-                const float2 v1 = warp_sum(acc1[kRowF ? q : 0]);
-                if (lane == 0 && q < cnt) red1[kRowF ? warp : 0][kRowF ? q0 + q : 0] = v1;
-            }
-        }
     }
+#pragma unroll
+    for (int r = 0; r < NR * kS; ++r) red[threadIdx.x][r] = acc[r];
     __syncthreads();
-    if (threadIdx.x < cnt_all) {
-        const int q = threadIdx.x;
-        float2 v = red[0][q];
-#pragma unroll
-        for (int w = 1; w < kNW; ++w) v = cadd(v, red[w][q]);
-        const int64_t i = e0 + q;
+    for (int t = threadIdx.x; t < cnt * NR; t += blockDim.x) {
+        const int qq = t % cnt, r = t / cnt;
+        float2 v = red[qq][r * kS];
+        for (int w = 1; w < nsl; ++w) v = cadd(v, red[w * cnt + qq][r * kS]);
+        const int64_t i = e0 + qq;
         if (kRowF) {
-            float2 v1 = red1[0][kRowF ? q : 0];
-#pragma unroll
-            for (int w = 1; w < kNW; ++w) v1 = cadd(v1, red1[kRowF ? w : 0][kRowF ? q : 0]);
-            const float4 f = a.rowf[i];
-            v = cadd(cmul(make_float2(f.x, f.y), v), cmul(make_float2(f.z, f.w), v1));
+            float2 v1 = red[qq][kS - 1];
+            for (int w = 1; w < nsl; ++w) v1 = cadd(v1, red[w * cnt + qq][kS - 1]);
+            const float4 rf = a.rowf[i];
+            v = cadd(cmul(make_float2(rf.x, rf.y), v), cmul(make_float2(rf.z, rf.w), v1));
         }
         // (ik / 16 pi^2) v
-        const float sc = a.k * 0.00633257397764611f;   // k / (16 pi^2)
-        const float2 far = make_float2(-sc * v.y, sc * v.x);
-        const float2 out = ynear ? cadd(ynear[i], far) : far;
-        if (a.perm) y[a.perm[i]] = out;
-        else y[i] = out;
-    }
-}
-
-// The disaggregation of NR right-hand sides at once (forward row factor
-// 1 + s.n_i): the same blocks and staging as disaggregate_body, with the
-// weighted rows (A, B) of every plane in shared memory, so that one phase per
-// element and direction pair serves all planes; chunks of 8 / NR elements
-// keep the accumulators in registers.  Planes are n apart in ynear and y.
-template <int NR>
-__device__ __forceinline__ void disaggregate_multi_body(const DisaggArgs &a, const float2 *__restrict__ ynear,
-                                                        float2 *__restrict__ y)
-{
-    constexpr int kCh = kDisChunk / NR;
-    extern __shared__ float4 dsm[];   // [HP] first-half directions, then [NR][HP] (A, B) pairs
-    float4 *dir_s = dsm;
-    constexpr int kNW = kDisThreads / 32;
-    __shared__ int s_lev[kMaxFarLevels], s_poff[kMaxFarLevels + 1];
-    __shared__ int s_nact;
-    __shared__ float4 dzs[kDisTask][kMaxFarLevels];
-    __shared__ float4 ns[kDisTask];
-    __shared__ float2 red[NR][kNW][kDisTask];
-    const int2 tk = a.tasks[blockIdx.x];
-    const int64_t e0 = tk.x, e1 = tk.y;
-    const int cnt_all = (int)min((int64_t)kDisTask, e1 - e0);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
-        int na = 0, poff = 0;
-        for (int l = 0; l < a.nlev; ++l) {
-            const FarArgs &f = a.lev[l];
-            const int c = f.elem_cl[e0];
-            if (f.il_ptr[c] == f.il_ptr[c + 1]) continue;
-            s_lev[na] = l;
-            s_poff[na] = poff;
-            poff += f.nd / 2;
-            ++na;
-        }
-        s_poff[na] = poff;
-        s_nact = na;
-    }
-    __syncthreads();
-    const int na = s_nact, HP = s_poff[na];
-    float4 *ab_s = dsm + a.sum_nd / 2;   // plane r at ab_s + r * (sum_nd / 2)
-    const int abp = a.sum_nd / 2;
-    for (int u = 0; u < na; ++u) {
-        const FarArgs &f = a.lev[s_lev[u]];
-        const int h = f.nd / 2;
-        for (int q = threadIdx.x; q < h; q += blockDim.x) {
-            const float4 d = f.dirs[q];
-            dir_s[s_poff[u] + q] = make_float4(d.x, d.y, d.z, __int_as_float(u));
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const float2 *__restrict__ src = f.Lam + r * f.lplane + (int64_t)f.elem_cl[e0] * f.nd;
-                const float2 lp = cscale(src[q], d.w), lm = cscale(src[q + h], d.w);
-                ab_s[r * abp + s_poff[u] + q] = make_float4(lp.x + lm.x, lp.y + lm.y, lp.x - lm.x, lp.y - lm.y);
-            }
-        }
-    }
-    for (int v = threadIdx.x; v < cnt_all * na; v += blockDim.x) {
-        const int q = v / na, u = v % na;
-        const FarArgs &f = a.lev[s_lev[u]];
-        const float kt = -f.k * 0.15915494309189535f;
-        const float4 dz = f.dz[e0 + q];
-        dzs[q][u] = make_float4(kt * dz.x, kt * dz.y, kt * dz.z, 0.f);
-    }
-    for (int q = threadIdx.x; q < cnt_all; q += blockDim.x) ns[q] = a.nrm[e0 + q];
-    __syncthreads();
-    for (int q0 = 0; q0 < cnt_all; q0 += kCh) {
-        const int cnt = min(kCh, cnt_all - q0);
-        float2 acc[kCh][NR];
-#pragma unroll
-        for (int q = 0; q < kCh; ++q)
-#pragma unroll
-            for (int r = 0; r < NR; ++r) acc[q][r] = make_float2(0.f, 0.f);
-        for (int pf = threadIdx.x; pf < HP; pf += blockDim.x) {
-            const float4 sv = dir_s[pf];
-            const int u = __float_as_int(sv.w);
-            float4 ab[NR];
-#pragma unroll
-            for (int r = 0; r < NR; ++r) ab[r] = ab_s[r * abp + pf];
-#pragma unroll
-            for (int q = 0; q < kCh; ++q) {
-                if (q < cnt) {
-                    const float4 d = dzs[q0 + q][u], n = ns[q0 + q];
-                    float sn0, cs0;
-                    sincos_turns(fmaf(d.x, sv.x, fmaf(d.y, sv.y, d.z * sv.z)), &sn0, &cs0);
-                    const float tn = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
-#pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        // (cs + i sn)(1 + t) lp + (cs - i sn)(1 - t) lm = cs sp + i sn dm
-                        const float spx = fmaf(tn, ab[r].z, ab[r].x), spy = fmaf(tn, ab[r].w, ab[r].y);
-                        const float dmx = fmaf(tn, ab[r].x, ab[r].z), dmy = fmaf(tn, ab[r].y, ab[r].w);
-                        acc[q][r].x = fmaf(cs0, spx, fmaf(-sn0, dmy, acc[q][r].x));
-                        acc[q][r].y = fmaf(cs0, spy, fmaf(sn0, dmx, acc[q][r].y));
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < kCh; ++q)
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const float2 v = warp_sum(acc[q][r]);
-                if (lane == 0 && q < cnt) red[r][warp][q0 + q] = v;
-            }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < cnt_all * NR; t += blockDim.x) {
-        const int q = t % cnt_all, r = t / cnt_all;
-        float2 v = red[r][0][q];
-#pragma unroll
-        for (int w = 1; w < kNW; ++w) v = cadd(v, red[r][w][q]);
-        const int64_t i = e0 + q;
         const float sc = a.k * 0.00633257397764611f;   // k / (16 pi^2)
         const float2 far = make_float2(-sc * v.y, sc * v.x);
         const float2 out = ynear ? cadd(ynear[r * a.n + i], far) : far;
@@ -1301,31 +1220,25 @@ __device__ __forceinline__ void disaggregate_multi_body(const DisaggArgs &a, con
     }
 }
 
-#define BEM_DISAGG_MULTI_KERNEL(NR)                                                                                 \
+#define BEM_DISAGG_KERNEL(NR)                                                                                       \
     __global__ void __launch_bounds__(kDisThreads) k_disaggregate_m##NR(DisaggArgs a, const float2 *__restrict__ ynear, \
                                                                         float2 *__restrict__ y, const int *skip)     \
     {                                                                                                               \
         if (skip_now(skip)) return;                                                                                 \
-        disaggregate_multi_body<NR>(a, ynear, y);                                                                   \
+        disaggregate_body<NR, false>(a, ynear, y);                                                                  \
     }
-BEM_DISAGG_MULTI_KERNEL(2)
-BEM_DISAGG_MULTI_KERNEL(4)
-#undef BEM_DISAGG_MULTI_KERNEL
-
-__global__ void __launch_bounds__(kDisThreads, 16) k_disaggregate(DisaggArgs a, const float2 *__restrict__ ynear,
-                                                                  float2 *__restrict__ y, const int *skip)
-{
-    if (skip_now(skip)) return;
-    disaggregate_body<false>(a, ynear, y);
-}
+BEM_DISAGG_KERNEL(1)
+BEM_DISAGG_KERNEL(2)
+BEM_DISAGG_KERNEL(4)
+#undef BEM_DISAGG_KERNEL
 
 // The disaggregation of the transposed product: row factor a_i + b_i (s.n_i)
 // from a.rowf (see k_prep_t).
-__global__ void __launch_bounds__(kDisThreads, 16) k_disaggregate_t(DisaggArgs a, const float2 *__restrict__ ynear,
-                                                                    float2 *__restrict__ y, const int *skip)
+__global__ void __launch_bounds__(kDisThreads) k_disaggregate_t(DisaggArgs a, const float2 *__restrict__ ynear,
+                                                                float2 *__restrict__ y, const int *skip)
 {
     if (skip_now(skip)) return;
-    disaggregate_body<true>(a, ynear, y);
+    disaggregate_body<1, true>(a, ynear, y);
 }
 
 // Translation table per distinct offset X (Eq. FMMBase):

@@ -132,7 +132,6 @@ struct DisaggArgs {
     float k;
     int nlev;
     const int2 *tasks;       // element ranges [x, y) within one leaf, one per block
-    int sum_nd;              // sum of nd over the levels (shared-memory rows)
     const float4 *rowf;      // k_disaggregate_t: per-element row factor (a, b); else unused
     FarArgs lev[kMaxFarLevels];
 };
@@ -251,9 +250,14 @@ constexpr int kTransferWarps = 2;          // warps sharing one target's list
 constexpr int kTransferUnroll = 8;         // list entries per warp in flight
 constexpr int kTransferEntries = 512;     // interaction-list entries staged per pass
 __global__ void k_transfer_split(const LevelsArgs *A, const int *skip);
-__global__ void k_disaggregate(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
-// 2 or 4 right-hand sides at once (one phase per element and pair for all);
-// dynamic shared memory (sum_nd / 2) (1 + NR) float4
+// The same for 2 or 4 right-hand sides (M and Lambda planes mplane and
+// lplane apart): each D value is loaded once for all of them.
+__global__ void k_transfer_m2(const LevelsArgs *A, const int *skip);
+__global__ void k_transfer_m4(const LevelsArgs *A, const int *skip);
+// 1, 2 or 4 right-hand sides at once (one phase per element and pair for
+// all), element-major with the directions staged in chunks (no dynamic
+// shared memory)
+__global__ void k_disaggregate_m1(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
 __global__ void k_disaggregate_m2(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
 __global__ void k_disaggregate_m4(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
 __global__ void k_disaggregate_t(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);

@@ -733,6 +733,15 @@ def test_multi_rhs_product_matches_oracle(bem, nrhs):
         y1 = mesh.matvec(freq, Xt[r].contiguous(), admittance=adm, c=C, rho=RHO).cpu().numpy()
         _check(Y[r], y1, 1e-6, 5e-5, "multi-rhs product vs single, rhs %d" % r)
     mesh.close()
+    # the columns staged in chunks of 64 (many chunks per leaf, ragged last
+    # chunks) give the same products up to the order of the row sums
+    mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region, trunc_factor=6.0, near_chunk=64)
+    Yc = mesh.matvec(freq, Xt, admittance=adm, c=C, rho=RHO).cpu().numpy()
+    y0 = mesh.matvec(freq, Xt[0].contiguous(), admittance=adm, c=C, rho=RHO).cpu().numpy()
+    mesh.close()
+    for r in range(nrhs):
+        _check(Yc[r], Y[r], 1e-6, 5e-5, "near_chunk 64 vs default, rhs %d" % r)
+    _check(y0, Y[0], 1e-6, 5e-5, "near_chunk 64, one right-hand side")
 
 
 @pytest.mark.parametrize("precond", ["none", "block_jacobi"])
