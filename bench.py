@@ -651,6 +651,7 @@ def run_adjoint(args):
     if args.restart > 0:
         mkw["restart"] = args.restart
     mesh = bemfmm.Mesh(nodes, tris, bc_type=np.full(n, bemfmm.ADMI, np.int32), region=region, **mkw)
+    st = mesh.stats(f, c=c)
     stream = torch.cuda.current_stream()
     kw = dict(tol=args.tol, c=c, rho=rho)
     for _ in range(args.warmup):
@@ -674,6 +675,8 @@ def run_adjoint(args):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "dtype": "f32",
         "data": "synthetic", "all_converged": conv, "loss": L, "grad_abs_max": float(np.abs(g).max()),
         "forward_products": last[4]["iterations"],
+        "adjoint_near_part": "stored values read by column" if st["asymmetric_near_pairs"] == 0 else
+                             "recomputed by quadrature (near lists not symmetric)",
         "config": {"workload": "head_adjoint_c4", "n_elements": n, "freq_hz": f, "regions": 8,
                    "field_points": int(pts.shape[0]), "tol": args.tol, "trunc_factor": args.trunc_factor,
                    "source": "point, 1 mm off the surface at +y"},

@@ -206,6 +206,8 @@ typedef struct bem_plan_stats {
                                    pairs each, Sec. 3.3.3 T(l))                             */
     int64_t n_tgt_elements[16]; /* per used level: elements of the clusters with an
                                    interaction list (disaggregated, S(l))                   */
+    int64_t asymmetric_near_pairs; /* the part of asymmetric_pairs from near leaf pairs: 0
+                                   lets bem_matvec_transpose read the stored values      */
 } bem_plan_stats;
 
 /* Paper defaults (Sec. 3.1, Eq. FMMTruncation, Eq. Farfieldcond). */
@@ -245,8 +247,9 @@ int bem_matvec(void *mesh, double freq_hz, const bem_medium *medium, const doubl
  * bem_plan_stats.asymmetric_pairs it takes the other direction's rule (the
  * plane-wave expansion where A used quadrature of a higher order, or the
  * reverse), which agree within the quadrature tolerance and the truncation.
- * Near part: the same entries as A, recomputed by quadrature in every call
- * (not the stored ones).  Far part (FMM mode): the antipodal symmetry of the sphere grid of
+ * Near part: the same entries as A: the stored values (near_store = 1) read
+ * by column when every near leaf pair of the plan has its mirror, else
+ * recomputed by quadrature in every call.  Far part (FMM mode): the antipodal symmetry of the sphere grid of
  * Sec. 3.3.3 and D(-X, s) = D(X, -s) in Eq. FMMBase make it the forward
  * aggregation of x with the source factor 1 - s.n, the forward transfer and
  * a disaggregation with A's column factor A_j (c^q_j - ik c^p_j s.n_j) as

@@ -75,6 +75,7 @@ class PlanStats(ctypes.Structure):
         ("near_light_entries", ctypes.c_int64), ("near_light_points", ctypes.c_int64),
         ("near_heavy_entries", ctypes.c_int64), ("near_heavy_points", ctypes.c_int64),
         ("n_src_elements", ctypes.c_int64 * 16), ("n_tgt_elements", ctypes.c_int64 * 16),
+        ("asymmetric_near_pairs", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -90,6 +91,7 @@ class PlanStats(ctypes.Structure):
             "near_light_entries": self.near_light_entries, "near_light_points": self.near_light_points,
             "near_heavy_entries": self.near_heavy_entries, "near_heavy_points": self.near_heavy_points,
             "n_src_elements": list(self.n_src_elements[:n]), "n_tgt_elements": list(self.n_tgt_elements[:n]),
+            "asymmetric_near_pairs": self.asymmetric_near_pairs,
             "autotune": [(self.tuned_depth[q], self.tuned_seconds[q]) for q in range(self.n_tuned)],
         }
 

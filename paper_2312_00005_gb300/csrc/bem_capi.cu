@@ -272,6 +272,12 @@ struct Lists {
     // expensive near pairs (row, position), listed on first use
     DevArr<int2> heavy;
     int64_t n_heavy = -1;
+    // transposed near product from the stored values: per leaf t, the leaves
+    // s of its near list as (first row, rows, column of t's first element in
+    // s's rows); usable when every near pair has its mirror (tsym)
+    DevArr<int> tptr;
+    DevArr<int4> tent;
+    bool tsym = false;
     // block-Jacobi sub-blocks (first element, size, offset of the inverse)
     std::vector<int4> h_bj;
     DevArr<int4> bj;
@@ -468,16 +474,49 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
     // near columns of each leaf as runs of consecutive leaves
     std::vector<int> run_ptr(nl + 1, 0), ncol(nl, 0);
     std::vector<int2> runs;
+    std::vector<int> colpos(F.near_src.size());   // column of near entry q's first element
     for (int t = 0; t < nl; ++t) {
         int pos = 0, prev = -2;
         for (int q = F.near_ptr[t]; q < F.near_ptr[t + 1]; ++q) {
             const int sl = F.near_src[q];
             if (sl != prev + 1) runs.push_back(make_int2((int)Lf.start[sl], pos));
+            colpos[q] = pos;
             pos += (int)Lf.count[sl];
             prev = sl;
         }
         ncol[t] = pos;
         run_ptr[t + 1] = (int)runs.size();
+    }
+    {
+        // transposed near product: for leaf t and each s in its near list,
+        // the column of t's first element in s's rows (s must list t)
+        std::vector<std::pair<int64_t, int>> key;   // (s nl + listed leaf, column)
+        key.reserve(F.near_src.size());
+        for (int s2 = 0; s2 < nl; ++s2)
+            for (int q = F.near_ptr[s2]; q < F.near_ptr[s2 + 1]; ++q)
+                key.emplace_back((int64_t)s2 * nl + F.near_src[q], colpos[q]);
+        std::sort(key.begin(), key.end());
+        std::vector<int> tptr(nl + 1, 0);
+        std::vector<int4> tent;
+        bool sym = true;
+        for (int t = 0; t < nl && sym; ++t) {
+            for (int q = F.near_ptr[t]; q < F.near_ptr[t + 1]; ++q) {
+                const int sl = F.near_src[q];
+                if (Lf.count[sl] == 0 || Lf.count[t] == 0) continue;
+                const auto it = std::lower_bound(key.begin(), key.end(), std::make_pair((int64_t)sl * nl + t, INT_MIN));
+                if (it == key.end() || it->first != (int64_t)sl * nl + t) {
+                    sym = false;
+                    break;
+                }
+                tent.push_back(make_int4((int)Lf.start[sl], (int)Lf.count[sl], it->second, 0));
+            }
+            tptr[t + 1] = (int)tent.size();
+        }
+        Ls->tsym = sym;
+        if (sym) {
+            Ls->tptr.upload(tptr, s);
+            Ls->tent.upload(tent, s);
+        }
     }
     std::vector<int> leaf_of(M.n);
     std::vector<int64_t> row_ptr(M.n + 1, 0), leaf_start(nl + 1, M.n);
@@ -1305,7 +1344,9 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
 }
 
 // y = A^T x with the given column coefficients (the adjoint solve): the
-// near part by k_near_fused_t (entries recomputed), the far part by the
+// near part by k_near_spmv_t (the stored values, when they were made with
+// these coefficients and the near lists are symmetric) or k_near_fused_t
+// (entries recomputed), the far part by the
 // forward aggregation and transfer kernels on the weights k_prep_t forms
 // and k_disaggregate_t.  x: internal order, or null when x_int already
 // holds x (formed by k_gs_finish).  y: caller order when perm_out, else
@@ -1345,12 +1386,25 @@ void matvec_t_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, con
         }
         ck_launch("k_transfer");
     }
-    NearArgs na = near_args(M, P, cp, cq);
-    {
-        KTimer kt_("k_near_fused_t", s);
-        k_near_fused_t<<<nblocks(n, 8), 256, 0, s>>>(na, M.xint.p, M.ynear.p, nullptr, fr(M).err.p, skip);
+    const Lists &Ls = *P.lists;
+    if (cp == fr(M).cp.p && cq == fr(M).cq.p && P.val_valid && M.prm.near_store && !P.fp().direct && Ls.tsym) {
+        // the stored values of A (made with these coefficients), read by column
+        {
+            KTimer kt_("k_near_spmv_t", s);
+            const int nl = (int)Ls.fp.near_ptr.size() - 1;
+            if (nl > 0)
+                k_near_spmv_t<<<nl, kSpmvTThreads, 0, s>>>(Ls.leaf_start.p, Ls.row_ptr.p, Ls.tptr.p, Ls.tent.p,
+                                                            P.val.p, M.xint.p, M.ynear.p, skip);
+        }
+        ck_launch("k_near_spmv_t");
+    } else {
+        NearArgs na = near_args(M, P, cp, cq);
+        {
+            KTimer kt_("k_near_fused_t", s);
+            k_near_fused_t<<<nblocks(n, 8), 256, 0, s>>>(na, M.xint.p, M.ynear.p, nullptr, fr(M).err.p, skip);
+        }
+        ck_launch("k_near_fused_t");
     }
-    ck_launch("k_near_fused_t");
     if (fork) {
         ck(cudaEventRecord(M.ev_join, sf), "record join");
         ck(cudaStreamWaitEvent(s, M.ev_join, 0), "wait join");
@@ -1591,6 +1645,7 @@ void fill_stats(const Geometry &g, const Tree &t, const FreqPlan &fp, const bem_
             for (int q = fp.near_ptr[a]; q < fp.near_ptr[a + 1]; ++q) keys.push_back(a * nl + fp.near_src[q]);
         if (nl > 0) count_asym(keys, nl, t.lv[fp.leaf_depth].count);
     }
+    out->asymmetric_near_pairs = asym;
     for (const FarLevel &F : fp.far) {
         std::vector<int64_t> keys;
         for (int c = 0; c < F.nc; ++c)

@@ -392,6 +392,60 @@ __global__ void __launch_bounds__(kSpmvThreads) k_near_spmv_items(NearArgs a, co
     }
 }
 
+// Transposed near-field product from the stored values (the near relation
+// of the leaves being symmetric): for the elements j of leaf t = blockIdx.x,
+//   y_j = sum_{s in near(t)} sum_{i in s} A_ij x_i,
+// where A_ij sits in row i's stored values at the column of t's first
+// element in s's near list plus (j - first element of t).  Lanes take 32
+// consecutive j (one coalesced segment of a row), warps take rows; the warps'
+// sums are added in warp order.
+__global__ void __launch_bounds__(kSpmvTThreads) k_near_spmv_t(const int64_t *__restrict__ leaf_start,
+                                                               const int64_t *__restrict__ row_ptr,
+                                                               const int *__restrict__ tptr,
+                                                               const int4 *__restrict__ tent,
+                                                               const float2 *__restrict__ val,
+                                                               const float2 *__restrict__ x, float2 *__restrict__ y,
+                                                               const int *skip)
+{
+    if (skip_now(skip)) return;
+    constexpr int kW = kSpmvTThreads / 32;
+    __shared__ float2 part[kW][32];
+    const int t = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t j0 = leaf_start[t];
+    const int cnt = (int)(leaf_start[t + 1] - j0);
+    const int e0 = tptr[t], e1 = tptr[t + 1];
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+        const bool live = c0 + lane < cnt;
+        float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+        for (int e = e0; e < e1; ++e) {
+            const int4 en = tent[e];   // (first row, rows, column of t's first element)
+            int r = warp;
+            for (; r + kW < en.y; r += 2 * kW) {
+                const int64_t i = en.x + r, i2 = i + kW;
+                const float2 xa = x[i], xb = x[i2];
+                if (live) {
+                    acc0 = cfma(__ldcs(val + row_ptr[i] + en.z + c0 + lane), xa, acc0);
+                    acc1 = cfma(__ldcs(val + row_ptr[i2] + en.z + c0 + lane), xb, acc1);
+                }
+            }
+            if (r < en.y && live) {
+                const int64_t i = en.x + r;
+                acc0 = cfma(__ldcs(val + row_ptr[i] + en.z + c0 + lane), x[i], acc0);
+            }
+        }
+        part[warp][lane] = cadd(acc0, acc1);
+        __syncthreads();
+        if (warp == 0 && live) {
+            float2 sum = part[0][lane];
+#pragma unroll
+            for (int w = 1; w < kW; ++w) sum = cadd(sum, part[w][lane]);
+            y[j0 + c0 + lane] = sum;
+        }
+        __syncthreads();
+    }
+}
+
 // sum_{c0 <= c < c1} v[c] xs_r[c] for the planes r < nr of xs (ncp floats2
 // apart), as spmv_segment for one plane: each 16-byte load of v serves all
 // planes.

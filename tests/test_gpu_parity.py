@@ -445,6 +445,47 @@ def test_transposed_product_matches_oracle(bem, mode):
         _check(yt, yo, l2, el, "transposed fmm product, factor %g" % tf)
 
 
+def test_transposed_product_from_stored_values(bem):
+    """With symmetric far verdicts every near leaf pair has its mirror, so
+    bem_matvec_transpose reads the stored values of A by column
+    (k_near_spmv_t) instead of recomputing them: equal to the recomputed
+    transposed product (near_store = 0) up to rounding order, within the
+    truncation of the oracle's A^T x, and the exact transpose of bem_matvec
+    (z.(A^T x) = x.(A z) to FP32 rounding).  5120 elements, 2 kHz, mixed
+    boundary conditions, three far levels."""
+    nodes, tris = inputs.icosphere(4, 0.1)
+    n = tris.shape[0]
+    freq = 2000.0
+    k = 2 * np.pi * freq / C
+    bct, region, adm = _mixed_bc(n, 7)
+    x, z = inputs.random_complex(n, 23), inputs.random_complex(n, 24)
+    cp, cq = _oracle_coeffs(bct, region, adm, k)
+    yo = oracle.assemble(nodes, tris, k, cp, cq).T @ x
+    xt = torch.tensor(x, dtype=torch.complex64, device="cuda")
+    zt = torch.tensor(z, dtype=torch.complex64, device="cuda")
+    kw = dict(bc_type=bct, region=region, trunc_factor=6.0, symmetric_far=1)
+    mesh = bem.Mesh(nodes, tris, **kw)
+    st = mesh.stats(freq, c=C)
+    assert st["levels"] >= 2 and st["asymmetric_pairs"] == 0 and st["asymmetric_near_pairs"] == 0, st
+    az = mesh.matvec(freq, zt, admittance=adm, c=C, rho=RHO).cpu().numpy()
+    bem.timing_enable(True)
+    try:
+        before = bem.timing_get("k_near_spmv_t")[1]
+        y1 = mesh.matvec_transpose(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy()
+        assert bem.timing_get("k_near_spmv_t")[1] == before + 1
+    finally:
+        bem.timing_enable(False)
+    mesh.close()
+    mesh = bem.Mesh(nodes, tris, near_store=0, **kw)
+    y0 = mesh.matvec_transpose(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy()
+    mesh.close()
+    _check(y1, y0, 1e-6, 5e-5, "transposed product, stored vs recomputed near part")
+    _check(y1, yo, 1e-4, 1e-3, "transposed product from stored values vs oracle")
+    lhs, rhs = np.dot(z, y1), np.dot(x, az)
+    print("z.(A^T x) %s, x.(A z) %s" % (lhs, rhs))
+    assert abs(lhs - rhs) < 1e-5 * np.linalg.norm(z) * np.linalg.norm(y1)
+
+
 def test_admittance_gradient_fmm_matches_oracle(bem):
     """The adjoint gradient through the FMM (5120 elements, 2 kHz, eight
     octant regions, truncation factor 6) against the oracle's dense adjoint:

@@ -199,6 +199,7 @@ def test_symmetric_far_test_gives_mirrored_lists(lib, mesh, freq):
     a = bemfmm.plan_stats_host(nodes, tris, freq)
     b = bemfmm.plan_stats_host(nodes, tris, freq, params=bemfmm.default_params(symmetric_far=1))
     assert a["asymmetric_pairs"] > 0 and b["asymmetric_pairs"] == 0
+    assert 0 <= a["asymmetric_near_pairs"] <= a["asymmetric_pairs"] and b["asymmetric_near_pairs"] == 0
     assert b["near_nnz"] + b["far_pairs"] == n * n
     assert a["near_nnz"] <= b["near_nnz"] <= 1.5 * a["near_nnz"], (a["near_nnz"], b["near_nnz"])
 
