@@ -134,6 +134,15 @@ typedef struct bem_params {
                                several); an even number in 64..4096: that many for any
                                number of right-hand sides.  Results agree to rounding order
                                of the row sums.  Other values: BEM_E_ARG.                     */
+    int32_t field_mode;     /* bem_evaluate: 1 the direct sum over every element with the rules
+                               of Sec. 3.1 at each point; 2 (FMM meshes) near elements by the
+                               same rules and the rest through the plane-wave expansions of
+                               Sec. 3.3 (the points clustered on the element tree's grid, the
+                               far test of the lists with the points as targets, the
+                               one-point rule beyond R_1; the point plan is kept for the next
+                               call with the same points and frequency); 0 (default): 2 on an
+                               FMM mesh from 1e9 point-element pairs, else 1.  Other values:
+                               BEM_E_ARG.                                                      */
 } bem_params;
 
 typedef struct bem_medium {
@@ -384,6 +393,26 @@ int bem_mesh_stats(void *mesh, double freq_hz, const bem_medium *medium, bem_pla
  * the plan's octree, each split into runs of at most 64 elements of its
  * Morton-ordered element list.  Builds the plan if needed. */
 int bem_mesh_blocks(void *mesh, double freq_hz, const bem_medium *medium, int32_t *block_of);
+
+/* The field-point plan of bem_evaluate's FMM path (field_mode 2), computed on
+ * the host only (no CUDA call) with the tree of bem_plan_stats_host: pts is
+ * host double [n_pts][3] in metres. */
+typedef struct bem_field_stats {
+    int32_t leaf_level;          /* depth of the point leaves                           */
+    int32_t levels;              /* depths with point-cluster interactions               */
+    int32_t level_depth[16];
+    int32_t L[16];               /* expansion length per level (Eq. FMMTruncation)       */
+    int32_t n_point_clusters[16];
+    int64_t n_interactions[16];  /* (point cluster, element cluster) list entries        */
+    int32_t n_offsets[16];       /* distinct translation vectors                         */
+    int64_t near_pairs;          /* point-element pairs summed by the element rules ...  */
+    int64_t far_pairs;           /* ... and through the expansions: together
+                                    n_pts x n_tris                                       */
+    int64_t n_point_leaves;
+} bem_field_stats;
+int bem_field_plan_stats_host(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tris,
+                              const double *pts, int64_t n_pts, const bem_params *params, double freq_hz,
+                              double c, bem_field_stats *out);
 
 /* The same statistics computed on the host only (no CUDA call): geometry,
  * clustering and the near / interaction lists of Sec. 3.3.4 for the given

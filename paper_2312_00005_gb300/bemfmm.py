@@ -43,6 +43,7 @@ class Params(ctypes.Structure):
         ("autotune", ctypes.c_int32), ("tau", ctypes.c_double), ("row_scaling", ctypes.c_int32),
         ("check_orientation", ctypes.c_int32), ("symmetric_far", ctypes.c_int32),
         ("block_jacobi", ctypes.c_int32), ("far_precision", ctypes.c_int32), ("near_chunk", ctypes.c_int32),
+        ("field_mode", ctypes.c_int32),
     ]
 
 
@@ -131,6 +132,8 @@ def lib():
             "bem_mesh_stats": (ctypes.c_int, [P, d, ctypes.POINTER(Medium), ctypes.POINTER(PlanStats)]),
             "bem_mesh_check_host": (ctypes.c_int, [P, i64, P, i64, ctypes.POINTER(d), ctypes.POINTER(i64),
                                                    ctypes.POINTER(i64)]),
+            "bem_field_plan_stats_host": (ctypes.c_int, [P, i64, P, i64, P, i64, ctypes.POINTER(Params), d, d,
+                                                         ctypes.POINTER(FieldStats)]),
             "bem_plan_stats_host": (ctypes.c_int, [P, i64, P, i64, ctypes.POINTER(Params), d, d,
                                                    ctypes.POINTER(PlanStats)]),
             "bem_mesh_release_plan": (ctypes.c_int, [P]),
@@ -300,6 +303,37 @@ def plan_stats_host(nodes, tris, freq, c=343.0, params=None) -> dict:
     _check(lib().bem_plan_stats_host(nodes.ctypes.data_as(ctypes.c_void_p), nodes.shape[0],
                                      tris.ctypes.data_as(ctypes.c_void_p), tris.shape[0], ctypes.byref(p),
                                      float(freq), float(c), ctypes.byref(st)))
+    return st.as_dict()
+
+
+class FieldStats(ctypes.Structure):
+    _fields_ = [
+        ("leaf_level", ctypes.c_int32), ("levels", ctypes.c_int32), ("level_depth", ctypes.c_int32 * 16),
+        ("L", ctypes.c_int32 * 16), ("n_point_clusters", ctypes.c_int32 * 16),
+        ("n_interactions", ctypes.c_int64 * 16), ("n_offsets", ctypes.c_int32 * 16),
+        ("near_pairs", ctypes.c_int64), ("far_pairs", ctypes.c_int64), ("n_point_leaves", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        n = self.levels
+        return {"leaf_level": self.leaf_level, "levels": n, "level_depth": list(self.level_depth[:n]),
+                "L": list(self.L[:n]), "n_point_clusters": list(self.n_point_clusters[:n]),
+                "n_interactions": list(self.n_interactions[:n]), "n_offsets": list(self.n_offsets[:n]),
+                "near_pairs": self.near_pairs, "far_pairs": self.far_pairs, "n_point_leaves": self.n_point_leaves}
+
+
+def field_plan_stats_host(nodes, tris, points, freq, c=343.0, params=None) -> dict:
+    """The field-point plan of the FMM evaluation path, built on the host
+    only (no GPU needed)."""
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    p = params if params is not None else default_params()
+    st = FieldStats()
+    _check(lib().bem_field_plan_stats_host(nodes.ctypes.data_as(ctypes.c_void_p), nodes.shape[0],
+                                           tris.ctypes.data_as(ctypes.c_void_p), tris.shape[0],
+                                           pts.ctypes.data_as(ctypes.c_void_p), pts.shape[0], ctypes.byref(p),
+                                           float(freq), float(c), ctypes.byref(st)))
     return st.as_dict()
 
 

@@ -23,6 +23,10 @@
 
 using namespace bem;
 
+// bem_evaluate with field_mode 0 takes the FMM path from this many
+// point-element pairs (below it the direct sum takes about as long as the
+// host build of the point plan)
+constexpr double kFieldFmmMinPairs = 1e9;
 // Arnoldi steps captured in one CUDA graph (one status read per graph)
 constexpr int kStepsPerGraph = 4;
 // values per work item of the stored near-field product
@@ -360,6 +364,40 @@ struct Frame {
     bool known_nonzero = false;
 };
 
+// Device data of the FMM field evaluation at points (one call's plan).
+struct EvalLevelDev {
+    int L = 0, nd = 0, noff = 0, npc = 0, nc = 0, nextra = 0;
+    DevArr<int> il_ptr, il_src, il_off, pcl, red_ptr, red_c;
+    DevArr<double> offs, dirs_d;
+    DevArr<float4> dirs, dzp;
+    DevArr<float2> D, Mx, Lam;
+};
+struct EvalDev {
+    // the plan below serves calls with the same points, wavenumber, tree depth
+    // and expansion parameters (key), so repeated evaluations skip the host
+    // build, the uploads and the translation tables
+    bool valid = false;
+    std::vector<double> key_pts;
+    double key_k = 0.0, key_trunc = 0.0;
+    int key_depth = -1;
+    int64_t np = 0;
+    int npl = 0, n_dtasks = 0;
+    bool far = false;
+    LevelsArgs A;
+    DisaggArgs da;
+    std::vector<std::unique_ptr<EvalLevelDev>> lev;
+    DevArr<AggTask> tasks;
+    DevArr<int2> reds, dtasks, nruns;
+    DevArr<unsigned int> red_cnt;
+    DevArr<int4> tgroups;
+    DevArr<LevelsArgs> largs;
+    DevArr<int> pleaf, nptr;
+    DevArr<double> pts;
+    DevArr<int64_t> perm;
+    DevArr<float4> wts, zeros;
+    DevArr<float2> vnear, vall;
+};
+
 struct bem_mesh_impl {
     int device = 0;
     bem_params prm;
@@ -409,6 +447,7 @@ struct bem_mesh_impl {
     std::vector<std::unique_ptr<DevArr<float2>>> spare_bufs;
     DevArr<SourceDev> srcbuf;
     DevArr<float2> fieldpart;     // per-point partial sums of the field (point-major)
+    std::unique_ptr<EvalDev> eval;  // FMM field evaluation
     DevArr<double> ptsbuf;
     std::map<int, std::unique_ptr<DepthDev>> depth_dev;
     std::map<int, double> growth_root;                 // x*(L) of the Hankel stability test
@@ -1693,6 +1732,7 @@ void bem_params_default(bem_params *p)
     p->block_jacobi = 0;
     p->far_precision = 0;
     p->near_chunk = 0;
+    p->field_mode = 0;
 }
 
 const char *bem_last_error(void) { return g_err.c_str(); }
@@ -1722,6 +1762,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
     if (p.far_precision != 0 && p.far_precision != 1) return set_err(BEM_E_ARG, "far_precision must be 0 or 1");
     if (p.near_chunk != 0 && (p.near_chunk < 64 || p.near_chunk > 4096 || (p.near_chunk & 1)))
         return set_err(BEM_E_ARG, "near_chunk must be 0 or an even number in 64..4096");
+    if (p.field_mode < 0 || p.field_mode > 2) return set_err(BEM_E_ARG, "field_mode must be 0, 1 or 2");
     if (p.block_jacobi && p.row_scaling)
         return set_err(BEM_E_ARG, "row_scaling and block_jacobi are alternatives: set at most one");
     if (!(p.quad_tol > 0) || !(p.rt_subdiv > 0) || !(p.admissibility > 0) || p.L_min < 1 || p.L_min > 200)
@@ -2704,6 +2745,278 @@ int bem_solve_sweep(void *mesh, const double *freqs_hz, int32_t n_freq, const be
     }
 }
 
+// The field at points through the plane-wave expansions (build_eval_plan):
+// near pairs by the element rules of k_field over the point leaves' near
+// lists; far pairs by an aggregation of the weights (-A q, -ik A p) at every
+// level the plan uses, translation tables for the point-cluster offsets, the
+// transfer onto the point clusters and the disaggregation onto the points
+// (no normal factor).  p, q: internal element order; out: caller point order.
+void field_fmm_plan(bem_mesh_impl &M, double k, const double *pts, int64_t np, cudaStream_t s)
+{
+    if (!M.eval) M.eval = std::make_unique<EvalDev>();
+    EvalDev &V = *M.eval;
+    if (V.valid && V.np == np && V.key_k == k && V.key_depth == M.leaf_depth && V.key_trunc == M.prm.trunc_factor &&
+        std::equal(pts, pts + 3 * np, V.key_pts.begin()))
+        return;
+    V.valid = false;
+    EvalPlan ep;
+    const std::string msg = build_eval_plan(M.g, M.t, M.prm, k, M.leaf_depth, pts, np, kMaxTableL, ep);
+    if (!msg.empty()) throw Fail{set_err(BEM_E_ARG, msg)};
+    if ((int)ep.far.size() > kMaxFarLevels)
+        throw Fail{set_err(BEM_E_ARG, "field evaluation: more far levels than the kernels take")};
+    // the points in internal order, their leaf clusters and near element runs
+    std::vector<double> hp(3 * (size_t)np);
+    for (int64_t i = 0; i < np; ++i)
+        for (int a = 0; a < 3; ++a) hp[3 * i + a] = pts[3 * ep.perm[i] + a];
+    V.pts.upload(hp, s);
+    V.perm.upload(ep.perm, s);
+    const int npl = (int)ep.leaf_start.size() - 1;
+    std::vector<int> pleaf((size_t)np);
+    for (int c = 0; c < npl; ++c)
+        for (int64_t i = ep.leaf_start[c]; i < ep.leaf_start[c + 1]; ++i) pleaf[i] = c;
+    V.pleaf.upload(pleaf, s);
+    const Level &EL = M.t.lv[ep.leaf_depth];
+    std::vector<int> nptr(npl + 1, 0);
+    std::vector<int2> nruns;
+    for (int c = 0; c < npl; ++c) {
+        int prev = -2;
+        for (int q2 = ep.near_ptr[c]; q2 < ep.near_ptr[c + 1]; ++q2) {
+            const int sl = ep.near_src[q2];
+            if (EL.count[sl] == 0) continue;
+            if (sl == prev + 1) nruns.back().y += (int)EL.count[sl];   // consecutive leaves: one run
+            else nruns.push_back(make_int2((int)EL.start[sl], (int)EL.count[sl]));
+            prev = sl;
+        }
+        nptr[c + 1] = (int)nruns.size();
+    }
+    V.nptr.upload(nptr, s);
+    V.nruns.upload(nruns, s);
+    V.vnear.alloc(np);
+    V.vall.alloc(np);
+    V.np = np;
+    V.npl = npl;
+    V.far = !ep.far.empty();
+    V.n_dtasks = 0;
+    if (V.far) {
+        while (V.lev.size() < ep.far.size()) V.lev.push_back(std::make_unique<EvalLevelDev>());
+        std::vector<AggTask> tasks;
+        std::vector<int2> reds;
+        std::vector<int4> tg;
+        DTableArgs ta;
+        memset(&ta, 0, sizeof ta);
+        ta.k = k;
+        int nb = 0;
+        LevelsArgs &A = V.A;
+        memset(&A, 0, sizeof A);
+        DisaggArgs &da = V.da;
+        memset(&da, 0, sizeof da);
+        for (size_t l = 0; l < ep.far.size(); ++l) {
+            const EvalLevel &F = ep.far[l];
+            EvalLevelDev &Ld = *V.lev[l];
+            const Level &E = M.t.lv[F.depth];
+            Ld.L = F.L;
+            Ld.nd = 2 * F.L * F.L;
+            Ld.noff = (int)(F.offsets.size() / 3);
+            Ld.npc = F.npc;
+            Ld.nc = (int)E.start.size();
+            const int nd = Ld.nd;
+            std::vector<double> sd, sw;
+            sphere_grid(F.L, sd, sw);
+            std::vector<float4> dirs(nd);
+            for (int q2 = 0; q2 < nd; ++q2)
+                dirs[q2] = make_float4((float)sd[3 * q2], (float)sd[3 * q2 + 1], (float)sd[3 * q2 + 2], (float)sw[q2]);
+            Ld.dirs.upload(dirs, s);
+            Ld.dirs_d.upload(sd, s);
+            Ld.il_ptr.upload(F.il_ptr, s);
+            Ld.il_src.upload(F.il_src, s);
+            Ld.il_off.upload(F.il_off, s);
+            Ld.offs.upload(F.offsets, s);
+            Ld.pcl.upload(F.pcl, s);
+            std::vector<float4> dzp((size_t)np);
+            for (int64_t i = 0; i < np; ++i) {
+                const int c = F.pcl[i];
+                dzp[i] = make_float4((float)(F.zp[3 * c] - hp[3 * i]), (float)(F.zp[3 * c + 1] - hp[3 * i + 1]),
+                                     (float)(F.zp[3 * c + 2] - hp[3 * i + 2]), 0.f);
+            }
+            Ld.dzp.upload(dzp, s);
+            // aggregation tasks over this level's source clusters: element
+            // chunks of at most kAggChunk (split clusters summed by the last
+            // block) times ranges of kAggThreads direction pairs
+            std::vector<char> is_src(Ld.nc, 0);
+            for (int v : F.il_src) is_src[v] = 1;
+            std::vector<int> red_ptr{Ld.nc}, red_c;
+            int extra = 0;
+            for (int c = 0; c < Ld.nc; ++c) {
+                if (!is_src[c]) continue;
+                const int64_t cnt = E.count[c];
+                const int64_t nch = std::max<int64_t>(1, (cnt + kAggChunk - 1) / kAggChunk);
+                if (nch == 1) {
+                    for (int p0 = 0; p0 < nd / 2; p0 += kAggThreads)
+                        tasks.push_back(AggTask{c, c, E.start[c], (int)cnt, (int)l, -1, -1, p0});
+                    continue;
+                }
+                const int red = (int)red_c.size();
+                const int gred = (int)reds.size() + red;
+                for (int64_t q2 = 0; q2 < nch; ++q2) {
+                    const int64_t a = cnt * q2 / nch, b = cnt * (q2 + 1) / nch;
+                    for (int p0 = 0; p0 < nd / 2; p0 += kAggThreads)
+                        tasks.push_back(AggTask{c, Ld.nc + extra, E.start[c] + a, (int)(b - a), (int)l, red, gred, p0});
+                    ++extra;
+                }
+                red_c.push_back(c);
+                red_ptr.push_back(Ld.nc + extra);
+            }
+            for (size_t q2 = 0; q2 < red_c.size(); ++q2) reds.push_back(make_int2((int)l, (int)q2));
+            Ld.nextra = extra;
+            Ld.red_ptr.upload(red_ptr, s);
+            Ld.red_c.upload(red_c, s);
+            Ld.Mx.alloc((size_t)(Ld.nc + extra) * nd);
+            Ld.Lam.alloc((size_t)Ld.npc * nd);
+            Ld.D.alloc((size_t)Ld.noff * nd);
+            if (Ld.noff > 0) {
+                ta.start[ta.nlev] = nb;
+                ta.lev[ta.nlev] = DTableLevel{Ld.offs.p, Ld.dirs_d.p, Ld.D.p, nd, F.L};
+                nb += Ld.noff;
+                ++ta.nlev;
+            }
+            for (int c = 0; c < F.npc; ++c)
+                if (F.il_ptr[c + 1] > F.il_ptr[c])
+                    for (int nu0 = 0; nu0 < nd; nu0 += kTransferDirs) tg.push_back(make_int4((int)l, c, nu0, 0));
+            const DepthDev *dd = depth_data(M, F.depth);
+            FarArgs f;
+            memset(&f, 0, sizeof f);
+            f.nd = nd;
+            f.k = (float)k;
+            f.red_ptr = Ld.red_ptr.p;
+            f.red_c = Ld.red_c.p;
+            f.nred = (int)red_c.size();
+            f.dirs = Ld.dirs.p;
+            f.il_ptr = Ld.il_ptr.p;
+            f.il_src = Ld.il_src.p;
+            f.il_off = Ld.il_off.p;
+            f.D = Ld.D.p;
+            f.M = Ld.Mx.p;
+            f.Lam = Ld.Lam.p;
+            f.cstart = dd->cstart.p;
+            f.dz = dd->dz.p;
+            f.elem_cl = dd->elem_cl.p;
+            f.mplane = (int64_t)(Ld.nc + extra) * nd;
+            f.lplane = (int64_t)Ld.npc * nd;
+            A.lev[l] = f;
+            // the disaggregation sees the points: their clusters and z_P - x_m
+            f.dz = Ld.dzp.p;
+            f.elem_cl = Ld.pcl.p;
+            da.lev[l] = f;
+        }
+        ta.start[ta.nlev] = nb;
+        A.nlev = (int)ep.far.size();
+        V.tasks.upload(tasks, s);
+        A.tasks = V.tasks.p;
+        A.ntasks = (int)tasks.size();
+        V.reds.upload(reds, s);
+        A.reds = V.reds.p;
+        A.nreds = (int)reds.size();
+        V.red_cnt.alloc(std::max<size_t>(1, reds.size()));
+        ck(cudaMemsetAsync(V.red_cnt.p, 0, std::max<size_t>(1, reds.size()) * sizeof(unsigned int), s), "memset");
+        A.red_cnt = V.red_cnt.p;
+        V.tgroups.upload(tg, s);
+        A.tgroups = V.tgroups.p;
+        A.ntgroups = (int)tg.size();
+        std::vector<LevelsArgs> hv(1, A);
+        V.largs.upload(hv, s);
+        if (nb > 0) {
+            {
+                KTimer kt_("k_dtable", s);
+                k_dtable<<<nb, 128, 0, s>>>(ta);
+            }
+            ck_launch("k_dtable");
+        }
+        // disaggregation onto the points: tasks of at most kDisTask points of
+        // one point leaf (zero normals: no row factor)
+        std::vector<int2> dt;
+        for (int c = 0; c < npl; ++c) {
+            const int64_t a = ep.leaf_start[c], cnt = ep.leaf_start[c + 1] - a;
+            const int64_t nch = (cnt + kDisTask - 1) / kDisTask;
+            for (int64_t q2 = 0; q2 < nch; ++q2)
+                dt.push_back(make_int2((int)(a + cnt * q2 / nch), (int)(a + cnt * (q2 + 1) / nch)));
+        }
+        V.dtasks.upload(dt, s);
+        V.n_dtasks = (int)dt.size();
+        V.zeros.alloc(np);
+        ck(cudaMemsetAsync(V.zeros.p, 0, np * sizeof(float4), s), "memset");
+        da.n = np;
+        da.nrm = V.zeros.p;
+        da.perm = nullptr;
+        da.k = (float)k;
+        da.nlev = A.nlev;
+        da.tasks = V.dtasks.p;
+        da.rowf = nullptr;
+    }
+    ck(cudaStreamSynchronize(s), "sync");   // the host vectors above are uploaded before they go
+    V.key_pts.assign(pts, pts + 3 * np);
+    V.key_k = k;
+    V.key_depth = M.leaf_depth;
+    V.key_trunc = M.prm.trunc_factor;
+    V.valid = true;
+}
+
+// The field at points through the plane-wave expansions (build_eval_plan):
+// near pairs by the element rules of k_field over the point leaves' near
+// lists; far pairs by an aggregation of the weights (-A q, -ik A p) at every
+// level the plan uses, translation tables for the point-cluster offsets, the
+// transfer onto the point clusters and the disaggregation onto the points
+// (no normal factor).  p, q: internal element order; out: caller point order.
+void field_fmm(bem_mesh_impl &M, double k, const double *pts, int64_t np, const float2 *p, const float2 *q,
+               const SourceDev *src, int nsrc, float2 *out, cudaStream_t s)
+{
+    field_fmm_plan(M, k, pts, np, s);
+    EvalDev &V = *M.eval;
+    const int64_t n = M.n;
+    {
+        KTimer kt_("k_field_near", s);
+        k_field_near<<<nblocks(np, 8), 256, 0, s>>>(M.elem(), M.Q.p, V.pts.p, np, (float)k, p, q, V.pleaf.p,
+                                                   V.nptr.p, V.nruns.p, V.vnear.p, fr(M).err.p);
+    }
+    ck_launch("k_field_near");
+    const float2 *vres = V.vnear.p;
+    if (V.far) {
+        V.wts.alloc(n);
+        {
+            KTimer kt_("k_field_weights", s);
+            k_field_weights<<<nblocks(n, 256), 256, 0, s>>>(n, p, q, M.chi.p, (float)k, V.wts.p);
+        }
+        ck_launch("k_field_weights");
+        if (V.A.ntasks > 0) {
+            {
+                KTimer kt_("k_aggregate", s);
+                k_aggregate_1<<<V.A.ntasks, kAggThreads, 0, s>>>(V.largs.p, V.wts.p, n, M.nrm.p, nullptr);
+            }
+            ck_launch("k_aggregate");
+        }
+        if (V.A.ntgroups > 0) {
+            {
+                KTimer kt_("k_transfer", s);
+                k_transfer_split<<<V.A.ntgroups, 32 * kTransferWarps, 0, s>>>(V.largs.p, nullptr);
+            }
+            ck_launch("k_transfer");
+        }
+        if (V.n_dtasks > 0) {
+            {
+                KTimer kt_("k_disaggregate", s);
+                k_disaggregate_m1<<<(unsigned)V.n_dtasks, kDisThreads, 0, s>>>(V.da, V.vnear.p, V.vall.p, nullptr);
+            }
+            ck_launch("k_disaggregate");
+        }
+        vres = V.vall.p;
+    }
+    {
+        KTimer kt_("k_field_eval_finish", s);
+        k_field_eval_finish<<<nblocks(np, 128), 128, 0, s>>>(V.pts.p, np, (float)k, (float)M.prm.tau, src, nsrc, vres,
+                                                             V.perm.p, out);
+    }
+    ck_launch("k_field_eval_finish");
+}
+
 int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem_source *srcs, int32_t n_src,
                  const void *p_dev, const void *q_dev, const double *pts, int64_t M_pts, void *out_dev,
                  void *stream)
@@ -2740,6 +3053,14 @@ int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem
         sdev.upload(sv, s);
         reset_err(M);
         const double k = wavenumber(freq_hz, c);
+        if (M.prm.mode == BEM_MODE_FMM &&
+            (M.prm.field_mode == 2 || (M.prm.field_mode == 0 && (double)M_pts * (double)n >= kFieldFmmMinPairs))) {
+            field_fmm(M, k, pts, M_pts, M.tmp.p, M.tmp2.p, sdev.p, n_src, (float2 *)out_dev, s);
+            check_err(M);
+            join_streams(s, us);
+            resolve_timing();
+            return BEM_OK;
+        }
         // each point's element sum split over S blocks when the points alone
         // would leave SMs idle (partials added in slice order)
         int nsm = 0;
@@ -3032,6 +3353,46 @@ int bem_plan_stats_host(const double *nodes, int64_t n_nodes, const int32_t *tri
         FreqPlan fp;
         build_plan(g, t, p, wavenumber(freq_hz, c > 0 ? c : 343.0), fp);
         fill_stats(g, t, fp, p, out);
+        return BEM_OK;
+    } catch (std::bad_alloc &) {
+        return set_err(BEM_E_OOM, "host allocation failed");
+    }
+}
+
+int bem_field_plan_stats_host(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tris,
+                              const double *pts, int64_t n_pts, const bem_params *params, double freq_hz,
+                              double c, bem_field_stats *out)
+{
+    if (!nodes || !tris || !pts || !out || n_nodes < 3 || n_tris < 1 || n_pts < 1 || !(freq_hz > 0))
+        return set_err(BEM_E_ARG, "bad argument");
+    bem_params p;
+    bem_params_default(&p);
+    if (params) p = *params;
+    if (p.m_max < 1 || p.m_max > kMaxRule) return set_err(BEM_E_ARG, "m_max must be in 1..6");
+    try {
+        Geometry g;
+        std::string e = compute_geometry(nodes, n_nodes, tris, n_tris, g);
+        if (!e.empty()) return set_err(BEM_E_ARG, e);
+        Tree t;
+        const double leaf = p.mode == BEM_MODE_DIRECT ? 0.0 : (p.leaf_edge > 0 ? p.leaf_edge : auto_leaf_edge(g, p));
+        build_tree(g, leaf, t);
+        EvalPlan ep;
+        e = build_eval_plan(g, t, p, wavenumber(freq_hz, c > 0 ? c : 343.0), -1, pts, n_pts, kMaxTableL, ep);
+        if (!e.empty()) return set_err(BEM_E_ARG, e);
+        memset(out, 0, sizeof *out);
+        out->leaf_level = ep.leaf_depth;
+        out->levels = (int)std::min<size_t>(16, ep.far.size());
+        for (int l = 0; l < out->levels; ++l) {
+            const EvalLevel &F = ep.far[l];
+            out->level_depth[l] = F.depth;
+            out->L[l] = F.L;
+            out->n_point_clusters[l] = F.npc;
+            out->n_interactions[l] = F.n_inter;
+            out->n_offsets[l] = (int)(F.offsets.size() / 3);
+        }
+        out->near_pairs = ep.near_pairs;
+        out->far_pairs = ep.far_pairs;
+        out->n_point_leaves = (int64_t)ep.leaf_start.size() - 1;
         return BEM_OK;
     } catch (std::bad_alloc &) {
         return set_err(BEM_E_OOM, "host allocation failed");

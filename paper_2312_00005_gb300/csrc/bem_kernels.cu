@@ -1507,6 +1507,70 @@ __global__ void k_field_finish(const double *__restrict__ pts, int64_t M, int S,
     out[m] = make_float2((float)br, (float)bi);
 }
 
+// Far-field weights of the representation formula (Eq. BIE with lambda = 1)
+// for the aggregation T(l) (Sec. 3.3.3): with the one-point element rule,
+//   H_j p_j - G_j q_j ~ A_j (-q_j - ik (n_j.s) p_j) e^{ik (z_s - y_j).s} (...),
+// i.e. (alpha, c) = (-A q, -ik A p) in the form sum_j E_pj (alpha_j + t_pj c_j)
+// of the aggregation (internal element order).
+__global__ void k_field_weights(int64_t n, const float2 *__restrict__ p, const float2 *__restrict__ q,
+                                const float4 *__restrict__ chi, float k, float4 *__restrict__ wts)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float A = chi[i].w;
+    const float2 pv = p[i], qv = q[i];
+    wts[i] = make_float4(-A * qv.x, -A * qv.y, k * A * pv.y, -k * A * pv.x);
+}
+
+// Near part of the field at points (internal point order): the element
+// rules of k_field over the element runs (first element, count) of the
+// point's leaf near list, one warp per point; v_m = sum_j H_j p_j - G_j q_j.
+__global__ void k_field_near(ElemDev E, const QuadTables *__restrict__ Qp, const double *__restrict__ pts, int64_t M,
+                             float k, const float2 *__restrict__ p, const float2 *__restrict__ q,
+                             const int *__restrict__ pleaf, const int *__restrict__ nptr,
+                             const int2 *__restrict__ nruns, float2 *__restrict__ v, int *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t m = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (m >= M) return;
+    const QuadTables &Q = *Qp;
+    const double xd[3] = {pts[3 * m], pts[3 * m + 1], pts[3 * m + 2]};
+    const float3 xhi = make_float3((float)xd[0], (float)xd[1], (float)xd[2]);
+    const float3 xlo = make_float3((float)(xd[0] - (double)xhi.x), (float)(xd[1] - (double)xhi.y),
+                                   (float)(xd[2] - (double)xhi.z));
+    const int pl = pleaf[m];
+    float2 acc = make_float2(0.f, 0.f);
+    for (int r = nptr[pl]; r < nptr[pl + 1]; ++r) {
+        const int2 run = nruns[r];
+        for (int u = lane; u < run.y; u += 32) {
+            const int64_t j = run.x + u;
+            float2 G = make_float2(0.f, 0.f), H = make_float2(0.f, 0.f);
+            if (!integrate_regular<true>(E, j, xhi, xlo, xd, make_float3(0.f, 0.f, 1.f), k, 1.0f / k, Q, G, H)) {
+                atomicMin(err, (int)j);
+                continue;
+            }
+            acc = cadd(acc, csub(cmul(H, p[j]), cmul(G, q[j])));
+        }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) v[m] = acc;
+}
+
+// The field at the points: tau (near + far) plus the incident field (FP64),
+// written in caller order.
+__global__ void k_field_eval_finish(const double *__restrict__ pts, int64_t M, float k, float tau,
+                                    const SourceDev *__restrict__ src, int nsrc, const float2 *__restrict__ v,
+                                    const int64_t *__restrict__ perm, float2 *__restrict__ out)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const double xd[3] = {pts[3 * m], pts[3 * m + 1], pts[3 * m + 2]};
+    const float2 w = cscale(v[m], tau);
+    double br = w.x, bi = w.y;
+    field_incident(xd, k, src, nsrc, br, bi);
+    out[perm[m]] = make_float2((float)br, (float)bi);
+}
+
 // Gradient of the incident fields at x (FP64): plane wave grad p = ik d p,
 // point source grad p = p (ik - 1/R) (x - x0) / R.
 __device__ void incident_grad(const double *xd, float k, const SourceDev *__restrict__ src, int nsrc, double *gr,

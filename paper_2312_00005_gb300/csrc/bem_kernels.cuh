@@ -297,6 +297,14 @@ __global__ void k_field_velocity(ElemDev E, const QuadTables *Q, const double *p
 __global__ void k_field_velocity_finish(const double *pts, int64_t M, int S, float k, float inv_omega_rho,
                                         const SourceDev *src, int nsrc, const float2 *part, float2 *out);
 __global__ void k_gather(const float2 *x, const int64_t *perm, int64_t n, float2 *y);
+// FMM evaluation of the field at points (see the definitions)
+__global__ void k_field_weights(int64_t n, const float2 *p, const float2 *q, const float4 *chi, float k, float4 *wts);
+__global__ void k_field_near(ElemDev E, const QuadTables *Q, const double *pts, int64_t M, float k, const float2 *p,
+                             const float2 *q, const int *pleaf, const int *nptr, const int2 *nruns, float2 *v,
+                             int *err);
+__global__ void k_field_eval_finish(const double *pts, int64_t M, float k, float tau, const SourceDev *src, int nsrc,
+                                    const float2 *v, const int64_t *perm, float2 *out);
+
 __global__ void k_near_fused_t(NearArgs a, const float2 *x, float2 *y, float2 *zero, int *err, const int *skip);
 __global__ void k_prep_t(int64_t n, const float2 *x, float2 *xint, float4 *wts, float4 *rowf, const float4 *chi,
                          const float2 *cp, const float2 *cq, float k, const int *skip);

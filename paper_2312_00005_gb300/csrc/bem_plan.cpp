@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <map>
 #include <cstdio>
 #include <numeric>
 #include <tuple>
@@ -519,6 +520,195 @@ void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k,
             fp.far.push_back(std::move(far_all[d]));
             fp.max_L = std::max(fp.max_L, fp.far.back().L);
         }
+}
+
+std::string build_eval_plan(const Geometry &g, const Tree &t, const bem_params &p, double k, int leaf_depth,
+                            const double *pts, int64_t m, int max_L, EvalPlan &ep)
+{
+    ep = EvalPlan();
+    const int D = (leaf_depth < 0 || leaf_depth > t.leaf_depth) ? t.leaf_depth : leaf_depth;
+    ep.leaf_depth = D;
+    const double boxD = t.edge / (double)((int64_t)1 << D);
+    // integer box coordinates at the leaf depth, shifted by B so that every
+    // coarser depth's coordinate is a right shift (B divisible by 2^D)
+    const int64_t B = (int64_t)1 << 20;
+    std::vector<int64_t> U(3 * (size_t)m);
+    std::vector<uint64_t> code(m);
+    for (int64_t j = 0; j < m; ++j) {
+        for (int i = 0; i < 3; ++i) {
+            const double v = std::floor((pts[3 * j + i] - t.origin[i]) / boxD);
+            if (!(v > (double)-B && v < (double)B))
+                return "field point " + std::to_string(j) + " lies more than 2^20 leaf boxes from the mesh";
+            U[3 * j + i] = (int64_t)v + B;
+        }
+        code[j] = spread3((uint64_t)U[3 * j]) | (spread3((uint64_t)U[3 * j + 1]) << 1) |
+                  (spread3((uint64_t)U[3 * j + 2]) << 2);
+    }
+    {
+        std::vector<std::pair<uint64_t, int64_t>> ci(m);
+        for (int64_t j = 0; j < m; ++j) ci[j] = {code[j], j};
+        std::sort(ci.begin(), ci.end());   // by code, then by caller index
+        ep.perm.resize(m);
+        for (int64_t j = 0; j < m; ++j) ep.perm[j] = ci[j].second;
+    }
+    // codes, coordinates and points in the sorted order (sequential access below)
+    std::vector<uint64_t> scode(m);
+    std::vector<int64_t> sU(3 * (size_t)m);
+    std::vector<double> sp(3 * (size_t)m);
+    for (int64_t i = 0; i < m; ++i) {
+        const int64_t e = ep.perm[i];
+        scode[i] = code[e];
+        for (int a = 0; a < 3; ++a) {
+            sU[3 * i + a] = U[3 * e + a];
+            sp[3 * i + a] = pts[3 * e + a];
+        }
+    }
+    // point clusters of every depth: runs of equal code prefixes
+    struct PDepth {
+        std::vector<int64_t> start;
+        std::vector<int64_t> ix, iy, iz;
+        std::vector<double> rad;
+        std::vector<int32_t> parent, pcl;
+    };
+    std::vector<PDepth> pd(D + 1);
+    for (int d = 0; d <= D; ++d) {
+        PDepth &P = pd[d];
+        const int sh = D - d;
+        const double box = t.edge / (double)((int64_t)1 << d);
+        P.pcl.assign(m, -1);
+        int64_t i = 0;
+        while (i < m) {
+            const uint64_t key = scode[i] >> (3 * sh);
+            int64_t j = i;
+            while (j < m && (scode[j] >> (3 * sh)) == key) ++j;
+            const int32_t c = (int32_t)P.start.size();
+            P.start.push_back(i);
+            P.ix.push_back((sU[3 * i] >> sh) - (B >> sh));
+            P.iy.push_back((sU[3 * i + 1] >> sh) - (B >> sh));
+            P.iz.push_back((sU[3 * i + 2] >> sh) - (B >> sh));
+            const double z[3] = {t.origin[0] + (P.ix.back() + 0.5) * box, t.origin[1] + (P.iy.back() + 0.5) * box,
+                                 t.origin[2] + (P.iz.back() + 0.5) * box};
+            double rad = 0.0;
+            for (int64_t q = i; q < j; ++q) {
+                P.pcl[q] = c;
+                double d3[3];
+                sub3(&sp[3 * q], z, d3);
+                rad = std::max(rad, norm3(d3));
+            }
+            P.rad.push_back(rad);
+            P.parent.push_back(d > 0 ? pd[d - 1].pcl[i] : -1);
+            i = j;
+        }
+        P.start.push_back(m);
+    }
+    double R[kMaxRule + 1] = {0};
+    order_thresholds(p.quad_tol, std::max(2, p.m_max), R);
+    const double r1 = R[1] * (1.0 + 1e-9);
+    const bool direct = p.mode == BEM_MODE_DIRECT;
+    // near element clusters of each point cluster at the previous depth (CSR)
+    std::vector<int32_t> nprev_ptr(pd[0].parent.size() + 1), nprev;
+    for (size_t c = 0; c < pd[0].parent.size(); ++c) {
+        nprev.push_back(0);   // the root element cluster
+        nprev_ptr[c + 1] = (int32_t)nprev.size();
+    }
+    for (int d = 1; d <= D; ++d) {
+        const Level &E = t.lv[d], &Ep = t.lv[d - 1];
+        const PDepth &P = pd[d];
+        const int npc = (int)P.parent.size();
+        const double xL = 2.0 * E.rmax * k;
+        const int L = std::max(p.L_min, (int)std::ceil(xL + p.trunc_factor * std::log10(xL + M_PI) - 1e-12));
+        const bool stab_on = p.stability_max < 1e300;
+        const bool allowed = !direct && L <= max_L && (!stab_on || (double)(L + 1) * (L + 1) <= p.stability_max);
+        // the growth sum decreases with x, so an offset is stable when k |X|
+        // reaches the root x* of growth = stability_max (bisection, once per
+        // level)
+        double xstar = 0.0;
+        if (allowed && stab_on) {
+            double lo = 1e-9, hi = 1.0;
+            for (int it = 0; it < 64 && !(hankel_growth(hi, L) <= p.stability_max); ++it) hi *= 2.0;
+            for (int it = 0; it < 200 && hi - lo > 1e-13 * hi; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (hankel_growth(mid, L) <= p.stability_max) hi = mid;
+                else lo = mid;
+            }
+            xstar = hi;
+        }
+        EvalLevel F;
+        F.depth = d;
+        F.L = L;
+        F.npc = npc;
+        F.il_ptr.assign(npc + 1, 0);
+        std::map<std::tuple<int64_t, int64_t, int64_t>, int32_t> off_index;   // -1: unstable
+        std::vector<int32_t> ncur_ptr(npc + 1, 0), ncur;
+        for (int c = 0; c < npc; ++c) {
+            const int par = P.parent[c];
+            const int64_t cnt = P.start[c + 1] - P.start[c];
+            for (int q = nprev_ptr[par]; q < nprev_ptr[par + 1]; ++q) {
+                const int sp = nprev[q];
+                for (int s = Ep.child0[sp]; s < Ep.child0[sp] + Ep.nchild[sp]; ++s) {
+                    const int64_t dx = P.ix[c] - E.ix[s], dy = P.iy[c] - E.iy[s], dz = P.iz[c] - E.iz[s];
+                    const double X[3] = {dx * E.box, dy * E.box, dz * E.box};
+                    const double dist = norm3(X);
+                    bool far = allowed && P.rad[c] <= E.rmax && dist > p.admissibility * (P.rad[c] + E.rad[s]) &&
+                               dist - P.rad[c] - E.crad[s] > r1 * std::sqrt(E.amax[s]);
+                    int32_t oi = -1;
+                    if (far) {
+                        auto key = std::make_tuple(dx, dy, dz);
+                        auto it = off_index.find(key);
+                        if (it == off_index.end()) {
+                            const bool ok = !stab_on || k * dist >= xstar;
+                            int32_t idx = -1;
+                            if (ok) {
+                                idx = (int32_t)(F.offsets.size() / 3);
+                                F.offsets.insert(F.offsets.end(), X, X + 3);
+                            }
+                            it = off_index.emplace(key, idx).first;
+                        }
+                        oi = it->second;
+                        far = oi >= 0;
+                    }
+                    if (far) {
+                        F.il_src.push_back(s);
+                        F.il_off.push_back(oi);
+                        ep.far_pairs += cnt * E.count[s];
+                    } else {
+                        ncur.push_back(s);
+                    }
+                }
+            }
+            F.il_ptr[c + 1] = (int32_t)F.il_src.size();
+            ncur_ptr[c + 1] = (int32_t)ncur.size();
+        }
+        F.n_inter = (int64_t)F.il_src.size();
+        if (F.n_inter > 0) {
+            F.pcl = P.pcl;
+            F.zp.resize(3 * (size_t)npc);
+            for (int c = 0; c < npc; ++c) {
+                F.zp[3 * c] = t.origin[0] + (P.ix[c] + 0.5) * E.box;
+                F.zp[3 * c + 1] = t.origin[1] + (P.iy[c] + 0.5) * E.box;
+                F.zp[3 * c + 2] = t.origin[2] + (P.iz[c] + 0.5) * E.box;
+            }
+            ep.far.push_back(std::move(F));
+        }
+        nprev_ptr.swap(ncur_ptr);
+        nprev.swap(ncur);
+    }
+    // leaf near lists (sorted element leaves)
+    const PDepth &PL = pd[D];
+    const int npl = (int)PL.parent.size();
+    ep.leaf_start = PL.start;
+    ep.near_ptr.assign(npl + 1, 0);
+    const Level &EL = t.lv[D];
+    for (int c = 0; c < npl; ++c) {
+        std::vector<int32_t> v(nprev.begin() + nprev_ptr[c], nprev.begin() + nprev_ptr[c + 1]);
+        std::sort(v.begin(), v.end());
+        for (int32_t s2 : v) {
+            ep.near_src.push_back(s2);
+            ep.near_pairs += (PL.start[c + 1] - PL.start[c]) * EL.count[s2];
+        }
+        ep.near_ptr[c + 1] = (int32_t)ep.near_src.size();
+    }
+    return "";
 }
 
 // Kernel evaluations of one near pair (row element at x, column element e):

@@ -138,6 +138,40 @@ struct NearCount {
 };
 NearCount count_near_points(const Geometry &g, const Tree &t, const FreqPlan &fp, const bem_params &p);
 
+// Field-point plan: the representation formula (Eq. BIE with lambda = 1) at
+// points off the surface through the same plane-wave expansions (Sec. 3.3):
+// the points are clustered on the element tree's box grid (boxes outside the
+// root cube included), and a point cluster P and an element cluster s of the
+// same depth interact in the far field when the element pair test of
+// build_plan holds for them (Eq. Farfieldcond with the points' radius, the
+// stability test, every point-element distance above R_1 times the square
+// root of the largest element area, so the one-point rule of the
+// aggregation is the element rule of the field) and the point radius stays
+// within the depth's element radius (which sets L); pairs still near at the
+// leaf depth are summed directly.
+struct EvalLevel {
+    int depth = 0, L = 0;
+    int npc = 0;                          // point clusters at this depth
+    std::vector<int32_t> il_ptr;          // npc + 1
+    std::vector<int32_t> il_src, il_off;  // element clusters of this depth, translation rows
+    std::vector<double> offsets;          // 3 * noff vectors z_P - z_s
+    std::vector<int32_t> pcl;             // per point (internal order): cluster at this depth
+    std::vector<double> zp;               // 3 * npc box centres
+    int64_t n_inter = 0;
+};
+struct EvalPlan {
+    int leaf_depth = 0;
+    std::vector<int64_t> perm;            // internal -> caller point index
+    std::vector<int64_t> leaf_start;      // point clusters at leaf_depth: internal ranges (+ end)
+    std::vector<EvalLevel> far;           // levels with interactions, coarse to fine
+    std::vector<int32_t> near_ptr, near_src;  // per point leaf: element leaves at leaf_depth
+    int64_t near_pairs = 0, far_pairs = 0;    // point-element pairs
+};
+// Returns an empty string or an error message.  max_L: the largest expansion
+// length the translation tables support.
+std::string build_eval_plan(const Geometry &g, const Tree &t, const bem_params &p, double k, int leaf_depth,
+                            const double *pts, int64_t m, int max_L, EvalPlan &ep);
+
 // Sets the calling thread's message returned by bem_last_error.
 void set_last_error(const std::string &msg);
 

@@ -211,6 +211,62 @@ def test_restarted_gmres_matches_oracle(bem, restart):
     _check(p.cpu().numpy(), po, 1e-4, 1e-3, "restarted GMRES(%d)" % restart)
 
 
+@pytest.mark.parametrize("tf,l2,el", [(1.8, 2e-3, 2e-2), (6.0, 1e-4, 1e-3)])
+def test_fmm_field_evaluation_matches_oracle(bem, tf, l2, el):
+    """bem_evaluate's FMM path (field_mode 2): 5120 elements at 2 kHz with
+    random surface data p, q, at 3000 points on spheres of radius 0.105 m
+    (near the surface: mostly the element rules), 0.3 m and 1 m (through the
+    expansions at one to three levels), against the oracle's representation
+    formula with the same p, q (no incident field, so only the integrals are
+    compared), within the bounds of the FMM products at the same truncation
+    factor, per sphere of points: relative l2 error, and each point's error
+    against the sphere's largest value (random surface data make the field
+    at a point a cancelling sum, so its own value can be far below the size
+    of the parts the truncation acts on); the direct sum (field_mode 1)
+    within FP32 rounding; and a plane wave adds exactly its incident
+    field.  A second call with the same points reuses the point plan."""
+    nodes, tris = inputs.icosphere(4, 0.1)
+    n = tris.shape[0]
+    freq = 2000.0
+    pts = np.vstack([inputs.fibonacci_sphere(600, 0.105), inputs.fibonacci_sphere(1800, 0.3),
+                     inputs.fibonacci_sphere(600, 1.0)])
+    p = inputs.random_complex(n, 81)
+    q = inputs.random_complex(n, 82)
+    pt = torch.tensor(p, dtype=torch.complex64, device="cuda")
+    qt = torch.tensor(q, dtype=torch.complex64, device="cuda")
+    fo = oracle.field(nodes, tris, freq, p, q, pts, c=C)
+    mesh = bem.Mesh(nodes, tris, trunc_factor=tf, field_mode=2)
+    bem.timing_enable(True)
+    try:
+        f = mesh.evaluate(freq, pt, qt, pts, [], c=C, rho=RHO).cpu().numpy()
+        assert bem.timing_get("k_field_near")[1] == 1 and bem.timing_get("k_transfer")[1] == 1
+        assert bem.timing_get("k_field")[1] == 0
+    finally:
+        bem.timing_enable(False)
+    src = [bem.plane_wave((0, 0, 1))]
+    bem.timing_enable(True)
+    try:
+        fs = mesh.evaluate(freq, pt, qt, pts, src, c=C, rho=RHO).cpu().numpy()
+        assert bem.timing_get("k_dtable")[1] == 0     # the plan and its tables were kept
+    finally:
+        bem.timing_enable(False)
+    mesh.close()
+    mesh = bem.Mesh(nodes, tris, field_mode=1)
+    fd = mesh.evaluate(freq, pt, qt, pts, [], c=C, rho=RHO).cpu().numpy()
+    mesh.close()
+    _check(fd, fo, 2e-5, 2e-4, "direct field sum vs oracle")
+    o = 0
+    for m in (600, 1800, 600):
+        a, b = f[o:o + m], fo[o:o + m]
+        e2, ee = _rel(a, b), float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+        print("FMM field, factor %g, %d points: rel l2 %.3g, max error / max value %.3g" % (tf, m, e2, ee))
+        assert e2 < l2 and ee < el, (tf, m, e2, ee)
+        o += m
+    k = 2 * np.pi * freq / C
+    inc = np.exp(1j * k * pts[:, 2])
+    assert np.max(np.abs((fs - f) - inc)) < 1e-5
+
+
 def test_field_velocity_matches_oracle(bem):
     """Particle velocity at field points (Eq. utopandv, gradient of Eq. BIE_I)
     from the GPU solution, against the oracle's velocity from the same p, q:

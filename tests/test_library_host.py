@@ -244,3 +244,32 @@ def test_near_quadrature_counts_cover_the_near_field(lib):
     assert st["near_heavy_points"] >= 132 * n
     assert st["near_light_entries"] <= st["near_light_points"] <= 9 * st["near_light_entries"]
     assert st["near_quad_points"] == st["near_light_points"] + st["near_heavy_points"]
+
+
+@pytest.mark.parametrize("mesh", ["ico4", "head22"])
+def test_field_point_plan_partitions_point_element_pairs(lib, mesh):
+    """The field-point plan of the FMM evaluation (points clustered on the
+    element tree's box grid, far pairs by the element lists' test with the
+    points as targets): every point-element pair is either summed directly
+    or taken through the expansions, exactly once; distant points go through
+    the expansions at coarse levels, points near the surface mostly stay
+    near; in direct mode everything is near; a point 2^20 leaf boxes away is
+    refused."""
+    nodes, tris = inputs.icosphere(4, 0.1) if mesh == "ico4" else inputs.bumpy_ellipsoid(22)
+    n = tris.shape[0]
+    sets = {"near": inputs.fibonacci_sphere(700, 0.105), "mid": inputs.fibonacci_sphere(900, 0.3),
+            "far": inputs.fibonacci_sphere(1500, 1.0)}
+    frac = {}
+    for name, pts in sets.items():
+        st = bemfmm.field_plan_stats_host(nodes, tris, pts, 2000.0)
+        m = pts.shape[0]
+        assert st["near_pairs"] + st["far_pairs"] == m * n, (name, st)
+        assert sum(st["n_point_clusters"]) > 0 or st["far_pairs"] == 0
+        assert all(L >= 8 for L in st["L"])
+        frac[name] = st["near_pairs"] / (m * n)
+    assert frac["far"] == 0.0 and frac["mid"] < 0.01 and frac["near"] > 0.05, frac
+    allp = np.vstack(list(sets.values()))
+    st = bemfmm.field_plan_stats_host(nodes, tris, allp, 2000.0, params=bemfmm.default_params(mode=bemfmm.MODE_DIRECT))
+    assert st["far_pairs"] == 0 and st["near_pairs"] == allp.shape[0] * n
+    with pytest.raises(bemfmm.BemError):
+        bemfmm.field_plan_stats_host(nodes, tris, np.array([[1e6, 0.0, 0.0]]), 2000.0)
