@@ -5,7 +5,8 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
-#include <map>
+#include <thread>
+#include <unordered_map>
 #include <cstdio>
 #include <numeric>
 #include <tuple>
@@ -522,10 +523,27 @@ void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k,
         }
 }
 
+namespace {
+struct OffKey {
+    int64_t x, y, z;
+    bool operator==(const OffKey &o) const { return x == o.x && y == o.y && z == o.z; }
+};
+struct OffKeyHash {
+    size_t operator()(const OffKey &k) const
+    {
+        uint64_t h = (uint64_t)k.x * 0x9E3779B97F4A7C15ULL;
+        h ^= (uint64_t)k.y * 0xC2B2AE3D27D4EB4FULL + (h << 6) + (h >> 2);
+        h ^= (uint64_t)k.z * 0x165667B19E3779F9ULL + (h << 6) + (h >> 2);
+        return (size_t)h;
+    }
+};
+}  // namespace
+
 std::string build_eval_plan(const Geometry &g, const Tree &t, const bem_params &p, double k, int leaf_depth,
                             const double *pts, int64_t m, int max_L, EvalPlan &ep)
 {
     ep = EvalPlan();
+    const int n_threads = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
     const int D = (leaf_depth < 0 || leaf_depth > t.leaf_depth) ? t.leaf_depth : leaf_depth;
     ep.leaf_depth = D;
     const double boxD = t.edge / (double)((int64_t)1 << D);
@@ -607,9 +625,13 @@ std::string build_eval_plan(const Geometry &g, const Tree &t, const bem_params &
     const bool direct = p.mode == BEM_MODE_DIRECT;
     // near element clusters of each point cluster at the previous depth (CSR)
     std::vector<int32_t> nprev_ptr(pd[0].parent.size() + 1), nprev;
+    int64_t rnear_prev = 0;   // largest |offset component| among the previous depth's near pairs
     for (size_t c = 0; c < pd[0].parent.size(); ++c) {
         nprev.push_back(0);   // the root element cluster
         nprev_ptr[c + 1] = (int32_t)nprev.size();
+        rnear_prev = std::max(rnear_prev, std::max(std::abs(pd[0].ix[c] - t.lv[0].ix[0]),
+                                                   std::max(std::abs(pd[0].iy[c] - t.lv[0].iy[0]),
+                                                            std::abs(pd[0].iz[c] - t.lv[0].iz[0]))));
     }
     for (int d = 1; d <= D; ++d) {
         const Level &E = t.lv[d], &Ep = t.lv[d - 1];
@@ -638,46 +660,110 @@ std::string build_eval_plan(const Geometry &g, const Tree &t, const bem_params &
         F.L = L;
         F.npc = npc;
         F.il_ptr.assign(npc + 1, 0);
-        std::map<std::tuple<int64_t, int64_t, int64_t>, int32_t> off_index;   // -1: unstable
-        std::vector<int32_t> ncur_ptr(npc + 1, 0), ncur;
-        for (int c = 0; c < npc; ++c) {
-            const int par = P.parent[c];
-            const int64_t cnt = P.start[c + 1] - P.start[c];
-            for (int q = nprev_ptr[par]; q < nprev_ptr[par + 1]; ++q) {
-                const int sp = nprev[q];
-                for (int s = Ep.child0[sp]; s < Ep.child0[sp] + Ep.nchild[sp]; ++s) {
-                    const int64_t dx = P.ix[c] - E.ix[s], dy = P.iy[c] - E.iy[s], dz = P.iz[c] - E.iz[s];
-                    const double X[3] = {dx * E.box, dy * E.box, dz * E.box};
-                    const double dist = norm3(X);
-                    bool far = allowed && P.rad[c] <= E.rmax && dist > p.admissibility * (P.rad[c] + E.rad[s]) &&
-                               dist - P.rad[c] - E.crad[s] > r1 * std::sqrt(E.amax[s]);
-                    int32_t oi = -1;
-                    if (far) {
-                        auto key = std::make_tuple(dx, dy, dz);
-                        auto it = off_index.find(key);
-                        if (it == off_index.end()) {
-                            const bool ok = !stab_on || k * dist >= xstar;
-                            int32_t idx = -1;
-                            if (ok) {
-                                idx = (int32_t)(F.offsets.size() / 3);
-                                F.offsets.insert(F.offsets.end(), X, X + 3);
+        // the point clusters in contiguous chunks, one per thread; each chunk
+        // numbers its stable far offsets itself, and the chunks' numbers are
+        // merged in chunk order afterwards (the plan does not depend on the
+        // thread count's timing)
+        struct Chunk {
+            std::vector<int32_t> il_src, il_off, ncur, nil, nnear;   // nil / nnear: per cluster
+            std::vector<OffKey> keys;                                 // local offset index -> key
+            std::vector<double> X;                                    // 3 per local offset
+            int64_t far_pairs = 0;
+            int64_t rnear = 0;                                        // largest |offset component| of near pairs
+        };
+        // candidates are children of the previous depth's near pairs, so their
+        // offsets lie in [-Rb, Rb]^3: a dense table of offset states when that
+        // window is small, else a hash map
+        const int64_t Rb = 2 * rnear_prev + 1, W = 2 * Rb + 1;
+        const bool dense = W * W * W <= ((int64_t)1 << 21);
+        const int64_t work = (int64_t)nprev.size() * 8;
+        const int nth = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)n_threads, work / 20000, (int64_t)npc}));
+        std::vector<Chunk> ch(nth);
+        auto run = [&](int ti) {
+            Chunk &C = ch[ti];
+            const int c0 = (int)((int64_t)npc * ti / nth), c1 = (int)((int64_t)npc * (ti + 1) / nth);
+            std::unordered_map<OffKey, int32_t, OffKeyHash> off_index;   // local index, -1: unstable
+            std::vector<int32_t> off_state(dense ? (size_t)(W * W * W) : 0, -2);   // -2: not seen yet
+            C.nil.assign(c1 - c0, 0);
+            C.nnear.assign(c1 - c0, 0);
+            for (int c = c0; c < c1; ++c) {
+                const int par = P.parent[c];
+                const int64_t cnt = P.start[c + 1] - P.start[c];
+                const size_t il0 = C.il_src.size(), nn0 = C.ncur.size();
+                for (int q = nprev_ptr[par]; q < nprev_ptr[par + 1]; ++q) {
+                    const int sp = nprev[q];
+                    for (int s = Ep.child0[sp]; s < Ep.child0[sp] + Ep.nchild[sp]; ++s) {
+                        const int64_t dx = P.ix[c] - E.ix[s], dy = P.iy[c] - E.iy[s], dz = P.iz[c] - E.iz[s];
+                        const double X[3] = {dx * E.box, dy * E.box, dz * E.box};
+                        const double dist = norm3(X);
+                        bool far = allowed && P.rad[c] <= E.rmax && dist > p.admissibility * (P.rad[c] + E.rad[s]) &&
+                                   dist - P.rad[c] - E.crad[s] > r1 * std::sqrt(E.amax[s]);
+                        int32_t oi = -1;
+                        if (far) {
+                            auto local_index = [&]() {
+                                if (stab_on && !(k * dist >= xstar)) return -1;
+                                C.keys.push_back(OffKey{dx, dy, dz});
+                                C.X.insert(C.X.end(), X, X + 3);
+                                return (int)C.keys.size() - 1;
+                            };
+                            if (dense) {
+                                int32_t &st = off_state[(size_t)(((dx + Rb) * W + (dy + Rb)) * W + (dz + Rb))];
+                                if (st == -2) st = local_index();
+                                oi = st;
+                            } else {
+                                const OffKey key{dx, dy, dz};
+                                auto it = off_index.find(key);
+                                if (it == off_index.end()) it = off_index.emplace(key, local_index()).first;
+                                oi = it->second;
                             }
-                            it = off_index.emplace(key, idx).first;
+                            far = oi >= 0;
                         }
-                        oi = it->second;
-                        far = oi >= 0;
-                    }
-                    if (far) {
-                        F.il_src.push_back(s);
-                        F.il_off.push_back(oi);
-                        ep.far_pairs += cnt * E.count[s];
-                    } else {
-                        ncur.push_back(s);
+                        if (far) {
+                            C.il_src.push_back(s);
+                            C.il_off.push_back(oi);
+                            C.far_pairs += cnt * E.count[s];
+                        } else {
+                            C.ncur.push_back(s);
+                            C.rnear = std::max(C.rnear, std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))));
+                        }
                     }
                 }
+                C.nil[c - c0] = (int32_t)(C.il_src.size() - il0);
+                C.nnear[c - c0] = (int32_t)(C.ncur.size() - nn0);
             }
-            F.il_ptr[c + 1] = (int32_t)F.il_src.size();
-            ncur_ptr[c + 1] = (int32_t)ncur.size();
+        };
+        if (nth == 1) {
+            run(0);
+        } else {
+            std::vector<std::thread> th;
+            for (int ti = 0; ti < nth; ++ti) th.emplace_back(run, ti);
+            for (auto &x : th) x.join();
+        }
+        std::unordered_map<OffKey, int32_t, OffKeyHash> off_index;   // global index
+        std::vector<int32_t> ncur_ptr(npc + 1, 0), ncur;
+        int64_t rnear = 0;
+        for (int ti = 0; ti < nth; ++ti) {
+            Chunk &C = ch[ti];
+            std::vector<int32_t> remap(C.keys.size());
+            for (size_t u = 0; u < C.keys.size(); ++u) {
+                auto it = off_index.find(C.keys[u]);
+                if (it == off_index.end()) {
+                    it = off_index.emplace(C.keys[u], (int32_t)(F.offsets.size() / 3)).first;
+                    F.offsets.insert(F.offsets.end(), &C.X[3 * u], &C.X[3 * u] + 3);
+                }
+                remap[u] = it->second;
+            }
+            const int c0 = (int)((int64_t)npc * ti / nth);
+            for (size_t u = 0; u < C.nil.size(); ++u) {
+                F.il_ptr[c0 + u + 1] = F.il_ptr[c0 + u] + C.nil[u];
+                ncur_ptr[c0 + u + 1] = ncur_ptr[c0 + u] + C.nnear[u];
+            }
+            F.il_src.insert(F.il_src.end(), C.il_src.begin(), C.il_src.end());
+            for (int32_t oi : C.il_off) F.il_off.push_back(remap[oi]);
+            ncur.insert(ncur.end(), C.ncur.begin(), C.ncur.end());
+            ep.far_pairs += C.far_pairs;
+            rnear = std::max(rnear, C.rnear);
+            Chunk().il_src.swap(C.il_src);
         }
         F.n_inter = (int64_t)F.il_src.size();
         if (F.n_inter > 0) {
@@ -692,6 +778,7 @@ std::string build_eval_plan(const Geometry &g, const Tree &t, const bem_params &
         }
         nprev_ptr.swap(ncur_ptr);
         nprev.swap(ncur);
+        rnear_prev = rnear;
     }
     // leaf near lists (sorted element leaves)
     const PDepth &PL = pd[D];
