@@ -276,12 +276,16 @@ struct Lists {
     // expensive near pairs (row, position), listed on first use
     DevArr<int2> heavy;
     int64_t n_heavy = -1;
-    // transposed near product from the stored values: per leaf t, the leaves
-    // s of its near list as (first row, rows, column of t's first element in
-    // s's rows); usable when every near pair has its mirror (tsym)
-    DevArr<int> tptr;
-    DevArr<int4> tent;
-    bool tsym = false;
+    // transposed near product from the stored values: per leaf t, the rows i
+    // of the leaves s in its near list, each with the position of A_i,t0 (t's
+    // first element) in the stored values; usable when every near pair has
+    // its mirror (tsym)
+    DevArr<int> trow_ptr, trow_i;
+    DevArr<int64_t> trow_off;
+    bool tsym = false, trow_ready = false;
+    std::vector<std::pair<int, int>> h_tent;   // per leaf t (h_tptr): (leaf s, column of t in s's rows)
+    std::vector<int> h_tptr;
+    std::vector<int64_t> h_row_ptr;
     // block-Jacobi sub-blocks (first element, size, offset of the inverse)
     std::vector<int4> h_bj;
     DevArr<int4> bj;
@@ -535,8 +539,8 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
             for (int q = F.near_ptr[s2]; q < F.near_ptr[s2 + 1]; ++q)
                 key.emplace_back((int64_t)s2 * nl + F.near_src[q], colpos[q]);
         std::sort(key.begin(), key.end());
+        std::vector<std::pair<int, int>> tent;   // (leaf s, column of t in s's rows)
         std::vector<int> tptr(nl + 1, 0);
-        std::vector<int4> tent;
         bool sym = true;
         for (int t = 0; t < nl && sym; ++t) {
             for (int q = F.near_ptr[t]; q < F.near_ptr[t + 1]; ++q) {
@@ -547,14 +551,14 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
                     sym = false;
                     break;
                 }
-                tent.push_back(make_int4((int)Lf.start[sl], (int)Lf.count[sl], it->second, 0));
+                tent.emplace_back(sl, it->second);
             }
             tptr[t + 1] = (int)tent.size();
         }
         Ls->tsym = sym;
         if (sym) {
-            Ls->tptr.upload(tptr, s);
-            Ls->tent.upload(tent, s);
+            Ls->h_tent = std::move(tent);
+            Ls->h_tptr = std::move(tptr);
         }
     }
     std::vector<int> leaf_of(M.n);
@@ -603,6 +607,7 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
         Ls->bj.upload(Ls->h_bj, s);
     }
     Ls->nnz = row_ptr[M.n];
+    if (Ls->tsym) Ls->h_row_ptr = row_ptr;
     Ls->leaf_of.upload(leaf_of, s);
     Ls->run_ptr.upload(run_ptr, s);
     Ls->ncol.upload(ncol, s);
@@ -1382,6 +1387,37 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
     }
 }
 
+// The rows of the transposed product from the stored values (per leaf t,
+// every row i of its near leaves with the position of A_i,t0 in the stored
+// values), built on the first transposed product of a plan's lists: outside
+// any graph capture (the callers of the transposed products run it first).
+void ensure_transposed_rows(bem_mesh_impl &M)
+{
+    Lists &Ls = *fr(M).plan->lists;
+    if (!Ls.tsym || Ls.trow_ready || !M.prm.near_store || Ls.fp.direct) return;
+    const Level &Lf = M.t.lv[Ls.fp.leaf_depth];
+    const int nl = (int)Lf.start.size();
+    std::vector<int> rptr(nl + 1, 0), ri;
+    std::vector<int64_t> roff;
+    for (int t = 0; t < nl; ++t) {
+        for (int e = Ls.h_tptr[t]; e < Ls.h_tptr[t + 1]; ++e) {
+            const int sl = Ls.h_tent[e].first, col = Ls.h_tent[e].second;
+            for (int64_t i = Lf.start[sl]; i < Lf.start[sl] + Lf.count[sl]; ++i) {
+                ri.push_back((int)i);
+                roff.push_back(Ls.h_row_ptr[i] + col);
+            }
+        }
+        if (ri.size() > (size_t)INT_MAX) throw Fail{set_err(BEM_E_ARG, "transposed near rows exceed 2^31")};
+        rptr[t + 1] = (int)ri.size();
+    }
+    cudaStream_t s = fr(M).s;
+    Ls.trow_ptr.upload(rptr, s);
+    Ls.trow_i.upload(ri, s);
+    Ls.trow_off.upload(roff, s);
+    ck(cudaStreamSynchronize(s), "sync");
+    Ls.trow_ready = true;
+}
+
 // y = A^T x with the given column coefficients (the adjoint solve): the
 // near part by k_near_spmv_t (the stored values, when they were made with
 // these coefficients and the near lists are symmetric) or k_near_fused_t
@@ -1426,14 +1462,14 @@ void matvec_t_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, con
         ck_launch("k_transfer");
     }
     const Lists &Ls = *P.lists;
-    if (cp == fr(M).cp.p && cq == fr(M).cq.p && P.val_valid && M.prm.near_store && !P.fp().direct && Ls.tsym) {
+    if (cp == fr(M).cp.p && cq == fr(M).cq.p && P.val_valid && M.prm.near_store && !P.fp().direct && Ls.trow_ready) {
         // the stored values of A (made with these coefficients), read by column
         {
             KTimer kt_("k_near_spmv_t", s);
             const int nl = (int)Ls.fp.near_ptr.size() - 1;
             if (nl > 0)
-                k_near_spmv_t<<<nl, kSpmvTThreads, 0, s>>>(Ls.leaf_start.p, Ls.row_ptr.p, Ls.tptr.p, Ls.tent.p,
-                                                            P.val.p, M.xint.p, M.ynear.p, skip);
+                k_near_spmv_t<<<nl, kSpmvTThreads, 0, s>>>(Ls.leaf_start.p, Ls.trow_ptr.p, Ls.trow_i.p,
+                                                            Ls.trow_off.p, P.val.p, M.xint.p, M.ynear.p, skip);
         }
         ck_launch("k_near_spmv_t");
     } else {
@@ -1958,6 +1994,7 @@ int bem_matvec_transpose(void *mesh, double freq_hz, const bem_medium *medium, c
             k_gather<<<nblocks(M.n, 256), 256, 0, M.s>>>((const float2 *)x_dev, M.perm.p, M.n, M.tmp.p);
         }
         ck_launch("k_gather");
+        ensure_transposed_rows(M);
         matvec_t_internal(M, fr(M).cp.p, fr(M).cq.p, M.tmp.p, (float2 *)y_dev, true, false, nullptr, M.s);
         check_err(M);
         join_streams(M.s, us);
@@ -3207,6 +3244,7 @@ int bem_admittance_gradient(void *mesh, double freq_hz, const bem_medium *medium
         }
         ck_launch("k_field_t");
         // adjoint solve A^T lambda = F^T conj(f) (lambda in uvec)
+        ensure_transposed_rows(M);
         GmresResult R = run_gmres(M, tol, max_iter, true);
         // aq = A_q^T lambda: the transposed product with c^p = 0 and c^q = 1
         // (tau folded in as for the unknowns' coefficients)

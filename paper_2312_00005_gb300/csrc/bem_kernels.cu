@@ -395,14 +395,15 @@ __global__ void __launch_bounds__(kSpmvThreads) k_near_spmv_items(NearArgs a, co
 // Transposed near-field product from the stored values (the near relation
 // of the leaves being symmetric): for the elements j of leaf t = blockIdx.x,
 //   y_j = sum_{s in near(t)} sum_{i in s} A_ij x_i,
-// where A_ij sits in row i's stored values at the column of t's first
-// element in s's near list plus (j - first element of t).  Lanes take 32
-// consecutive j (one coalesced segment of a row), warps take rows; the warps'
-// sums are added in warp order.
+// where A_ij sits at trow_off[k] + (j - first element of t) for row k of the
+// leaf's list.  A warp takes R = 32 / w rows at a time (w the power of two at
+// or above the leaf size, at most 32): lane (sub, jj) reads one row's value at
+// column jj of a w-wide segment (a coalesced run per row); the sub-rows' and
+// then the warps' sums are added in a fixed order.
 __global__ void __launch_bounds__(kSpmvTThreads) k_near_spmv_t(const int64_t *__restrict__ leaf_start,
-                                                               const int64_t *__restrict__ row_ptr,
-                                                               const int *__restrict__ tptr,
-                                                               const int4 *__restrict__ tent,
+                                                               const int *__restrict__ trow_ptr,
+                                                               const int *__restrict__ trow_i,
+                                                               const int64_t *__restrict__ trow_off,
                                                                const float2 *__restrict__ val,
                                                                const float2 *__restrict__ x, float2 *__restrict__ y,
                                                                const int *skip)
@@ -414,32 +415,37 @@ __global__ void __launch_bounds__(kSpmvTThreads) k_near_spmv_t(const int64_t *__
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t j0 = leaf_start[t];
     const int cnt = (int)(leaf_start[t + 1] - j0);
-    const int e0 = tptr[t], e1 = tptr[t + 1];
-    for (int c0 = 0; c0 < cnt; c0 += 32) {
-        const bool live = c0 + lane < cnt;
+    int w = 1;
+    while (w < cnt && w < 32) w <<= 1;
+    const int R = 32 / w, sub = lane / w, jj = lane % w;
+    const int k0 = trow_ptr[t], k1 = trow_ptr[t + 1];
+    for (int c0 = 0; c0 < cnt; c0 += w) {
+        const bool live = c0 + jj < cnt;
         float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
-        for (int e = e0; e < e1; ++e) {
-            const int4 en = tent[e];   // (first row, rows, column of t's first element)
-            int r = warp;
-            for (; r + kW < en.y; r += 2 * kW) {
-                const int64_t i = en.x + r, i2 = i + kW;
-                const float2 xa = x[i], xb = x[i2];
-                if (live) {
-                    acc0 = cfma(__ldcs(val + row_ptr[i] + en.z + c0 + lane), xa, acc0);
-                    acc1 = cfma(__ldcs(val + row_ptr[i2] + en.z + c0 + lane), xb, acc1);
-                }
-            }
-            if (r < en.y && live) {
-                const int64_t i = en.x + r;
-                acc0 = cfma(__ldcs(val + row_ptr[i] + en.z + c0 + lane), x[i], acc0);
+        int k = k0 + warp * R + sub;
+        const int step = kW * R;
+        for (; k + step < k1; k += 2 * step) {
+            const int i0 = trow_i[k], i1 = trow_i[k + step];
+            const int64_t o0 = trow_off[k], o1 = trow_off[k + step];
+            const float2 xa = x[i0], xb = x[i1];
+            if (live) {
+                acc0 = cfma(__ldcs(val + o0 + c0 + jj), xa, acc0);
+                acc1 = cfma(__ldcs(val + o1 + c0 + jj), xb, acc1);
             }
         }
-        part[warp][lane] = cadd(acc0, acc1);
+        if (k < k1 && live) acc0 = cfma(__ldcs(val + trow_off[k] + c0 + jj), x[trow_i[k]], acc0);
+        float2 acc = cadd(acc0, acc1);
+        // add the R sub-rows (lanes jj, jj + w, ...) in a fixed order
+        for (int o = w; o < 32; o <<= 1) {
+            acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+        }
+        if (sub == 0) part[warp][jj] = acc;
         __syncthreads();
-        if (warp == 0 && live) {
+        if (warp == 0 && lane < w && c0 + lane < cnt) {
             float2 sum = part[0][lane];
 #pragma unroll
-            for (int w = 1; w < kW; ++w) sum = cadd(sum, part[w][lane]);
+            for (int v = 1; v < kW; ++v) sum = cadd(sum, part[v][lane]);
             y[j0 + c0 + lane] = sum;
         }
         __syncthreads();

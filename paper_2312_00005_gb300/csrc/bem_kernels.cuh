@@ -154,11 +154,12 @@ constexpr int kSpmvMaxItemRows = 32;
 __global__ void k_near_spmv_items(NearArgs a, const int4 *items, const float2 *val, const float2 *x, float2 *y,
                                   const int *skip);
 // Transposed product from the stored values: one block per leaf t, the
-// rows of its near leaves listed by tptr / tent (first row, rows, column of
-// t's first element in those rows).
+// rows of its near leaves listed in [trow_ptr[t], trow_ptr[t + 1]) with the
+// row element trow_i and the position trow_off of its value at t's first
+// element.
 constexpr int kSpmvTThreads = 256;
-__global__ void k_near_spmv_t(const int64_t *leaf_start, const int64_t *row_ptr, const int *tptr, const int4 *tent,
-                              const float2 *val, const float2 *x, float2 *y, const int *skip);
+__global__ void k_near_spmv_t(const int64_t *leaf_start, const int *trow_ptr, const int *trow_i,
+                              const int64_t *trow_off, const float2 *val, const float2 *x, float2 *y, const int *skip);
 // The same for nr <= kMaxPlanes right-hand sides (planes `plane` elements
 // apart in x and y): the stored values are streamed once for all of them.
 // The leaf's columns are staged in chunks of cw (even) columns: dynamic
