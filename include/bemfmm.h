@@ -478,6 +478,17 @@ int bem_matvec_direct_noalloc(const double *nodes_dev, int64_t n_nodes, const in
  *     allocations (every mesh's buffers) at the time of the call. */
 int bem_test_hooks(int64_t alloc_fail_after, int64_t *live_device_bytes);
 
+/* The Krylov basis of the last GMRES cycle of the mesh's last solve (no
+ * counterpart in the paper; for measuring the orthogonality of the FP32
+ * basis): right-hand side `plane` (0 for bem_solve), its ncols normalised
+ * basis vectors V_0 .. V_{ncols-1} (Arnoldi step ncols - 1 was the last),
+ * each n_tris complex float32 values in the library's internal element
+ * order (one permutation for all, so V^H V is unchanged).  v_dev: device
+ * buffer of max_cols * n_tris cf32, receives min(ncols, max_cols) vectors
+ * one after the other; *n_cols receives ncols.  Waits for the copy.  Errors:
+ * BEM_E_ARG (bad argument, plane out of range or no solve yet). */
+int bem_krylov_basis(void *mesh, int32_t plane, void *v_dev, int32_t max_cols, int32_t *n_cols);
+
 /* Number of kernels this library has launched in this process. */
 uint64_t bem_launch_count(void);
 

@@ -144,6 +144,7 @@ def lib():
             "bem_selftest_sincos": (ctypes.c_int, [P, i64, P, P]),
             "bem_matvec_direct_noalloc": (ctypes.c_int, [P, i64, P, i64, d, ctypes.POINTER(Medium), P, P, P]),
             "bem_test_hooks": (ctypes.c_int, [i64, ctypes.POINTER(i64)]),
+            "bem_krylov_basis": (ctypes.c_int, [P, i32, P, i32, ctypes.POINTER(i32)]),
             "bem_launch_count": (ctypes.c_uint64, []),
             "bem_last_error": (ctypes.c_char_p, []),
         }
@@ -581,6 +582,16 @@ class Mesh:
         med = self._medium(c, rho)
         _check(lib().bem_mesh_blocks(self._h, float(freq), ctypes.byref(med), out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+    def krylov_basis(self, plane=0, max_cols=1024):
+        """The last GMRES cycle's basis vectors as a [cols, n] complex64 device
+        tensor (internal element order)."""
+        import torch
+        v = torch.empty((max_cols, self.n), dtype=torch.complex64, device="cuda")
+        nc = ctypes.c_int32(0)
+        _check(lib().bem_krylov_basis(self._h, int(plane), _dptr(v, max_cols * self.n), int(max_cols),
+                                      ctypes.byref(nc)))
+        return v[:min(nc.value, max_cols)]
 
     def release_plan(self):
         """Free the per-frequency plan; the next call rebuilds it."""

@@ -2120,6 +2120,7 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
         if (oa[r].next.wts) oa[r].next.wts = M.wts.p + r * n;
         oa[r].wnear = M.ynear.p + r * n;
         oa[r].acc = M.gsacc.p + 8 * r;
+        oa[r].g.gs_acc = oa[r].acc;
         oa[r].h2 = M.gsh2.p + (int64_t)2 * (m + 1) * r;
         oa[r].rows = orows;
     }
@@ -3353,6 +3354,30 @@ int bem_test_hooks(int64_t alloc_fail_after, int64_t *live_device_bytes)
     g_alloc_budget.store(alloc_fail_after < 0 ? -1 : alloc_fail_after);
     if (live_device_bytes) *live_device_bytes = g_live_bytes.load();
     return BEM_OK;
+}
+
+int bem_krylov_basis(void *mesh, int32_t plane, void *v_dev, int32_t max_cols, int32_t *n_cols)
+{
+    if (!mesh || !v_dev || max_cols < 0 || !n_cols) return set_err(BEM_E_ARG, "bad argument");
+    auto &M = *(bem_mesh_impl *)mesh;
+    try {
+        if (!M.st.p || !M.V.p || plane < 0 || (size_t)(plane + 1) > M.st.n)
+            return set_err(BEM_E_ARG, "no GMRES state for this right-hand side");
+        ck(cudaSetDevice(M.device), "cudaSetDevice");
+        ck(cudaStreamSynchronize(M.s), "sync");
+        GmresState st;
+        ck(cudaMemcpy(&st, M.st.p + plane, sizeof st, cudaMemcpyDeviceToHost), "D2H state");
+        const int64_t n = M.n;
+        const int64_t vplane = (int64_t)(M.V.n / M.st.n);
+        const int nc = std::min<int>(st.ncols, max_cols);
+        if (nc > 0)
+            ck(cudaMemcpy(v_dev, M.V.p + plane * vplane, (size_t)nc * n * sizeof(float2), cudaMemcpyDeviceToDevice),
+               "D2D basis");
+        *n_cols = st.ncols;
+        return BEM_OK;
+    } catch (Fail &f) {
+        return f.code;
+    }
 }
 
 int bem_mesh_check_host(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t n_tris, double *volume,

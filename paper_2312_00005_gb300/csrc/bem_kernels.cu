@@ -2064,8 +2064,11 @@ __device__ double gs_load_h(const double2 *src, int64_t stride, float2 *hs, int 
     return s_hh;
 }
 
-// DGKS test from the FP64 sums: ||w_1||^2 = ||w||^2 - |h|^2 < 0.01 ||w||^2.
-__device__ __forceinline__ bool gs_second_pass(double ww, double hh) { return ww - hh < 0.01 * ww; }
+// DGKS test from the FP64 sums with the classical threshold 1/sqrt(2):
+// ||w_1||^2 = ||w||^2 - |h|^2 < ||w||^2 / 2.  (A threshold of 0.1 let the
+// FP32 basis lose orthogonality roughly as eps / relres over a GMRES cycle:
+// 0.02 after 19 steps, 1 after 53.)
+__device__ __forceinline__ bool gs_second_pass(double ww, double hh) { return ww - hh < 0.5 * ww; }
 
 __global__ void __launch_bounds__(kGsThreads) k_gs_dots(GsArgs a)
 {
@@ -2086,13 +2089,20 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_dots(GsArgs a)
     const int j = jd.x, done = jd.y;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->skip_prod = done;
     if (done) return;
+    // v_j was stored unnormalised (||v_j||^2 = st->nn, set by k_gm_givens of
+    // step j - 1, or 1 by k_gm_start): scale the block's rows of v_j and of
+    // the product
+    const float sc = (float)(1.0 / sqrt(__ldcv(&st->nn)));
+    float2 *vj = g.V + (int64_t)j * g.n + r0;
     __shared__ float2 ws[kGsMaxRows];
 #pragma unroll
     for (int u = 0; u < kWr; ++u) {
         const int i = threadIdx.x + u * kGsThreads;
         if (i < R) {
-            ws[i] = wv[u];
-            g.w[r0 + i] = wv[u];
+            const float2 wsc = cscale(wv[u], sc);
+            ws[i] = wsc;
+            g.w[r0 + i] = wsc;
+            if (j > 0) vj[i] = cscale(vj[i], sc);
         }
     }
     __syncthreads();
@@ -2123,23 +2133,21 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_update(GsArgs a)
     if (need) gs_dots_part(a, ws, R, r0, j, a.h2 + (int64_t)(j & 1) * (g.m + 1), 1);
 }
 
-// v_{j+1} = ws / sqrt(nn) over the block's rows, with the next product's
-// inputs; block 0 keeps the books of step j: H column j takes the second
-// pass's h_2 (when there was one), nn goes to the state, and the other
-// parity's sums are cleared for step j + 1.
-__device__ void gs_normalise(const GsArgs &a, const float2 *ws, int R, int64_t r0, int j, double nn, bool need)
+// v_{j+1} = ws (unnormalised; its squared norm is in the sums) over the
+// block's rows, with the next product's inputs; block 0 keeps the books of
+// step j: H column j takes the second pass's h_2 (when there was one), and
+// the other parity's sums are cleared for step j + 1.
+__device__ void gs_store(const GsArgs &a, const float2 *ws, int R, int64_t r0, int j, bool need)
 {
     const GmresArgs &g = a.g;
     GmresState *st = g.st;
-    const float nf = (float)nn;
-    const float sc = nf > 0.f ? 1.f / sqrtf(nf) : 0.f;
     float2 *vn = g.V + (int64_t)(j + 1) * g.n;
     for (int i = threadIdx.x; i < R; i += kGsThreads) {
-        const float2 xv = cscale(ws[i], sc);
+        const float2 xv = ws[i];
         vn[r0 + i] = xv;
         prep_store(a.next, r0 + i, xv);
     }
-    if (need || blockIdx.x == 0) {   // after a second pass: the last block (the only caller)
+    if (blockIdx.x == 0) {
         const double2 *h2 = a.h2 + (int64_t)(j & 1) * (g.m + 1);
         if (need)
             for (int l = threadIdx.x; l <= j; l += kGsThreads) {
@@ -2150,10 +2158,7 @@ __device__ void gs_normalise(const GsArgs &a, const float2 *ws, int R, int64_t r
         double2 *h2n = a.h2 + (int64_t)((j + 1) & 1) * (g.m + 1);
         for (int l = threadIdx.x; l <= j + 1 && l <= g.m; l += kGsThreads) h2n[l] = make_double2(0.0, 0.0);
         if (threadIdx.x < 4) a.acc[4 * ((j + 1) & 1) + threadIdx.x] = 0.0;
-        if (threadIdx.x == 0) {
-            st->n_reorth += need;
-            st->nn = nn;
-        }
+        if (threadIdx.x == 0) st->n_reorth += need;
     }
 }
 
@@ -2170,41 +2175,17 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_finish(GsArgs a)
     __shared__ float2 hs[kMaxRestart + 1];
     for (int i = threadIdx.x; i < R; i += kGsThreads) ws[i] = g.w[r0 + i];
     const bool need = __ldcv(&st->reorth) != 0;      // k_gs_update's decision
-    if (!need) {
-        // ||w_1||^2 summed by k_gs_update
-        gs_normalise(a, ws, R, r0, j, __ldcg(a.acc + 4 * (j & 1) + 1), false);
-        return;
+    if (need) {
+        // second pass: w_2 = w_1 - V h_2 and its partial ||w_2||^2 (summed, as
+        // every norm here: when w_1 is mostly rounding noise inside span(V),
+        // ||w_1||^2 - |h_2|^2 would cancel to nothing)
+        gs_load_h(a.h2 + (int64_t)(j & 1) * (g.m + 1), 1, hs, j);
+        gs_update(a, ws, hs, R, r0, j);
+        gs_norm_part(ws, R, a.acc + 4 * (j & 1) + 2);
+    } else {
+        __syncthreads();
     }
-    // second pass: w_2 = w_1 - V h_2 and its partial ||w_2||^2 (summed, as
-    // every norm here: when w_1 is mostly rounding noise inside span(V),
-    // ||w_1||^2 - |h_2|^2 would cancel to nothing); the last block to finish
-    // normalises every row (second passes are rare, so this keeps a launch
-    // off the common path)
-    gs_load_h(a.h2 + (int64_t)(j & 1) * (g.m + 1), 1, hs, j);
-    gs_update(a, ws, hs, R, r0, j);
-    for (int i = threadIdx.x; i < R; i += kGsThreads) g.w[r0 + i] = ws[i];
-    gs_norm_part(ws, R, a.acc + 4 * (j & 1) + 2);
-    __shared__ bool s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned int *cnt = reinterpret_cast<unsigned int *>(a.acc + 4 * (j & 1) + 3);
-        s_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const double nn = __ldcg(a.acc + 4 * (j & 1) + 2);
-    const float nf = (float)nn;
-    const float sc = nf > 0.f ? 1.f / sqrtf(nf) : 0.f;
-    float2 *vn = g.V + (int64_t)(j + 1) * g.n;
-    for (int64_t i = threadIdx.x; i < g.n; i += kGsThreads) {
-        const float2 xv = cscale(__ldcg(g.w + i), sc);
-        vn[i] = xv;
-        prep_store(a.next, i, xv);
-    }
-    // the books of block 0 in gs_normalise, with no rows of its own
-    gs_normalise(a, ws, 0, 0, j, nn, true);
+    gs_store(a, ws, R, r0, j, need);
 }
 
 // Givens step of the column the Gram-Schmidt kernels just formed (one warp).
@@ -2212,7 +2193,12 @@ __global__ void k_gm_givens(GmresArgs a)
 {
     GmresState *st = a.st;
     if (*(volatile int *)&st->done) return;
-    gm_givens_warp(a, st->nn, st->j);
+    // ||v_{j+1}||^2 from the Gram-Schmidt sums (after the second pass when
+    // there was one); k_gs_dots of step j + 1 scales v_{j+1} by it
+    const int j = st->j;
+    const double nn = __ldcg(a.gs_acc + 4 * (j & 1) + (*(volatile int *)&st->reorth ? 2 : 1));
+    if (threadIdx.x == 0) st->nn = nn;
+    gm_givens_warp(a, nn, j);
 }
 
 // st[0].skip_all = every plane's skip_prod (the product kernels of several
@@ -2307,6 +2293,7 @@ __global__ void k_gm_start(GmresState *st, float2 *__restrict__ V, const float2 
         if (first) st->bnorm = beta;
         st->beta = beta;
         st->j = 0;
+        st->nn = 1.0;      // v_0 is stored normalised
         st->ncols = 0;
         st->done = 0;
         st->skip_prod = 0;

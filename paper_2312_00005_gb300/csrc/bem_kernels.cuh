@@ -334,11 +334,16 @@ struct GmresArgs {
     double2 *H, *cs, *sn, *g;
     double *normpart;        // [nblk] norm partials
     int m;
+    const double *gs_acc;    // the Gram-Schmidt sums [2][4] (k_gm_givens reads ||v_{j+1}||^2 there)
 };
 
 // One Gram-Schmidt step of the Arnoldi process in three launches
-// (k_gs_dots, k_gs_update, k_gs_finish) with no waits between blocks: each
-// reduction is finished by the last block to arrive.
+// (k_gs_dots, k_gs_update, k_gs_finish) with no waits between blocks: sums
+// are FP64 atomic additions of the blocks' partials, read by the next
+// launch.  v_{j+1} is stored unnormalised with its squared norm in the sums;
+// k_gm_givens takes the norm (h_{j+1,j}) from there, and the next step's
+// k_gs_dots scales its rows of v_{j+1} and of the product A v_{j+1} (formed
+// from the unnormalised vector; the product is linear).
 struct GsArgs {
     GmresArgs g;             // g.nblk = gridDim.x
     PrepArgs next;           // inputs of the next product, formed from V_{j+1}
