@@ -1953,6 +1953,9 @@ __device__ __forceinline__ void atomic_add_c(double2 *p, float2 v)
     atomicAdd(&p->y, (double)v.y);
 }
 
+// (The basis is read through L1 here and in gs_update: a block reads only
+// its own rows, which k_gs_update reads twice, for the update and then the
+// second pass's dots.)
 // Partial dots sum_{i in block} conj(V_l[i]) ws[i], l <= j, added into
 // dst[l * stride]: warp w takes the columns l = w (mod 8), four at a time,
 // its lanes the rows, so that every warp keeps several independent loads in
@@ -1973,7 +1976,7 @@ __device__ void gs_dots_part(const GsArgs &a, const float2 *ws, int R, int64_t r
             for (int u = 0; u < 4; ++u) {
                 const int l = l0 + u * nwarp;
                 if (l <= j) {
-                    const float2 x = __ldcg(g.V + (int64_t)l * g.n + r0 + i);
+                    const float2 x = __ldca(g.V + (int64_t)l * g.n + r0 + i);
                     acc[u].x = fmaf(x.x, y.x, fmaf(x.y, y.y, acc[u].x));
                     acc[u].y = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc[u].y));
                 }
@@ -2021,7 +2024,7 @@ __device__ void gs_update(const GsArgs &a, float2 *ws, const float2 *hs, int R, 
             const float2 *vp = g.V + r0 + i;
 #pragma unroll 8
             for (int l = cg; l <= j; l += kCg) {
-                const float2 v = __ldcg(vp + (int64_t)l * g.n);
+                const float2 v = __ldca(vp + (int64_t)l * g.n);
                 const float2 h = hs[l];
                 acc.x = fmaf(h.x, v.x, fmaf(-h.y, v.y, acc.x));
                 acc.y = fmaf(h.x, v.y, fmaf(h.y, v.x, acc.y));
