@@ -402,14 +402,15 @@ def residual_vs_fp64(W, p, args, nrows=48):
 
 # DRAM traffic of one k_near_spmv_items launch from an ncu capture of this
 # workload with the tree the timed run chooses (leaf depth 4):
-# dram__bytes_read.sum 288.49 MB + dram__bytes_write.sum 3.15 MB = 291.64 MB,
-# 1.014 x the algorithmic 287.7 MB, taken with
-#   ncu --set full --clock-control none -k regex:k_near_spmv_items -s 45 -c 1 \
+# dram__bytes_read.sum 288.44 MB + dram__bytes_write.sum 2.80 MB = 291.24 MB,
+# 1.012 x the algorithmic 287.7 MB, taken with
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
+#       --clock-control none -k regex:k_near_spmv_items -s 45 -c 1 \
 #       python bench.py --steps 1 --warmup 3 --no-cpu-baseline --leaf-edge 0.0126
 # Valid only while the kernel's source and launch and the plan (near_nnz)
 # are the ones captured (the source hash below guards it).
-SPMV_TRAFFIC = {"source_sha256": "32082caf313f0d59cf420cac3dee7d59af1bd02e739ef517ed2c5684672ba875",
-                "near_nnz": 35925668, "bytes": 291635968}
+SPMV_TRAFFIC = {"source_sha256": "a7fef4cf6bccf4e82a272ac4743a8d4977c3ddf924e3189cd306f2b2b50762c7",
+                "near_nnz": 35925668, "bytes": 291244288}
 
 
 def _spmv_source_hash():
