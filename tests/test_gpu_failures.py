@@ -1,8 +1,9 @@
 """Failure paths of the library on the GPU, reached without a GPU fault
 (bem_test_hooks): a device allocation that fails must come back as an error
 code, leave the mesh usable and leak no device memory.  (No kernel of the
-library waits on another block or launch, so there is no device wait whose
-running out could be tested.)"""
+library waits on another block or launch; the one device wait, the
+tensor-core aggregation's bounded wait for its own MMAs, is not forced to
+give up, since that would free tensor memory under MMAs in flight.)"""
 import numpy as np
 import pytest
 
