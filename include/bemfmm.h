@@ -60,8 +60,9 @@ extern "C" {
                                      message names the element */
 #define BEM_E_CUDA            -3  /* a CUDA call failed */
 #define BEM_E_OOM             -4  /* device allocation failed */
-#define BEM_E_TIMEOUT         -5  /* reserved: no device code of this library waits on another
-                                     block or launch, so no call returns it */
+#define BEM_E_TIMEOUT         -5  /* a bounded device wait gave up: the tensor-core aggregation's
+                                      wait for its own MMAs (far_precision 1); no device code of
+                                      this library waits on another block or launch */
 #define BEM_E_INTERNAL        -6
 #define BEM_W_NOT_CONVERGED    1  /* GMRES stopped at max_iter above tol (cf. Sec. 3.2 warning) */
 #define BEM_W_UNDERRESOLVED    2  /* mean edge longer than a sixth of the wavelength (Sec. 2.2) */
