@@ -135,6 +135,11 @@ typedef struct bem_params {
                                several); an even number in 64..4096: that many for any
                                number of right-hand sides.  Results agree to rounding order
                                of the row sums.  Other values: BEM_E_ARG.                     */
+    int32_t gs_rows;        /* GMRES Gram-Schmidt step: rows of the basis per block (its sums
+                               are FP64 atomic additions of the blocks' partials, one per
+                               basis column and block).  0 (default): 128, or more to keep the
+                               blocks at most 1024; 64..1024 otherwise.  Results agree to the
+                               summation order.  Other values: BEM_E_ARG.                     */
     int32_t field_mode;     /* bem_evaluate: 1 the direct sum over every element with the rules
                                of Sec. 3.1 at each point; 2 (FMM meshes) near elements by the
                                same rules and the rest through the plane-wave expansions of

@@ -1768,6 +1768,7 @@ void bem_params_default(bem_params *p)
     p->block_jacobi = 0;
     p->far_precision = 0;
     p->near_chunk = 0;
+    p->gs_rows = 0;
     p->field_mode = 0;
 }
 
@@ -1799,6 +1800,8 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
     if (p.near_chunk != 0 && (p.near_chunk < 64 || p.near_chunk > 4096 || (p.near_chunk & 1)))
         return set_err(BEM_E_ARG, "near_chunk must be 0 or an even number in 64..4096");
     if (p.field_mode < 0 || p.field_mode > 2) return set_err(BEM_E_ARG, "field_mode must be 0, 1 or 2");
+    if (p.gs_rows != 0 && (p.gs_rows < 64 || p.gs_rows > kGsMaxRows))
+        return set_err(BEM_E_ARG, "gs_rows must be 0 or in 64..1024");
     if (p.block_jacobi && p.row_scaling)
         return set_err(BEM_E_ARG, "row_scaling and block_jacobi are alternatives: set at most one");
     if (!(p.quad_tol > 0) || !(p.rt_subdiv > 0) || !(p.admissibility > 0) || p.L_min < 1 || p.L_min > 200)
@@ -2067,12 +2070,13 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     M.g_.alloc((size_t)nr * (m + 1));
     M.yv.alloc((size_t)nr * (m + 1));
     // the Gram-Schmidt step: block b owns rows [b R, b R + R), R <= kGsMaxRows
-    // (staged in shared memory); 64 rows per block, so that many blocks keep
-    // many loads of the basis in flight, and more when that would exceed
-    // about 1024 blocks (each block adds its partial sums atomically)
+    // (staged in shared memory); 128 rows per block (measured against 64,
+    // 256 and 512: 64 made twice the atomic additions, the larger ones kept
+    // fewer loads of the basis in flight), and more when that would exceed
+    // about 1024 blocks
     int nblk = 0;
     {
-        const int64_t rows = std::max<int64_t>(64, (n + 1023) / 1024);
+        const int64_t rows = M.prm.gs_rows > 0 ? (int64_t)M.prm.gs_rows : std::max<int64_t>(128, (n + 1023) / 1024);
         nblk = (int)std::max<int64_t>(1, (n + rows - 1) / rows);
     }
     const int orows = (int)((n + nblk - 1) / nblk);
