@@ -282,9 +282,7 @@ struct Lists {
     // its mirror (tsym)
     DevArr<int> trow_ptr, trow_i;
     DevArr<int64_t> trow_off;
-    bool tsym = false, trow_ready = false;
-    std::vector<std::pair<int, int>> h_tent;   // per leaf t (h_tptr): (leaf s, column of t in s's rows)
-    std::vector<int> h_tptr;
+    bool tsym = false, trow_checked = false, trow_ready = false;
     std::vector<int64_t> h_row_ptr;
     // block-Jacobi sub-blocks (first element, size, offset of the inverse)
     std::vector<int4> h_bj;
@@ -517,49 +515,16 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
     // near columns of each leaf as runs of consecutive leaves
     std::vector<int> run_ptr(nl + 1, 0), ncol(nl, 0);
     std::vector<int2> runs;
-    std::vector<int> colpos(F.near_src.size());   // column of near entry q's first element
     for (int t = 0; t < nl; ++t) {
         int pos = 0, prev = -2;
         for (int q = F.near_ptr[t]; q < F.near_ptr[t + 1]; ++q) {
             const int sl = F.near_src[q];
             if (sl != prev + 1) runs.push_back(make_int2((int)Lf.start[sl], pos));
-            colpos[q] = pos;
             pos += (int)Lf.count[sl];
             prev = sl;
         }
         ncol[t] = pos;
         run_ptr[t + 1] = (int)runs.size();
-    }
-    {
-        // transposed near product: for leaf t and each s in its near list,
-        // the column of t's first element in s's rows (s must list t)
-        std::vector<std::pair<int64_t, int>> key;   // (s nl + listed leaf, column)
-        key.reserve(F.near_src.size());
-        for (int s2 = 0; s2 < nl; ++s2)
-            for (int q = F.near_ptr[s2]; q < F.near_ptr[s2 + 1]; ++q)
-                key.emplace_back((int64_t)s2 * nl + F.near_src[q], colpos[q]);
-        std::sort(key.begin(), key.end());
-        std::vector<std::pair<int, int>> tent;   // (leaf s, column of t in s's rows)
-        std::vector<int> tptr(nl + 1, 0);
-        bool sym = true;
-        for (int t = 0; t < nl && sym; ++t) {
-            for (int q = F.near_ptr[t]; q < F.near_ptr[t + 1]; ++q) {
-                const int sl = F.near_src[q];
-                if (Lf.count[sl] == 0 || Lf.count[t] == 0) continue;
-                const auto it = std::lower_bound(key.begin(), key.end(), std::make_pair((int64_t)sl * nl + t, INT_MIN));
-                if (it == key.end() || it->first != (int64_t)sl * nl + t) {
-                    sym = false;
-                    break;
-                }
-                tent.emplace_back(sl, it->second);
-            }
-            tptr[t + 1] = (int)tent.size();
-        }
-        Ls->tsym = sym;
-        if (sym) {
-            Ls->h_tent = std::move(tent);
-            Ls->h_tptr = std::move(tptr);
-        }
     }
     std::vector<int> leaf_of(M.n);
     std::vector<int64_t> row_ptr(M.n + 1, 0), leaf_start(nl + 1, M.n);
@@ -607,7 +572,7 @@ std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
         Ls->bj.upload(Ls->h_bj, s);
     }
     Ls->nnz = row_ptr[M.n];
-    if (Ls->tsym) Ls->h_row_ptr = row_ptr;
+    Ls->h_row_ptr = row_ptr;   // for the transposed product's rows, built when first needed
     Ls->leaf_of.upload(leaf_of, s);
     Ls->run_ptr.upload(run_ptr, s);
     Ls->ncol.upload(ncol, s);
@@ -1394,17 +1359,37 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
 void ensure_transposed_rows(bem_mesh_impl &M)
 {
     Lists &Ls = *fr(M).plan->lists;
-    if (!Ls.tsym || Ls.trow_ready || !M.prm.near_store || Ls.fp.direct) return;
-    const Level &Lf = M.t.lv[Ls.fp.leaf_depth];
+    if (Ls.trow_checked || !M.prm.near_store || Ls.fp.direct) return;
+    Ls.trow_checked = true;
+    const FreqPlan &F = Ls.fp;
+    const Level &Lf = M.t.lv[F.leaf_depth];
     const int nl = (int)Lf.start.size();
+    // the column of each near entry's first element in its row leaf's list,
+    // and per (row leaf s, listed leaf) that column, sorted for lookups
+    std::vector<std::pair<int64_t, int>> key;
+    key.reserve(F.near_src.size());
+    for (int s2 = 0; s2 < nl; ++s2) {
+        int pos = 0;
+        for (int q = F.near_ptr[s2]; q < F.near_ptr[s2 + 1]; ++q) {
+            key.emplace_back((int64_t)s2 * nl + F.near_src[q], pos);
+            pos += (int)Lf.count[F.near_src[q]];
+        }
+    }
+    std::sort(key.begin(), key.end());
+    // per leaf t, every row i of its near leaves with the position of A_i,t0
+    // (row_ptr[i] + the column of t in i's row); every near pair must have
+    // its mirror, else the transposed product recomputes its entries
     std::vector<int> rptr(nl + 1, 0), ri;
     std::vector<int64_t> roff;
     for (int t = 0; t < nl; ++t) {
-        for (int e = Ls.h_tptr[t]; e < Ls.h_tptr[t + 1]; ++e) {
-            const int sl = Ls.h_tent[e].first, col = Ls.h_tent[e].second;
+        for (int q = F.near_ptr[t]; q < F.near_ptr[t + 1]; ++q) {
+            const int sl = F.near_src[q];
+            if (Lf.count[sl] == 0 || Lf.count[t] == 0) continue;
+            const auto it = std::lower_bound(key.begin(), key.end(), std::make_pair((int64_t)sl * nl + t, INT_MIN));
+            if (it == key.end() || it->first != (int64_t)sl * nl + t) return;   // tsym stays false
             for (int64_t i = Lf.start[sl]; i < Lf.start[sl] + Lf.count[sl]; ++i) {
                 ri.push_back((int)i);
-                roff.push_back(Ls.h_row_ptr[i] + col);
+                roff.push_back(Ls.h_row_ptr[i] + it->second);
             }
         }
         if (ri.size() > (size_t)INT_MAX) throw Fail{set_err(BEM_E_ARG, "transposed near rows exceed 2^31")};
@@ -1415,6 +1400,7 @@ void ensure_transposed_rows(bem_mesh_impl &M)
     Ls.trow_i.upload(ri, s);
     Ls.trow_off.upload(roff, s);
     ck(cudaStreamSynchronize(s), "sync");
+    Ls.tsym = true;
     Ls.trow_ready = true;
 }
 
@@ -1532,6 +1518,10 @@ void autotune_leaf_depth(bem_mesh_impl &M, double k)
     std::vector<std::tuple<int, double, std::shared_ptr<Lists>>> cand;
     for (int d = M.leaf_depth - 1; d <= M.leaf_depth + 1; ++d) {
         if (d < 1 || d > M.t.leaf_depth) continue;
+        // a deeper candidate whose leaves average under 8 elements is not
+        // tried: its lists (tens of millions of leaf pairs on large meshes)
+        // take longer to build than the tuner can gain
+        if (d > M.leaf_depth && (double)n < 8.0 * (double)M.t.lv[d].start.size()) continue;
         bem_params gp = M.prm;
         gp.stability_max = 1e308;
         FreqPlan fp;
