@@ -878,7 +878,7 @@ def run_multi(args):
         "mesh_seconds": round(t_mesh, 2), "clocks": clocks,
         "config": {"workload": W["name"], "n_elements": n, "freq_hz": f, "sweep_step_hz": 0.25,
                    "rhs": "4 plane waves, tetrahedral directions", "gmres_budget_products": budget,
-                   "gmres_restart": restart, "block_jacobi": mkw["block_jacobi"], "autotune": mkw["autotune"], "gmres_tol": args.tol,
+                   "gmres_restart": restart, "block_jacobi": mkw["block_jacobi"], "gmres_tol": args.tol,
                    "trunc_factor": args.trunc_factor, "far_precision": args.far_precision,
                    "near_chunk": args.near_chunk, "solve_call": "bem_solve_multi (4 right-hand sides together)"},
     }))
