@@ -131,7 +131,7 @@ typedef struct bem_params {
                                form's accuracy).  Other values: BEM_E_ARG.                     */
     int32_t near_chunk;     /* stored near-field product: columns of a leaf's near list staged
                                in shared memory per pass.  0 (default): the library's choice
-                               (every column at once for one right-hand side, 1024 for
+                               (every column at once for one right-hand side, 512 for
                                several); an even number in 64..4096: that many for any
                                number of right-hand sides.  Results agree to rounding order
                                of the row sums.  Other values: BEM_E_ARG.                     */

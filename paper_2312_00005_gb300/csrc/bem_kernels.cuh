@@ -164,7 +164,7 @@ __global__ void k_near_spmv_t(const int64_t *leaf_start, const int *trow_ptr, co
 // apart in x and y): the stored values are streamed once for all of them.
 // The leaf's columns are staged in chunks of cw (even) columns: dynamic
 // shared memory nr * cw * 8 bytes, small enough for several blocks per SM.
-constexpr int kSpmvMultiChunk = 1024;
+constexpr int kSpmvMultiChunk = 512;
 __global__ void k_near_spmv_items_multi(NearArgs a, const int4 *items, const float2 *val, const float2 *x, float2 *y,
                                         int nr, int64_t plane, int cw, const int *skip);
 __global__ void k_near_fused(NearArgs a, const float2 *x, float2 *y, int *err, const int *skip);
