@@ -245,7 +245,8 @@ constexpr int kMaxPlanes = 4;            // right-hand sides per multi-plane lau
 // fault is set when the wait for the tensor cores runs out.
 constexpr int kTcThreads = 256;
 constexpr int kTcPairs = 128;
-constexpr size_t kTcSmemBytes = 2 * (size_t)kTcPairs * 4 * kAggChunk * 2 + 2 * (size_t)4 * kMaxPlanes * 4 * kAggChunk * 2 +
+constexpr int kTcSub = 16;               // elements per pass of the MMAs (a chunk takes up to four)
+constexpr size_t kTcSmemBytes = 2 * (size_t)kTcPairs * 4 * kTcSub * 2 + 2 * (size_t)4 * kMaxPlanes * 4 * kTcSub * 2 +
                                 1024;
 __global__ void k_aggregate_tc(const LevelsArgs *A, const AggTask *tasks, const float4 *wts, int64_t wplane,
                                const float4 *nrm, int nr, int *fault, const int *skip);

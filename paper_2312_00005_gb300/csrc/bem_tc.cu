@@ -35,10 +35,10 @@ namespace bem {
 namespace {
 
 constexpr int kTcM = 128;                  // direction pairs per tile (MMA M)
-constexpr int kTcK = 4 * kAggChunk;        // 256: four reals per element (MMA K total)
+constexpr int kTcK = 4 * kTcSub;           // 64: four reals per element of a sub-chunk (MMA K per pass)
 constexpr int kTcN = 4 * kMaxPlanes;       // 16: four reals per right-hand side (MMA N)
-constexpr uint32_t kTcSmemA = kTcM * kTcK * 2;          // one BF16 part of A: 64 KB
-constexpr uint32_t kTcSmemB = kTcN * kTcK * 2;          // one BF16 part of B: 8 KB
+constexpr uint32_t kTcSmemA = kTcM * kTcK * 2;          // one BF16 part of A: 16 KB
+constexpr uint32_t kTcSmemB = kTcN * kTcK * 2;          // one BF16 part of B: 2 KB
 constexpr uint32_t kTcLboA = (kTcM / 8) * 128, kTcSboA = 128;   // 2048, 128
 constexpr uint32_t kTcLboB = (kTcN / 8) * 128, kTcSboB = 128;   // 256, 128
 constexpr uint32_t kTcStepA = 2 * kTcLboA, kTcStepB = 2 * kTcLboB;   // bytes per K step of 16
@@ -77,29 +77,44 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-__device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c, __nv_bfloat16 d)
+// (a, b) = hi + lo, both parts as BF16 pairs (two values per conversion;
+// the same roundings as split_bf16 on each value).
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t &hi, uint32_t &lo)
 {
-    const uint32_t lo = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-    const uint32_t hi = (uint32_t)__bfloat16_as_ushort(c) | ((uint32_t)__bfloat16_as_ushort(d) << 16);
-    return make_uint2(lo, hi);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
 // Stores (v0, v1, v2, v3) as hi and lo parts at one 8-byte place of two tiles.
 __device__ __forceinline__ void store_split4(unsigned char *hi_tile, unsigned char *lo_tile, uint32_t off, float v0,
                                              float v1, float v2, float v3)
 {
-    __nv_bfloat16 h0, h1, h2, h3, l0, l1, l2, l3;
-    split_bf16(v0, h0, l0);
-    split_bf16(v1, h1, l1);
-    split_bf16(v2, h2, l2);
-    split_bf16(v3, h3, l3);
-    *reinterpret_cast<uint2 *>(hi_tile + off) = pack4(h0, h1, h2, h3);
-    *reinterpret_cast<uint2 *>(lo_tile + off) = pack4(l0, l1, l2, l3);
+    uint32_t h01, l01, h23, l23;
+    split_bf16x2(v0, v1, h01, l01);
+    split_bf16x2(v2, v3, h23, l23);
+    *reinterpret_cast<uint2 *>(hi_tile + off) = make_uint2(h01, h23);
+    *reinterpret_cast<uint2 *>(lo_tile + off) = make_uint2(l01, l23);
+}
+
+// Bounded wait for the completion of phase `parity` of the barrier the MMAs
+// signal: false when it ran out (the caller sets the fault flag).
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
+{
+    uint32_t ready = 0;
+    for (unsigned int it = 0; it < kTcSpin && !ready; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, q;\n\t}"
+            : "=r"(ready) : "r"(addr), "r"(parity) : "memory");
+    }
+    return ready != 0;
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_aggregate_tc(const LevelsArgs *__restrict__ A,
+__global__ void __launch_bounds__(kTcThreads, 4) k_aggregate_tc(const LevelsArgs *__restrict__ A,
                                                                 const AggTask *__restrict__ tasks,
                                                                 const float4 *__restrict__ wts, int64_t wplane,
                                                                 const float4 *__restrict__ nrm, int nr, int *fault,
@@ -137,80 +152,96 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_aggregate_tc(const LevelsArgs
         sd[q] = make_float4(kt * d.x, kt * d.y, kt * d.z, 0.f);
         sn[q] = nrm[j];
     }
-    // B: element q's four rows, right-hand side r's four columns (zero
-    // beyond ne elements and nr right-hand sides)
-    for (int idx = threadIdx.x; idx < kAggChunk * (kTcN / 4); idx += kTcThreads) {
-        const int q = idx / (kTcN / 4), r = idx % (kTcN / 4);
-        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (q < T.ne && r < nr) w = wts[r * wplane + T.e0 + q];
-        const float ar = w.x, ai = w.y, cr = w.z, ci = w.w;
-        // rows 4q .. 4q + 3 (Re E, Im E, Re F, Im F), columns 4r .. 4r + 3
-        const float rows[4][4] = {{ar, ai, ar, ai}, {-ai, ar, ai, -ar}, {cr, ci, -cr, -ci}, {-ci, cr, -ci, cr}};
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                __nv_bfloat16 hi, lo;
-                split_bf16(rows[e][c], hi, lo);
-                const uint32_t off = b_off(4 * r + c, 4 * q + e);
-                *reinterpret_cast<__nv_bfloat16 *>(Bhi + off) = hi;
-                *reinterpret_cast<__nv_bfloat16 *>(Blo + off) = lo;
-            }
-    }
-    __syncthreads();
-    // A: thread takes direction pair p (fixed) and every other element
-    const int p = threadIdx.x & (kTcM - 1);
-    const bool pv = T.p0 + p < h;
-    const float4 sv = pv ? f.dirs[T.p0 + p] : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int q = threadIdx.x / kTcM; q < kAggChunk; q += kTcThreads / kTcM) {
-        float er = 0.f, ei = 0.f, fr = 0.f, fi = 0.f;
-        if (pv && q < T.ne) {
-            const float4 d = sd[q], n = sn[q];
-            sincos_turns(fmaf(d.x, sv.x, fmaf(d.y, sv.y, d.z * sv.z)), &ei, &er);
-            const float t = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
-            fr = t * er;
-            fi = t * ei;
-        }
-        store_split4(Ahi, Alo, a_off(p, 4 * q), er, ei, fr, fi);
-    }
-    // the operands written by the threads are read by the tensor cores
-    // (async proxy)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    // tcgen05.alloc wrote the tensor-memory address into shared memory
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    if (threadIdx.x == 0) {
-        // only the K steps that hold elements
-        const int ksteps = (4 * T.ne + 15) / 16;
-        const uint32_t aH = smem_u32(Ahi), aL = smem_u32(Alo), bH = smem_u32(Bhi), bL = smem_u32(Blo);
-        uint32_t acc = 0;
-        for (int term = 0; term < 3; ++term) {
-            const uint32_t a0 = term == 2 ? aL : aH;   // hi hi, hi lo, lo hi
-            const uint32_t b0 = term == 1 ? bL : bH;
-            for (int st = 0; st < ksteps; ++st) {
-                const uint64_t ad = smem_desc(a0 + st * kTcStepA, kTcLboA, kTcSboA);
-                const uint64_t bd = smem_desc(b0 + st * kTcStepB, kTcLboB, kTcSboB);
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                    :: "r"(tmem), "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc) : "memory");
-                acc = 1;
+    const uint32_t mb = smem_u32(&mbar);
+    const int p = threadIdx.x & (kTcM - 1);
+    const bool pv = T.p0 + p < h;
+    const float4 sv = pv ? f.dirs[T.p0 + p] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // the chunk in passes of kTcSub elements, the MMAs of every pass adding
+    // into the same accumulator; a pass rewrites the operands only after the
+    // previous pass's MMAs have completed
+    const int npass = (T.ne + kTcSub - 1) / kTcSub;
+    bool ok = true;
+    for (int ps = 0; ps < npass && ok; ++ps) {
+        const int q0 = ps * kTcSub, qn = min(kTcSub, T.ne - q0);
+        if (ps > 0) {
+            // the same decision in every thread (a wait that ran out in any
+            // thread ends the passes for the whole block)
+            ok = __syncthreads_and(mbar_wait(mb, (uint32_t)((ps - 1) & 1)) ? 1 : 0) != 0;
+            if (!ok) {
+                if (threadIdx.x == 0) atomicExch(fault, 1);
+                break;
             }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(smem_u32(&mbar)) : "memory");
+        // B: element q's four rows, right-hand side r's four columns (zero
+        // beyond the pass's elements and nr right-hand sides)
+        for (int idx = threadIdx.x; idx < kTcSub * (kTcN / 4); idx += kTcThreads) {
+            const int q = idx / (kTcN / 4), r = idx % (kTcN / 4);
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q < qn && r < nr) w = wts[r * wplane + T.e0 + q0 + q];
+            const float ar = w.x, ai = w.y, cr = w.z, ci = w.w;
+            // rows 4q .. 4q + 3 (Re E, Im E, Re F, Im F), columns 4r .. 4r + 3
+            const float rows[4][4] = {{ar, ai, ar, ai}, {-ai, ar, ai, -ar}, {cr, ci, -cr, -ci}, {-ci, cr, -ci, cr}};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    __nv_bfloat16 hi, lo;
+                    split_bf16(rows[e][c], hi, lo);
+                    const uint32_t off = b_off(4 * r + c, 4 * q + e);
+                    *reinterpret_cast<__nv_bfloat16 *>(Bhi + off) = hi;
+                    *reinterpret_cast<__nv_bfloat16 *>(Blo + off) = lo;
+                }
+        }
+        // A: thread takes direction pair p (fixed) and every other element
+        for (int q = threadIdx.x / kTcM; q < kTcSub; q += kTcThreads / kTcM) {
+            float er = 0.f, ei = 0.f, fr = 0.f, fi = 0.f;
+            if (pv && q < qn) {
+                const float4 d = sd[q0 + q], n = sn[q0 + q];
+                sincos_turns(fmaf(d.x, sv.x, fmaf(d.y, sv.y, d.z * sv.z)), &ei, &er);
+                const float t = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
+                fr = t * er;
+                fi = t * ei;
+            }
+            store_split4(Ahi, Alo, a_off(p, 4 * q), er, ei, fr, fi);
+        }
+        // the operands written by the threads are read by the tensor cores
+        // (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (threadIdx.x == 0) {
+            // only the K steps that hold elements
+            const int ksteps = (4 * qn + 15) / 16;
+            const uint32_t aH = smem_u32(Ahi), aL = smem_u32(Alo), bH = smem_u32(Bhi), bL = smem_u32(Blo);
+            uint32_t acc = ps > 0 ? 1u : 0u;
+            for (int term = 0; term < 3; ++term) {
+                const uint32_t a0 = term == 2 ? aL : aH;   // hi hi, hi lo, lo hi
+                const uint32_t b0 = term == 1 ? bL : bH;
+                for (int st = 0; st < ksteps; ++st) {
+                    const uint64_t ad = smem_desc(a0 + st * kTcStepA, kTcLboA, kTcSboA);
+                    const uint64_t bd = smem_desc(b0 + st * kTcStepB, kTcLboB, kTcSboB);
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                        :: "r"(tmem), "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc) : "memory");
+                    acc = 1;
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(mb) : "memory");
+        }
     }
-    // wait for the MMAs (bounded: a wait that runs out sets the fault flag,
-    // which the host reports, instead of hanging the GPU)
+    // wait for the last pass's MMAs (bounded: a wait that runs out sets the
+    // fault flag, which the host reports, instead of hanging the GPU)
     if (warp < 4) {
-        uint32_t ready = 0;
-        for (unsigned int it = 0; it < kTcSpin && !ready; ++it) {
-            asm volatile(
-                "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\n\t"
-                "selp.u32 %0, 1, 0, q;\n\t}"
-                : "=r"(ready) : "r"(smem_u32(&mbar)) : "memory");
-        }
+        const bool ready = ok && mbar_wait(mb, (uint32_t)((npass - 1) & 1));
         if (!ready && lane == 0) atomicExch(fault, 1);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // row 32 warp + lane of the accumulator: pair p0 + 32 warp + lane
