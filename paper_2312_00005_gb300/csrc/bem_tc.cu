@@ -70,15 +70,8 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                               ((uint32_t)(kTcM >> 4) << 24);
 
-// x = hi + lo with both parts BF16.
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
-{
-    hi = __float2bfloat16_rn(x);
-    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-}
-
 // (a, b) = hi + lo, both parts as BF16 pairs (two values per conversion;
-// the same roundings as split_bf16 on each value).
+// each value rounded to BF16, then its remainder).
 __device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t &hi, uint32_t &lo)
 {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -178,25 +171,24 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_aggregate_tc(const LevelsArgs
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
-        // B: element q's four rows, right-hand side r's four columns (zero
-        // beyond the pass's elements and nr right-hand sides)
-        for (int idx = threadIdx.x; idx < kTcSub * (kTcN / 4); idx += kTcThreads) {
-            const int q = idx / (kTcN / 4), r = idx % (kTcN / 4);
+        // B: thread (element q, column n) forms element q's four rows (Re E,
+        // Im E, Re F, Im F) of column n = 4 r + c (right-hand side r, its
+        // (Re M, Im M, Re M', Im M') column c), zero beyond the pass's
+        // elements and nr right-hand sides; the four rows are consecutive in
+        // K, one 8-byte store per part
+        {
+            static_assert(kTcThreads == kTcSub * kTcN, "one thread per (element, column) of B");
+            const int q = threadIdx.x / kTcN, nn = threadIdx.x % kTcN;
+            const int r = nn >> 2, c = nn & 3;
             float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
             if (q < qn && r < nr) w = wts[r * wplane + T.e0 + q0 + q];
             const float ar = w.x, ai = w.y, cr = w.z, ci = w.w;
-            // rows 4q .. 4q + 3 (Re E, Im E, Re F, Im F), columns 4r .. 4r + 3
-            const float rows[4][4] = {{ar, ai, ar, ai}, {-ai, ar, ai, -ar}, {cr, ci, -cr, -ci}, {-ci, cr, -ci, cr}};
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    __nv_bfloat16 hi, lo;
-                    split_bf16(rows[e][c], hi, lo);
-                    const uint32_t off = b_off(4 * r + c, 4 * q + e);
-                    *reinterpret_cast<__nv_bfloat16 *>(Bhi + off) = hi;
-                    *reinterpret_cast<__nv_bfloat16 *>(Blo + off) = lo;
-                }
+            // rows[e][c] = {{ar, ai, ar, ai}, {-ai, ar, ai, -ar}, {cr, ci, -cr, -ci}, {-ci, cr, -ci, cr}}
+            const float v0 = (c & 1) ? ai : ar;
+            const float v1 = c == 0 ? -ai : (c == 1 ? ar : (c == 2 ? ai : -ar));
+            const float v2 = (c & 1) ? ((c == 1) ? ci : -ci) : ((c == 0) ? cr : -cr);
+            const float v3 = (c & 1) ? cr : -ci;
+            store_split4(Bhi, Blo, b_off(nn, 4 * q), v0, v1, v2, v3);
         }
         // A: thread takes direction pair p (fixed) and every other element
         for (int q = threadIdx.x / kTcM; q < kTcSub; q += kTcThreads / kTcM) {
