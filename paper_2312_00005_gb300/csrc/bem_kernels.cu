@@ -424,16 +424,31 @@ __global__ void __launch_bounds__(kSpmvTThreads) k_near_spmv_t(const int64_t *__
         float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
         int k = k0 + warp * R + sub;
         const int step = kW * R;
-        for (; k + step < k1; k += 2 * step) {
-            const int i0 = trow_i[k], i1 = trow_i[k + step];
-            const int64_t o0 = trow_off[k], o1 = trow_off[k + step];
-            const float2 xa = x[i0], xb = x[i1];
-            if (live) {
-                acc0 = cfma(__ldcs(val + o0 + c0 + jj), xa, acc0);
-                acc1 = cfma(__ldcs(val + o1 + c0 + jj), xb, acc1);
+        // kTU rows per warp step: their positions first, then all their
+        // values and x in flight together
+        constexpr int kTU = 4;
+        for (; k + (kTU - 1) * step < k1; k += kTU * step) {
+            int iv[kTU];
+            int64_t ov[kTU];
+#pragma unroll
+            for (int u = 0; u < kTU; ++u) {
+                iv[u] = trow_i[k + u * step];
+                ov[u] = trow_off[k + u * step];
+            }
+            float2 xv[kTU], vv[kTU];
+#pragma unroll
+            for (int u = 0; u < kTU; ++u) {
+                xv[u] = x[iv[u]];
+                vv[u] = live ? __ldcs(val + ov[u] + c0 + jj) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kTU; u += 2) {
+                acc0 = cfma(vv[u], xv[u], acc0);
+                acc1 = cfma(vv[u + 1], xv[u + 1], acc1);
             }
         }
-        if (k < k1 && live) acc0 = cfma(__ldcs(val + trow_off[k] + c0 + jj), x[trow_i[k]], acc0);
+        for (; k < k1; k += step)
+            if (live) acc0 = cfma(__ldcs(val + trow_off[k] + c0 + jj), x[trow_i[k]], acc0);
         float2 acc = cadd(acc0, acc1);
         // add the R sub-rows (lanes jj, jj + w, ...) in a fixed order
         for (int o = w; o < 32; o <<= 1) {
