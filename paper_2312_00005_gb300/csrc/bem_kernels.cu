@@ -1980,15 +1980,16 @@ __device__ void gs_dots_part(const GsArgs &a, const float2 *ws, int R, int64_t r
     const GmresArgs &g = a.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nwarp = kGsThreads / 32;
-    for (int l0 = warp; l0 <= j; l0 += 4 * nwarp) {
-        float2 acc[4];
+    constexpr int kC = 8;     // columns per warp at a time (their loads in flight together)
+    for (int l0 = warp; l0 <= j; l0 += kC * nwarp) {
+        float2 acc[kC];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
+        for (int u = 0; u < kC; ++u) acc[u] = make_float2(0.f, 0.f);
 #pragma unroll 2
         for (int i = lane; i < R; i += 32) {
             const float2 y = ws[i];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kC; ++u) {
                 const int l = l0 + u * nwarp;
                 if (l <= j) {
                     const float2 x = __ldca(g.V + (int64_t)l * g.n + r0 + i);
@@ -1998,7 +1999,7 @@ __device__ void gs_dots_part(const GsArgs &a, const float2 *ws, int R, int64_t r
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kC; ++u) {
             const int l = l0 + u * nwarp;
             const float2 d = warp_sum(acc[u]);
             if (lane == u && l <= j) atomic_add_c(dst + (int64_t)l * stride, d);
@@ -2030,31 +2031,40 @@ __device__ void gs_update(const GsArgs &a, float2 *ws, const float2 *hs, int R, 
 {
     const GmresArgs &g = a.g;
     constexpr int kRowsPerPass = 64, kCg = kGsThreads / kRowsPerPass;
-    __shared__ float2 cpart[kGsThreads];
+    __shared__ float2 cpart[2][kGsThreads];
     const int cg = threadIdx.x / kRowsPerPass, rr = threadIdx.x % kRowsPerPass;
-    for (int i0 = 0; i0 < R; i0 += kRowsPerPass) {
-        const int i = i0 + rr;
-        float2 acc = make_float2(0.f, 0.f);
-        if (i < R) {
-            const float2 *vp = g.V + r0 + i;
+    // two passes of rows at a time, so each thread has the loads of two rows
+    // in flight
+    for (int i0 = 0; i0 < R; i0 += 2 * kRowsPerPass) {
+        const int ia = i0 + rr, ib = i0 + kRowsPerPass + rr;
+        const bool va = ia < R, vb = ib < R;
+        float2 acca = make_float2(0.f, 0.f), accb = acca;
+        const float2 *pa = g.V + r0 + ia, *pb = g.V + r0 + ib;
 #pragma unroll 8
-            for (int l = cg; l <= j; l += kCg) {
-                const float2 v = __ldca(vp + (int64_t)l * g.n);
-                const float2 h = hs[l];
-                acc.x = fmaf(h.x, v.x, fmaf(-h.y, v.y, acc.x));
-                acc.y = fmaf(h.x, v.y, fmaf(h.y, v.x, acc.y));
-            }
+        for (int l = cg; l <= j; l += kCg) {
+            const float2 h = hs[l];
+            const int64_t o = (int64_t)l * g.n;
+            const float2 v = va ? __ldca(pa + o) : make_float2(0.f, 0.f);
+            const float2 w = vb ? __ldca(pb + o) : make_float2(0.f, 0.f);
+            acca.x = fmaf(h.x, v.x, fmaf(-h.y, v.y, acca.x));
+            acca.y = fmaf(h.x, v.y, fmaf(h.y, v.x, acca.y));
+            accb.x = fmaf(h.x, w.x, fmaf(-h.y, w.y, accb.x));
+            accb.y = fmaf(h.x, w.y, fmaf(h.y, w.x, accb.y));
         }
-        cpart[threadIdx.x] = acc;
+        cpart[0][threadIdx.x] = acca;
+        cpart[1][threadIdx.x] = accb;
         __syncthreads();
-        if (cg == 0 && i < R) {
-            float2 c = cpart[rr];
+        if (cg < 2) {
+            const int i = cg == 0 ? ia : ib;
+            if (i < R) {
+                float2 c = cpart[cg][rr];
 #pragma unroll
-            for (int q = 1; q < kCg; ++q) {
-                c.x += cpart[rr + q * kRowsPerPass].x;
-                c.y += cpart[rr + q * kRowsPerPass].y;
+                for (int q = 1; q < kCg; ++q) {
+                    c.x += cpart[cg][rr + q * kRowsPerPass].x;
+                    c.y += cpart[cg][rr + q * kRowsPerPass].y;
+                }
+                ws[i] = make_float2(ws[i].x - c.x, ws[i].y - c.y);
             }
-            ws[i] = make_float2(ws[i].x - c.x, ws[i].y - c.y);
         }
         __syncthreads();
     }
