@@ -402,15 +402,15 @@ def residual_vs_fp64(W, p, args, nrows=48):
 
 # DRAM traffic of one k_near_spmv_items launch from an ncu capture of this
 # workload with the tree the timed run chooses (leaf depth 4):
-# dram__bytes_read.sum 288.44 MB + dram__bytes_write.sum 2.80 MB = 291.24 MB,
-# 1.012 x the algorithmic 287.7 MB, taken with
+# dram__bytes_read.sum 288.65 MB + dram__bytes_write.sum 2.79 MB = 291.44 MB,
+# 1.013 x the algorithmic 287.7 MB, taken with
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
 #       --clock-control none -k regex:k_near_spmv_items -s 45 -c 1 \
 #       python bench.py --steps 1 --warmup 3 --no-cpu-baseline --leaf-edge 0.0126
 # Valid only while the kernel's source and launch and the plan (near_nnz)
 # are the ones captured (the source hash below guards it).
-SPMV_TRAFFIC = {"source_sha256": "a7fef4cf6bccf4e82a272ac4743a8d4977c3ddf924e3189cd306f2b2b50762c7",
-                "near_nnz": 35925668, "bytes": 291244288}
+SPMV_TRAFFIC = {"source_sha256": "db2463538395424353b36850b2d41a4b78dc3f4392a9654b16dd22976cd5a783",
+                "near_nnz": 35925668, "bytes": 291443712}
 
 
 def _spmv_source_hash():

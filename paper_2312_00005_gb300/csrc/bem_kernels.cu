@@ -288,6 +288,16 @@ __global__ void k_near_spmv(NearArgs a, const float2 *__restrict__ val, const fl
 // One block per item: items are small, so the block scheduler balances the
 // work across SMs (and shares them with the far-field kernels running
 // beside) whatever the leaf sizes.
+// Streamed 16-byte load of stored values: read-only path, no L1 allocation,
+// and an L2 fetch of the surrounding 256 bytes (the next lanes' values).
+__device__ __forceinline__ float4 ld_stream4(const float4 *p)
+{
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+
 __device__ __forceinline__ float2 spmv_segment(const float2 *__restrict__ v, const float2 *__restrict__ xs, int c0,
                                                int c1, int lane)
 {
@@ -301,7 +311,7 @@ __device__ __forceinline__ float2 spmv_segment(const float2 *__restrict__ v, con
     for (; q + 224 < qe; q += 256) {
         float4 vv[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) vv[u] = __ldcs(v4 + q + 32 * u);
+        for (int u = 0; u < 8; ++u) vv[u] = ld_stream4(v4 + q + 32 * u);
 #pragma unroll
         for (int u = 0; u < 8; u += 2) {
             const float4 xa = x4[q + 32 * u], xb = x4[q + 32 * (u + 1)];
@@ -314,7 +324,7 @@ __device__ __forceinline__ float2 spmv_segment(const float2 *__restrict__ v, con
     for (; q + 96 < qe; q += 128) {
         float4 vv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) vv[u] = __ldcs(v4 + q + 32 * u);
+        for (int u = 0; u < 4; ++u) vv[u] = ld_stream4(v4 + q + 32 * u);
 #pragma unroll
         for (int u = 0; u < 4; u += 2) {
             const float4 xa = x4[q + 32 * u], xb = x4[q + 32 * (u + 1)];
@@ -325,7 +335,7 @@ __device__ __forceinline__ float2 spmv_segment(const float2 *__restrict__ v, con
         }
     }
     for (; q < qe; q += 32) {
-        const float4 vv = __ldcs(v4 + q), xa = x4[q];
+        const float4 vv = ld_stream4(v4 + q), xa = x4[q];
         acc0 = cfma(make_float2(vv.x, vv.y), make_float2(xa.x, xa.y), acc0);
         acc1 = cfma(make_float2(vv.z, vv.w), make_float2(xa.z, xa.w), acc1);
     }
@@ -482,7 +492,7 @@ __device__ __forceinline__ void spmv_segment_multi(const float2 *__restrict__ v,
     for (; q + 96 < qe; q += 128) {
         float4 vv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) vv[u] = __ldcs(v4 + q + 32 * u);
+        for (int u = 0; u < 4; ++u) vv[u] = ld_stream4(v4 + q + 32 * u);
 #pragma unroll
         for (int r = 0; r < kMaxPlanes; ++r) {
             if (r >= nr) break;
@@ -496,7 +506,7 @@ __device__ __forceinline__ void spmv_segment_multi(const float2 *__restrict__ v,
         }
     }
     for (; q < qe; q += 32) {
-        const float4 vv = __ldcs(v4 + q);
+        const float4 vv = ld_stream4(v4 + q);
 #pragma unroll
         for (int r = 0; r < kMaxPlanes; ++r) {
             if (r >= nr) break;
