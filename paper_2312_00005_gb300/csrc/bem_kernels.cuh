@@ -89,7 +89,7 @@ struct AggTask {
 // Disaggregation work item: elements [x, y) of one leaf, at most kDisTask,
 // one block of kDisThreads threads each.
 constexpr int kDisTask = 16;
-constexpr int kDisThreads = 64;
+constexpr int kDisThreads = 128;
 
 struct FarArgs {
     int nd;                  // 2 L^2 directions
