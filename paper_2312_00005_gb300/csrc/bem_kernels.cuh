@@ -74,7 +74,7 @@ struct PrepArgs {
 // cluster c and the antipodal direction pairs [p0, p0 + kAggThreads),
 // written to row `row` of the multipole buffer (row c when the cluster is
 // one element chunk).
-constexpr int kAggThreads = 64;
+constexpr int kAggThreads = 128;
 constexpr int kAggChunk = 64;
 struct AggTask {
     int c, row;
