@@ -871,6 +871,8 @@ def run_multi(args):
         "higher_is_better": True, "dtype": "cf32" if args.far_precision == 0 else "cf32 + split-bf16 aggregation",
         "data": "synthetic", "products_per_step": prods / args.steps,
         "relres_reached": [i["relres"] for i in infos],
+        "relres_kind": ("GMRES estimate of the preconditioned residual" if args.far_precision == 0 else
+                        "true residual of the unpreconditioned FP32 operator (refinement)"),
         "rel_error": {"product_vs_fp64_rows": errs, "rows_per_rhs": args.check_rows},
         "kernels_one_product_ms": kern,
         "plan": {kk: st[kk] for kk in ("levels", "L", "n_clusters", "n_interactions", "near_nnz", "leaf_edge",
