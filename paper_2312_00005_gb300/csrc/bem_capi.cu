@@ -461,11 +461,10 @@ struct bem_mesh_impl {
     // side stream and events of the GMRES Givens steps inside one graph
     cudaStream_t s_giv = nullptr;
     cudaEvent_t ev_orth[kStepsPerGraph] = {}, ev_giv[kStepsPerGraph] = {};
-    // GMRES status after each graph: two pinned host copies and their events,
-    // so that the next graph is queued before the host waits for a status
+    // GMRES status after each Arnoldi cycle (or step, with event timing):
+    // pinned host copies of every plane's state (room for two copies)
     GmresState *h_st = nullptr;
     int h_st_planes = 0;                       // planes h_st holds per copy (two copies)
-    cudaEvent_t ev_st[2] = {};
     std::vector<float> coef_key;
 
     ElemDev elem() const
@@ -482,8 +481,6 @@ struct bem_mesh_impl {
             if (ev_orth[t]) cudaEventDestroy(ev_orth[t]);
             if (ev_giv[t]) cudaEventDestroy(ev_giv[t]);
         }
-        for (int t = 0; t < 2; ++t)
-            if (ev_st[t]) cudaEventDestroy(ev_st[t]);
         if (h_st) cudaFreeHost(h_st);
         if (s_giv) cudaStreamDestroy(s_giv);
         if (s_setup) cudaStreamDestroy(s_setup);
@@ -1864,7 +1861,6 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
                 ck(cudaEventCreateWithFlags(&M->ev_orth[t], cudaEventDisableTiming), "event");
                 ck(cudaEventCreateWithFlags(&M->ev_giv[t], cudaEventDisableTiming), "event");
             }
-            for (int t = 0; t < 2; ++t) ck(cudaEventCreateWithFlags(&M->ev_st[t], cudaEventDisableTiming), "event");
             ck(cudaMallocHost(&M->h_st, 2 * sizeof(GmresState)), "cudaMallocHost");
             M->h_st_planes = 1;
         }
@@ -2148,9 +2144,6 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
         prep_v0();
     };
     start(M.bvec.p, 1);
-    // one Arnoldi step, captured once as a graph and replayed
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
     // skip flag of the product kernels: uniform within every launch; with
     // several planes the product runs until every plane is done
     const int *done = nr == 1 ? &M.st.p->skip_prod : &M.st.p->skip_all;
@@ -2252,51 +2245,60 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
         }
         if (side) ck(cudaStreamWaitEvent(s, M.ev_giv[nsteps - 1], 0), "join givens");
     };
+    // Bodies of `batch` Arnoldi steps per cycle at most (the cycle's m
+    // steps and one body of skipped steps to spare).
+    const int max_graphs = (m + batch + batch - 1) / batch;
+    // With graphs, one Arnoldi cycle is one graph launch: a WHILE node whose
+    // body is `batch` Arnoldi steps and k_gm_continue, which sets the loop
+    // condition on the device (some plane not done, fewer than max_graphs
+    // bodies run), so the host waits once per cycle and no body is queued
+    // after the cycle has ended.
     uint64_t per_graph = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
     if (use_graph) {
+        ck(cudaGraphCreate(&graph, 0), "graph create");
+        cudaGraphConditionalHandle loop;
+        ck(cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault), "conditional handle");
+        cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};   // the rest zero
+        np.conditional.handle = loop;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        ck(cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &np), "conditional node");
+        cudaGraph_t body = np.conditional.phGraph_out[0];
         const uint64_t before = g_launches.load();
-        ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
+        ck(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal), "capture");
         arnoldi_steps(batch);
-        ck(cudaStreamEndCapture(s, &graph), "end capture");
+        k_gm_continue<<<1, 32, 0, s>>>(loop, M.st.p, nr, max_graphs);
+        ck_launch("k_gm_continue");
+        ck(cudaStreamEndCapture(s, &body), "end capture");
         per_graph = g_launches.load() - before;
         g_launches.fetch_sub(per_graph);   // captured, not launched
         ck(cudaGraphInstantiate(&gexec, graph, 0), "instantiate");
     }
     R.hp.assign(nr, GmresState());
     for (;;) {
-        // Arnoldi cycle.  With graphs, graph g + 1 is queued before the
-        // host waits for the status copied after graph g, so the GPU
-        // does not idle while the host reads it; a graph queued after
-        // the cycle ended runs its steps as skips.
-        const int max_graphs = (m + batch + batch - 1) / batch;
-        int launched = 0, checked = 0;
         product();
-        auto launch_graph = [&]() {
-            if (use_graph) {
-                ck(cudaGraphLaunch(gexec, s), "graph launch");
-                g_launches.fetch_add(per_graph);
-            } else {
+        if (use_graph) {
+            ck(cudaGraphLaunch(gexec, s), "graph launch");
+            ck(cudaMemcpyAsync(M.h_st, M.st.p, nr * sizeof(GmresState), cudaMemcpyDeviceToHost, s), "D2H st");
+            ck(cudaStreamSynchronize(s), "sync st");
+            g_launches.fetch_add(per_graph * (uint64_t)std::max(0, M.h_st[0].bodies));
+            for (int r = 0; r < nr; ++r) R.hp[r] = M.h_st[r];
+        } else {
+            // one step per status read (event timing: every kernel on one
+            // stream, timed alone)
+            for (int launched = 0; launched < max_graphs; ++launched) {
                 arnoldi_steps(1);
-            }
-            GmresState *dst = M.h_st + (launched & 1) * nr;
-            ck(cudaMemcpyAsync(dst, M.st.p, nr * sizeof *dst, cudaMemcpyDeviceToHost, s), "D2H st");
-            ck(cudaEventRecord(M.ev_st[launched & 1], s), "record st");
-            ++launched;
-        };
-        launch_graph();
-        for (;;) {
-            if (use_graph && launched < max_graphs) launch_graph();
-            ck(cudaEventSynchronize(M.ev_st[checked & 1]), "sync st");
-            bool all_done = true;
-            for (int r = 0; r < nr; ++r) {
-                R.hp[r] = M.h_st[(checked & 1) * nr + r];
-                all_done = all_done && R.hp[r].done;
-            }
-            ++checked;
-            if (all_done) break;
-            if (checked == launched) {
-                if (launched >= max_graphs) break;
-                launch_graph();
+                ck(cudaMemcpyAsync(M.h_st, M.st.p, nr * sizeof(GmresState), cudaMemcpyDeviceToHost, s), "D2H st");
+                ck(cudaStreamSynchronize(s), "sync st");
+                bool all_done = true;
+                for (int r = 0; r < nr; ++r) {
+                    R.hp[r] = M.h_st[r];
+                    all_done = all_done && R.hp[r].done;
+                }
+                if (all_done) break;
             }
         }
         for (int r = 0; r < nr; ++r) {
@@ -2493,7 +2495,6 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
         Plan &P = *fr(M).plan;
         cudaStream_t s = M.s;
         const int64_t n = M.n;
-        const int m = M.prm.restart;
         // right-hand side: incident field minus the known boundary data
         std::vector<SourceDev> sv = sources_of(srcs, n_src);
         DevArr<SourceDev> &sdev = M.srcbuf;

@@ -2249,6 +2249,21 @@ __global__ void k_gm_skip_all(GmresState *st, int nr)
     st[0].skip_all = all;
 }
 
+// The condition of the WHILE node that runs one Arnoldi cycle on the device
+// (each body a few Arnoldi steps, then this kernel, after every step of the
+// body, the Givens steps included, has finished): set to 1 while some plane
+// is not done and fewer than max_bodies bodies have run, so the loop ends
+// even if no plane ever reports done.
+__global__ void k_gm_continue(cudaGraphConditionalHandle h, GmresState *st, int nr, int max_bodies)
+{
+    if (threadIdx.x != 0) return;
+    int all = 1;
+    for (int r = 0; r < nr; ++r) all &= __ldcv(&st[r].done) != 0;
+    const int b = st[0].bodies + 1;
+    st[0].bodies = b;
+    cudaGraphSetConditional(h, (!all && b < max_bodies) ? 1u : 0u);
+}
+
 // Back substitution y = R^{-1} g over ncols columns (FP64), one warp:
 // column-oriented, each step scales one entry by the reciprocal of its
 // diagonal and the lanes update the rest.  The reciprocals 1 / R_ll are
@@ -2336,6 +2351,7 @@ __global__ void k_gm_start(GmresState *st, float2 *__restrict__ V, const float2 
         st->done = 0;
         st->skip_prod = 0;
         st->converged = 0;
+        st->bodies = 0;
         st->resid = st->bnorm > 0.0 ? beta / st->bnorm : 0.0;
         for (int l = 0; l <= m; ++l) g[l] = make_double2(0.0, 0.0);
         g[0] = make_double2(beta, 0.0);

@@ -54,6 +54,9 @@ struct GmresState {
     // With several right-hand sides (plane 0's state only): the product
     // kernels skip once every plane's skip_prod is set (k_gm_skip_all).
     int skip_all;
+    // Bodies of the device-driven Arnoldi loop run in the current cycle
+    // (plane 0's state; k_gm_continue counts, k_gm_start resets).
+    int bodies;
 };
 
 struct PrepArgs {
@@ -360,6 +363,9 @@ __global__ void k_gs_update(GsArgs a);
 __global__ void k_gs_finish(GsArgs a);
 __global__ void k_gm_givens(GmresArgs a);
 __global__ void k_gm_skip_all(GmresState *st, int nr);
+// Loop condition of the WHILE node of a device-driven Arnoldi cycle: one
+// more body while some plane is not done and fewer than max_bodies have run.
+__global__ void k_gm_continue(cudaGraphConditionalHandle h, GmresState *st, int nr, int max_bodies);
 __global__ void k_gm_backsolve(const GmresState *st, const double2 *H, const double2 *g, double2 *y, int m,
                                int smem_cols);
 __global__ void k_gm_xupdate(float2 *x, const float2 *V, int64_t n, const GmresState *st, const double2 *y);
