@@ -173,7 +173,7 @@ def run_ours(args):
     n = tris.shape[0]
     pts = W["field_points"]
     src = [bemfmm.plane_wave(W["plane_dir"], W["amp"])]
-    mkw = {"trunc_factor": args.trunc_factor, "near_chunk": args.near_chunk}
+    mkw = {"trunc_factor": args.trunc_factor, "near_chunk": args.near_chunk, "far_table": args.far_table}
     if args.restart > 0:
         mkw["restart"] = args.restart
     if args.leaf_edge > 0:
@@ -332,7 +332,7 @@ def run_ours(args):
         "config": {"workload": W["name"], "n_elements": n, "freq_hz": f, "sweep_step_hz": 0.25,
                    "mesh": "icosphere r=0.1 m",
                    "source": "plane wave +z", "field_points": int(pts.shape[0]), "gmres_tol": args.tol,
-                   "trunc_factor": args.trunc_factor, "near_chunk": args.near_chunk,
+                   "trunc_factor": args.trunc_factor, "near_chunk": args.near_chunk, "far_table": args.far_table,
                    "l2_flush": ("256 MB write between steps" if args.no_sweep else
                                 "256 MB write before the sweep; per step the stored near field (8 B x near_nnz, "
                                 "> L2) is streamed again"),
@@ -914,6 +914,8 @@ def main():
                     help="one bem_solve call per frequency (default: the steps as one bem_solve_sweep call)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="head_bands_c3: the automatic leaf size without the timing autotuner")
+    ap.add_argument("--far-table", type=int, default=0, choices=(0, 1),
+                    help="1: far-field phases stored once per frequency (default 0: regenerated per product)")
     ap.add_argument("--near-chunk", type=int, default=0,
                     help="columns staged per pass of the stored near-field product (0: the library's choice)")
     ap.add_argument("--leaf-edge", type=float, default=0.0,

@@ -149,6 +149,18 @@ typedef struct bem_params {
                                call with the same points and frequency); 0 (default): 2 on an
                                FMM mesh from 1e9 point-element pairs, else 1.  Other values:
                                BEM_E_ARG.                                                      */
+    int32_t far_table;      /* phases e^{ik (z_c - x_j).s} of the aggregation T(l) and, conjugated,
+                               of the disaggregation S(l) (Sec. 3.3.3) in products with one
+                               right-hand side (and the transposed product): 0 (default)
+                               regenerated in every product (one sine and cosine per element
+                               and antipodal direction pair); 1 computed once per frequency
+                               for every level, element and pair and stored, 8 bytes each
+                               (64 MB for 20,480 elements and 389 pairs over three levels), as
+                               the paper stores T and S, unless that would exceed 4 GiB; the
+                               products then read them instead.  The stored values are those
+                               the products regenerate, so the results are the same.
+                               Products with several right-hand sides always regenerate them
+                               (one phase serves all their planes).  Other values: BEM_E_ARG. */
 } bem_params;
 
 typedef struct bem_medium {

@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
         ("autotune", ctypes.c_int32), ("tau", ctypes.c_double), ("row_scaling", ctypes.c_int32),
         ("check_orientation", ctypes.c_int32), ("symmetric_far", ctypes.c_int32),
         ("block_jacobi", ctypes.c_int32), ("far_precision", ctypes.c_int32), ("near_chunk", ctypes.c_int32),
-        ("gs_rows", ctypes.c_int32), ("field_mode", ctypes.c_int32),
+        ("gs_rows", ctypes.c_int32), ("field_mode", ctypes.c_int32), ("far_table", ctypes.c_int32),
     ]
 
 

@@ -23,6 +23,9 @@
 
 using namespace bem;
 
+// Largest stored far-field phase table of a plan (far_table); above it the
+// products regenerate the phases.
+constexpr double kPhaseTableMaxBytes = 4.0 * 1024 * 1024 * 1024;
 // bem_evaluate with field_mode 0 takes the FMM path from this many
 // point-element pairs (below it the direct sum takes about as long as the
 // host build of the point plan)
@@ -305,9 +308,12 @@ struct LevelDev {
     DevArr<float4> dirs;
     DevArr<double> dirs_d;
     DevArr<float2> D, M, Lam;
+    DevArr<float2> ph;            // stored phases [n][phs] (far_table), else empty
+    int phs = 0;
     FarArgs args() const
     {
         FarArgs f;
+        memset(&f, 0, sizeof f);
         f.nd = nd;
         f.k = 0.f;
         f.dirs = dirs.p;
@@ -326,6 +332,8 @@ struct LevelDev {
         f.nred = ll->nred;
         f.dz = dd->dz.p;
         f.elem_cl = dd->elem_cl.p;
+        f.ph = ph.p;
+        f.phs = phs;
         return f;
     }
 };
@@ -343,6 +351,7 @@ struct Plan {
     DevArr<LevelsArgs> largs;     // device copy of the per-level arguments
     LevelsArgs hargs;
     DevArr<float2> val;
+    bool has_phases = false;      // every level's stored phases built (far_table)
     std::vector<float> val_key;   // host copy of the coefficients the stored values were made with
     bool val_valid = false;
     int64_t nnz() const { return lists->nnz; }
@@ -696,7 +705,8 @@ void recycle_plan(bem_mesh_impl &M)
     ck(cudaStreamSynchronize(fr(M).s), "sync");
     M.spare_val.swap(fr(M).plan->val);
     for (auto &L : fr(M).plan->lev) {
-        for (DevArr<float2> *b : {&L->D, &L->M, &L->Lam}) {
+        for (DevArr<float2> *b : {&L->D, &L->M, &L->Lam, &L->ph}) {
+            if (!b->p) continue;
             auto d = std::make_unique<DevArr<float2>>();
             d->swap(*b);
             M.spare_bufs.push_back(std::move(d));
@@ -773,6 +783,39 @@ void finish_plan(bem_mesh_impl &M, Plan &Pl)
                 k_dtable<<<nb, 128, 0, s>>>(ta);
             }
             ck_launch("k_dtable");
+        }
+    }
+    {
+        // the phases of the aggregation and (conjugated) of the
+        // disaggregation, once per frequency for every level, element and
+        // antipodal pair (far_table; single-right-hand-side products read
+        // them), unless they would take more than kPhaseTableMaxBytes
+        P->has_phases = false;
+        const int64_t n = M.n;
+        double bytes = 0.0;
+        for (const auto &D : P->lev) bytes += (double)n * (double)((D->nd / 2 + 1) & ~1) * sizeof(float2);
+        if (M.prm.far_table == 1 && !P->lev.empty() && bytes <= kPhaseTableMaxBytes) {
+            PhaseTableArgs pa;
+            memset(&pa, 0, sizeof pa);
+            pa.n = n;
+            pa.k = (float)k;
+            const int per = (int)((n + kPhaseElems - 1) / kPhaseElems);
+            int nb = 0;
+            for (const auto &D : P->lev) {
+                D->phs = (D->nd / 2 + 1) & ~1;
+                take_spare(M, D->ph, (size_t)n * D->phs);
+                pa.start[pa.nlev] = nb;
+                pa.lev[pa.nlev] = PhaseLevel{D->dd->dz.p, D->dirs.p, D->ph.p, D->nd / 2, D->phs};
+                nb += per;
+                ++pa.nlev;
+            }
+            pa.start[pa.nlev] = nb;
+            {
+                KTimer kt_("k_phase_table", s);
+                k_phase_table<<<nb, 128, 0, s>>>(pa);
+            }
+            ck_launch("k_phase_table");
+            P->has_phases = true;
         }
     }
     LevelsArgs &A = P->hargs;
@@ -1226,7 +1269,10 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
         {
             KTimer kt_("k_aggregate", sf);
             switch (nr) {
-                case 1: k_aggregate_1<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, n, M.nrm.p, skip); break;
+                case 1:
+                    if (P.has_phases) k_aggregate_1t<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, n, M.nrm.p, skip);
+                    else k_aggregate_1<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, n, M.nrm.p, skip);
+                    break;
                 case 2: k_aggregate_2<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, n, M.nrm.p, skip); break;
                 case 3: k_aggregate_3<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, n, M.nrm.p, skip); break;
                 default: k_aggregate_4<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, n, M.nrm.p, skip); break;
@@ -1323,8 +1369,9 @@ void matvec_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, bool 
         KTimer kt_("k_disaggregate", sd);
         if (P.lists->n_dis_tasks > 0) {
             if (nr == 1) {
-                k_disaggregate_m1<<<P.lists->n_dis_tasks, kDisThreads, 0, sd>>>(da, far_only ? nullptr : M.ynear.p, y,
-                                                                               skip);
+                const float2 *yn = far_only ? nullptr : M.ynear.p;
+                if (P.has_phases) k_disaggregate_m1t<<<P.lists->n_dis_tasks, kDisThreads, 0, sd>>>(da, yn, y, skip);
+                else k_disaggregate_m1<<<P.lists->n_dis_tasks, kDisThreads, 0, sd>>>(da, yn, y, skip);
             } else {
                 // the planes in groups of four (or two): one phase per element
                 // and direction pair serves a whole group
@@ -1433,7 +1480,8 @@ void matvec_t_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, con
     if (A.ntasks > 0) {
         {
             KTimer kt_("k_aggregate", sf);
-            k_aggregate_1<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, n, M.nrm.p, skip);
+            if (P.has_phases) k_aggregate_1t<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, n, M.nrm.p, skip);
+            else k_aggregate_1<<<A.ntasks, kAggThreads, 0, sf>>>(P.largs.p, M.wts.p, n, M.nrm.p, skip);
         }
         ck_launch("k_aggregate");
     }
@@ -1478,9 +1526,11 @@ void matvec_t_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, con
     da.tasks = P.lists->dis_tasks.p;
     {
         KTimer kt_("k_disaggregate_t", s);
-        if (P.lists->n_dis_tasks > 0)
-            k_disaggregate_t<<<P.lists->n_dis_tasks, kDisThreads, 0, s>>>(da, far_only ? nullptr : M.ynear.p, y,
-                                                                          skip);
+        const float2 *yn = far_only ? nullptr : M.ynear.p;
+        if (P.lists->n_dis_tasks > 0) {
+            if (P.has_phases) k_disaggregate_tt<<<P.lists->n_dis_tasks, kDisThreads, 0, s>>>(da, yn, y, skip);
+            else k_disaggregate_t<<<P.lists->n_dis_tasks, kDisThreads, 0, s>>>(da, yn, y, skip);
+        }
     }
     ck_launch("k_disaggregate_t");
 }
@@ -1757,6 +1807,7 @@ void bem_params_default(bem_params *p)
     p->near_chunk = 0;
     p->gs_rows = 0;
     p->field_mode = 0;
+    p->far_table = 0;
 }
 
 const char *bem_last_error(void) { return g_err.c_str(); }
@@ -1787,6 +1838,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
     if (p.near_chunk != 0 && (p.near_chunk < 64 || p.near_chunk > 4096 || (p.near_chunk & 1)))
         return set_err(BEM_E_ARG, "near_chunk must be 0 or an even number in 64..4096");
     if (p.field_mode < 0 || p.field_mode > 2) return set_err(BEM_E_ARG, "field_mode must be 0, 1 or 2");
+    if (p.far_table != 0 && p.far_table != 1) return set_err(BEM_E_ARG, "far_table must be 0 or 1");
     if (p.gs_rows != 0 && (p.gs_rows < 64 || p.gs_rows > kGsMaxRows))
         return set_err(BEM_E_ARG, "gs_rows must be 0 or in 64..1024");
     if (p.block_jacobi && p.row_scaling)
@@ -3503,7 +3555,7 @@ int bem_mesh_stats(void *mesh, double freq_hz, const bem_medium *medium, bem_pla
         int64_t bytes = 0;
         bytes += M.chi.bytes() * 6 + M.cd.bytes() * 4 + M.ad.bytes() + M.perm.bytes();
         bytes += P.lists->runs.bytes() + P.lists->row_ptr.bytes() + P.val.bytes();
-        for (auto &L : P.lev) bytes += L->D.bytes() + L->M.bytes() + L->Lam.bytes();
+        for (auto &L : P.lev) bytes += L->D.bytes() + L->M.bytes() + L->Lam.bytes() + L->ph.bytes();
         for (auto &kv : M.depth_dev) bytes += kv.second->dz.bytes() + kv.second->elem_cl.bytes();
         out->device_bytes = bytes;
         return BEM_OK;

@@ -964,29 +964,41 @@ __global__ void k_prep(PrepArgs a, const int *skip)
     prep_store(a, i, a.perm ? xb[a.perm[i]] : xb[i]);
 }
 
+// Streamed 8-byte load of a stored phase (read once per product): read-only
+// path, no L1 allocation.
+__device__ __forceinline__ float2 ld_stream2(const float2 *p)
+{
+    float2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+
 // Aggregation (Sec. 3.3.3, matrix T(l) with the centroid rule): for every
 // source cluster c and direction s_nu,
 //   M_c(nu) = sum_{j in c} e^{ik (z_c - x_j).s_nu} (alpha_j + c_j (n_j . s_nu)).
 // One block per task: a chunk of at most kAggChunk elements of one cluster
 // and kAggThreads antipodal direction pairs, one pair per thread; phases in
-// turns.  Tasks of equal size keep every block short, so no large cluster
-// sets the kernel's length.  For a cluster split into several element
-// chunks, the last of its blocks to finish sums the chunks' partial rows in
-// row order.
-template <int NR>
+// turns, regenerated (kTab false) or read from the level's stored phases
+// (kTab, the same values: k_phase_table evaluates the same expression).
+// Tasks of equal size keep every block short, so no large cluster sets the
+// kernel's length.  For a cluster split into several element chunks, the
+// last of its blocks to finish sums the chunks' partial rows in row order.
+template <int NR, bool kTab>
 __device__ __forceinline__ void aggregate_body(const LevelsArgs *__restrict__ A, const float4 *__restrict__ wts,
                                                int64_t wplane, const float4 *__restrict__ nrm)
 {
     const AggTask T = A->tasks[blockIdx.x];
     const FarArgs &f = A->lev[T.lev];
-    __shared__ float4 sd[kAggChunk];       // (z_c - x_j) k / (2 pi)
-    __shared__ float4 sw[NR][kAggChunk];   // (alpha_j, c_j) per right-hand side
-    __shared__ float4 sn[kAggChunk];       // n_j
+    __shared__ float4 sd[kTab ? 1 : kAggChunk];   // (z_c - x_j) k / (2 pi)
+    __shared__ float4 sw[NR][kAggChunk];           // (alpha_j, c_j) per right-hand side
+    __shared__ float4 sn[kAggChunk];               // n_j
     const float kt = f.k * 0.15915494309189535f;
     for (int q = threadIdx.x; q < T.ne; q += blockDim.x) {
         const int64_t j = T.e0 + q;
-        const float4 d = f.dz[j];
-        sd[q] = make_float4(kt * d.x, kt * d.y, kt * d.z, 0.f);
+        if (!kTab) {
+            const float4 d = f.dz[j];
+            sd[q] = make_float4(kt * d.x, kt * d.y, kt * d.z, 0.f);
+        }
 #pragma unroll
         for (int r = 0; r < NR; ++r) sw[r][q] = wts[r * wplane + j];
         sn[q] = nrm[j];
@@ -1002,10 +1014,9 @@ __device__ __forceinline__ void aggregate_body(const LevelsArgs *__restrict__ A,
         float2 accp[NR], accm[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) accp[r] = accm[r] = make_float2(0.f, 0.f);
-        for (int q = 0; q < T.ne; ++q) {
-            const float4 d = sd[q], n = sn[q];
-            float sn0, cs0;
-            sincos_turns(fmaf(d.x, sv.x, fmaf(d.y, sv.y, d.z * sv.z)), &sn0, &cs0);
+        // element q of the chunk with the phase cs0 + i sn0
+        auto term = [&](int q, float sn0, float cs0) {
+            const float4 n = sn[q];
             const float t = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
@@ -1018,6 +1029,29 @@ __device__ __forceinline__ void aggregate_body(const LevelsArgs *__restrict__ A,
                 accm[r].x = fmaf(cs0, wm.x, fmaf(sn0, wm.y, accm[r].x));
                 accm[r].y = fmaf(cs0, wm.y, fmaf(-sn0, wm.x, accm[r].y));
             }
+        };
+        if (kTab) {
+            // the chunk's rows of stored phases, 16 loads per thread in flight
+            const float2 *__restrict__ ph = f.ph + (int64_t)T.e0 * f.phs + p;
+            int q = 0;
+            for (; q + 16 <= T.ne; q += 16) {
+                float2 e[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) e[u] = ld_stream2(ph + (int64_t)(q + u) * f.phs);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) term(q + u, e[u].y, e[u].x);
+            }
+            for (; q < T.ne; ++q) {
+                const float2 e = ld_stream2(ph + (int64_t)q * f.phs);
+                term(q, e.y, e.x);
+            }
+        } else {
+            for (int q = 0; q < T.ne; ++q) {
+                const float4 d = sd[q];
+                float sn0, cs0;
+                sincos_turns(fmaf(d.x, sv.x, fmaf(d.y, sv.y, d.z * sv.z)), &sn0, &cs0);
+                term(q, sn0, cs0);
+            }
         }
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
@@ -1028,19 +1062,50 @@ __device__ __forceinline__ void aggregate_body(const LevelsArgs *__restrict__ A,
     aggregate_reduce(A, T, f, kAggThreads, NR);
 }
 
-#define BEM_AGGREGATE_KERNEL(NR)                                                                                      \
+#define BEM_AGGREGATE_KERNEL(NR, TAB, NAME)                                                                           \
     __global__ void __launch_bounds__(kAggThreads)                                                                   \
-        k_aggregate_##NR(const LevelsArgs *__restrict__ A, const float4 *__restrict__ wts, int64_t wplane,           \
-                         const float4 *__restrict__ nrm, const int *skip)                                            \
+        NAME(const LevelsArgs *__restrict__ A, const float4 *__restrict__ wts, int64_t wplane,                       \
+             const float4 *__restrict__ nrm, const int *skip)                                                        \
     {                                                                                                                 \
         if (skip_now(skip)) return;                                                                                   \
-        aggregate_body<NR>(A, wts, wplane, nrm);                                                                     \
+        aggregate_body<NR, TAB>(A, wts, wplane, nrm);                                                                \
     }
-BEM_AGGREGATE_KERNEL(1)
-BEM_AGGREGATE_KERNEL(2)
-BEM_AGGREGATE_KERNEL(3)
-BEM_AGGREGATE_KERNEL(4)
+BEM_AGGREGATE_KERNEL(1, false, k_aggregate_1)
+BEM_AGGREGATE_KERNEL(2, false, k_aggregate_2)
+BEM_AGGREGATE_KERNEL(3, false, k_aggregate_3)
+BEM_AGGREGATE_KERNEL(4, false, k_aggregate_4)
+BEM_AGGREGATE_KERNEL(1, true, k_aggregate_1t)
 #undef BEM_AGGREGATE_KERNEL
+
+// Stored phases of the aggregation (and, conjugated, of the
+// disaggregation) for every level, element and antipodal direction pair,
+// by the expression the products evaluate when they regenerate them:
+// ph[j][p] = (cos, sin) 2 pi t, t = (k / 2 pi)(z_c - x_j).s_p in turns;
+// the padding column of odd rows holds zero.
+__global__ void k_phase_table(PhaseTableArgs a)
+{
+    int l = 0;
+    while (l + 1 < a.nlev && (int)blockIdx.x >= a.start[l + 1]) ++l;
+    const PhaseLevel &L = a.lev[l];
+    const int64_t e0 = (int64_t)((int)blockIdx.x - a.start[l]) * kPhaseElems;
+    const float kt = a.k * 0.15915494309189535f;
+    for (int p = threadIdx.x; p < L.phs; p += blockDim.x) {
+        const float4 sv = p < L.h ? L.dirs[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int u = 0; u < kPhaseElems; ++u) {
+            const int64_t j = e0 + u;
+            if (j >= a.n) break;
+            float2 v = make_float2(0.f, 0.f);
+            if (p < L.h) {
+                const float4 d = L.dz[j];
+                const float dx = kt * d.x, dy = kt * d.y, dzz = kt * d.z;
+                float sn0, cs0;
+                sincos_turns(fmaf(dx, sv.x, fmaf(dy, sv.y, dzz * sv.z)), &sn0, &cs0);
+                v = make_float2(cs0, sn0);
+            }
+            L.ph[j * L.phs + p] = v;
+        }
+    }
+}
 
 // sin / cos of 2 pi x by sincos_turns and by sincospif, for the unit tests.
 __global__ void k_selftest_sincos(const float *__restrict__ x, int64_t n, float4 *__restrict__ out)
@@ -1211,14 +1276,20 @@ BEM_TRANSFER_MULTI_KERNEL(4)
 // a.rowf[i] in place of 1 + s.n_i (the transposed product: two sums per
 // element, S0 = sum (1-part) and S1 = sum (s.n-part), combined as a S0 + b S1).
 constexpr int kDisPairChunk = 256;
-template <int NR, bool kRowF>
+template <int NR, bool kRowF, bool kTab>
 __device__ __forceinline__ void disaggregate_body(const DisaggArgs &a, const float2 *__restrict__ ynear,
                                                   float2 *__restrict__ y)
 {
     static_assert(!kRowF || NR == 1, "the transposed product has one right-hand side");
     constexpr int kS = kRowF ? 2 : 1;           // sums per element and plane
-    __shared__ float4 dir_s[kDisPairChunk];
-    __shared__ float4 ab_s[NR][kDisPairChunk];
+    // pairs per staged chunk; with stored phases the chunk's rows of them
+    // are staged too (row stride kChunk + 1: the 16 elements of a half-warp
+    // read one pair's phases from distinct banks)
+    constexpr int kChunk = kTab ? kDisTabChunk : kDisPairChunk;
+    static_assert(!kTab || kDisTabChunk <= kDisThreads, "the phase staging takes one pair per thread");
+    __shared__ float4 dir_s[kChunk];
+    __shared__ float4 ab_s[NR][kChunk];
+    __shared__ float2 ph_s[kTab ? kDisTask : 1][kTab ? kChunk + 1 : 1];
     __shared__ float2 red[kDisThreads][NR * kS];
     const int2 tk = a.tasks[blockIdx.x];
     const int64_t e0 = tk.x, e1 = tk.y;
@@ -1237,10 +1308,10 @@ __device__ __forceinline__ void disaggregate_body(const DisaggArgs &a, const flo
         if (f.il_ptr[c] == f.il_ptr[c + 1]) continue;   // no interaction list at this level
         const int h = f.nd / 2;
         const float kt = -f.k * 0.15915494309189535f;
-        const float4 dz = f.dz[e0 + q];                  // z_c - x_i
+        const float4 dz = kTab ? make_float4(0.f, 0.f, 0.f, 0.f) : f.dz[e0 + q];   // z_c - x_i
         const float dx = kt * dz.x, dy = kt * dz.y, dzz = kt * dz.z;
-        for (int p0 = 0; p0 < h; p0 += kDisPairChunk) {
-            const int np = min(kDisPairChunk, h - p0);
+        for (int p0 = 0; p0 < h; p0 += kChunk) {
+            const int np = min(kChunk, h - p0);
             __syncthreads();
             // per antipodal pair: s_p and, with lp = w Lambda(s_p), lm =
             // w Lambda(-s_p), A = lp + lm and B = lp - lm, so that
@@ -1255,12 +1326,33 @@ __device__ __forceinline__ void disaggregate_body(const DisaggArgs &a, const flo
                     ab_s[r][i] = make_float4(lp.x + lm.x, lp.y + lm.y, lp.x - lm.x, lp.y - lm.y);
                 }
             }
+            if (kTab) {
+                // the task's rows of the chunk's phases (coalesced along the pairs)
+                const float2 *__restrict__ src = f.ph + e0 * f.phs + p0;
+                // (np <= blockDim.x: one pair per thread, every row's load in flight together)
+                if (threadIdx.x < np) {
+                    float2 v[kDisTask];
+#pragma unroll
+                    for (int qq = 0; qq < kDisTask; ++qq)
+                        if (qq < cnt) v[qq] = ld_stream2(src + (int64_t)qq * f.phs + threadIdx.x);
+#pragma unroll
+                    for (int qq = 0; qq < kDisTask; ++qq)
+                        if (qq < cnt) ph_s[qq][threadIdx.x] = v[qq];
+                }
+            }
             __syncthreads();
             if (!act) continue;
             for (int i = sl; i < np; i += nsl) {
                 const float4 sv = dir_s[i];
                 float sn0, cs0;
-                sincos_turns(fmaf(dx, sv.x, fmaf(dy, sv.y, dzz * sv.z)), &sn0, &cs0);
+                if (kTab) {
+                    // the phase of (x_i - z_c).s is the conjugate of the stored one
+                    const float2 e = ph_s[q][i];
+                    cs0 = e.x;
+                    sn0 = -e.y;
+                } else {
+                    sincos_turns(fmaf(dx, sv.x, fmaf(dy, sv.y, dzz * sv.z)), &sn0, &cs0);
+                }
                 const float tn = fmaf(n.x, sv.x, fmaf(n.y, sv.y, n.z * sv.z));
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
@@ -1310,12 +1402,19 @@ __device__ __forceinline__ void disaggregate_body(const DisaggArgs &a, const flo
                                                                         float2 *__restrict__ y, const int *skip)     \
     {                                                                                                               \
         if (skip_now(skip)) return;                                                                                 \
-        disaggregate_body<NR, false>(a, ynear, y);                                                                  \
+        disaggregate_body<NR, false, false>(a, ynear, y);                                                           \
     }
 BEM_DISAGG_KERNEL(1)
 BEM_DISAGG_KERNEL(2)
 BEM_DISAGG_KERNEL(4)
 #undef BEM_DISAGG_KERNEL
+
+__global__ void __launch_bounds__(kDisThreads) k_disaggregate_m1t(DisaggArgs a, const float2 *__restrict__ ynear,
+                                                                  float2 *__restrict__ y, const int *skip)
+{
+    if (skip_now(skip)) return;
+    disaggregate_body<1, false, true>(a, ynear, y);
+}
 
 // The disaggregation of the transposed product: row factor a_i + b_i (s.n_i)
 // from a.rowf (see k_prep_t).
@@ -1323,7 +1422,14 @@ __global__ void __launch_bounds__(kDisThreads) k_disaggregate_t(DisaggArgs a, co
                                                                 float2 *__restrict__ y, const int *skip)
 {
     if (skip_now(skip)) return;
-    disaggregate_body<1, true>(a, ynear, y);
+    disaggregate_body<1, true, false>(a, ynear, y);
+}
+
+__global__ void __launch_bounds__(kDisThreads) k_disaggregate_tt(DisaggArgs a, const float2 *__restrict__ ynear,
+                                                                 float2 *__restrict__ y, const int *skip)
+{
+    if (skip_now(skip)) return;
+    disaggregate_body<1, true, true>(a, ynear, y);
 }
 
 // Translation table per distinct offset X (Eq. FMMBase):

@@ -93,6 +93,7 @@ struct AggTask {
 // one block of kDisThreads threads each.
 constexpr int kDisTask = 16;
 constexpr int kDisThreads = 128;
+constexpr int kDisTabChunk = 128;   // direction pairs per staged chunk when the phases are stored
 
 struct FarArgs {
     int nd;                  // 2 L^2 directions
@@ -111,7 +112,31 @@ struct FarArgs {
     const float4 *dz;        // per element: z_c - x_j
     const int *elem_cl;      // per element: cluster at this level
     int64_t mplane, lplane;  // stride (in float2) between the right-hand sides' M and Lam planes
+    // stored phases of this level (null when the products regenerate them):
+    // ph[j * phs + p] = (cos, sin) of k (z_c - x_j).s_p for every element j
+    // and antipodal pair p < nd / 2, rows padded to the even length phs
+    const float2 *ph;
+    int phs;
 };
+
+// Stored far-field phases of every level of a plan, built in one launch
+// (k_phase_table): block b fills kPhaseElems elements of level l, where
+// start[l] <= b < start[l + 1].
+constexpr int kPhaseElems = 16;
+struct PhaseLevel {
+    const float4 *dz;        // z_c - x_j per element
+    const float4 *dirs;      // (s, w) per direction
+    float2 *ph;              // [n][phs]
+    int h, phs;              // antipodal pairs, row length (h rounded up to even)
+};
+struct PhaseTableArgs {
+    int64_t n;
+    float k;
+    int nlev;
+    PhaseLevel lev[kMaxFarLevels];
+    int start[kMaxFarLevels + 1];
+};
+__global__ void k_phase_table(PhaseTableArgs a);
 
 // All far levels of a plan, for the kernels that run every level in one launch.
 struct LevelsArgs {
@@ -242,6 +267,8 @@ __global__ void k_aggregate_1(const LevelsArgs *A, const float4 *wts, int64_t wp
 __global__ void k_aggregate_2(const LevelsArgs *A, const float4 *wts, int64_t wplane, const float4 *nrm, const int *skip);
 __global__ void k_aggregate_3(const LevelsArgs *A, const float4 *wts, int64_t wplane, const float4 *nrm, const int *skip);
 __global__ void k_aggregate_4(const LevelsArgs *A, const float4 *wts, int64_t wplane, const float4 *nrm, const int *skip);
+// One right-hand side, with the level's stored phases (FarArgs::ph).
+__global__ void k_aggregate_1t(const LevelsArgs *A, const float4 *wts, int64_t wplane, const float4 *nrm, const int *skip);
 constexpr int kMaxPlanes = 4;            // right-hand sides per multi-plane launch
 // Aggregation on the tensor cores (bem_tc.cu): tasks of one element chunk
 // and kTcPairs direction pairs, split-BF16 operands, FP32 accumulation;
@@ -272,6 +299,10 @@ __global__ void k_disaggregate_m1(DisaggArgs a, const float2 *ynear, float2 *y, 
 __global__ void k_disaggregate_m2(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
 __global__ void k_disaggregate_m4(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
 __global__ void k_disaggregate_t(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
+// One right-hand side (m1t) and the transposed product (tt) with the levels'
+// stored phases (FarArgs::ph), staged per chunk of kDisTabChunk pairs.
+__global__ void k_disaggregate_m1t(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
+__global__ void k_disaggregate_tt(DisaggArgs a, const float2 *ynear, float2 *y, const int *skip);
 // largest expansion length of the translation tables (shared-memory rows)
 constexpr int kMaxTableL = 255;
 // Translation tables of every far level: block b serves offset

@@ -196,10 +196,10 @@ def test_solve_and_field_match_oracle(bem):
 
 @pytest.mark.parametrize("restart", [4, 6, 7])
 def test_restarted_gmres_matches_oracle(bem, restart):
-    """GMRES restarted every 4, 6 or 7 steps (the Arnoldi steps run as
-    graphs of four, and the next graph is queued before the previous one's
-    status is read, so cycles end inside and at the end of graphs): several
-    restarts, and the solution still matches the oracle's."""
+    """GMRES restarted every 4, 6 or 7 steps (each cycle is one graph whose
+    device-side loop runs bodies of four Arnoldi steps, so cycles end inside
+    and at the end of a body): several restarts, and the solution still
+    matches the oracle's."""
     nodes, tris = inputs.icosphere(3, 0.1)
     freq = 1000.0
     mesh = bem.Mesh(nodes, tris, restart=restart)
@@ -209,6 +209,35 @@ def test_restarted_gmres_matches_oracle(bem, restart):
     assert info["converged"] and info["restarts"] >= 1, info
     po, qo, _ = oracle.solve(nodes, tris, freq, c=C, rho=RHO, sources=[("plane", (0, 0, 1.0), 1.0)])
     _check(p.cpu().numpy(), po, 1e-4, 1e-3, "restarted GMRES(%d)" % restart)
+
+
+@pytest.mark.parametrize("restart", [6, 100])
+def test_device_loop_matches_stepwise_loop(bem, restart):
+    """The cycle's graph, whose WHILE node repeats bodies of four Arnoldi
+    steps until the device sets its condition to 0, against the same solve
+    with event timing on, where the host runs one step at a time and reads
+    the state after each: the same number of products and restarts, and the
+    same solution up to the order of the FP64 atomic sums in the
+    Gram-Schmidt step (FMM product with far pairs, 1280 elements at 3 kHz)."""
+    nodes, tris = inputs.icosphere(3, 0.1)
+    src = [bem.plane_wave((0, 0, 1))]
+    res = []
+    for timed in (False, True):
+        mesh = bem.Mesh(nodes, tris, restart=restart, trunc_factor=6.0)
+        bem.timing_enable(timed)
+        try:
+            p, q, info = mesh.solve(3000.0, src, tol=1e-6, c=C, rho=RHO)
+            if timed:
+                # one status read per step: every Gram-Schmidt launch timed
+                assert bem.timing_get("k_gs_dots")[1] == info["iterations"]
+        finally:
+            bem.timing_enable(False)
+            mesh.close()
+        assert info["converged"], info
+        res.append((p.cpu().numpy(), info))
+    (pg, ig), (pt, it) = res
+    assert abs(ig["iterations"] - it["iterations"]) <= 1 and ig["restarts"] == it["restarts"], (ig, it)
+    assert _rel(pg, pt) < 1e-5
 
 
 @pytest.mark.parametrize("tf,l2,el", [(1.8, 2e-3, 2e-2), (6.0, 1e-4, 1e-3)])
@@ -527,6 +556,48 @@ def test_transposed_product_matches_oracle(bem, mode):
         yt = mesh.matvec_transpose(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy()
         mesh.close()
         _check(yt, yo, l2, el, "transposed fmm product, factor %g" % tf)
+
+
+def test_stored_phases_match_regenerated(bem):
+    """far_table 1 (the phases of T and S computed once per frequency and
+    read by the single-right-hand-side products) against far_table 0 (the
+    same phases regenerated in every product), with mixed boundary
+    conditions on 5120 elements at 2 kHz (three levels): the forward and the
+    transposed product agree to rounding, and the forward product with
+    stored phases meets the oracle's rows at the truncation bound of its
+    factor.  k_phase_table runs (once per plan built) only when the phases
+    are stored; several right-hand sides regenerate them."""
+    nodes, tris = inputs.icosphere(4, 0.1)
+    n = tris.shape[0]
+    freq = 2000.0
+    k = 2 * np.pi * freq / C
+    bct, region, adm = _mixed_bc(n, 7)
+    x = inputs.random_complex(n, 23)
+    xt = torch.tensor(x, dtype=torch.complex64, device="cuda")
+    out = {}
+    for ft in (0, 1):
+        mesh = bem.Mesh(nodes, tris, bc_type=bct, region=region, trunc_factor=6.0, far_table=ft)
+        bem.timing_enable(True)
+        try:
+            assert mesh.stats(freq, c=C)["levels"] >= 2
+            y = mesh.matvec(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy()
+            tables = bem.timing_get("k_phase_table")[1]
+            yt = mesh.matvec_transpose(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy()
+            Y = mesh.matvec(freq, torch.stack([xt, xt]), admittance=adm, c=C, rho=RHO).cpu().numpy()
+        finally:
+            bem.timing_enable(False)
+            mesh.close()
+        assert (tables > 0) == (ft == 1), (ft, tables)   # one per plan built (the autotuner's trials too)
+        out[ft] = (y, yt, Y)
+    (y0, yt0, Y0), (y1, yt1, Y1) = out[0], out[1]
+    _check(y1, y0, 1e-6, 1e-5, "forward product, stored against regenerated phases")
+    _check(yt1, yt0, 1e-6, 1e-5, "transposed product, stored against regenerated phases")
+    for r in range(2):
+        _check(Y1[r], y1, 1e-6, 1e-5, "two right-hand sides (regenerated phases) against one (stored)")
+    rows = np.arange(0, n, 37)
+    cp, cq = _oracle_coeffs(bct, region, adm, k)
+    yo = oracle.matvec_rows(nodes, tris, k, cp, cq, x, rows)
+    _check(y1[rows], yo, 1e-4, 1e-3, "forward product with stored phases, oracle rows")
 
 
 def test_transposed_product_from_stored_values(bem):

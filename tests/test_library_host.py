@@ -45,6 +45,7 @@ def test_params_default_are_the_papers(lib):
     assert abs(p.admissibility - 2 / np.sqrt(3)) < 1e-15
     assert p.tau == 1.0          # exterior problem unless asked otherwise
     assert p.row_scaling == 0    # no preconditioner unless asked (Sec. 3.2: an option)
+    assert p.far_table == 0      # phases of T and S regenerated in every product (faster on this GPU)
 
 
 @pytest.mark.parametrize("rs", [-1, 2])
@@ -52,6 +53,13 @@ def test_row_scaling_other_than_zero_or_one_is_rejected(lib, rs):
     nodes, tris = inputs.icosphere(1, 0.1)
     with pytest.raises(bemfmm.BemError):
         bemfmm.Mesh(nodes, tris, row_scaling=rs)
+
+
+@pytest.mark.parametrize("ft", [-1, 2])
+def test_far_table_other_than_zero_or_one_is_rejected(lib, ft):
+    nodes, tris = inputs.icosphere(1, 0.1)
+    with pytest.raises(bemfmm.BemError, match="far_table"):
+        bemfmm.Mesh(nodes, tris, far_table=ft)
 
 
 @pytest.mark.parametrize("tau", [0.0, 0.5, -2.0, float("nan")])
