@@ -174,6 +174,8 @@ def run_ours(args):
     pts = W["field_points"]
     src = [bemfmm.plane_wave(W["plane_dir"], W["amp"])]
     mkw = {"trunc_factor": args.trunc_factor, "near_chunk": args.near_chunk, "far_table": args.far_table}
+    if args.no_graphs:
+        mkw["graphs"] = 0
     if args.restart > 0:
         mkw["restart"] = args.restart
     if args.leaf_edge > 0:
@@ -340,6 +342,7 @@ def run_ours(args):
                    "mesh": "icosphere r=0.1 m",
                    "source": "plane wave +z", "field_points": int(pts.shape[0]), "gmres_tol": args.tol,
                    "trunc_factor": args.trunc_factor, "near_chunk": args.near_chunk, "far_table": args.far_table,
+                   "gmres_graphs": not args.no_graphs,
                    "l2_flush": ("256 MB write between steps" if args.no_sweep else
                                 "256 MB write before the sweep; per step the stored near field (8 B x near_nnz, "
                                 "> L2) is streamed again"),
@@ -922,6 +925,8 @@ def main():
                     help="one bem_solve call per frequency (default: the steps as one bem_solve_sweep call)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="head_bands_c3: the automatic leaf size without the timing autotuner")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="GMRES steps launched one at a time (for the ncu launch list: ncu does not profile the kernels inside conditional graph nodes)")
     ap.add_argument("--far-table", type=int, default=0, choices=(0, 1),
                     help="1: far-field phases stored once per frequency (default 0: regenerated per product)")
     ap.add_argument("--near-chunk", type=int, default=0,

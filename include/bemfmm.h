@@ -161,6 +161,12 @@ typedef struct bem_params {
                                the products regenerate, so the results are the same.
                                Products with several right-hand sides always regenerate them
                                (one phase serves all their planes).  Other values: BEM_E_ARG. */
+    int32_t graphs;         /* GMRES launches: 1 (default) each restart cycle is one CUDA graph
+                               launch (a conditional WHILE node over bodies of four Arnoldi
+                               steps, the condition set on the device); 0 the steps are launched
+                               one at a time with a status read after each (for profilers that
+                               do not see into conditional graph nodes).  Same kernels, same
+                               results.  Other values: BEM_E_ARG.                             */
 } bem_params;
 
 typedef struct bem_medium {

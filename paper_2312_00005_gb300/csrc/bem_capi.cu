@@ -1808,6 +1808,7 @@ void bem_params_default(bem_params *p)
     p->gs_rows = 0;
     p->field_mode = 0;
     p->far_table = 0;
+    p->graphs = 1;
 }
 
 const char *bem_last_error(void) { return g_err.c_str(); }
@@ -1839,6 +1840,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
         return set_err(BEM_E_ARG, "near_chunk must be 0 or an even number in 64..4096");
     if (p.field_mode < 0 || p.field_mode > 2) return set_err(BEM_E_ARG, "field_mode must be 0, 1 or 2");
     if (p.far_table != 0 && p.far_table != 1) return set_err(BEM_E_ARG, "far_table must be 0 or 1");
+    if (p.graphs != 0 && p.graphs != 1) return set_err(BEM_E_ARG, "graphs must be 0 or 1");
     if (p.gs_rows != 0 && (p.gs_rows < 64 || p.gs_rows > kGsMaxRows))
         return set_err(BEM_E_ARG, "gs_rows must be 0 or in 64..1024");
     if (p.block_jacobi && p.row_scaling)
@@ -2201,7 +2203,7 @@ GmresResult run_gmres(bem_mesh_impl &M, double tol, int32_t max_iter, bool trans
     const int *done = nr == 1 ? &M.st.p->skip_prod : &M.st.p->skip_all;
     // one Arnoldi step: product of v_j (inputs already formed), then the
     // Gram-Schmidt / Givens step, which also forms v_{j+1}
-    const bool use_graph = !g_timing;
+    const bool use_graph = !g_timing && M.prm.graphs != 0;
     // Arnoldi steps per graph (and per status read).  With event timing
     // on, one step per read and every kernel on one stream, so that each
     // kernel is timed alone and no timed launch is a skipped one.

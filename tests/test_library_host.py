@@ -46,6 +46,7 @@ def test_params_default_are_the_papers(lib):
     assert p.tau == 1.0          # exterior problem unless asked otherwise
     assert p.row_scaling == 0    # no preconditioner unless asked (Sec. 3.2: an option)
     assert p.far_table == 0      # phases of T and S regenerated in every product (faster on this GPU)
+    assert p.graphs == 1         # each GMRES restart cycle one graph launch
 
 
 @pytest.mark.parametrize("rs", [-1, 2])
@@ -60,6 +61,13 @@ def test_far_table_other_than_zero_or_one_is_rejected(lib, ft):
     nodes, tris = inputs.icosphere(1, 0.1)
     with pytest.raises(bemfmm.BemError, match="far_table"):
         bemfmm.Mesh(nodes, tris, far_table=ft)
+
+
+@pytest.mark.parametrize("g", [-1, 2])
+def test_graphs_other_than_zero_or_one_is_rejected(lib, g):
+    nodes, tris = inputs.icosphere(1, 0.1)
+    with pytest.raises(bemfmm.BemError, match="graphs"):
+        bemfmm.Mesh(nodes, tris, graphs=g)
 
 
 @pytest.mark.parametrize("tau", [0.0, 0.5, -2.0, float("nan")])
