@@ -669,7 +669,7 @@ def run_adjoint(args):
     Y = rng.uniform(0.0, 0.5, 8) * np.exp(1j * rng.uniform(-np.pi / 2, np.pi / 2, 8)) / (rho * c)
     pts = inputs.fibonacci_sphere(100, 1.0)
     src = [bemfmm.point_source(inputs.head_point_source(), 1.0)]
-    mkw = {"trunc_factor": args.trunc_factor}
+    mkw = {"trunc_factor": args.trunc_factor, "near_transpose": args.near_transpose}
     if args.restart > 0:
         mkw["restart"] = args.restart
     mesh = bemfmm.Mesh(nodes, tris, bc_type=np.full(n, bemfmm.ADMI, np.int32), region=region, **mkw)
@@ -697,8 +697,9 @@ def run_adjoint(args):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "dtype": "f32",
         "data": "synthetic", "all_converged": conv, "loss": L, "grad_abs_max": float(np.abs(g).max()),
         "forward_products": last[4]["iterations"],
-        "adjoint_near_part": "stored values read by column" if st["asymmetric_near_pairs"] == 0 else
-                             "recomputed by quadrature (near lists not symmetric)",
+        "adjoint_near_part": ("recomputed by quadrature (near lists not symmetric)" if st["asymmetric_near_pairs"]
+                              else "A^T stored in A's layout, streamed like A" if args.near_transpose
+                              else "stored values of A read by column"),
         "config": {"workload": "head_adjoint_c4", "n_elements": n, "freq_hz": f, "regions": 8,
                    "field_points": int(pts.shape[0]), "tol": args.tol, "trunc_factor": args.trunc_factor,
                    "source": "point, 1 mm off the surface at +y"},
@@ -927,6 +928,8 @@ def main():
                     help="head_bands_c3: the automatic leaf size without the timing autotuner")
     ap.add_argument("--no-graphs", action="store_true",
                     help="GMRES steps launched one at a time (for the ncu launch list: ncu does not profile the kernels inside conditional graph nodes)")
+    ap.add_argument("--near-transpose", type=int, default=1, choices=(0, 1),
+                    help="head_adjoint_c4: 1 A^T stored in A's layout for the adjoint products, 0 A read by column")
     ap.add_argument("--far-table", type=int, default=0, choices=(0, 1),
                     help="1: far-field phases stored once per frequency (default 0: regenerated per product)")
     ap.add_argument("--near-chunk", type=int, default=0,

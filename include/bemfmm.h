@@ -167,6 +167,13 @@ typedef struct bem_params {
                                one at a time with a status read after each (for profilers that
                                do not see into conditional graph nodes).  Same kernels, same
                                results.  Other values: BEM_E_ARG.                             */
+    int32_t near_transpose; /* transposed product (bem_matvec_transpose, the adjoint solve of
+                               bem_admittance_gradient) with the stored near field: 1 (default)
+                               A^T is stored once per frequency in the layout of A (8 bytes
+                               per stored value more, made from A's values when the near lists
+                               are symmetric) and streamed like A; 0 A's values are read by
+                               column.  Results agree to the rounding of the sums.  Other
+                               values: BEM_E_ARG.                                             */
 } bem_params;
 
 typedef struct bem_medium {

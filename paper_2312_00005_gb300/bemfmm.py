@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
         ("check_orientation", ctypes.c_int32), ("symmetric_far", ctypes.c_int32),
         ("block_jacobi", ctypes.c_int32), ("far_precision", ctypes.c_int32), ("near_chunk", ctypes.c_int32),
         ("gs_rows", ctypes.c_int32), ("field_mode", ctypes.c_int32), ("far_table", ctypes.c_int32),
-        ("graphs", ctypes.c_int32),
+        ("graphs", ctypes.c_int32), ("near_transpose", ctypes.c_int32),
     ]
 
 

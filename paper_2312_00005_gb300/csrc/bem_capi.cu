@@ -287,6 +287,7 @@ struct Lists {
     DevArr<int64_t> trow_off;
     bool tsym = false, trow_checked = false, trow_ready = false;
     std::vector<int64_t> h_row_ptr;
+    std::vector<int> h_trow_ptr;  // host copy of trow_ptr
     // block-Jacobi sub-blocks (first element, size, offset of the inverse)
     std::vector<int4> h_bj;
     DevArr<int4> bj;
@@ -351,6 +352,8 @@ struct Plan {
     DevArr<LevelsArgs> largs;     // device copy of the per-level arguments
     LevelsArgs hargs;
     DevArr<float2> val;
+    DevArr<float2> valT;          // A^T in A's layout (near_transpose), made from val
+    bool valT_valid = false;
     bool has_phases = false;      // every level's stored phases built (far_table)
     std::vector<float> val_key;   // host copy of the coefficients the stored values were made with
     bool val_valid = false;
@@ -1166,6 +1169,7 @@ void ensure_near_values(bem_mesh_impl &M, const Coeffs &C)
         return;
     }
     if (P.val_valid && key == P.val_key) return;
+    P.valT_valid = false;
     store_near(M, P, fr(M).cp.p, fr(M).cq.p);
     P.val_key.swap(key);
     P.val_valid = true;
@@ -1441,11 +1445,46 @@ void ensure_transposed_rows(bem_mesh_impl &M)
     }
     cudaStream_t s = fr(M).s;
     Ls.trow_ptr.upload(rptr, s);
+    Ls.h_trow_ptr = rptr;
     Ls.trow_i.upload(ri, s);
     Ls.trow_off.upload(roff, s);
     ck(cudaStreamSynchronize(s), "sync");
     Ls.tsym = true;
     Ls.trow_ready = true;
+}
+
+// A^T stored in A's layout (near_transpose), made from the stored values of
+// A once they exist and the transposed rows are listed: the transposed
+// product then streams it with the forward kernel instead of reading A's
+// columns.  Each leaf's transposed rows must fill exactly the stride of its
+// forward rows (they do when the near lists are symmetric); else nothing is
+// made and the product reads by column.  Not inside a graph capture (it
+// allocates).
+void ensure_transposed_values(bem_mesh_impl &M)
+{
+    ensure_transposed_rows(M);
+    Plan &P = *fr(M).plan;
+    const Lists &Ls = *P.lists;
+    if (M.prm.near_transpose != 1 || !Ls.trow_ready || !P.val_valid || P.valT_valid) return;
+    const Level &Lf = M.t.lv[Ls.fp.leaf_depth];
+    const int nl = (int)Lf.start.size();
+    if ((int)Ls.h_trow_ptr.size() != nl + 1) return;
+    for (int t = 0; t < nl; ++t) {
+        if (Lf.count[t] == 0) continue;
+        const int nk = Ls.h_trow_ptr[t + 1] - Ls.h_trow_ptr[t];
+        const int64_t i0 = Lf.start[t];
+        if ((int64_t)((nk + 1) & ~1) != Ls.h_row_ptr[i0 + 1] - Ls.h_row_ptr[i0]) return;
+    }
+    cudaStream_t s = fr(M).s;
+    P.valT.alloc(P.val.n);
+    {
+        KTimer kt_("k_near_transpose", s);
+        k_near_transpose<<<nl, 256, 0, s>>>(Ls.leaf_start.p, Ls.trow_ptr.p, Ls.trow_off.p, Ls.row_ptr.p, P.val.p,
+                                            P.valT.p);
+    }
+    ck_launch("k_near_transpose");
+    ck(cudaStreamSynchronize(s), "sync");
+    P.valT_valid = true;
 }
 
 // y = A^T x with the given column coefficients (the adjoint solve): the
@@ -1493,7 +1532,19 @@ void matvec_t_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, con
         ck_launch("k_transfer");
     }
     const Lists &Ls = *P.lists;
-    if (cp == fr(M).cp.p && cq == fr(M).cq.p && P.val_valid && M.prm.near_store && !P.fp().direct && Ls.trow_ready) {
+    const bool stored = cp == fr(M).cp.p && cq == fr(M).cq.p && P.val_valid && M.prm.near_store && !P.fp().direct;
+    const size_t xs_bytes = (size_t)Ls.max_ncol * sizeof(float2);
+    if (stored && P.valT_valid && xs_bytes <= 160 * 1024) {
+        // A^T stored in A's layout, streamed by the forward product's kernel
+        NearArgs na = near_args(M, P, cp, cq);
+        {
+            KTimer kt_("k_near_spmv_t", s);
+            if (Ls.n_spmv_items > 0)
+                k_near_spmv_items<<<Ls.n_spmv_items, kSpmvThreads, xs_bytes, s>>>(na, Ls.spmv_items.p, P.valT.p,
+                                                                                  M.xint.p, M.ynear.p, skip);
+        }
+        ck_launch("k_near_spmv_t");
+    } else if (stored && Ls.trow_ready) {
         // the stored values of A (made with these coefficients), read by column
         {
             KTimer kt_("k_near_spmv_t", s);
@@ -1809,6 +1860,7 @@ void bem_params_default(bem_params *p)
     p->field_mode = 0;
     p->far_table = 0;
     p->graphs = 1;
+    p->near_transpose = 1;
 }
 
 const char *bem_last_error(void) { return g_err.c_str(); }
@@ -1841,6 +1893,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
     if (p.field_mode < 0 || p.field_mode > 2) return set_err(BEM_E_ARG, "field_mode must be 0, 1 or 2");
     if (p.far_table != 0 && p.far_table != 1) return set_err(BEM_E_ARG, "far_table must be 0 or 1");
     if (p.graphs != 0 && p.graphs != 1) return set_err(BEM_E_ARG, "graphs must be 0 or 1");
+    if (p.near_transpose != 0 && p.near_transpose != 1) return set_err(BEM_E_ARG, "near_transpose must be 0 or 1");
     if (p.gs_rows != 0 && (p.gs_rows < 64 || p.gs_rows > kGsMaxRows))
         return set_err(BEM_E_ARG, "gs_rows must be 0 or in 64..1024");
     if (p.block_jacobi && p.row_scaling)
@@ -2037,7 +2090,7 @@ int bem_matvec_transpose(void *mesh, double freq_hz, const bem_medium *medium, c
             k_gather<<<nblocks(M.n, 256), 256, 0, M.s>>>((const float2 *)x_dev, M.perm.p, M.n, M.tmp.p);
         }
         ck_launch("k_gather");
-        ensure_transposed_rows(M);
+        ensure_transposed_values(M);
         matvec_t_internal(M, fr(M).cp.p, fr(M).cq.p, M.tmp.p, (float2 *)y_dev, true, false, nullptr, M.s);
         check_err(M);
         join_streams(M.s, us);
@@ -3294,7 +3347,7 @@ int bem_admittance_gradient(void *mesh, double freq_hz, const bem_medium *medium
         }
         ck_launch("k_field_t");
         // adjoint solve A^T lambda = F^T conj(f) (lambda in uvec)
-        ensure_transposed_rows(M);
+        ensure_transposed_values(M);
         GmresResult R = run_gmres(M, tol, max_iter, true);
         // aq = A_q^T lambda: the transposed product with c^p = 0 and c^q = 1
         // (tau folded in as for the unknowns' coefficients)

@@ -402,6 +402,27 @@ __global__ void __launch_bounds__(kSpmvThreads) k_near_spmv_items(NearArgs a, co
     }
 }
 
+// A^T from the stored values of A, in A's layout: the rows j of leaf t, each
+// padded to an even length ncp (the stride of t's rows), take at column c
+// the value A_i,j of t's c-th transposed row i, which sits at trow_off[k0 +
+// c] + (j - t0).  Threads take consecutive columns of a row (coalesced
+// writes); the reads are the scattered column segments.
+__global__ void k_near_transpose(const int64_t *__restrict__ leaf_start, const int *__restrict__ trow_ptr,
+                                 const int64_t *__restrict__ trow_off, const int64_t *__restrict__ row_ptr,
+                                 const float2 *__restrict__ val, float2 *__restrict__ valT)
+{
+    const int t = blockIdx.x;
+    const int64_t t0 = leaf_start[t];
+    const int nt = (int)(leaf_start[t + 1] - t0);
+    const int k0 = trow_ptr[t], nk = trow_ptr[t + 1] - k0;
+    const int ncp = (nk + 1) & ~1;
+    const int64_t total = (int64_t)nt * ncp;
+    for (int64_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int jj = (int)(idx / ncp), c = (int)(idx - (int64_t)jj * ncp);
+        valT[row_ptr[t0 + jj] + c] = c < nk ? val[trow_off[k0 + c] + jj] : make_float2(0.f, 0.f);
+    }
+}
+
 // Transposed near-field product from the stored values (the near relation
 // of the leaves being symmetric): for the elements j of leaf t = blockIdx.x,
 //   y_j = sum_{s in near(t)} sum_{i in s} A_ij x_i,

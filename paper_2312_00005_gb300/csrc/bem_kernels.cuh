@@ -188,6 +188,13 @@ __global__ void k_near_spmv_items(NearArgs a, const int4 *items, const float2 *v
 constexpr int kSpmvTThreads = 256;
 __global__ void k_near_spmv_t(const int64_t *leaf_start, const int *trow_ptr, const int *trow_i,
                               const int64_t *trow_off, const float2 *val, const float2 *x, float2 *y, const int *skip);
+// A^T in the layout of A (the near relation of the leaves being symmetric,
+// row j of leaf t has the same near columns in both): column c of t's rows
+// takes A_i,j for the c-th transposed row i of t (trow_*); pad columns 0.
+// One block per leaf; the forward product k_near_spmv_items then streams
+// valT as it streams val.
+__global__ void k_near_transpose(const int64_t *leaf_start, const int *trow_ptr, const int64_t *trow_off,
+                                 const int64_t *row_ptr, const float2 *val, float2 *valT);
 // The same for nr <= kMaxPlanes right-hand sides (planes `plane` elements
 // apart in x and y): the stored values are streamed once for all of them.
 // The leaf's columns are staged in chunks of cw (even) columns: dynamic

@@ -605,12 +605,14 @@ def test_stored_phases_match_regenerated(bem):
 
 def test_transposed_product_from_stored_values(bem):
     """With symmetric far verdicts every near leaf pair has its mirror, so
-    bem_matvec_transpose reads the stored values of A by column
-    (k_near_spmv_t) instead of recomputing them: equal to the recomputed
-    transposed product (near_store = 0) up to rounding order, within the
-    truncation of the oracle's A^T x, and the exact transpose of bem_matvec
-    (z.(A^T x) = x.(A z) to FP32 rounding).  5120 elements, 2 kHz, mixed
-    boundary conditions, three far levels."""
+    bem_matvec_transpose takes its near part from the stored values of A
+    instead of recomputing them: by default A^T made once in A's layout
+    (k_near_transpose) and streamed like A, with near_transpose = 0 A's
+    values read by column (k_near_spmv_t).  Both equal the recomputed
+    transposed product (near_store = 0) up to rounding order, lie within the
+    truncation of the oracle's A^T x, and are the exact transpose of
+    bem_matvec (z.(A^T x) = x.(A z) to FP32 rounding).  5120 elements,
+    2 kHz, mixed boundary conditions, three far levels."""
     nodes, tris = inputs.icosphere(4, 0.1)
     n = tris.shape[0]
     freq = 2000.0
@@ -628,16 +630,28 @@ def test_transposed_product_from_stored_values(bem):
     az = mesh.matvec(freq, zt, admittance=adm, c=C, rho=RHO).cpu().numpy()
     bem.timing_enable(True)
     try:
-        before = bem.timing_get("k_near_spmv_t")[1]
         y1 = mesh.matvec_transpose(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy()
-        assert bem.timing_get("k_near_spmv_t")[1] == before + 1
+        y1b = mesh.matvec_transpose(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy()
+        assert bem.timing_get("k_near_spmv_t")[1] == 2
+        assert bem.timing_get("k_near_transpose")[1] == 1     # made once, reused
+    finally:
+        bem.timing_enable(False)
+    mesh.close()
+    assert np.array_equal(y1, y1b)
+    mesh = bem.Mesh(nodes, tris, near_transpose=0, **kw)
+    mesh.matvec(freq, zt, admittance=adm, c=C, rho=RHO)
+    bem.timing_enable(True)
+    try:
+        y2 = mesh.matvec_transpose(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy()
+        assert bem.timing_get("k_near_transpose")[1] == 0 and bem.timing_get("k_near_spmv_t")[1] == 1
     finally:
         bem.timing_enable(False)
     mesh.close()
     mesh = bem.Mesh(nodes, tris, near_store=0, **kw)
     y0 = mesh.matvec_transpose(freq, xt, admittance=adm, c=C, rho=RHO).cpu().numpy()
     mesh.close()
-    _check(y1, y0, 1e-6, 5e-5, "transposed product, stored vs recomputed near part")
+    _check(y1, y0, 1e-6, 5e-5, "transposed product, stored A^T vs recomputed near part")
+    _check(y2, y0, 1e-6, 5e-5, "transposed product, A read by column vs recomputed near part")
     _check(y1, yo, 1e-4, 1e-3, "transposed product from stored values vs oracle")
     lhs, rhs = np.dot(z, y1), np.dot(x, az)
     print("z.(A^T x) %s, x.(A z) %s" % (lhs, rhs))

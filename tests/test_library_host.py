@@ -47,6 +47,7 @@ def test_params_default_are_the_papers(lib):
     assert p.row_scaling == 0    # no preconditioner unless asked (Sec. 3.2: an option)
     assert p.far_table == 0      # phases of T and S regenerated in every product (faster on this GPU)
     assert p.graphs == 1         # each GMRES restart cycle one graph launch
+    assert p.near_transpose == 1 # A^T stored for the transposed product
 
 
 @pytest.mark.parametrize("rs", [-1, 2])
@@ -61,6 +62,13 @@ def test_far_table_other_than_zero_or_one_is_rejected(lib, ft):
     nodes, tris = inputs.icosphere(1, 0.1)
     with pytest.raises(bemfmm.BemError, match="far_table"):
         bemfmm.Mesh(nodes, tris, far_table=ft)
+
+
+@pytest.mark.parametrize("v", [-1, 2])
+def test_near_transpose_other_than_zero_or_one_is_rejected(lib, v):
+    nodes, tris = inputs.icosphere(1, 0.1)
+    with pytest.raises(bemfmm.BemError, match="near_transpose"):
+        bemfmm.Mesh(nodes, tris, near_transpose=v)
 
 
 @pytest.mark.parametrize("g", [-1, 2])
