@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <functional>
 #include <thread>
 #include <unordered_map>
 #include <cstdio>
@@ -431,67 +432,138 @@ void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k,
         for (int c = 0; c < nc; ++c) r1sq[c] = r1 * std::sqrt(L.amax[c]);
         const int Rb = 2 * rnear_prev + 1;           // candidate offsets lie in [-Rb, Rb]^3
         const int W = 2 * Rb + 1;
-        // per offset: -2 unknown, -1 not far by offset, >= 0 offset index (far-capable)
-        std::vector<int32_t> off_state((size_t)W * W * W, -2);
-        std::vector<double> off_dist((size_t)W * W * W, 0.0);
-        std::vector<int32_t> ncur_ptr(nc + 1, 0), ncur;
-        std::vector<int32_t> il_src, il_off;
-        il_src.reserve(16 * nc);
-        ncur.reserve(16 * nc);
-        int rnear = 0;
-        for (int c = 0; c < nc; ++c) {
-            const int par = L.parent[c];
-            for (int q = nprev_ptr[par]; q < nprev_ptr[par + 1]; ++q) {
-                const int sp = nprev[q];
-                for (int s = P.child0[sp]; s < P.child0[sp] + P.nchild[sp]; ++s) {
-                    const int dx = L.ix[c] - L.ix[s], dy = L.iy[c] - L.iy[s], dz = L.iz[c] - L.iz[s];
-                    bool far = false;
-                    int oi = -1;
-                    if (!fp.direct && (dx | dy | dz) != 0) {
-                        const size_t key = ((size_t)(dx + Rb) * W + (dy + Rb)) * W + (dz + Rb);
-                        int32_t &st = off_state[key];
-                        if (st == -2) {
+        // The clusters in contiguous ranges, scanned in parallel; each range
+        // keeps its lists with far entries tagged by offset key, and the keys
+        // in the order it first met them.  The merge below visits the ranges
+        // in order, so offset rows and verdicts come out in the order of a
+        // scan of the clusters one by one.
+        struct Part {
+            std::vector<int32_t> il_src, ncur, il_cnt, n_cnt;
+            std::vector<int64_t> il_key;
+            std::vector<int64_t> met;           // keys in the order first met
+            std::vector<char> met_ok;           // their stability verdicts
+            std::vector<int64_t> first_far;     // keys in the order of their first far use
+            int rnear = 0;
+        };
+        const int nthr = nc >= 2048 ? (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency())) : 1;
+        std::vector<Part> parts(nthr);
+        auto scan = [&](int c0, int c1, Part &pt) {
+            // per offset: -2 unknown, -1 not far by offset (unstable), -3 far-capable
+            std::vector<int8_t> st_loc((size_t)W * W * W, -2);
+            std::vector<char> used_loc((size_t)W * W * W, 0);
+            pt.il_cnt.assign(c1 - c0, 0);
+            pt.n_cnt.assign(c1 - c0, 0);
+            for (int c = c0; c < c1; ++c) {
+                const int par = L.parent[c];
+                int nfar = 0, nnear = 0;
+                for (int q = nprev_ptr[par]; q < nprev_ptr[par + 1]; ++q) {
+                    const int sp = nprev[q];
+                    for (int s = P.child0[sp]; s < P.child0[sp] + P.nchild[sp]; ++s) {
+                        const int dx = L.ix[c] - L.ix[s], dy = L.iy[c] - L.iy[s], dz = L.iz[c] - L.iz[s];
+                        bool far = false;
+                        int64_t key = -1;
+                        if (!fp.direct && (dx | dy | dz) != 0) {
+                            key = ((int64_t)(dx + Rb) * W + (dy + Rb)) * W + (dz + Rb);
+                            int8_t &stl = st_loc[(size_t)key];
                             const double X[3] = {dx * L.box, dy * L.box, dz * L.box};
                             const double dist = norm3(X);
-                            off_dist[key] = dist;
-                            if (p.stability_max >= 1e300) {
-                                st = -3;
-                            } else {
-                                const bool ok = hankel_growth(k * dist, F.L) <= p.stability_max;
-                                st = ok ? -3 : -1;
-                                fp.verdicts.push_back(Verdict{d, dx, dy, dz, F.L, ok});
+                            if (stl == -2) {
+                                const bool ok = p.stability_max >= 1e300 || hankel_growth(k * dist, F.L) <= p.stability_max;
+                                stl = ok ? -3 : -1;
+                                pt.met.push_back(key);
+                                pt.met_ok.push_back(ok ? 1 : 0);
+                            }
+                            if (stl != -1) {
+                                // r~ of every element pair above R_1: bounded with the
+                                // source cluster's largest area, or with the larger
+                                // of both clusters' (symmetric_far: the same verdict
+                                // both ways, so the lists have mirrors)
+                                const double rb = p.symmetric_far ? std::max(r1sq[c], r1sq[s]) : r1sq[s];
+                                far = dist > p.admissibility * (L.rad[c] + L.rad[s]) &&
+                                      dist - L.crad[c] - L.crad[s] > rb;
                             }
                         }
-                        if (st != -1) {
-                            const double dist = off_dist[key];
-                            // r~ of every element pair above R_1: bounded with the
-                            // source cluster's largest area, or with the larger
-                            // of both clusters' (symmetric_far: the same verdict
-                            // both ways, so the lists have mirrors)
-                            const double rb = p.symmetric_far ? std::max(r1sq[c], r1sq[s]) : r1sq[s];
-                            far = dist > p.admissibility * (L.rad[c] + L.rad[s]) &&
-                                  dist - L.crad[c] - L.crad[s] > rb;
-                            if (far && st == -3) {
-                                // first far use of this offset: give it a translation row
-                                st = (int32_t)(F.offsets.size() / 3);
-                                F.offsets.push_back(dx * L.box);
-                                F.offsets.push_back(dy * L.box);
-                                F.offsets.push_back(dz * L.box);
+                        if (far) {
+                            pt.il_src.push_back(s);
+                            pt.il_key.push_back(key);
+                            if (!used_loc[(size_t)key]) {
+                                used_loc[(size_t)key] = 1;
+                                pt.first_far.push_back(key);
                             }
-                            oi = st;
+                            ++nfar;
+                        } else {
+                            pt.ncur.push_back(s);
+                            pt.rnear = std::max(pt.rnear, std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))));
+                            ++nnear;
                         }
-                    }
-                    if (far) {
-                        il_src.push_back(s);
-                        il_off.push_back(oi);
-                    } else {
-                        ncur.push_back(s);
-                        rnear = std::max(rnear, std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))));
                     }
                 }
+                pt.il_cnt[c - c0] = nfar;
+                pt.n_cnt[c - c0] = nnear;
             }
-            F.il_ptr[c + 1] = (int32_t)il_src.size();
-            ncur_ptr[c + 1] = (int32_t)ncur.size();
+        };
+        std::vector<int> cut(nthr + 1);
+        for (int q = 0; q <= nthr; ++q) cut[q] = (int)((int64_t)nc * q / nthr);
+        if (nthr == 1) {
+            scan(0, nc, parts[0]);
+        } else {
+            std::vector<std::thread> th;
+            for (int q = 0; q < nthr; ++q) th.emplace_back(scan, cut[q], cut[q + 1], std::ref(parts[q]));
+            for (auto &x : th) x.join();
+        }
+        // merge in cluster order: verdicts at the first meeting of each
+        // offset and translation rows at its first far use (short lists,
+        // serial), then every range's entries copied to their places
+        std::vector<int32_t> off_row((size_t)W * W * W, -1);
+        std::vector<char> seen((size_t)W * W * W, 0);
+        int rnear = 0;
+        std::vector<size_t> far_base(nthr + 1, 0), near_base(nthr + 1, 0);
+        for (int q = 0; q < nthr; ++q) {
+            const Part &pt = parts[q];
+            rnear = std::max(rnear, pt.rnear);
+            far_base[q + 1] = far_base[q] + pt.il_src.size();
+            near_base[q + 1] = near_base[q] + pt.ncur.size();
+            if (p.stability_max < 1e300)
+                for (size_t u = 0; u < pt.met.size(); ++u) {
+                    const int64_t key = pt.met[u];
+                    if (seen[(size_t)key]) continue;
+                    seen[(size_t)key] = 1;
+                    const int ddz = (int)(key % W) - Rb, ddy = (int)((key / W) % W) - Rb,
+                              ddx = (int)(key / ((int64_t)W * W)) - Rb;
+                    fp.verdicts.push_back(Verdict{d, ddx, ddy, ddz, F.L, pt.met_ok[u] != 0});
+                }
+            for (const int64_t key : pt.first_far) {
+                int32_t &row = off_row[(size_t)key];
+                if (row >= 0) continue;
+                const int ddz = (int)(key % W) - Rb, ddy = (int)((key / W) % W) - Rb,
+                          ddx = (int)(key / ((int64_t)W * W)) - Rb;
+                row = (int32_t)(F.offsets.size() / 3);
+                F.offsets.push_back(ddx * L.box);
+                F.offsets.push_back(ddy * L.box);
+                F.offsets.push_back(ddz * L.box);
+            }
+        }
+        std::vector<int32_t> ncur_ptr(nc + 1, 0), ncur(near_base[nthr]);
+        std::vector<int32_t> il_src(far_base[nthr]), il_off(far_base[nthr]);
+        auto place = [&](int q) {
+            const Part &pt = parts[q];
+            size_t fe = 0, ne = 0;
+            for (int c = cut[q]; c < cut[q + 1]; ++c) {
+                for (int u = 0; u < pt.il_cnt[c - cut[q]]; ++u, ++fe) {
+                    il_src[far_base[q] + fe] = pt.il_src[fe];
+                    il_off[far_base[q] + fe] = off_row[(size_t)pt.il_key[fe]];
+                }
+                for (int u = 0; u < pt.n_cnt[c - cut[q]]; ++u, ++ne) ncur[near_base[q] + ne] = pt.ncur[ne];
+                F.il_ptr[c + 1] = (int32_t)(far_base[q] + fe);
+                ncur_ptr[c + 1] = (int32_t)(near_base[q] + ne);
+            }
+        };
+        if (nthr == 1) {
+            place(0);
+        } else {
+            std::vector<std::thread> th;
+            for (int q = 0; q < nthr; ++q) th.emplace_back(place, q);
+            for (auto &x : th) x.join();
         }
         F.il_src.swap(il_src);
         F.il_off.swap(il_off);
@@ -500,22 +572,35 @@ void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k,
         nprev.swap(ncur);
         rnear_prev = rnear;
     }
-    // leaf near lists (sorted source leaves)
+    // leaf near lists (sorted source leaves): each leaf's sorted list takes
+    // the places of its unsorted one, so the leaves sort in parallel
     const Level &Lf = t.lv[D];
     const int nl = (int)Lf.start.size();
-    fp.near_ptr.assign(nl + 1, 0);
-    fp.near_src.clear();
-    fp.near_src.reserve(nprev.size());
-    fp.nnz = 0;
-    for (int c = 0; c < nl; ++c) {
-        const int b0 = nprev_ptr[c], b1 = nprev_ptr[c + 1];
-        std::vector<int32_t> v(nprev.begin() + b0, nprev.begin() + b1);
-        std::sort(v.begin(), v.end());
-        int64_t cols = 0;
-        for (int32_t s : v) { fp.near_src.push_back(s); cols += Lf.count[s]; }
-        fp.near_ptr[c + 1] = (int32_t)fp.near_src.size();
-        fp.nnz += cols * Lf.count[c];
+    fp.near_ptr = nprev_ptr;
+    fp.near_src = nprev;
+    const int nthl = nl >= 2048 ? (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency())) : 1;
+    std::vector<int64_t> nnz_part(nthl, 0);
+    auto sort_leaves = [&](int q) {
+        const int c0 = (int)((int64_t)nl * q / nthl), c1 = (int)((int64_t)nl * (q + 1) / nthl);
+        int64_t z = 0;
+        for (int c = c0; c < c1; ++c) {
+            const int b0 = fp.near_ptr[c], b1 = fp.near_ptr[c + 1];
+            std::sort(fp.near_src.begin() + b0, fp.near_src.begin() + b1);
+            int64_t cols = 0;
+            for (int u = b0; u < b1; ++u) cols += Lf.count[fp.near_src[u]];
+            z += cols * Lf.count[c];
+        }
+        nnz_part[q] = z;
+    };
+    if (nthl == 1) {
+        sort_leaves(0);
+    } else {
+        std::vector<std::thread> th;
+        for (int q = 0; q < nthl; ++q) th.emplace_back(sort_leaves, q);
+        for (auto &x : th) x.join();
     }
+    fp.nnz = 0;
+    for (int64_t z : nnz_part) fp.nnz += z;
     for (int d = 1; d <= D; ++d)
         if (far_all[d].n_inter > 0) {
             fp.far.push_back(std::move(far_all[d]));
