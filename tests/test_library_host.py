@@ -99,6 +99,22 @@ def test_plan_partitions_all_pairs(lib, lev, freq):
         assert L >= 8
 
 
+def test_plan_with_parallel_list_building_partitions_all_pairs(lib):
+    """69,620 elements at 16 kHz (leaf depth 6, 12,416 leaves): the list
+    builder scans every level of 2048 clusters or more in parallel ranges and
+    merges them; the near and far pairs still partition all N^2 pairs, and
+    with symmetric_far every verdict has its mirror."""
+    nodes, tris = inputs.bumpy_ellipsoid(59)
+    n = tris.shape[0]
+    for sym in (0, 1):
+        st = bemfmm.plan_stats_host(nodes, tris, 16000.0, params=bemfmm.default_params(trunc_factor=8.0,
+                                                                                           symmetric_far=sym))
+        assert st["leaf_level"] >= 6, st
+        assert st["near_nnz"] + st["far_pairs"] == n * n
+        if sym:
+            assert st["asymmetric_pairs"] == 0 and st["asymmetric_near_pairs"] == 0, st
+
+
 def test_plan_on_ragged_head_like_surface(lib):
     nodes, tris = inputs.bumpy_ellipsoid(13)      # 3380 triangles, uneven sizes
     n = tris.shape[0]
