@@ -590,7 +590,7 @@ def run_bands(args):
     # --restart / --no-block-jacobi say otherwise
     restart = args.restart if args.restart > 0 else min(1024, args.max_iter)
     mkw = dict(trunc_factor=args.trunc_factor, restart=restart, block_jacobi=0 if args.no_block_jacobi else 1,
-               autotune=0 if args.no_autotune else 1)
+               autotune=0 if args.no_autotune else 1, gs_rows=args.gs_rows)
     nodes, tris = inputs.bumpy_ellipsoid(bands[0][0])
     mesh = bemfmm.Mesh(nodes, tris, **mkw)
     mesh.solve_sweep(bands[0][1][:args.warmup], src, **kw)
@@ -636,6 +636,7 @@ def run_bands(args):
         "config": {"workload": "head_bands_c3", "frequencies": nfreq, "f_hz": [bands[0][1][0], bands[-1][1][-1]],
                    "bands": rows, "source": "point, 1 mm off the surface at +y", "tol": args.tol,
                    "gmres_restart": restart, "block_jacobi": mkw["block_jacobi"], "autotune": mkw["autotune"],
+                   "gs_rows": args.gs_rows,
                    "trunc_factor": args.trunc_factor, "field_points": int(pts.shape[0]),
                    "l2": "not flushed; every frequency computes fresh near-field entries"},
     }))
@@ -928,6 +929,8 @@ def main():
                     help="head_bands_c3: the automatic leaf size without the timing autotuner")
     ap.add_argument("--no-graphs", action="store_true",
                     help="GMRES steps launched one at a time (for the ncu launch list: ncu does not profile the kernels inside conditional graph nodes)")
+    ap.add_argument("--gs-rows", type=int, default=0,
+                    help="head_bands_c3: Gram-Schmidt rows per block (0: the library's choice, else 64..1024)")
     ap.add_argument("--near-transpose", type=int, default=1, choices=(0, 1),
                     help="head_adjoint_c4: 1 A^T stored in A's layout for the adjoint products, 0 A read by column")
     ap.add_argument("--far-table", type=int, default=0, choices=(0, 1),
