@@ -1458,8 +1458,8 @@ void ensure_transposed_rows(bem_mesh_impl &M)
 // product then streams it with the forward kernel instead of reading A's
 // columns.  Each leaf's transposed rows must fill exactly the stride of its
 // forward rows (they do when the near lists are symmetric); else nothing is
-// made and the product reads by column.  Not inside a graph capture (it
-// allocates).
+// made and the product reads by column, as it does when the device has no
+// room for A^T.  Not inside a graph capture (it allocates).
 void ensure_transposed_values(bem_mesh_impl &M)
 {
     ensure_transposed_rows(M);
@@ -1476,7 +1476,16 @@ void ensure_transposed_values(bem_mesh_impl &M)
         if ((int64_t)((nk + 1) & ~1) != Ls.h_row_ptr[i0 + 1] - Ls.h_row_ptr[i0]) return;
     }
     cudaStream_t s = fr(M).s;
-    P.valT.alloc(P.val.n);
+    try {
+        P.valT.alloc(P.val.n);
+    } catch (Fail &) {
+        // no room for A^T (8 bytes per stored value): the transposed
+        // product reads A by column instead
+        P.valT.release();
+        (void)cudaGetLastError();
+        g_err.clear();
+        return;
+    }
     {
         KTimer kt_("k_near_transpose", s);
         k_near_transpose<<<nl, 256, 0, s>>>(Ls.leaf_start.p, Ls.trow_ptr.p, Ls.trow_off.p, Ls.row_ptr.p, P.val.p,
