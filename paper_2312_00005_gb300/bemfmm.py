@@ -340,7 +340,15 @@ def field_plan_stats_host(nodes, tris, points, freq, c=343.0, params=None) -> di
 
 
 class Mesh:
-    """A surface mesh on the current CUDA device (App. A of the paper)."""
+    """A surface mesh on the current CUDA device (App. A of the paper).
+
+    nodes float64 [n_nodes, 3], tris int32 [n_tris, 3]; bc_type (VELO, PRES
+    or ADMI per element), bc_value (complex per element) and region (per
+    element, for admittances by region) as bem_mesh_create takes them.
+    params: a Params (the C struct bem_params), or keyword overrides of its
+    library defaults, e.g. Mesh(nodes, tris, trunc_factor=8.0,
+    block_jacobi=1, near_transpose=0); every field is described in
+    include/bemfmm.h."""
 
     def __init__(self, nodes, tris, bc_type=None, bc_value=None, region=None, params=None, **kw):
         L = lib()
