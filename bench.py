@@ -837,8 +837,21 @@ def run_multi(args):
     P = torch.empty((nr, n), dtype=torch.complex64, device=dev)
     Q = torch.empty((nr, n), dtype=torch.complex64, device=dev)
     kw = dict(tol=args.tol, max_iter=budget, c=c, rho=rho, p=P, q=Q)
+
+    def solve_all(fs):
+        # the four systems together (one product pass per GMRES step), or
+        # (--one-at-a-time) one bem_solve per right-hand side at the same
+        # frequency, each with the same budget of products
+        if not args.one_at_a_time:
+            return mesh.solve_multi(fs, src, **kw)[2]
+        infos = []
+        for r in range(nr):
+            _, _, info = mesh.solve(fs, [src[r]], tol=args.tol, max_iter=budget, c=c, rho=rho, p=P[r], q=Q[r])
+            infos.append(info)
+        return infos
+
     for w in range(args.warmup):
-        mesh.solve_multi(f + 0.25 * w, src, **kw)
+        solve_all(f + 0.25 * w)
     clk = Clocks(local)
     clk.start()
     tot_ms, prods, last = 0.0, 0, None
@@ -848,7 +861,7 @@ def run_multi(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, _, infos = mesh.solve_multi(fs, src, **kw)
+        infos = solve_all(fs)
         e1.record(stream)
         torch.cuda.synchronize()
         tot_ms += e0.elapsed_time(e1)
@@ -895,7 +908,9 @@ def run_multi(args):
                    "rhs": "4 plane waves, tetrahedral directions", "gmres_budget_products": budget,
                    "gmres_restart": restart, "block_jacobi": mkw["block_jacobi"], "gmres_tol": args.tol,
                    "trunc_factor": args.trunc_factor, "far_precision": args.far_precision,
-                   "near_chunk": args.near_chunk, "solve_call": "bem_solve_multi (4 right-hand sides together)"},
+                   "near_chunk": args.near_chunk,
+                   "solve_call": ("bem_solve per right-hand side (4 calls)" if args.one_at_a_time else
+                                  "bem_solve_multi (4 right-hand sides together)")},
     }))
 
 
@@ -929,6 +944,8 @@ def main():
                     help="head_bands_c3: the automatic leaf size without the timing autotuner")
     ap.add_argument("--no-graphs", action="store_true",
                     help="GMRES steps launched one at a time (for the ncu launch list: ncu does not profile the kernels inside conditional graph nodes)")
+    ap.add_argument("--one-at-a-time", action="store_true",
+                    help="bumpy158k_20k: one bem_solve per right-hand side instead of bem_solve_multi")
     ap.add_argument("--gs-rows", type=int, default=0,
                     help="head_bands_c3: Gram-Schmidt rows per block (0: the library's choice, else 64..1024)")
     ap.add_argument("--near-transpose", type=int, default=1, choices=(0, 1),
