@@ -690,14 +690,39 @@ def run_adjoint(args):
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
         conv = conv and last[4]["converged"]
-    mesh.close()
     L, g = last[0], last[1]
     ms = total_ms / args.steps
+
+    # the same gradient by central differences of the loss (a solve and a
+    # field evaluation per loss; 2 x 16 real parameters), timed on the host
+    # clock around the whole loop, for comparison with the adjoint
+    def loss(Yv):
+        p_, q_, _ = mesh.solve(f, src, admittance=Yv, tol=args.tol, c=c, rho=rho)
+        fl = mesh.evaluate(f, p_, q_, pts, src, c=c, rho=rho).cpu().numpy()
+        return float(np.sum(np.abs(fl) ** 2))
+
+    hstep = 0.05 * float(np.abs(Y).max())
+    loss(Y)                                  # warm-up (first use of the host copy path)
+    torch.cuda.synchronize()
+    t_fd = time.perf_counter()
+    g_fd = np.zeros(Y.shape[0], complex)
+    for r in range(Y.shape[0]):
+        for part in (1.0, 1j):
+            dY = np.zeros(Y.shape[0], complex)
+            dY[r] = part * hstep
+            dL = (loss(Y + dY) - loss(Y - dY)) / (2 * hstep)
+            g_fd[r] += dL if part == 1.0 else 1j * dL
+    torch.cuda.synchronize()
+    fd_ms = 1e3 * (time.perf_counter() - t_fd)
+    mesh.close()
     print(json.dumps({
         "metric": "admittance_gradients_per_s", "value": 1e3 / ms, "unit": "gradient/s", "higher_is_better": True,
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "dtype": "f32",
         "data": "synthetic", "all_converged": conv, "loss": L, "grad_abs_max": float(np.abs(g).max()),
         "forward_products": last[4]["iterations"],
+        "central_differences": {"ms": round(fd_ms, 2), "losses": 4 * Y.shape[0], "step": hstep,
+                                "adjoint_speedup": round(fd_ms / ms, 2),
+                                "rel_difference_to_adjoint": float(np.linalg.norm(g_fd - g) / np.linalg.norm(g))},
         "adjoint_near_part": ("recomputed by quadrature (near lists not symmetric)" if st["asymmetric_near_pairs"]
                               else "A^T stored in A's layout, streamed like A" if args.near_transpose
                               else "stored values of A read by column"),
