@@ -2,6 +2,7 @@
 // mesh set-up, per-frequency plans, the FMM matrix-vector product, the
 // device-resident GMRES driver and the field evaluation.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -139,6 +140,16 @@ cudaEvent_t pool_event()
 
 // Records an event pair around the kernel launched in its scope when timing
 // is on and the stream is not being captured.
+// NVTX range over a scope, so that profilers show the library's calls and
+// phases by name (without a tool attached a push or pop only checks a
+// function pointer).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 struct KTimer {
     const char *name;
     cudaStream_t s;
@@ -737,6 +748,7 @@ void take_spare(bem_mesh_impl &M, DevArr<float2> &dst, size_t count)
 // grids, translation tables (GPU), buffers and the kernel argument block.
 void finish_plan(bem_mesh_impl &M, Plan &Pl)
 {
+    NvtxRange nvtx_("plan: expansions and translation tables");
     Plan *P = &Pl;
     const double k = P->k;
     cudaStream_t s = fr(M).s;
@@ -1085,6 +1097,7 @@ void reset_err(bem_mesh_impl &M)
 // their own kernel.
 void store_near(bem_mesh_impl &M, Plan &P, const float2 *cp, const float2 *cq)
 {
+    NvtxRange nvtx_("near-field entries");
     if (!P.val.p) P.val.swap(M.spare_val);
     P.val.alloc((size_t)P.nnz());
     reset_err(M);
@@ -1601,6 +1614,7 @@ void matvec_t_internal(bem_mesh_impl &M, const float2 *cp, const float2 *cq, con
 // estimated solve time (entries + 40 products).  Runs once per mesh.
 void autotune_leaf_depth(bem_mesh_impl &M, double k)
 {
+    NvtxRange nvtx_("leaf-depth autotuner");
     M.tuned = true;
     if (!M.prm.autotune || M.prm.mode == BEM_MODE_DIRECT || M.prm.leaf_edge > 0 || M.n < 4096) return;
     const int64_t n = M.n;
@@ -1880,6 +1894,7 @@ int bem_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris, i
                     const int32_t *bc_type, const double *bc_value, const int32_t *region,
                     const bem_params *params, void **out)
 {
+    NvtxRange nvtx_("bem_mesh_create");
     if (!out) return set_err(BEM_E_ARG, "out is NULL");
     *out = nullptr;
     if (!nodes || !tris || n_nodes < 3 || n_tris < 1) return set_err(BEM_E_ARG, "empty mesh");
@@ -2058,6 +2073,7 @@ int bem_mesh_destroy(void *mesh)
 int bem_matvec(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
                int32_t n_regions, const void *x_dev, void *y_dev, int32_t n_rhs, void *stream)
 {
+    NvtxRange nvtx_("bem_matvec");
     if (!mesh || !x_dev || !y_dev || n_rhs < 1) return set_err(BEM_E_ARG, "bad argument");
     auto &M = *(bem_mesh_impl *)mesh;
     try {
@@ -2085,6 +2101,7 @@ int bem_matvec(void *mesh, double freq_hz, const bem_medium *medium, const doubl
 int bem_matvec_transpose(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
                          int32_t n_regions, const void *x_dev, void *y_dev, void *stream)
 {
+    NvtxRange nvtx_("bem_matvec_transpose");
     if (!mesh || !x_dev || !y_dev) return set_err(BEM_E_ARG, "bad argument");
     auto &M = *(bem_mesh_impl *)mesh;
     try {
@@ -2112,6 +2129,7 @@ int bem_matvec_transpose(void *mesh, double freq_hz, const bem_medium *medium, c
 int bem_matvec_host(void *mesh, double freq_hz, const bem_medium *medium, const double *admittance,
                     int32_t n_regions, const void *x_host, void *y_host, int32_t n_rhs, void *stream)
 {
+    NvtxRange nvtx_("bem_matvec_host");
     if (!mesh || !x_host || !y_host || n_rhs < 1) return set_err(BEM_E_ARG, "bad argument");
     auto &M = *(bem_mesh_impl *)mesh;
     try {
@@ -2677,8 +2695,11 @@ int solve_frame(bem_mesh_impl &M, double freq_hz, const bem_medium *medium, cons
         if (M.prm.far_precision != 1) precondition_rhs(M, M.bvec.p, nr);
         ck(cudaStreamSynchronize(s), "sync");
         auto t_rhs = std::chrono::steady_clock::now();
-        GmresResult R = M.prm.far_precision == 1 ? run_refined(M, tol, max_iter, nr)
-                                                 : run_gmres(M, tol, max_iter, false, nr);
+        GmresResult R;
+        {
+            NvtxRange nvtx_(M.prm.far_precision == 1 ? "refined GMRES" : "GMRES");
+            R = M.prm.far_precision == 1 ? run_refined(M, tol, max_iter, nr) : run_gmres(M, tol, max_iter, false, nr);
+        }
         check_tc_fault(M);
         auto t_gmres = std::chrono::steady_clock::now();
         // p and q in the caller's order
@@ -2761,6 +2782,7 @@ int bem_solve(void *mesh, double freq_hz, const bem_medium *medium, const double
               int32_t n_regions, const bem_source *srcs, int32_t n_src, double tol, int32_t max_iter,
               void *p_dev, void *q_dev, bem_solve_info *info, void *stream)
 {
+    NvtxRange nvtx_("bem_solve");
     auto t0 = std::chrono::steady_clock::now();
     if (!mesh || !p_dev || n_src < 0 || (n_src > 0 && !srcs) || !(tol > 0) || max_iter < 1)
         return set_err(BEM_E_ARG, "bad argument");
@@ -2783,6 +2805,7 @@ int bem_solve_multi(void *mesh, double freq_hz, const bem_medium *medium, const 
                     int32_t n_regions, const bem_source *srcs, int32_t n_rhs, double tol, int32_t max_iter,
                     void *p_dev, void *q_dev, bem_solve_info *infos, void *stream)
 {
+    NvtxRange nvtx_("bem_solve_multi");
     auto t0 = std::chrono::steady_clock::now();
     if (!mesh || !p_dev || n_rhs < 1 || n_rhs > kMaxPlanes || !srcs || !(tol > 0) || max_iter < 1)
         return set_err(BEM_E_ARG, "bad argument (n_rhs must be in 1..4)");
@@ -2806,6 +2829,7 @@ int bem_solve_sweep(void *mesh, const double *freqs_hz, int32_t n_freq, const be
                     int32_t max_iter, void *p_dev, void *q_dev, const double *pts, int64_t n_pts, void *field_dev,
                     bem_solve_info *infos, void *stream)
 {
+    NvtxRange nvtx_("bem_solve_sweep");
     if (!mesh || !freqs_hz || n_freq < 1 || !p_dev || n_src < 0 || (n_src > 0 && !srcs) || !(tol > 0) ||
         max_iter < 1 || n_pts < 0 || (n_pts > 0 && (!pts || !field_dev || !q_dev)))
         return set_err(BEM_E_ARG, "bad argument");
@@ -3170,6 +3194,7 @@ int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem
                  const void *p_dev, const void *q_dev, const double *pts, int64_t M_pts, void *out_dev,
                  void *stream)
 {
+    NvtxRange nvtx_("bem_evaluate");
     if (!mesh || !p_dev || !q_dev || !pts || M_pts < 0 || !out_dev || n_src < 0 || (n_src > 0 && !srcs))
         return set_err(BEM_E_ARG, "bad argument");
     if (M_pts == 0) return BEM_OK;
@@ -3248,6 +3273,7 @@ int bem_evaluate_velocity(void *mesh, double freq_hz, const bem_medium *medium, 
                           int32_t n_src, const void *p_dev, const void *q_dev, const double *pts, int64_t M_pts,
                           void *v_out_dev, void *stream)
 {
+    NvtxRange nvtx_("bem_evaluate_velocity");
     if (!mesh || !p_dev || !q_dev || !pts || M_pts < 0 || !v_out_dev || n_src < 0 || (n_src > 0 && !srcs))
         return set_err(BEM_E_ARG, "bad argument");
     if (M_pts == 0) return BEM_OK;
@@ -3318,6 +3344,7 @@ int bem_admittance_gradient(void *mesh, double freq_hz, const bem_medium *medium
                             int64_t n_pts, double tol, int32_t max_iter, void *p_dev, void *q_dev, double *loss,
                             double *grad, bem_solve_info *info, void *stream)
 {
+    NvtxRange nvtx_("bem_admittance_gradient");
     if (!mesh || !admittance || n_regions < 1 || n_src < 0 || (n_src > 0 && !srcs) || !pts || n_pts < 1 ||
         !(tol > 0) || max_iter < 1 || !p_dev || !q_dev || !loss || !grad)
         return set_err(BEM_E_ARG, "bad argument");
