@@ -526,6 +526,11 @@ double wavenumber(double f, double c) { return 2.0 * M_PI * f / c; }
 // ------------------------------------------------------------------ plan
 std::shared_ptr<Lists> upload_lists(bem_mesh_impl &M, FreqPlan &&fp)
 {
+    {
+        // the kernels index with these lists: check them on the host first
+        const std::string bad = validate_plan(M.t, fp);
+        if (!bad.empty()) throw Fail{set_err(BEM_E_INTERNAL, "plan check: " + bad)};
+    }
     auto Ls = std::make_shared<Lists>();
     Ls->fp = std::move(fp);
     const FreqPlan &F = Ls->fp;
@@ -3553,6 +3558,8 @@ int bem_plan_stats_host(const double *nodes, int64_t n_nodes, const int32_t *tri
         build_tree(g, leaf, t);
         FreqPlan fp;
         build_plan(g, t, p, wavenumber(freq_hz, c > 0 ? c : 343.0), fp);
+        const std::string bad = validate_plan(t, fp);
+        if (!bad.empty()) return set_err(BEM_E_INTERNAL, "plan check: " + bad);
         fill_stats(g, t, fp, p, out);
         return BEM_OK;
     } catch (std::bad_alloc &) {

@@ -608,6 +608,47 @@ void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k,
         }
 }
 
+std::string validate_plan(const Tree &t, const FreqPlan &fp)
+{
+    if (fp.leaf_depth < 0 || fp.leaf_depth >= (int)t.lv.size()) return "leaf depth out of range";
+    const Level &Lf = t.lv[fp.leaf_depth];
+    const int nl = (int)Lf.start.size();
+    if ((int)fp.near_ptr.size() != nl + 1 || fp.near_ptr[0] != 0) return "near list pointers of the wrong length";
+    if ((size_t)fp.near_ptr[nl] != fp.near_src.size()) return "near list pointers do not end at the entries";
+    int64_t nnz = 0;
+    for (int c = 0; c < nl; ++c) {
+        if (fp.near_ptr[c + 1] < fp.near_ptr[c]) return "near list pointers not monotone at leaf " + std::to_string(c);
+        bool self = Lf.count[c] == 0;
+        int64_t cols = 0;
+        for (int q = fp.near_ptr[c]; q < fp.near_ptr[c + 1]; ++q) {
+            const int s2 = fp.near_src[q];
+            if (s2 < 0 || s2 >= nl) return "near list of leaf " + std::to_string(c) + " names leaf " + std::to_string(s2);
+            self = self || s2 == c;
+            cols += Lf.count[s2];
+        }
+        if (!self) return "leaf " + std::to_string(c) + " is not in its own near list";
+        nnz += cols * Lf.count[c];
+    }
+    if (nnz != fp.nnz) return "near-field entry count disagrees with the lists";
+    for (const FarLevel &F : fp.far) {
+        if (F.depth < 1 || F.depth >= (int)t.lv.size()) return "far level depth out of range";
+        const int nc = (int)t.lv[F.depth].start.size();
+        if (F.nc != nc || (int)F.il_ptr.size() != nc + 1 || F.il_ptr[0] != 0)
+            return "interaction list pointers of the wrong length at depth " + std::to_string(F.depth);
+        if ((size_t)F.il_ptr[nc] != F.il_src.size() || F.il_src.size() != F.il_off.size())
+            return "interaction list pointers do not end at the entries at depth " + std::to_string(F.depth);
+        const int64_t noff = (int64_t)(F.offsets.size() / 3);
+        if (F.offsets.size() % 3 != 0) return "translation offsets not in triples";
+        for (int c = 0; c < nc; ++c)
+            if (F.il_ptr[c + 1] < F.il_ptr[c]) return "interaction list pointers not monotone";
+        for (size_t q = 0; q < F.il_src.size(); ++q) {
+            if (F.il_src[q] < 0 || F.il_src[q] >= nc) return "interaction list names a cluster out of range";
+            if (F.il_off[q] < 0 || F.il_off[q] >= noff) return "interaction list names a translation row out of range";
+        }
+    }
+    return "";
+}
+
 namespace {
 struct OffKey {
     int64_t x, y, z;

@@ -178,6 +178,12 @@ void set_last_error(const std::string &msg);
 // Builds near and interaction lists (Sec. 3.3.4) for wavenumber k.
 // leaf_depth < 0: the tree's own leaf depth; otherwise any depth 0..leaf_depth
 // (clusters at every depth are runs of the same element order).
+// Structural check of a plan before the device kernels index with it: every
+// list's pointer array monotone and of the right length, every leaf, cluster
+// and translation-row index in range, every leaf near itself, and nnz the
+// sum of its near blocks.  Returns an empty string or what is wrong.
+std::string validate_plan(const Tree &t, const FreqPlan &fp);
+
 void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k, FreqPlan &fp,
                 int leaf_depth = -1);
 
