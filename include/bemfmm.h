@@ -15,7 +15,8 @@
  *     truncation of Eq. FMMTruncation and the admissibility of
  *     Eq. Farfieldcond, per level (Sec. 3.3.4: operator
  *     N + sum_l S(l) D(l) T(l));
- *   - restarted GMRES on the device, optionally row-scaled (Sec. 3.2);
+ *   - restarted GMRES on the device, optionally row-scaled or block-Jacobi
+ *     preconditioned (Sec. 3.2);
  *   - beyond the paper: the transposed product and the adjoint gradient of a
  *     field loss with respect to the region admittances
  *     (bem_matvec_transpose, bem_admittance_gradient), and an opt-in check
@@ -306,8 +307,10 @@ int bem_matvec_host(void *mesh, double freq_hz, const bem_medium *medium,
 
 /* Solve Eq. SystemI at one frequency for the incident field of n_src
  * sources and the mesh's boundary data, with restarted GMRES on the device
- * (classical Gram-Schmidt with compensated FP32 sums, FP64 Hessenberg
- * matrix and Givens rotations; FP32 products).  Writes the
+ * (classical Gram-Schmidt with a second pass when the first cancels more
+ * than half of the vector, its sums FP64 additions of FP32 block partials;
+ * FP64 Hessenberg matrix and Givens rotations; FP32 products and basis;
+ * each restart cycle one CUDA graph launch, see bem_params.graphs).  Writes the
  * surface pressure p_dev and q_dev = dp/dn (device cf32 [n_tris] each, caller
  * order; q_dev may be NULL).  tol: relative residual target (e.g. 1e-6).
  * max_iter: cap on products.  info may be NULL.  Returns BEM_OK,
