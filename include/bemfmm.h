@@ -288,9 +288,11 @@ int bem_matvec(void *mesh, double freq_hz, const bem_medium *medium, const doubl
  * bem_plan_stats.asymmetric_pairs it takes the other direction's rule (the
  * plane-wave expansion where A used quadrature of a higher order, or the
  * reverse), which agree within the quadrature tolerance and the truncation.
- * Near part: the same entries as A: the stored values (near_store = 1) read
- * by column when every near leaf pair of the plan has its mirror, else
- * recomputed by quadrature in every call.  Far part (FMM mode): the antipodal symmetry of the sphere grid of
+ * Near part: the same entries as A: from the stored values (near_store = 1)
+ * when every near leaf pair of the plan has its mirror (A^T stored once per
+ * frequency in A's layout and streamed like A, near_transpose = 1, or A read
+ * by column, near_transpose = 0 or no room for A^T), else recomputed by
+ * quadrature in every call.  Far part (FMM mode): the antipodal symmetry of the sphere grid of
  * Sec. 3.3.3 and D(-X, s) = D(X, -s) in Eq. FMMBase make it the forward
  * aggregation of x with the source factor 1 - s.n, the forward transfer and
  * a disaggregation with A's column factor A_j (c^q_j - ik c^p_j s.n_j) as
