@@ -366,7 +366,8 @@ int bem_solve_sweep(void *mesh, const double *freqs_hz, int32_t n_freq, const be
  * p(x) = p_inc(x) + tau sum_j [H(x)_j p_j - G(x)_j q_j], element integrals by
  * the regular / quasi-singular rules measured from x.  p_dev, q_dev: device
  * cf32 [n_tris] (caller order, as written by bem_solve).  pts: host double
- * [M][3].  out_dev: device cf32 [M]. */
+ * [M][3].  out_dev: device cf32 [M].  M = 0 returns BEM_OK at once (pts and
+ * out_dev may then be NULL). */
 int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem_source *srcs,
                  int32_t n_src, const void *p_dev, const void *q_dev, const double *pts,
                  int64_t M, void *out_dev, void *stream);

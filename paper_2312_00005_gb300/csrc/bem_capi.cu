@@ -3200,9 +3200,10 @@ int bem_evaluate(void *mesh, double freq_hz, const bem_medium *medium, const bem
                  void *stream)
 {
     NvtxRange nvtx_("bem_evaluate");
-    if (!mesh || !p_dev || !q_dev || !pts || M_pts < 0 || !out_dev || n_src < 0 || (n_src > 0 && !srcs))
+    if (!mesh || !p_dev || !q_dev || M_pts < 0 || n_src < 0 || (n_src > 0 && !srcs))
         return set_err(BEM_E_ARG, "bad argument");
-    if (M_pts == 0) return BEM_OK;
+    if (M_pts == 0) return BEM_OK;   // nothing to evaluate (pts and out_dev may be NULL)
+    if (!pts || !out_dev) return set_err(BEM_E_ARG, "bad argument");
     auto &M = *(bem_mesh_impl *)mesh;
     try {
         double c, rho;
@@ -3279,9 +3280,10 @@ int bem_evaluate_velocity(void *mesh, double freq_hz, const bem_medium *medium, 
                           void *v_out_dev, void *stream)
 {
     NvtxRange nvtx_("bem_evaluate_velocity");
-    if (!mesh || !p_dev || !q_dev || !pts || M_pts < 0 || !v_out_dev || n_src < 0 || (n_src > 0 && !srcs))
+    if (!mesh || !p_dev || !q_dev || M_pts < 0 || n_src < 0 || (n_src > 0 && !srcs))
         return set_err(BEM_E_ARG, "bad argument");
-    if (M_pts == 0) return BEM_OK;
+    if (M_pts == 0) return BEM_OK;   // nothing to evaluate (pts and v_out_dev may be NULL)
+    if (!pts || !v_out_dev) return set_err(BEM_E_ARG, "bad argument");
     auto &M = *(bem_mesh_impl *)mesh;
     try {
         double c, rho;

@@ -194,6 +194,52 @@ def test_solve_and_field_match_oracle(bem):
     assert np.allclose(q.cpu().numpy(), 0)
 
 
+def _outward(nodes, tris):
+    """Faces of a convex closed surface wound so that their normals point away
+    from the centroid."""
+    c0 = nodes.mean(axis=0)
+    out = tris.copy()
+    for f, (a, b, c) in enumerate(tris):
+        nrm = np.cross(nodes[b] - nodes[a], nodes[c] - nodes[a])
+        if np.dot(nrm, nodes[[a, b, c]].mean(axis=0) - c0) < 0:
+            out[f] = (a, c, b)
+    return out
+
+
+def test_smallest_closed_surfaces_match_oracle(bem):
+    """A regular tetrahedron (4 triangles) and an octahedron (8), the smallest
+    closed surfaces, 5 cm across at 1 kHz: the product in direct and FMM mode
+    (no far pairs at this size, so the near field alone) against the
+    oracle's dense A x; the solve, whose Krylov space is exhausted after N
+    steps (N < the restart length), against the oracle's solve; an
+    evaluation at no points returns nothing."""
+    tet = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], float) * 0.025
+    tet_t = np.array([[0, 1, 2], [0, 3, 1], [0, 2, 3], [1, 3, 2]], np.int32)
+    octa = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], float) * 0.025
+    octa_t = np.array([[0, 2, 4], [2, 1, 4], [1, 3, 4], [3, 0, 4], [2, 0, 5], [1, 2, 5], [3, 1, 5], [0, 3, 5]],
+                      np.int32)
+    freq = 1000.0
+    k = 2 * np.pi * freq / C
+    src = [bem.plane_wave((0, 0, 1))]
+    for nodes, tris in ((tet, _outward(tet, tet_t)), (octa, _outward(octa, octa_t))):
+        n = tris.shape[0]
+        x = inputs.random_complex(n, 5)
+        xt = torch.tensor(x, dtype=torch.complex64, device="cuda")
+        yo = oracle.assemble(nodes, tris, k, np.ones(n, complex), np.zeros(n, complex)) @ x
+        po, qo, _ = oracle.solve(nodes, tris, freq, c=C, rho=RHO, sources=[("plane", (0, 0, 1.0), 1.0)])
+        for mode in (bem.MODE_DIRECT, bem.MODE_FMM):
+            mesh = bem.Mesh(nodes, tris, mode=mode)
+            try:
+                y = mesh.matvec(freq, xt, c=C, rho=RHO).cpu().numpy()
+                _check(y, yo, 2e-5, 2e-4, "N = %d product, mode %d" % (n, mode))
+                p, q, info = mesh.solve(freq, src, tol=1e-7, c=C, rho=RHO)
+                assert info["converged"] and info["iterations"] <= n + 1, info
+                _check(p.cpu().numpy(), po, 1e-4, 1e-3, "N = %d solve, mode %d" % (n, mode))
+                out = mesh.evaluate(freq, p, q, np.zeros((0, 3)), src, c=C, rho=RHO)
+                assert out.numel() == 0
+            finally:
+                mesh.close()
+
 @pytest.mark.parametrize("restart", [4, 6, 7])
 def test_restarted_gmres_matches_oracle(bem, restart):
     """GMRES restarted every 4, 6 or 7 steps (each cycle is one graph whose
