@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <exception>
 #include <functional>
 #include <thread>
 #include <unordered_map>
@@ -15,6 +16,41 @@
 namespace bem {
 
 namespace {
+// Runs fn(q) for q = 0 .. n - 1, on n threads when n > 1, and once every one
+// has finished rethrows the first exception any of them raised, so that a
+// failure in a worker (a host allocation) reaches the caller as it would from
+// a serial run.  A thread that cannot be started runs its share, and the
+// rest, on the calling thread.
+template <typename F>
+void run_parallel(int n, F &&fn)
+{
+    if (n <= 1) {
+        fn(0);
+        return;
+    }
+    std::vector<std::exception_ptr> err(n);
+    auto body = [&](int q) {
+        try {
+            fn(q);
+        } catch (...) {
+            err[q] = std::current_exception();
+        }
+    };
+    std::vector<std::thread> th;
+    th.reserve(n);
+    for (int q = 0; q < n; ++q) {
+        try {
+            th.emplace_back(body, q);
+        } catch (...) {
+            for (int r = q; r < n; ++r) body(r);
+            break;
+        }
+    }
+    for (auto &t : th) t.join();
+    for (auto &e : err)
+        if (e) std::rethrow_exception(e);
+}
+
 inline void sub3(const double *a, const double *b, double *o) { o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }
 inline double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 inline void cross3(const double *a, const double *b, double *o)
@@ -504,13 +540,7 @@ void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k,
         };
         std::vector<int> cut(nthr + 1);
         for (int q = 0; q <= nthr; ++q) cut[q] = (int)((int64_t)nc * q / nthr);
-        if (nthr == 1) {
-            scan(0, nc, parts[0]);
-        } else {
-            std::vector<std::thread> th;
-            for (int q = 0; q < nthr; ++q) th.emplace_back(scan, cut[q], cut[q + 1], std::ref(parts[q]));
-            for (auto &x : th) x.join();
-        }
+        run_parallel(nthr, [&](int q) { scan(cut[q], cut[q + 1], parts[q]); });
         // merge in cluster order: verdicts at the first meeting of each
         // offset and translation rows at its first far use (short lists,
         // serial), then every range's entries copied to their places
@@ -558,13 +588,7 @@ void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k,
                 ncur_ptr[c + 1] = (int32_t)(near_base[q] + ne);
             }
         };
-        if (nthr == 1) {
-            place(0);
-        } else {
-            std::vector<std::thread> th;
-            for (int q = 0; q < nthr; ++q) th.emplace_back(place, q);
-            for (auto &x : th) x.join();
-        }
+        run_parallel(nthr, place);
         F.il_src.swap(il_src);
         F.il_off.swap(il_off);
         F.n_inter = (int64_t)F.il_src.size();
@@ -592,13 +616,7 @@ void build_plan(const Geometry &g, const Tree &t, const bem_params &p, double k,
         }
         nnz_part[q] = z;
     };
-    if (nthl == 1) {
-        sort_leaves(0);
-    } else {
-        std::vector<std::thread> th;
-        for (int q = 0; q < nthl; ++q) th.emplace_back(sort_leaves, q);
-        for (auto &x : th) x.join();
-    }
+    run_parallel(nthl, sort_leaves);
     fp.nnz = 0;
     for (int64_t z : nnz_part) fp.nnz += z;
     for (int d = 1; d <= D; ++d)
@@ -858,13 +876,7 @@ std::string build_eval_plan(const Geometry &g, const Tree &t, const bem_params &
                 C.nnear[c - c0] = (int32_t)(C.ncur.size() - nn0);
             }
         };
-        if (nth == 1) {
-            run(0);
-        } else {
-            std::vector<std::thread> th;
-            for (int ti = 0; ti < nth; ++ti) th.emplace_back(run, ti);
-            for (auto &x : th) x.join();
-        }
+        run_parallel(nth, run);
         std::unordered_map<OffKey, int32_t, OffKeyHash> off_index;   // global index
         std::vector<int32_t> ncur_ptr(npc + 1, 0), ncur;
         int64_t rnear = 0;
